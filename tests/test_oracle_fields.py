@@ -1,0 +1,105 @@
+"""Pins for the oracle's fields: analytic SDFs against closed forms and finite
+differences; the MLP (value, gradient tangents and hand-written adjoint)
+against torch FP64 autograd on the same weights."""
+import numpy as np
+import pytest
+import torch
+
+import geraf_inputs as gi
+
+
+def _fd_grad(fn, x, h=1e-6):
+    g = np.zeros_like(x)
+    for d in range(3):
+        e = np.zeros_like(x); e[d] = h
+        g[d] = (fn(x + e) - fn(x - e)) / (2 * h)
+    return g
+
+
+def test_sphere_closed_form(oracle):
+    sc = gi.Scene([gi.Prim(gi.PRIM_SPHERE, 0.7, (0.01, -0.02, 0.15), (0.03, 0, 0))])
+    x = np.array([[0.01, 0.01, 0.01 + 0.05], [-0.02, -0.02, -0.02], [0.15, 0.15 + 0.02, 0.15]])
+    f, G, a = oracle.analytic_fields(sc, x)
+    np.testing.assert_allclose(f, [-0.03, 0.02 - 0.03, 0.05 - 0.03], atol=1e-15)
+    np.testing.assert_allclose(G[:, 1], [0, 0, 1], atol=1e-15)
+    np.testing.assert_allclose(G[:, 2], [1, 0, 0], atol=1e-15)
+    assert np.all(a == 0.7)
+
+
+@pytest.mark.parametrize("kind,p", [(gi.PRIM_SPHERE, (0.03, 0, 0)), (gi.PRIM_BOX, (0.02, 0.01, 0.015)),
+                                    (gi.PRIM_ELLIPSOID, (0.04, 0.02, 0.03)),
+                                    (gi.PRIM_HALFSPACE, (0.0, 0.6, -0.8))])
+def test_gradient_matches_finite_differences(oracle, kind, p):
+    sc = gi.Scene([gi.Prim(kind, 1.0, (0.005, -0.004, 0.15), p)])
+    rng = np.random.default_rng(3)
+    x = np.array([0.0, 0.0, 0.15])[:, None] + rng.uniform(-0.06, 0.06, size=(3, 400))
+    _, G, _ = oracle.analytic_fields(sc, x)
+    Gfd = _fd_grad(lambda y: oracle.analytic_fields(sc, y)[0], x)
+    # box SDF has gradient kinks on the medial axis: compare where smooth
+    ok = np.abs(Gfd - G).max(0) < 1e-4
+    assert ok.mean() > 0.97
+    if kind != gi.PRIM_ELLIPSOID:
+        np.testing.assert_allclose(np.linalg.norm(G, axis=0), 1.0, atol=1e-12)
+
+
+def test_box_and_ellipsoid_distances(oracle):
+    box = gi.Scene([gi.Prim(gi.PRIM_BOX, 1.0, (0, 0, 0.1), (0.02, 0.01, 0.03))])
+    x = np.array([[0.05, 0.0, 0.0, 0.03], [0.0, 0.0, 0.0, 0.02], [0.1, 0.1, 0.2, 0.1 + 0.04]])
+    f, _, _ = oracle.analytic_fields(box, x)
+    np.testing.assert_allclose(f, [0.03, -0.01, 0.07, np.sqrt(0.01**2 + 0.01**2 + 0.01**2)], atol=1e-15)
+    ell = gi.Scene([gi.Prim(gi.PRIM_ELLIPSOID, 1.0, (0, 0, 0.1), (0.04, 0.02, 0.03))])
+    # exact along the smallest semi-axis
+    x = np.array([[0.0, 0.0], [0.05, 0.01], [0.1, 0.1]])
+    f, _, _ = oracle.analytic_fields(ell, x)
+    np.testing.assert_allclose(f, [0.03, -0.01], atol=1e-15)
+
+
+def test_union_takes_nearest_primitive(oracle):
+    sc = gi.Scene([gi.Prim(gi.PRIM_SPHERE, 0.2, (0, 0, 0.1), (0.01, 0, 0)),
+                   gi.Prim(gi.PRIM_SPHERE, 0.9, (0, 0, 0.2), (0.01, 0, 0))])
+    x = np.array([[0.0, 0.0], [0.0, 0.0], [0.12, 0.17]])
+    f, G, a = oracle.analytic_fields(sc, x)
+    np.testing.assert_allclose(f, [0.01, 0.02], atol=1e-15)
+    np.testing.assert_allclose(a, [0.2, 0.9])
+    np.testing.assert_allclose(G[2], [1.0, -1.0])
+
+
+def _torch_mlp(spec, params, xyz):
+    """Independent autograd reference of the same network."""
+    shapes = spec.shapes()
+    p = torch.tensor(params.astype(np.float64), requires_grad=True)
+    x = torch.tensor(xyz.T.astype(np.float64), requires_grad=True)
+    c = torch.tensor(spec.center, dtype=torch.float64)
+    xt = (x - c) / spec.half
+    feats = []
+    for k in range(spec.n_levels):
+        feats.append(torch.sin((2.0 ** k) * np.pi * xt))
+        feats.append(torch.cos((2.0 ** k) * np.pi * xt))
+    z = torch.cat(feats, dim=1)
+    off = 0
+    for li, (o, i) in enumerate(shapes):
+        W = p[off:off + o * i].view(o, i); off += o * i
+        b = p[off:off + o]; off += o
+        z = z @ W.T + b
+        if li < len(shapes) - 1:
+            z = torch.nn.functional.softplus(z, beta=spec.beta, threshold=1e6)
+    f, a = z[:, 0], torch.sigmoid(z[:, 1])
+    G = torch.autograd.grad(f.sum(), x, create_graph=True)[0]
+    return p, f, G, a
+
+
+def test_mlp_matches_torch_autograd(oracle):
+    spec = gi.MLPSpec(n_levels=3, width=16, n_hidden=3, beta=20.0)
+    params = gi.mlp_init(spec, seed=5)
+    rng = np.random.default_rng(1)
+    xyz = (np.array(spec.center)[:, None] + rng.uniform(-0.05, 0.05, (3, 37))).astype(np.float32)
+    f, G, a, cache = oracle.mlp_forward(spec, params, xyz)
+    p, tf, tG, ta = _torch_mlp(spec, params, xyz)
+    np.testing.assert_allclose(f, tf.detach().numpy(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(a, ta.detach().numpy(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(G, tG.detach().numpy().T, rtol=1e-10, atol=1e-11)
+    d_f, d_G, d_a = rng.standard_normal(37), rng.standard_normal((3, 37)), rng.standard_normal(37)
+    gp = oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)
+    L = (tf * torch.tensor(d_f)).sum() + (tG * torch.tensor(d_G.T)).sum() + (ta * torch.tensor(d_a)).sum()
+    tgp = torch.autograd.grad(L, p)[0].numpy()
+    np.testing.assert_allclose(gp, tgp, rtol=1e-9, atol=1e-10 * np.abs(tgp).max())
