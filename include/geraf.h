@@ -1,0 +1,249 @@
+/*
+ * geraf.h — C ABI of the GB300 (sm_103a) lensless RF volumetric rendering
+ * hot path of GeRaF ("GeRaF: Neural Geometry Reconstruction from Radio
+ * Frequency Signals", arXiv 2605.29097).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller, who also
+ *   allocates every output. Nothing is allocated inside a call except where a
+ *   call says so; scratch memory is the caller's workspace `ws`.
+ * - Workspace protocol: calls taking (void* ws, size_t* ws_bytes) write the
+ *   bytes they need to *ws_bytes and return GERAF_OK without launching when
+ *   ws == NULL; otherwise *ws_bytes must hold at least that many bytes
+ *   (GERAF_ERR_WORKSPACE if not). `ws` must be 256-byte aligned.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call is asynchronous on that stream; none synchronises the device.
+ * - Layouts: FP32 structure-of-arrays. Positions/gradients are [3][n]
+ *   (all x, then all y, then all z). Complex arrays are interleaved FP32
+ *   (re, im) pairs, row-major [n_ant][n_f] for signals.
+ * - Sample points are depth-major: point index = k * n_ray + ray, ray index =
+ *   iy * nx + ix of the primary column.
+ * - Every call returns a geraf_status; on error nothing was launched (argument
+ *   errors) or the CUDA error is reported (GERAF_ERR_CUDA).
+ *   geraf_last_error_string() gives a one-line description of the last error
+ *   on the calling thread. No exception crosses the ABI.
+ * - Results are deterministic: no floating-point atomics; split reductions are
+ *   summed in a fixed order in FP64.
+ */
+#ifndef GERAF_H
+#define GERAF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GERAF_OK = 0,
+    GERAF_ERR_INVALID_ARG = 1,   /* null pointer, bad size or mode         */
+    GERAF_ERR_ALIGNMENT = 2,     /* pointer not aligned as documented      */
+    GERAF_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed   */
+    GERAF_ERR_WORKSPACE = 4,     /* workspace smaller than required        */
+    GERAF_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out     */
+    GERAF_ERR_UNSUPPORTED = 6    /* size or option outside the supported set */
+} geraf_status;
+
+/* Sample grid (section 6 "Primary Ray"): n[0] x n[1] primary columns parallel
+ * to +z over the face of an axis-aligned box, n[2] depths per column. Cell
+ * (ix, iy, k) spans lo + (i, i+1) * pitch on each axis. aperture_z is the
+ * plane (z) of the primary rays' start points x_apr. */
+typedef struct {
+    float lo[3];
+    float pitch[3];
+    int32_t n[3];
+    float aperture_z;
+} geraf_grid;
+
+/* Stepped frequencies f_n = f0 + n * df, n = 0 .. n_f-1 (section 3, Eq. fmcw:
+ * FMCW sample n of a chirp with slope k is the frequency f + k t_n). FP64.
+ * 1 <= n_f <= 1024, f0 > 0, df >= 0. */
+typedef struct {
+    double f0;
+    double df;
+    int32_t n_f;
+} geraf_band;
+
+enum { GERAF_SAMPLE_UNIFORM = 0, GERAF_SAMPLE_STRATIFIED = 1 };
+enum { GERAF_FIELD_ANALYTIC = 0, GERAF_FIELD_MLP = 1 };
+enum { GERAF_PREC_FP32 = 0, GERAF_PREC_BF16 = 1 };
+enum { GERAF_PRIM_SPHERE = 0, GERAF_PRIM_BOX = 1, GERAF_PRIM_ELLIPSOID = 2, GERAF_PRIM_HALFSPACE = 3 };
+enum { GERAF_RENDER_DIRECTIONAL = 1 };
+
+/* Field description for geraf_fields.
+ * ANALYTIC: `prims` points to n_prims records of 8 FP32 values
+ *   (kind, a, c[3], p[3]); sphere p[0] = radius, box p = half extents,
+ *   ellipsoid p = radii (first-order distance (|d/R| - 1) min R), half-space
+ *   c = point on the plane, p = unit normal towards free space. The scene SDF
+ *   is the minimum over primitives; G and a are the minimiser's.
+ * MLP: `params` points to the packed FP32 parameters
+ *   [W1 b1 ... W_nh b_nh W_head b_head], W row-major [out][in]; input is the
+ *   positional encoding (section 9.3) of (x - center)/half with n_levels
+ *   octaves (6 n_levels features: 6k+d = sin(2^k pi x_d), 6k+3+d = cos),
+ *   n_hidden softplus(beta) layers of `width`, head [f, a_logit],
+ *   a = sigmoid(a_logit). width must be 128 (the supported kernel shape). */
+typedef struct {
+    int32_t kind;
+    const float* prims;
+    int32_t n_prims;
+    const float* params;
+    int32_t n_levels;
+    int32_t width;
+    int32_t n_hidden;
+    float beta;
+    float center[3];
+    float half;
+    int32_t precision;
+} geraf_field_desc;
+
+const char* geraf_last_error_string(void);
+int32_t geraf_version(void);
+
+/*
+ * geraf_poll_device_error — synchronises `stream`, then reads and clears the
+ * device error word of the current device. Returns GERAF_ERR_TIMEOUT when a
+ * kernel gave up a bounded wait (a TMA copy or barrier that did not complete
+ * within ~2 s; the kernel then left without writing its outputs), GERAF_OK
+ * otherwise, GERAF_ERR_CUDA when synchronisation fails.
+ */
+geraf_status geraf_poll_device_error(void* stream);
+
+/*
+ * geraf_sample — lensless sampling (section 6 "Primary Ray"; section 4 step 1).
+ * Writes n_pts = n[0]*n[1]*n[2] points xyz [3][n_pts] (depth-major) and the
+ * n_ray = n[0]*n[1] primary-ray start points xyz_apr [3][n_ray] = (x, y,
+ * aperture_z). UNIFORM: cell centres. STRATIFIED: ray start jittered once per
+ * column (x, y) and depth jittered per point, U = (SplitMix64 output number
+ * (step<<42 | stream<<40 | index) of `seed`) >> 11 times 2^-53, streams
+ * 0 = x (index ray), 1 = y (index ray), 2 = z (index point). Each coordinate
+ * is float(lo + (i + U) * pitch) evaluated in FP64 with one rounding per
+ * operation, so results are bit-exact with any IEEE implementation.
+ * Errors: INVALID_ARG for null outputs, non-positive n or pitch, index space
+ * above 2^40 points or step >= 2^22.
+ */
+geraf_status geraf_sample(const geraf_grid* grid, int32_t mode, uint64_t seed, uint64_t step,
+                          float* xyz, float* xyz_apr, void* stream);
+
+/*
+ * geraf_fields — SDF f, its gradient G = grad f (section 5.2: the normal is
+ * the SDF gradient) and reflectiveness a at n points xyz [3][n].
+ * sdf [n], grad [3][n], refl [n] are outputs (grad and refl may be NULL for
+ * the ray-origin evaluations that need f only).
+ * MLP fields need `saved` (activations kept for the backward pass) of
+ * geraf_fields_saved_bytes() bytes, or NULL when no backward pass follows.
+ * Errors: INVALID_ARG (null/bad sizes), UNSUPPORTED (width != 128),
+ * WORKSPACE (saved too small).
+ */
+geraf_status geraf_fields_saved_bytes(const geraf_field_desc* desc, int64_t n, size_t* bytes);
+geraf_status geraf_fields(const geraf_field_desc* desc, const float* xyz, int64_t n,
+                          float* sdf, float* grad, float* refl, void* saved, size_t saved_bytes,
+                          void* stream);
+
+/*
+ * geraf_fields_backward — adjoint of the MLP fields (value, the three
+ * gradient tangents and the reflectiveness head) for upstream d_sdf [n],
+ * d_grad [3][n], d_refl [n] (any may be NULL = zero). Writes the parameter
+ * gradient d_params (same packed layout as params, overwritten, not
+ * accumulated). Needs the `saved` buffer of the matching geraf_fields call and
+ * a workspace (query with ws == NULL).
+ */
+geraf_status geraf_fields_backward(const geraf_field_desc* desc, const float* xyz, int64_t n,
+                                   const void* saved, const float* d_sdf, const float* d_grad,
+                                   const float* d_refl, float* d_params,
+                                   void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * geraf_blend — lensless alpha blending (section 5.2 "Discretization",
+ * section 6 "Lensless Alpha Blending", App. B).
+ * Inputs: sdf, refl [n_ray*n_z] depth-major; sdf_apr [n_ray] = f(x_apr);
+ * sdf_ant [n_ant] = f at the antennas; sharpness s > 0 of the logistic CDF
+ * Phi_s(x) = 1/(1+exp(-s x)); a_tx = A'_tx.
+ * Outputs [n_ray*n_z]: alpha_k = max((Phi(f_k)-Phi(f_{k+1}))/Phi(f_k), 0)
+ * (0 at the last depth), T_k = prod_{m<k}(1-alpha_m), w_k = a_k alpha_k A'_tx,
+ * t_eff_k = T_k + Phi_s(f(x_apr)); c_ant [n_ant] = Phi_s(f(x_ant)).
+ * Antenna i then sees T' = clamp(t_eff - c_ant_i, 0, 1) (App. B.2 integration;
+ * the origin terms carry no gradient, section 6).
+ */
+geraf_status geraf_blend(const float* sdf, const float* refl, int32_t n_ray, int32_t n_z,
+                         const float* sdf_apr, const float* sdf_ant, int32_t n_ant,
+                         float s, float a_tx,
+                         float* alpha, float* T, float* w, float* t_eff, float* c_ant, void* stream);
+
+/*
+ * geraf_blend_backward — adjoint of geraf_blend for upstream d_w, d_teff
+ * [n_ray*n_z] (either may be NULL = zero). Writes d_sdf, d_refl [n_ray*n_z]
+ * and d_scalars[2] = {dL/ds, dL/dA'_tx} (device, overwritten).
+ */
+geraf_status geraf_blend_backward(const float* sdf, const float* refl, const float* alpha,
+                                  const float* T, int32_t n_ray, int32_t n_z, float s, float a_tx,
+                                  const float* d_w, const float* d_teff,
+                                  float* d_sdf, float* d_refl, float* d_scalars,
+                                  void* ws, size_t* ws_bytes, void* stream);
+
+/*
+ * geraf_render — signal tracing (section 5.1, Eq. ref_sim; App. A.5-A.6,
+ * Algorithm 2 [1]) with the amplitude of Eq. signal_amp_tracing:
+ *   s(i, n) = sum_j A_ij exp(-j 2 pi f_n tau_ij),  tau_ij = 2 |x_j - a_i| / c,
+ *   A_ij = w_j T'_ij^2 gamma_ij D_ij,  gamma = 1/(4 pi r)^2,
+ *   T'_ij = clamp(t_eff_j - c_ant_i, 0, 1),
+ *   D_ij = max(0, 2 (n_j . w_ij)^2 - 1) with n_j = G_j/|G_j| (monostatic
+ *   shifted-Lambertian factor, section 3; D = 1 when G_j = 0 or without
+ *   GERAF_RENDER_DIRECTIONAL in flags).
+ * Inputs: xyz, grad [3][n_pts]; w, t_eff [n_pts]; ant_xyz [3][n_ant];
+ * c_ant [n_ant]; band. Output s_out [n_ant][n_f] complex (overwritten).
+ * Points must not coincide with antennas (r = 0 is clamped, result then
+ * meaningless). Workspace holds the packed point tiles and split partials.
+ */
+geraf_status geraf_render(const float* xyz, const float* grad, const float* w, const float* t_eff,
+                          int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                          const geraf_band* band, int32_t flags,
+                          void* ws, size_t* ws_bytes, float* s_out, void* stream);
+
+/*
+ * geraf_render_backward — adjoint of geraf_render (App. A.5, Algorithm 2
+ * [2]) for g_s = dL/dRe s + j dL/dIm s [n_ant][n_f] complex:
+ *   q_ij = sum_n Re(conj(g_in) exp(-j 2 pi f_n tau_ij)),
+ * then d_w_j = sum_i T'^2 gamma D q, d_teff_j = sum_i w 2 T' [0<=t_eff-c_ant<=1]
+ * gamma D q, d_grad_j = sum_i w T'^2 gamma q dD/dG. Outputs overwritten.
+ */
+geraf_status geraf_render_backward(const float* xyz, const float* grad, const float* w,
+                                   const float* t_eff, int64_t n_pts, const float* ant_xyz,
+                                   const float* c_ant, int32_t n_ant, const geraf_band* band,
+                                   int32_t flags, const float* g_s,
+                                   void* ws, size_t* ws_bytes,
+                                   float* d_w, float* d_teff, float* d_grad, void* stream);
+
+/*
+ * geraf_filter — matched filter heatmap (section 3, Eq. mf-sm; App. A.5,
+ * Algorithm 1 [1]) and the L2 heatmap loss (section 4 step 5):
+ *   M_v = sum_i sum_n s(i, n) exp(+j 2 pi f_n tau_iv),  P_v = |M_v|,
+ *   loss = sum_v m_v (P_v - P*_v)^2,  dloss_dP_v = 2 m_v (P_v - P*_v).
+ * Inputs: s [n_ant][n_f] complex, ant_xyz [3][n_ant], band, vox_xyz
+ * [3][n_vox]; target P* [n_vox] and mask m [n_vox] optional (NULL mask = 1).
+ * Outputs: P [n_vox], M [n_vox] complex (kept for the backward pass);
+ * loss (one double, device) and dloss_dP [n_vox] only when target != NULL
+ * (either output pointer may be NULL).
+ */
+geraf_status geraf_filter(const float* s, const float* ant_xyz, int32_t n_ant, const geraf_band* band,
+                          const float* vox_xyz, int64_t n_vox, const float* target, const float* mask,
+                          void* ws, size_t* ws_bytes,
+                          float* P, float* M, double* loss, float* dloss_dP, void* stream);
+
+/*
+ * geraf_filter_backward — adjoint of P = |M(s)| (App. A.5, Algorithm 1 [2])
+ * for upstream d_P [n_vox]:
+ *   g(i, n) = sum_v d_P_v (M_v/|M_v|) exp(-j 2 pi f_n tau_iv)
+ * (the printed gradient omits the M_v/|M_v| factor; a voxel with M_v = 0
+ * contributes 0). Output g_s [n_ant][n_f] complex (overwritten).
+ */
+geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const geraf_band* band,
+                                   const float* vox_xyz, int64_t n_vox, const float* M,
+                                   const float* d_P, void* ws, size_t* ws_bytes,
+                                   float* g_s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GERAF_H */

@@ -1,0 +1,15 @@
+"""GB300-native lensless RF volumetric rendering (GeRaF hot path).
+
+The compute path is the CUDA library ``libgeraf.so`` (C ABI in
+``include/geraf.h``); this package only marshals torch tensors to it.
+"""
+from .geraf import (AnalyticField, Band, MLPField, make_grid, geraf_sample, geraf_fields,
+                    geraf_fields_backward, geraf_blend, geraf_blend_backward, geraf_render,
+                    geraf_render_backward, geraf_filter, geraf_filter_backward, geraf_poll_device_error,
+                    SAMPLE_UNIFORM, SAMPLE_STRATIFIED, PREC_FP32, PREC_BF16)
+from ._lib import GerafError
+
+__all__ = ["AnalyticField", "Band", "MLPField", "make_grid", "geraf_sample", "geraf_fields",
+           "geraf_fields_backward", "geraf_blend", "geraf_blend_backward", "geraf_render",
+           "geraf_render_backward", "geraf_filter", "geraf_filter_backward", "geraf_poll_device_error",
+           "GerafError", "SAMPLE_UNIFORM", "SAMPLE_STRATIFIED", "PREC_FP32", "PREC_BF16"]

@@ -1,0 +1,278 @@
+// C-ABI entry points: argument validation, status codes, error strings and
+// dispatch to the kernels. No exception crosses this boundary.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace geraf {
+
+// implemented in fields_blend.cu, phasor.cu, mlp.cu
+geraf_status sample_impl(const geraf_grid*, int32_t, uint64_t, uint64_t, float*, float*, cudaStream_t);
+geraf_status analytic_fields_impl(const float*, int, const float*, int64_t, float*, float*, float*, cudaStream_t);
+geraf_status blend_impl(const float*, const float*, int32_t, int32_t, const float*, const float*, int32_t, float,
+                        float, float*, float*, float*, float*, float*, cudaStream_t);
+geraf_status blend_backward_impl(const float*, const float*, const float*, const float*, int32_t, int32_t, float,
+                                 float, const float*, const float*, float*, float*, float*, void*, size_t*,
+                                 cudaStream_t);
+geraf_status render_impl(const float*, const float*, const float*, const float*, int64_t, const float*,
+                         const float*, int32_t, const geraf_band*, int32_t, void*, size_t*, float*, cudaStream_t);
+geraf_status render_backward_impl(const float*, const float*, const float*, const float*, int64_t, const float*,
+                                  const float*, int32_t, const geraf_band*, int32_t, const float*, void*, size_t*,
+                                  float*, float*, float*, cudaStream_t);
+geraf_status filter_impl(const float*, const float*, int32_t, const geraf_band*, const float*, int64_t,
+                         const float*, const float*, void*, size_t*, float*, float*, double*, float*, cudaStream_t);
+geraf_status filter_backward_impl(const float*, int32_t, const geraf_band*, const float*, int64_t, const float*,
+                                  const float*, void*, size_t*, float*, cudaStream_t);
+geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
+geraf_status mlp_forward_impl(const geraf_field_desc*, const float*, int64_t, float*, float*, float*, void*, size_t,
+                              cudaStream_t);
+geraf_status mlp_backward_impl(const geraf_field_desc*, const float*, int64_t, const void*, const float*,
+                               const float*, const float*, float*, void*, size_t*, cudaStream_t);
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+geraf_status fail(geraf_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+geraf_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return GERAF_OK;
+    return fail(GERAF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+__device__ int g_device_error_word;
+
+static std::mutex g_dev_mu;
+static int* g_err_ptr[64];
+static int g_sm_count[64];
+
+static int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d < 64 ? d : 63;
+}
+
+int* device_error_word() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_err_ptr[d]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_error_word) == cudaSuccess) g_err_ptr[d] = static_cast<int*>(p);
+    }
+    return g_err_ptr[d];
+}
+
+int device_sm_count() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_sm_count[d]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 148;
+        g_sm_count[d] = n;
+    }
+    return g_sm_count[d];
+}
+
+bool make_band_k(const geraf_band* band, BandK* out) {
+    if (!band || band->n_f < 1 || !(band->f0 > 0.0) || !(band->df >= 0.0)) {
+        set_error("band: need n_f >= 1, f0 > 0, df >= 0");
+        return false;
+    }
+    const int g = (band->n_f + kBinsPerBlock - 1) / kBinsPerBlock;
+    if (g > 32) {
+        set_error("band: n_f = %d above the supported 1024", band->n_f);
+        return false;
+    }
+    memset(out, 0, sizeof(*out));
+    out->g = g;
+    for (int b = 0; b < g; ++b) {
+        const double K = 2.0 * (band->f0 + (double)(kBinsPerBlock * b) * band->df) / kC;
+        const float hi = (float)K;
+        out->k[2 * b] = hi;
+        out->k[2 * b + 1] = (float)(K - (double)hi);
+    }
+    out->kd = (float)(2.0 * band->df / kC);
+    return true;
+}
+
+}  // namespace geraf
+
+using namespace geraf;
+
+#define REQUIRE(cond, ...)                                      \
+    do {                                                        \
+        if (!(cond)) return fail(GERAF_ERR_INVALID_ARG, __VA_ARGS__); \
+    } while (0)
+
+static inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+static geraf_status check_ws(void* ws, size_t* ws_bytes) {
+    if (!ws_bytes) return fail(GERAF_ERR_INVALID_ARG, "ws_bytes must not be NULL");
+    if (ws && (reinterpret_cast<uintptr_t>(ws) & 255u))
+        return fail(GERAF_ERR_ALIGNMENT, "workspace must be 256-byte aligned");
+    return GERAF_OK;
+}
+
+extern "C" {
+
+const char* geraf_last_error_string(void) { return g_err; }
+
+int32_t geraf_version(void) { return 1; }
+
+geraf_status geraf_poll_device_error(void* stream) {
+    cudaError_t e = cudaStreamSynchronize(S(stream));
+    if (e != cudaSuccess) return cuda_status(e, "poll_device_error");
+    int* p = device_error_word();
+    if (!p) return fail(GERAF_ERR_CUDA, "device error word unavailable");
+    int v = 0;
+    e = cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e, "poll_device_error");
+    if (v) {
+        int z = 0;
+        cudaMemcpy(p, &z, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(GERAF_ERR_TIMEOUT, "a kernel gave up a bounded wait (device error word %d)", v);
+    }
+    return GERAF_OK;
+}
+
+geraf_status geraf_sample(const geraf_grid* grid, int32_t mode, uint64_t seed, uint64_t step, float* xyz,
+                          float* xyz_apr, void* stream) {
+    REQUIRE(grid && xyz, "sample: grid and xyz must not be NULL");
+    REQUIRE(mode == GERAF_SAMPLE_UNIFORM || mode == GERAF_SAMPLE_STRATIFIED, "sample: unknown mode %d", mode);
+    for (int d = 0; d < 3; ++d) {
+        REQUIRE(grid->n[d] > 0, "sample: n[%d] = %d must be positive", d, grid->n[d]);
+        REQUIRE(grid->pitch[d] > 0.0f, "sample: pitch[%d] must be positive", d);
+    }
+    const int64_t n = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
+    REQUIRE(n < (1ll << 40), "sample: %lld points exceed the 2^40 index space", (long long)n);
+    REQUIRE(step < (1ull << 22), "sample: step must be below 2^22");
+    return sample_impl(grid, mode, seed, step, xyz, xyz_apr, S(stream));
+}
+
+geraf_status geraf_fields_saved_bytes(const geraf_field_desc* desc, int64_t n, size_t* bytes) {
+    REQUIRE(desc && bytes && n >= 0, "fields_saved_bytes: bad arguments");
+    if (desc->kind == GERAF_FIELD_ANALYTIC) {
+        *bytes = 0;
+        return GERAF_OK;
+    }
+    return mlp_saved_bytes(desc, n, bytes);
+}
+
+geraf_status geraf_fields(const geraf_field_desc* desc, const float* xyz, int64_t n, float* sdf, float* grad,
+                          float* refl, void* saved, size_t saved_bytes, void* stream) {
+    REQUIRE(desc && xyz && sdf, "fields: desc, xyz and sdf must not be NULL");
+    REQUIRE(n >= 0, "fields: n must be >= 0");
+    if (n == 0) return GERAF_OK;
+    if (desc->kind == GERAF_FIELD_ANALYTIC) {
+        REQUIRE(desc->prims && desc->n_prims > 0 && desc->n_prims <= 1024, "fields: need 1..1024 primitives");
+        return analytic_fields_impl(desc->prims, desc->n_prims, xyz, n, sdf, grad, refl, S(stream));
+    }
+    REQUIRE(desc->kind == GERAF_FIELD_MLP, "fields: unknown kind %d", desc->kind);
+    REQUIRE(desc->params, "fields: params must not be NULL");
+    return mlp_forward_impl(desc, xyz, n, sdf, grad, refl, saved, saved_bytes, S(stream));
+}
+
+geraf_status geraf_fields_backward(const geraf_field_desc* desc, const float* xyz, int64_t n, const void* saved,
+                                   const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
+                                   void* ws, size_t* ws_bytes, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(desc && desc->kind == GERAF_FIELD_MLP, "fields_backward: needs an MLP field");
+    REQUIRE(n >= 1, "fields_backward: n must be >= 1");
+    if (ws) REQUIRE(xyz && saved && d_params && desc->params, "fields_backward: null input or output");
+    return mlp_backward_impl(desc, xyz, n, saved, d_sdf, d_grad, d_refl, d_params, ws, ws_bytes, S(stream));
+}
+
+geraf_status geraf_blend(const float* sdf, const float* refl, int32_t n_ray, int32_t n_z, const float* sdf_apr,
+                         const float* sdf_ant, int32_t n_ant, float s, float a_tx, float* alpha, float* T, float* w,
+                         float* t_eff, float* c_ant, void* stream) {
+    REQUIRE(n_ray >= 1 && n_z >= 1 && n_ant >= 0, "blend: bad sizes");
+    REQUIRE(sdf && refl && sdf_apr && alpha && T && w && t_eff, "blend: null input or output");
+    REQUIRE(n_ant == 0 || (sdf_ant && c_ant), "blend: null antenna arrays");
+    REQUIRE(s > 0.0f, "blend: sharpness s must be positive");
+    return blend_impl(sdf, refl, n_ray, n_z, sdf_apr, sdf_ant, n_ant, s, a_tx, alpha, T, w, t_eff, c_ant, S(stream));
+}
+
+geraf_status geraf_blend_backward(const float* sdf, const float* refl, const float* alpha, const float* T,
+                                  int32_t n_ray, int32_t n_z, float s, float a_tx, const float* d_w,
+                                  const float* d_teff, float* d_sdf, float* d_refl, float* d_scalars, void* ws,
+                                  size_t* ws_bytes, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_ray >= 1 && n_z >= 1, "blend_backward: bad sizes");
+    if (ws)
+        REQUIRE(sdf && refl && alpha && T && d_sdf && d_refl && d_scalars, "blend_backward: null input or output");
+    return blend_backward_impl(sdf, refl, alpha, T, n_ray, n_z, s, a_tx, d_w, d_teff, d_sdf, d_refl, d_scalars, ws,
+                               ws_bytes, S(stream));
+}
+
+geraf_status geraf_render(const float* xyz, const float* grad, const float* w, const float* t_eff, int64_t n_pts,
+                          const float* ant_xyz, const float* c_ant, int32_t n_ant, const geraf_band* band,
+                          int32_t flags, void* ws, size_t* ws_bytes, float* s_out, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_pts >= 1 && n_ant >= 1, "render: need n_pts >= 1 and n_ant >= 1");
+    REQUIRE(n_pts < (1ll << 31), "render: n_pts must be below 2^31");
+    REQUIRE(band, "render: band must not be NULL");
+    if (ws) REQUIRE(xyz && grad && w && t_eff && ant_xyz && c_ant && s_out, "render: null input or output");
+    return render_impl(xyz, grad, w, t_eff, n_pts, ant_xyz, c_ant, n_ant, band, flags, ws, ws_bytes, s_out,
+                       S(stream));
+}
+
+geraf_status geraf_render_backward(const float* xyz, const float* grad, const float* w, const float* t_eff,
+                                   int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                                   const geraf_band* band, int32_t flags, const float* g_s, void* ws,
+                                   size_t* ws_bytes, float* d_w, float* d_teff, float* d_grad, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_pts >= 1 && n_ant >= 1, "render_backward: need n_pts >= 1 and n_ant >= 1");
+    REQUIRE(n_pts < (1ll << 31), "render_backward: n_pts must be below 2^31");
+    REQUIRE(band, "render_backward: band must not be NULL");
+    if (ws)
+        REQUIRE(xyz && grad && w && t_eff && ant_xyz && c_ant && g_s && d_w && d_teff && d_grad,
+                "render_backward: null input or output");
+    return render_backward_impl(xyz, grad, w, t_eff, n_pts, ant_xyz, c_ant, n_ant, band, flags, g_s, ws, ws_bytes,
+                                d_w, d_teff, d_grad, S(stream));
+}
+
+geraf_status geraf_filter(const float* s, const float* ant_xyz, int32_t n_ant, const geraf_band* band,
+                          const float* vox_xyz, int64_t n_vox, const float* target, const float* mask, void* ws,
+                          size_t* ws_bytes, float* P, float* M, double* loss, float* dloss_dP, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_vox >= 1 && n_ant >= 1, "filter: need n_vox >= 1 and n_ant >= 1");
+    REQUIRE(n_vox < (1ll << 31), "filter: n_vox must be below 2^31");
+    REQUIRE(band, "filter: band must not be NULL");
+    if (ws) REQUIRE(s && ant_xyz && vox_xyz && P && M, "filter: null input or output");
+    return filter_impl(s, ant_xyz, n_ant, band, vox_xyz, n_vox, target, mask, ws, ws_bytes, P, M, loss, dloss_dP,
+                       S(stream));
+}
+
+geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const geraf_band* band, const float* vox_xyz,
+                                   int64_t n_vox, const float* M, const float* d_P, void* ws, size_t* ws_bytes,
+                                   float* g_s, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_vox >= 1 && n_ant >= 1, "filter_backward: need n_vox >= 1 and n_ant >= 1");
+    REQUIRE(n_vox < (1ll << 31), "filter_backward: n_vox must be below 2^31");
+    REQUIRE(band, "filter_backward: band must not be NULL");
+    if (ws) REQUIRE(ant_xyz && vox_xyz && M && d_P && g_s, "filter_backward: null input or output");
+    return filter_backward_impl(ant_xyz, n_ant, band, vox_xyz, n_vox, M, d_P, ws, ws_bytes, g_s, S(stream));
+}
+
+}  // extern "C"

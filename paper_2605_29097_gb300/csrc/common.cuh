@@ -1,0 +1,162 @@
+// Shared device helpers of the GB300 rendering kernels: status reporting,
+// double-single (hi + lo FP32 pair) arithmetic, mbarrier waits with a time
+// limit, 1-D TMA bulk copies, launch geometry.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/geraf.h"
+
+namespace geraf {
+
+// ---------------------------------------------------------------- host side
+void set_error(const char* fmt, ...);
+geraf_status fail(geraf_status st, const char* fmt, ...);
+geraf_status cuda_status(cudaError_t e, const char* what);
+int device_sm_count();
+
+// device error word: bit 0 = a bounded wait timed out. Read and cleared by
+// geraf_poll_device_error().
+int* device_error_word();
+
+constexpr double kC = 299792458.0;   // m/s, exact SI value
+constexpr int kBinsPerBlock = 32;    // phasor recurrence re-seeded every 32 bins
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Splits a caller workspace into 256-byte aligned slices.
+struct WsCarver {
+    char* base;
+    size_t used = 0;
+    explicit WsCarver(void* p) : base(static_cast<char*>(p)) {}
+    template <class T> T* take(size_t count) {
+        used = align_up(used, 256);
+        T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+        used += count * sizeof(T);
+        return p;
+    }
+};
+
+// Per-band constants: K_b = 2 f_{32 b} / c split into FP32 hi + lo (cycles per
+// metre at the first frequency of bin block b) and Kd = 2 df / c.
+struct BandK {
+    float k[2 * 64];
+    float kd;
+    int g;          // number of 32-bin blocks
+};
+bool make_band_k(const geraf_band* band, BandK* out);
+
+// ---------------------------------------------------------------- device side
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Range r = |p - q| as a double-single pair (rh + rl), from FP32 coordinates
+// taken as exact. Also returns the FP32 difference vector and rsqrt(r^2).
+struct Range {
+    float dx, dy, dz;   // rounded differences
+    float rh, rl;       // r = rh + rl to ~2^-44 relative
+    float rs;           // ~1 / r
+};
+
+__device__ __forceinline__ Range pair_range(float px, float py, float pz,
+                                            float qx, float qy, float qz) {
+    Range R;
+    float lx, ly, lz;
+    two_sum(px, -qx, R.dx, lx);
+    two_sum(py, -qy, R.dy, ly);
+    two_sum(pz, -qz, R.dz, lz);
+    // squares as hi + lo
+    float sx = __fmul_rn(R.dx, R.dx), ex = __fmaf_rn(R.dx, R.dx, -sx);
+    float sy = __fmul_rn(R.dy, R.dy), ey = __fmaf_rn(R.dy, R.dy, -sy);
+    float sz = __fmul_rn(R.dz, R.dz), ez = __fmaf_rn(R.dz, R.dz, -sz);
+    ex = __fmaf_rn(2.0f * R.dx, lx, ex);
+    ey = __fmaf_rn(2.0f * R.dy, ly, ey);
+    ez = __fmaf_rn(2.0f * R.dz, lz, ez);
+    float s12, t12, S, t3;
+    two_sum(sx, sy, s12, t12);
+    two_sum(s12, sz, S, t3);
+    float lo = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), __fadd_rn(ez, t12)), t3);
+    S = fmaxf(S, 1e-30f);
+    float rs = rsqrtf(S);
+    float r0 = __fmul_rn(S, rs);
+    // one Newton step on the double-single square
+    float resid = __fadd_rn(__fmaf_rn(-r0, r0, S), lo);
+    R.rh = r0;
+    R.rl = __fmul_rn(resid, __fmul_rn(0.5f, rs));
+    R.rs = rs;
+    return R;
+}
+
+// Fractional part (in cycles, |.| <= 0.5 + tiny) of (rh + rl) * (kh + kl).
+__device__ __forceinline__ float phase_frac(float rh, float rl, float kh, float kl) {
+    float p = __fmul_rn(rh, kh);
+    float e = __fmaf_rn(rh, kh, -p);
+    e = __fmaf_rn(rh, kl, e);
+    e = __fmaf_rn(rl, kh, e);
+    float n = rintf(p);
+    return __fadd_rn(__fsub_rn(p, n), e);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of `bar` for at most ~limit_ns. Returns false on
+// timeout (the caller records it and leaves).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+}  // namespace geraf

@@ -1,0 +1,773 @@
+// Phasor-sum kernels of the rendering path: signal tracing (render) and the
+// matched filter (filter), each with its adjoint.
+//
+// Two kernel shapes cover the four sums:
+//  * "to bins"  (render, filter backward): outputs indexed by (antenna, bin);
+//    each thread owns one antenna x 32 consecutive bins, point tiles stream
+//    through shared memory by TMA, the phasor steps across the 32 bins by the
+//    angle-addition recurrence q <- q * exp(-j 2 pi df tau) from a fresh seed
+//    exp(-j 2 pi f_32b tau), i.e. re-seeded every 32 bins. Per-pair quantities
+//    (range as a double-single, amplitude, step phasor) are computed once per
+//    (antenna, point) by the whole CTA and shared by the 32-bin blocks of that
+//    antenna. Split over points; per-thread sums are two-level (FP32 inner
+//    sum over 128 points, Kahan-compensated outer sum), split partials are
+//    added in FP64 by a second kernel in a fixed order.
+//  * "to points" (filter, render backward): outputs indexed by point/voxel;
+//    each thread owns 2 points, antenna tiles (position + the 32-bin-padded
+//    signal row) stream through shared memory by TMA, and the per-block
+//    frequency sum is evaluated by Horner's rule in the step phasor
+//    z = exp(+j 2 pi df tau), then rotated by the block seed. Split over
+//    antennas with FP64 partial reduction.
+// The phase of every term is exact to ~1e-6 rad: r is formed as a
+// double-single from the FP32 coordinates, r * 2 f / c is reduced to its
+// fractional cycle in double-single before the seed's sincos.
+#include <math.h>
+#include <stdio.h>
+
+#include "common.cuh"
+
+namespace geraf {
+
+namespace {
+
+constexpr float kInv16Pi2 = 0.0063325739776461107f;   // 1 / (16 pi^2)
+constexpr float kSqrt2 = 1.41421356237309505f;
+
+// ------------------------------------------------------------------ records
+// Point record of the phasor kernels (48 bytes):
+//  render / render backward: a = (x, y, z, w), b = (sqrt2*nx, sqrt2*ny, sqrt2*nz, t_eff),
+//                            c = (e, 1/|G|, 0, 0); e = 1 directional, -1 isotropic
+//  filter backward:          a = (x, y, z, c_re), b = (c_im, 0, 0, 0), c = 0
+struct __align__(16) PtRec {
+    float4 a, b, c;
+};
+
+// --------------------------------------------------------------- pack kernels
+__global__ void pack_render_points(const float* __restrict__ xyz, const float* __restrict__ grad,
+                                   const float* __restrict__ w, const float* __restrict__ t_eff,
+                                   int64_t n, int64_t n_pad, int directional, PtRec* __restrict__ out) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_pad) return;
+    PtRec r;
+    if (j < n) {
+        float x = xyz[j], y = xyz[n + j], z = xyz[2 * n + j];
+        float gx = grad[j], gy = grad[n + j], gz = grad[2 * n + j];
+        float g2 = gx * gx + gy * gy + gz * gz;
+        bool dir = directional && g2 > 0.0f;
+        float gn = sqrtf(g2);
+        float k = dir ? kSqrt2 / gn : 0.0f;
+        r.a = make_float4(x, y, z, w[j]);
+        r.b = make_float4(gx * k, gy * k, gz * k, t_eff[j]);
+        r.c = make_float4(dir ? 1.0f : -1.0f, dir ? 1.0f / gn : 0.0f, 0.0f, 0.0f);
+    } else {
+        r.a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        r.c = make_float4(-1.0f, 0.0f, 0.0f, 0.0f);
+    }
+    out[j] = r;
+}
+
+__global__ void pack_filter_bwd_points(const float* __restrict__ vox, const float2* __restrict__ M,
+                                       const float* __restrict__ dP, int64_t n, int64_t n_pad,
+                                       PtRec* __restrict__ out) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_pad) return;
+    PtRec r;
+    r.c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (j < n) {
+        float2 m = M[j];
+        double mag = sqrt((double)m.x * m.x + (double)m.y * m.y);
+        float cr = 0.0f, ci = 0.0f;
+        if (mag > 0.0) {
+            cr = (float)(dP[j] * (double)m.x / mag);
+            ci = (float)(dP[j] * (double)m.y / mag);
+        }
+        r.a = make_float4(vox[j], vox[n + j], vox[2 * n + j], cr);
+        r.b = make_float4(ci, 0.0f, 0.0f, 0.0f);
+    } else {
+        r.a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    out[j] = r;
+}
+
+// antenna records (x, y, z, c_ant), padded with copies of antenna 0
+__global__ void pack_antennas(const float* __restrict__ ant, const float* __restrict__ c_ant, int n_ant,
+                              int n_pad, float4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    int k = i < n_ant ? i : 0;
+    out[i] = make_float4(ant[k], ant[n_ant + k], ant[2 * n_ant + k], c_ant ? c_ant[k] : 0.0f);
+}
+
+// antenna tile rows for the to-points kernels: 16-byte head (x, y, z, c)
+// followed by the signal row zero-padded to 32*G bins.
+__global__ void pack_antenna_rows(const float* __restrict__ ant, const float* __restrict__ c_ant,
+                                  const float2* __restrict__ sig, int n_ant, int n_ant_pad, int n_f,
+                                  int n_f_pad, float4* __restrict__ out) {
+    int i = blockIdx.x;
+    if (i >= n_ant_pad) return;
+    float4* row = out + (size_t)i * (1 + n_f_pad / 2);
+    if (threadIdx.x == 0) {
+        int k = i < n_ant ? i : 0;
+        row[0] = make_float4(ant[k], ant[n_ant + k], ant[2 * n_ant + k], c_ant ? c_ant[k] : 0.0f);
+    }
+    float2* bins = reinterpret_cast<float2*>(row + 1);
+    for (int n = threadIdx.x; n < n_f_pad; n += blockDim.x) {
+        float2 v = make_float2(0.0f, 0.0f);
+        if (i < n_ant && n < n_f) v = sig[(size_t)i * n_f + n];
+        bins[n] = v;
+    }
+}
+
+// ------------------------------------------------------------ to-bins kernel
+constexpr int TB_THREADS = 128;
+constexpr int TB_FLUSH_TILES = 4;
+
+struct ToBinsArgs {
+    const PtRec* pts;        // n_tiles * tp records
+    const float4* ant;       // n_ant_pad records
+    float2* partial;         // [splits][n_ant_pad][32 G]
+    int* err;
+    int tp;                  // points per tile (16 or 32)
+    int n_tiles;             // total point tiles
+    int tiles_per_split;
+    int n_ant_pad;
+    int a_t;                 // antennas per CTA
+    BandK bk;
+};
+
+template <bool kComplexAmp>
+__global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = args.bk.g;
+    const int A_T = args.a_t;
+    const int TP = args.tp;
+    const int t = threadIdx.x;
+
+    // shared layout
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);                       // 2 barriers
+    int* abort_flag = reinterpret_cast<int*>(smem + 16);
+    PtRec* tiles = reinterpret_cast<PtRec*>(smem + 32);                      // [2][TP]
+    float4* ant_s = reinterpret_cast<float4*>(smem + 32 + 2 * TP * sizeof(PtRec));
+    float* prep = reinterpret_cast<float*>(ant_s + A_T);                     // [5][TP][A_T]
+    float2* outer = reinterpret_cast<float2*>(prep + 5 * TP * A_T);          // [2][32][TB_THREADS]
+
+    const int ant0 = blockIdx.x * A_T;
+    const int split = blockIdx.y;
+    const int tile0 = split * args.tiles_per_split;
+    const int tile1 = min(tile0 + args.tiles_per_split, args.n_tiles);
+    const int n_my = tile1 - tile0;
+
+    const int a_slot = t / G;
+    const int blk = t - a_slot * G;
+    const bool active = a_slot < A_T;
+
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    for (int i = t; i < A_T; i += TB_THREADS) ant_s[i] = args.ant[ant0 + i];
+    for (int i = t; i < 2 * 32 * TB_THREADS; i += TB_THREADS) outer[i] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+
+    const uint32_t tile_bytes = (uint32_t)(TP * sizeof(PtRec));
+    if (t == 0) {
+        for (int s = 0; s < 2 && s < n_my; ++s) {
+            mbar_arrive_expect_tx(&bar[s], tile_bytes);
+            tma_load_1d(tiles + s * TP, args.pts + (size_t)(tile0 + s) * TP, tile_bytes, &bar[s]);
+        }
+    }
+
+    const float kh = args.bk.k[2 * blk], kl = args.bk.k[2 * blk + 1];
+    const float kd = args.bk.kd;
+    float2 acc[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) acc[m] = make_float2(0.0f, 0.0f);
+
+    for (int it = 0; it < n_my; ++it) {
+        const int buf = it & 1;
+        bool ok = mbar_wait(&bar[buf], (it >> 1) & 1);
+        if (!ok) atomicOr(abort_flag, 1);
+        __syncthreads();
+        if (*abort_flag) {
+            if (t == 0) atomicOr(args.err, 1);
+            return;
+        }
+        const PtRec* tile = tiles + buf * TP;
+        // ---- per-pair preparation shared by the G bin blocks of an antenna
+        for (int q = t; q < TP * A_T; q += TB_THREADS) {
+            const int p = q / A_T, a = q - p * A_T;
+            const PtRec P = tile[p];
+            const float4 A4 = ant_s[a];
+            Range R = pair_range(P.a.x, P.a.y, P.a.z, A4.x, A4.y, A4.z);
+            float amp = 0.0f;
+            if (!kComplexAmp) {
+                float inv_r2 = R.rs * R.rs;
+                float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
+                float D = fmaxf(nd * nd * inv_r2 - P.c.x, 0.0f);
+                float tt = __saturatef(P.b.w - A4.w);
+                amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
+            }
+            float dl = R.rh * kd;
+            dl = dl - rintf(dl);
+            float sn, cs;
+            sincospif(2.0f * dl, &sn, &cs);
+            prep[(0 * TP + p) * A_T + a] = R.rh;
+            prep[(1 * TP + p) * A_T + a] = R.rl;
+            prep[(2 * TP + p) * A_T + a] = amp;
+            prep[(3 * TP + p) * A_T + a] = cs;
+            prep[(4 * TP + p) * A_T + a] = -sn;     // step exp(-j 2 pi delta)
+        }
+        __syncthreads();
+        // ---- 32-bin recurrence per (point, my antenna, my block)
+        if (active) {
+            for (int p = 0; p < TP; ++p) {
+                const float rh = prep[(0 * TP + p) * A_T + a_slot];
+                const float rl = prep[(1 * TP + p) * A_T + a_slot];
+                const float wr = prep[(3 * TP + p) * A_T + a_slot];
+                const float wi = prep[(4 * TP + p) * A_T + a_slot];
+                const float fr = phase_frac(rh, rl, kh, kl);
+                float sn, cs;
+                __sincosf(6.28318530717958648f * fr, &sn, &cs);
+                float qr, qi;
+                if (!kComplexAmp) {
+                    const float amp = prep[(2 * TP + p) * A_T + a_slot];
+                    qr = amp * cs;
+                    qi = -amp * sn;
+                } else {
+                    const float cr = tile[p].a.w, ci = tile[p].b.x;
+                    // (cr + j ci)(cs - j sn)
+                    qr = cr * cs + ci * sn;
+                    qi = ci * cs - cr * sn;
+                }
+#pragma unroll
+                for (int m = 0; m < 32; ++m) {
+                    acc[m].x += qr;
+                    acc[m].y += qi;
+                    const float nr = fmaf(qr, wr, -qi * wi);
+                    const float ni = fmaf(qr, wi, qi * wr);
+                    qr = nr;
+                    qi = ni;
+                }
+            }
+        }
+        // ---- Kahan flush of the inner sums
+        if (active && (((it + 1) % TB_FLUSH_TILES) == 0 || it + 1 == n_my)) {
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                float2 hi = outer[m * TB_THREADS + t];
+                float2 lo = outer[(32 + m) * TB_THREADS + t];
+                float yx = __fsub_rn(acc[m].x, lo.x), yy = __fsub_rn(acc[m].y, lo.y);
+                float sx = __fadd_rn(hi.x, yx), sy = __fadd_rn(hi.y, yy);
+                lo.x = __fsub_rn(__fsub_rn(sx, hi.x), yx);
+                lo.y = __fsub_rn(__fsub_rn(sy, hi.y), yy);
+                outer[m * TB_THREADS + t] = make_float2(sx, sy);
+                outer[(32 + m) * TB_THREADS + t] = lo;
+                acc[m] = make_float2(0.0f, 0.0f);
+            }
+        }
+        __syncthreads();   // tile and prep buffers are free again
+        if (t == 0 && it + 2 < n_my) {
+            mbar_arrive_expect_tx(&bar[buf], tile_bytes);
+            tma_load_1d(tiles + buf * TP, args.pts + (size_t)(tile0 + it + 2) * TP, tile_bytes, &bar[buf]);
+        }
+    }
+    if (active) {
+        const int n_f_pad = 32 * G;
+        float2* dst = args.partial + ((size_t)split * args.n_ant_pad + ant0 + a_slot) * n_f_pad + 32 * blk;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            float2 hi = outer[m * TB_THREADS + t];
+            float2 lo = outer[(32 + m) * TB_THREADS + t];
+            dst[m] = make_float2(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y));
+        }
+    }
+}
+
+// partial [splits][n_ant_pad][n_f_pad] -> out [n_ant][n_f], FP64 sum in split order
+__global__ void reduce_bins(const float2* __restrict__ partial, int splits, int n_ant, int n_ant_pad, int n_f,
+                            int n_f_pad, float2* __restrict__ out) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_ant * n_f) return;
+    int i = (int)(idx / n_f), n = (int)(idx - (int64_t)i * n_f);
+    double sr = 0.0, si = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        float2 v = partial[((size_t)s * n_ant_pad + i) * n_f_pad + n];
+        sr += v.x;
+        si += v.y;
+    }
+    out[idx] = make_float2((float)sr, (float)si);
+}
+
+// ----------------------------------------------------------- to-points kernel
+constexpr int TPK_THREADS = 128;
+constexpr int TPK_V = 2;          // points per thread
+constexpr int TPK_AT = 8;         // antennas per tile
+
+enum { MODE_FILTER = 0, MODE_RENDER_BWD = 1 };
+
+struct ToPointsArgs {
+    const PtRec* pts;          // padded point records (render backward)
+    const float* vox;          // [3][n] voxel positions (filter)
+    int64_t n;                 // points / voxels
+    const float4* rows;        // antenna tile rows
+    int row_f4;                // float4 per antenna row = 1 + n_f_pad/2
+    int n_ant_tiles;
+    int tiles_per_split;
+    float* partial;            // filter: float2 [splits][n]; render bwd: float [splits][5][n]
+    int* err;
+    BandK bk;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    int* abort_flag = reinterpret_cast<int*>(smem + 16);
+    float4* rows = reinterpret_cast<float4*>(smem + 32);   // [2][TPK_AT][row_f4]
+    const int G = args.bk.g;
+    const int row_f4 = args.row_f4;
+    const int t = threadIdx.x;
+    const int split = blockIdx.y;
+    const int tile0 = split * args.tiles_per_split;
+    const int tile1 = min(tile0 + args.tiles_per_split, args.n_ant_tiles);
+    const int n_my = tile1 - tile0;
+    const uint32_t tile_bytes = (uint32_t)(TPK_AT * row_f4 * sizeof(float4));
+
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int s = 0; s < 2 && s < n_my; ++s) {
+            mbar_arrive_expect_tx(&bar[s], tile_bytes);
+            tma_load_1d(rows + s * TPK_AT * row_f4, args.rows + (size_t)(tile0 + s) * TPK_AT * row_f4,
+                        tile_bytes, &bar[s]);
+        }
+    }
+
+    // my points
+    const int64_t jbase = (blockIdx.x * (int64_t)TPK_THREADS + t) * TPK_V;
+    float px[TPK_V], py[TPK_V], pz[TPK_V];
+    float pw[TPK_V], pnx[TPK_V], pny[TPK_V], pnz[TPK_V], pte[TPK_V], pe[TPK_V];
+#pragma unroll
+    for (int v = 0; v < TPK_V; ++v) {
+        const int64_t j = min(jbase + v, args.n - 1);
+        if (MODE == MODE_FILTER) {
+            px[v] = args.vox[j];
+            py[v] = args.vox[args.n + j];
+            pz[v] = args.vox[2 * args.n + j];
+            pw[v] = pnx[v] = pny[v] = pnz[v] = pte[v] = pe[v] = 0.0f;
+        } else {
+            const PtRec P = args.pts[j];
+            px[v] = P.a.x; py[v] = P.a.y; pz[v] = P.a.z; pw[v] = P.a.w;
+            pnx[v] = P.b.x; pny[v] = P.b.y; pnz[v] = P.b.z; pte[v] = P.b.w;
+            pe[v] = P.c.x;
+        }
+    }
+    // outer (Kahan) accumulators; filter: M (re, im); render bwd: d_w, d_teff, Ud(3), Un
+    constexpr int NACC = (MODE == MODE_FILTER) ? 2 : 6;
+    float hi[TPK_V][NACC], lo[TPK_V][NACC];
+#pragma unroll
+    for (int v = 0; v < TPK_V; ++v)
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) hi[v][k] = lo[v][k] = 0.0f;
+
+    const float kd = args.bk.kd;
+    for (int it = 0; it < n_my; ++it) {
+        const int buf = it & 1;
+        bool ok = mbar_wait(&bar[buf], (it >> 1) & 1);
+        if (!ok) atomicOr(abort_flag, 1);
+        __syncthreads();
+        if (*abort_flag) {
+            if (t == 0) atomicOr(args.err, 1);
+            return;
+        }
+        const float4* tile = rows + buf * TPK_AT * row_f4;
+        float in[TPK_V][NACC];
+#pragma unroll
+        for (int v = 0; v < TPK_V; ++v)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
+
+        for (int a = 0; a < TPK_AT; ++a) {
+            const float4 head = tile[a * row_f4];
+            const float2* sig = reinterpret_cast<const float2*>(tile + a * row_f4 + 1);
+            Range R[TPK_V];
+            float zr[TPK_V], zi[TPK_V], hr[TPK_V], him[TPK_V];
+#pragma unroll
+            for (int v = 0; v < TPK_V; ++v) {
+                R[v] = pair_range(px[v], py[v], pz[v], head.x, head.y, head.z);
+                float dl = R[v].rh * kd;
+                dl = dl - rintf(dl);
+                float sn, cs;
+                sincospif(2.0f * dl, &sn, &cs);
+                zr[v] = cs;
+                zi[v] = sn;      // z = exp(+j 2 pi delta)
+                hr[v] = 0.0f;
+                him[v] = 0.0f;
+            }
+            for (int b = 0; b < G; ++b) {
+                const float kh = args.bk.k[2 * b], kl = args.bk.k[2 * b + 1];
+                const float4* s4 = reinterpret_cast<const float4*>(sig + 32 * b);
+                float ar[TPK_V], ai[TPK_V];
+                {
+                    const float4 top = s4[15];   // bins 30, 31
+#pragma unroll
+                    for (int v = 0; v < TPK_V; ++v) {
+                        ar[v] = top.z;
+                        ai[v] = top.w;
+                        const float nr = fmaf(ar[v], zr[v], fmaf(-ai[v], zi[v], top.x));
+                        const float ni = fmaf(ar[v], zi[v], fmaf(ai[v], zr[v], top.y));
+                        ar[v] = nr;
+                        ai[v] = ni;
+                    }
+                }
+#pragma unroll
+                for (int m2 = 14; m2 >= 0; --m2) {
+                    const float4 sv = s4[m2];    // bins 2 m2, 2 m2 + 1
+#pragma unroll
+                    for (int v = 0; v < TPK_V; ++v) {
+                        float nr = fmaf(ar[v], zr[v], fmaf(-ai[v], zi[v], sv.z));
+                        float ni = fmaf(ar[v], zi[v], fmaf(ai[v], zr[v], sv.w));
+                        ar[v] = fmaf(nr, zr[v], fmaf(-ni, zi[v], sv.x));
+                        ai[v] = fmaf(nr, zi[v], fmaf(ni, zr[v], sv.y));
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < TPK_V; ++v) {
+                    const float fr = phase_frac(R[v].rh, R[v].rl, kh, kl);
+                    float sn, cs;
+                    __sincosf(6.28318530717958648f * fr, &sn, &cs);
+                    // seed exp(+j 2 pi psi_b) times the block's Horner sum
+                    hr[v] = fmaf(cs, ar[v], fmaf(-sn, ai[v], hr[v]));
+                    him[v] = fmaf(cs, ai[v], fmaf(sn, ar[v], him[v]));
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < TPK_V; ++v) {
+                if (MODE == MODE_FILTER) {
+                    in[v][0] += hr[v];
+                    in[v][1] += him[v];
+                } else {
+                    // q = Re(sum_n g e^{+j phi}); gradients of A = w T'^2 gamma D
+                    const float q = hr[v];
+                    const float inv_r2 = R[v].rs * R[v].rs;
+                    const float gam = inv_r2 * kInv16Pi2;
+                    const float nd = pnx[v] * R[v].dx + pny[v] * R[v].dy + pnz[v] * R[v].dz;
+                    const float c2x2 = nd * nd * inv_r2;          // 2 c^2 (0 when isotropic)
+                    const float Dm = c2x2 - pe[v];
+                    const float D = fmaxf(Dm, 0.0f);
+                    const float vv = pte[v] - head.w;
+                    const float tt = __saturatef(vv);
+                    const float gq = gam * q;
+                    in[v][0] += tt * tt * D * gq;
+                    if (vv >= 0.0f && vv <= 1.0f) in[v][1] += pw[v] * 2.0f * tt * D * gq;
+                    if (pe[v] > 0.0f && Dm > 0.0f) {
+                        // dD/dG = 4 c (w_i - c n)/|G|, c = nd / (sqrt2 r): split into
+                        // Ud += k 4 c / r * d  and  Un += k 4 c^2 / sqrt2 (times n' later)
+                        const float kq = pw[v] * tt * tt * gq;
+                        const float c = nd * R[v].rs * (1.0f / kSqrt2);
+                        const float k1 = kq * 4.0f * c * R[v].rs;
+                        in[v][2] += k1 * R[v].dx;
+                        in[v][3] += k1 * R[v].dy;
+                        in[v][4] += k1 * R[v].dz;
+                        in[v][5] += kq * 4.0f * c * c * (1.0f / kSqrt2);
+                    }
+                }
+            }
+        }
+        // Kahan accumulate the tile's inner sums
+#pragma unroll
+        for (int v = 0; v < TPK_V; ++v)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                const float y = __fsub_rn(in[v][k], lo[v][k]);
+                const float s = __fadd_rn(hi[v][k], y);
+                lo[v][k] = __fsub_rn(__fsub_rn(s, hi[v][k]), y);
+                hi[v][k] = s;
+            }
+        __syncthreads();
+        if (t == 0 && it + 2 < n_my) {
+            mbar_arrive_expect_tx(&bar[buf], tile_bytes);
+            tma_load_1d(rows + buf * TPK_AT * row_f4, args.rows + (size_t)(tile0 + it + 2) * TPK_AT * row_f4,
+                        tile_bytes, &bar[buf]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < TPK_V; ++v) {
+        const int64_t j = jbase + v;
+        if (j >= args.n) continue;
+        if (MODE == MODE_FILTER) {
+            float2* dst = reinterpret_cast<float2*>(args.partial) + (size_t)split * args.n + j;
+            *dst = make_float2(__fsub_rn(hi[v][0], lo[v][0]), __fsub_rn(hi[v][1], lo[v][1]));
+        } else {
+            float* dst = args.partial + (size_t)split * 6 * args.n + j;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = __fsub_rn(hi[v][k], lo[v][k]);
+        }
+    }
+}
+
+// filter finalize: M = sum of split partials (FP64), P = |M|, loss terms
+__global__ void filter_finalize(const float2* __restrict__ partial, int splits, int64_t n,
+                                const float* __restrict__ target, const float* __restrict__ mask,
+                                float* __restrict__ P, float2* __restrict__ M, float* __restrict__ dP,
+                                double* __restrict__ loss_blocks) {
+    __shared__ double red[256];
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (j < n) {
+        double mr = 0.0, mi = 0.0;
+        for (int s = 0; s < splits; ++s) {
+            float2 v = partial[(size_t)s * n + j];
+            mr += v.x;
+            mi += v.y;
+        }
+        double p = sqrt(mr * mr + mi * mi);
+        M[j] = make_float2((float)mr, (float)mi);
+        P[j] = (float)p;
+        if (target) {
+            double m = mask ? (double)mask[j] : 1.0;
+            double r = p - (double)target[j];
+            l = m * r * r;
+            if (dP) dP[j] = (float)(2.0 * m * r);
+        }
+    }
+    if (loss_blocks) {
+        red[threadIdx.x] = l;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) loss_blocks[blockIdx.x] = red[0];
+    }
+}
+
+__global__ void sum_doubles(const double* __restrict__ x, int n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void render_bwd_finalize(const float* __restrict__ partial, int splits, int64_t n,
+                                    const PtRec* __restrict__ pts, float* __restrict__ d_w,
+                                    float* __restrict__ d_teff, float* __restrict__ d_grad) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < splits; ++s)
+        for (int k = 0; k < 6; ++k) acc[k] += partial[((size_t)s * 6 + k) * n + j];
+    d_w[j] = (float)acc[0];
+    d_teff[j] = (float)acc[1];
+    const PtRec P = pts[j];
+    const double ig = P.c.y;   // 1/|G| (0 when isotropic)
+    d_grad[j] = (float)((acc[2] - acc[5] * P.b.x) * ig);
+    d_grad[n + j] = (float)((acc[3] - acc[5] * P.b.y) * ig);
+    d_grad[2 * n + j] = (float)((acc[4] - acc[5] * P.b.z) * ig);
+}
+
+// --------------------------------------------------------------- launch glue
+
+int choose_splits(int64_t base_ctas, int resident_per_sm, int64_t max_splits) {
+    const int64_t slots = (int64_t)device_sm_count() * resident_per_sm;
+    int64_t waves = (base_ctas + slots - 1) / slots;
+    if (waves < 4) waves = 4;
+    int64_t s = (waves * slots + base_ctas - 1) / base_ctas;
+    if (s > max_splits) s = max_splits;
+    if (s < 1) s = 1;
+    return (int)s;
+}
+
+struct ToBinsPlan {
+    int G, A_T, TP, n_ant_pad, ant_ctas, n_tiles, splits, tiles_per_split;
+    size_t smem;
+};
+
+ToBinsPlan plan_to_bins(int64_t n_pts, int n_ant, int G) {
+    ToBinsPlan p;
+    p.G = G;
+    p.A_T = TB_THREADS / G;
+    if (p.A_T < 1) p.A_T = 1;
+    p.TP = (p.A_T >= 64) ? 16 : 32;
+    p.n_ant_pad = (int)((n_ant + p.A_T - 1) / p.A_T) * p.A_T;
+    p.ant_ctas = p.n_ant_pad / p.A_T;
+    p.n_tiles = (int)((n_pts + p.TP - 1) / p.TP);
+    if (p.n_tiles < 1) p.n_tiles = 1;
+    p.splits = choose_splits(p.ant_ctas, 2, p.n_tiles);
+    p.tiles_per_split = (p.n_tiles + p.splits - 1) / p.splits;
+    p.splits = (p.n_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
+    p.smem = 32 + 2 * p.TP * sizeof(PtRec) + p.A_T * sizeof(float4) + 5 * p.TP * p.A_T * sizeof(float) +
+             2 * 32 * TB_THREADS * sizeof(float2);
+    return p;
+}
+
+struct ToPointsPlan {
+    int G, n_f_pad, row_f4, n_ant_pad, n_ant_tiles, pt_ctas, splits, tiles_per_split;
+    size_t smem;
+};
+
+ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
+    ToPointsPlan p;
+    p.G = G;
+    p.n_f_pad = 32 * G;
+    p.row_f4 = 1 + p.n_f_pad / 2;
+    p.n_ant_pad = (n_ant + TPK_AT - 1) / TPK_AT * TPK_AT;
+    p.n_ant_tiles = p.n_ant_pad / TPK_AT;
+    p.pt_ctas = (int)((n + TPK_THREADS * TPK_V - 1) / (TPK_THREADS * TPK_V));
+    p.splits = choose_splits(p.pt_ctas, 8, p.n_ant_tiles);
+    p.tiles_per_split = (p.n_ant_tiles + p.splits - 1) / p.splits;
+    p.splits = (p.n_ant_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
+    p.smem = 32 + 2 * TPK_AT * p.row_f4 * sizeof(float4);
+    return p;
+}
+
+geraf_status check_launch(const char* what) { return cuda_status(cudaGetLastError(), what); }
+
+inline unsigned grid1d(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+// ============================================================== entry points
+
+geraf_status render_impl(const float* xyz, const float* grad, const float* w, const float* t_eff, int64_t n_pts,
+                         const float* ant_xyz, const float* c_ant, int32_t n_ant, const geraf_band* band,
+                         int32_t flags, void* ws, size_t* ws_bytes, float* s_out, cudaStream_t st) {
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    ToBinsPlan p = plan_to_bins(n_pts, n_ant, bk.g);
+    WsCarver c(ws);
+    PtRec* pts = c.take<PtRec>((size_t)p.n_tiles * p.TP);
+    float4* ant = c.take<float4>(p.n_ant_pad);
+    float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "render: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    int* err = device_error_word();
+    const int64_t n_pad = (int64_t)p.n_tiles * p.TP;
+    pack_render_points<<<grid1d(n_pad, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pad,
+                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
+    pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, p.n_ant_pad, ant);
+    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk};
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    to_bins_kernel<false><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
+    reduce_bins<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(part, p.splits, n_ant, p.n_ant_pad,
+                                                                         band->n_f, 32 * p.G,
+                                                                         reinterpret_cast<float2*>(s_out));
+    return check_launch("render");
+}
+
+geraf_status filter_backward_impl(const float* ant_xyz, int32_t n_ant, const geraf_band* band, const float* vox,
+                                  int64_t n_vox, const float* M, const float* d_P, void* ws, size_t* ws_bytes,
+                                  float* g_s, cudaStream_t st) {
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    ToBinsPlan p = plan_to_bins(n_vox, n_ant, bk.g);
+    WsCarver c(ws);
+    PtRec* pts = c.take<PtRec>((size_t)p.n_tiles * p.TP);
+    float4* ant = c.take<float4>(p.n_ant_pad);
+    float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used)
+        return fail(GERAF_ERR_WORKSPACE, "filter_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    int* err = device_error_word();
+    const int64_t n_pad = (int64_t)p.n_tiles * p.TP;
+    pack_filter_bwd_points<<<grid1d(n_pad, 256), 256, 0, st>>>(vox, reinterpret_cast<const float2*>(M), d_P,
+                                                               n_vox, n_pad, pts);
+    pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, nullptr, n_ant, p.n_ant_pad, ant);
+    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk};
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    to_bins_kernel<true><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
+    reduce_bins<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(part, p.splits, n_ant, p.n_ant_pad,
+                                                                         band->n_f, 32 * p.G,
+                                                                         reinterpret_cast<float2*>(g_s));
+    return check_launch("filter_backward");
+}
+
+geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, const geraf_band* band,
+                         const float* vox, int64_t n_vox, const float* target, const float* mask, void* ws,
+                         size_t* ws_bytes, float* P, float* M, double* loss, float* dloss_dP, cudaStream_t st) {
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    ToPointsPlan p = plan_to_points(n_vox, n_ant, bk.g);
+    WsCarver c(ws);
+    float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
+    float2* part = c.take<float2>((size_t)p.splits * n_vox);
+    const int fin_blocks = (int)grid1d(n_vox, 256);
+    double* loss_blocks = c.take<double>(fin_blocks);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    int* err = device_error_word();
+    pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s),
+                                                           n_ant, p.n_ant_pad, band->n_f, p.n_f_pad, rows);
+    ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.n_ant_tiles, p.tiles_per_split,
+                   reinterpret_cast<float*>(part), err, bk};
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(to_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    to_points_kernel<MODE_FILTER><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
+    const bool want_loss = target != nullptr;
+    filter_finalize<<<fin_blocks, 256, 0, st>>>(part, p.splits, n_vox, target, mask, P,
+                                                reinterpret_cast<float2*>(M), want_loss ? dloss_dP : nullptr,
+                                                want_loss ? loss_blocks : nullptr);
+    if (want_loss && loss) sum_doubles<<<1, 256, 0, st>>>(loss_blocks, fin_blocks, loss);
+    return check_launch("filter");
+}
+
+geraf_status render_backward_impl(const float* xyz, const float* grad, const float* w, const float* t_eff,
+                                  int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                                  const geraf_band* band, int32_t flags, const float* g_s, void* ws,
+                                  size_t* ws_bytes, float* d_w, float* d_teff, float* d_grad, cudaStream_t st) {
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    ToPointsPlan p = plan_to_points(n_pts, n_ant, bk.g);
+    WsCarver c(ws);
+    PtRec* pts = c.take<PtRec>((size_t)n_pts);
+    float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
+    float* part = c.take<float>((size_t)p.splits * 6 * n_pts);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used)
+        return fail(GERAF_ERR_WORKSPACE, "render_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    int* err = device_error_word();
+    pack_render_points<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pts,
+                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
+    pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s),
+                                                           n_ant, p.n_ant_pad, band->n_f, p.n_f_pad, rows);
+    ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.n_ant_tiles, p.tiles_per_split, part, err, bk};
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(to_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        attr_set = true;
+    }
+    to_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
+    render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, d_w, d_teff, d_grad);
+    return check_launch("render_backward");
+}
+
+}  // namespace geraf

@@ -1,0 +1,224 @@
+"""CUDA path vs the FP64 oracle, stage by stage, through the C ABI.
+
+Each stage gets identical FP32 inputs on both sides (the oracle promotes them
+to FP64). Tolerances: integer/bit work is exact; FP32 outputs must match to
+relative L2 <= 1e-5 (the FP32-path bound), a few gradient outputs whose
+directional-factor branch can flip within FP32 rounding of 2c^2 - 1 get 3e-5.
+Sizes are ragged on purpose: points not a multiple of the point tile, antennas
+not a multiple of the CTA's antenna slice, bins not a multiple of 32.
+"""
+import numpy as np
+import pytest
+import torch
+
+import geraf_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) else np.float64)
+    b = np.asarray(b, dtype=a.dtype)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_29097_gb300 import _build
+    _build.build()
+    import paper_2605_29097_gb300 as G
+    return G
+
+
+def cu(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _band(G, b):
+    return G.Band(b.f0, b.df, b.n_f)
+
+
+def _scene_points(rng, n, centre=(0.0, 0.0, 0.15), half=0.05):
+    xyz = (np.array(centre)[:, None] + rng.uniform(-half, half, (3, n))).astype(np.float32)
+    grad = rng.standard_normal((3, n)).astype(np.float32)
+    grad[:, ::17] = 0.0                              # some isotropic points
+    w = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    t_eff = rng.uniform(0.3, 2.0, n).astype(np.float32)
+    return xyz, grad, w, t_eff
+
+
+# ----------------------------------------------------------------- sampling
+@pytest.mark.parametrize("mode", [gi.SAMPLE_UNIFORM, gi.SAMPLE_STRATIFIED])
+def test_sample_bit_exact(G, oracle, mode):
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.1, (33, 17, 29))
+    grid = G.make_grid(g.lo, g.pitch, g.n, g.aperture_z)
+    xyz, apr = G.geraf_sample(grid, mode, seed=1234, step=7)
+    oxyz, oapr = oracle.sample(g, mode, seed=1234, step=7)
+    np.testing.assert_array_equal(host(xyz).view(np.uint32), oxyz.view(np.uint32))
+    np.testing.assert_array_equal(host(apr).view(np.uint32), oapr.view(np.uint32))
+
+
+def test_sample_bit_exact_full_size_spots(G, oracle):
+    """128^3 stratified (the MLP workload's sampling): every point from the
+    CUDA path equals the oracle at 20 000 random indices."""
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.1, (128, 128, 128))
+    grid = G.make_grid(g.lo, g.pitch, g.n)
+    xyz, _ = G.geraf_sample(grid, gi.SAMPLE_STRATIFIED, seed=3, step=2)
+    full, _ = oracle.sample(g, gi.SAMPLE_STRATIFIED, seed=3, step=2)
+    idx = np.random.default_rng(0).integers(0, g.n_pts, 20000)
+    np.testing.assert_array_equal(host(xyz)[:, idx].view(np.uint32), full[:, idx].view(np.uint32))
+
+
+# ----------------------------------------------------------- analytic fields
+def test_analytic_fields(G, oracle):
+    rng = np.random.default_rng(1)
+    sc = gi.Scene([gi.Prim(gi.PRIM_SPHERE, 0.9, (0.0, 0.0, 0.15), (0.03, 0, 0)),
+                   gi.Prim(gi.PRIM_BOX, 0.5, (0.02, 0.01, 0.13), (0.01, 0.015, 0.008)),
+                   gi.Prim(gi.PRIM_ELLIPSOID, 0.3, (-0.02, 0.0, 0.17), (0.02, 0.01, 0.015)),
+                   gi.Prim(gi.PRIM_HALFSPACE, 0.7, (0.0, 0.0, 0.195), (0.0, 0.0, -1.0))])
+    xyz = (np.array([0, 0, 0.15])[:, None] + rng.uniform(-0.05, 0.05, (3, 5001))).astype(np.float32)
+    f, g, a, _ = G.geraf_fields(G.AnalyticField(cu(sc.packed())), cu(xyz))
+    of, og, oa = oracle.analytic_fields(sc, xyz)
+    np.testing.assert_allclose(host(f), of, rtol=0, atol=2e-8)
+    assert np.mean(np.abs(host(g) - og).max(0) < 1e-5) > 0.999
+    np.testing.assert_array_equal(host(a), oa.astype(np.float32))
+
+
+# -------------------------------------------------------------------- blend
+def test_blend_and_backward(G, oracle):
+    rng = np.random.default_rng(2)
+    n_ray, n_z, n_ant = 301, 37, 19
+    z = np.linspace(0.1, 0.2, n_z)
+    sdf = (0.15 - z[:, None] + 0.01 * rng.standard_normal((n_z, n_ray))).astype(np.float32).reshape(-1)
+    refl = rng.uniform(0.2, 1.0, n_ray * n_z).astype(np.float32)
+    sdf_apr = rng.uniform(0.0, 0.02, n_ray).astype(np.float32)
+    sdf_ant = rng.uniform(-0.005, 0.02, n_ant).astype(np.float32)
+    s, atx = 300.0, 1.3
+    out = G.geraf_blend(cu(sdf), cu(refl), n_ray, n_z, cu(sdf_apr), cu(sdf_ant), s, atx)
+    ref = oracle.blend(sdf, refl, n_ray, n_z, sdf_apr, sdf_ant, np.float32(s), np.float32(atx))
+    for name, got, want in zip(["alpha", "T", "w", "t_eff", "c_ant"], out, ref):
+        assert rel_l2(host(got), want) < TOL, name
+    d_w = rng.standard_normal(n_ray * n_z).astype(np.float32)
+    d_t = rng.standard_normal(n_ray * n_z).astype(np.float32)
+    d_sdf, d_refl, d_sc = G.geraf_blend_backward(cu(sdf), cu(refl), out[0], out[1], n_ray, n_z, s, atx,
+                                                 cu(d_w), cu(d_t))
+    od_f, od_a, od_s, od_atx = oracle.blend_backward(sdf, refl, n_ray, n_z, np.float32(s), np.float32(atx), d_w, d_t)
+    assert rel_l2(host(d_sdf), od_f) < 1e-4   # s * Phi(1-Phi) amplifies FP32 alpha rounding
+    assert rel_l2(host(d_refl), od_a) < TOL
+    np.testing.assert_allclose(host(d_sc), [od_s, od_atx], rtol=1e-4)
+
+
+# ------------------------------------------------------------------- render
+@pytest.mark.parametrize("n_pts,n_ant_side,n_f,directional", [
+    (5003, (10, 10), 45, True),       # G = 2 with a 13-bin tail; 100 antennas
+    (777, (7, 5), 32, True),          # G = 1
+    (2049, (9, 9), 128, False),       # G = 4, isotropic
+    (1, (3, 1), 7, True),             # single point, tiny band
+])
+def test_render(G, oracle, n_pts, n_ant_side, n_f, directional):
+    rng = np.random.default_rng(n_pts)
+    xyz, grad, w, t_eff = _scene_points(rng, n_pts)
+    ant = gi.antenna_array(*n_ant_side, 0.002)
+    c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
+    b = gi.band(77e9, 81e9, n_f)
+    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), _band(G, b), directional)
+    G.geraf_poll_device_error()
+    want = oracle.render(xyz, grad, w, t_eff, ant, c_ant, b, use_dir=directional)
+    assert rel_l2(host(s), want) < TOL
+
+
+def test_render_backward(G, oracle):
+    rng = np.random.default_rng(5)
+    n_pts = 1203
+    xyz, grad, w, t_eff = _scene_points(rng, n_pts)
+    ant = gi.antenna_array(7, 9, 0.002)
+    c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
+    b = gi.band(77e9, 81e9, 70)
+    g = gi.complex_normal(rng, (ant.shape[1], b.n_f)).astype(np.complex64)
+    d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant),
+                                            _band(G, b), torch.as_tensor(g, device="cuda"))
+    G.geraf_poll_device_error()
+    ow, ot, og = oracle.render_backward(xyz, grad, w, t_eff, ant, c_ant, b, g)
+    assert rel_l2(host(d_w), ow) < TOL
+    assert rel_l2(host(d_t), ot) < TOL
+    assert rel_l2(host(d_g), og) < 3 * TOL
+
+
+# ------------------------------------------------------------------- filter
+@pytest.mark.parametrize("n_vox,n_ant_side,n_f", [(3001, (6, 7), 40), (256, (16, 16), 32), (1, (2, 2), 3)])
+def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f):
+    rng = np.random.default_rng(n_vox)
+    ant = gi.antenna_array(*n_ant_side, 0.002)
+    b = gi.band(77e9, 81e9, n_f)
+    s = gi.complex_normal(rng, (ant.shape[1], n_f)).astype(np.complex64)
+    vox = (np.array([0, 0, 0.15])[:, None] + rng.uniform(-0.05, 0.05, (3, n_vox))).astype(np.float32)
+    target = rng.uniform(0, 5, n_vox).astype(np.float32)
+    P, M, loss, dP = G.geraf_filter(torch.as_tensor(s, device="cuda"), cu(ant), _band(G, b), cu(vox), cu(target))
+    G.geraf_poll_device_error()
+    oM, oP = oracle.filter_forward(s, ant, vox, b)
+    assert rel_l2(host(M), oM) < TOL
+    assert rel_l2(host(P), oP) < TOL
+    oL, odP = oracle.heatmap_loss(oP, target)
+    np.testing.assert_allclose(float(loss), oL, rtol=1e-5)
+    assert rel_l2(host(dP), odP) < 1e-4
+    # backward from the kernel's own M (the oracle gets the same FP32 M)
+    d_P = rng.standard_normal(n_vox).astype(np.float32)
+    g = G.geraf_filter_backward(cu(ant), _band(G, b), cu(vox), M, cu(d_P))
+    G.geraf_poll_device_error()
+    og = oracle.filter_backward(host(M), d_P, ant, vox, b)
+    assert rel_l2(host(g), og) < TOL
+
+
+# ------------------------------------------- the analytic-scene workload chain
+def test_sphere_and_point_reflector_chain(G, oracle):
+    """32^3 uniform samples of a 10 cm cube, sphere r = 3 cm at 15 cm plus a
+    point reflector, 16x16 array at 2 mm, 32 bins over 77-81 GHz: every stage on
+    the GPU from the GPU's own previous stage, compared with the oracle run on
+    the same FP32 stage inputs, and the final heatmap against the all-oracle
+    chain."""
+    wl = gi.workload("c1")
+    g = wl.grid
+    grid = G.make_grid(g.lo, g.pitch, g.n, g.aperture_z)
+    xyz, apr = G.geraf_sample(grid, gi.SAMPLE_UNIFORM)
+    field = G.AnalyticField(cu(gi.c1_scene().packed()))
+    ant = cu(gi.antenna_array(16, 16, 0.002))
+    f, grad, a, _ = G.geraf_fields(field, xyz)
+    f_apr, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    f_ant, _, _, _ = G.geraf_fields(field, ant, want_grad=False, want_refl=False)
+    alpha, T, w, t_eff, c_ant = G.geraf_blend(f, a, g.n_ray, g.n[2], f_apr, f_ant, wl.sharpness, wl.a_tx)
+    # the isotropic point reflector, appended: w = 1, T' = 1, zero normal
+    pr = gi.c1_point_reflector(g)
+    xyz2 = torch.cat([xyz, cu(pr).reshape(3, 1)], 1).contiguous()
+    grad2 = torch.cat([grad, torch.zeros(3, 1, device="cuda")], 1).contiguous()
+    w2 = torch.cat([w, torch.ones(1, device="cuda")]).contiguous()
+    t2 = torch.cat([t_eff, torch.full((1,), 2.0, device="cuda")]).contiguous()
+    b = gi.band(77e9, 81e9, wl.n_f)
+    s = G.geraf_render(xyz2, grad2, w2, t2, ant, c_ant, _band(G, b))
+    P, M, _, _ = G.geraf_filter(s, ant, _band(G, b), xyz)
+    G.geraf_poll_device_error()
+    # stage parity on identical inputs
+    os_ = oracle.render(host(xyz2), host(grad2), host(w2), host(t2), host(ant), host(c_ant), b)
+    assert rel_l2(host(s), os_) < TOL
+    oM, oP = oracle.filter_forward(host(s), host(ant), host(xyz), b)
+    assert rel_l2(host(P), oP) < TOL
+    # all-oracle chain from the same sample points
+    sc = gi.c1_scene()
+    of, oG, oa = oracle.analytic_fields(sc, host(xyz))
+    ofa, _, _ = oracle.analytic_fields(sc, host(apr))
+    ofn, _, _ = oracle.analytic_fields(sc, host(ant))
+    oal, oT, ow, ote, oca = oracle.blend(of, oa, g.n_ray, g.n[2], ofa, ofn, wl.sharpness, wl.a_tx)
+    ox = np.concatenate([host(xyz), pr.reshape(3, 1)], 1)
+    os2 = oracle.render(ox, np.concatenate([oG, np.zeros((3, 1))], 1), np.append(ow, 1.0), np.append(ote, 2.0),
+                        host(ant), oca, b)
+    _, oP2 = oracle.filter_forward(os2, host(ant), host(xyz), b)
+    # FP32 SDF rounding enters through exp(s f) with s f up to ~60: looser bound for the whole chain
+    assert rel_l2(host(P), oP2) < 1e-4
+    assert int(np.argmax(host(P))) == int(np.argmax(oP2))
