@@ -1,0 +1,345 @@
+"""Benchmark of the rendering hot path: phasor terms/s for forward + adjoint.
+
+One step = one pass of the whole hot path over one batch of synthetic input
+(stratified sampling, MLP fields with gradient tangents, lensless blending,
+signal tracing, matched filter + L2 loss, and the adjoints of all of them down
+to the MLP parameter gradient). Workload (default): 64x64 array at 2 mm,
+128 frequencies over 77-81 GHz, 128^3 stratified samples of a 10 cm cube,
+SDF/reflectiveness MLP 4x128 (softplus, PE 6 octaves, FP32, seeded init),
+64^3 heatmap against a synthetic target (sphere + point reflector).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (no collective on
+the data path; weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point·antenna·freq phasor terms/s fwd+adj; train-step ms at ≤2e-3 rel err"
+WORKLOAD = ("64x64 array @2mm, 128 freqs 77-81 GHz, 128^3 stratified samples, MLP 4x128 fp32, "
+            "64^3 heatmap, forward + adjoint of every step")
+FLOPS_PER_TERM = 10          # complex rotation (4 FP32-pipe instr, 6 flops) + accumulate (2 FMA, 4 flops)
+INSTR_PER_TERM = 6
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, P_target, max_pts=32768, n_ant=64, n_vox=4096,
+                        filt_ant=256):
+    """Times the FP64 oracle's four phasor sums on a bounded sample of the
+    workload (first max_pts points x first n_ant antennas x all bins for the
+    tracing pair; first n_vox voxels x first filt_ant antennas for the filter
+    pair). Returns (terms/s, seconds, terms, description)."""
+    import numpy as np
+    from oracle import geraf_oracle as O
+    import geraf_inputs as gi
+    b = gi.Band(geo.band.f0, geo.band.df, geo.band.n_f)
+    h = lambda t: t.detach().cpu().numpy()
+    X, Gr, W, Te = h(xyz)[:, :max_pts], h(grad)[:, :max_pts], h(w)[:max_pts], h(t_eff)[:max_pts]
+    A, C = h(geo.ant)[:, :n_ant], h(c_ant)[:n_ant]
+    V = h(geo.vox)[:, :n_vox]
+    Af = h(geo.ant)[:, :filt_ant]
+    rng = np.random.default_rng(0)
+    g = gi.complex_normal(rng, (n_ant, b.n_f))
+    t0 = time.perf_counter()
+    s = O.render(X, Gr, W, Te, A, C, b)
+    O.render_backward(X, Gr, W, Te, A, C, b, g)
+    sf = gi.complex_normal(rng, (filt_ant, b.n_f))
+    M, P = O.filter_forward(sf, Af, V, b)
+    O.filter_backward(M, np.ones(n_vox), Af, V, b)
+    dt = time.perf_counter() - t0
+    terms = 2 * X.shape[1] * n_ant * b.n_f + 2 * n_vox * filt_ant * b.n_f
+    desc = (f"oracle render+render_backward on {X.shape[1]} points x {n_ant} antennas x {b.n_f} bins, "
+            f"filter+filter_backward on {n_vox} voxels x {filt_ant} antennas x {b.n_f} bins (FP64 C, OpenMP)")
+    del s
+    return terms / dt, dt, terms, desc
+
+
+def oracle_threads():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
+    except ValueError:
+        return os.cpu_count()
+
+
+def run_reference(args, rank):
+    """The oracle as the reference arm: K bounded samples of the workload on
+    the host cores, timed like steps."""
+    if rank != 0:
+        return
+    import torch  # noqa: F401  (CUDA not needed)
+    import numpy as np
+    import geraf_inputs as gi
+    from oracle import geraf_oracle as O
+    wl = gi.workload("c2")
+    b = gi.band(77e9, 81e9, wl.n_f)
+    xyz, apr = O.sample(wl.grid, gi.SAMPLE_STRATIFIED, seed=0, step=0)
+    n_pts, n_ant, n_vox, filt_ant = 16384, 32, 2048, 128
+    X = xyz[:, :n_pts]
+    rng = np.random.default_rng(0)
+    Gr = rng.standard_normal((3, n_pts))
+    W, Te = rng.uniform(0, 1e-3, n_pts), np.full(n_pts, 2.0)
+    A = gi.antenna_array(wl.array_n, wl.array_n, wl.array_pitch)[:, :n_ant]
+    Af = gi.antenna_array(wl.array_n, wl.array_n, wl.array_pitch)[:, :filt_ant]
+    V, _ = O.sample(wl.heat, gi.SAMPLE_UNIFORM)
+    V = V[:, :n_vox]
+    g = gi.complex_normal(rng, (n_ant, b.n_f))
+    sf = gi.complex_normal(rng, (filt_ant, b.n_f))
+
+    def step():
+        O.render(X, Gr, W, Te, A, np.ones(n_ant), b)
+        O.render_backward(X, Gr, W, Te, A, np.ones(n_ant), b, g)
+        M, _ = O.filter_forward(sf, Af, V, b)
+        O.filter_backward(M, np.ones(n_vox), Af, V, b)
+
+    terms = 2 * n_pts * n_ant * b.n_f + 2 * n_vox * filt_ant * b.n_f
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = terms * args.steps / dt
+    cores = oracle_threads()
+    desc = (f"per step: oracle render+render_backward {n_pts} points x {n_ant} antennas x {b.n_f} bins, "
+            f"filter+filter_backward {n_vox} voxels x {filt_ant} antennas (FP64 C + OpenMP, host cores)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bounded oracle sample"},
+            "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import geraf_inputs as gi
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import pipeline as PL
+    from paper_2605_29097_gb300 import _build
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    _build.build()
+
+    wl = gi.workload(args.workload)
+    geo = PL.make_geometry(wl, dev)
+    spec = gi.MLPSpec()
+    params_np = gi.mlp_init(spec, seed=1234 + rank)
+    params = torch.as_tensor(params_np, device=dev)
+    field = G.MLPField(params)
+    target = PL.synthetic_target(geo, dev)
+    torch.cuda.synchronize()
+    n_pts = wl.grid.n_pts
+    terms = PL.terms_per_step(geo, n_pts)
+    seed = 7 + 1000 * rank
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    step_id = 0
+    for _ in range(args.warmup):
+        PL.forward_backward(geo, field, target, seed, step_id)
+        step_id += 1
+    G.geraf_poll_device_error()
+    torch.cuda.synchronize()
+
+    names = ["render", "render_backward", "filter", "filter_backward", "fields_backward"]
+    ev = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+          for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for k in range(args.steps):
+        res = PL.forward_backward(geo, field, target, seed, step_id, timers=ev[k])
+        step_id += 1
+    t_end.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    G.geraf_poll_device_error()
+    ms = t_start.elapsed_time(t_end)
+    per_kernel = {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev) / args.steps for nm in names}
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = terms * args.steps * world / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: per step the
+    # inputs (MLP parameters, target heatmap, antenna positions) go host ->
+    # device from pinned memory and the results (loss, parameter gradient,
+    # scalar gradients) come back.
+    h_params = torch.as_tensor(params_np).pin_memory()
+    h_target = target.cpu().pin_memory()
+    h_ant = geo.ant.cpu().pin_memory()
+    h_loss = torch.empty((), dtype=torch.float64).pin_memory()
+    h_dp = torch.empty_like(h_params).pin_memory()
+    h_sc = torch.empty(2).pin_memory()
+    d_params = torch.empty_like(params)
+    d_target = torch.empty_like(target)
+    d_ant = torch.empty_like(geo.ant)
+    geo_e = PL.Geometry(geo.grid, geo.n_ray, geo.n_z, d_ant, geo.vox, geo.band, geo.sharpness, geo.a_tx, geo.mode)
+    field_e = G.MLPField(d_params)
+    e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e_steps):
+        d_params.copy_(h_params, non_blocking=True)
+        d_target.copy_(h_target, non_blocking=True)
+        d_ant.copy_(h_ant, non_blocking=True)
+        r = PL.forward_backward(geo_e, field_e, d_target, seed, step_id)
+        step_id += 1
+        h_loss.copy_(r.loss, non_blocking=True)
+        h_dp.copy_(r.d_params, non_blocking=True)
+        h_sc.copy_(r.d_scalars, non_blocking=True)
+        torch.cuda.synchronize()
+    e_s = time.perf_counter() - w0
+    barrier()
+    e_t = torch.tensor([e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+    e_value = terms * e_steps * world / float(e_t.item())
+    h2d = (h_params.numel() + h_target.numel() + h_ant.numel()) * 4
+    d2h = 8 + h_dp.numel() * 4 + 8
+
+    if rank == 0:
+        peaks = measured_peaks()
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        dom = max(["render", "render_backward"], key=lambda k: per_kernel[k])
+        n_units = n_pts * geo.ant.shape[1] * geo.band.n_f
+        achieved = n_units * FLOPS_PER_TERM / (per_kernel[dom] * 1e-3) / 1e12
+        peak = sm_count * 128 * max_mhz * 1e6 / INSTR_PER_TERM * FLOPS_PER_TERM / 1e12
+        cpu = None
+        if not args.no_cpu_baseline:
+            # intermediate arrays of one step for the oracle sample
+            xyz, apr = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
+            f, grad, a, _ = G.geraf_fields(field, xyz)
+            fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+            fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+            _, _, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
+            tps, secs, cterms, desc = cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, target)
+            cpu = {"value": tps, "unit": "terms/s", "cores": oracle_threads(), "kind": "oracle",
+                   "sample": desc + f"; {cterms:.3g} terms in {secs:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.workload == "c2" else args.workload, "n_pts": n_pts, "n_ant": int(geo.ant.shape[1]),
+                       "n_f": geo.band.n_f, "n_vox": int(geo.vox.shape[1]), "terms_per_step": terms,
+                       "l2": "inputs larger than L2 (per-step MLP activations ~17 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "per_call_ms": {k: round(v, 3) for k, v in per_kernel.items()},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz / "
+                                       f"{INSTR_PER_TERM} instr per term x {FLOPS_PER_TERM} flops per term"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": PL.launches_per_step(field) * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

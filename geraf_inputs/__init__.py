@@ -207,6 +207,12 @@ def workload(name: str) -> Workload:
         h = cube_grid((0.0, 0.0, 0.15), 0.10, (64, 64, 64))
         return Workload(name, 64, 0.002, 128, g, h, SAMPLE_STRATIFIED, "mlp", "fp32",
                         sharpness=2.0 / h.pitch[2])
+    if name == "c2-small":
+        # same array, band and network as c2 with 1/32 of the samples (profiling size)
+        g = cube_grid((0.0, 0.0, 0.15), 0.10, (64, 64, 16))
+        h = cube_grid((0.0, 0.0, 0.15), 0.10, (32, 32, 32))
+        return Workload(name, 64, 0.002, 128, g, h, SAMPLE_STRATIFIED, "mlp", "fp32",
+                        sharpness=2.0 / h.pitch[2])
     if name == "c3":
         g = cube_grid((0.0, 0.0, 0.15), 0.10, (256, 256, 256))
         h = cube_grid((0.0, 0.0, 0.15), 0.10, (64, 64, 64))

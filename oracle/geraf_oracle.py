@@ -169,9 +169,13 @@ def _sigmoid(x):
 def positional_encoding(spec, xyz):
     """gamma [6L, N] and its x-derivatives dgamma [3, 6L, N]. Feature 6k+d is
     sin(2^k pi xt_d), 6k+3+d is cos(2^k pi xt_d), xt = (x - center)/half."""
+    # center and half are FP32 fields of the network description, like every
+    # other input: promote their FP32 values (at octave 2^9 the FP32 rounding
+    # of 0.15 m alone shifts the phase by ~2e-4 rad)
     x = np.asarray(xyz, dtype=np.float64)
-    c = np.asarray(spec.center, dtype=np.float64)[:, None]
-    xt = (x - c) / np.float64(spec.half)
+    c = np.asarray(spec.center, dtype=np.float32).astype(np.float64)[:, None]
+    half = np.float64(np.float32(spec.half))
+    xt = (x - c) / half
     L, N = spec.n_levels, x.shape[1]
     g = np.zeros((6 * L, N))
     dg = np.zeros((3, 6 * L, N))
@@ -180,8 +184,8 @@ def positional_encoding(spec, xyz):
         for d in range(3):
             g[6 * k + d] = np.sin(w * xt[d])
             g[6 * k + 3 + d] = np.cos(w * xt[d])
-            dg[d, 6 * k + d] = w / spec.half * np.cos(w * xt[d])
-            dg[d, 6 * k + 3 + d] = -w / spec.half * np.sin(w * xt[d])
+            dg[d, 6 * k + d] = w / half * np.cos(w * xt[d])
+            dg[d, 6 * k + 3 + d] = -w / half * np.sin(w * xt[d])
     return g, dg
 
 

@@ -1,22 +1,499 @@
-// SDF + reflectiveness MLP (positional encoding, softplus layers, three
-// forward-mode gradient tangents) and its adjoint.
+// SDF + reflectiveness MLP (section 5.2; App. C): sinusoidal positional
+// encoding (section 9.3) of the cube-normalised position, softplus(beta)
+// hidden layers of width 128, head [f, a_logit], a = sigmoid(a_logit), and the
+// SDF gradient G = grad f (the surface normal direction) by three forward-mode
+// tangents carried through every layer. FP32 CUDA-core path.
+//
+// Forward: persistent CTAs of 256 threads; a tile is 32 points x 4 streams
+// (value, d/dx, d/dy, d/dz) = 128 columns. Each layer is a 128 x K x 128 GEMM
+// from shared memory with an 8 x 8 register tile per thread, followed by the
+// fused epilogue (bias, softplus on the value, sigmoid(beta h) times the
+// tangents). Pre-activations of every layer are saved for the adjoint.
+// Adjoint: one kernel for the head, one per hidden layer (top down). Each
+// computes the pre-activation adjoint tile, accumulates the layer's weight
+// gradient in registers across the CTA's tiles (a GEMM reducing over the
+// 128 columns) and propagates the activation adjoint (a GEMM with W^T) in
+// place. Per-CTA weight-gradient partials are summed in FP64 in a fixed order.
+#include <math.h>
+
 #include "common.cuh"
 
 namespace geraf {
 
-geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t* bytes) {
-    *bytes = 0;
-    return fail(GERAF_ERR_UNSUPPORTED, "MLP fields are not built yet");
+namespace {
+
+constexpr int MW = 128;        // hidden width
+constexpr int MTP = 32;        // points per tile
+constexpr int MCOL = 4 * MTP;  // columns per tile
+constexpr int XS = 132;        // padded shared-memory row stride (floats)
+constexpr int MTHREADS = 256;
+
+struct MlpGeom {
+    int L, K0, NH;
+    float beta, cx, cy, cz, half;
+    int64_t n;
+    int n_tiles;
+    int64_t n_params;
+    int64_t off_w[8], off_b[8];   // per layer (hidden layers then head)
+    int k_in[8];
+};
+
+bool make_geom(const geraf_field_desc* d, int64_t n, MlpGeom* g) {
+    if (d->width != MW) {
+        set_error("fields: MLP width %d unsupported (128 only)", d->width);
+        return false;
+    }
+    if (d->n_levels < 1 || 6 * d->n_levels > MW || d->n_hidden < 1 || d->n_hidden > 7 || !(d->half > 0.0f)) {
+        set_error("fields: MLP needs 1 <= n_levels <= 21, 1 <= n_hidden <= 7, half > 0");
+        return false;
+    }
+    g->L = d->n_levels;
+    g->K0 = 6 * d->n_levels;
+    g->NH = d->n_hidden;
+    g->beta = d->beta;
+    g->cx = d->center[0]; g->cy = d->center[1]; g->cz = d->center[2];
+    g->half = d->half;
+    g->n = n;
+    g->n_tiles = (int)((n + MTP - 1) / MTP);
+    int64_t off = 0;
+    for (int l = 0; l <= g->NH; ++l) {
+        const int kin = l == 0 ? g->K0 : MW;
+        const int out = l == g->NH ? 2 : MW;
+        g->k_in[l] = kin;
+        g->off_w[l] = off; off += (int64_t)out * kin;
+        g->off_b[l] = off; off += out;
+    }
+    g->n_params = off;
+    return true;
 }
 
-geraf_status mlp_forward_impl(const geraf_field_desc*, const float*, int64_t, float*, float*, float*, void*, size_t,
-                              cudaStream_t) {
-    return fail(GERAF_ERR_UNSUPPORTED, "MLP fields are not built yet");
+__device__ __forceinline__ float softplus_b(float h, float beta) {
+    return fmaxf(h, 0.0f) + log1pf(expf(-beta * fabsf(h))) / beta;
+}
+__device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Positional encoding of tile points j0 .. j0+31 with their x-derivatives.
+// Column c = 4 p + s (s = 0 value, 1..3 d/dx_{s-1}); feature k in 0 .. K0-1.
+// T = false: X[k * XS + c]; T = true: X[c * XS + k].
+template <bool T>
+__device__ void pe_tile(float* X, const float* __restrict__ xyz, const MlpGeom& g, int64_t j0) {
+    const int t = threadIdx.x;
+    if (t >= 3 * MTP) return;
+    const int p = t / 3, d = t - 3 * (t / 3);
+    int64_t j = j0 + p;
+    if (j >= g.n) j = g.n - 1;
+    const float x = xyz[d * g.n + j];
+    const float c = d == 0 ? g.cx : (d == 1 ? g.cy : g.cz);
+    const double xt = ((double)x - (double)c) / (double)g.half;
+    for (int k = 0; k < g.L; ++k) {
+        const double t2 = xt * (double)(1 << k);
+        const double r = t2 - 2.0 * rint(0.5 * t2);          // exact reduction mod 2
+        float sn, cs;
+        sincospif((float)r, &sn, &cs);                        // sin, cos of 2^k pi xt
+        const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
+        const int fs = 6 * k + d, fc = 6 * k + 3 + d;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            float vs, vc;
+            if (s == 0) { vs = sn; vc = cs; }
+            else if (s - 1 == d) { vs = wk * cs; vc = -wk * sn; }
+            else { vs = 0.0f; vc = 0.0f; }
+            const int col = 4 * p + s;
+            if (T) { X[col * XS + fs] = vs; X[col * XS + fc] = vc; }
+            else { X[fs * XS + col] = vs; X[fc * XS + col] = vc; }
+        }
+    }
 }
 
-geraf_status mlp_backward_impl(const geraf_field_desc*, const float*, int64_t, const void*, const float*, const float*,
-                               const float*, float*, void*, size_t*, cudaStream_t) {
-    return fail(GERAF_ERR_UNSUPPORTED, "MLP fields are not built yet");
+struct FwdArgs {
+    MlpGeom g;
+    const float* params;
+    const float* xyz;
+    float* sdf;
+    float* grad;
+    float* refl;
+    float* saved;   // [NH][n][4][128] pre-activations, then [n] reflectiveness; may be null
+};
+
+__global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    float* X0 = sm;
+    float* X1 = X0 + MW * XS;
+    float* Wt = X1 + MW * XS;             // Wt[k][u]
+    float* bias = Wt + MW * XS;           // [128]
+    float* head = bias + MW;              // [2][128], then 2 biases
+    const MlpGeom& g = a.g;
+    const int t = threadIdx.x;
+    const int ub = t >> 4, cb = t & 15;
+
+    for (int i = t; i < 2 * MW; i += MTHREADS) head[i] = a.params[g.off_w[g.NH] + i];
+    if (t < 2) head[2 * MW + t] = a.params[g.off_b[g.NH] + t];
+    for (int i = t; i < MW * XS; i += MTHREADS) X0[i] = 0.0f;
+    __syncthreads();
+
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+        const int64_t j0 = (int64_t)tile * MTP;
+        pe_tile<false>(X0, a.xyz, g, j0);
+        float* Xin = X0;
+        float* Xout = X1;
+        for (int l = 0; l < g.NH; ++l) {
+            const int K = g.k_in[l];
+            const float* W = a.params + g.off_w[l];
+            for (int idx = t; idx < MW * K; idx += MTHREADS) {
+                const int u = idx / K, k = idx - u * K;
+                Wt[k * XS + u] = W[idx];
+            }
+            if (t < MW) bias[t] = a.params[g.off_b[l] + t];
+            __syncthreads();
+            float acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0f;
+#pragma unroll 2
+            for (int k = 0; k < K; ++k) {
+                const float4 w0 = *reinterpret_cast<const float4*>(Wt + k * XS + 8 * ub);
+                const float4 w1 = *reinterpret_cast<const float4*>(Wt + k * XS + 8 * ub + 4);
+                const float4 x0 = *reinterpret_cast<const float4*>(Xin + k * XS + 4 * cb);
+                const float4 x1 = *reinterpret_cast<const float4*>(Xin + k * XS + 64 + 4 * cb);
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(wv[i], xv[jj], acc[i][jj]);
+            }
+            // epilogue: value column (bias, softplus) and tangents (sigmoid(beta h) * dh)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int u = 8 * ub + i;
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    const int col0 = pp * 64 + 4 * cb;
+                    const float h = acc[i][4 * pp] + bias[u];
+                    const float sg = sigm(g.beta * h);
+                    Xout[u * XS + col0] = softplus_b(h, g.beta);
+                    Xout[u * XS + col0 + 1] = sg * acc[i][4 * pp + 1];
+                    Xout[u * XS + col0 + 2] = sg * acc[i][4 * pp + 2];
+                    Xout[u * XS + col0 + 3] = sg * acc[i][4 * pp + 3];
+                    acc[i][4 * pp] = h;
+                }
+            }
+            if (a.saved) {
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    const int64_t j = j0 + pp * 16 + cb;
+                    if (j < g.n) {
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            float* dst = a.saved + (((int64_t)l * g.n + j) * 4 + s) * MW + 8 * ub;
+                            *reinterpret_cast<float4*>(dst) = make_float4(acc[0][4 * pp + s], acc[1][4 * pp + s],
+                                                                          acc[2][4 * pp + s], acc[3][4 * pp + s]);
+                            *reinterpret_cast<float4*>(dst + 4) = make_float4(
+                                acc[4][4 * pp + s], acc[5][4 * pp + s], acc[6][4 * pp + s], acc[7][4 * pp + s]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            float* tmp = Xin; Xin = Xout; Xout = tmp;
+        }
+        // head: f and a_logit on value columns, G on tangent columns
+        if (t < MCOL) {
+            const int c = t, p = c >> 2, s = c & 3;
+            const int64_t j = j0 + p;
+            float v0 = 0.0f, v1 = 0.0f;
+            for (int u = 0; u < MW; ++u) {
+                const float x = Xin[u * XS + c];
+                v0 = fmaf(head[u], x, v0);
+                v1 = fmaf(head[MW + u], x, v1);
+            }
+            if (j < g.n) {
+                if (s == 0) {
+                    a.sdf[j] = v0 + head[2 * MW];
+                    const float av = sigm(v1 + head[2 * MW + 1]);
+                    if (a.refl) a.refl[j] = av;
+                    if (a.saved) a.saved[(int64_t)g.NH * g.n * 4 * MW + j] = av;
+                } else if (a.grad) {
+                    a.grad[(int64_t)(s - 1) * g.n + j] = v0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- adjoint
+struct BwdArgs {
+    MlpGeom g;
+    const float* params;
+    const float* xyz;
+    const float* saved;
+    const float* d_sdf;
+    const float* d_grad;
+    const float* d_refl;
+    float* zbar;        // [n][4][128] activation adjoint, updated in place layer by layer
+    float* partial;     // [gridDim.x][n_params]
+    int layer;          // hidden layer index for the layer kernel
+};
+
+// head: dL/dW_head, dL/db_head and the adjoint of the last hidden activation
+__global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a) {
+    __shared__ float red[MTHREADS * 2];
+    __shared__ float redb[2 * 8];
+    const MlpGeom& g = a.g;
+    const int t = threadIdx.x, u = t & (MW - 1), half = t >> 7;
+    const float* Wh = a.params + g.off_w[g.NH];
+    const float w0 = Wh[u], w1 = Wh[MW + u];
+    const float* hsv = a.saved + (int64_t)(g.NH - 1) * g.n * 4 * MW;
+    const float* asv = a.saved + (int64_t)g.NH * g.n * 4 * MW;
+    float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+        for (int p = half; p < MTP; p += 2) {
+            const int64_t j = (int64_t)tile * MTP + p;
+            if (j >= g.n) break;
+            const float df = a.d_sdf ? a.d_sdf[j] : 0.0f;
+            const float av = asv[j];
+            const float dl = a.d_refl ? a.d_refl[j] * av * (1.0f - av) : 0.0f;
+            float dG[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) dG[d] = a.d_grad ? a.d_grad[(int64_t)d * g.n + j] : 0.0f;
+            const float* h = hsv + j * 4 * MW;
+            const float h0 = h[u];
+            const float sg = sigm(g.beta * h0);
+            const float z = softplus_b(h0, g.beta);
+            gw0 += df * z;
+            gw1 += dl * z;
+            float* zb = a.zbar + j * 4 * MW;
+            zb[u] = w0 * df + w1 * dl;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                gw0 += dG[d] * sg * h[(d + 1) * MW + u];
+                zb[(d + 1) * MW + u] = w0 * dG[d];
+            }
+            if (u == 0) { gb0 += df; gb1 += dl; }
+        }
+    }
+    red[t] = gw0;
+    red[MTHREADS + t] = gw1;
+    if (u == 0) { redb[2 * half] = gb0; redb[2 * half + 1] = gb1; }
+    __syncthreads();
+    float* out = a.partial + (int64_t)blockIdx.x * g.n_params;
+    if (t < MW) {
+        out[g.off_w[g.NH] + t] = red[t] + red[t + MW];
+        out[g.off_w[g.NH] + MW + t] = red[MTHREADS + t] + red[MTHREADS + t + MW];
+    }
+    if (t == 0) {
+        out[g.off_b[g.NH]] = redb[0] + redb[2];
+        out[g.off_b[g.NH] + 1] = redb[1] + redb[3];
+    }
+}
+
+// hidden layer `layer`: pre-activation adjoint, weight/bias gradient, adjoint of the layer input
+__global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    float* HbT = sm;                 // [128 c][XS]  HbT[c][u]
+    float* ZT = HbT + MCOL * XS;     // [128 c][XS]  ZT[c][k]
+    float* Ws = ZT + MCOL * XS;      // [128 u][XS]  W[u][k]
+    float* redb = Ws + MW * XS;      // [256]
+    const MlpGeom& g = a.g;
+    const int li = a.layer;
+    const int K = g.k_in[li];
+    const int t = threadIdx.x;
+    const float* W = a.params + g.off_w[li];
+    for (int idx = t; idx < MW * K; idx += MTHREADS) {
+        const int u = idx / K, k = idx - u * K;
+        Ws[u * XS + k] = W[idx];
+    }
+    for (int i = t; i < MCOL * XS; i += MTHREADS) ZT[i] = 0.0f;
+    __syncthreads();
+
+    const int ub = t >> 4, kb = t & 15;          // weight-gradient tile
+    const int kq = t >> 4, cq = t & 15;          // input-adjoint tile
+    const int eu = t & (MW - 1), ehalf = t >> 7; // elementwise mapping
+    float accw[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) accw[i][jj] = 0.0f;
+    float accb = 0.0f;
+    const float* hs = a.saved + (int64_t)li * g.n * 4 * MW;
+    const float* hin = li > 0 ? a.saved + (int64_t)(li - 1) * g.n * 4 * MW : nullptr;
+
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+        const int64_t j0 = (int64_t)tile * MTP;
+        // pre-activation adjoint (HbT) and input activations (ZT)
+        for (int p = ehalf; p < MTP; p += 2) {
+            const int64_t j = j0 + p;
+            float hb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            float zi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (j < g.n) {
+                const float* zb = a.zbar + j * 4 * MW;
+                const float* h = hs + j * 4 * MW;
+                const float h0 = h[eu];
+                const float sg = sigm(g.beta * h0);
+                const float dsg = g.beta * sg * (1.0f - sg);
+                const float z0 = zb[eu], z1 = zb[MW + eu], z2 = zb[2 * MW + eu], z3 = zb[3 * MW + eu];
+                hb[0] = z0 * sg + (z1 * h[MW + eu] + z2 * h[2 * MW + eu] + z3 * h[3 * MW + eu]) * dsg;
+                hb[1] = sg * z1; hb[2] = sg * z2; hb[3] = sg * z3;
+                if (hin) {
+                    const float* hi = hin + j * 4 * MW;
+                    const float x0 = hi[eu];
+                    const float s0 = sigm(g.beta * x0);
+                    zi[0] = softplus_b(x0, g.beta);
+                    zi[1] = s0 * hi[MW + eu]; zi[2] = s0 * hi[2 * MW + eu]; zi[3] = s0 * hi[3 * MW + eu];
+                }
+            }
+            accb += hb[0];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                HbT[(4 * p + s) * XS + eu] = hb[s];
+                if (hin) ZT[(4 * p + s) * XS + eu] = zi[s];
+            }
+        }
+        // first layer: its input is the positional encoding (columns of points beyond n
+        // meet a zero HbT and contribute nothing)
+        if (!hin) pe_tile<true>(ZT, a.xyz, g, j0);
+        __syncthreads();
+        // weight gradient: accw[u][k] += sum_c HbT[c][u] ZT[c][k]
+#pragma unroll 2
+        for (int c = 0; c < MCOL; ++c) {
+            const float4 h0 = *reinterpret_cast<const float4*>(HbT + c * XS + 8 * ub);
+            const float4 h1 = *reinterpret_cast<const float4*>(HbT + c * XS + 8 * ub + 4);
+            const float4 z0 = *reinterpret_cast<const float4*>(ZT + c * XS + 4 * kb);
+            const float4 z1 = *reinterpret_cast<const float4*>(ZT + c * XS + 64 + 4 * kb);
+            const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+            const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) accw[i][jj] = fmaf(hv[i], zv[jj], accw[i][jj]);
+        }
+        // adjoint of the layer input: zbar[c][k] = sum_u HbT[c][u] W[u][k]  (in place)
+        if (hin) {
+            float acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) acc[i][kk] = 0.0f;
+            for (int u = 0; u < MW; u += 4) {
+                float4 hv[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) hv[i] = *reinterpret_cast<const float4*>(HbT + (cq + 16 * i) * XS + u);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 wa = *reinterpret_cast<const float4*>(Ws + (u + q) * XS + 8 * kq);
+                    const float4 wb = *reinterpret_cast<const float4*>(Ws + (u + q) * XS + 8 * kq + 4);
+                    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float hq = q == 0 ? hv[i].x : (q == 1 ? hv[i].y : (q == 2 ? hv[i].z : hv[i].w));
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) acc[i][kk] = fmaf(hq, wv[kk], acc[i][kk]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = cq + 16 * i, p = c >> 2, s = c & 3;
+                const int64_t j = j0 + p;
+                if (j < g.n) {
+                    float* dst = a.zbar + (j * 4 + s) * MW + 8 * kq;
+                    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // per-CTA partials
+    float* out = a.partial + (int64_t)blockIdx.x * g.n_params;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int u = 8 * ub + i;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int k = jj < 4 ? 4 * kb + jj : 64 + 4 * kb + (jj - 4);
+            if (k < K) out[g.off_w[li] + (int64_t)u * K + k] = accw[i][jj];
+        }
+    }
+    redb[t] = accb;
+    __syncthreads();
+    if (t < MW) out[g.off_b[li] + t] = redb[t] + redb[t + MW];
+}
+
+__global__ void reduce_partials(const float* __restrict__ partial, int n_cta, int64_t n_params,
+                                float* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_params) return;
+    double s = 0.0;
+    for (int c = 0; c < n_cta; ++c) s += partial[(int64_t)c * n_params + i];
+    out[i] = (float)s;
+}
+
+size_t fwd_smem() { return (size_t)(3 * MW * XS + MW + 2 * MW + 2) * sizeof(float); }
+size_t bwd_smem() { return (size_t)(2 * MCOL * XS + MW * XS + MTHREADS) * sizeof(float); }
+
+int n_ctas_for(int n_tiles) {
+    const int sms = device_sm_count();
+    return n_tiles < sms ? (n_tiles > 0 ? n_tiles : 1) : sms;
+}
+
+}  // namespace
+
+geraf_status mlp_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* bytes) {
+    MlpGeom g;
+    if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
+    *bytes = ((size_t)g.NH * n * 4 * MW + (size_t)n) * sizeof(float);
+    return GERAF_OK;
+}
+
+geraf_status mlp_forward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
+                              float* refl, void* saved, size_t saved_bytes, cudaStream_t st) {
+    MlpGeom g;
+    if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
+    if (d->precision != GERAF_PREC_FP32) return fail(GERAF_ERR_UNSUPPORTED, "fields: MLP precision %d not built", d->precision);
+    if (saved) {
+        size_t need = 0;
+        mlp_saved_bytes(d, n, &need);
+        if (saved_bytes < need) return fail(GERAF_ERR_WORKSPACE, "fields: saved %zu < %zu bytes", saved_bytes, need);
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+        attr = true;
+    }
+    FwdArgs a{g, d->params, xyz, sdf, grad, refl, static_cast<float*>(saved)};
+    mlp_fwd_kernel<<<n_ctas_for(g.n_tiles), MTHREADS, fwd_smem(), st>>>(a);
+    return cuda_status(cudaGetLastError(), "fields(mlp)");
+}
+
+geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
+                               const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
+                               void* ws, size_t* ws_bytes, cudaStream_t st) {
+    MlpGeom g;
+    if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
+    if (d->precision != GERAF_PREC_FP32) return fail(GERAF_ERR_UNSUPPORTED, "fields: MLP precision %d not built", d->precision);
+    const int n_cta = n_ctas_for(g.n_tiles);
+    WsCarver c(ws);
+    float* zbar = c.take<float>((size_t)n * 4 * MW);
+    float* partial = c.take<float>((size_t)n_cta * g.n_params);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used)
+        return fail(GERAF_ERR_WORKSPACE, "fields_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_layer_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
+        attr = true;
+    }
+    BwdArgs a{g, d->params, xyz, static_cast<const float*>(saved), d_sdf, d_grad, d_refl, zbar, partial, 0};
+    mlp_head_bwd_kernel<<<n_cta, MTHREADS, 0, st>>>(a);
+    for (int l = g.NH - 1; l >= 0; --l) {
+        a.layer = l;
+        mlp_layer_bwd_kernel<<<n_cta, MTHREADS, bwd_smem(), st>>>(a);
+    }
+    reduce_partials<<<(unsigned)((g.n_params + 255) / 256), 256, 0, st>>>(partial, n_cta, g.n_params, d_params);
+    return cuda_status(cudaGetLastError(), "fields_backward(mlp)");
 }
 
 }  // namespace geraf

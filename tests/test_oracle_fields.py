@@ -69,8 +69,9 @@ def _torch_mlp(spec, params, xyz):
     shapes = spec.shapes()
     p = torch.tensor(params.astype(np.float64), requires_grad=True)
     x = torch.tensor(xyz.T.astype(np.float64), requires_grad=True)
-    c = torch.tensor(spec.center, dtype=torch.float64)
-    xt = (x - c) / spec.half
+    # the network description carries center and half as FP32 values
+    c = torch.tensor(np.asarray(spec.center, np.float32).astype(np.float64))
+    xt = (x - c) / float(np.float32(spec.half))
     feats = []
     for k in range(spec.n_levels):
         feats.append(torch.sin((2.0 ** k) * np.pi * xt))
