@@ -202,6 +202,27 @@ geraf_status geraf_render(const float* xyz, const float* grad, const float* w, c
                           void* ws, size_t* ws_bytes, float* s_out, void* stream);
 
 /*
+ * geraf_render_noalloc — the same signal tracing as geraf_render, for callers
+ * that cannot allocate device memory themselves (for example a plug-in whose
+ * host application owns every device allocation, or code that runs where the
+ * application forbids new allocations): it takes no workspace and allocates
+ * nothing. The paper has no counterpart; this is an interface convenience.
+ * Its scratch is one static device array of 32 MiB inside this library, held
+ * by every GPU that loads the library until the process exits. The first call
+ * on a device looks up that array's device address (once per device, with
+ * the device current); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (on different
+ * streams or from different host threads) race and give undefined results.
+ * Inputs that need more than 32 MiB of scratch (the packed points, 48 bytes
+ * each, plus at least one n_ant x 32*ceil(n_f/32) complex partial) are
+ * rejected with GERAF_ERR_UNSUPPORTED; use geraf_render for them. Results
+ * match geraf_render to FP32 rounding (the split of the point sum may differ).
+ */
+geraf_status geraf_render_noalloc(const float* xyz, const float* grad, const float* w, const float* t_eff,
+                                  int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                                  const geraf_band* band, int32_t flags, float* s_out, void* stream);
+
+/*
  * geraf_render_backward — adjoint of geraf_render (App. A.5, Algorithm 2
  * [2]) for g_s = dL/dRe s + j dL/dIm s [n_ant][n_f] complex:
  *   q_ij = sum_n Re(conj(g_in) exp(-j 2 pi f_n tau_ij)),

@@ -42,6 +42,7 @@ SIGNATURES = {
     "geraf_blend": [vp, vp, i32, i32, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp, vp],
     "geraf_blend_backward": [vp, vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp, vp, vp, szp, vp],
     "geraf_render": [vp, vp, vp, vp, i64, vp, vp, i32, ctypes.POINTER(GerafBand), i32, vp, szp, vp, vp],
+    "geraf_render_noalloc": [vp, vp, vp, vp, i64, vp, vp, i32, ctypes.POINTER(GerafBand), i32, vp, vp],
     "geraf_render_backward": [vp, vp, vp, vp, i64, vp, vp, i32, ctypes.POINTER(GerafBand), i32, vp, vp, szp,
                               vp, vp, vp, vp],
     "geraf_filter": [vp, vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp, vp, vp, vp],

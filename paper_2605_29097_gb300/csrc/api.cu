@@ -23,6 +23,8 @@ geraf_status render_impl(const float*, const float*, const float*, const float*,
 geraf_status render_backward_impl(const float*, const float*, const float*, const float*, int64_t, const float*,
                                   const float*, int32_t, const geraf_band*, int32_t, const float*, void*, size_t*,
                                   float*, float*, float*, cudaStream_t);
+geraf_status render_noalloc_impl(const float*, const float*, const float*, const float*, int64_t, const float*,
+                                 const float*, int32_t, const geraf_band*, int32_t, float*, cudaStream_t);
 geraf_status filter_impl(const float*, const float*, int32_t, const geraf_band*, const float*, int64_t,
                          const float*, const float*, void*, size_t*, float*, float*, double*, float*, cudaStream_t);
 geraf_status filter_backward_impl(const float*, int32_t, const geraf_band*, const float*, int64_t, const float*,
@@ -232,6 +234,16 @@ geraf_status geraf_render(const float* xyz, const float* grad, const float* w, c
     if (ws) REQUIRE(xyz && grad && w && t_eff && ant_xyz && c_ant && s_out, "render: null input or output");
     return render_impl(xyz, grad, w, t_eff, n_pts, ant_xyz, c_ant, n_ant, band, flags, ws, ws_bytes, s_out,
                        S(stream));
+}
+
+geraf_status geraf_render_noalloc(const float* xyz, const float* grad, const float* w, const float* t_eff,
+                                  int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                                  const geraf_band* band, int32_t flags, float* s_out, void* stream) {
+    REQUIRE(n_pts >= 1 && n_ant >= 1, "render_noalloc: need n_pts >= 1 and n_ant >= 1");
+    REQUIRE(n_pts < (1ll << 31), "render_noalloc: n_pts must be below 2^31");
+    REQUIRE(band, "render_noalloc: band must not be NULL");
+    REQUIRE(xyz && grad && w && t_eff && ant_xyz && c_ant && s_out, "render_noalloc: null input or output");
+    return render_noalloc_impl(xyz, grad, w, t_eff, n_pts, ant_xyz, c_ant, n_ant, band, flags, s_out, S(stream));
 }
 
 geraf_status geraf_render_backward(const float* xyz, const float* grad, const float* w, const float* t_eff,

@@ -24,6 +24,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace geraf {
@@ -768,6 +770,85 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     to_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
     render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, d_w, d_teff, d_grad);
     return check_launch("render_backward");
+}
+
+}  // namespace geraf
+
+// ================================================= render without allocation
+// Variant of render for callers that cannot allocate device memory: its
+// scratch (packed point tiles, antenna records, split partials) lives in one
+// file-scope device array of kNoAllocScratchBytes, which every GPU that loads
+// this library holds until the process exits. All calls share the array, so
+// calls that overlap on the GPU (other streams, other host threads) race on
+// it. Nothing in it must start at zero: every call rewrites all the records
+// and partials it later reads.
+namespace geraf {
+namespace {
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_render_scratch[kNoAllocScratchBytes];
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64];
+}  // namespace
+
+geraf_status render_noalloc_impl(const float* xyz, const float* grad, const float* w, const float* t_eff,
+                                 int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                                 const geraf_band* band, int32_t flags, float* s_out, cudaStream_t st) {
+    // once per device, with that device current: the device address of the scratch array
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "render_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(GERAF_ERR_UNSUPPORTED, "render_noalloc: device index %d above 63", dev);
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_render_scratch);
+            if (e != cudaSuccess) return cuda_status(e, "render_noalloc: cudaGetSymbolAddress");
+            g_scratch_addr[dev] = p;
+        }
+        base = g_scratch_addr[dev];
+    }
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    ToBinsPlan p = plan_to_bins(n_pts, n_ant, bk.g);
+    // fewer point splits when the partials would not fit the static scratch
+    WsCarver fixed(nullptr);
+    fixed.take<PtRec>((size_t)p.n_tiles * p.TP);
+    fixed.take<float4>(p.n_ant_pad);
+    const size_t head = align_up(fixed.used, 256);
+    const size_t per_split = (size_t)p.n_ant_pad * 32 * p.G * sizeof(float2);
+    if (head + per_split > kNoAllocScratchBytes)
+        return fail(GERAF_ERR_UNSUPPORTED,
+                    "render_noalloc: %lld points x %d antennas x %d bins need %zu bytes of scratch, above the "
+                    "%zu-byte static limit (use geraf_render with a caller workspace)",
+                    (long long)n_pts, n_ant, band->n_f, head + per_split, kNoAllocScratchBytes);
+    const int max_splits = (int)((kNoAllocScratchBytes - head) / per_split);
+    if (p.splits > max_splits) {
+        p.tiles_per_split = (p.n_tiles + max_splits - 1) / max_splits;
+        p.splits = (p.n_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
+    }
+    WsCarver c(base);
+    PtRec* pts = c.take<PtRec>((size_t)p.n_tiles * p.TP);
+    float4* ant = c.take<float4>(p.n_ant_pad);
+    float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
+    if (c.used > kNoAllocScratchBytes) return fail(GERAF_ERR_UNSUPPORTED, "render_noalloc: scratch overflow");
+    int* err = device_error_word();
+    const int64_t n_pad = (int64_t)p.n_tiles * p.TP;
+    pack_render_points<<<grid1d(n_pad, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pad,
+                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
+    pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, p.n_ant_pad, ant);
+    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk};
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    to_bins_kernel<false><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
+    reduce_bins<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(part, p.splits, n_ant, p.n_ant_pad,
+                                                                         band->n_f, 32 * p.G,
+                                                                         reinterpret_cast<float2*>(s_out));
+    return check_launch("render_noalloc");
 }
 
 }  // namespace geraf

@@ -211,6 +211,22 @@ def geraf_render(xyz, grad, w, t_eff, ant, c_ant, band: Band, directional=True):
     return torch.view_as_complex(out)
 
 
+def geraf_render_noalloc(xyz, grad, w, t_eff, ant, c_ant, band: Band, directional=True):
+    """Signal tracing without a workspace (the library's static scratch); only
+    the output is allocated here. For callers that must not allocate device
+    scratch per call; see include/geraf.h for the size limit and the rule that
+    overlapping calls race."""
+    for t, nm in ((xyz, "xyz"), (grad, "grad"), (w, "w"), (t_eff, "t_eff"), (ant, "ant"), (c_ant, "c_ant")):
+        _req(t, nm)
+    n_pts, n_ant = xyz.shape[-1], ant.shape[-1]
+    out = torch.empty(n_ant, band.n_f, 2, dtype=torch.float32, device=xyz.device)
+    cb = band.c()
+    check(_lib.lib().geraf_render_noalloc(_p(xyz), _p(grad), _p(w), _p(t_eff), n_pts, _p(ant), _p(c_ant), n_ant,
+                                          ctypes.byref(cb), RENDER_DIRECTIONAL if directional else 0, _p(out),
+                                          _stream()))
+    return torch.view_as_complex(out)
+
+
 def geraf_render_backward(xyz, grad, w, t_eff, ant, c_ant, band: Band, g_s, directional=True):
     """Adjoint of render -> (d_w [n], d_teff [n], d_grad [3, n])."""
     g = _sig(g_s, "g_s")
