@@ -103,22 +103,23 @@ __global__ void pack_antennas(const float* __restrict__ ant, const float* __rest
 }
 
 // antenna tile rows for the to-points kernels: 16-byte head (x, y, z, c)
-// followed by the signal row zero-padded to 32*G bins.
+// followed by one float4 (s_re, s_re, s_im, s_im) per bin, zero-padded to
+// 32*G bins, so that one 16-byte load gives the packed pairs (s_re, s_re)
+// and (s_im, s_im) of the two-lane Horner sums.
 __global__ void pack_antenna_rows(const float* __restrict__ ant, const float* __restrict__ c_ant,
                                   const float2* __restrict__ sig, int n_ant, int n_ant_pad, int n_f,
                                   int n_f_pad, float4* __restrict__ out) {
     int i = blockIdx.x;
     if (i >= n_ant_pad) return;
-    float4* row = out + (size_t)i * (1 + n_f_pad / 2);
+    float4* row = out + (size_t)i * (1 + n_f_pad);
     if (threadIdx.x == 0) {
         int k = i < n_ant ? i : 0;
         row[0] = make_float4(ant[k], ant[n_ant + k], ant[2 * n_ant + k], c_ant ? c_ant[k] : 0.0f);
     }
-    float2* bins = reinterpret_cast<float2*>(row + 1);
     for (int n = threadIdx.x; n < n_f_pad; n += blockDim.x) {
         float2 v = make_float2(0.0f, 0.0f);
         if (i < n_ant && n < n_f) v = sig[(size_t)i * n_f + n];
-        bins[n] = v;
+        row[1 + n] = make_float4(v.x, v.x, v.y, v.y);
     }
 }
 
@@ -131,7 +132,7 @@ struct ToBinsArgs {
     const float4* ant;       // n_ant_pad records
     float2* partial;         // [splits][n_ant_pad][32 G]
     int* err;
-    int tp;                  // points per tile (16 or 32)
+    int tp;                  // points per tile (8, 16 or 32; even)
     int n_tiles;             // total point tiles
     int tiles_per_split;
     int n_ant_pad;
@@ -152,8 +153,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
     int* abort_flag = reinterpret_cast<int*>(smem + 16);
     PtRec* tiles = reinterpret_cast<PtRec*>(smem + 32);                      // [2][TP]
     float4* ant_s = reinterpret_cast<float4*>(smem + 32 + 2 * TP * sizeof(PtRec));
-    float* prep = reinterpret_cast<float*>(ant_s + A_T);                     // [5][TP][A_T]
-    float2* outer = reinterpret_cast<float2*>(prep + 5 * TP * A_T);          // [2][32][TB_THREADS]
+    float* prep = reinterpret_cast<float*>(ant_s + A_T);                     // [6][TP][A_T]
+    float2* outer = reinterpret_cast<float2*>(prep + 6 * TP * A_T);          // [2][32][TB_THREADS]
 
     const int ant0 = blockIdx.x * A_T;
     const int split = blockIdx.y;
@@ -185,9 +186,10 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
 
     const float kh = args.bk.k[2 * blk], kl = args.bk.k[2 * blk + 1];
     const float kd = args.bk.kd;
-    float2 acc[32];
+    // accumulators of bins 32 blk + m: lanes = even / odd points of the tile
+    f2 accr[32], acci[32];
 #pragma unroll
-    for (int m = 0; m < 32; ++m) acc[m] = make_float2(0.0f, 0.0f);
+    for (int m = 0; m < 32; ++m) accr[m] = acci[m] = 0ull;
 
     for (int it = 0; it < n_my; ++it) {
         const int buf = it & 1;
@@ -212,6 +214,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
                 float D = fmaxf(nd * nd * inv_r2 - P.c.x, 0.0f);
                 float tt = __saturatef(P.b.w - A4.w);
                 amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
+            } else {
+                amp = P.a.w;         // c_re (c_im goes to prep row 5)
             }
             float dl = R.rh * kd;
             dl = dl - rintf(dl);
@@ -222,53 +226,63 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
             prep[(2 * TP + p) * A_T + a] = amp;
             prep[(3 * TP + p) * A_T + a] = cs;
             prep[(4 * TP + p) * A_T + a] = -sn;     // step exp(-j 2 pi delta)
+            if (kComplexAmp) prep[(5 * TP + p) * A_T + a] = P.b.x;
         }
         __syncthreads();
-        // ---- 32-bin recurrence per (point, my antenna, my block)
+        // ---- 32-bin recurrence per (point pair, my antenna, my block), packed f32x2
         if (active) {
-            for (int p = 0; p < TP; ++p) {
-                const float rh = prep[(0 * TP + p) * A_T + a_slot];
-                const float rl = prep[(1 * TP + p) * A_T + a_slot];
-                const float wr = prep[(3 * TP + p) * A_T + a_slot];
-                const float wi = prep[(4 * TP + p) * A_T + a_slot];
-                const float fr = phase_frac(rh, rl, kh, kl);
-                float sn, cs;
-                __sincosf(6.28318530717958648f * fr, &sn, &cs);
-                float qr, qi;
-                if (!kComplexAmp) {
-                    const float amp = prep[(2 * TP + p) * A_T + a_slot];
-                    qr = amp * cs;
-                    qi = -amp * sn;
-                } else {
-                    const float cr = tile[p].a.w, ci = tile[p].b.x;
-                    // (cr + j ci)(cs - j sn)
-                    qr = cr * cs + ci * sn;
-                    qi = ci * cs - cr * sn;
+            for (int p = 0; p < TP; p += 2) {
+                float qr[2], qi[2], wr[2], wi[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float rh = prep[(0 * TP + p + h) * A_T + a_slot];
+                    const float rl = prep[(1 * TP + p + h) * A_T + a_slot];
+                    wr[h] = prep[(3 * TP + p + h) * A_T + a_slot];
+                    wi[h] = prep[(4 * TP + p + h) * A_T + a_slot];
+                    const float fr = phase_frac(rh, rl, kh, kl);
+                    float sn, cs;
+                    __sincosf(6.28318530717958648f * fr, &sn, &cs);
+                    const float amp = prep[(2 * TP + p + h) * A_T + a_slot];
+                    if (!kComplexAmp) {
+                        qr[h] = amp * cs;
+                        qi[h] = -amp * sn;
+                    } else {
+                        const float ci = prep[(5 * TP + p + h) * A_T + a_slot];
+                        // (c_re + j c_im)(cs - j sn)
+                        qr[h] = amp * cs + ci * sn;
+                        qi[h] = ci * cs - amp * sn;
+                    }
                 }
+                f2 Qr = pk2(qr[0], qr[1]), Qi = pk2(qi[0], qi[1]);
+                const f2 Wr = pk2(wr[0], wr[1]), Wi = pk2(wi[0], wi[1]), NWi = pk2(-wi[0], -wi[1]);
 #pragma unroll
                 for (int m = 0; m < 32; ++m) {
-                    acc[m].x += qr;
-                    acc[m].y += qi;
-                    const float nr = fmaf(qr, wr, -qi * wi);
-                    const float ni = fmaf(qr, wi, qi * wr);
-                    qr = nr;
-                    qi = ni;
+                    accr[m] = add2(accr[m], Qr);
+                    acci[m] = add2(acci[m], Qi);
+                    const f2 t1 = mul2(Qi, NWi);
+                    const f2 t2 = mul2(Qi, Wr);
+                    const f2 nr = fma2(Qr, Wr, t1);
+                    Qi = fma2(Qr, Wi, t2);
+                    Qr = nr;
                 }
             }
         }
-        // ---- Kahan flush of the inner sums
+        // ---- Kahan flush of the inner sums (both lanes)
         if (active && (((it + 1) % TB_FLUSH_TILES) == 0 || it + 1 == n_my)) {
 #pragma unroll
             for (int m = 0; m < 32; ++m) {
+                float r0, r1, i0, i1;
+                upk2(accr[m], r0, r1);
+                upk2(acci[m], i0, i1);
                 float2 hi = outer[m * TB_THREADS + t];
                 float2 lo = outer[(32 + m) * TB_THREADS + t];
-                float yx = __fsub_rn(acc[m].x, lo.x), yy = __fsub_rn(acc[m].y, lo.y);
+                float yx = __fsub_rn(__fadd_rn(r0, r1), lo.x), yy = __fsub_rn(__fadd_rn(i0, i1), lo.y);
                 float sx = __fadd_rn(hi.x, yx), sy = __fadd_rn(hi.y, yy);
                 lo.x = __fsub_rn(__fsub_rn(sx, hi.x), yx);
                 lo.y = __fsub_rn(__fsub_rn(sy, hi.y), yy);
                 outer[m * TB_THREADS + t] = make_float2(sx, sy);
                 outer[(32 + m) * TB_THREADS + t] = lo;
-                acc[m] = make_float2(0.0f, 0.0f);
+                accr[m] = acci[m] = 0ull;
             }
         }
         __syncthreads();   // tile and prep buffers are free again
@@ -306,8 +320,7 @@ __global__ void reduce_bins(const float2* __restrict__ partial, int splits, int 
 
 // ----------------------------------------------------------- to-points kernel
 constexpr int TPK_THREADS = 128;
-constexpr int TPK_V = 2;          // points per thread
-constexpr int TPK_AT = 8;         // antennas per tile
+constexpr int TPK_V = 2;          // points per thread = the two lanes of the packed Horner sums
 
 enum { MODE_FILTER = 0, MODE_RENDER_BWD = 1 };
 
@@ -315,11 +328,12 @@ struct ToPointsArgs {
     const PtRec* pts;          // padded point records (render backward)
     const float* vox;          // [3][n] voxel positions (filter)
     int64_t n;                 // points / voxels
-    const float4* rows;        // antenna tile rows
-    int row_f4;                // float4 per antenna row = 1 + n_f_pad/2
+    const float4* rows;        // antenna rows: head (x, y, z, c) + per bin (s_re, s_re, s_im, s_im)
+    int row_f4;                // float4 per antenna row = 1 + n_f_pad
+    int at;                    // antennas per tile
     int n_ant_tiles;
     int tiles_per_split;
-    float* partial;            // filter: float2 [splits][n]; render bwd: float [splits][5][n]
+    float* partial;            // filter: float2 [splits][n]; render bwd: float [splits][6][n]
     int* err;
     BandK bk;
 };
@@ -329,15 +343,16 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int* abort_flag = reinterpret_cast<int*>(smem + 16);
-    float4* rows = reinterpret_cast<float4*>(smem + 32);   // [2][TPK_AT][row_f4]
+    float4* rows = reinterpret_cast<float4*>(smem + 32);   // [2][at][row_f4]
     const int G = args.bk.g;
     const int row_f4 = args.row_f4;
+    const int AT = args.at;
     const int t = threadIdx.x;
     const int split = blockIdx.y;
     const int tile0 = split * args.tiles_per_split;
     const int tile1 = min(tile0 + args.tiles_per_split, args.n_ant_tiles);
     const int n_my = tile1 - tile0;
-    const uint32_t tile_bytes = (uint32_t)(TPK_AT * row_f4 * sizeof(float4));
+    const uint32_t tile_bytes = (uint32_t)(AT * row_f4 * sizeof(float4));
 
     if (t == 0) {
         mbar_init(&bar[0], 1);
@@ -349,8 +364,7 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
     if (t == 0) {
         for (int s = 0; s < 2 && s < n_my; ++s) {
             mbar_arrive_expect_tx(&bar[s], tile_bytes);
-            tma_load_1d(rows + s * TPK_AT * row_f4, args.rows + (size_t)(tile0 + s) * TPK_AT * row_f4,
-                        tile_bytes, &bar[s]);
+            tma_load_1d(rows + s * AT * row_f4, args.rows + (size_t)(tile0 + s) * AT * row_f4, tile_bytes, &bar[s]);
         }
     }
 
@@ -391,16 +405,16 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
             if (t == 0) atomicOr(args.err, 1);
             return;
         }
-        const float4* tile = rows + buf * TPK_AT * row_f4;
+        const float4* tile = rows + buf * AT * row_f4;
         float in[TPK_V][NACC];
 #pragma unroll
         for (int v = 0; v < TPK_V; ++v)
 #pragma unroll
             for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
 
-        for (int a = 0; a < TPK_AT; ++a) {
+        for (int a = 0; a < AT; ++a) {
             const float4 head = tile[a * row_f4];
-            const float2* sig = reinterpret_cast<const float2*>(tile + a * row_f4 + 1);
+            const ulonglong2* sig = reinterpret_cast<const ulonglong2*>(tile + a * row_f4 + 1);
             Range R[TPK_V];
             float zr[TPK_V], zi[TPK_V], hr[TPK_V], him[TPK_V];
 #pragma unroll
@@ -415,33 +429,25 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
                 hr[v] = 0.0f;
                 him[v] = 0.0f;
             }
+            const f2 Zr = pk2(zr[0], zr[1]), Zi = pk2(zi[0], zi[1]), NZi = pk2(-zi[0], -zi[1]);
             for (int b = 0; b < G; ++b) {
                 const float kh = args.bk.k[2 * b], kl = args.bk.k[2 * b + 1];
-                const float4* s4 = reinterpret_cast<const float4*>(sig + 32 * b);
+                const ulonglong2* sb = sig + 32 * b;
+                // Horner: sum_m s_m z^m, both points at once (lanes), s broadcast to both lanes
+                const ulonglong2 top = sb[31];
+                f2 Ar = top.x, Ai = top.y;
+#pragma unroll
+                for (int m = 30; m >= 0; --m) {
+                    const ulonglong2 sv = sb[m];
+                    const f2 t1 = fma2(Ai, NZi, sv.x);
+                    const f2 t2 = fma2(Ai, Zr, sv.y);
+                    const f2 nr = fma2(Ar, Zr, t1);
+                    Ai = fma2(Ar, Zi, t2);
+                    Ar = nr;
+                }
                 float ar[TPK_V], ai[TPK_V];
-                {
-                    const float4 top = s4[15];   // bins 30, 31
-#pragma unroll
-                    for (int v = 0; v < TPK_V; ++v) {
-                        ar[v] = top.z;
-                        ai[v] = top.w;
-                        const float nr = fmaf(ar[v], zr[v], fmaf(-ai[v], zi[v], top.x));
-                        const float ni = fmaf(ar[v], zi[v], fmaf(ai[v], zr[v], top.y));
-                        ar[v] = nr;
-                        ai[v] = ni;
-                    }
-                }
-#pragma unroll
-                for (int m2 = 14; m2 >= 0; --m2) {
-                    const float4 sv = s4[m2];    // bins 2 m2, 2 m2 + 1
-#pragma unroll
-                    for (int v = 0; v < TPK_V; ++v) {
-                        float nr = fmaf(ar[v], zr[v], fmaf(-ai[v], zi[v], sv.z));
-                        float ni = fmaf(ar[v], zi[v], fmaf(ai[v], zr[v], sv.w));
-                        ar[v] = fmaf(nr, zr[v], fmaf(-ni, zi[v], sv.x));
-                        ai[v] = fmaf(nr, zi[v], fmaf(ni, zr[v], sv.y));
-                    }
-                }
+                upk2(Ar, ar[0], ar[1]);
+                upk2(Ai, ai[0], ai[1]);
 #pragma unroll
                 for (int v = 0; v < TPK_V; ++v) {
                     const float fr = phase_frac(R[v].rh, R[v].rl, kh, kl);
@@ -498,8 +504,8 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
         __syncthreads();
         if (t == 0 && it + 2 < n_my) {
             mbar_arrive_expect_tx(&bar[buf], tile_bytes);
-            tma_load_1d(rows + buf * TPK_AT * row_f4, args.rows + (size_t)(tile0 + it + 2) * TPK_AT * row_f4,
-                        tile_bytes, &bar[buf]);
+            tma_load_1d(rows + buf * AT * row_f4, args.rows + (size_t)(tile0 + it + 2) * AT * row_f4, tile_bytes,
+                        &bar[buf]);
         }
     }
 #pragma unroll
@@ -605,7 +611,7 @@ ToBinsPlan plan_to_bins(int64_t n_pts, int n_ant, int G) {
     p.G = G;
     p.A_T = TB_THREADS / G;
     if (p.A_T < 1) p.A_T = 1;
-    p.TP = (p.A_T >= 64) ? 16 : 32;
+    p.TP = (p.A_T >= 128) ? 8 : (p.A_T >= 64 ? 16 : 32);   // prep rows <= 32 KB, two CTAs per SM
     p.n_ant_pad = (int)((n_ant + p.A_T - 1) / p.A_T) * p.A_T;
     p.ant_ctas = p.n_ant_pad / p.A_T;
     p.n_tiles = (int)((n_pts + p.TP - 1) / p.TP);
@@ -613,13 +619,13 @@ ToBinsPlan plan_to_bins(int64_t n_pts, int n_ant, int G) {
     p.splits = choose_splits(p.ant_ctas, 2, p.n_tiles);
     p.tiles_per_split = (p.n_tiles + p.splits - 1) / p.splits;
     p.splits = (p.n_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
-    p.smem = 32 + 2 * p.TP * sizeof(PtRec) + p.A_T * sizeof(float4) + 5 * p.TP * p.A_T * sizeof(float) +
+    p.smem = 32 + 2 * p.TP * sizeof(PtRec) + p.A_T * sizeof(float4) + 6 * p.TP * p.A_T * sizeof(float) +
              2 * 32 * TB_THREADS * sizeof(float2);
     return p;
 }
 
 struct ToPointsPlan {
-    int G, n_f_pad, row_f4, n_ant_pad, n_ant_tiles, pt_ctas, splits, tiles_per_split;
+    int G, n_f_pad, row_f4, at, n_ant_pad, n_ant_tiles, pt_ctas, splits, tiles_per_split;
     size_t smem;
 };
 
@@ -627,14 +633,15 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
     ToPointsPlan p;
     p.G = G;
     p.n_f_pad = 32 * G;
-    p.row_f4 = 1 + p.n_f_pad / 2;
-    p.n_ant_pad = (n_ant + TPK_AT - 1) / TPK_AT * TPK_AT;
-    p.n_ant_tiles = p.n_ant_pad / TPK_AT;
+    p.row_f4 = 1 + p.n_f_pad;
+    p.at = G <= 8 ? 8 : (G <= 16 ? 4 : 2);     // two tiles <= ~132 KB of shared memory
+    p.n_ant_pad = (n_ant + p.at - 1) / p.at * p.at;
+    p.n_ant_tiles = p.n_ant_pad / p.at;
     p.pt_ctas = (int)((n + TPK_THREADS * TPK_V - 1) / (TPK_THREADS * TPK_V));
     p.splits = choose_splits(p.pt_ctas, 8, p.n_ant_tiles);
     p.tiles_per_split = (p.n_ant_tiles + p.splits - 1) / p.splits;
     p.splits = (p.n_ant_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
-    p.smem = 32 + 2 * TPK_AT * p.row_f4 * sizeof(float4);
+    p.smem = 32 + 2 * (size_t)p.at * p.row_f4 * sizeof(float4);
     return p;
 }
 
@@ -725,7 +732,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     int* err = device_error_word();
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s),
                                                            n_ant, p.n_ant_pad, band->n_f, p.n_f_pad, rows);
-    ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.n_ant_tiles, p.tiles_per_split,
+    ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split,
                    reinterpret_cast<float*>(part), err, bk};
     static bool attr_set = false;
     if (!attr_set) {
@@ -760,7 +767,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
                                                            (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s),
                                                            n_ant, p.n_ant_pad, band->n_f, p.n_f_pad, rows);
-    ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.n_ant_tiles, p.tiles_per_split, part, err, bk};
+    ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split, part, err, bk};
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
