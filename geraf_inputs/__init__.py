@@ -180,6 +180,32 @@ def c1_point_reflector(grid: Grid):
                      for d in range(3)], dtype=np.float32)
 
 
+C4_OCCLUDER_Z = 0.10       # thin dielectric occluder plane between the array and the objects
+C4_OCCLUDER_ATTEN = 0.5    # round-trip amplitude factor behind it
+C4_SNR_DB = 10.0
+
+
+def c4_noise(seed: int, shape, signal_power: float) -> np.ndarray:
+    """Complex Gaussian noise of power signal_power / 10^(SNR/10), seeded."""
+    rng = np.random.default_rng(10_000 + seed)
+    return complex_normal(rng, shape, scale=np.sqrt(signal_power / 10.0 ** (C4_SNR_DB / 10.0)))
+
+
+def c4_scene(seed: int, center=(0.0, 0.0, 0.15), side=0.12) -> Scene:
+    """1-8 random ellipsoids and boxes, axes U[1, 4] cm, reflectiveness
+    U[0.2, 1], centres inside the cube shrunk by the largest axis."""
+    rng = np.random.default_rng(seed)
+    prims = []
+    for _ in range(int(rng.integers(1, 9))):
+        kind = PRIM_ELLIPSOID if rng.uniform() < 0.5 else PRIM_BOX
+        axes = rng.uniform(0.01, 0.04, 3)          # full axes; radii / half extents are half of them
+        ext = axes / 2.0
+        lim = side / 2.0 - ext.max()
+        c = tuple(float(center[d] + rng.uniform(-lim, lim)) for d in range(3))
+        prims.append(Prim(kind, float(rng.uniform(0.2, 1.0)), c, tuple(float(v) for v in ext)))
+    return Scene(prims)
+
+
 @dataclass
 class Workload:
     name: str
@@ -221,6 +247,11 @@ def workload(name: str) -> Workload:
     if name == "c4":
         g = cube_grid((0.0, 0.0, 0.15), 0.12, (256, 256, 256))
         h = cube_grid((0.0, 0.0, 0.15), 0.12, (64, 64, 64))
-        return Workload(name, 64, 0.002, 128, g, h, SAMPLE_STRATIFIED, "mlp", "bf16",
+        return Workload(name, 64, 0.002, 128, g, h, SAMPLE_STRATIFIED, "mlp", "fp32",
+                        sharpness=2.0 / h.pitch[2])
+    if name == "c4-small":
+        g = cube_grid((0.0, 0.0, 0.15), 0.12, (32, 32, 32))
+        h = cube_grid((0.0, 0.0, 0.15), 0.12, (16, 16, 16))
+        return Workload(name, 8, 0.004, 16, g, h, SAMPLE_STRATIFIED, "mlp", "fp32",
                         sharpness=2.0 / h.pitch[2])
     raise KeyError(name)

@@ -411,3 +411,145 @@ def heatmap_loss(P, target, mask=None):
     m = np.ones_like(P) if mask is None else np.asarray(mask, np.float64)
     r = P - t
     return float((m * r * r).sum()), 2.0 * m * r
+
+
+# --------------------------------------------------------------------------
+# Learned proposal sampler (the paper is silent; its definition here follows
+# the proposal-network idea of mip-NeRF 360: a small network predicts, per
+# primary column, a depth distribution from which the lensless samples are
+# drawn; it is trained online on the blended weights of the method itself).
+#   grid cell (gx, gy, gz) of a G0 x G1 x G2 grid over the sample cube holds an
+#   F-dim feature (FP16 values); an MLP (n_hidden layers of `width`,
+#   softplus(beta) like the field network, output 1 logit) maps it to a logit;
+#   per grid column q_k = (1 - eps) softmax(logits)_k + eps / G2.
+#   Sampling column (ix, iy) of the fine grid uses grid column
+#   (ix * G0 // nx, iy * G1 // ny). Integer CDF: c_k = max(1, floor(q_k 2^20)),
+#   C_{k+1} = C_k + c_k, W = C_G2; sample j of D: m_j = SplitMix64 output
+#   (step<<42 | 3<<40 | ray*D + j) >> 40 (24 bits), u_j = ((j<<24) + m_j) W //
+#   (D<<24); k = the cell with C_k <= u_j < C_{k+1}; depth
+#   z = z0 + (k + (u_j - C_k + 0.5)/c_k) * pz_cell in FP64, rounded to FP32.
+# --------------------------------------------------------------------------
+
+def proposal_shapes(feat, width, n_hidden):
+    dims = [feat] + [width] * n_hidden
+    return [(dims[l + 1], dims[l]) for l in range(n_hidden)] + [(1, width)]
+
+
+def _unpack(shapes, params):
+    out, off = [], 0
+    params = np.asarray(params, dtype=np.float32).astype(np.float64)
+    for o, i in shapes:
+        W = params[off:off + o * i].reshape(o, i); off += o * i
+        b = params[off:off + o]; off += o
+        out.append((W, b))
+    return out
+
+
+def proposal_logits(features, params, width, n_hidden, beta):
+    """features [n_cells, F] (FP16 values) -> logits [n_cells] and a cache."""
+    Fe = np.asarray(features, dtype=np.float16).astype(np.float64)
+    layers = _unpack(proposal_shapes(Fe.shape[1], width, n_hidden), params)
+    z = Fe.T
+    cache = {"z": [z], "h": []}
+    for W, b in layers[:-1]:
+        h = W @ z + b[:, None]
+        z = _softplus(h, beta)
+        cache["h"].append(h); cache["z"].append(z)
+    W, b = layers[-1]
+    return (W @ z + b[:, None])[0], cache
+
+
+def proposal_q(logits, gshape, eps):
+    """Per grid column depth distribution q [G2, G1, G0] from logits laid out
+    [G2][G1][G0] (cell index (gz*G1 + gy)*G0 + gx)."""
+    G0, G1, G2 = gshape
+    L = np.asarray(logits, np.float64).reshape(G2, G1, G0)
+    e = np.exp(L - L.max(0, keepdims=True))
+    sm = e / e.sum(0, keepdims=True)
+    return (1.0 - eps) * sm + eps / G2
+
+
+def proposal_sample(grid, gshape, q_f32, D, seed, step):
+    """Inverse-CDF depth samples per fine column from FP32 probabilities
+    q_f32 [G2, G1, G0]. Returns (xyz [3, n_ray*D] float32, apr, cell idx int32)."""
+    nx, ny, _ = grid.n
+    G0, G1, G2 = gshape
+    n_ray = nx * ny
+    ray = np.arange(n_ray, dtype=np.int64)
+    ix, iy = ray % nx, ray // nx
+    ux = uniform01(seed, step, 0, ray)
+    uy = uniform01(seed, step, 1, ray)
+    xr = _coord(grid.lo[0], ix, ux, grid.pitch[0])
+    yr = _coord(grid.lo[1], iy, uy, grid.pitch[1])
+    gxi, gyi = ix * G0 // nx, iy * G1 // ny
+    q = np.asarray(q_f32, dtype=np.float32)
+    c = np.maximum(np.floor(q.astype(np.float64) * 2.0 ** 20), 1.0).astype(np.int64)   # [G2, G1, G0]
+    C = np.concatenate([np.zeros((1, G1, G0), np.int64), np.cumsum(c, 0)], 0)         # [G2+1, G1, G0]
+    Cr = C[:, gyi, gxi]                                                                  # [G2+1, n_ray]
+    cr = c[:, gyi, gxi]
+    W = Cr[-1]
+    j = np.arange(D, dtype=np.int64)
+    idx = (ray[:, None] * D + j[None, :]).astype(np.uint64)
+    k = (np.uint64(step) << np.uint64(42)) | (np.uint64(3) << np.uint64(40)) | idx
+    m = (splitmix64(seed, k) >> np.uint64(40)).astype(np.int64)
+    u = ((j[None, :] << 24) + m) * W[:, None] // (np.int64(D) << 24)                   # [n_ray, D]
+    cell = np.empty((n_ray, D), np.int64)
+    for r in range(n_ray):
+        cell[r] = np.searchsorted(Cr[:, r], u[r], side="right") - 1
+    Ck = np.take_along_axis(Cr.T, cell, 1)
+    ck = np.take_along_axis(cr.T, cell, 1)
+    frac = (u - Ck).astype(np.float64) + 0.5
+    frac = frac / ck.astype(np.float64)
+    pz_cell = np.float64(np.float32(grid.pitch[2] * grid.n[2] / G2))
+    zc = np.float64(np.float32(grid.lo[2])) + (cell.astype(np.float64) + frac) * pz_cell
+    xyz = np.empty((3, D * n_ray), np.float32)        # depth-major: point = j * n_ray + ray
+    xyz[0] = np.tile(xr, D)
+    xyz[1] = np.tile(yr, D)
+    xyz[2] = zc.T.reshape(-1).astype(np.float32)
+    apr = np.stack([xr, yr, np.full(n_ray, np.float32(grid.aperture_z))]).astype(np.float32)
+    gcell = (cell * G1 + gyi[:, None]) * G0 + gxi[:, None]
+    return xyz, apr, gcell.T.reshape(-1).astype(np.int32)
+
+
+def proposal_targets(omega, idx, n_cells):
+    """Histogram of the blended geometric weights omega = T alpha over grid cells."""
+    return np.bincount(np.asarray(idx, np.int64), weights=np.asarray(omega, np.float64), minlength=n_cells)
+
+
+def proposal_loss(logits, gshape, eps, hist):
+    """Sum over grid columns of KL(p || q), p = normalised weight histogram of
+    the column (columns without weight are skipped); returns (loss, dL/dlogits)."""
+    G0, G1, G2 = gshape
+    L = np.asarray(logits, np.float64).reshape(G2, G1, G0)
+    e = np.exp(L - L.max(0, keepdims=True))
+    sm = e / e.sum(0, keepdims=True)
+    q = (1.0 - eps) * sm + eps / G2
+    h = np.asarray(hist, np.float64).reshape(G2, G1, G0)
+    tot = h.sum(0, keepdims=True)
+    has = tot > 0
+    p = np.where(has, h / np.where(has, tot, 1.0), 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kl = np.where(p > 0, p * (np.log(p) - np.log(q)), 0.0).sum()
+    r = p / q
+    dz = (1.0 - eps) * sm * (-r + (r * sm).sum(0, keepdims=True))
+    dz = np.where(has, dz, 0.0)
+    return float(kl), dz.reshape(-1)
+
+
+def proposal_backward(features, params, width, n_hidden, beta, cache, d_logits):
+    """Adjoint of proposal_logits: (d_params FP64 packed, d_features [n_cells, F])."""
+    Fe = np.asarray(features, dtype=np.float16).astype(np.float64)
+    layers = _unpack(proposal_shapes(Fe.shape[1], width, n_hidden), params)
+    g = np.asarray(d_logits, np.float64)[None, :]
+    W, b = layers[-1]
+    grads = [None] * len(layers)
+    grads[-1] = (g @ cache["z"][-1].T, g.sum(1))
+    zbar = W.T @ g
+    for l in range(len(layers) - 2, -1, -1):
+        W, b = layers[l]
+        h = cache["h"][l]
+        hbar = zbar * _sigmoid(beta * h)
+        grads[l] = (hbar @ cache["z"][l].T, hbar.sum(1))
+        zbar = W.T @ hbar
+    d_params = np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
+    return d_params, zbar.T

@@ -1,0 +1,106 @@
+"""Pins for the oracle's learned proposal sampler: the network and its
+adjoint against torch autograd, the KL loss gradient against finite
+differences, and the integer inverse-CDF sampler against its distribution,
+ordering and the closed form of the uniform case."""
+import numpy as np
+import torch
+from scipy import stats
+
+import geraf_inputs as gi
+
+
+def _spec(F=8, width=16, n_hidden=2):
+    shapes = [(width, F)] + [(width, width)] * (n_hidden - 1) + [(1, width)]
+    rng = np.random.default_rng(0)
+    parts = []
+    for o, i in shapes:
+        parts += [rng.uniform(-1 / np.sqrt(i), 1 / np.sqrt(i), o * i), rng.uniform(-0.1, 0.1, o)]
+    return np.concatenate(parts).astype(np.float32), shapes
+
+
+def test_proposal_network_and_adjoint_match_torch(oracle):
+    params, shapes = _spec()
+    rng = np.random.default_rng(1)
+    feats = rng.standard_normal((50, 8)).astype(np.float16)
+    logits, cache = oracle.proposal_logits(feats, params, 16, 2, 10.0)
+    p = torch.tensor(params.astype(np.float64), requires_grad=True)
+    x = torch.tensor(feats.astype(np.float64), requires_grad=True)
+    z, off = x, 0
+    for li, (o, i) in enumerate(shapes):
+        W = p[off:off + o * i].view(o, i); off += o * i
+        b = p[off:off + o]; off += o
+        z = z @ W.T + b
+        if li < len(shapes) - 1:
+            z = torch.nn.functional.softplus(z, beta=10.0, threshold=1e6)
+    np.testing.assert_allclose(logits, z[:, 0].detach().numpy(), rtol=1e-12, atol=1e-13)
+    g = rng.standard_normal(50)
+    dp, dx = oracle.proposal_backward(feats, params, 16, 2, 10.0, cache, g)
+    tp, tx = torch.autograd.grad((z[:, 0] * torch.tensor(g)).sum(), (p, x))
+    np.testing.assert_allclose(dp, tp.numpy(), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(dx, tx.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_kl_loss_gradient_and_minimum(oracle):
+    gshape = (2, 3, 8)
+    rng = np.random.default_rng(2)
+    logits = rng.standard_normal(48)
+    hist = rng.uniform(0, 1, 48) * (rng.uniform(0, 1, 48) > 0.3)
+    hist.reshape(8, 3, 2)[:, 0, 1] = 0.0          # one column without weight
+    eps = 0.05
+    L, d = oracle.proposal_loss(logits, gshape, eps, hist)
+    assert L >= 0
+    h = 1e-6
+    for k in range(48):
+        e = np.zeros(48); e[k] = h
+        fd = (oracle.proposal_loss(logits + e, gshape, eps, hist)[0]
+              - oracle.proposal_loss(logits - e, gshape, eps, hist)[0]) / (2 * h)
+        np.testing.assert_allclose(d[k], fd, rtol=1e-6, atol=1e-9)
+    # at eps = 0 the minimum is reached when softmax(logits) equals the histogram
+    p = np.full(48, 1.0)
+    L0, d0 = oracle.proposal_loss(np.zeros(48), gshape, 0.0, p)
+    assert abs(L0) < 1e-14 and np.abs(d0).max() < 1e-14
+
+
+def test_inverse_cdf_sampling_distribution_and_order(oracle):
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.1, (64, 64, 64))
+    gshape = (4, 4, 16)
+    rng = np.random.default_rng(3)
+    logits = rng.standard_normal(16 * 4 * 4) * 2
+    q = oracle.proposal_q(logits, gshape, 0.01).astype(np.float32)
+    D = 16
+    xyz, apr, idx = oracle.proposal_sample(g, gshape, q, D, seed=5, step=1)
+    z = xyz[2].reshape(D, -1)
+    assert np.all(np.diff(z, axis=0) > 0)                         # sorted along every column
+    np.testing.assert_array_equal(xyz[0].reshape(D, -1), np.broadcast_to(apr[0], (D, g.n_ray)))
+    # cells of all samples of grid column (0, 0) vs q: 16 x 16 fine columns x 16 samples
+    cell_z = idx // 16
+    col = idx % 16
+    sel = col == 0
+    counts = np.bincount(cell_z[sel], minlength=16)
+    expected = q[:, 0, 0].astype(np.float64) / q[:, 0, 0].sum() * sel.sum()
+    # stratified draws: counts never differ from expectation by more than the strata allow
+    assert np.abs(counts - expected).max() <= 16 + 1e-9
+    assert stats.chisquare(counts + 0.0, expected).pvalue > 1e-6 or np.abs(counts - expected).max() < 3
+    # samples lie inside their cells
+    pz = np.float64(np.float32(g.pitch[2] * 64 / 16))
+    lo = np.float64(np.float32(g.lo[2])) + cell_z * pz
+    assert np.all(xyz[2] >= lo - 1e-7) and np.all(xyz[2] <= lo + pz + 1e-7)
+
+
+def test_uniform_proposal_is_stratified_closed_form(oracle):
+    """q uniform over 64 cells, 16 samples: sample j falls in cells 4j..4j+3 at
+    z = z0 + (u + 0.5) / 2^14 * pz_cell with u = ((j << 24) + m) >> 8."""
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.1, (8, 8, 64))
+    gshape = (2, 2, 64)
+    q = np.full((64, 2, 2), 1.0 / 64, np.float32)
+    xyz, _, idx = oracle.proposal_sample(g, gshape, q, 16, seed=9, step=0)
+    cz = (idx // 4).reshape(16, -1)
+    j = np.arange(16)[:, None]
+    assert np.all((cz >= 4 * j) & (cz < 4 * j + 4))
+    ray = np.arange(64)
+    k = (np.uint64(0) << np.uint64(42)) | (np.uint64(3) << np.uint64(40)) | (ray[None, :] * 16 + j).astype(np.uint64)
+    m = (oracle.splitmix64(9, k) >> np.uint64(40)).astype(np.int64)
+    u = ((j << 24) + m) >> 8
+    pz = np.float64(np.float32(g.pitch[2] * 64 / 64))
+    want = (np.float64(np.float32(g.lo[2])) + (u + 0.5) / 2.0 ** 14 * pz).astype(np.float32)
+    np.testing.assert_array_equal(xyz[2].reshape(16, -1), want)
