@@ -264,6 +264,74 @@ geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const ge
                                    const float* d_P, void* ws, size_t* ws_bytes,
                                    float* g_s, void* stream);
 
+/*
+ * Learned proposal sampler (the paper is silent on it; it cuts the number of
+ * lensless samples per step). A G0 x G1 x G2 grid of FP16 features over the
+ * sample cube (cell index (gz*G1 + gy)*G0 + gx, features [n_cells][feat])
+ * feeds a softplus(beta) MLP (n_hidden layers of `width`, one output logit;
+ * packed FP32 params [W1 b1 ... W_out b_out], W row-major [out][in]). Per grid
+ * column, q = (1 - eps) softmax(logits over gz) + eps / G2. A fine primary
+ * column (ix, iy) of the sample grid uses grid column (ix*G0/nx, iy*G1/ny)
+ * and draws `depth` depth samples by inverse CDF (see geraf_sample_proposal).
+ */
+typedef struct {
+    const void* features;   /* FP16 [n_cells][feat], device */
+    const float* params;    /* FP32 packed MLP parameters, device */
+    int32_t g[3];           /* G0, G1, G2 (2 <= G2 <= 256) */
+    int32_t feat;           /* 1 .. 16 */
+    int32_t width;          /* 1 .. 64 */
+    int32_t n_hidden;       /* 1 .. 4 */
+    float beta;             /* softplus sharpness */
+    float eps;              /* uniform floor of q, 0 <= eps < 1 */
+    int32_t depth;          /* samples per primary column, 1 .. 256 */
+} geraf_proposal;
+
+/*
+ * geraf_proposal_density — logits [n_cells] of every grid cell and (q != NULL)
+ * the per-column depth distribution q [n_cells] (same cell order). `saved`
+ * (geraf_proposal_saved_bytes, may be NULL) keeps the pre-activations for
+ * geraf_sample_backward.
+ */
+geraf_status geraf_proposal_saved_bytes(const geraf_proposal* p, size_t* bytes);
+geraf_status geraf_proposal_density(const geraf_proposal* p, float* logits, float* q, void* saved,
+                                    size_t saved_bytes, void* stream);
+
+/*
+ * geraf_sample_proposal — lensless samples of `grid`'s n[0] x n[1] primary
+ * columns, `depth` per column, drawn from q (section 6 "Primary Ray" with the
+ * depths importance-sampled). Integer CDF per column: c_k = max(1,
+ * floor(q_k 2^20)), C_{k+1} = C_k + c_k, W = C_G2; sample j: m_j = SplitMix64
+ * output number (step<<42 | 3<<40 | ray*depth + j) of seed, shifted right by
+ * 40 (24 bits); u_j = ((j<<24) + m_j) W / (depth<<24) (integer division);
+ * cell k with C_k <= u_j < C_{k+1}; z = lo_z + (k + (u_j - C_k + 0.5)/c_k) *
+ * pz_cell in FP64 with pz_cell = float(pitch_z n_z / G2), rounded to FP32.
+ * The column's (x, y) are jittered as in STRATIFIED sampling. Outputs:
+ * xyz [3][n_ray*depth] depth-major (samples sorted along every column),
+ * xyz_apr [3][n_ray] (may be NULL), idx [n_ray*depth] = grid cell of each
+ * sample. Bit-exact with any IEEE implementation given the same FP32 q.
+ * Requires n[0] % G0 == 0 and n[1] % G1 == 0.
+ */
+geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal* p, const float* q,
+                                   uint64_t seed, uint64_t step, float* xyz, float* xyz_apr, int32_t* idx,
+                                   void* stream);
+
+/*
+ * geraf_sample_backward — online training signal of the proposal from the
+ * blended weights of a render: target p per grid column = normalised
+ * histogram of T*alpha (geraf_blend outputs, [n_z][n_ray] of `grid`) over the
+ * column's cells; loss = sum over columns with weight of KL(p || q).
+ * idx = the sample cells of geraf_sample_proposal, or NULL for samples of the
+ * regular grid (n_z = grid.n[2], which must be a multiple of G2). Writes
+ * d_params (packed like params), d_features (FP32 [n_cells][feat]) and loss
+ * (one double, may be NULL). Needs `logits` and `saved` of
+ * geraf_proposal_density and a workspace.
+ */
+geraf_status geraf_sample_backward(const geraf_proposal* p, const geraf_grid* grid, int32_t n_z,
+                                   const float* alpha, const float* T, const int32_t* idx,
+                                   const float* logits, const void* saved, float* d_params,
+                                   float* d_features, double* loss, void* ws, size_t* ws_bytes,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

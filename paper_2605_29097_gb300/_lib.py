@@ -32,6 +32,12 @@ class GerafFieldDesc(ctypes.Structure):
                 ("precision", ctypes.c_int32)]
 
 
+class GerafProposal(ctypes.Structure):
+    _fields_ = [("features", vp), ("params", vp), ("g", ctypes.c_int32 * 3), ("feat", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("beta", ctypes.c_float),
+                ("eps", ctypes.c_float), ("depth", ctypes.c_int32)]
+
+
 # name -> argtypes (all return geraf_status as int)
 SIGNATURES = {
     "geraf_poll_device_error": [vp],
@@ -47,6 +53,11 @@ SIGNATURES = {
                               vp, vp, vp, vp],
     "geraf_filter": [vp, vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp, vp, vp, vp],
     "geraf_filter_backward": [vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp],
+    "geraf_proposal_saved_bytes": [ctypes.POINTER(GerafProposal), szp],
+    "geraf_proposal_density": [ctypes.POINTER(GerafProposal), vp, vp, vp, sz, vp],
+    "geraf_sample_proposal": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, u64, u64, vp, vp, vp, vp],
+    "geraf_sample_backward": [ctypes.POINTER(GerafProposal), ctypes.POINTER(GerafGrid), i32, vp, vp, vp, vp, vp, vp,
+                              vp, vp, vp, szp, vp],
 }
 
 STATUS = {0: "GERAF_OK", 1: "GERAF_ERR_INVALID_ARG", 2: "GERAF_ERR_ALIGNMENT", 3: "GERAF_ERR_CUDA",

@@ -30,6 +30,13 @@ geraf_status filter_impl(const float*, const float*, int32_t, const geraf_band*,
 geraf_status filter_backward_impl(const float*, int32_t, const geraf_band*, const float*, int64_t, const float*,
                                   const float*, void*, size_t*, float*, cudaStream_t);
 geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
+geraf_status proposal_saved_bytes(const geraf_proposal*, size_t*);
+geraf_status proposal_density_impl(const geraf_proposal*, float*, float*, void*, size_t, cudaStream_t);
+geraf_status sample_proposal_impl(const geraf_grid*, const geraf_proposal*, const float*, uint64_t, uint64_t, float*,
+                                  float*, int32_t*, cudaStream_t);
+geraf_status sample_backward_impl(const geraf_proposal*, const geraf_grid*, int32_t, const float*, const float*,
+                                  const int32_t*, const float*, const void*, float*, float*, double*, void*, size_t*,
+                                  cudaStream_t);
 geraf_status mlp_forward_impl(const geraf_field_desc*, const float*, int64_t, float*, float*, float*, void*, size_t,
                               cudaStream_t);
 geraf_status mlp_backward_impl(const geraf_field_desc*, const float*, int64_t, const void*, const float*,
@@ -285,6 +292,54 @@ geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const ge
     REQUIRE(band, "filter_backward: band must not be NULL");
     if (ws) REQUIRE(ant_xyz && vox_xyz && M && d_P && g_s, "filter_backward: null input or output");
     return filter_backward_impl(ant_xyz, n_ant, band, vox_xyz, n_vox, M, d_P, ws, ws_bytes, g_s, S(stream));
+}
+
+geraf_status geraf_proposal_saved_bytes(const geraf_proposal* p, size_t* bytes) {
+    REQUIRE(p && bytes, "proposal_saved_bytes: null argument");
+    return proposal_saved_bytes(p, bytes);
+}
+
+geraf_status geraf_proposal_density(const geraf_proposal* p, float* logits, float* q, void* saved, size_t saved_bytes,
+                                    void* stream) {
+    REQUIRE(p && logits, "proposal_density: p and logits must not be NULL");
+    return proposal_density_impl(p, logits, q, saved, saved_bytes, S(stream));
+}
+
+static geraf_status check_prop_grid(const geraf_grid* grid, const geraf_proposal* p) {
+    REQUIRE(grid && p, "proposal: grid and p must not be NULL");
+    for (int d = 0; d < 3; ++d) {
+        REQUIRE(grid->n[d] > 0 && grid->pitch[d] > 0.0f, "proposal: bad grid");
+        REQUIRE(p->g[d] > 0, "proposal: bad proposal grid");
+    }
+    REQUIRE(grid->n[0] % p->g[0] == 0 && grid->n[1] % p->g[1] == 0,
+            "proposal: sample columns (%d x %d) must be multiples of the proposal grid (%d x %d)", grid->n[0],
+            grid->n[1], p->g[0], p->g[1]);
+    return GERAF_OK;
+}
+
+geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal* p, const float* q, uint64_t seed,
+                                   uint64_t step, float* xyz, float* xyz_apr, int32_t* idx, void* stream) {
+    geraf_status st = check_prop_grid(grid, p);
+    if (st != GERAF_OK) return st;
+    REQUIRE(q && xyz && idx, "sample_proposal: q, xyz and idx must not be NULL");
+    REQUIRE((int64_t)grid->n[0] * grid->n[1] * p->depth < (1ll << 40), "sample_proposal: too many samples");
+    REQUIRE(step < (1ull << 22), "sample_proposal: step must be below 2^22");
+    return sample_proposal_impl(grid, p, q, seed, step, xyz, xyz_apr, idx, S(stream));
+}
+
+geraf_status geraf_sample_backward(const geraf_proposal* p, const geraf_grid* grid, int32_t n_z, const float* alpha,
+                                   const float* T, const int32_t* idx, const float* logits, const void* saved,
+                                   float* d_params, float* d_features, double* loss, void* ws, size_t* ws_bytes,
+                                   void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    st = check_prop_grid(grid, p);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_z >= 1, "sample_backward: n_z must be >= 1");
+    if (!idx) REQUIRE(n_z % p->g[2] == 0, "sample_backward: regular-grid depths %d not a multiple of G2 %d", n_z, p->g[2]);
+    if (ws) REQUIRE(alpha && T && logits && saved && d_params && d_features, "sample_backward: null input or output");
+    return sample_backward_impl(p, grid, n_z, alpha, T, idx, logits, saved, d_params, d_features, loss, ws, ws_bytes,
+                                S(stream));
 }
 
 }  // extern "C"

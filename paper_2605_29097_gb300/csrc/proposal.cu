@@ -1,0 +1,459 @@
+// Learned proposal sampler: a coarse G0 x G1 x G2 grid of FP16 features with a
+// small softplus MLP gives a logit per cell; per grid column the depth
+// distribution is q = (1 - eps) softmax(logits) + eps / G2. Lensless samples
+// of a fine primary column are drawn by inverse CDF from an integer CDF of q
+// (bit-exact), so the network concentrates the column's depth samples where
+// the blended weights are. The network is trained online on those weights:
+// loss = sum over grid columns of KL(p || q), p = the normalised histogram of
+// the geometric weights T alpha of the rendered samples in the column's cells.
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace geraf {
+
+namespace {
+
+constexpr int PW = 64;        // maximum hidden width (kernels use fixed 64-wide registers)
+constexpr int PF = 16;        // maximum feature dimension
+constexpr int PNH = 4;        // maximum hidden layers
+constexpr int PBT = 128;      // cells per backward tile / threads per CTA
+
+struct PropGeom {
+    int G0, G1, G2, F, W, NH, D;
+    float beta, eps;
+    int64_t n_cells, n_params;
+    int off_w[PNH + 1], off_b[PNH + 1], k_in[PNH + 1], n_out[PNH + 1];
+};
+
+bool make_prop(const geraf_proposal* p, PropGeom* g) {
+    if (!p || !p->features || !p->params) {
+        set_error("proposal: features and params must not be NULL");
+        return false;
+    }
+    if (p->g[0] < 1 || p->g[1] < 1 || p->g[2] < 2 || p->g[2] > 256 || p->feat < 1 || p->feat > PF ||
+        p->width < 1 || p->width > PW || p->n_hidden < 1 || p->n_hidden > PNH || p->depth < 1 || p->depth > 256 ||
+        !(p->eps >= 0.0f && p->eps < 1.0f)) {
+        set_error("proposal: need G2 in [2, 256], 1 <= feat <= 16, 1 <= width <= 64, 1 <= n_hidden <= 4, "
+                  "1 <= depth <= 256, 0 <= eps < 1");
+        return false;
+    }
+    g->G0 = p->g[0]; g->G1 = p->g[1]; g->G2 = p->g[2];
+    g->F = p->feat; g->W = p->width; g->NH = p->n_hidden; g->D = p->depth;
+    g->beta = p->beta; g->eps = p->eps;
+    g->n_cells = (int64_t)g->G0 * g->G1 * g->G2;
+    int off = 0;
+    for (int l = 0; l <= g->NH; ++l) {
+        g->k_in[l] = l == 0 ? g->F : g->W;
+        g->n_out[l] = l == g->NH ? 1 : g->W;
+        g->off_w[l] = off; off += g->n_out[l] * g->k_in[l];
+        g->off_b[l] = off; off += g->n_out[l];
+    }
+    g->n_params = off;
+    return true;
+}
+
+__device__ __forceinline__ float sp_b(float h, float beta) {
+    return fmaxf(h, 0.0f) + log1pf(expf(-beta * fabsf(h))) / beta;
+}
+__device__ __forceinline__ float sig(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// ---------------------------------------------------------- network forward
+__global__ void __launch_bounds__(128) prop_forward_kernel(PropGeom g, const __half* __restrict__ feat,
+                                                           const float* __restrict__ params,
+                                                           float* __restrict__ logits, float* __restrict__ saved) {
+    extern __shared__ float sw[];
+    for (int i = threadIdx.x; i < g.n_params; i += blockDim.x) sw[i] = params[i];
+    __syncthreads();
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= g.n_cells) return;
+    float z[PW], h[PW];
+#pragma unroll
+    for (int k = 0; k < PW; ++k) z[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PF; ++k)
+        if (k < g.F) z[k] = __half2float(feat[c * g.F + k]);
+    for (int l = 0; l < g.NH; ++l) {
+        const float* Wl = sw + g.off_w[l];
+        const float* bl = sw + g.off_b[l];
+        const int K = g.k_in[l];
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            float a = 0.0f;
+            if (u < g.W) {
+                a = bl[u];
+#pragma unroll
+                for (int k = 0; k < PW; ++k)
+                    if (k < K) a = fmaf(Wl[u * K + k], z[k], a);
+            }
+            h[u] = a;
+        }
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            if (u < g.W) {
+                if (saved) saved[((int64_t)l * g.W + u) * g.n_cells + c] = h[u];
+                z[u] = sp_b(h[u], g.beta);
+            } else {
+                z[u] = 0.0f;
+            }
+        }
+    }
+    const float* Wo = sw + g.off_w[g.NH];
+    float a = sw[g.off_b[g.NH]];
+#pragma unroll
+    for (int k = 0; k < PW; ++k)
+        if (k < g.W) a = fmaf(Wo[k], z[k], a);
+    logits[c] = a;
+}
+
+// per grid column: q = (1 - eps) softmax + eps / G2 (FP64 internally)
+__global__ void prop_q_kernel(PropGeom g, const float* __restrict__ logits, float* __restrict__ q) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int plane = g.G0 * g.G1;
+    if (col >= plane) return;
+    double mx = -1e300;
+    for (int k = 0; k < g.G2; ++k) mx = fmax(mx, (double)logits[(int64_t)k * plane + col]);
+    double s = 0.0;
+    for (int k = 0; k < g.G2; ++k) s += exp((double)logits[(int64_t)k * plane + col] - mx);
+    for (int k = 0; k < g.G2; ++k) {
+        const double e = exp((double)logits[(int64_t)k * plane + col] - mx) / s;
+        q[(int64_t)k * plane + col] = (float)((1.0 - (double)g.eps) * e + (double)g.eps / g.G2);
+    }
+}
+
+// ------------------------------------------------------------------ sampling
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float grid_coord(float lo, int64_t i, double u, float pitch) {
+    double t = __dadd_rn((double)i, u);
+    t = __dmul_rn(t, (double)pitch);
+    return __double2float_rn(__dadd_rn((double)lo, t));
+}
+
+__global__ void prop_sample_kernel(geraf_grid gr, PropGeom g, const float* __restrict__ q, uint64_t seed,
+                                   uint64_t step, float pz_cell, float* __restrict__ xyz, float* __restrict__ apr,
+                                   int32_t* __restrict__ idx) {
+    const int64_t n_ray = (int64_t)gr.n[0] * gr.n[1];
+    const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ray >= n_ray) return;
+    const int64_t n = n_ray * g.D;
+    const int64_t ix = ray % gr.n[0], iy = ray / gr.n[0];
+    const int gx = (int)(ix * g.G0 / gr.n[0]), gy = (int)(iy * g.G1 / gr.n[1]);
+    const int plane = g.G0 * g.G1;
+    const int col = gy * g.G0 + gx;
+    const uint64_t s0 = step << 42;
+    const double ux = (double)(splitmix64(seed, s0 | (0ull << 40) | (uint64_t)ray) >> 11) * 0x1.0p-53;
+    const double uy = (double)(splitmix64(seed, s0 | (1ull << 40) | (uint64_t)ray) >> 11) * 0x1.0p-53;
+    const float x = grid_coord(gr.lo[0], ix, ux, gr.pitch[0]);
+    const float y = grid_coord(gr.lo[1], iy, uy, gr.pitch[1]);
+    if (apr) {
+        apr[ray] = x;
+        apr[n_ray + ray] = y;
+        apr[2 * n_ray + ray] = gr.aperture_z;
+    }
+    // integer CDF weights c_k = max(1, floor(q_k 2^20)), total W
+    uint64_t Wt = 0;
+    for (int k = 0; k < g.G2; ++k) {
+        const double ck = floor((double)q[(int64_t)k * plane + col] * 1048576.0);
+        Wt += ck < 1.0 ? 1ull : (uint64_t)ck;
+    }
+    const uint64_t den = (uint64_t)g.D << 24;
+    auto u_of = [&](int j) -> uint64_t {
+        const uint64_t m = splitmix64(seed, s0 | (3ull << 40) | (uint64_t)(ray * g.D + j)) >> 40;
+        return ((((uint64_t)j) << 24) + m) * Wt / den;
+    };
+    int j = 0;
+    uint64_t uj = u_of(0);
+    uint64_t C = 0;
+    for (int k = 0; k < g.G2 && j < g.D; ++k) {
+        const double ckd = floor((double)q[(int64_t)k * plane + col] * 1048576.0);
+        const uint64_t ck = ckd < 1.0 ? 1ull : (uint64_t)ckd;
+        while (j < g.D && uj < C + ck) {
+            const double frac = __ddiv_rn(__dadd_rn((double)(uj - C), 0.5), (double)ck);
+            const double zc = __dadd_rn((double)gr.lo[2], __dmul_rn(__dadd_rn((double)k, frac), (double)pz_cell));
+            const int64_t p = (int64_t)j * n_ray + ray;
+            xyz[p] = x;
+            xyz[n + p] = y;
+            xyz[2 * n + p] = __double2float_rn(zc);
+            idx[p] = k * plane + col;
+            ++j;
+            if (j < g.D) uj = u_of(j);
+        }
+        C += ck;
+    }
+}
+
+// --------------------------------------------------------- targets and loss
+// histogram of T alpha over grid cells, gathered per cell in a fixed order
+__global__ void prop_hist_kernel(geraf_grid gr, PropGeom g, int n_z, const float* __restrict__ alpha,
+                                 const float* __restrict__ T, const int32_t* __restrict__ idx,
+                                 double* __restrict__ hist) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= g.n_cells) return;
+    const int plane = g.G0 * g.G1;
+    const int gz = (int)(cell / plane), rem = (int)(cell - (int64_t)gz * plane);
+    const int gy = rem / g.G0, gx = rem - gy * g.G0;
+    const int fx = gr.n[0] / g.G0, fy = gr.n[1] / g.G1;
+    const int64_t n_ray = (int64_t)gr.n[0] * gr.n[1];
+    double s = 0.0;
+    for (int iy = gy * fy; iy < (gy + 1) * fy; ++iy)
+        for (int ix = gx * fx; ix < (gx + 1) * fx; ++ix) {
+            const int64_t ray = (int64_t)iy * gr.n[0] + ix;
+            if (idx) {
+                for (int j = 0; j < n_z; ++j) {
+                    const int64_t p = (int64_t)j * n_ray + ray;
+                    if (idx[p] == cell) s += (double)T[p] * (double)alpha[p];
+                }
+            } else {
+                const int fz = n_z / g.G2;
+                for (int j = gz * fz; j < (gz + 1) * fz; ++j) {
+                    const int64_t p = (int64_t)j * n_ray + ray;
+                    s += (double)T[p] * (double)alpha[p];
+                }
+            }
+        }
+    hist[cell] = s;
+}
+
+// per grid column: KL(p || q) and dL/dlogits (FP64 internally)
+__global__ void prop_loss_kernel(PropGeom g, const float* __restrict__ logits, const double* __restrict__ hist,
+                                 float* __restrict__ d_logits, double* __restrict__ col_loss) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int plane = g.G0 * g.G1;
+    if (col >= plane) return;
+    double tot = 0.0, mx = -1e300;
+    for (int k = 0; k < g.G2; ++k) {
+        tot += hist[(int64_t)k * plane + col];
+        mx = fmax(mx, (double)logits[(int64_t)k * plane + col]);
+    }
+    if (!(tot > 0.0)) {
+        for (int k = 0; k < g.G2; ++k) d_logits[(int64_t)k * plane + col] = 0.0f;
+        col_loss[col] = 0.0;
+        return;
+    }
+    double se = 0.0;
+    for (int k = 0; k < g.G2; ++k) se += exp((double)logits[(int64_t)k * plane + col] - mx);
+    const double eps = g.eps, a = 1.0 - eps;
+    double kl = 0.0, rs = 0.0;
+    for (int k = 0; k < g.G2; ++k) {
+        const double sm = exp((double)logits[(int64_t)k * plane + col] - mx) / se;
+        const double qk = a * sm + eps / g.G2;
+        const double pk = hist[(int64_t)k * plane + col] / tot;
+        if (pk > 0.0) kl += pk * (log(pk) - log(qk));
+        rs += pk / qk * sm;
+    }
+    for (int k = 0; k < g.G2; ++k) {
+        const double sm = exp((double)logits[(int64_t)k * plane + col] - mx) / se;
+        const double qk = a * sm + eps / g.G2;
+        const double pk = hist[(int64_t)k * plane + col] / tot;
+        d_logits[(int64_t)k * plane + col] = (float)(a * sm * (-(pk / qk) + rs));
+    }
+    col_loss[col] = kl;
+}
+
+__global__ void sum_doubles_1(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// --------------------------------------------------------- network adjoint
+// Persistent CTAs over tiles of PBT cells. Thread = cell for the per-cell
+// parts (pre-activation adjoint, input adjoint); thread = parameter entry for
+// the weight-gradient sums over the tile's cells, accumulated in a per-CTA
+// shared buffer (fixed order, no atomics).
+__global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const __half* __restrict__ feat,
+                                                               const float* __restrict__ params,
+                                                               const float* __restrict__ saved,
+                                                               const float* __restrict__ d_logits,
+                                                               float* __restrict__ d_feat,
+                                                               float* __restrict__ partial) {
+    extern __shared__ float sm[];
+    float* sw = sm;                               // parameters
+    float* gacc = sw + g.n_params;                // parameter gradient of this CTA
+    float* hb = gacc + g.n_params;                // [PBT][PW] pre-activation adjoint
+    float* zi = hb + PBT * PW;                    // [PBT][PW] layer input
+    float* dl = zi + PBT * PW;                    // [PBT] d logits
+    const int t = threadIdx.x;
+    for (int i = t; i < g.n_params; i += PBT) {
+        sw[i] = params[i];
+        gacc[i] = 0.0f;
+    }
+    __syncthreads();
+    const int W = g.W;
+    for (int64_t tile = blockIdx.x; tile * PBT < g.n_cells; tile += gridDim.x) {
+        const int64_t c = tile * PBT + t;
+        const bool valid = c < g.n_cells;
+        const int64_t cc = valid ? c : g.n_cells - 1;
+        // output layer: zin = softplus(h_{NH-1}), hbar = d_logit
+        const float dlog = valid ? d_logits[cc] : 0.0f;
+        dl[t] = dlog;
+        float zb[PW];
+        const float* Wo = sw + g.off_w[g.NH];
+#pragma unroll
+        for (int u = 0; u < PW; ++u) {
+            float zz = 0.0f, b = 0.0f;
+            if (u < W) {
+                zz = sp_b(saved[((int64_t)(g.NH - 1) * W + u) * g.n_cells + cc], g.beta);
+                b = Wo[u] * dlog;
+            }
+            zi[t * PW + u] = zz;
+            zb[u] = b;
+        }
+        __syncthreads();
+        for (int k = t; k < W; k += PBT) {
+            float a = 0.0f;
+            for (int q = 0; q < PBT; ++q) a = fmaf(dl[q], zi[q * PW + k], a);
+            gacc[g.off_w[g.NH] + k] += a;
+        }
+        if (t == 0) {
+            float a = 0.0f;
+            for (int q = 0; q < PBT; ++q) a += dl[q];
+            gacc[g.off_b[g.NH]] += a;
+        }
+        __syncthreads();
+        for (int l = g.NH - 1; l >= 0; --l) {
+            const int K = g.k_in[l];
+            // pre-activation adjoint and this layer's input, thread = cell
+#pragma unroll
+            for (int u = 0; u < PW; ++u) {
+                float v = 0.0f;
+                if (u < W && valid) {
+                    const float h = saved[((int64_t)l * W + u) * g.n_cells + cc];
+                    v = zb[u] * sig(g.beta * h);
+                }
+                hb[t * PW + u] = v;
+            }
+#pragma unroll
+            for (int k = 0; k < PW; ++k) {
+                float v = 0.0f;
+                if (k < K) {
+                    if (l > 0) v = sp_b(saved[((int64_t)(l - 1) * W + k) * g.n_cells + cc], g.beta);
+                    else v = __half2float(feat[cc * g.F + k]);
+                }
+                zi[t * PW + k] = v;
+            }
+            __syncthreads();
+            // weight / bias gradient sums over the tile's cells, thread = entry
+            for (int e = t; e < W * K; e += PBT) {
+                const int u = e / K, k = e - u * K;
+                float a = 0.0f;
+                for (int q = 0; q < PBT; ++q) a = fmaf(hb[q * PW + u], zi[q * PW + k], a);
+                gacc[g.off_w[l] + e] += a;
+            }
+            for (int u = t; u < W; u += PBT) {
+                float a = 0.0f;
+                for (int q = 0; q < PBT; ++q) a += hb[q * PW + u];
+                gacc[g.off_b[l] + u] += a;
+            }
+            // adjoint of the layer input, thread = cell
+            const float* Wl = sw + g.off_w[l];
+            float nz[PW];
+#pragma unroll
+            for (int k = 0; k < PW; ++k) {
+                float a = 0.0f;
+                if (k < K) {
+                    for (int u = 0; u < W; ++u) a = fmaf(Wl[u * K + k], hb[t * PW + u], a);
+                }
+                nz[k] = a;
+            }
+            if (l == 0 && valid) {
+                for (int k = 0; k < g.F; ++k) d_feat[c * g.F + k] = nz[k];
+            }
+#pragma unroll
+            for (int k = 0; k < PW; ++k) zb[k] = nz[k];
+            __syncthreads();
+        }
+    }
+    float* out = partial + (int64_t)blockIdx.x * g.n_params;
+    for (int i = t; i < g.n_params; i += PBT) out[i] = gacc[i];
+}
+
+__global__ void reduce_params(const float* __restrict__ partial, int n_cta, int64_t n, float* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < n_cta; ++c) s += partial[(int64_t)c * n + i];
+    out[i] = (float)s;
+}
+
+inline unsigned g1(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+geraf_status proposal_saved_bytes(const geraf_proposal* p, size_t* bytes) {
+    PropGeom g;
+    if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
+    *bytes = (size_t)g.NH * g.W * g.n_cells * sizeof(float);
+    return GERAF_OK;
+}
+
+geraf_status proposal_density_impl(const geraf_proposal* p, float* logits, float* q, void* saved, size_t saved_bytes,
+                                   cudaStream_t st) {
+    PropGeom g;
+    if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
+    if (saved && saved_bytes < (size_t)g.NH * g.W * g.n_cells * sizeof(float))
+        return fail(GERAF_ERR_WORKSPACE, "proposal_density: saved buffer too small");
+    prop_forward_kernel<<<g1(g.n_cells, 128), 128, g.n_params * sizeof(float), st>>>(
+        g, static_cast<const __half*>(p->features), p->params, logits, static_cast<float*>(saved));
+    if (q) prop_q_kernel<<<g1((int64_t)g.G0 * g.G1, 128), 128, 0, st>>>(g, logits, q);
+    return cuda_status(cudaGetLastError(), "proposal_density");
+}
+
+geraf_status sample_proposal_impl(const geraf_grid* gr, const geraf_proposal* p, const float* q, uint64_t seed,
+                                  uint64_t step, float* xyz, float* apr, int32_t* idx, cudaStream_t st) {
+    PropGeom g;
+    if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
+    const float pz_cell = (float)((double)gr->pitch[2] * (double)gr->n[2] / (double)g.G2);
+    const int64_t n_ray = (int64_t)gr->n[0] * gr->n[1];
+    prop_sample_kernel<<<g1(n_ray, 128), 128, 0, st>>>(*gr, g, q, seed, step, pz_cell, xyz, apr, idx);
+    return cuda_status(cudaGetLastError(), "sample_proposal");
+}
+
+geraf_status sample_backward_impl(const geraf_proposal* p, const geraf_grid* gr, int32_t n_z, const float* alpha,
+                                  const float* T, const int32_t* idx, const float* logits, const void* saved,
+                                  float* d_params, float* d_features, double* loss, void* ws, size_t* ws_bytes,
+                                  cudaStream_t st) {
+    PropGeom g;
+    if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
+    const int plane = g.G0 * g.G1;
+    int n_cta = device_sm_count();
+    const int64_t n_tiles = (g.n_cells + PBT - 1) / PBT;
+    if (n_cta > n_tiles) n_cta = (int)n_tiles;
+    WsCarver c(ws);
+    double* hist = c.take<double>(g.n_cells);
+    float* dlog = c.take<float>(g.n_cells);
+    double* col_loss = c.take<double>(plane);
+    float* partial = c.take<float>((size_t)n_cta * g.n_params);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used)
+        return fail(GERAF_ERR_WORKSPACE, "sample_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    prop_hist_kernel<<<g1(g.n_cells, 128), 128, 0, st>>>(*gr, g, n_z, alpha, T, idx, hist);
+    prop_loss_kernel<<<g1(plane, 128), 128, 0, st>>>(g, logits, hist, dlog, col_loss);
+    if (loss) sum_doubles_1<<<1, 256, 0, st>>>(col_loss, plane, loss);
+    const size_t smem = (size_t)(2 * g.n_params + 2 * PBT * PW + PBT) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(prop_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr = true;
+    }
+    prop_backward_kernel<<<n_cta, PBT, smem, st>>>(g, static_cast<const __half*>(p->features), p->params,
+                                                   static_cast<const float*>(saved), dlog, d_features, partial);
+    reduce_params<<<g1(g.n_params, 256), 256, 0, st>>>(partial, n_cta, g.n_params, d_params);
+    return cuda_status(cudaGetLastError(), "sample_backward");
+}
+
+}  // namespace geraf

@@ -12,7 +12,7 @@ from typing import Optional, Sequence
 import torch
 
 from . import _lib
-from ._lib import GerafBand, GerafFieldDesc, GerafGrid, check
+from ._lib import GerafBand, GerafFieldDesc, GerafGrid, GerafProposal, check
 
 SAMPLE_UNIFORM, SAMPLE_STRATIFIED = 0, 1
 FIELD_ANALYTIC, FIELD_MLP = 0, 1
@@ -283,3 +283,81 @@ def geraf_filter_backward(ant, band: Band, vox, M, d_P):
     ws, wsz = _workspace(args, vox.device)
     check(args(_p(ws), ctypes.byref(wsz)))
     return torch.view_as_complex(out)
+
+
+class Proposal:
+    """Learned proposal: FP16 feature grid [G2, G1, G0, feat] and FP32 MLP params."""
+
+    def __init__(self, features: torch.Tensor, params: torch.Tensor, width=64, n_hidden=3, beta=10.0, eps=0.01,
+                 depth=16):
+        if features.dtype != torch.float16 or features.dim() != 4:
+            raise ValueError("features must be float16 [G2, G1, G0, feat]")
+        self.features = _req(features, "features", torch.float16)
+        self.params = _req(params, "params")
+        self.width, self.n_hidden, self.beta, self.eps, self.depth = width, n_hidden, beta, eps, depth
+
+    @property
+    def gshape(self):
+        G2, G1, G0, _ = self.features.shape
+        return (G0, G1, G2)
+
+    @property
+    def n_cells(self):
+        return self.features.shape[0] * self.features.shape[1] * self.features.shape[2]
+
+    def c(self) -> GerafProposal:
+        p = GerafProposal()
+        p.features = self.features.data_ptr()
+        p.params = self.params.data_ptr()
+        G0, G1, G2 = self.gshape
+        p.g[0], p.g[1], p.g[2] = G0, G1, G2
+        p.feat = self.features.shape[3]
+        p.width, p.n_hidden, p.beta, p.eps, p.depth = self.width, self.n_hidden, float(self.beta), float(self.eps), \
+            self.depth
+        return p
+
+
+def geraf_proposal_density(prop: Proposal, keep_saved=True):
+    """-> (logits [n_cells], q [n_cells], saved | None), cells ordered (gz, gy, gx)."""
+    dev = prop.features.device
+    cp = prop.c()
+    logits = torch.empty(prop.n_cells, dtype=torch.float32, device=dev)
+    q = torch.empty(prop.n_cells, dtype=torch.float32, device=dev)
+    saved, nbytes = None, 0
+    if keep_saved:
+        sz = ctypes.c_size_t(0)
+        check(_lib.lib().geraf_proposal_saved_bytes(ctypes.byref(cp), ctypes.byref(sz)))
+        nbytes = sz.value
+        saved = _alloc_ws(nbytes, dev)
+    check(_lib.lib().geraf_proposal_density(ctypes.byref(cp), _p(logits), _p(q), _p(saved), nbytes, _stream()))
+    return logits, q, saved
+
+
+def geraf_sample_proposal(grid: GerafGrid, prop: Proposal, q, seed=0, step=0):
+    """-> (xyz [3, n_ray*depth], xyz_apr [3, n_ray], idx int32 [n_ray*depth])."""
+    dev = prop.features.device
+    n_ray = grid.n[0] * grid.n[1]
+    n = n_ray * prop.depth
+    xyz = torch.empty(3, n, dtype=torch.float32, device=dev)
+    apr = torch.empty(3, n_ray, dtype=torch.float32, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    cp = prop.c()
+    check(_lib.lib().geraf_sample_proposal(ctypes.byref(grid), ctypes.byref(cp), _p(_req(q, "q")), int(seed),
+                                           int(step), _p(xyz), _p(apr), _p(idx), _stream()))
+    return xyz, apr, idx
+
+
+def geraf_sample_backward(prop: Proposal, grid: GerafGrid, n_z: int, alpha, T, idx, logits, saved):
+    """-> (d_params, d_features FP32 [G2, G1, G0, feat], loss 0-d float64)."""
+    dev = prop.features.device
+    cp = prop.c()
+    d_params = torch.empty_like(prop.params)
+    d_feat = torch.empty(prop.features.shape, dtype=torch.float32, device=dev)
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    L = _lib.lib()
+    args = lambda w, b: L.geraf_sample_backward(ctypes.byref(cp), ctypes.byref(grid), int(n_z), _p(alpha), _p(T),
+                                                _p(idx), _p(logits), _p(saved), _p(d_params), _p(d_feat), _p(loss),
+                                                w, b, _stream())
+    ws, wsz = _workspace(args, dev)
+    check(args(_p(ws), ctypes.byref(wsz)))
+    return d_params, d_feat, loss

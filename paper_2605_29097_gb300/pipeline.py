@@ -139,3 +139,138 @@ def synthetic_target(geo: Geometry, device="cuda") -> torch.Tensor:
     pr = torch.tensor([[0.0265625], [0.0015625], [0.1203125]], dtype=torch.float32, device=device)
     P, _ = render_heatmap(geo, field, G.SAMPLE_UNIFORM, extra=(pr, torch.ones(1, device=device)))
     return P
+
+
+# ------------------------------------------------------------- training step
+def scene_field(scene, device="cuda"):
+    return G.AnalyticField(torch.as_tensor(scene.packed(), device=device))
+
+
+def scene_signal(geo: Geometry, scene, occluder_z=None, atten=1.0, mode=G.SAMPLE_UNIFORM, seed=0, device="cuda"):
+    """Clean signal of an analytic scene; points beyond the occluder plane get
+    the round-trip amplitude factor `atten` (set-up only: torch scales w)."""
+    field = scene_field(scene, device)
+    xyz, apr = G.geraf_sample(geo.grid, mode, seed, 0, device=device)
+    f, grad, a, _ = G.geraf_fields(field, xyz)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+    _, _, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
+    if occluder_z is not None:
+        w = torch.where(xyz[2] > occluder_z, w * atten, w).contiguous()
+    return G.geraf_render(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band)
+
+
+def scene_target(geo: Geometry, scene, noise_seed=0, device="cuda"):
+    """Synthetic target of the training workload: analytic scene behind a
+    0.5-attenuation occluder plane, complex Gaussian noise at 10 dB SNR on the
+    signal, matched-filtered on the heatmap voxels."""
+    import geraf_inputs as gi
+    s = scene_signal(geo, scene, gi.C4_OCCLUDER_Z, gi.C4_OCCLUDER_ATTEN, device=device)
+    power = float((s.abs() ** 2).mean())
+    noise = torch.as_tensor(gi.c4_noise(noise_seed, tuple(s.shape), power).astype(np.complex64), device=device)
+    P, _, _, _ = G.geraf_filter((s + noise).contiguous(), geo.ant, geo.band, geo.vox)
+    return P
+
+
+def geometry_with_depths(geo: Geometry, n_z: int) -> Geometry:
+    """Same columns, cube and radar with n_z depth cells per column."""
+    g = G.make_grid([geo.grid.lo[d] for d in range(3)],
+                    [geo.grid.pitch[0], geo.grid.pitch[1], geo.grid.pitch[2] * geo.grid.n[2] / n_z],
+                    [geo.grid.n[0], geo.grid.n[1], n_z], geo.grid.aperture_z)
+    return Geometry(g, geo.n_ray, n_z, geo.ant, geo.vox, geo.band, geo.sharpness, geo.a_tx, geo.mode)
+
+
+def proposal_forward_backward(geo: Geometry, field, prop, target, seed: int, step: int, timers=None):
+    """One hot-path pass with depths drawn from the learned proposal (depth
+    samples per column = prop.depth), plus the proposal's own training signal
+    from the blended weights of this pass."""
+    def tic(name):
+        if timers is not None and name in timers:
+            timers[name][0].record()
+
+    def toc(name):
+        if timers is not None and name in timers:
+            timers[name][1].record()
+
+    logits, q, psaved = G.geraf_proposal_density(prop)
+    xyz, apr, idx = G.geraf_sample_proposal(geo.grid, prop, q, seed, step)
+    n_z = prop.depth
+    is_mlp = isinstance(field, G.MLPField)
+    f, grad, a, saved = G.geraf_fields(field, xyz, keep_saved=is_mlp)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+    alpha, T, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, n_z, fa, fn, geo.sharpness, geo.a_tx)
+    tic("render")
+    s = G.geraf_render(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band)
+    toc("render")
+    P, M, loss, dP = G.geraf_filter(s, geo.ant, geo.band, geo.vox, target)
+    g_s = G.geraf_filter_backward(geo.ant, geo.band, geo.vox, M, dP)
+    tic("render_backward")
+    d_w, d_t, d_G = G.geraf_render_backward(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band, g_s)
+    toc("render_backward")
+    d_f, d_a, d_sc = G.geraf_blend_backward(f, a, alpha, T, geo.n_ray, n_z, geo.sharpness, geo.a_tx, d_w, d_t)
+    d_params = G.geraf_fields_backward(field, xyz, saved, d_f, d_G, d_a) if is_mlp else None
+    dp_prop, df_prop, ploss = G.geraf_sample_backward(prop, geo.grid, n_z, alpha, T, idx, logits, psaved)
+    res = StepResult(loss, d_params, d_sc, P)
+    res.proposal = (dp_prop, df_prop, ploss)
+    return res
+
+
+def proposal_signal_dense(geo: Geometry, field, prop, seed: int, step: int):
+    """Proposal training signal from a dense regular-grid render of `field`
+    (geo.grid's own depths, a multiple of the proposal's G2)."""
+    logits, q, psaved = G.geraf_proposal_density(prop)
+    xyz, apr = G.geraf_sample(geo.grid, geo.mode, seed, step, device=geo.ant.device)
+    f, _, a, _ = G.geraf_fields(field, xyz, want_grad=False)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+    alpha, T, _, _, _ = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
+    return G.geraf_sample_backward(prop, geo.grid, geo.n_z, alpha, T, None, logits, psaved)
+
+
+def proposal_heatmap(geo: Geometry, field, prop, seed=0, step=0):
+    """Forward-only heatmap with proposal-drawn depths."""
+    _, q, _ = G.geraf_proposal_density(prop, keep_saved=False)
+    xyz, apr, _ = G.geraf_sample_proposal(geo.grid, prop, q, seed, step)
+    f, grad, a, _ = G.geraf_fields(field, xyz)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+    _, _, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, prop.depth, fa, fn, geo.sharpness, geo.a_tx)
+    s = G.geraf_render(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band)
+    P, _, _, _ = G.geraf_filter(s, geo.ant, geo.band, geo.vox)
+    return P
+
+
+def init_proposal(gshape=(64, 64, 64), feat=8, width=64, n_hidden=3, depth=16, seed=0, eps=0.01, device="cuda"):
+    """Seeded initial proposal (small random features, U(+-1/sqrt(fan_in)) MLP)."""
+    G0, G1, G2 = gshape
+    rng = np.random.default_rng(seed)
+    feats = (0.1 * rng.standard_normal((G2, G1, G0, feat))).astype(np.float32)
+    shapes = [(width, feat)] + [(width, width)] * (n_hidden - 1) + [(1, width)]
+    parts = []
+    for o, i in shapes:
+        parts += [rng.uniform(-1 / np.sqrt(i), 1 / np.sqrt(i), o * i), np.zeros(o)]
+    params = np.concatenate(parts).astype(np.float32)
+    master = torch.as_tensor(feats, device=device).requires_grad_(False)
+    prop = G.Proposal(master.half(), torch.as_tensor(params, device=device), width=width, n_hidden=n_hidden,
+                      eps=eps, depth=depth)
+    return prop, master
+
+
+class ProposalTrainer:
+    """AdamW on the proposal (FP32 master features, FP16 copy for the kernels)."""
+
+    def __init__(self, prop, master, lr=1e-2):
+        self.prop, self.master = prop, master
+        self.params = prop.params.detach().clone().requires_grad_(True)
+        self.feats = master.detach().clone().requires_grad_(True)
+        self.opt = torch.optim.Adam([self.params, self.feats], lr=lr)
+
+    def step(self, d_params, d_feat):
+        self.opt.zero_grad(set_to_none=False)
+        self.params.grad = d_params.clone()
+        self.feats.grad = d_feat.clone()
+        self.opt.step()
+        with torch.no_grad():
+            self.prop.params.copy_(self.params)
+            self.prop.features.copy_(self.feats.half())
