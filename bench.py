@@ -181,6 +181,78 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
+    """Training step on the random-scene workload: 2^24 stratified samples
+    (256^2 columns x 256 depths) vs 2^20 proposal samples (256^2 x 16), both
+    with the MLP's Adam update (and the proposal's own update); then, at fixed
+    parameters, heatmap rel L2 and MLP-gradient cosine of proposal vs uniform
+    sampling and the fallback decision (proposal error > 2e-3 -> uniform)."""
+    import numpy as np
+    import torch
+    import geraf_inputs as gi
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import pipeline as PL
+    wl = gi.workload("c4")
+    geo = PL.make_geometry(wl, dev)
+    target = PL.scene_target(geo, gi.c4_scene(4), noise_seed=4, device=dev)
+    spec = gi.MLPSpec(center=(0.0, 0.0, 0.15), half=0.06)
+    p = torch.as_tensor(gi.mlp_init(spec, seed=11, sdf_bias=0.02), device=dev)
+    field = G.MLPField(p, center=spec.center, half=spec.half)
+    master = p.clone().requires_grad_(True)
+    opt = torch.optim.Adam([master], lr=1e-3)
+    prop, pm = PL.init_proposal(gshape=(64, 64, 64), depth=16, seed=5, device=dev)
+    ptrain = PL.ProposalTrainer(prop, pm, lr=1e-2)
+
+    def apply(d):
+        opt.zero_grad(set_to_none=False)
+        master.grad = d.clone()
+        opt.step()
+        with torch.no_grad():
+            p.copy_(master)
+
+    def uniform_step(k):
+        r = PL.forward_backward(geo, field, target, seed=21, step=k)
+        apply(r.d_params)
+        return r
+
+    def proposal_step(k):
+        r = PL.proposal_forward_backward(geo, field, prop, target, seed=23, step=k)
+        apply(r.d_params)
+        dp, df, _ = r.proposal
+        ptrain.step(dp, df)
+        return r
+
+    def timed(fn, w, n, k0):
+        for i in range(w):
+            fn(k0 + i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(n):
+            fn(k0 + w + i)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms_u = timed(uniform_step, warmup, steps, 0)
+    torch.cuda.empty_cache()
+    ms_p = timed(proposal_step, p_warmup, p_steps, 100)
+    # fixed-parameter comparison
+    ru = PL.forward_backward(geo, field, target, seed=31, step=0)
+    rp = PL.proposal_forward_backward(geo, field, prop, target, seed=31, step=0)
+    Pu, Pp = ru.P.double(), rp.P.double()
+    err = float(torch.linalg.norm(Pp - Pu) / torch.linalg.norm(Pu))
+    gu, gp = ru.d_params.double(), rp.d_params.double()
+    cos = float((gu @ gp) / (torch.linalg.norm(gu) * torch.linalg.norm(gp)))
+    torch.cuda.synchronize()
+    return {"workload": "random ellipsoids/boxes behind a 0.5 occluder, 10 dB noise; 64x64 array, 128 freqs, "
+                        "MLP 4x128 fp32, 64^3 heatmap",
+            "uniform_samples": wl.grid.n_pts, "proposal_samples": geo.n_ray * prop.depth,
+            "uniform_step_ms": ms_u, "proposal_step_ms": ms_p, "speedup": ms_u / ms_p,
+            "heatmap_rel_l2": err, "grad_cosine": cos, "tolerance": 2e-3, "fallback_to_uniform": err > 2e-3,
+            "steps": {"uniform": steps, "proposal": p_steps}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,6 +261,7 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -307,6 +380,7 @@ def main():
         n_units = n_pts * geo.ant.shape[1] * geo.band.n_f
         achieved = n_units * FLOPS_PER_TERM / (per_kernel[dom] * 1e-3) / 1e12
         peak = sm_count * 128 * max_mhz * 1e6 / INSTR_PER_TERM * FLOPS_PER_TERM / 1e12
+        launches = PL.launches_per_step(field) * args.steps
         cpu = None
         if not args.no_cpu_baseline:
             # intermediate arrays of one step for the oracle sample
@@ -333,9 +407,14 @@ def main():
                                        f"{INSTR_PER_TERM} instr per term x {FLOPS_PER_TERM} flops per term"},
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": PL.launches_per_step(field) * args.steps,
+            "gpu_launches": launches,
             "clocks": clocks,
+            "train_step": None,
         }
+        if not args.no_train and args.workload == "c2":
+            del geo, field, target, params, geo_e, field_e
+            torch.cuda.empty_cache()
+            line["train_step"] = train_step_compare(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
