@@ -181,6 +181,26 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value of x over all ranks (the job's time is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank: int) -> dict:
+    """Each rank runs an independent replica: its own sampling seed and MLP init."""
+    return {"sample": 7 + 1000 * rank, "mlp": 1234 + rank}
+
+
+def job_rate(units_per_step_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return units_per_step_per_rank * steps * world / (max_ms * 1e-3)
+
+
 def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
     """Training step on the random-scene workload: 2^24 stratified samples
     (256^2 columns x 256 depths) vs 2^20 proposal samples (256^2 x 16), both
@@ -289,14 +309,15 @@ def main():
     wl = gi.workload(args.workload)
     geo = PL.make_geometry(wl, dev)
     spec = gi.MLPSpec()
-    params_np = gi.mlp_init(spec, seed=1234 + rank)
+    seeds = replica_seeds(rank)
+    params_np = gi.mlp_init(spec, seed=seeds["mlp"])
     params = torch.as_tensor(params_np, device=dev)
     field = G.MLPField(params)
     target = PL.synthetic_target(geo, dev)
     torch.cuda.synchronize()
     n_pts = wl.grid.n_pts
     terms = PL.terms_per_step(geo, n_pts)
-    seed = 7 + 1000 * rank
+    seed = seeds["sample"]
 
     def barrier():
         if world > 1:
@@ -328,11 +349,8 @@ def main():
     G.geraf_poll_device_error()
     ms = t_start.elapsed_time(t_end)
     per_kernel = {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev) / args.steps for nm in names}
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = terms * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, dev)
+    value = job_rate(terms, args.steps, world, ms)
 
     # end to end through the public API with host buffers: per step the
     # inputs (MLP parameters, target heatmap, antenna positions) go host ->
@@ -365,10 +383,7 @@ def main():
         torch.cuda.synchronize()
     e_s = time.perf_counter() - w0
     barrier()
-    e_t = torch.tensor([e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-    e_value = terms * e_steps * world / float(e_t.item())
+    e_value = job_rate(terms, e_steps, world, 1e3 * max_over_ranks(e_s, world, dev))
     h2d = (h_params.numel() + h_target.numel() + h_ant.numel()) * 4
     d2h = 8 + h_dp.numel() * 4 + 8
 
