@@ -189,25 +189,40 @@ def positional_encoding(spec, xyz):
     return g, dg
 
 
-def mlp_forward(spec, params, xyz):
-    """Returns (f [N], G [3, N], a [N], cache)."""
+def bf16_round(x):
+    """Round to bfloat16 (through FP32, round to nearest even), returned as FP64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_forward(spec, params, xyz, precision="fp32"):
+    """Returns (f [N], G [3, N], a [N], cache). precision "bf16" is the BF16
+    network: hidden-layer weights and every hidden layer's inputs (encoding,
+    activations, tangents) rounded to bfloat16, sums exact (FP64); biases and
+    the head weights FP32, the head reads the last BF16 activations."""
     from geraf_inputs import unpack_params
     layers = [(W.astype(np.float64), b.astype(np.float64))
               for W, b in unpack_params(spec, np.asarray(params, dtype=np.float32))]
+    bf = precision == "bf16"
+    r = bf16_round if bf else (lambda v: v)
     z, dz = positional_encoding(spec, xyz)
     cache = {"z": [z], "dz": [dz], "h": [], "dh": []}
     for W, b in layers[:-1]:
-        h = W @ z + b[:, None]
-        dh = np.einsum("oi,din->don", W, dz)
+        Wr, zr, dzr = r(W), r(z), r(dz)
+        h = Wr @ zr + b[:, None]
+        dh = np.einsum("oi,din->don", Wr, dzr)
         s = _sigmoid(spec.beta * h)
         z = _softplus(h, spec.beta)
         dz = s[None] * dh
         cache["h"].append(h); cache["dh"].append(dh)
         cache["z"].append(z); cache["dz"].append(dz)
     Wh, bh = layers[-1]
-    f = Wh[0] @ z + bh[0]
-    logit = Wh[1] @ z + bh[1]
-    G = np.einsum("i,din->dn", Wh[0], dz)
+    zr, dzr = r(z), r(dz)
+    f = Wh[0] @ zr + bh[0]
+    logit = Wh[1] @ zr + bh[1]
+    G = np.einsum("i,din->dn", Wh[0], dzr)
     a = _sigmoid(logit)
     cache["a"] = a
     return f, G, a, cache

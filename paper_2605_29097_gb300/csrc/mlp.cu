@@ -448,16 +448,21 @@ geraf_status mlp_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* bytes
     return GERAF_OK;
 }
 
+geraf_status mlp_tc_forward_impl(const geraf_field_desc*, const float*, int64_t, float*, float*, float*, void*,
+                                 cudaStream_t);
+
 geraf_status mlp_forward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
                               float* refl, void* saved, size_t saved_bytes, cudaStream_t st) {
     MlpGeom g;
     if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
-    if (d->precision != GERAF_PREC_FP32) return fail(GERAF_ERR_UNSUPPORTED, "fields: MLP precision %d not built", d->precision);
+    if (d->precision != GERAF_PREC_FP32 && d->precision != GERAF_PREC_BF16)
+        return fail(GERAF_ERR_UNSUPPORTED, "fields: MLP precision %d unknown", d->precision);
     if (saved) {
         size_t need = 0;
         mlp_saved_bytes(d, n, &need);
         if (saved_bytes < need) return fail(GERAF_ERR_WORKSPACE, "fields: saved %zu < %zu bytes", saved_bytes, need);
     }
+    if (d->precision == GERAF_PREC_BF16) return mlp_tc_forward_impl(d, xyz, n, sdf, grad, refl, saved, st);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
@@ -473,7 +478,8 @@ geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int6
                                void* ws, size_t* ws_bytes, cudaStream_t st) {
     MlpGeom g;
     if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
-    if (d->precision != GERAF_PREC_FP32) return fail(GERAF_ERR_UNSUPPORTED, "fields: MLP precision %d not built", d->precision);
+    // BF16 networks: the adjoint runs in FP32 on CUDA cores from the FP32 pre-activations the
+    // tensor-core forward saved (the BF16 roundings are passed through as identities)
     const int n_cta = n_ctas_for(g.n_tiles);
     WsCarver c(ws);
     float* zbar = c.take<float>((size_t)n * 4 * MW);

@@ -64,3 +64,32 @@ def test_mlp_origins_only_sdf(G, oracle):
     of, _, _, _ = oracle.mlp_forward(spec, params, xyz)
     assert g is None and a is None and s is None
     assert rel_l2(f.cpu().numpy(), of) < 1e-5
+
+
+@pytest.mark.parametrize("n,n_levels,n_hidden", [(1000, 6, 4), (77, 10, 3)])
+def test_mlp_bf16_tensor_cores(G, oracle, n, n_levels, n_hidden):
+    """BF16 network on tcgen05 vs the oracle's BF16 definition (weights and
+    layer inputs rounded to bfloat16, exact sums): relative L2 <= 2e-3."""
+    spec = gi.MLPSpec(n_levels=n_levels, n_hidden=n_hidden)
+    params = gi.mlp_init(spec, seed=n + 1)
+    rng = np.random.default_rng(n + 1)
+    xyz = (np.array(spec.center)[:, None] + rng.uniform(-spec.half, spec.half, (3, n))).astype(np.float32)
+    field = G.MLPField(torch.as_tensor(params, device="cuda"), n_levels=n_levels, n_hidden=n_hidden,
+                       beta=spec.beta, center=spec.center, half=spec.half, precision=G.PREC_BF16)
+    xt = torch.as_tensor(xyz, device="cuda")
+    f, grad, a, saved = G.geraf_fields(field, xt, keep_saved=True)
+    G.geraf_poll_device_error()
+    h = lambda t: t.detach().cpu().numpy()
+    of, oG, oa, cache = oracle.mlp_forward(spec, params, xyz, precision="bf16")
+    e = (rel_l2(h(f), of), rel_l2(h(a), oa), rel_l2(h(grad), oG))
+    f32, G32, a32, _ = oracle.mlp_forward(spec, params, xyz)
+    print(f"bf16 vs bf16 definition: f {e[0]:.2e} a {e[1]:.2e} G {e[2]:.2e}; vs fp32 network: "
+          f"f {rel_l2(h(f), f32):.2e} G {rel_l2(h(grad), G32):.2e}")
+    assert max(e) < 2e-3
+    d_f = rng.standard_normal(n).astype(np.float32)
+    d_G = rng.standard_normal((3, n)).astype(np.float32)
+    d_a = rng.standard_normal(n).astype(np.float32)
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    gp = G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a))
+    ogp = oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)
+    assert rel_l2(h(gp), ogp) < 2e-3
