@@ -273,6 +273,51 @@ def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
             "steps": {"uniform": steps, "proposal": p_steps}}
 
 
+def mlp_bench(n_pts=1 << 21, reps=5):
+    """Fields kernels alone on n_pts points (4x128 MLP, PE 6 octaves, value +
+    3 gradient tangents): FP32 CUDA-core forward, BF16 tensor-core forward and
+    the adjoint, with algorithmic TFLOP/s (2 flops per MAC of the 4-stream GEMMs)."""
+    import numpy as np
+    import torch
+    import geraf_inputs as gi
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import _build
+    _build.build()
+    spec = gi.MLPSpec()
+    rng = np.random.default_rng(0)
+    xyz = torch.as_tensor((np.array(spec.center)[:, None] + rng.uniform(-spec.half, spec.half, (3, n_pts)))
+                          .astype(np.float32), device="cuda")
+    p = torch.as_tensor(gi.mlp_init(spec, seed=1), device="cuda")
+    macs = 4 * (spec.in_dim * 128 + (spec.n_hidden - 1) * 128 * 128) + 128 * 5
+    out = {"mode": "mlp", "n_pts": n_pts, "mac_per_point": macs}
+    for name, prec in (("fp32", G.PREC_FP32), ("bf16", G.PREC_BF16)):
+        field = G.MLPField(p, precision=prec)
+        for _ in range(2):
+            f, grad, a, saved = G.geraf_fields(field, xyz, keep_saved=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            G.geraf_fields(field, xyz)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[f"forward_{name}_ms"] = ms
+        out[f"forward_{name}_tflops"] = 2 * macs * n_pts / (ms * 1e-3) / 1e12
+        d = torch.ones(n_pts, device="cuda")
+        dg = torch.ones(3, n_pts, device="cuda")
+        G.geraf_fields_backward(field, xyz, saved, d, dg, d)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            G.geraf_fields_backward(field, xyz, saved, d, dg, d)
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"backward_{name}_ms"] = e0.elapsed_time(e1) / reps
+    G.geraf_poll_device_error()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,6 +327,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
     ap.add_argument("--no-train", action="store_true", help="skip the training-step comparison")
+    ap.add_argument("--mlp-bench", type=int, default=0, metavar="N_PTS",
+                    help="time only the fields kernels on N_PTS points and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -291,6 +338,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.mlp_bench:
+        mlp_bench(args.mlp_bench)
         return
 
     import torch
