@@ -129,6 +129,11 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -186,6 +191,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
         if ((it & 63u) == 63u && global_timer_ns() - t0 > limit_ns) return false;
     }
     return false;
+}
+
+// After a timed-out wait at iteration `it` of a two-buffer TMA pipeline: give
+// the copies still in flight (that iteration's and, if issued, the next one's)
+// a bounded time to land before the CTA leaves, since its shared memory is
+// handed to the next CTA on the SM.
+__device__ __forceinline__ void mbar_drain2(uint64_t* bar, int it, int n_my) {
+    mbar_wait(&bar[it & 1], (it >> 1) & 1, 100000000ull);
+    if (it + 1 < n_my) mbar_wait(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1, 100000000ull);
 }
 
 }  // namespace geraf

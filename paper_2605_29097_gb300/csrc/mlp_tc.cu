@@ -238,7 +238,10 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs
         }
         __syncthreads();   // the next tile's encoding overwrites the tile the head read
     }
-    if (*abort_flag && t == 0) atomicOr(a.err, 1);
+    if (*abort_flag && t == 0) {
+        atomicOr(a.err, 1);
+        mbar_wait(bar, phase ^ 1u, 100000000ull);   // bounded: let the timed-out MMA finish before TMEM is freed
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();

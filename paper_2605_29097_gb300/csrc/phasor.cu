@@ -24,6 +24,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -62,7 +63,8 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
         r.b = make_float4(gx * k, gy * k, gz * k, t_eff[j]);
         r.c = make_float4(dir ? 1.0f : -1.0f, dir ? 1.0f / gn : 0.0f, 0.0f, 0.0f);
     } else {
-        r.a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // padding: point 0's position with zero weight (inside every range bound)
+        r.a = make_float4(xyz[0], xyz[n], xyz[2 * n], 0.0f);
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         r.c = make_float4(-1.0f, 0.0f, 0.0f, 0.0f);
     }
@@ -87,7 +89,7 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
         r.a = make_float4(vox[j], vox[n + j], vox[2 * n + j], cr);
         r.b = make_float4(ci, 0.0f, 0.0f, 0.0f);
     } else {
-        r.a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        r.a = make_float4(vox[0], vox[n], vox[2 * n], 0.0f);
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     out[j] = r;
@@ -138,10 +140,12 @@ struct ToBinsArgs {
     int n_ant_pad;
     int a_t;                 // antennas per CTA
     BandK bk;
+    const int* run_if;       // when set, the kernel runs only if *run_if != 0
 };
 
 template <bool kComplexAmp>
 __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs args) {
+    if (args.run_if && *args.run_if == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int G = args.bk.g;
     const int A_T = args.a_t;
@@ -197,7 +201,10 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
         if (!ok) atomicOr(abort_flag, 1);
         __syncthreads();
         if (*abort_flag) {
-            if (t == 0) atomicOr(args.err, 1);
+            if (t == 0) {
+                atomicOr(args.err, 1);
+                mbar_drain2(bar, it, n_my);
+            }
             return;
         }
         const PtRec* tile = tiles + buf * TP;
@@ -305,7 +312,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
 
 // partial [splits][n_ant_pad][n_f_pad] -> out [n_ant][n_f], FP64 sum in split order
 __global__ void reduce_bins(const float2* __restrict__ partial, int splits, int n_ant, int n_ant_pad, int n_f,
-                            int n_f_pad, float2* __restrict__ out) {
+                            int n_f_pad, float2* __restrict__ out, const int* run_if = nullptr) {
+    if (run_if && *run_if == 0) return;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n_ant * n_f) return;
     int i = (int)(idx / n_f), n = (int)(idx - (int64_t)i * n_f);
@@ -336,10 +344,12 @@ struct ToPointsArgs {
     float* partial;            // filter: float2 [splits][n]; render bwd: float [splits][6][n]
     int* err;
     BandK bk;
+    const int* run_if;         // when set, the kernel runs only if *run_if != 0
 };
 
 template <int MODE>
 __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsArgs args) {
+    if (args.run_if && *args.run_if == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int* abort_flag = reinterpret_cast<int*>(smem + 16);
@@ -402,7 +412,10 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
         if (!ok) atomicOr(abort_flag, 1);
         __syncthreads();
         if (*abort_flag) {
-            if (t == 0) atomicOr(args.err, 1);
+            if (t == 0) {
+                atomicOr(args.err, 1);
+                mbar_drain2(bar, it, n_my);
+            }
             return;
         }
         const float4* tile = rows + buf * AT * row_f4;
@@ -645,6 +658,563 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
     return p;
 }
 
+// ==================================================== Chebyshev phasor sums
+// Per antenna i, the frequency dependence of a term is exp(-j 2 pi (f0 + n df)
+// 2 r / c). The f0 part is folded into the point's complex amplitude (one
+// double-single phase and one sincos per pair); with r = r_c + dr x, |x| <= 1
+// over the whole call, the Jacobi-Anger expansion
+//   exp(-j a_n x) = sum_k eps_k (-j)^k J_k(a_n) T_k(x),  a_n = 2 pi n (2 df / c) dr,
+// truncated where the Bessel tail falls below 1e-9, turns the bin sums into
+// K Chebyshev moments per antenna (K ~ a_max + 15, about 30 for a 4 GHz sweep
+// over a 15 cm range spread, independent of the number of bins):
+//   to bins:   s(i, n) = sum_k C_k(n) M_k(i),  M_k(i) = sum_j A'_ij T_k(x_ij)
+//   to points: sum_n s(i, n) exp(+j ...) = exp(+j 2 pi K0 r) sum_k T_k(x) S_k(i),
+//              evaluated per pair by Clenshaw's recurrence.
+// C_k(n) = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n) is computed on the device
+// (Miller's backward recurrence in FP64) from a range bound of the call's
+// points and antennas, so the call stays asynchronous. If K would exceed
+// CH_KMAX the exact recurrence kernels run instead (decided on the device).
+constexpr int CH_KMAX = 64;
+constexpr int CH_THREADS = 128;
+constexpr int CH_TP = 32;             // points per TMA tile
+constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before it joins the outer sum
+constexpr size_t CH_PARTIAL_BYTES = 256ull << 20;   // bound on the split partials of one call
+
+struct ChebPlan {
+    float r_c;        // range centre (FP32; the coefficients use this value)
+    float inv_dr;     // 1 / half range (FP32; the coefficients use 1 / inv_dr)
+    int K;            // Chebyshev order
+    int use_direct;   // 1: the exact recurrence kernels must run instead
+    int run_cheb;     // = !use_direct
+    int pad[3];
+};
+
+__global__ void bbox_partial_kernel(const float* __restrict__ xyz, int64_t n, float* __restrict__ part) {
+    __shared__ float red[6][256];
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            const float v = xyz[d * n + j];
+            mn[d] = fminf(mn[d], v);
+            mx[d] = fmaxf(mx[d], v);
+        }
+    for (int d = 0; d < 3; ++d) {
+        red[d][threadIdx.x] = mn[d];
+        red[3 + d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k)
+            for (int d = 0; d < 3; ++d) {
+                red[d][threadIdx.x] = fminf(red[d][threadIdx.x], red[d][threadIdx.x + k]);
+                red[3 + d][threadIdx.x] = fmaxf(red[3 + d][threadIdx.x], red[3 + d][threadIdx.x + k]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// J_0 .. J_{kcount-1}(a) by Miller's backward recurrence (normalised by
+// J_0 + 2 sum J_2m = 1), FP64
+__device__ void bessel_j(double a, int kcount, double* out) {
+    if (a < 1e-300) {
+        for (int k = 0; k < kcount; ++k) out[k] = k == 0 ? 1.0 : 0.0;
+        return;
+    }
+    int start = kcount + 20 + (int)a;
+    start += start & 1;
+    double jp1 = 0.0, j = 1e-300, norm = 0.0;
+    for (int k = start; k >= 1; --k) {
+        const double jm1 = (2.0 * k / a) * j - jp1;
+        jp1 = j;
+        j = jm1;                      // j = J_{k-1}
+        if (k - 1 < kcount) out[k - 1] = j;
+        if ((k - 1) % 2 == 0 && k - 1 > 0) norm += 2.0 * j;
+        if (fabs(j) > 1e250) {        // rescale
+            jp1 *= 1e-250;
+            j *= 1e-250;
+            norm *= 1e-250;
+            for (int q = k - 1; q < kcount; ++q) out[q] *= 1e-250;
+        }
+    }
+    norm += j;                        // J_0
+    for (int k = 0; k < kcount; ++k) out[k] /= norm;
+}
+
+// one block: points bbox + antennas -> range bound, order K, coefficients C[k][n]
+__global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, const float* __restrict__ ant,
+                                 int n_ant, double Kd, int n_f, double eps, ChebPlan* __restrict__ plan,
+                                 double2* __restrict__ C) {
+    __shared__ float box[6];
+    __shared__ float rr[2][256];
+    __shared__ int sK;
+    __shared__ float s_rc, s_inv;
+    const int t = threadIdx.x;
+    if (t < 6) {
+        float v = t < 3 ? INFINITY : -INFINITY;
+        for (int b = 0; b < n_part; ++b) v = t < 3 ? fminf(v, part[b * 6 + t]) : fmaxf(v, part[b * 6 + t]);
+        box[t] = v;
+    }
+    __syncthreads();
+    float lo = INFINITY, hi = 0.0f;
+    for (int i = t; i < n_ant; i += blockDim.x) {
+        float dn = 0.0f, df = 0.0f;
+        for (int d = 0; d < 3; ++d) {
+            const float a = ant[d * n_ant + i];
+            const float e = fmaxf(fmaxf(box[d] - a, a - box[3 + d]), 0.0f);
+            const float f = fmaxf(fabsf(a - box[d]), fabsf(box[3 + d] - a));
+            dn += e * e;
+            df += f * f;
+        }
+        lo = fminf(lo, sqrtf(dn));
+        hi = fmaxf(hi, sqrtf(df));
+    }
+    rr[0][t] = lo;
+    rr[1][t] = hi;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (t < k) {
+            rr[0][t] = fminf(rr[0][t], rr[0][t + k]);
+            rr[1][t] = fmaxf(rr[1][t], rr[1][t + k]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double rl = rr[0][0], rh = rr[1][0];
+        const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6, 1e-5);
+        const float rc = (float)(0.5 * (rh + rl));
+        const float inv = (float)(1.0 / dr);
+        const double a_max = 2.0 * 3.14159265358979323846 * (n_f - 1) * Kd / (double)inv;
+        double J[CH_KMAX + 8];
+        bessel_j(a_max, CH_KMAX + 8, J);
+        int K = CH_KMAX + 1;
+        double tail = 0.0;
+        for (int k = CH_KMAX + 7; k >= 0; --k) {
+            tail += 2.0 * fabs(J[k]);
+            if (tail > eps) { K = k + 1; break; }
+        }
+        if (K < 2) K = 2;
+        const int direct = K > CH_KMAX;
+        if (K > CH_KMAX) K = CH_KMAX;
+        plan->r_c = rc;
+        plan->inv_dr = inv;
+        plan->K = K;
+        plan->use_direct = direct;
+        plan->run_cheb = !direct;
+        sK = K;
+        s_rc = rc;
+        s_inv = inv;
+    }
+    __syncthreads();
+    const int K = sK;
+    const double dr = 1.0 / (double)s_inv;
+    for (int n = t; n < n_f; n += blockDim.x) {
+        double J[CH_KMAX];
+        const double an = 2.0 * 3.14159265358979323846 * n * Kd * dr;
+        bessel_j(an, K, J);
+        // exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
+        double sphi, cphi;
+        sincospi(-2.0 * (double)n * Kd * (double)s_rc, &sphi, &cphi);
+        for (int k = 0; k < K; ++k) {
+            const double m = (k == 0 ? 1.0 : 2.0) * J[k];
+            double pr, pi;      // (-j)^k
+            switch (k & 3) {
+                case 0: pr = 1.0; pi = 0.0; break;
+                case 1: pr = 0.0; pi = -1.0; break;
+                case 2: pr = -1.0; pi = 0.0; break;
+                default: pr = 0.0; pi = 1.0; break;
+            }
+            const double ar = m * pr, ai = m * pi;
+            C[(size_t)k * n_f + n] = make_double2(cphi * ar - sphi * ai, cphi * ai + sphi * ar);
+        }
+    }
+}
+
+struct ChebBinsArgs {
+    const PtRec* pts;          // tiles of CH_TP records
+    const float4* ant;         // n_ant_pad (x, y, z, c_ant)
+    int n_ant;
+    int n_tiles;
+    int tiles_per_split;
+    const ChebPlan* plan;
+    float kh, kl;              // K0 = 2 f0 / c as double-single (cycles per metre)
+    float2* partial;           // [splits][n_ant][CH_KMAX]
+    int* err;
+};
+
+// thread = antenna: Chebyshev moments of the antenna over the split's points.
+// Inner sums over CH_FLUSH tiles in registers, outer FP32 sums in shared memory.
+template <bool kComplexAmp>
+__global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArgs args) {
+    if (!args.plan->run_cheb) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    PtRec* tiles = reinterpret_cast<PtRec*>(smem);                              // [2][CH_TP]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * CH_TP * sizeof(PtRec));
+    int* abort_flag = reinterpret_cast<int*>(bar + 2);
+    float2* outer = reinterpret_cast<float2*>(smem + 2 * CH_TP * sizeof(PtRec) + 32);   // [CH_KMAX][CH_THREADS]
+    const int t = threadIdx.x;
+    const int ia = blockIdx.x * CH_THREADS + t;
+    const int split = blockIdx.y;
+    const int tile0 = split * args.tiles_per_split;
+    const int tile1 = min(tile0 + args.tiles_per_split, args.n_tiles);
+    const int n_my = tile1 - tile0;
+    const int K = args.plan->K;
+    const float r_c = args.plan->r_c, inv_dr = args.plan->inv_dr;
+    const float4 A4 = args.ant[ia];                          // padded: always readable
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    for (int k = 0; k < CH_KMAX; ++k) outer[k * CH_THREADS + t] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    const uint32_t tile_bytes = (uint32_t)(CH_TP * sizeof(PtRec));
+    if (t == 0)
+        for (int s = 0; s < 2 && s < n_my; ++s) {
+            mbar_arrive_expect_tx(&bar[s], tile_bytes);
+            tma_load_1d(tiles + s * CH_TP, args.pts + (size_t)(tile0 + s) * CH_TP, tile_bytes, &bar[s]);
+        }
+    float mr[CH_KMAX], mi[CH_KMAX];
+#pragma unroll
+    for (int k = 0; k < CH_KMAX; ++k) mr[k] = mi[k] = 0.0f;
+
+    for (int it = 0; it < n_my; ++it) {
+        const int buf = it & 1;
+        if (!mbar_wait(&bar[buf], (it >> 1) & 1)) atomicOr(abort_flag, 1);
+        __syncthreads();
+        if (*abort_flag) {
+            if (t == 0) {
+                atomicOr(args.err, 1);
+                mbar_drain2(bar, it, n_my);
+            }
+            return;
+        }
+        const PtRec* tile = tiles + buf * CH_TP;
+        for (int p = 0; p < CH_TP; ++p) {
+            const PtRec P = tile[p];
+            const Range R = pair_range(P.a.x, P.a.y, P.a.z, A4.x, A4.y, A4.z);
+            float ar_, ai_;
+            {
+                const float fr = phase_frac(R.rh, R.rl, args.kh, args.kl);
+                float sn, cs;
+                __sincosf(6.28318530717958648f * fr, &sn, &cs);
+                if (!kComplexAmp) {
+                    const float inv_r2 = R.rs * R.rs;
+                    const float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
+                    const float D = fmaxf(nd * nd * inv_r2 - P.c.x, 0.0f);
+                    const float tt = __saturatef(P.b.w - A4.w);
+                    const float amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
+                    ar_ = amp * cs;                          // A exp(-j 2 pi K0 r)
+                    ai_ = -amp * sn;
+                } else {
+                    const float cr = P.a.w, ci = P.b.x;
+                    ar_ = cr * cs + ci * sn;
+                    ai_ = ci * cs - cr * sn;
+                }
+            }
+            const float x = __fmul_rn(__fadd_rn(__fsub_rn(R.rh, r_c), R.rl), inv_dr);
+            const float x2 = 2.0f * x;
+            float tkm1 = 1.0f, tk = x;                       // T_0, T_1
+            mr[0] += ar_;
+            mi[0] += ai_;
+            mr[1] = fmaf(ar_, x, mr[1]);
+            mi[1] = fmaf(ai_, x, mi[1]);
+#pragma unroll
+            for (int kc = 0; kc < CH_KMAX; kc += 8) {
+                if (kc < K) {
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const int k = kc + kk;
+                        if (k >= 2) {
+                            const float tn = fmaf(x2, tk, -tkm1);
+                            tkm1 = tk;
+                            tk = tn;
+                            mr[k] = fmaf(ar_, tn, mr[k]);
+                            mi[k] = fmaf(ai_, tn, mi[k]);
+                        }
+                    }
+                }
+            }
+        }
+        if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
+#pragma unroll
+            for (int kc = 0; kc < CH_KMAX; kc += 8)
+                if (kc < K)
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        float2 o = outer[(kc + kk) * CH_THREADS + t];
+                        o.x += mr[kc + kk];
+                        o.y += mi[kc + kk];
+                        outer[(kc + kk) * CH_THREADS + t] = o;
+                        mr[kc + kk] = mi[kc + kk] = 0.0f;
+                    }
+        }
+        __syncthreads();
+        if (t == 0 && it + 2 < n_my) {
+            mbar_arrive_expect_tx(&bar[buf], tile_bytes);
+            tma_load_1d(tiles + buf * CH_TP, args.pts + (size_t)(tile0 + it + 2) * CH_TP, tile_bytes, &bar[buf]);
+        }
+    }
+    if (ia < args.n_ant) {
+        float2* dst = args.partial + ((size_t)split * args.n_ant + ia) * CH_KMAX;
+        for (int k = 0; k < K; ++k) dst[k] = outer[k * CH_THREADS + t];
+    }
+}
+
+size_t cheb_bins_smem() { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)CH_KMAX * CH_THREADS * sizeof(float2); }
+
+// out(i, n) = sum_k C_k(n) sum_splits M_k(i), FP64
+__global__ void cheb_reconstruct_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
+                                        const ChebPlan* __restrict__ plan, const double2* __restrict__ C,
+                                        float2* __restrict__ out) {
+    if (!plan->run_cheb) return;
+    extern __shared__ double2 Mi[];          // [CH_KMAX] moments of this block's antenna
+    const int i = blockIdx.x;
+    const int K = plan->K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        for (int s = 0; s < splits; ++s) {
+            const float2 v = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
+            sr += v.x;
+            si += v.y;
+        }
+        Mi[k] = make_double2(sr, si);
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < n_f; n += blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double2 c = C[(size_t)k * n_f + n], m = Mi[k];
+            sr += c.x * m.x - c.y * m.y;
+            si += c.x * m.y + c.y * m.x;
+        }
+        out[(size_t)i * n_f + n] = make_float2((float)sr, (float)si);
+    }
+}
+
+// antenna rows for the Clenshaw kernels: head (x, y, z, c) + CH_KMAX float4
+// (h_re, h_re, h_im, h_im) with h_k = sum_n sig(n) * (conj ? conj(C_k(n)) : C_k(n))
+// and sig = (conj_sig ? conj(v) : v)
+__global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __restrict__ c_ant,
+                                 const float2* __restrict__ sig, int n_ant, int n_ant_pad, int n_f,
+                                 const ChebPlan* __restrict__ plan, const double2* __restrict__ C, int conj_c,
+                                 int conj_sig, float4* __restrict__ rows) {
+    if (!plan->run_cheb) return;
+    const int i = blockIdx.x;
+    if (i >= n_ant_pad) return;
+    float4* row = rows + (size_t)i * (1 + CH_KMAX);
+    if (threadIdx.x == 0) {
+        const int q = i < n_ant ? i : 0;
+        row[0] = make_float4(ant[q], ant[n_ant + q], ant[2 * n_ant + q], c_ant ? c_ant[q] : 0.0f);
+    }
+    const int K = plan->K;
+    for (int k = threadIdx.x; k < CH_KMAX; k += blockDim.x) {
+        double hr = 0.0, hi = 0.0;
+        if (i < n_ant && k < K) {
+            for (int n = 0; n < n_f; ++n) {
+                const float2 v = sig[(size_t)i * n_f + n];
+                const double vr = v.x, vi = conj_sig ? -(double)v.y : (double)v.y;
+                const double2 c = C[(size_t)k * n_f + n];
+                const double cr = c.x, ci = conj_c ? -c.y : c.y;
+                hr += vr * cr - vi * ci;
+                hi += vr * ci + vi * cr;
+            }
+        }
+        row[1 + k] = make_float4((float)hr, (float)hr, (float)hi, (float)hi);
+    }
+}
+
+struct ChebPointsArgs {
+    const PtRec* pts;
+    const float* vox;
+    int64_t n;
+    const float4* rows;
+    int at;                    // antennas per tile
+    int n_ant_tiles;
+    int tiles_per_split;
+    const ChebPlan* plan;
+    float kh, kl;
+    float* partial;
+    int* err;
+};
+
+// thread = 2 points (lanes of the packed Clenshaw sums)
+static_assert(TPK_V == 2, "the packed Clenshaw sums carry two points per thread");
+
+template <int MODE>
+__global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPointsArgs args) {
+    if (!args.plan->run_cheb) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    int* abort_flag = reinterpret_cast<int*>(smem + 16);
+    constexpr int ROW = 1 + CH_KMAX;
+    float4* rows = reinterpret_cast<float4*>(smem + 32);   // [2][at][ROW]
+    const int AT = args.at;
+    const int t = threadIdx.x;
+    const int split = blockIdx.y;
+    const int tile0 = split * args.tiles_per_split;
+    const int tile1 = min(tile0 + args.tiles_per_split, args.n_ant_tiles);
+    const int n_my = tile1 - tile0;
+    const uint32_t tile_bytes = (uint32_t)(AT * ROW * sizeof(float4));
+    const int K = args.plan->K;
+    const float r_c = args.plan->r_c, inv_dr = args.plan->inv_dr;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (t == 0)
+        for (int s = 0; s < 2 && s < n_my; ++s) {
+            mbar_arrive_expect_tx(&bar[s], tile_bytes);
+            tma_load_1d(rows + s * AT * ROW, args.rows + (size_t)(tile0 + s) * AT * ROW, tile_bytes, &bar[s]);
+        }
+    const int64_t jbase = (blockIdx.x * (int64_t)TPK_THREADS + t) * TPK_V;
+    float px[TPK_V], py[TPK_V], pz[TPK_V];
+    float pw[TPK_V], pnx[TPK_V], pny[TPK_V], pnz[TPK_V], pte[TPK_V], pe[TPK_V];
+#pragma unroll
+    for (int v = 0; v < TPK_V; ++v) {
+        const int64_t j = min(jbase + v, args.n - 1);
+        if (MODE == MODE_FILTER) {
+            px[v] = args.vox[j];
+            py[v] = args.vox[args.n + j];
+            pz[v] = args.vox[2 * args.n + j];
+            pw[v] = pnx[v] = pny[v] = pnz[v] = pte[v] = pe[v] = 0.0f;
+        } else {
+            const PtRec P = args.pts[j];
+            px[v] = P.a.x; py[v] = P.a.y; pz[v] = P.a.z; pw[v] = P.a.w;
+            pnx[v] = P.b.x; pny[v] = P.b.y; pnz[v] = P.b.z; pte[v] = P.b.w;
+            pe[v] = P.c.x;
+        }
+    }
+    constexpr int NACC = (MODE == MODE_FILTER) ? 2 : 6;
+    float hi[TPK_V][NACC], lo[TPK_V][NACC];
+#pragma unroll
+    for (int v = 0; v < TPK_V; ++v)
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) hi[v][k] = lo[v][k] = 0.0f;
+
+    for (int it = 0; it < n_my; ++it) {
+        const int buf = it & 1;
+        if (!mbar_wait(&bar[buf], (it >> 1) & 1)) atomicOr(abort_flag, 1);
+        __syncthreads();
+        if (*abort_flag) {
+            if (t == 0) {
+                atomicOr(args.err, 1);
+                mbar_drain2(bar, it, n_my);
+            }
+            return;
+        }
+        const float4* tile = rows + buf * AT * ROW;
+        float in[TPK_V][NACC];
+#pragma unroll
+        for (int v = 0; v < TPK_V; ++v)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
+        for (int a = 0; a < AT; ++a) {
+            const float4 head = tile[a * ROW];
+            const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 1);
+            Range R[TPK_V];
+            float xs[TPK_V];
+#pragma unroll
+            for (int v = 0; v < TPK_V; ++v) {
+                R[v] = pair_range(px[v], py[v], pz[v], head.x, head.y, head.z);
+                xs[v] = __fmul_rn(__fadd_rn(__fsub_rn(R[v].rh, r_c), R[v].rl), inv_dr);
+            }
+            // Clenshaw: b_k = h_k + 2 x b_{k+1} - b_{k+2}, sum = h_0 + x b_1 - b_2 (both points packed)
+            const f2 X2 = pk2(2.0f * xs[0], 2.0f * xs[1]);
+            f2 b1r = 0ull, b1i = 0ull, b2r = 0ull, b2i = 0ull;
+            for (int k = K - 1; k >= 1; --k) {
+                const ulonglong2 h = hk[k];
+                const f2 nr = fma2(X2, b1r, sub2(h.x, b2r));
+                const f2 ni = fma2(X2, b1i, sub2(h.y, b2i));
+                b2r = b1r; b2i = b1i;
+                b1r = nr; b1i = ni;
+            }
+            float sr[TPK_V], si[TPK_V], b1rv[TPK_V], b1iv[TPK_V], b2rv[TPK_V], b2iv[TPK_V];
+            upk2(b1r, b1rv[0], b1rv[1]); upk2(b1i, b1iv[0], b1iv[1]);
+            upk2(b2r, b2rv[0], b2rv[1]); upk2(b2i, b2iv[0], b2iv[1]);
+            const float4 h0 = reinterpret_cast<const float4*>(hk)[0];
+#pragma unroll
+            for (int v = 0; v < TPK_V; ++v) {
+                sr[v] = h0.x + xs[v] * b1rv[v] - b2rv[v];
+                si[v] = h0.z + xs[v] * b1iv[v] - b2iv[v];
+            }
+#pragma unroll
+            for (int v = 0; v < TPK_V; ++v) {
+                const float fr = phase_frac(R[v].rh, R[v].rl, args.kh, args.kl);
+                float sn, cs;
+                __sincosf(6.28318530717958648f * fr, &sn, &cs);
+                if (MODE == MODE_FILTER) {
+                    // exp(+j 2 pi K0 r) * sum
+                    in[v][0] += cs * sr[v] - sn * si[v];
+                    in[v][1] += cs * si[v] + sn * sr[v];
+                } else {
+                    // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k)
+                    const float q = cs * sr[v] + sn * si[v];
+                    const float inv_r2 = R[v].rs * R[v].rs;
+                    const float gam = inv_r2 * kInv16Pi2;
+                    const float nd = pnx[v] * R[v].dx + pny[v] * R[v].dy + pnz[v] * R[v].dz;
+                    const float Dm = nd * nd * inv_r2 - pe[v];
+                    const float D = fmaxf(Dm, 0.0f);
+                    const float vv = pte[v] - head.w;
+                    const float tt = __saturatef(vv);
+                    const float gq = gam * q;
+                    in[v][0] += tt * tt * D * gq;
+                    if (vv >= 0.0f && vv <= 1.0f) in[v][1] += pw[v] * 2.0f * tt * D * gq;
+                    if (pe[v] > 0.0f && Dm > 0.0f) {
+                        const float kq = pw[v] * tt * tt * gq;
+                        const float c = nd * R[v].rs * (1.0f / kSqrt2);
+                        const float k1 = kq * 4.0f * c * R[v].rs;
+                        in[v][2] += k1 * R[v].dx;
+                        in[v][3] += k1 * R[v].dy;
+                        in[v][4] += k1 * R[v].dz;
+                        in[v][5] += kq * 4.0f * c * c * (1.0f / kSqrt2);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < TPK_V; ++v)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                const float y = __fsub_rn(in[v][k], lo[v][k]);
+                const float s = __fadd_rn(hi[v][k], y);
+                lo[v][k] = __fsub_rn(__fsub_rn(s, hi[v][k]), y);
+                hi[v][k] = s;
+            }
+        __syncthreads();
+        if (t == 0 && it + 2 < n_my) {
+            mbar_arrive_expect_tx(&bar[buf], tile_bytes);
+            tma_load_1d(rows + buf * AT * ROW, args.rows + (size_t)(tile0 + it + 2) * AT * ROW, tile_bytes,
+                        &bar[buf]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < TPK_V; ++v) {
+        const int64_t j = jbase + v;
+        if (j >= args.n) continue;
+        if (MODE == MODE_FILTER) {
+            float2* dst = reinterpret_cast<float2*>(args.partial) + (size_t)split * args.n + j;
+            *dst = make_float2(__fsub_rn(hi[v][0], lo[v][0]), __fsub_rn(hi[v][1], lo[v][1]));
+        } else {
+            float* dst = args.partial + (size_t)split * 6 * args.n + j;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = __fsub_rn(hi[v][k], lo[v][k]);
+        }
+    }
+}
+
+bool use_cheb(int n_f) { return n_f >= 64; }
+
+void k0_split(const geraf_band* band, float* kh, float* kl) {
+    const double K0 = 2.0 * band->f0 / kC;
+    *kh = (float)K0;
+    *kl = (float)(K0 - (double)*kh);
+}
+
 geraf_status check_launch(const char* what) { return cuda_status(cudaGetLastError(), what); }
 
 inline unsigned grid1d(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -653,67 +1223,124 @@ inline unsigned grid1d(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ============================================================== entry points
 
-geraf_status render_impl(const float* xyz, const float* grad, const float* w, const float* t_eff, int64_t n_pts,
-                         const float* ant_xyz, const float* c_ant, int32_t n_ant, const geraf_band* band,
-                         int32_t flags, void* ws, size_t* ws_bytes, float* s_out, cudaStream_t st) {
+namespace {
+
+struct ChebWs {
+    float* bbox;
+    ChebPlan* plan;
+    double2* C;
+    int n_bbox_blocks;
+};
+
+ChebWs take_cheb(WsCarver& c, int64_t n_bbox, int n_f) {
+    ChebWs w;
+    w.n_bbox_blocks = (int)std::min<int64_t>((n_bbox + 255) / 256, 1024);
+    w.bbox = c.take<float>((size_t)w.n_bbox_blocks * 6);
+    w.plan = c.take<ChebPlan>(1);
+    w.C = c.take<double2>((size_t)CH_KMAX * n_f);
+    return w;
+}
+
+void launch_cheb_plan(const ChebWs& w, const float* pts, int64_t n, const float* ant, int n_ant,
+                      const geraf_band* band, cudaStream_t st) {
+    bbox_partial_kernel<<<w.n_bbox_blocks, 256, 0, st>>>(pts, n, w.bbox);
+    cheb_plan_kernel<<<1, 256, 0, st>>>(w.bbox, w.n_bbox_blocks, ant, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
+                                        w.plan, w.C);
+}
+
+struct ChebBinsPlan {
+    int ant_blocks, n_tiles, splits, tiles_per_split;
+};
+
+ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant) {
+    ChebBinsPlan q;
+    q.ant_blocks = (n_ant + CH_THREADS - 1) / CH_THREADS;
+    q.n_tiles = (int)(n_pad / CH_TP);
+    const int64_t max_splits = std::max<int64_t>(1, (int64_t)(CH_PARTIAL_BYTES / ((size_t)n_ant * CH_KMAX * 8)));
+    const int64_t want = std::max<int64_t>(1, (4LL * 2 * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
+    int64_t sp = std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles);
+    q.tiles_per_split = (int)((q.n_tiles + sp - 1) / sp);
+    q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
+    return q;
+}
+
+template <bool kComplexAmp>
+geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_ant, int32_t n_ant,
+                          const geraf_band* band, int32_t flags, const float* xyz, const float* grad, const float* w,
+                          const float* t_eff, const float* vox, const float2* M, const float* dP, void* ws,
+                          size_t* ws_bytes, float* out, cudaStream_t st, const char* name) {
+    // render packs points xyz (weights w, t_eff, grad); the filter adjoint packs voxels vox (M, dP)
+    const float* positions = kComplexAmp ? vox : xyz;
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    ToBinsPlan p = plan_to_bins(n_pts, n_ant, bk.g);
+    const bool cheb = use_cheb(band->n_f);
+    const int64_t n_pad = cheb ? (n_pts + CH_TP - 1) / CH_TP * CH_TP : n_pts;
+    ToBinsPlan p = plan_to_bins(n_pad, n_ant, bk.g);
+    const int64_t n_rec = (int64_t)p.n_tiles * p.TP;
+    const int n_ant_rec = std::max(p.n_ant_pad, (n_ant + CH_THREADS - 1) / CH_THREADS * CH_THREADS);
+    ChebBinsPlan q{};
+    if (cheb) q = plan_cheb_bins(n_rec, n_ant);
     WsCarver c(ws);
-    PtRec* pts = c.take<PtRec>((size_t)p.n_tiles * p.TP);
-    float4* ant = c.take<float4>(p.n_ant_pad);
+    PtRec* pts = c.take<PtRec>((size_t)n_rec);
+    float4* ant = c.take<float4>(n_ant_rec);
     float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
+    ChebWs cw{};
+    float2* cpart = nullptr;
+    if (cheb) {
+        cw = take_cheb(c, n_pts, band->n_f);
+        cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
+    }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
-    if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "render: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", name, *ws_bytes, c.used);
     int* err = device_error_word();
-    const int64_t n_pad = (int64_t)p.n_tiles * p.TP;
-    pack_render_points<<<grid1d(n_pad, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pad,
-                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
-    pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, p.n_ant_pad, ant);
-    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk};
+    if (!kComplexAmp)
+        pack_render_points<<<grid1d(n_rec, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_rec,
+                                                               (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
+    else
+        pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts);
+    pack_antennas<<<grid1d(n_ant_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, n_ant_rec, ant);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    to_bins_kernel<false><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
+    const int* run_direct = nullptr;
+    if (cheb) {
+        launch_cheb_plan(cw, positions, n_pts, ant_xyz, n_ant, band, st);
+        float kh, kl;
+        k0_split(band, &kh, &kl);
+        ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, kh, kl, cpart, err};
+        cheb_bins_kernel<kComplexAmp><<<dim3(q.ant_blocks, q.splits), CH_THREADS, cheb_bins_smem(), st>>>(ca);
+        cheb_reconstruct_kernel<<<n_ant, 128, CH_KMAX * sizeof(double2), st>>>(cpart, q.splits, n_ant, band->n_f,
+                                                                               cw.plan, cw.C,
+                                                                               reinterpret_cast<float2*>(out));
+        run_direct = &cw.plan->use_direct;
+    }
+    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk, run_direct};
+    to_bins_kernel<kComplexAmp><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
     reduce_bins<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(part, p.splits, n_ant, p.n_ant_pad,
                                                                          band->n_f, 32 * p.G,
-                                                                         reinterpret_cast<float2*>(s_out));
-    return check_launch("render");
+                                                                         reinterpret_cast<float2*>(out), run_direct);
+    return check_launch(name);
+}
+
+}  // namespace
+
+geraf_status render_impl(const float* xyz, const float* grad, const float* w, const float* t_eff, int64_t n_pts,
+                         const float* ant_xyz, const float* c_ant, int32_t n_ant, const geraf_band* band,
+                         int32_t flags, void* ws, size_t* ws_bytes, float* s_out, cudaStream_t st) {
+    return to_bins_call<false>(n_pts, ant_xyz, c_ant, n_ant, band, flags, xyz, grad, w, t_eff, nullptr, nullptr,
+                               nullptr, ws, ws_bytes, s_out, st, "render");
 }
 
 geraf_status filter_backward_impl(const float* ant_xyz, int32_t n_ant, const geraf_band* band, const float* vox,
                                   int64_t n_vox, const float* M, const float* d_P, void* ws, size_t* ws_bytes,
                                   float* g_s, cudaStream_t st) {
-    BandK bk;
-    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    ToBinsPlan p = plan_to_bins(n_vox, n_ant, bk.g);
-    WsCarver c(ws);
-    PtRec* pts = c.take<PtRec>((size_t)p.n_tiles * p.TP);
-    float4* ant = c.take<float4>(p.n_ant_pad);
-    float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
-    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
-    if (*ws_bytes < c.used)
-        return fail(GERAF_ERR_WORKSPACE, "filter_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
-    int* err = device_error_word();
-    const int64_t n_pad = (int64_t)p.n_tiles * p.TP;
-    pack_filter_bwd_points<<<grid1d(n_pad, 256), 256, 0, st>>>(vox, reinterpret_cast<const float2*>(M), d_P,
-                                                               n_vox, n_pad, pts);
-    pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, nullptr, n_ant, p.n_ant_pad, ant);
-    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk};
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    to_bins_kernel<true><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
-    reduce_bins<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(part, p.splits, n_ant, p.n_ant_pad,
-                                                                         band->n_f, 32 * p.G,
-                                                                         reinterpret_cast<float2*>(g_s));
-    return check_launch("filter_backward");
+    return to_bins_call<true>(n_vox, ant_xyz, nullptr, n_ant, band, 0, nullptr, nullptr, nullptr, nullptr, vox,
+                              reinterpret_cast<const float2*>(M), d_P, ws, ws_bytes, g_s, st, "filter_backward");
 }
 
 geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, const geraf_band* band,
@@ -721,24 +1348,46 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
                          size_t* ws_bytes, float* P, float* M, double* loss, float* dloss_dP, cudaStream_t st) {
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    const bool cheb = use_cheb(band->n_f);
     ToPointsPlan p = plan_to_points(n_vox, n_ant, bk.g);
     WsCarver c(ws);
     float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
     float2* part = c.take<float2>((size_t)p.splits * n_vox);
     const int fin_blocks = (int)grid1d(n_vox, 256);
     double* loss_blocks = c.take<double>(fin_blocks);
+    ChebWs cw{};
+    float4* crows = nullptr;
+    if (cheb) {
+        cw = take_cheb(c, n_vox, band->n_f);
+        crows = c.take<float4>((size_t)p.n_ant_pad * (1 + CH_KMAX));
+    }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
     int* err = device_error_word();
-    pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s),
-                                                           n_ant, p.n_ant_pad, band->n_f, p.n_f_pad, rows);
-    ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split,
-                   reinterpret_cast<float*>(part), err, bk};
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
         attr_set = true;
     }
+    const int* run_direct = nullptr;
+    if (cheb) {
+        launch_cheb_plan(cw, vox, n_vox, ant_xyz, n_ant, band, st);
+        cheb_rows_kernel<<<p.n_ant_pad, 64, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
+                                                    p.n_ant_pad, band->n_f, cw.plan, cw.C, 1, 0, crows);
+        float kh, kl;
+        k0_split(band, &kh, &kl);
+        ChebPointsArgs ca{nullptr, vox, n_vox, crows, p.at, p.n_ant_tiles, p.tiles_per_split, cw.plan, kh, kl,
+                          reinterpret_cast<float*>(part), err};
+        const size_t smem = 32 + 2 * (size_t)p.at * (1 + CH_KMAX) * sizeof(float4);
+        cheb_points_kernel<MODE_FILTER><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
+        run_direct = &cw.plan->use_direct;
+    }
+    pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
+                                                   p.n_ant_pad, band->n_f, p.n_f_pad, rows);
+    ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split,
+                   reinterpret_cast<float*>(part), err, bk, run_direct};
     to_points_kernel<MODE_FILTER><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
     const bool want_loss = target != nullptr;
     filter_finalize<<<fin_blocks, 256, 0, st>>>(part, p.splits, n_vox, target, mask, P,
@@ -754,26 +1403,49 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
                                   size_t* ws_bytes, float* d_w, float* d_teff, float* d_grad, cudaStream_t st) {
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    const bool cheb = use_cheb(band->n_f);
     ToPointsPlan p = plan_to_points(n_pts, n_ant, bk.g);
     WsCarver c(ws);
     PtRec* pts = c.take<PtRec>((size_t)n_pts);
     float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
     float* part = c.take<float>((size_t)p.splits * 6 * n_pts);
+    ChebWs cw{};
+    float4* crows = nullptr;
+    if (cheb) {
+        cw = take_cheb(c, n_pts, band->n_f);
+        crows = c.take<float4>((size_t)p.n_ant_pad * (1 + CH_KMAX));
+    }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "render_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
     int* err = device_error_word();
     pack_render_points<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pts,
                                                            (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
-    pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s),
-                                                           n_ant, p.n_ant_pad, band->n_f, p.n_f_pad, rows);
-    ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split, part, err, bk};
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
         attr_set = true;
     }
+    const int* run_direct = nullptr;
+    if (cheb) {
+        launch_cheb_plan(cw, xyz, n_pts, ant_xyz, n_ant, band, st);
+        cheb_rows_kernel<<<p.n_ant_pad, 64, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
+                                                    p.n_ant_pad, band->n_f, cw.plan, cw.C, 0, 1, crows);
+        float kh, kl;
+        k0_split(band, &kh, &kl);
+        ChebPointsArgs ca{pts, nullptr, n_pts, crows, p.at, p.n_ant_tiles, p.tiles_per_split, cw.plan, kh, kl, part,
+                          err};
+        const size_t smem = 32 + 2 * (size_t)p.at * (1 + CH_KMAX) * sizeof(float4);
+        cheb_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
+        run_direct = &cw.plan->use_direct;
+    }
+    pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
+                                                   p.n_ant_pad, band->n_f, p.n_f_pad, rows);
+    ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split, part, err, bk,
+                   run_direct};
     to_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
     render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, d_w, d_teff, d_grad);
     return check_launch("render_backward");
@@ -845,7 +1517,7 @@ geraf_status render_noalloc_impl(const float* xyz, const float* grad, const floa
     pack_render_points<<<grid1d(n_pad, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pad,
                                                            (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
     pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, p.n_ant_pad, ant);
-    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk};
+    ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk, nullptr};
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -120,7 +120,8 @@ def test_blend_and_backward(G, oracle):
 @pytest.mark.parametrize("n_pts,n_ant_side,n_f,directional", [
     (5003, (10, 10), 45, True),       # G = 2 with a 13-bin tail; 100 antennas
     (777, (7, 5), 32, True),          # G = 1
-    (2049, (9, 9), 128, False),       # G = 4, isotropic
+    (2049, (9, 9), 128, False),       # Chebyshev moments, isotropic
+    (4099, (12, 11), 256, True),      # Chebyshev: 132 antennas over two 128-antenna CTAs, ragged point tile
     (1, (3, 1), 7, True),             # single point, tiny band
 ])
 def test_render(G, oracle, n_pts, n_ant_side, n_f, directional):
@@ -135,13 +136,61 @@ def test_render(G, oracle, n_pts, n_ant_side, n_f, directional):
     assert rel_l2(host(s), want) < TOL
 
 
-def test_render_backward(G, oracle):
+# Range spreads that put the Chebyshev order on either side of its 64-term cap
+# (the direct recurrence kernels run above it; the choice is made on the device):
+# 0.29 m spread -> about 40 terms over 4 GHz; 1.2 m spread -> above 64 terms.
+SPREADS = [((0.0, 0.0, 0.30), 0.12), ((0.0, 0.0, 0.60), 0.50)]
+
+
+@pytest.mark.parametrize("centre,half", SPREADS)
+def test_render_range_spread(G, oracle, centre, half):
+    rng = np.random.default_rng(11)
+    n_pts, n_f = 3000, 128
+    xyz, grad, w, t_eff = _scene_points(rng, n_pts, centre, half)
+    ant = gi.antenna_array(10, 9, 0.002)
+    c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
+    b = gi.band(77e9, 81e9, n_f)
+    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), _band(G, b), True)
+    G.geraf_poll_device_error()
+    want = oracle.render(xyz, grad, w, t_eff, ant, c_ant, b)
+    assert rel_l2(host(s), want) < TOL
+    g = gi.complex_normal(rng, (ant.shape[1], n_f)).astype(np.complex64)
+    d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant),
+                                            _band(G, b), torch.as_tensor(g, device="cuda"))
+    G.geraf_poll_device_error()
+    ow, ot, og = oracle.render_backward(xyz, grad, w, t_eff, ant, c_ant, b, g)
+    assert rel_l2(host(d_w), ow) < TOL
+    assert rel_l2(host(d_t), ot) < TOL
+    assert rel_l2(host(d_g), og) < 3 * TOL
+
+
+@pytest.mark.parametrize("centre,half", SPREADS)
+def test_filter_range_spread(G, oracle, centre, half):
+    rng = np.random.default_rng(12)
+    n_vox, n_f = 2500, 128
+    ant = gi.antenna_array(9, 10, 0.002)
+    s = gi.complex_normal(rng, (ant.shape[1], n_f)).astype(np.complex64)
+    vox = (np.array(centre)[:, None] + rng.uniform(-half, half, (3, n_vox))).astype(np.float32)
+    b = gi.band(77e9, 81e9, n_f)
+    P, M, _, _ = G.geraf_filter(torch.as_tensor(s, device="cuda"), cu(ant), _band(G, b), cu(vox))
+    G.geraf_poll_device_error()
+    oM, oP = oracle.filter_forward(s, ant, vox, b)
+    assert rel_l2(host(M), oM) < TOL
+    d_P = rng.standard_normal(n_vox).astype(np.float32)
+    g = G.geraf_filter_backward(cu(ant), _band(G, b), cu(vox), M, cu(d_P))
+    G.geraf_poll_device_error()
+    og = oracle.filter_backward(host(M), d_P, ant, vox, b)
+    assert rel_l2(host(g), og) < TOL
+
+
+@pytest.mark.parametrize("n_f", [40, 70, 256])
+def test_render_backward(G, oracle, n_f):
     rng = np.random.default_rng(5)
     n_pts = 1203
     xyz, grad, w, t_eff = _scene_points(rng, n_pts)
     ant = gi.antenna_array(7, 9, 0.002)
     c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
-    b = gi.band(77e9, 81e9, 70)
+    b = gi.band(77e9, 81e9, n_f)
     g = gi.complex_normal(rng, (ant.shape[1], b.n_f)).astype(np.complex64)
     d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant),
                                             _band(G, b), torch.as_tensor(g, device="cuda"))
@@ -153,7 +202,8 @@ def test_render_backward(G, oracle):
 
 
 # ------------------------------------------------------------------- filter
-@pytest.mark.parametrize("n_vox,n_ant_side,n_f", [(3001, (6, 7), 40), (256, (16, 16), 32), (1, (2, 2), 3)])
+@pytest.mark.parametrize("n_vox,n_ant_side,n_f", [(3001, (6, 7), 40), (256, (16, 16), 32), (1, (2, 2), 3),
+                                                  (3001, (6, 7), 64), (2000, (12, 11), 200)])
 def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f):
     rng = np.random.default_rng(n_vox)
     ant = gi.antenna_array(*n_ant_side, 0.002)
