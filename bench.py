@@ -28,8 +28,17 @@ if ROOT not in sys.path:
 METRIC = "point·antenna·freq phasor terms/s fwd+adj; train-step ms at ≤2e-3 rel err"
 WORKLOAD = ("64x64 array @2mm, 128 freqs 77-81 GHz, 128^3 stratified samples, MLP 4x128 fp32, "
             "64^3 heatmap, forward + adjoint of every step")
-FLOPS_PER_TERM = 10          # complex rotation (4 FP32-pipe instr, 6 flops) + accumulate (2 FMA, 4 flops)
-INSTR_PER_TERM = 6
+# Algorithmic FP32 flops (FMA = 2) of the phasor sums.
+# Per-bin recurrence, per (point, antenna, bin) term: real amplitude times the
+# unit phasor into a complex sum (2 FMA) and the angle-addition step (2 MUL +
+# 2 FMA) = 10 flops (render, filter adjoint); complex coefficients summed by
+# Horner's rule over a 32-bin block = 4 FMA = 8 flops (filter, render adjoint).
+# Chebyshev form, per (point, antenna) pair and order k: the three-term
+# recurrence of T_k (1 FMA) and the complex moment or series sum (2 FMA) =
+# 6 flops per order.
+FLOPS_PER_TERM = {"render": 10, "filter_backward": 10, "filter": 8, "render_backward": 8}
+CHEB_FLOPS_PER_ORDER = 6
+PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
 
 
 def _env_int(k, d):
@@ -318,6 +327,26 @@ def mlp_bench(n_pts=1 << 21, reps=5):
     print(json.dumps(out), flush=True)
 
 
+def mlp_backward_macs(spec) -> int:
+    """MACs per point of the MLP adjoint: weight gradients of every layer and
+    input adjoints of the hidden layers above the first, over the 4 streams
+    (value and 3 tangents), plus the head."""
+    w = 128
+    weight = 4 * w * (spec.in_dim + (spec.n_hidden - 1) * w)
+    inputs = 4 * w * w * (spec.n_hidden - 1)
+    head = 4 * w * 2 * 2
+    return weight + inputs + head
+
+
+def call_flops(name, pairs, n_f, order, mlp_macs=0, n_mlp_pts=0):
+    """Algorithmic FP32 flops of one call (see FLOPS_PER_TERM)."""
+    if name == "fields_backward":
+        return 2 * mlp_macs * n_mlp_pts
+    if order > 0:
+        return pairs * order * CHEB_FLOPS_PER_ORDER
+    return pairs * n_f * FLOPS_PER_TERM[name]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,15 +466,46 @@ def main():
     h2d = (h_params.numel() + h_target.numel() + h_ant.numel()) * 4
     d2h = 8 + h_dp.numel() * 4 + 8
 
+    # the same step with the per-bin recurrence forced (for comparison; untimed in `value`)
+    import dataclasses
+    b0 = geo.band
+    geo_rec = dataclasses.replace(geo, band=G.Band(b0.f0, b0.df, b0.n_f, G.PHASOR_RECURRENCE))
+    PL.forward_backward(geo_rec, field, target, seed, step_id)
+    rec_steps = 2
+    ev_rec = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+              for _ in range(rec_steps)]
+    torch.cuda.synchronize()
+    for k in range(rec_steps):
+        PL.forward_backward(geo_rec, field, target, seed, step_id + k, timers=ev_rec[k])
+    torch.cuda.synchronize()
+    per_kernel_rec = {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev_rec) / rec_steps for nm in names}
+    xyz_o, _ = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
+    orders = {"points": G.geraf_chebyshev_order(xyz_o, geo.ant, geo.band),
+              "voxels": G.geraf_chebyshev_order(geo.vox, geo.ant, geo.band)}
+    del xyz_o
+
     if rank == 0:
         peaks = measured_peaks()
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        dom = max(["render", "render_backward"], key=lambda k: per_kernel[k])
-        n_units = n_pts * geo.ant.shape[1] * geo.band.n_f
-        achieved = n_units * FLOPS_PER_TERM / (per_kernel[dom] * 1e-3) / 1e12
-        peak = sm_count * 128 * max_mhz * 1e6 / INSTR_PER_TERM * FLOPS_PER_TERM / 1e12
-        launches = PL.launches_per_step(field) * args.steps
+        fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12       # FMA = 2 flops per lane per clock
+        n_ant = int(geo.ant.shape[1])
+        n_vox = int(geo.vox.shape[1])
+        pairs = {"render": n_pts * n_ant, "render_backward": n_pts * n_ant,
+                 "filter": n_vox * n_ant, "filter_backward": n_vox * n_ant, "fields_backward": n_pts}
+        order_of = {"render": orders["points"], "render_backward": orders["points"],
+                    "filter": orders["voxels"], "filter_backward": orders["voxels"], "fields_backward": 0}
+        macs = mlp_backward_macs(spec)
+
+        def roof(nm, ms, order):
+            fl = call_flops(nm, pairs[nm], geo.band.n_f, order, macs, n_pts)
+            return {"ms": round(ms, 3), "tflops": fl / (ms * 1e-3) / 1e12,
+                    "frac": fl / (ms * 1e-3) / 1e12 / fp32_peak}
+
+        per_call_roof = {nm: roof(nm, per_kernel[nm], order_of[nm]) for nm in names}
+        rec_roof = {nm: roof(nm, per_kernel_rec[nm], 0) for nm in PHASOR_CALLS}
+        dom = max(names, key=lambda k: per_kernel[k])
+        launches = PL.launches_per_step(field, geo.band) * args.steps
         cpu = None
         if not args.no_cpu_baseline:
             # intermediate arrays of one step for the oracle sample
@@ -466,10 +526,18 @@ def main():
                        "l2": "inputs larger than L2 (per-step MLP activations ~17 GB)",
                        "parallelism": f"replicas x{world}"},
             "per_call_ms": {k: round(v, 3) for k, v in per_kernel.items()},
-            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz / "
-                                       f"{INSTR_PER_TERM} instr per term x {FLOPS_PER_TERM} flops per term"},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": per_call_roof[dom]["tflops"],
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": per_call_roof[dom]["frac"], "traffic": None,
+                         "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz",
+                         "work_basis": ("Chebyshev phasor sums: pairs x order x 6 flops; per-bin recurrence: "
+                                        "terms x 10 (render, filter adjoint) or 8 (filter, render adjoint) flops; "
+                                        f"MLP adjoint: 2 x {macs} MAC per point"),
+                         "calls": per_call_roof},
+            "phasor_method": {"chebyshev_order": orders,
+                              "recurrence_per_call_ms": {k: round(per_kernel_rec[k], 3) for k in PHASOR_CALLS},
+                              "recurrence_roofline": rec_roof,
+                              "recurrence_terms_per_s": 2 * (n_pts + n_vox) * n_ant * geo.band.n_f
+                              / (sum(per_kernel_rec[k] for k in PHASOR_CALLS) * 1e-3)},
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

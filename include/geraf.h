@@ -59,12 +59,27 @@ typedef struct {
 
 /* Stepped frequencies f_n = f0 + n * df, n = 0 .. n_f-1 (section 3, Eq. fmcw:
  * FMCW sample n of a chirp with slope k is the frequency f + k t_n). FP64.
- * 1 <= n_f <= 1024, f0 > 0, df >= 0. */
+ * 1 <= n_f <= 1024, f0 > 0, df >= 0.
+ * `method` picks how the four phasor sums (render, filter and their
+ * adjoints) step across the bins; all give the same sums within FP32
+ * rounding:
+ *   GERAF_PHASOR_RECURRENCE: exact phasor per bin by angle-addition
+ *     recurrence, re-seeded from a sincos every 32 bins;
+ *   GERAF_PHASOR_CHEBYSHEV: the bin phase exp(-j 2 pi n df 2r/c) expanded in
+ *     Chebyshev polynomials of the range over the call's range interval
+ *     (Jacobi-Anger, terms kept until the Bessel tail is below 1e-9), so the
+ *     work per (point, antenna) pair follows the order K instead of n_f;
+ *     when K would exceed 64 the recurrence runs instead (decided on the
+ *     device; geraf_chebyshev_order reports the choice);
+ *   GERAF_PHASOR_AUTO (0): Chebyshev for n_f >= 64, recurrence below. */
 typedef struct {
     double f0;
     double df;
     int32_t n_f;
+    int32_t method;
 } geraf_band;
+
+enum { GERAF_PHASOR_AUTO = 0, GERAF_PHASOR_RECURRENCE = 1, GERAF_PHASOR_CHEBYSHEV = 2 };
 
 enum { GERAF_SAMPLE_UNIFORM = 0, GERAF_SAMPLE_STRATIFIED = 1 };
 enum { GERAF_FIELD_ANALYTIC = 0, GERAF_FIELD_MLP = 1 };
@@ -263,6 +278,20 @@ geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const ge
                                    const float* vox_xyz, int64_t n_vox, const float* M,
                                    const float* d_P, void* ws, size_t* ws_bytes,
                                    float* g_s, void* stream);
+
+/*
+ * geraf_chebyshev_order — the Chebyshev order K that the phasor sums use for
+ * points (or voxels) xyz [3][n] against ant_xyz [3][n_ant] over `band`
+ * (band->method honoured): *order = K (2..64) when the Chebyshev form runs,
+ * 0 when the recurrence runs (method RECURRENCE, AUTO with n_f < 64, or an
+ * order above 64). Runs the same device-side plan as the sums (range bound
+ * from the points' bounding box and the antennas, Bessel tail below 1e-9),
+ * then waits for the stream: synchronous. The paper has no counterpart; this
+ * reports the cost model of a call. ws: ws == NULL queries *ws_bytes.
+ */
+geraf_status geraf_chebyshev_order(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
+                                   const geraf_band* band, void* ws, size_t* ws_bytes, int32_t* order,
+                                   void* stream);
 
 /*
  * Learned proposal sampler (the paper is silent on it; it cuts the number of

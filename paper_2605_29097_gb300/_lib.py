@@ -22,7 +22,7 @@ class GerafGrid(ctypes.Structure):
 
 
 class GerafBand(ctypes.Structure):
-    _fields_ = [("f0", ctypes.c_double), ("df", ctypes.c_double), ("n_f", ctypes.c_int32)]
+    _fields_ = [("f0", ctypes.c_double), ("df", ctypes.c_double), ("n_f", ctypes.c_int32), ("method", ctypes.c_int32)]
 
 
 class GerafFieldDesc(ctypes.Structure):
@@ -53,6 +53,7 @@ SIGNATURES = {
                               vp, vp, vp, vp],
     "geraf_filter": [vp, vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp, vp, vp, vp],
     "geraf_filter_backward": [vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp],
+    "geraf_chebyshev_order": [vp, i64, vp, i32, ctypes.POINTER(GerafBand), vp, szp, ctypes.POINTER(i32), vp],
     "geraf_proposal_saved_bytes": [ctypes.POINTER(GerafProposal), szp],
     "geraf_proposal_density": [ctypes.POINTER(GerafProposal), vp, vp, vp, sz, vp],
     "geraf_sample_proposal": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, u64, u64, vp, vp, vp, vp],

@@ -29,6 +29,8 @@ geraf_status filter_impl(const float*, const float*, int32_t, const geraf_band*,
                          const float*, const float*, void*, size_t*, float*, float*, double*, float*, cudaStream_t);
 geraf_status filter_backward_impl(const float*, int32_t, const geraf_band*, const float*, int64_t, const float*,
                                   const float*, void*, size_t*, float*, cudaStream_t);
+geraf_status chebyshev_order_impl(const float*, int64_t, const float*, int32_t, const geraf_band*, void*, size_t*,
+                                  int32_t*, cudaStream_t);
 geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
 geraf_status proposal_saved_bytes(const geraf_proposal*, size_t*);
 geraf_status proposal_density_impl(const geraf_proposal*, float*, float*, void*, size_t, cudaStream_t);
@@ -100,6 +102,10 @@ int device_sm_count() {
 bool make_band_k(const geraf_band* band, BandK* out) {
     if (!band || band->n_f < 1 || !(band->f0 > 0.0) || !(band->df >= 0.0)) {
         set_error("band: need n_f >= 1, f0 > 0, df >= 0");
+        return false;
+    }
+    if (band->method < GERAF_PHASOR_AUTO || band->method > GERAF_PHASOR_CHEBYSHEV) {
+        set_error("band: unknown method %d", band->method);
         return false;
     }
     const int g = (band->n_f + kBinsPerBlock - 1) / kBinsPerBlock;
@@ -292,6 +298,18 @@ geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const ge
     REQUIRE(band, "filter_backward: band must not be NULL");
     if (ws) REQUIRE(ant_xyz && vox_xyz && M && d_P && g_s, "filter_backward: null input or output");
     return filter_backward_impl(ant_xyz, n_ant, band, vox_xyz, n_vox, M, d_P, ws, ws_bytes, g_s, S(stream));
+}
+
+geraf_status geraf_chebyshev_order(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
+                                   const geraf_band* band, void* ws, size_t* ws_bytes, int32_t* order,
+                                   void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n >= 1 && n_ant >= 1, "chebyshev_order: need n >= 1 and n_ant >= 1");
+    REQUIRE(n < (1ll << 31), "chebyshev_order: n must be below 2^31");
+    REQUIRE(band, "chebyshev_order: band must not be NULL");
+    if (ws) REQUIRE(xyz && ant_xyz && order, "chebyshev_order: null input or output");
+    return chebyshev_order_impl(xyz, n, ant_xyz, n_ant, band, ws, ws_bytes, order, S(stream));
 }
 
 geraf_status geraf_proposal_saved_bytes(const geraf_proposal* p, size_t* bytes) {

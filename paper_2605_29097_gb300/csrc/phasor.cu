@@ -110,7 +110,8 @@ __global__ void pack_antennas(const float* __restrict__ ant, const float* __rest
 // and (s_im, s_im) of the two-lane Horner sums.
 __global__ void pack_antenna_rows(const float* __restrict__ ant, const float* __restrict__ c_ant,
                                   const float2* __restrict__ sig, int n_ant, int n_ant_pad, int n_f,
-                                  int n_f_pad, float4* __restrict__ out) {
+                                  int n_f_pad, float4* __restrict__ out, const int* run_if = nullptr) {
+    if (run_if && *run_if == 0) return;
     int i = blockIdx.x;
     if (i >= n_ant_pad) return;
     float4* row = out + (size_t)i * (1 + n_f_pad);
@@ -669,7 +670,7 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
 // over a 15 cm range spread, independent of the number of bins):
 //   to bins:   s(i, n) = sum_k C_k(n) M_k(i),  M_k(i) = sum_j A'_ij T_k(x_ij)
 //   to points: sum_n s(i, n) exp(+j ...) = exp(+j 2 pi K0 r) sum_k T_k(x) S_k(i),
-//              evaluated per pair by Clenshaw's recurrence.
+//              evaluated per pair with T_k from the three-term recurrence.
 // C_k(n) = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n) is computed on the device
 // (Miller's backward recurrence in FP64) from a range bound of the call's
 // points and antennas, so the call stays asynchronous. If K would exceed
@@ -993,7 +994,7 @@ __global__ void cheb_reconstruct_kernel(const float2* __restrict__ partial, int 
     }
 }
 
-// antenna rows for the Clenshaw kernels: head (x, y, z, c) + CH_KMAX float4
+// antenna rows for the Chebyshev point kernels: head (x, y, z, c) + CH_KMAX float4
 // (h_re, h_re, h_im, h_im) with h_k = sum_n sig(n) * (conj ? conj(C_k(n)) : C_k(n))
 // and sig = (conj_sig ? conj(v) : v)
 __global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __restrict__ c_ant,
@@ -1039,8 +1040,8 @@ struct ChebPointsArgs {
     int* err;
 };
 
-// thread = 2 points (lanes of the packed Clenshaw sums)
-static_assert(TPK_V == 2, "the packed Clenshaw sums carry two points per thread");
+// thread = 2 points (the two lanes of the packed Chebyshev sums)
+static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread");
 
 template <int MODE>
 __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPointsArgs args) {
@@ -1123,25 +1124,31 @@ __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPoin
                 R[v] = pair_range(px[v], py[v], pz[v], head.x, head.y, head.z);
                 xs[v] = __fmul_rn(__fadd_rn(__fsub_rn(R[v].rh, r_c), R[v].rl), inv_dr);
             }
-            // Clenshaw: b_k = h_k + 2 x b_{k+1} - b_{k+2}, sum = h_0 + x b_1 - b_2 (both points packed)
-            const f2 X2 = pk2(2.0f * xs[0], 2.0f * xs[1]);
-            f2 b1r = 0ull, b1i = 0ull, b2r = 0ull, b2i = 0ull;
-            for (int k = K - 1; k >= 1; --k) {
+            // sum_k h_k T_k(x): T_k by the forward three-term recurrence (one
+            // FMA per point), the products accumulated for both points at
+            // once in the two lanes of packed FMAs
+            const ulonglong2 h0u = hk[0], h1u = hk[1];
+            float ta0 = 1.0f, tb0 = 1.0f, ta1 = xs[0], tb1 = xs[1];
+            const float x2a = 2.0f * xs[0], x2b = 2.0f * xs[1];
+            f2 Sr = h0u.x, Si = h0u.y;                       // T_0 = 1
+            {
+                const f2 T1 = pk2(ta1, tb1);
+                Sr = fma2(T1, h1u.x, Sr);
+                Si = fma2(T1, h1u.y, Si);
+            }
+#pragma unroll 4
+            for (int k = 2; k < K; ++k) {
+                const float ta2 = fmaf(x2a, ta1, -ta0), tb2 = fmaf(x2b, tb1, -tb0);
+                ta0 = ta1; tb0 = tb1;
+                ta1 = ta2; tb1 = tb2;
                 const ulonglong2 h = hk[k];
-                const f2 nr = fma2(X2, b1r, sub2(h.x, b2r));
-                const f2 ni = fma2(X2, b1i, sub2(h.y, b2i));
-                b2r = b1r; b2i = b1i;
-                b1r = nr; b1i = ni;
+                const f2 Tk = pk2(ta2, tb2);
+                Sr = fma2(Tk, h.x, Sr);
+                Si = fma2(Tk, h.y, Si);
             }
-            float sr[TPK_V], si[TPK_V], b1rv[TPK_V], b1iv[TPK_V], b2rv[TPK_V], b2iv[TPK_V];
-            upk2(b1r, b1rv[0], b1rv[1]); upk2(b1i, b1iv[0], b1iv[1]);
-            upk2(b2r, b2rv[0], b2rv[1]); upk2(b2i, b2iv[0], b2iv[1]);
-            const float4 h0 = reinterpret_cast<const float4*>(hk)[0];
-#pragma unroll
-            for (int v = 0; v < TPK_V; ++v) {
-                sr[v] = h0.x + xs[v] * b1rv[v] - b2rv[v];
-                si[v] = h0.z + xs[v] * b1iv[v] - b2iv[v];
-            }
+            float sr[TPK_V], si[TPK_V];
+            upk2(Sr, sr[0], sr[1]);
+            upk2(Si, si[0], si[1]);
 #pragma unroll
             for (int v = 0; v < TPK_V; ++v) {
                 const float fr = phase_frac(R[v].rh, R[v].rl, args.kh, args.kl);
@@ -1207,7 +1214,11 @@ __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPoin
     }
 }
 
-bool use_cheb(int n_f) { return n_f >= 64; }
+bool use_cheb(const geraf_band* band) {
+    if (band->method == GERAF_PHASOR_RECURRENCE) return false;
+    if (band->method == GERAF_PHASOR_CHEBYSHEV) return true;
+    return band->n_f >= 64;
+}
 
 void k0_split(const geraf_band* band, float* kh, float* kl) {
     const double K0 = 2.0 * band->f0 / kC;
@@ -1273,7 +1284,7 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     const float* positions = kComplexAmp ? vox : xyz;
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    const bool cheb = use_cheb(band->n_f);
+    const bool cheb = use_cheb(band);
     const int64_t n_pad = cheb ? (n_pts + CH_TP - 1) / CH_TP * CH_TP : n_pts;
     ToBinsPlan p = plan_to_bins(n_pad, n_ant, bk.g);
     const int64_t n_rec = (int64_t)p.n_tiles * p.TP;
@@ -1348,7 +1359,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
                          size_t* ws_bytes, float* P, float* M, double* loss, float* dloss_dP, cudaStream_t st) {
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    const bool cheb = use_cheb(band->n_f);
+    const bool cheb = use_cheb(band);
     ToPointsPlan p = plan_to_points(n_vox, n_ant, bk.g);
     WsCarver c(ws);
     float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
@@ -1385,7 +1396,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
         run_direct = &cw.plan->use_direct;
     }
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
-                                                   p.n_ant_pad, band->n_f, p.n_f_pad, rows);
+                                                   p.n_ant_pad, band->n_f, p.n_f_pad, rows, run_direct);
     ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split,
                    reinterpret_cast<float*>(part), err, bk, run_direct};
     to_points_kernel<MODE_FILTER><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
@@ -1403,7 +1414,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
                                   size_t* ws_bytes, float* d_w, float* d_teff, float* d_grad, cudaStream_t st) {
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    const bool cheb = use_cheb(band->n_f);
+    const bool cheb = use_cheb(band);
     ToPointsPlan p = plan_to_points(n_pts, n_ant, bk.g);
     WsCarver c(ws);
     PtRec* pts = c.take<PtRec>((size_t)n_pts);
@@ -1443,12 +1454,37 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
         run_direct = &cw.plan->use_direct;
     }
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
-                                                   p.n_ant_pad, band->n_f, p.n_f_pad, rows);
+                                                   p.n_ant_pad, band->n_f, p.n_f_pad, rows, run_direct);
     ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split, part, err, bk,
                    run_direct};
     to_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
     render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, d_w, d_teff, d_grad);
     return check_launch("render_backward");
+}
+
+geraf_status chebyshev_order_impl(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
+                                  const geraf_band* band, void* ws, size_t* ws_bytes, int32_t* order,
+                                  cudaStream_t st) {
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    WsCarver c(ws);
+    ChebWs cw = take_cheb(c, n, band->n_f);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used)
+        return fail(GERAF_ERR_WORKSPACE, "chebyshev_order: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    if (!use_cheb(band)) {
+        *order = 0;
+        return GERAF_OK;
+    }
+    launch_cheb_plan(cw, xyz, n, ant_xyz, n_ant, band, st);
+    geraf_status s = check_launch("chebyshev_order");
+    if (s != GERAF_OK) return s;
+    ChebPlan h;
+    cudaError_t e = cudaMemcpyAsync(&h, cw.plan, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "chebyshev_order: read back");
+    *order = h.use_direct ? 0 : h.K;
+    return GERAF_OK;
 }
 
 }  // namespace geraf

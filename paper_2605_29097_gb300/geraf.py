@@ -18,6 +18,7 @@ SAMPLE_UNIFORM, SAMPLE_STRATIFIED = 0, 1
 FIELD_ANALYTIC, FIELD_MLP = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 RENDER_DIRECTIONAL = 1
+PHASOR_AUTO, PHASOR_RECURRENCE, PHASOR_CHEBYSHEV = 0, 1, 2
 
 
 def _p(t: Optional[torch.Tensor]):
@@ -66,9 +67,10 @@ class Band:
     f0: float
     df: float
     n_f: int
+    method: int = 0          # PHASOR_AUTO / PHASOR_RECURRENCE / PHASOR_CHEBYSHEV
 
     def c(self):
-        return GerafBand(float(self.f0), float(self.df), int(self.n_f))
+        return GerafBand(float(self.f0), float(self.df), int(self.n_f), int(self.method))
 
 
 def make_grid(lo: Sequence[float], pitch: Sequence[float], n: Sequence[int], aperture_z: float = 0.0) -> GerafGrid:
@@ -283,6 +285,21 @@ def geraf_filter_backward(ant, band: Band, vox, M, d_P):
     ws, wsz = _workspace(args, vox.device)
     check(args(_p(ws), ctypes.byref(wsz)))
     return torch.view_as_complex(out)
+
+
+def geraf_chebyshev_order(xyz, ant, band: Band) -> int:
+    """Chebyshev order the phasor sums use for these points and antennas
+    (0: the per-bin recurrence runs). Synchronous."""
+    _req(xyz, "xyz")
+    _req(ant, "ant")
+    cb = band.c()
+    order = ctypes.c_int32(-1)
+    L = _lib.lib()
+    args = lambda wsp, b: L.geraf_chebyshev_order(_p(xyz), xyz.shape[-1], _p(ant), ant.shape[-1], ctypes.byref(cb),
+                                                  wsp, b, ctypes.byref(order), _stream())
+    ws, wsz = _workspace(args, xyz.device)
+    check(args(_p(ws), ctypes.byref(wsz)))
+    return int(order.value)
 
 
 class Proposal:

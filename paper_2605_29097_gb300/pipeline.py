@@ -16,6 +16,16 @@ from . import geraf as G
 # kernel launches made by one call of each entry point (for launch accounting)
 LAUNCHES = {"sample": 1, "fields": 1, "blend": 2, "render": 4, "filter": 4, "filter_backward": 4,
             "render_backward": 4, "blend_backward": 2}
+# with the Chebyshev form each phasor call adds the range bound, the plan and
+# the moment kernels; the recurrence kernels are still launched and return at
+# once unless the device-side plan falls back to them
+LAUNCHES_CHEBYSHEV = {"render": 8, "filter": 8, "filter_backward": 8, "render_backward": 8}
+
+
+def uses_chebyshev(band) -> bool:
+    if band.method == G.PHASOR_RECURRENCE:
+        return False
+    return band.method == G.PHASOR_CHEBYSHEV or band.n_f >= 64
 
 
 def fields_backward_launches(n_hidden: int) -> int:
@@ -115,9 +125,10 @@ def forward_backward(geo: Geometry, field, target: torch.Tensor, seed: int, step
     return StepResult(loss, d_params, d_sc, P)
 
 
-def launches_per_step(field) -> int:
-    n = LAUNCHES["sample"] + 3 * LAUNCHES["fields"] + LAUNCHES["blend"] + LAUNCHES["render"]
-    n += LAUNCHES["filter"] + LAUNCHES["filter_backward"] + LAUNCHES["render_backward"] + LAUNCHES["blend_backward"]
+def launches_per_step(field, band) -> int:
+    ph = LAUNCHES_CHEBYSHEV if uses_chebyshev(band) else LAUNCHES
+    n = LAUNCHES["sample"] + 3 * LAUNCHES["fields"] + LAUNCHES["blend"] + LAUNCHES["blend_backward"]
+    n += ph["render"] + ph["filter"] + ph["filter_backward"] + ph["render_backward"]
     if isinstance(field, G.MLPField):
         n += fields_backward_launches(field.n_hidden)
     return n

@@ -50,4 +50,21 @@ def test_argument_errors_return_status_without_device(libgeraf):
     st = libgeraf.geraf_render(None, None, None, None, 1000, None, None, 64, ctypes.byref(bad), 1, None,
                                ctypes.byref(n), None, None)
     assert st == 1
+    # unknown phasor method
+    bad = _lib.GerafBand(77e9, 1e8, 32, 7)
+    st = libgeraf.geraf_render(None, None, None, None, 1000, None, None, 64, ctypes.byref(bad), 1, None,
+                               ctypes.byref(n), None, None)
+    assert st == 1 and b"method" in libgeraf.geraf_last_error_string()
+    # the Chebyshev form's workspace (moment partials, coefficient table) is part of the size query
+    cheb = _lib.GerafBand(77e9, 1e8, 128, 2)
+    rec = _lib.GerafBand(77e9, 1e8, 128, 1)
+    n_rec = ctypes.c_size_t(0)
+    assert libgeraf.geraf_render(None, None, None, None, 1000, None, None, 64, ctypes.byref(cheb), 1, None,
+                                 ctypes.byref(n), None, None) == 0
+    assert libgeraf.geraf_render(None, None, None, None, 1000, None, None, 64, ctypes.byref(rec), 1, None,
+                                 ctypes.byref(n_rec), None, None) == 0
+    assert n.value > n_rec.value
+    order = ctypes.c_int32(-1)
+    assert libgeraf.geraf_chebyshev_order(None, 100, None, 4, ctypes.byref(cheb), None, ctypes.byref(n),
+                                          ctypes.byref(order), None) == 0 and n.value > 0
     assert libgeraf.geraf_version() >= 1

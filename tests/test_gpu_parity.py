@@ -42,8 +42,12 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def _band(G, b):
-    return G.Band(b.f0, b.df, b.n_f)
+def _band(G, b, method=0):
+    return G.Band(b.f0, b.df, b.n_f, method)
+
+
+# both ways of stepping across the bins, forced (the default picks by n_f)
+METHODS = [pytest.param(1, id="recurrence"), pytest.param(2, id="chebyshev")]
 
 
 def _scene_points(rng, n, centre=(0.0, 0.0, 0.15), half=0.05):
@@ -124,13 +128,14 @@ def test_blend_and_backward(G, oracle):
     (4099, (12, 11), 256, True),      # Chebyshev: 132 antennas over two 128-antenna CTAs, ragged point tile
     (1, (3, 1), 7, True),             # single point, tiny band
 ])
-def test_render(G, oracle, n_pts, n_ant_side, n_f, directional):
+@pytest.mark.parametrize("method", METHODS)
+def test_render(G, oracle, n_pts, n_ant_side, n_f, directional, method):
     rng = np.random.default_rng(n_pts)
     xyz, grad, w, t_eff = _scene_points(rng, n_pts)
     ant = gi.antenna_array(*n_ant_side, 0.002)
     c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
     b = gi.band(77e9, 81e9, n_f)
-    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), _band(G, b), directional)
+    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), _band(G, b, method), directional)
     G.geraf_poll_device_error()
     want = oracle.render(xyz, grad, w, t_eff, ant, c_ant, b, use_dir=directional)
     assert rel_l2(host(s), want) < TOL
@@ -184,7 +189,8 @@ def test_filter_range_spread(G, oracle, centre, half):
 
 
 @pytest.mark.parametrize("n_f", [40, 70, 256])
-def test_render_backward(G, oracle, n_f):
+@pytest.mark.parametrize("method", METHODS)
+def test_render_backward(G, oracle, n_f, method):
     rng = np.random.default_rng(5)
     n_pts = 1203
     xyz, grad, w, t_eff = _scene_points(rng, n_pts)
@@ -193,7 +199,7 @@ def test_render_backward(G, oracle, n_f):
     b = gi.band(77e9, 81e9, n_f)
     g = gi.complex_normal(rng, (ant.shape[1], b.n_f)).astype(np.complex64)
     d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant),
-                                            _band(G, b), torch.as_tensor(g, device="cuda"))
+                                            _band(G, b, method), torch.as_tensor(g, device="cuda"))
     G.geraf_poll_device_error()
     ow, ot, og = oracle.render_backward(xyz, grad, w, t_eff, ant, c_ant, b, g)
     assert rel_l2(host(d_w), ow) < TOL
@@ -204,14 +210,16 @@ def test_render_backward(G, oracle, n_f):
 # ------------------------------------------------------------------- filter
 @pytest.mark.parametrize("n_vox,n_ant_side,n_f", [(3001, (6, 7), 40), (256, (16, 16), 32), (1, (2, 2), 3),
                                                   (3001, (6, 7), 64), (2000, (12, 11), 200)])
-def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f):
+@pytest.mark.parametrize("method", METHODS)
+def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f, method):
     rng = np.random.default_rng(n_vox)
     ant = gi.antenna_array(*n_ant_side, 0.002)
     b = gi.band(77e9, 81e9, n_f)
     s = gi.complex_normal(rng, (ant.shape[1], n_f)).astype(np.complex64)
     vox = (np.array([0, 0, 0.15])[:, None] + rng.uniform(-0.05, 0.05, (3, n_vox))).astype(np.float32)
     target = rng.uniform(0, 5, n_vox).astype(np.float32)
-    P, M, loss, dP = G.geraf_filter(torch.as_tensor(s, device="cuda"), cu(ant), _band(G, b), cu(vox), cu(target))
+    P, M, loss, dP = G.geraf_filter(torch.as_tensor(s, device="cuda"), cu(ant), _band(G, b, method), cu(vox),
+                                    cu(target))
     G.geraf_poll_device_error()
     oM, oP = oracle.filter_forward(s, ant, vox, b)
     assert rel_l2(host(M), oM) < TOL
@@ -221,10 +229,47 @@ def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f):
     assert rel_l2(host(dP), odP) < 1e-4
     # backward from the kernel's own M (the oracle gets the same FP32 M)
     d_P = rng.standard_normal(n_vox).astype(np.float32)
-    g = G.geraf_filter_backward(cu(ant), _band(G, b), cu(vox), M, cu(d_P))
+    g = G.geraf_filter_backward(cu(ant), _band(G, b, method), cu(vox), M, cu(d_P))
     G.geraf_poll_device_error()
     og = oracle.filter_backward(host(M), d_P, ant, vox, b)
     assert rel_l2(host(g), og) < TOL
+
+
+def _host_order(xyz, ant, b, eps=1e-9, kmax=64):
+    """Chebyshev order from the bounding box and the Bessel tail, on the host
+    (scipy's J_k): the rule the device plan follows, stated independently."""
+    special = pytest.importorskip("scipy.special")
+    lo, hi = xyz.min(1).astype(np.float64), xyz.max(1).astype(np.float64)
+    a = ant.astype(np.float64)
+    near = np.sqrt((np.maximum(np.maximum(lo[:, None] - a, a - hi[:, None]), 0.0) ** 2).sum(0)).min()
+    far = np.sqrt((np.maximum(np.abs(a - lo[:, None]), np.abs(hi[:, None] - a)) ** 2).sum(0)).max()
+    dr = max(0.5 * (far - near) * 1.001 + 1e-6, 1e-5)
+    amax = 2 * np.pi * (b.n_f - 1) * (2 * b.df / 299792458.0) * dr
+    J = np.abs(special.jv(np.arange(kmax + 8), amax))
+    tail = np.cumsum((2 * J)[::-1])[::-1]            # tail[k] = sum_{m >= k} 2 |J_m|
+    above = np.nonzero(tail > eps)[0]
+    K = max(int(above[-1]) + 1, 2)
+    return 0 if K > kmax else K
+
+
+@pytest.mark.parametrize("centre,half", SPREADS)
+def test_chebyshev_order(G, centre, half):
+    rng = np.random.default_rng(13)
+    xyz = (np.array(centre)[:, None] + rng.uniform(-half, half, (3, 4000))).astype(np.float32)
+    ant = gi.antenna_array(16, 16, 0.002)
+    b = gi.band(77e9, 81e9, 128)
+    want = _host_order(xyz, ant, b)
+    got = G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b))
+    assert abs(got - want) <= 1 and (got == 0) == (want == 0), (got, want)
+    b32 = gi.band(77e9, 81e9, 32)
+    if half < 0.2:
+        assert 20 <= got <= 64
+        # the order follows the band's span, not its bin count
+        assert G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b32, 2)) == got
+    else:
+        assert got == 0                               # above the cap: the recurrence runs
+    assert G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b, 1)) == 0
+    assert G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b32)) == 0      # auto: recurrence below 64 bins
 
 
 # ------------------------------------------- the analytic-scene workload chain
