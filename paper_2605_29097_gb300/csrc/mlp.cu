@@ -289,6 +289,25 @@ __global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a)
     }
 }
 
+// 16-byte asynchronous global -> shared copy (zero-filled when src_bytes = 0)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Rows c = 4 p + s of a [n][4][128] array for the tile's points j0 + p into a
+// [128][XS] shared tile, all in flight at once; rows of points >= n read as 0.
+__device__ __forceinline__ void stage_rows(float* dst, const float* src, int64_t j0, int64_t n) {
+    for (int i = threadIdx.x; i < MCOL * (MW / 4); i += MTHREADS) {
+        const int c = i >> 5, q = i & 31;
+        const bool ok = j0 + (c >> 2) < n;
+        cp_async16(dst + c * XS + 4 * q, ok ? src + (j0 * 4 + c) * MW + 4 * q : src, ok ? 16 : 0);
+    }
+}
+
 // hidden layer `layer`: pre-activation adjoint, weight/bias gradient, adjoint of the layer input
 __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) float sm[];
@@ -322,33 +341,42 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
 
     for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
         const int64_t j0 = (int64_t)tile * MTP;
-        // pre-activation adjoint (HbT) and input activations (ZT)
+        // pre-activation adjoint (HbT), computed in place from the staged
+        // activation adjoint (in HbT) and pre-activations (in ZT)
+        stage_rows(HbT, a.zbar, j0, g.n);
+        stage_rows(ZT, hs, j0, g.n);
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll 4
         for (int p = ehalf; p < MTP; p += 2) {
-            const int64_t j = j0 + p;
-            float hb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            float zi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            if (j < g.n) {
-                const float* zb = a.zbar + j * 4 * MW;
-                const float* h = hs + j * 4 * MW;
-                const float h0 = h[eu];
-                const float sg = sigm(g.beta * h0);
-                const float dsg = g.beta * sg * (1.0f - sg);
-                const float z0 = zb[eu], z1 = zb[MW + eu], z2 = zb[2 * MW + eu], z3 = zb[3 * MW + eu];
-                hb[0] = z0 * sg + (z1 * h[MW + eu] + z2 * h[2 * MW + eu] + z3 * h[3 * MW + eu]) * dsg;
-                hb[1] = sg * z1; hb[2] = sg * z2; hb[3] = sg * z3;
-                if (hin) {
-                    const float* hi = hin + j * 4 * MW;
-                    const float x0 = hi[eu];
-                    const float s0 = sigm(g.beta * x0);
-                    zi[0] = softplus_b(x0, g.beta);
-                    zi[1] = s0 * hi[MW + eu]; zi[2] = s0 * hi[2 * MW + eu]; zi[3] = s0 * hi[3 * MW + eu];
-                }
-            }
-            accb += hb[0];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                HbT[(4 * p + s) * XS + eu] = hb[s];
-                if (hin) ZT[(4 * p + s) * XS + eu] = zi[s];
+            float* hb = HbT + 4 * p * XS + eu;
+            const float* h = ZT + 4 * p * XS + eu;
+            const float h0 = h[0];
+            const float sg = sigm(g.beta * h0);
+            const float dsg = g.beta * sg * (1.0f - sg);
+            const float z0 = hb[0], z1 = hb[XS], z2 = hb[2 * XS], z3 = hb[3 * XS];
+            const float b0 = z0 * sg + (z1 * h[XS] + z2 * h[2 * XS] + z3 * h[3 * XS]) * dsg;
+            accb += b0;                                   // 0 for points >= n (staged zeros)
+            hb[0] = b0;
+            hb[XS] = sg * z1;
+            hb[2 * XS] = sg * z2;
+            hb[3 * XS] = sg * z3;
+        }
+        __syncthreads();
+        // input activations (ZT) of the layer: from the previous layer's pre-activations
+        if (hin) {
+            stage_rows(ZT, hin, j0, g.n);
+            cp_async_wait_all();
+            __syncthreads();
+#pragma unroll 4
+            for (int p = ehalf; p < MTP; p += 2) {
+                float* z = ZT + 4 * p * XS + eu;
+                const float x0 = z[0];
+                const float s0 = sigm(g.beta * x0);
+                z[0] = softplus_b(x0, g.beta);
+                z[XS] *= s0;
+                z[2 * XS] *= s0;
+                z[3 * XS] *= s0;
             }
         }
         // first layer: its input is the positional encoding (columns of points beyond n
