@@ -1,0 +1,138 @@
+"""Precision form (BF16 network on tcgen05 tensor cores, FP32 phasor sums with
+double-single phase and compensated sums): every output of one forward +
+adjoint pass against the FP64 oracle on the subsample of the 128x128-antenna,
+256-bin, 256^3-sample workload:
+
+- antennas: every 4th of each row and column of the 128x128 array at 2 mm
+  (32x32 spanning the full aperture);
+- bins: every 4th of the 256 over 77-81 GHz (64 bins spanning the band);
+- points: a 32^3 stratified grid over the same 10 cm cube; heatmap voxels: the
+  32^3 voxel centres.
+
+Each stage gets identical FP32 inputs on both sides (the GPU's previous stage).
+Tolerances: 2e-3 relative L2 for the BF16 network's outputs and parameter
+gradient against the oracle's BF16 network definition; 1e-5 for the FP32
+stages (3e-5 for the normal gradient, 1e-4 for dL/df of the blend, whose FP32
+alpha rounding is amplified by s Phi (1 - Phi)). All errors are printed.
+"""
+import numpy as np
+import pytest
+import torch
+
+import geraf_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(b) else np.float64)
+    b = np.asarray(b, dtype=a.dtype)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2605_29097_gb300 import _build
+    _build.build()
+    import paper_2605_29097_gb300 as G
+    return G
+
+
+def test_precision_form_subsample(G, oracle):
+    full = gi.workload("c3")
+    assert full.array_n == 128 and full.n_f == 256 and full.grid.n == (256, 256, 256)
+    grid = gi.cube_grid((0.0, 0.0, 0.15), 0.10, (32, 32, 32))
+    ant_full = gi.antenna_array(full.array_n, full.array_n, full.array_pitch)
+    ant = np.ascontiguousarray(ant_full.reshape(3, 128, 128)[:, ::4, ::4].reshape(3, -1))
+    bf = gi.band(77e9, 81e9, full.n_f)
+    b = gi.Band(bf.f0, 4 * bf.df, 64)
+    band = G.Band(b.f0, b.df, b.n_f)
+    s_sharp = np.float32(2.0 / grid.pitch[2])
+    a_tx = np.float32(1.0)
+    spec = gi.MLPSpec()
+    params = gi.mlp_init(spec, seed=3, sdf_bias=0.02)
+    field = G.MLPField(torch.as_tensor(params, device="cuda"), n_levels=spec.n_levels, n_hidden=spec.n_hidden,
+                       beta=spec.beta, center=spec.center, half=spec.half, precision=G.PREC_BF16)
+    cu = lambda x: torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+    h = lambda t: t.detach().cpu().numpy()
+    errs = {}
+
+    # a1 sample (bit-exact)
+    ggrid = G.make_grid(grid.lo, grid.pitch, grid.n, grid.aperture_z)
+    xyz_t, apr_t = G.geraf_sample(ggrid, G.SAMPLE_STRATIFIED, 5, 2)
+    oxyz, oapr = oracle.sample(grid, gi.SAMPLE_STRATIFIED, 5, 2)
+    np.testing.assert_array_equal(h(xyz_t).view(np.uint32), oxyz.view(np.uint32))
+    xyz, apr = h(xyz_t), h(apr_t)
+
+    # a2 fields, BF16 network
+    ant_t = cu(ant.astype(np.float32))
+    f, grad, a, saved = G.geraf_fields(field, xyz_t, keep_saved=True)
+    fa, _, _, _ = G.geraf_fields(field, apr_t, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, ant_t, want_grad=False, want_refl=False)
+    of, oG, oa, cache = oracle.mlp_forward(spec, params, xyz, precision="bf16")
+    ofa, _, _, _ = oracle.mlp_forward(spec, params, apr, precision="bf16")
+    ofn, _, _, _ = oracle.mlp_forward(spec, params, ant.astype(np.float32), precision="bf16")
+    errs["fields f"] = rel(h(f), of)
+    errs["fields G"] = rel(h(grad), oG)
+    errs["fields a"] = rel(h(a), oa)
+    errs["fields f(apr)"] = rel(h(fa), ofa)
+    errs["fields f(ant)"] = rel(h(fn), ofn)
+
+    # a3 blend
+    n_ray, n_z = grid.n_ray, grid.n[2]
+    alpha, T, w, t_eff, c_ant = G.geraf_blend(f, a, n_ray, n_z, fa, fn, float(s_sharp), float(a_tx))
+    ob = oracle.blend(h(f), h(a), n_ray, n_z, h(fa), h(fn), s_sharp, a_tx)
+    for name, got, want in zip(["alpha", "T", "w", "t_eff", "c_ant"], (alpha, T, w, t_eff, c_ant), ob):
+        errs[f"blend {name}"] = rel(h(got), want)
+
+    # a4 render
+    s = G.geraf_render(xyz_t, grad, w, t_eff, ant_t, c_ant, band)
+    os_ = oracle.render(xyz, h(grad), h(w), h(t_eff), ant, h(c_ant), b)
+    errs["render s"] = rel(h(s), os_)
+
+    # a5 filter + loss against a fixed target
+    vox_t, _ = G.geraf_sample(ggrid, G.SAMPLE_UNIFORM)
+    vox = h(vox_t)
+    oM0, oP0 = oracle.filter_forward(h(s), ant, vox, b)
+    target = (oP0 * np.random.default_rng(7).uniform(0.5, 1.5, oP0.shape)).astype(np.float32)
+    P, M, loss, dP = G.geraf_filter(s, ant_t, band, vox_t, cu(target))
+    errs["filter M"] = rel(h(M), oM0)
+    errs["filter P"] = rel(h(P), oP0)
+    oL, odP = oracle.heatmap_loss(oP0, target)
+    errs["loss"] = abs(float(loss) - oL) / abs(oL)
+    errs["dL/dP"] = rel(h(dP), odP)
+
+    # a6 filter adjoint (from the kernel's own M and dP)
+    g = G.geraf_filter_backward(ant_t, band, vox_t, M, dP)
+    og = oracle.filter_backward(h(M), h(dP), ant, vox, b)
+    errs["filter adjoint g"] = rel(h(g), og)
+
+    # a7 render adjoint
+    d_w, d_t, d_G = G.geraf_render_backward(xyz_t, grad, w, t_eff, ant_t, c_ant, band, g)
+    ow, ot, oGd = oracle.render_backward(xyz, h(grad), h(w), h(t_eff), ant, h(c_ant), b, h(g))
+    errs["render adjoint d_w"] = rel(h(d_w), ow)
+    errs["render adjoint d_teff"] = rel(h(d_t), ot)
+    errs["render adjoint d_G"] = rel(h(d_G), oGd)
+
+    # a8 blend adjoint
+    d_f, d_a, d_sc = G.geraf_blend_backward(f, a, alpha, T, n_ray, n_z, float(s_sharp), float(a_tx), d_w, d_t)
+    od_f, od_a, od_s, od_atx = oracle.blend_backward(h(f), h(a), n_ray, n_z, s_sharp, a_tx, h(d_w), h(d_t))
+    errs["blend adjoint d_sdf"] = rel(h(d_f), od_f)
+    errs["blend adjoint d_refl"] = rel(h(d_a), od_a)
+
+    # a9 fields adjoint, BF16 network
+    gp = G.geraf_fields_backward(field, xyz_t, saved, d_f, d_G, d_a)
+    G.geraf_poll_device_error()
+    ogp = oracle.mlp_backward(spec, params, cache, h(d_f), h(d_G), h(d_a))
+    errs["fields adjoint d_params"] = rel(h(gp), ogp)
+
+    print("precision form, 32x32 antennas x 64 bins x 32^3 points:")
+    for k, v in errs.items():
+        print(f"  {k:28s} {v:.2e}")
+    bf16 = {"fields f", "fields G", "fields a", "fields f(apr)", "fields f(ant)", "fields adjoint d_params"}
+    loose = {"render adjoint d_G": 3e-5, "blend adjoint d_sdf": 1e-4}
+    for k, v in errs.items():
+        tol = 2e-3 if k in bf16 else loose.get(k, 1e-5)
+        assert v < tol, (k, v, tol)
