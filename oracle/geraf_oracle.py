@@ -208,7 +208,7 @@ def mlp_forward(spec, params, xyz, precision="fp32"):
     bf = precision == "bf16"
     r = bf16_round if bf else (lambda v: v)
     z, dz = positional_encoding(spec, xyz)
-    cache = {"z": [z], "dz": [dz], "h": [], "dh": []}
+    cache = {"z": [z], "dz": [dz], "h": [], "dh": [], "precision": precision}
     for W, b in layers[:-1]:
         Wr, zr, dzr = r(W), r(z), r(dz)
         h = Wr @ zr + b[:, None]
@@ -230,17 +230,21 @@ def mlp_forward(spec, params, xyz, precision="fp32"):
 
 def mlp_backward(spec, params, cache, d_f, d_G, d_a):
     """Hand-written adjoint of mlp_forward (value + three tangents). Returns the
-    gradient with respect to the packed parameters, FP64, same layout."""
+    gradient with respect to the packed parameters, FP64, same layout.
+    For the BF16 network it is the straight-through adjoint: each rounding is
+    passed through as the identity, so the products use the rounded operands
+    the forward multiplied (rounded hidden weights, rounded layer inputs)."""
     from geraf_inputs import unpack_params
     layers = [(W.astype(np.float64), b.astype(np.float64))
               for W, b in unpack_params(spec, np.asarray(params, dtype=np.float32))]
+    r = bf16_round if cache.get("precision") == "bf16" else (lambda v: v)
     d_f = np.asarray(d_f, np.float64)
     d_G = np.asarray(d_G, np.float64)
     a = cache["a"]
     d_logit = np.asarray(d_a, np.float64) * a * (1.0 - a)
     grads = [None] * len(layers)
     Wh, _ = layers[-1]
-    zL, dzL = cache["z"][-1], cache["dz"][-1]
+    zL, dzL = r(cache["z"][-1]), r(cache["dz"][-1])
     gW = np.zeros_like(Wh)
     gW[0] = zL @ d_f + np.einsum("dn,din->i", d_G, dzL)
     gW[1] = zL @ d_logit
@@ -248,13 +252,13 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
     zbar = np.outer(Wh[0], d_f) + np.outer(Wh[1], d_logit)
     dzbar = np.einsum("i,dn->din", Wh[0], d_G)
     for l in range(len(layers) - 2, -1, -1):
-        W, _ = layers[l]
+        W = r(layers[l][0])
         h, dh = cache["h"][l], cache["dh"][l]
         s = _sigmoid(spec.beta * h)
         ds = spec.beta * s * (1.0 - s)
         dhbar = s[None] * dzbar                        # through dz = s * dh
         hbar = zbar * s + (dzbar * dh).sum(0) * ds     # through z = softplus(h) and s(h)
-        zin, dzin = cache["z"][l], cache["dz"][l]
+        zin, dzin = r(cache["z"][l]), r(cache["dz"][l])
         gW = hbar @ zin.T + np.einsum("don,din->oi", dhbar, dzin)
         grads[l] = (gW, hbar.sum(1))
         zbar = W.T @ hbar

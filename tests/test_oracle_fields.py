@@ -104,3 +104,70 @@ def test_mlp_matches_torch_autograd(oracle):
     L = (tf * torch.tensor(d_f)).sum() + (tG * torch.tensor(d_G.T)).sum() + (ta * torch.tensor(d_a)).sum()
     tgp = torch.autograd.grad(L, p)[0].numpy()
     np.testing.assert_allclose(gp, tgp, rtol=1e-9, atol=1e-10 * np.abs(tgp).max())
+
+
+def _torch_bf16_streams(spec, params, xyz):
+    """Independent reference of the BF16 network (reading: hidden weights and
+    every hidden layer's inputs, value and tangents, rounded to bfloat16; head
+    weights FP32): value and the three x-tangents as explicit streams, the
+    tangents of the encoding by forward-mode AD, rounding by torch's own
+    float32 -> bfloat16 cast with a straight-through gradient, parameter
+    gradient by reverse-mode autograd."""
+    from torch.func import jvp
+    shapes = spec.shapes()
+    p = torch.tensor(params.astype(np.float64), requires_grad=True)
+    x = torch.tensor(xyz.T.astype(np.float64))
+    c = torch.tensor(np.asarray(spec.center, np.float32).astype(np.float64))
+    half = float(np.float32(spec.half))
+
+    def pe(xx):
+        xt = (xx - c) / half
+        feats = []
+        for k in range(spec.n_levels):
+            feats.append(torch.sin((2.0 ** k) * np.pi * xt))
+            feats.append(torch.cos((2.0 ** k) * np.pi * xt))
+        return torch.cat(feats, dim=1)
+
+    def rnd(t):
+        return t + (t.to(torch.float32).to(torch.bfloat16).to(torch.float64) - t).detach()
+
+    z = pe(x)
+    dz = [jvp(pe, (x,), (torch.nn.functional.one_hot(torch.full((x.shape[0],), d), 3).double(),))[1]
+          for d in range(3)]
+    off = 0
+    for li, (o, i) in enumerate(shapes):
+        W = p[off:off + o * i].view(o, i); off += o * i
+        b = p[off:off + o]; off += o
+        if li < len(shapes) - 1:
+            Wr, zr, dzr = rnd(W), rnd(z), [rnd(t) for t in dz]
+            h = zr @ Wr.T + b
+            dh = [t @ Wr.T for t in dzr]
+            s = torch.sigmoid(spec.beta * h)
+            z = torch.nn.functional.softplus(h, beta=spec.beta, threshold=1e6)
+            dz = [s * t for t in dh]
+        else:
+            zr, dzr = rnd(z), [rnd(t) for t in dz]
+            out = zr @ W.T + b
+            f, a = out[:, 0], torch.sigmoid(out[:, 1])
+            G = torch.stack([t @ W[0] for t in dzr], 1)
+    return p, f, G, a
+
+
+def test_mlp_bf16_network_and_straight_through_adjoint_match_torch(oracle):
+    spec = gi.MLPSpec(n_levels=3, width=16, n_hidden=3, beta=20.0)
+    params = gi.mlp_init(spec, seed=6)
+    rng = np.random.default_rng(2)
+    xyz = (np.array(spec.center)[:, None] + rng.uniform(-0.05, 0.05, (3, 41))).astype(np.float32)
+    f, G, a, cache = oracle.mlp_forward(spec, params, xyz, precision="bf16")
+    p, tf, tG, ta = _torch_bf16_streams(spec, params, xyz)
+    np.testing.assert_allclose(f, tf.detach().numpy(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(a, ta.detach().numpy(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(G, tG.detach().numpy().T, rtol=1e-10, atol=1e-11)
+    # the BF16 network differs from the FP32 one by the roundings (a dropped rounding would not)
+    f32, _, _, _ = oracle.mlp_forward(spec, params, xyz)
+    assert np.abs(f - f32).max() > 1e-6
+    d_f, d_G, d_a = rng.standard_normal(41), rng.standard_normal((3, 41)), rng.standard_normal(41)
+    gp = oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)
+    L = (tf * torch.tensor(d_f)).sum() + (tG * torch.tensor(d_G.T)).sum() + (ta * torch.tensor(d_a)).sum()
+    tgp = torch.autograd.grad(L, p)[0].numpy()
+    np.testing.assert_allclose(gp, tgp, rtol=1e-9, atol=1e-10 * np.abs(tgp).max())
