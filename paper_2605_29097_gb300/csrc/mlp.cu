@@ -289,15 +289,6 @@ __global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a)
     }
 }
 
-// 16-byte asynchronous global -> shared copy (zero-filled when src_bytes = 0)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 // Rows c = 4 p + s of a [n][4][128] array for the tile's points j0 + p into a
 // [128][XS] shared tile, all in flight at once; rows of points >= n read as 0.
 __device__ __forceinline__ void stage_rows(float* dst, const float* src, int64_t j0, int64_t n) {
@@ -501,20 +492,33 @@ geraf_status mlp_forward_impl(const geraf_field_desc* d, const float* xyz, int64
     return cuda_status(cudaGetLastError(), "fields(mlp)");
 }
 
+int mlp_tc_backward_ctas(int64_t n);
+geraf_status mlp_tc_backward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
+                                  const float* d_sdf, const float* d_grad, const float* d_refl, float* zbar,
+                                  float* partial, int64_t n_params, int n_cta, cudaStream_t st);
+
 geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
                                const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
                                void* ws, size_t* ws_bytes, cudaStream_t st) {
     MlpGeom g;
     if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
-    // BF16 networks: the adjoint runs in FP32 on CUDA cores from the FP32 pre-activations the
-    // tensor-core forward saved (the BF16 roundings are passed through as identities)
-    const int n_cta = n_ctas_for(g.n_tiles);
+    // BF16 networks: the straight-through adjoint on tcgen05 tensor cores; FP32
+    // networks: CUDA cores. Both leave per-CTA partials reduced here in FP64.
+    const bool bf16 = d->precision == GERAF_PREC_BF16;
+    const int n_cta = bf16 ? mlp_tc_backward_ctas(n) : n_ctas_for(g.n_tiles);
     WsCarver c(ws);
     float* zbar = c.take<float>((size_t)n * 4 * MW);
     float* partial = c.take<float>((size_t)n_cta * g.n_params);
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "fields_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    if (bf16) {
+        geraf_status s = mlp_tc_backward_impl(d, xyz, n, saved, d_sdf, d_grad, d_refl, zbar, partial, g.n_params,
+                                              n_cta, st);
+        if (s != GERAF_OK) return s;
+        reduce_partials<<<(unsigned)((g.n_params + 255) / 256), 256, 0, st>>>(partial, n_cta, g.n_params, d_params);
+        return cuda_status(cudaGetLastError(), "fields_backward(mlp bf16)");
+    }
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(mlp_layer_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());

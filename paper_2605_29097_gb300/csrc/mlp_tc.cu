@@ -65,6 +65,33 @@ __device__ __forceinline__ float sgm(float x) { return 1.0f / (1.0f + expf(-x));
 __device__ __forceinline__ void st_bf16(unsigned char* base, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
 }
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Encoding features of axis d of point x (FP32 coordinate) and their
+// x-derivatives: put(feature, stream, value) for stream 0 (value) and the
+// three tangent streams (only stream d + 1 is nonzero).
+template <class Put>
+__device__ __forceinline__ void encode_axis(const TcGeom& g, float x, int d, Put put) {
+    const float c = d == 0 ? g.cx : (d == 1 ? g.cy : g.cz);
+    const double xt_ = ((double)x - (double)c) / (double)g.half;
+    for (int k = 0; k < g.L; ++k) {
+        const double t2 = xt_ * (double)(1 << k);
+        const double r = t2 - 2.0 * rint(0.5 * t2);
+        float sn, cs;
+        sincospif((float)r, &sn, &cs);
+        const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
+        const int fs = 6 * k + d, fc = 6 * k + 3 + d;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            float vs, vc;
+            if (s == 0) { vs = sn; vc = cs; }
+            else if (s - 1 == d) { vs = wk * cs; vc = -wk * sn; }
+            else { vs = 0.0f; vc = 0.0f; }
+            put(fs, s, vs);
+            put(fc, s, vc);
+        }
+    }
+}
 
 struct TcFwdArgs {
     TcGeom g;
@@ -140,26 +167,9 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs
                 const int p = t / 3, d = t - 3 * (t / 3);
                 int64_t j = j0 + p;
                 if (j >= g.n) j = g.n - 1;
-                const float x = a.xyz[d * g.n + j];
-                const float c = d == 0 ? g.cx : (d == 1 ? g.cy : g.cz);
-                const double xt_ = ((double)x - (double)c) / (double)g.half;
-                for (int k = 0; k < g.L; ++k) {
-                    const double t2 = xt_ * (double)(1 << k);
-                    const double r = t2 - 2.0 * rint(0.5 * t2);
-                    float sn, cs;
-                    sincospif((float)r, &sn, &cs);
-                    const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
-                    const int fs = 6 * k + d, fc = 6 * k + 3 + d;
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        float vs, vc;
-                        if (s == 0) { vs = sn; vc = cs; }
-                        else if (s - 1 == d) { vs = wk * cs; vc = -wk * sn; }
-                        else { vs = 0.0f; vc = 0.0f; }
-                        st_bf16(xt, tc::kmajor_offset(4 * p + s, fs, TLBO, sbo0), vs);
-                        st_bf16(xt, tc::kmajor_offset(4 * p + s, fc, TLBO, sbo0), vc);
-                    }
-                }
+                encode_axis(g, a.xyz[d * g.n + j], d, [&](int f, int s, float v) {
+                    st_bf16(xt, tc::kmajor_offset(4 * p + s, f, TLBO, sbo0), v);
+                });
             }
         }
         for (int l = 0; l < g.NH; ++l) {
@@ -258,6 +268,299 @@ size_t tc_fwd_smem(const TcGeom& g) {
     return off + 16 + 1024;   // barrier, TMEM slot, abort flag; slack for the 1024-byte base alignment
 }
 
+// ------------------------------------------------------- adjoint (BF16 network)
+// Straight-through adjoint of the BF16 network: each rounding passes as the
+// identity, so the products use the operands the forward multiplied (BF16
+// weights, BF16 layer inputs and tangents); the head weights are FP32.
+// Hidden layer, per tile of 16 points (64 columns = 16 points x 4 streams):
+//   Hb[c][u]  pre-activation adjoint in FP32 from the activation adjoint and
+//             the saved pre-activations, split into BF16 hi + lo;
+//   dW[u][k] += sum_c Hb[c][u] Z[c][k]: M = 128 units, N = K_in, K = 64
+//             columns, accumulated in TMEM over all the CTA's tiles;
+//   Z'[k][c]  = sum_u W[u][k] Hb[c][u] (the adjoint of the layer input,
+//             transposed: M = K_in, N = 64, K = 128), read back per tile and
+//             written over the activation adjoint.
+// Every product is hi + lo of Hb against exact BF16 operands: 2 MMAs each.
+constexpr int BTP = 16;          // points per adjoint tile
+constexpr int BCOL = 4 * BTP;    // 64 columns
+constexpr uint32_t B_SBO_K128 = 16u * 128u;   // 8-row group stride of a K = 128 tile
+constexpr uint32_t B_SBO_K64 = 8u * 128u;     // 8-row group stride of a K = 64 tile
+
+struct TcBwdArgs {
+    TcGeom g;
+    const float* params;
+    const float* xyz;
+    const float* saved;     // [NH][n][4][128] FP32 pre-activations, then a[n]
+    const float* d_sdf;
+    const float* d_grad;
+    const float* d_refl;
+    float* zbar;            // [n][4][128] activation adjoint, updated layer by layer
+    float* partial;         // [gridDim.x][n_params]
+    int64_t n_params;
+    int layer;
+    int* err;
+};
+
+// head: dL/dW_head, dL/db_head (from the BF16-rounded last activations) and
+// the adjoint of the last hidden activation (through the FP32 head weights)
+__global__ void __launch_bounds__(256) mlp_tc_head_bwd_kernel(const TcBwdArgs a) {
+    __shared__ float red[2 * 256];
+    __shared__ float redb[2 * 2];
+    const TcGeom& g = a.g;
+    const int t = threadIdx.x, u = t & (TW - 1), half = t >> 7;
+    const float* Wh = a.params + g.off_w[g.NH];
+    const float w0 = Wh[u], w1 = Wh[TW + u];
+    const float* hsv = a.saved + (int64_t)(g.NH - 1) * g.n * 4 * TW;
+    const float* asv = a.saved + (int64_t)g.NH * g.n * 4 * TW;
+    float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
+    const int64_t n_pairs = (g.n + 1) / 2;
+    for (int64_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
+        const int64_t j = 2 * q + half;
+        if (j >= g.n) continue;
+        const float df = a.d_sdf ? a.d_sdf[j] : 0.0f;
+        const float av = asv[j];
+        const float dl = a.d_refl ? a.d_refl[j] * av * (1.0f - av) : 0.0f;
+        const float* h = hsv + j * 4 * TW;
+        const float h0 = h[u];
+        const float sg = sgm(g.beta * h0);
+        const float z = bf16r(sp_b(h0, g.beta));
+        gw0 += df * z;
+        gw1 += dl * z;
+        float* zb = a.zbar + j * 4 * TW;
+        zb[u] = w0 * df + w1 * dl;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float dG = a.d_grad ? a.d_grad[(int64_t)d * g.n + j] : 0.0f;
+            gw0 += dG * bf16r(sg * h[(d + 1) * TW + u]);
+            zb[(d + 1) * TW + u] = w0 * dG;
+        }
+        if (u == 0) { gb0 += df; gb1 += dl; }
+    }
+    red[t] = gw0;
+    red[256 + t] = gw1;
+    if (u == 0) { redb[2 * half] = gb0; redb[2 * half + 1] = gb1; }
+    __syncthreads();
+    float* out = a.partial + (int64_t)blockIdx.x * a.n_params;
+    if (t < TW) {
+        out[g.off_w[g.NH] + t] = red[t] + red[t + TW];
+        out[g.off_w[g.NH] + TW + t] = red[256 + t] + red[256 + t + TW];
+    }
+    if (t == 0) {
+        out[g.off_b[g.NH]] = redb[0] + redb[2];
+        out[g.off_b[g.NH] + 1] = redb[1] + redb[3];
+    }
+}
+
+struct BwdLayout {
+    uint32_t wt, hbB, hbA, zB, zs, hsb, bar;
+    uint32_t total;
+};
+
+__host__ __device__ inline BwdLayout bwd_layout(int kin) {
+    BwdLayout L;
+    uint32_t off = 0;
+    L.wt = off;  off += (uint32_t)kin * TW * 2u;            // W^T: rows k, K = 128 units
+    L.hbB = off; off += 2u * BCOL * TW * 2u;                // Hb hi, lo: rows c, K = 128 units
+    L.hbA = off; off += 2u * TW * BCOL * 2u;                // Hb hi, lo: rows u, K = 64 columns
+    L.zB = off;  off += (uint32_t)kin * BCOL * 2u;          // Z: rows k, K = 64 columns
+    L.zs = off;  off += BCOL * TW * 4u;                     // FP32 staging [64][128]
+    L.hsb = off; off += BCOL * TW * 4u;                     // FP32 staging [64][128]
+    L.bar = off; off += 16u;
+    L.total = off;
+    return L;
+}
+
+// Rows c = 4 p + s of a [n][4][128] FP32 array for points j0 + p (p < 16)
+// into a [64][128] shared tile, all in flight; rows of points >= n read as 0.
+__device__ __forceinline__ void stage64(float* dst, const float* src, int64_t j0, int64_t n) {
+    for (int i = threadIdx.x; i < BCOL * (TW / 4); i += TTHREADS) {
+        const int c = i >> 5, q = i & 31;
+        const bool ok = j0 + (c >> 2) < n;
+        cp_async16(dst + c * TW + 4 * q, ok ? src + (j0 * 4 + c) * TW + 4 * q : src, ok ? 16 : 0);
+    }
+}
+
+__global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcBwdArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw;
+    const TcGeom& g = a.g;
+    const int li = a.layer;
+    const int kin = li == 0 ? g.K0p : TW;     // padded input width (MMA N of dW, M of the input adjoint)
+    const int K = li == 0 ? g.K0 : TW;        // true input width
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const BwdLayout L = bwd_layout(kin);
+    unsigned char* wt = smem + L.wt;
+    unsigned char* hbB[2] = {smem + L.hbB, smem + L.hbB + BCOL * TW * 2};
+    unsigned char* hbA[2] = {smem + L.hbA, smem + L.hbA + TW * BCOL * 2};
+    unsigned char* zB = smem + L.zB;
+    float* zs = reinterpret_cast<float*>(smem + L.zs);
+    float* hsb = reinterpret_cast<float*>(smem + L.hsb);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 8);
+    int* abort_flag = reinterpret_cast<int*>(smem + L.bar + 12);
+
+    // W^T as the A operand of the input adjoint (layers above the first)
+    if (li > 0) {
+        const float* W = a.params + g.off_w[li];      // [128 u][128 k]
+        for (int i = t; i < TW * TW; i += TTHREADS) {
+            const int u = i / TW, k = i - u * TW;
+            st_bf16(wt, tc::kmajor_offset(k, u, TLBO, B_SBO_K128), W[i]);
+        }
+    } else {
+        // padding rows K0 .. K0p-1 of Z stay zero for every tile
+        for (int i = t; i < (kin - K) * BCOL; i += TTHREADS) {
+            const int k = K + i / BCOL, c = i % BCOL;
+            st_bf16(zB, tc::kmajor_offset(k, c, TLBO, B_SBO_K64), 0.0f);
+        }
+    }
+    if (t == 0) {
+        mbar_init(bar, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t t_dw = tbase, t_dx = tbase + 128u;   // dW: columns 0..kin-1; input adjoint: 128..191
+    const uint32_t id_dw = tc::idesc_bf16(128, kin);
+    const uint32_t id_dx = tc::idesc_bf16(128, BCOL);
+    const float* hs = a.saved + (int64_t)li * g.n * 4 * TW;
+    const float* hin = li > 0 ? a.saved + (int64_t)(li - 1) * g.n * 4 * TW : nullptr;
+    const int n_tiles = (int)((g.n + BTP - 1) / BTP);
+    uint32_t phase = 0;
+    float accb = 0.0f;
+    bool first = true;
+
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t j0 = (int64_t)tile * BTP;
+        stage64(zs, a.zbar, j0, g.n);
+        stage64(hsb, hs, j0, g.n);
+        cp_async_wait_all();
+        __syncthreads();
+        // pre-activation adjoint, thread = unit u
+        {
+            const int u = t;
+            for (int p = 0; p < BTP; ++p) {
+                const float* z = zs + 4 * p * TW + u;
+                const float* h = hsb + 4 * p * TW + u;
+                const float h0 = h[0];
+                const float sg = sgm(g.beta * h0);
+                const float dsg = g.beta * sg * (1.0f - sg);
+                const float z0 = z[0], z1 = z[TW], z2 = z[2 * TW], z3 = z[3 * TW];
+                const float b[4] = {z0 * sg + (z1 * h[TW] + z2 * h[2 * TW] + z3 * h[3 * TW]) * dsg, sg * z1, sg * z2,
+                                    sg * z3};
+                accb += b[0];                         // 0 for points >= n (staged zeros)
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const float hi = bf16r(b[s]);
+                    const float lo = b[s] - hi;
+                    const int c = 4 * p + s;
+                    st_bf16(hbB[0], tc::kmajor_offset(c, u, TLBO, B_SBO_K128), hi);
+                    st_bf16(hbB[1], tc::kmajor_offset(c, u, TLBO, B_SBO_K128), lo);
+                    st_bf16(hbA[0], tc::kmajor_offset(u, c, TLBO, B_SBO_K64), hi);
+                    st_bf16(hbA[1], tc::kmajor_offset(u, c, TLBO, B_SBO_K64), lo);
+                }
+            }
+        }
+        __syncthreads();
+        // the layer's BF16 input Z (thread = input unit k), as the forward rounded it
+        if (hin) {
+            stage64(zs, hin, j0, g.n);
+            cp_async_wait_all();
+            __syncthreads();
+            const int k = t;
+            for (int p = 0; p < BTP; ++p) {
+                const float* x = zs + 4 * p * TW + k;
+                const float x0 = x[0];
+                const float s0 = sgm(g.beta * x0);
+                const float v[4] = {sp_b(x0, g.beta), s0 * x[TW], s0 * x[2 * TW], s0 * x[3 * TW]};
+#pragma unroll
+                for (int s = 0; s < 4; ++s) st_bf16(zB, tc::kmajor_offset(k, 4 * p + s, TLBO, B_SBO_K64), v[s]);
+            }
+        } else if (t < 3 * BTP) {
+            const int p = t / 3, d = t - 3 * (t / 3);
+            int64_t j = j0 + p;
+            if (j >= g.n) j = g.n - 1;
+            encode_axis(g, a.xyz[d * g.n + j], d, [&](int f, int s, float v) {
+                st_bf16(zB, tc::kmajor_offset(f, 4 * p + s, TLBO, B_SBO_K64), v);
+            });
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+            const uint32_t zb_a = smem_u32(zB);
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t ha = smem_u32(hbA[h]);
+                for (int s = 0; s < BCOL / 16; ++s)
+                    tc::mma_bf16(t_dw, tc::smem_desc(ha + s * 256u, TLBO, B_SBO_K64),
+                                 tc::smem_desc(zb_a + s * 256u, TLBO, B_SBO_K64), id_dw,
+                                 (!first || h > 0 || s > 0) ? 1u : 0u);
+            }
+            if (li > 0) {
+                const uint32_t wa = smem_u32(wt);
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t hb = smem_u32(hbB[h]);
+                    for (int s = 0; s < TW / 16; ++s)
+                        tc::mma_bf16(t_dx, tc::smem_desc(wa + s * 256u, TLBO, B_SBO_K128),
+                                     tc::smem_desc(hb + s * 256u, TLBO, B_SBO_K128), id_dx,
+                                     (h > 0 || s > 0) ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(bar);
+        }
+        first = false;
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!ok) atomicOr(abort_flag, 1);
+        tc::fence_after_sync();
+        __syncthreads();
+        if (*abort_flag) break;
+        // adjoint of the layer input: thread = input unit k (TMEM lane), 64 columns
+        if (li > 0) {
+            const int k = warp * 32 + lane;
+            for (int cc = 0; cc < BCOL / 32; ++cc) {
+                float r[32];
+                tc::tmem_ld32(t_dx + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int c = cc * 32 + i;
+                    if (j0 + (c >> 2) < g.n) a.zbar[(j0 * 4 + c) * TW + k] = r[i];
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();     // the next tile's staging and operands overwrite this tile's
+    }
+    if (*abort_flag) {
+        if (t == 0) {
+            atomicOr(a.err, 1);
+            mbar_wait(bar, phase ^ 1u, 100000000ull);   // bounded: let the timed-out MMAs finish
+        }
+    } else {
+        // weight gradient of this CTA: thread = unit u (TMEM lane), columns k < K
+        const int u = warp * 32 + lane;
+        float* out = a.partial + (int64_t)blockIdx.x * a.n_params;
+        for (int cc = 0; cc < (kin + 31) / 32; ++cc) {
+            float r[32];
+            tc::tmem_ld32(t_dw + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int k = cc * 32 + i;
+                if (k < K) out[g.off_w[li] + (int64_t)u * K + k] = first ? 0.0f : r[i];
+            }
+        }
+        out[g.off_b[li] + u] = accb;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
 }  // namespace
 
 geraf_status mlp_tc_forward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
@@ -275,6 +578,36 @@ geraf_status mlp_tc_forward_impl(const geraf_field_desc* d, const float* xyz, in
     TcFwdArgs a{g, d->params, xyz, sdf, grad, refl, static_cast<float*>(saved), device_error_word()};
     mlp_tc_fwd_kernel<<<n_cta, TTHREADS, smem, st>>>(a);
     return cuda_status(cudaGetLastError(), "fields(mlp bf16)");
+}
+
+int mlp_tc_backward_ctas(int64_t n) {
+    const int64_t tiles = (n + BTP - 1) / BTP;
+    const int sms = device_sm_count();
+    return (int)(tiles < sms ? (tiles > 0 ? tiles : 1) : sms);
+}
+
+// Adjoint of the BF16 network: head on CUDA cores, hidden layers top down on
+// tcgen05; per-CTA weight-gradient partials [n_cta][n_params] for the caller
+// to reduce.
+geraf_status mlp_tc_backward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
+                                  const float* d_sdf, const float* d_grad, const float* d_refl, float* zbar,
+                                  float* partial, int64_t n_params, int n_cta, cudaStream_t st) {
+    TcGeom g;
+    if (!make_tc_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_tc_layer_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    TcBwdArgs a{g, d->params, xyz, static_cast<const float*>(saved), d_sdf, d_grad, d_refl, zbar, partial,
+                n_params, 0, device_error_word()};
+    mlp_tc_head_bwd_kernel<<<n_cta, 256, 0, st>>>(a);
+    for (int l = g.NH - 1; l >= 0; --l) {
+        a.layer = l;
+        const size_t smem = bwd_layout(l == 0 ? g.K0p : TW).total + 1024;
+        mlp_tc_layer_bwd_kernel<<<n_cta, TTHREADS, smem, st>>>(a);
+    }
+    return cuda_status(cudaGetLastError(), "fields_backward(mlp bf16)");
 }
 
 }  // namespace geraf
