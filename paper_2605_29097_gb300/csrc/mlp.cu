@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(16) float sm[];
     float* X0 = sm;
     float* X1 = X0 + MW * XS;
-    float* Wt = X1 + MW * XS;             // Wt[k][u]
+    float* Wt = X1 + MW * XS;             // W[u][k], rows padded to XS
     float* bias = Wt + MW * XS;           // [128]
     float* head = bias + MW;              // [2][128], then 2 biases
     const MlpGeom& g = a.g;
@@ -138,10 +138,22 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
         float* Xout = X1;
         for (int l = 0; l < g.NH; ++l) {
             const int K = g.k_in[l];
+            const int Kp = (K + 3) & ~3;                 // K rounded up to the float4 step
             const float* W = a.params + g.off_w[l];
-            for (int idx = t; idx < MW * K; idx += MTHREADS) {
-                const int u = idx / K, k = idx - u * K;
-                Wt[k * XS + u] = W[idx];
+            // W [u][k] into shared memory as it lies in memory (rows padded to
+            // XS, columns K .. Kp-1 zero): asynchronous 16-byte copies when the
+            // rows are 16-byte aligned
+            if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0) {
+                for (int idx = t; idx < MW * (K / 4); idx += MTHREADS) {
+                    const int u = idx / (K / 4), kq = idx - u * (K / 4);
+                    cp_async16(Wt + u * XS + 4 * kq, W + (int64_t)u * K + 4 * kq, 16);
+                }
+                cp_async_wait_all();
+            } else {
+                for (int idx = t; idx < MW * Kp; idx += MTHREADS) {
+                    const int u = idx / Kp, k = idx - u * Kp;
+                    Wt[u * XS + k] = k < K ? W[(int64_t)u * K + k] : 0.0f;
+                }
             }
             if (t < MW) bias[t] = a.params[g.off_b[l] + t];
             __syncthreads();
@@ -150,18 +162,23 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0f;
-#pragma unroll 2
-            for (int k = 0; k < K; ++k) {
-                const float4 w0 = *reinterpret_cast<const float4*>(Wt + k * XS + 8 * ub);
-                const float4 w1 = *reinterpret_cast<const float4*>(Wt + k * XS + 8 * ub + 4);
-                const float4 x0 = *reinterpret_cast<const float4*>(Xin + k * XS + 4 * cb);
-                const float4 x1 = *reinterpret_cast<const float4*>(Xin + k * XS + 64 + 4 * cb);
-                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            for (int kq = 0; kq < Kp / 4; ++kq) {
+                float4 wq[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i) wq[i] = *reinterpret_cast<const float4*>(Wt + (8 * ub + i) * XS + 4 * kq);
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(wv[i], xv[jj], acc[i][jj]);
+                for (int m = 0; m < 4; ++m) {
+                    const int k = 4 * kq + m;
+                    const float4 x0 = *reinterpret_cast<const float4*>(Xin + k * XS + 4 * cb);
+                    const float4 x1 = *reinterpret_cast<const float4*>(Xin + k * XS + 64 + 4 * cb);
+                    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float wv = m == 0 ? wq[i].x : (m == 1 ? wq[i].y : (m == 2 ? wq[i].z : wq[i].w));
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(wv, xv[jj], acc[i][jj]);
+                    }
+                }
             }
             // epilogue: value column (bias, softplus) and tangents (sigmoid(beta h) * dh)
 #pragma unroll
@@ -172,10 +189,9 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
                     const int col0 = pp * 64 + 4 * cb;
                     const float h = acc[i][4 * pp] + bias[u];
                     const float sg = sigm(g.beta * h);
-                    Xout[u * XS + col0] = softplus_b(h, g.beta);
-                    Xout[u * XS + col0 + 1] = sg * acc[i][4 * pp + 1];
-                    Xout[u * XS + col0 + 2] = sg * acc[i][4 * pp + 2];
-                    Xout[u * XS + col0 + 3] = sg * acc[i][4 * pp + 3];
+                    *reinterpret_cast<float4*>(Xout + u * XS + col0) =
+                        make_float4(softplus_b(h, g.beta), sg * acc[i][4 * pp + 1], sg * acc[i][4 * pp + 2],
+                                    sg * acc[i][4 * pp + 3]);
                     acc[i][4 * pp] = h;
                 }
             }
