@@ -39,6 +39,12 @@ WORKLOAD = ("64x64 array @2mm, 128 freqs 77-81 GHz, 128^3 stratified samples, ML
 FLOPS_PER_TERM = {"render": 10, "filter_backward": 10, "filter": 8, "render_backward": 8}
 CHEB_FLOPS_PER_ORDER = 6
 PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
+# DRAM bytes (read + write) of each Chebyshev phasor kernel from one ncu capture
+# of the small C2 case (65 536 points, 32^3 voxels, 4096 antennas, 128 bins),
+# scaled to a full launch by the points or voxels it processes (the records read
+# and the split partials written both grow in proportion).
+NCU_DRAM_SMALL = {"render": (4.21e6, "points", 65536), "render_backward": (7.42e6, "points", 65536),
+                  "filter": (4.66e6, "voxels", 32768), "filter_backward": (9.27e6, "voxels", 32768)}
 
 
 def _env_int(k, d):
@@ -102,8 +108,8 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, P_target, max_pts=32768, n_ant=64, n_vox=4096,
-                        filt_ant=256):
+def cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, P_target, max_pts=32768, n_ant=1024, n_vox=16384,
+                        filt_ant=1024):
     """Times the FP64 oracle's four phasor sums on a bounded sample of the
     workload (first max_pts points x first n_ant antennas x all bins for the
     tracing pair; first n_vox voxels x first filt_ant antennas for the filter
@@ -152,7 +158,7 @@ def run_reference(args, rank):
     wl = gi.workload("c2")
     b = gi.band(77e9, 81e9, wl.n_f)
     xyz, apr = O.sample(wl.grid, gi.SAMPLE_STRATIFIED, seed=0, step=0)
-    n_pts, n_ant, n_vox, filt_ant = 16384, 32, 2048, 128
+    n_pts, n_ant, n_vox, filt_ant = 16384, 128, 2048, 256
     X = xyz[:, :n_pts]
     rng = np.random.default_rng(0)
     Gr = rng.standard_normal((3, n_pts))
@@ -505,6 +511,13 @@ def main():
         per_call_roof = {nm: roof(nm, per_kernel[nm], order_of[nm]) for nm in names}
         rec_roof = {nm: roof(nm, per_kernel_rec[nm], 0) for nm in PHASOR_CALLS}
         dom = max(names, key=lambda k: per_kernel[k])
+        traffic, traffic_basis = None, "no ncu capture of this kernel version"
+        if dom in NCU_DRAM_SMALL and order_of[dom] > 0:
+            b_small, unit, n_small = NCU_DRAM_SMALL[dom]
+            n_full = n_pts if unit == "points" else n_vox
+            traffic = b_small * n_full / n_small
+            traffic_basis = (f"ncu dram__bytes_read+write of the small C2 case ({n_small} {unit}), "
+                             f"scaled by {unit} to {n_full}")
         launches = PL.launches_per_step(field, geo.band) * args.steps
         cpu = None
         if not args.no_cpu_baseline:
@@ -527,7 +540,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "per_call_ms": {k: round(v, 3) for k, v in per_kernel.items()},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": per_call_roof[dom]["tflops"],
-                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": per_call_roof[dom]["frac"], "traffic": None,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": per_call_roof[dom]["frac"],
+                         "traffic": traffic, "traffic_basis": traffic_basis,
                          "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz",
                          "work_basis": ("Chebyshev phasor sums: pairs x order x 6 flops; per-bin recurrence: "
                                         "terms x 10 (render, filter adjoint) or 8 (filter, render adjoint) flops; "
