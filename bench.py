@@ -485,6 +485,25 @@ def main():
         PL.forward_backward(geo_rec, field, target, seed, step_id + k, timers=ev_rec[k])
     torch.cuda.synchronize()
     per_kernel_rec = {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev_rec) / rec_steps for nm in names}
+    # the paper's signal tracing bank on the same workload: 16 x 16-antenna patches,
+    # one traced per step, the other 15 from the bank
+    bank = PL.SignalBank(geo, (wl.array_n, wl.array_n), (16, 16))
+    bank.fill(field, seed, 0)
+    for k in range(args.warmup):
+        PL.forward_backward_bank(bank, field, target, seed, step_id + k)
+    torch.cuda.synchronize()
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb0.record()
+    for k in range(args.steps):
+        PL.forward_backward_bank(bank, field, target, seed, step_id + args.warmup + k)
+    eb1.record()
+    torch.cuda.synchronize()
+    bank_ms = eb0.elapsed_time(eb1) / args.steps
+    n_ant_all, n_vox_all, nf = int(geo.ant.shape[1]), int(geo.vox.shape[1]), geo.band.n_f
+    bank_terms = (2 * n_pts * bank.patch_size * nf + n_vox_all * n_ant_all * nf + n_vox_all * bank.patch_size * nf)
+    bank_line = {"patch_antennas": bank.patch_size, "n_patches": bank.n_patch, "ms_per_step": bank_ms,
+                 "full_trace_ms_per_step": None, "terms_per_step": bank_terms}
+    del bank
     xyz_o, _ = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
     orders = {"points": G.geraf_chebyshev_order(xyz_o, geo.ant, geo.band),
               "voxels": G.geraf_chebyshev_order(geo.vox, geo.ant, geo.band)}
@@ -552,6 +571,8 @@ def main():
                               "recurrence_roofline": rec_roof,
                               "recurrence_terms_per_s": 2 * (n_pts + n_vox) * n_ant * geo.band.n_f
                               / (sum(per_kernel_rec[k] for k in PHASOR_CALLS) * 1e-3)},
+            "bank_step": dict(bank_line, full_trace_ms_per_step=ms / args.steps,
+                              speedup=(ms / args.steps) / bank_line["ms_per_step"]),
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -285,3 +285,92 @@ class ProposalTrainer:
         with torch.no_grad():
             self.prop.params.copy_(self.params)
             self.prop.features.copy_(self.feats.half())
+
+
+# ------------------------------------------------------ signal tracing bank
+class SignalBank:
+    """Signal tracing bank (section 5.3 "Signal Tracing Bank"): the aperture is
+    divided into patches of antennas, each step traces the signal of one patch
+    only and takes every other antenna's signal from the bank, which the step
+    then updates with the patch it traced. The matched filter has no
+    parameters, so bank entries carry no gradient: the filter adjoint and the
+    tracing adjoint run for the traced patch alone.
+
+    The antennas are reordered patch by patch (patches are px x py tiles of the
+    nx x ny array, patch k = qy * (nx / px) + qx) so that each patch is a
+    contiguous range of bank rows; `order[i]` is the original index of bank
+    row i and `geo` is the geometry in bank order."""
+
+    def __init__(self, geo: Geometry, array_shape, patch_shape):
+        nx, ny = array_shape
+        px, py = patch_shape
+        if nx * ny != geo.ant.shape[1] or nx % px or ny % py:
+            raise ValueError("patch shape must tile the antenna array")
+        idx = np.arange(nx * ny).reshape(ny, nx)
+        order = np.concatenate([idx[qy * py:(qy + 1) * py, qx * px:(qx + 1) * px].reshape(-1)
+                                for qy in range(ny // py) for qx in range(nx // px)])
+        self.order = order
+        dev = geo.ant.device
+        ant = geo.ant[:, torch.as_tensor(order, device=dev)].contiguous()
+        self.geo = Geometry(geo.grid, geo.n_ray, geo.n_z, ant, geo.vox, geo.band, geo.sharpness, geo.a_tx, geo.mode)
+        self.patch_size = px * py
+        self.n_patch = (nx // px) * (ny // py)
+        self.patch_ant = [ant[:, k * self.patch_size:(k + 1) * self.patch_size].contiguous()
+                          for k in range(self.n_patch)]
+        self.s = torch.zeros(nx * ny, geo.band.n_f, dtype=torch.complex64, device=dev)
+
+    def rows(self, k):
+        return k * self.patch_size, (k + 1) * self.patch_size
+
+    def fill(self, field, seed: int, step: int):
+        """Trace every antenna once (the bank's initial content)."""
+        _, s = render_heatmap(self.geo, field, self.geo.mode, seed, step)
+        self.s.copy_(s)
+
+
+def forward_backward_bank(bank: SignalBank, field, target: torch.Tensor, seed: int, step: int, patch=None,
+                          timers=None) -> StepResult:
+    """One hot-path pass with the signal tracing bank: trace patch `patch`
+    (default: step mod the number of patches), update its bank rows, filter
+    the whole bank against the target, and run the adjoints for that patch."""
+    def tic(name):
+        if timers is not None and name in timers:
+            timers[name][0].record()
+
+    def toc(name):
+        if timers is not None and name in timers:
+            timers[name][1].record()
+
+    geo = bank.geo
+    k = step % bank.n_patch if patch is None else patch
+    a0, a1 = bank.rows(k)
+    ant_p = bank.patch_ant[k]
+    xyz, apr = G.geraf_sample(geo.grid, geo.mode, seed, step, device=geo.ant.device)
+    is_mlp = isinstance(field, G.MLPField)
+    f, grad, a, saved = G.geraf_fields(field, xyz, keep_saved=is_mlp)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, ant_p, want_grad=False, want_refl=False)
+    alpha, T, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
+    tic("render")
+    s_p = G.geraf_render(xyz, grad, w, t_eff, ant_p, c_ant, geo.band)
+    toc("render")
+    bank.s[a0:a1].copy_(s_p)
+    tic("filter")
+    P, M, loss, dP = G.geraf_filter(bank.s, geo.ant, geo.band, geo.vox, target)
+    toc("filter")
+    tic("filter_backward")
+    g_p = G.geraf_filter_backward(ant_p, geo.band, geo.vox, M, dP)
+    toc("filter_backward")
+    tic("render_backward")
+    d_w, d_t, d_G = G.geraf_render_backward(xyz, grad, w, t_eff, ant_p, c_ant, geo.band, g_p)
+    toc("render_backward")
+    d_f, d_a, d_sc = G.geraf_blend_backward(f, a, alpha, T, geo.n_ray, geo.n_z, geo.sharpness, geo.a_tx, d_w, d_t)
+    d_params = None
+    if is_mlp:
+        tic("fields_backward")
+        d_params = G.geraf_fields_backward(field, xyz, saved, d_f, d_G, d_a)
+        toc("fields_backward")
+    res = StepResult(loss, d_params, d_sc, P)
+    res.bank = {"patch": k, "xyz": xyz, "grad": grad, "w": w, "t_eff": t_eff, "c_ant": c_ant, "M": M, "dP": dP,
+                "g": g_p, "d_w": d_w, "d_teff": d_t, "d_G": d_G}
+    return res
