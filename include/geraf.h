@@ -280,6 +280,23 @@ geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const ge
                                    float* g_s, void* stream);
 
 /*
+ * geraf_masked_loss — dynamic loss masking (section 6, "Dynamic loss
+ * masking") with the L2 heatmap loss (section 4, step 5): a voxel whose
+ * matched-filter response was high in an earlier call (history_v >= t_hi)
+ * but is low now (P_v < t_lo) is left out of the loss, m_v = 0, else m_v = 1;
+ *   loss = sum_v m_v (P_v - P*_v)^2,  dloss_dP_v = 2 m_v (P_v - P*_v),
+ * and then history_v = max(history_v, P_v) in place (a fresh history is all
+ * zeros). The paper gives no thresholds: t_hi and t_lo are absolute powers
+ * chosen by the caller, compared in FP32.
+ * P, target, history [n_vox] FP32 device arrays; loss: one double (device,
+ * overwritten); dloss_dP and mask [n_vox] (either may be NULL). The loss is
+ * summed in FP64 in a fixed order. ws: ws == NULL queries *ws_bytes.
+ */
+geraf_status geraf_masked_loss(const float* P, const float* target, float* history, int64_t n_vox, float t_hi,
+                               float t_lo, void* ws, size_t* ws_bytes, double* loss, float* dloss_dP, float* mask,
+                               void* stream);
+
+/*
  * geraf_chebyshev_order — the Chebyshev order K that the phasor sums use for
  * points (or voxels) xyz [3][n] against ant_xyz [3][n_ant] over `band`
  * (band->method honoured): *order = K (2..64) when the Chebyshev form runs,

@@ -423,6 +423,19 @@ def filter_backward(M, dP, ant, vox, band):
     return gr + 1j * gi
 
 
+def dynamic_mask(P, history, p_ref, rho_hi, rho_lo):
+    """Dynamic loss masking (section 6 "Dynamic loss masking"): a voxel whose
+    matched-filter response was high in an earlier iteration (history = the
+    running maximum of its earlier P >= rho_hi * p_ref) but is low now
+    (P < rho_lo * p_ref) is left out of the loss. Returns (mask [N] in {0, 1},
+    the updated history max(history, P)). The thresholds are relative to p_ref,
+    the maximum of the target heatmap (the paper gives no values)."""
+    P = np.asarray(P, np.float64)
+    H = np.asarray(history, np.float64)
+    drop = (H >= rho_hi * p_ref) & (P < rho_lo * p_ref)
+    return np.where(drop, 0.0, 1.0), np.maximum(H, P)
+
+
 def heatmap_loss(P, target, mask=None):
     """L2 heatmap loss (section 4, step 5): L = sum_v m_v (P_v - P*_v)^2 and dL/dP."""
     P = np.asarray(P, np.float64)

@@ -54,6 +54,7 @@ SIGNATURES = {
     "geraf_filter": [vp, vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp, vp, vp, vp],
     "geraf_filter_backward": [vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp],
     "geraf_chebyshev_order": [vp, i64, vp, i32, ctypes.POINTER(GerafBand), vp, szp, ctypes.POINTER(i32), vp],
+    "geraf_masked_loss": [vp, vp, vp, i64, f32, f32, vp, szp, vp, vp, vp, vp],
     "geraf_proposal_saved_bytes": [ctypes.POINTER(GerafProposal), szp],
     "geraf_proposal_density": [ctypes.POINTER(GerafProposal), vp, vp, vp, sz, vp],
     "geraf_sample_proposal": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, u64, u64, vp, vp, vp, vp],

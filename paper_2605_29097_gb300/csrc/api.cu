@@ -29,6 +29,8 @@ geraf_status filter_impl(const float*, const float*, int32_t, const geraf_band*,
                          const float*, const float*, void*, size_t*, float*, float*, double*, float*, cudaStream_t);
 geraf_status filter_backward_impl(const float*, int32_t, const geraf_band*, const float*, int64_t, const float*,
                                   const float*, void*, size_t*, float*, cudaStream_t);
+geraf_status masked_loss_impl(const float*, const float*, float*, int64_t, float, float, void*, size_t*, double*,
+                              float*, float*, cudaStream_t);
 geraf_status chebyshev_order_impl(const float*, int64_t, const float*, int32_t, const geraf_band*, void*, size_t*,
                                   int32_t*, cudaStream_t);
 geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
@@ -298,6 +300,16 @@ geraf_status geraf_filter_backward(const float* ant_xyz, int32_t n_ant, const ge
     REQUIRE(band, "filter_backward: band must not be NULL");
     if (ws) REQUIRE(ant_xyz && vox_xyz && M && d_P && g_s, "filter_backward: null input or output");
     return filter_backward_impl(ant_xyz, n_ant, band, vox_xyz, n_vox, M, d_P, ws, ws_bytes, g_s, S(stream));
+}
+
+geraf_status geraf_masked_loss(const float* P, const float* target, float* history, int64_t n_vox, float t_hi,
+                               float t_lo, void* ws, size_t* ws_bytes, double* loss, float* dloss_dP, float* mask,
+                               void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n_vox >= 1 && n_vox < (1ll << 31), "masked_loss: need 1 <= n_vox < 2^31");
+    if (ws) REQUIRE(P && target && history && loss, "masked_loss: null input or output");
+    return masked_loss_impl(P, target, history, n_vox, t_hi, t_lo, ws, ws_bytes, loss, dloss_dP, mask, S(stream));
 }
 
 geraf_status geraf_chebyshev_order(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,

@@ -1462,6 +1462,47 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     return check_launch("render_backward");
 }
 
+namespace {
+// dynamic loss mask, masked L2 loss (FP64 block partials), its gradient and
+// the running maximum of P, one voxel per thread
+__global__ void masked_loss_kernel(const float* __restrict__ P, const float* __restrict__ target,
+                                   float* __restrict__ hist, int64_t n, float t_hi, float t_lo,
+                                   float* __restrict__ mask, float* __restrict__ dP, double* __restrict__ blocks) {
+    __shared__ double red[256];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < n) {
+        const float p = P[i], h = hist[i];
+        const float m = (h >= t_hi && p < t_lo) ? 0.0f : 1.0f;
+        const float r = p - target[i];
+        l = (double)m * (double)r * (double)r;
+        if (dP) dP[i] = 2.0f * m * r;
+        if (mask) mask[i] = m;
+        hist[i] = fmaxf(h, p);
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) blocks[blockIdx.x] = red[0];
+}
+}  // namespace
+
+geraf_status masked_loss_impl(const float* P, const float* target, float* history, int64_t n_vox, float t_hi,
+                              float t_lo, void* ws, size_t* ws_bytes, double* loss, float* dloss_dP, float* mask,
+                              cudaStream_t st) {
+    const int blocks = (int)grid1d(n_vox, 256);
+    WsCarver c(ws);
+    double* part = c.take<double>(blocks);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "masked_loss: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    masked_loss_kernel<<<blocks, 256, 0, st>>>(P, target, history, n_vox, t_hi, t_lo, mask, dloss_dP, part);
+    sum_doubles<<<1, 256, 0, st>>>(part, blocks, loss);
+    return check_launch("masked_loss");
+}
+
 geraf_status chebyshev_order_impl(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
                                   const geraf_band* band, void* ws, size_t* ws_bytes, int32_t* order,
                                   cudaStream_t st) {

@@ -272,6 +272,23 @@ def geraf_filter(s, ant, band: Band, vox, target=None, mask=None):
     return P, torch.view_as_complex(M), loss, dP
 
 
+def geraf_masked_loss(P, target, history, t_hi: float, t_lo: float):
+    """Dynamic loss masking + masked L2 loss; `history` (running max of P) is
+    updated in place. -> (loss 0-d float64, dloss_dP [n], mask [n])."""
+    _req(P, "P"); _req(target, "target"); _req(history, "history")
+    n = P.shape[-1]
+    dev = P.device
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    dP = torch.empty(n, dtype=torch.float32, device=dev)
+    mask = torch.empty(n, dtype=torch.float32, device=dev)
+    L = _lib.lib()
+    args = lambda wsp, b: L.geraf_masked_loss(_p(P), _p(target), _p(history), n, float(t_hi), float(t_lo), wsp, b,
+                                              _p(loss), _p(dP), _p(mask), _stream())
+    ws, wsz = _workspace(args, dev)
+    check(args(_p(ws), ctypes.byref(wsz)))
+    return loss, dP, mask
+
+
 def geraf_filter_backward(ant, band: Band, vox, M, d_P):
     """Adjoint of |matched filter| -> g_s complex64 [n_ant, n_f]."""
     Mr = _sig(M, "M")

@@ -87,9 +87,24 @@ class StepResult:
     P: torch.Tensor
 
 
-def forward_backward(geo: Geometry, field, target: torch.Tensor, seed: int, step: int, timers=None) -> StepResult:
+class DynamicMask:
+    """State of the dynamic loss masking (section 6): the running maximum of
+    each voxel's rendered power over earlier steps, and the two thresholds,
+    taken relative to the target's maximum (the paper gives no values): high
+    = rho_hi * max(target), low = rho_lo * max(target)."""
+
+    def __init__(self, target: torch.Tensor, rho_hi=0.5, rho_lo=0.1):
+        p_ref = float(target.max())
+        self.t_hi = float(np.float32(rho_hi * p_ref))
+        self.t_lo = float(np.float32(rho_lo * p_ref))
+        self.history = torch.zeros_like(target)
+
+
+def forward_backward(geo: Geometry, field, target: torch.Tensor, seed: int, step: int, timers=None,
+                     dyn_mask: Optional[DynamicMask] = None) -> StepResult:
     """One hot-path pass (all forward steps and their adjoints). `timers` may map
-    a step name to a pair of CUDA events recorded around that call."""
+    a step name to a pair of CUDA events recorded around that call; with
+    `dyn_mask` the loss leaves out the voxels the dynamic mask drops."""
     def tic(name):
         if timers is not None and name in timers:
             timers[name][0].record()
@@ -108,7 +123,12 @@ def forward_backward(geo: Geometry, field, target: torch.Tensor, seed: int, step
     s = G.geraf_render(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band)
     toc("render")
     tic("filter")
-    P, M, loss, dP = G.geraf_filter(s, geo.ant, geo.band, geo.vox, target)
+    mask = None
+    if dyn_mask is None:
+        P, M, loss, dP = G.geraf_filter(s, geo.ant, geo.band, geo.vox, target)
+    else:
+        P, M, _, _ = G.geraf_filter(s, geo.ant, geo.band, geo.vox)
+        loss, dP, mask = G.geraf_masked_loss(P, target, dyn_mask.history, dyn_mask.t_hi, dyn_mask.t_lo)
     toc("filter")
     tic("filter_backward")
     g_s = G.geraf_filter_backward(geo.ant, geo.band, geo.vox, M, dP)
@@ -122,7 +142,9 @@ def forward_backward(geo: Geometry, field, target: torch.Tensor, seed: int, step
         tic("fields_backward")
         d_params = G.geraf_fields_backward(field, xyz, saved, d_f, d_G, d_a)
         toc("fields_backward")
-    return StepResult(loss, d_params, d_sc, P)
+    res = StepResult(loss, d_params, d_sc, P)
+    res.mask = mask
+    return res
 
 
 def launches_per_step(field, band) -> int:

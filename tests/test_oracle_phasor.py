@@ -276,3 +276,23 @@ def test_flat_plate_specular_response(oracle):
     np.testing.assert_allclose(slope, -4 * np.pi * D * band.df / C, rtol=0.02)
     mags = np.abs(s).sum(1)
     assert int(np.argmax(mags)) == centre
+
+
+def test_dynamic_mask_cases(oracle):
+    """Each case of the masking rule, and the masked loss against the plain
+    loss on the kept voxels only."""
+    p_ref, hi, lo = 10.0, 0.5, 0.1
+    P = np.array([0.5, 0.5, 6.0, 0.5, 0.99, 1.0])
+    H = np.array([0.0, 5.0, 9.0, 4.99, 7.0, 7.0])
+    m, H2 = oracle.dynamic_mask(P, H, p_ref, hi, lo)
+    # never high -> kept; high before and low now -> dropped; high now -> kept;
+    # just below the high threshold -> kept; just below / at the low threshold
+    np.testing.assert_array_equal(m, [1, 0, 1, 1, 0, 1])
+    np.testing.assert_array_equal(H2, [0.5, 5.0, 9.0, 4.99, 7.0, 7.0])
+    target = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 6.0])
+    L, dP = oracle.heatmap_loss(P, target, m)
+    keep = m > 0
+    L_keep, dP_keep = oracle.heatmap_loss(P[keep], target[keep])
+    assert abs(L - L_keep) < 1e-12
+    np.testing.assert_array_equal(dP[~keep], 0.0)
+    np.testing.assert_allclose(dP[keep], dP_keep)
