@@ -264,30 +264,41 @@ __global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a)
     const float* hsv = a.saved + (int64_t)(g.NH - 1) * g.n * 4 * MW;
     const float* asv = a.saved + (int64_t)g.NH * g.n * 4 * MW;
     float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
-    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
-        for (int p = half; p < MTP; p += 2) {
-            const int64_t j = (int64_t)tile * MTP + p;
-            if (j >= g.n) break;
-            const float df = a.d_sdf ? a.d_sdf[j] : 0.0f;
-            const float av = asv[j];
-            const float dl = a.d_refl ? a.d_refl[j] * av * (1.0f - av) : 0.0f;
-            float dG[3];
+    constexpr int R = 8;                                   // points per thread per round, loads in flight
+    for (int64_t base = (int64_t)blockIdx.x * 2 * R; base < g.n; base += (int64_t)gridDim.x * 2 * R) {
+        float df[R], dl[R], dG[R][3], h0[R], hd[R][3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) dG[d] = a.d_grad ? a.d_grad[(int64_t)d * g.n + j] : 0.0f;
-            const float* h = hsv + j * 4 * MW;
-            const float h0 = h[u];
-            const float sg = sigm(g.beta * h0);
-            const float z = softplus_b(h0, g.beta);
-            gw0 += df * z;
-            gw1 += dl * z;
-            float* zb = a.zbar + j * 4 * MW;
-            zb[u] = w0 * df + w1 * dl;
+        for (int r = 0; r < R; ++r) {
+            const int64_t j = base + 2 * r + half;
+            const bool ok = j < g.n;
+            const int64_t jj = ok ? j : 0;
+            const float* h = hsv + jj * 4 * MW;
+            df[r] = ok && a.d_sdf ? a.d_sdf[jj] : 0.0f;
+            const float av = asv[jj];
+            dl[r] = ok && a.d_refl ? a.d_refl[jj] * av * (1.0f - av) : 0.0f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                gw0 += dG[d] * sg * h[(d + 1) * MW + u];
-                zb[(d + 1) * MW + u] = w0 * dG[d];
+                dG[r][d] = ok && a.d_grad ? a.d_grad[(int64_t)d * g.n + jj] : 0.0f;
+                hd[r][d] = h[(d + 1) * MW + u];
             }
-            if (u == 0) { gb0 += df; gb1 += dl; }
+            h0[r] = h[u];
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t j = base + 2 * r + half;
+            if (j >= g.n) continue;
+            const float sg = sigm(g.beta * h0[r]);
+            const float z = softplus_b(h0[r], g.beta);
+            gw0 += df[r] * z;
+            gw1 += dl[r] * z;
+            float* zb = a.zbar + j * 4 * MW;
+            zb[u] = w0 * df[r] + w1 * dl[r];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                gw0 += dG[r][d] * sg * hd[r][d];
+                zb[(d + 1) * MW + u] = w0 * dG[r][d];
+            }
+            if (u == 0) { gb0 += df[r]; gb1 += dl[r]; }
         }
     }
     red[t] = gw0;

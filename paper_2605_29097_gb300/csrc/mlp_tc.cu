@@ -313,28 +313,42 @@ __global__ void __launch_bounds__(256) mlp_tc_head_bwd_kernel(const TcBwdArgs a)
     const float* hsv = a.saved + (int64_t)(g.NH - 1) * g.n * 4 * TW;
     const float* asv = a.saved + (int64_t)g.NH * g.n * 4 * TW;
     float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
-    const int64_t n_pairs = (g.n + 1) / 2;
-    for (int64_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
-        const int64_t j = 2 * q + half;
-        if (j >= g.n) continue;
-        const float df = a.d_sdf ? a.d_sdf[j] : 0.0f;
-        const float av = asv[j];
-        const float dl = a.d_refl ? a.d_refl[j] * av * (1.0f - av) : 0.0f;
-        const float* h = hsv + j * 4 * TW;
-        const float h0 = h[u];
-        const float sg = sgm(g.beta * h0);
-        const float z = bf16r(sp_b(h0, g.beta));
-        gw0 += df * z;
-        gw1 += dl * z;
-        float* zb = a.zbar + j * 4 * TW;
-        zb[u] = w0 * df + w1 * dl;
+    constexpr int R = 8;                                   // points per thread per round, loads in flight
+    for (int64_t base = (int64_t)blockIdx.x * 2 * R; base < g.n; base += (int64_t)gridDim.x * 2 * R) {
+        float df[R], dl[R], dG[R][3], h0[R], hd[R][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float dG = a.d_grad ? a.d_grad[(int64_t)d * g.n + j] : 0.0f;
-            gw0 += dG * bf16r(sg * h[(d + 1) * TW + u]);
-            zb[(d + 1) * TW + u] = w0 * dG;
+        for (int r = 0; r < R; ++r) {
+            const int64_t j = base + 2 * r + half;
+            const bool ok = j < g.n;
+            const int64_t jj = ok ? j : 0;
+            const float* h = hsv + jj * 4 * TW;
+            df[r] = ok && a.d_sdf ? a.d_sdf[jj] : 0.0f;
+            const float av = asv[jj];
+            dl[r] = ok && a.d_refl ? a.d_refl[jj] * av * (1.0f - av) : 0.0f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                dG[r][d] = ok && a.d_grad ? a.d_grad[(int64_t)d * g.n + jj] : 0.0f;
+                hd[r][d] = h[(d + 1) * TW + u];
+            }
+            h0[r] = h[u];
         }
-        if (u == 0) { gb0 += df; gb1 += dl; }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t j = base + 2 * r + half;
+            if (j >= g.n) continue;
+            const float sg = sgm(g.beta * h0[r]);
+            const float z = bf16r(sp_b(h0[r], g.beta));
+            gw0 += df[r] * z;
+            gw1 += dl[r] * z;
+            float* zb = a.zbar + j * 4 * TW;
+            zb[u] = w0 * df[r] + w1 * dl[r];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                gw0 += dG[r][d] * bf16r(sg * hd[r][d]);
+                zb[(d + 1) * TW + u] = w0 * dG[r][d];
+            }
+            if (u == 0) { gb0 += df[r]; gb1 += dl[r]; }
+        }
     }
     red[t] = gw0;
     red[256 + t] = gw1;
