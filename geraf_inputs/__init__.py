@@ -82,6 +82,36 @@ class Band:
     n_f: int
 
 
+def fmcw_band(f_start=77e9, slope=70.15e12, fs=1.25e6, n_samples=64) -> Band:
+    """FMCW chirp seen as stepped frequencies: ADC sample n at t_n = n / fs has
+    the instantaneous frequency f_start + slope * t_n (section 3, Eq. fmcw).
+    Defaults are the paper's radar (App. C): 77 GHz start, 70.15 MHz/us slope,
+    64 samples at 1.25 Msps."""
+    return Band(f0=float(f_start), df=float(slope / fs), n_f=int(n_samples))
+
+
+def multi_plane_array(n_planes, nx, ny, pitch, radius, center=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Virtual arrays on n_planes scanning planes around an object (App. C: the
+    object turns on a platform in front of a radar the arm sweeps over a 2-D
+    aperture): plane m is an nx x ny array at `pitch`, its centre at distance
+    `radius` from `center` in direction (sin t_m, 0, cos t_m), t_m = 2 pi m /
+    n_planes, facing the centre (array axes: horizontal (cos t_m, 0, -sin t_m)
+    and vertical (0, 1, 0)). FP32 SoA [3, n_planes*nx*ny], plane-major."""
+    ix = np.arange(nx, dtype=np.float64) - (nx - 1) / 2.0
+    iy = np.arange(ny, dtype=np.float64) - (ny - 1) / 2.0
+    X, Y = np.meshgrid(ix * pitch, iy * pitch, indexing="xy")
+    X, Y = X.reshape(-1), Y.reshape(-1)
+    c = np.asarray(center, np.float64)
+    out = []
+    for m in range(n_planes):
+        t = 2.0 * np.pi * m / n_planes
+        nrm = np.array([np.sin(t), 0.0, np.cos(t)])
+        hor = np.array([np.cos(t), 0.0, -np.sin(t)])
+        ver = np.array([0.0, 1.0, 0.0])
+        out.append(c[:, None] + radius * nrm[:, None] + hor[:, None] * X + ver[:, None] * Y)
+    return np.concatenate(out, axis=1).astype(np.float32)
+
+
 def band(f_lo=77e9, f_hi=81e9, n_f=32) -> Band:
     """n_f frequencies spanning [f_lo, f_hi], both end points included."""
     return Band(f0=float(f_lo), df=float((f_hi - f_lo) / (n_f - 1)), n_f=int(n_f))

@@ -317,3 +317,35 @@ def test_sphere_and_point_reflector_chain(G, oracle):
     # FP32 SDF rounding enters through exp(s f) with s f up to ~60: looser bound for the whole chain
     assert rel_l2(host(P), oP2) < 1e-4
     assert int(np.argmax(host(P))) == int(np.argmax(oP2))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_fmcw_multi_plane_scan(G, oracle, method):
+    """The paper's radar read as stepped frequencies (64 chirp samples from
+    77 GHz at 70.15 MHz/us, 1.25 Msps) on 8 scanning planes of 6x5 antennas
+    around a 10 cm cube at 0.4 m: all four phasor sums against the oracle."""
+    rng = np.random.default_rng(21)
+    b = gi.fmcw_band()
+    ant = gi.multi_plane_array(8, 6, 5, 0.002, 0.4)
+    xyz, grad, w, t_eff = _scene_points(rng, 2500, (0.0, 0.0, 0.0), 0.05)
+    c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
+    band = _band(G, b, method)
+    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), band, True)
+    G.geraf_poll_device_error()
+    assert rel_l2(host(s), oracle.render(xyz, grad, w, t_eff, ant, c_ant, b)) < TOL
+    g = gi.complex_normal(rng, (ant.shape[1], b.n_f)).astype(np.complex64)
+    d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), band,
+                                            torch.as_tensor(g, device="cuda"))
+    ow, ot, og = oracle.render_backward(xyz, grad, w, t_eff, ant, c_ant, b, g)
+    assert rel_l2(host(d_w), ow) < TOL and rel_l2(host(d_t), ot) < TOL and rel_l2(host(d_g), og) < 3 * TOL
+    vox = (rng.uniform(-0.05, 0.05, (3, 1500))).astype(np.float32)
+    sv = gi.complex_normal(rng, (ant.shape[1], b.n_f)).astype(np.complex64)
+    P, M, _, _ = G.geraf_filter(torch.as_tensor(sv, device="cuda"), cu(ant), band, cu(vox))
+    oM, oP = oracle.filter_forward(sv, ant, vox, b)
+    assert rel_l2(host(M), oM) < TOL
+    d_P = rng.standard_normal(vox.shape[1]).astype(np.float32)
+    gs = G.geraf_filter_backward(cu(ant), band, cu(vox), M, cu(d_P))
+    G.geraf_poll_device_error()
+    assert rel_l2(host(gs), oracle.filter_backward(host(M), d_P, ant, vox, b)) < TOL
+    if method == 2:
+        assert G.geraf_chebyshev_order(cu(xyz), cu(ant), band) > 0

@@ -296,3 +296,30 @@ def test_dynamic_mask_cases(oracle):
     assert abs(L - L_keep) < 1e-12
     np.testing.assert_array_equal(dP[~keep], 0.0)
     np.testing.assert_allclose(dP[keep], dP_keep)
+
+
+def test_fmcw_band_and_multi_plane_scan_geometry():
+    """The chirp read as stepped frequencies reproduces the paper's radar
+    (App. C): 56.12 MHz per ADC sample, 3.59 GHz over 64 samples, 4 cm range
+    resolution; scanning planes sit on a circle around the object, evenly
+    spaced, each facing it."""
+    rc = _radar_constants()
+    b = gi.fmcw_band()
+    assert b.f0 == rc["start_frequency_hz"] and b.n_f == rc["adc_samples"]
+    np.testing.assert_allclose(b.df, rc["chirp_slope_hz_per_s"] / rc["sample_rate_sps"])
+    np.testing.assert_allclose(b.n_f * b.df, rc["usable_bandwidth_hz"], rtol=2e-3)
+    np.testing.assert_allclose(299792458.0 / (2 * b.n_f * b.df), rc["range_resolution_m"], rtol=0.05)
+    n_planes, nx, ny, pitch, radius = 8, 5, 3, 0.002, 0.4
+    ctr = np.array([0.0, 0.0, 0.0])
+    A = gi.multi_plane_array(n_planes, nx, ny, pitch, radius, ctr).astype(np.float64)
+    assert A.shape == (3, n_planes * nx * ny)
+    P = A.reshape(3, n_planes, nx * ny)
+    mid = P.mean(2)                                               # plane centres
+    np.testing.assert_allclose(np.linalg.norm(mid[[0, 2]], axis=0), radius, rtol=1e-6)
+    ang = np.unwrap(np.arctan2(mid[0], mid[2]))
+    np.testing.assert_allclose(np.diff(ang), 2 * np.pi / n_planes, atol=1e-6)
+    for m in range(n_planes):
+        d = P[:, m] - mid[:, m:m + 1]
+        nrm = -mid[:, m] / np.linalg.norm(mid[:, m])
+        np.testing.assert_allclose(d.T @ nrm, 0.0, atol=1e-7)     # the plane faces the centre
+        np.testing.assert_allclose(np.sort(np.linalg.norm(d[:, :1] - d, axis=0))[1], pitch, rtol=1e-5)
