@@ -362,6 +362,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
     ap.add_argument("--no-train", action="store_true", help="skip the training-step comparison")
+    ap.add_argument("--phasor", default="auto", choices=["auto", "recurrence", "chebyshev"],
+                    help="how the phasor sums step across the bins (default: by the number of bins)")
     ap.add_argument("--mlp-bench", type=int, default=0, metavar="N_PTS",
                     help="time only the fields kernels on N_PTS points and exit")
     args = ap.parse_args()
@@ -393,6 +395,10 @@ def main():
 
     wl = gi.workload(args.workload)
     geo = PL.make_geometry(wl, dev)
+    if args.phasor != "auto":
+        import dataclasses
+        meth = G.PHASOR_RECURRENCE if args.phasor == "recurrence" else G.PHASOR_CHEBYSHEV
+        geo = dataclasses.replace(geo, band=G.Band(geo.band.f0, geo.band.df, geo.band.n_f, meth))
     spec = gi.MLPSpec()
     seeds = replica_seeds(rank)
     params_np = gi.mlp_init(spec, seed=seeds["mlp"])
