@@ -104,12 +104,55 @@ struct TcFwdArgs {
     int* err;
 };
 
-// shared memory: W tiles (BF16), X tile (BF16), biases and head (FP32), barrier, TMEM slot
-__global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs a) {
+// 8x8 transpose of 16-bit values across the 8 lanes of each aligned group of
+// 8 lanes: on entry lane i of the group holds row i (p[k] = elements 2k and
+// 2k + 1, the first in the low half), on exit it holds column i. Three
+// exchange stages between lanes i and i ^ 4, i ^ 2, i ^ 1.
+__device__ __forceinline__ void transpose8x8_b16(uint32_t (&p)[4]) {
+    const int i = threadIdx.x & 7;
+    {
+        const bool hi = (i & 4) != 0;
+        uint32_t s0 = hi ? p[0] : p[2], s1 = hi ? p[1] : p[3];
+        s0 = __shfl_xor_sync(0xffffffffu, s0, 4);
+        s1 = __shfl_xor_sync(0xffffffffu, s1, 4);
+        if (hi) { p[0] = s0; p[1] = s1; } else { p[2] = s0; p[3] = s1; }
+    }
+    {
+        const bool hi = (i & 2) != 0;
+        uint32_t s0 = hi ? p[0] : p[1], s1 = hi ? p[2] : p[3];
+        s0 = __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 = __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (hi) { p[0] = s0; p[2] = s1; } else { p[1] = s0; p[3] = s1; }
+    }
+    {
+        const bool hi = (i & 1) != 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w = __shfl_xor_sync(0xffffffffu, p[k], 1);
+            p[k] = hi ? ((p[k] & 0xFFFF0000u) | (w >> 16)) : ((p[k] & 0xFFFFu) | (w << 16));
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+
+constexpr int FTHREADS = 512;     // 16 warps: 4 TMEM lane quarters x 4 column chunks of 32
+
+// Forward, two 32-point tiles in flight per CTA (accumulators in TMEM columns
+// 0..127 and 128..255): while the epilogue of one tile runs, the MMAs of the
+// other execute. Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (units)
+// and columns 32 (w / 4) .. + 31 (8 points x 4 streams) of its tile, adds the
+// bias, applies softplus / sigmoid(beta h), saves the FP32 pre-activations and
+// writes the next BF16 operand as 16-byte rows (one 8x8 transpose per block
+// of 8 columns across each group of 8 lanes).
+__global__ void __launch_bounds__(FTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcGeom& g = a.g;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    // layout
     unsigned char* wt[4];
     uint32_t off = 0;
     for (int l = 0; l < g.NH; ++l) {
@@ -117,96 +160,108 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs
         off += (uint32_t)TW * (l == 0 ? g.K0p : TW) * 2u;
     }
     off = (off + 1023u) & ~1023u;
-    unsigned char* xt = smem + off;                        // [128 columns][128 K] BF16
-    off += TCOL * TW * 2u;
+    unsigned char* xt[2] = {smem + off, smem + off + TCOL * TW * 2u};   // [128 columns][128 K] BF16 each
+    off += 2u * TCOL * TW * 2u;
     float* bias = reinterpret_cast<float*>(smem + off);    // [NH][128]
     off += g.NH * TW * 4u;
     float* head = reinterpret_cast<float*>(smem + off);    // W_f[128], W_a[128], b_f, b_a
     off += (2 * TW + 2) * 4u;
     off = (off + 7u) & ~7u;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + off);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + off + 8);
-    int* abort_flag = reinterpret_cast<int*>(smem + off + 12);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + off);           // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + off + 16);
+    int* abort_flag = reinterpret_cast<int*>(smem + off + 20);
 
-    // weights -> BF16 K-major tiles (encoding layer zero-padded to K0p)
     for (int l = 0; l < g.NH; ++l) {
         const int K = l == 0 ? g.K0 : TW, Kp = l == 0 ? g.K0p : TW;
         const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
         const float* W = a.params + g.off_w[l];
-        for (int i = t; i < TW * Kp; i += TTHREADS) {
+        for (int i = t; i < TW * Kp; i += FTHREADS) {
             const int u = i / Kp, k = i - u * Kp;
             st_bf16(wt[l], tc::kmajor_offset(u, k, TLBO, sbo), k < K ? W[u * K + k] : 0.0f);
         }
-        for (int i = t; i < TW; i += TTHREADS) bias[l * TW + i] = a.params[g.off_b[l] + i];
+        for (int i = t; i < TW; i += FTHREADS) bias[l * TW + i] = a.params[g.off_b[l] + i];
     }
-    for (int i = t; i < 2 * TW; i += TTHREADS) head[i] = a.params[g.off_w[g.NH] + i];
+    for (int i = t; i < 2 * TW; i += FTHREADS) head[i] = a.params[g.off_w[g.NH] + i];
     if (t < 2) head[2 * TW + t] = a.params[g.off_b[g.NH] + t];
     if (t == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
     const uint32_t idesc = tc::idesc_bf16(128, TCOL);
-    uint32_t phase = 0;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    const int lq = warp & 3, cc = warp >> 2;
+    const int u = 32 * lq + lane;                         // unit = TMEM lane
+    const int n_pairs = (g.n_tiles + 1) / 2;
 
-    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
-        const int64_t j0 = (int64_t)tile * TTP;
-        // positional encoding and its x-derivatives -> X (BF16, K = K0p)
+    auto issue = [&](int s, int l) {                      // thread 0: layer l of tile slot s
+        const int Kp = l == 0 ? g.K0p : TW;
+        const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
+        const uint32_t wa = smem_u32(wt[l]), xa = smem_u32(xt[s]);
+        for (int q = 0; q < Kp / 16; ++q)
+            tc::mma_bf16(tbase + 128u * s, tc::smem_desc(wa + q * 256u, TLBO, sbo),
+                         tc::smem_desc(xa + q * 256u, TLBO, sbo), idesc, q > 0 ? 1u : 0u);
+        tc::mma_commit(&bar[s]);
+    };
+
+    for (int pair = blockIdx.x; pair < n_pairs; pair += gridDim.x) {
+        const int nslot = (2 * pair + 1 < g.n_tiles) ? 2 : 1;
+        // encoding of both tiles -> X (BF16, K = K0p; padding columns zero)
         {
             const uint32_t sbo0 = (uint32_t)(g.K0p / 8) * 128u;
-            for (int i = t; i < TCOL * (g.K0p - g.K0); i += TTHREADS) {
-                const int c = i / (g.K0p - g.K0), k = g.K0 + i % (g.K0p - g.K0);
-                st_bf16(xt, tc::kmajor_offset(c, k, TLBO, sbo0), 0.0f);
+            const int padw = g.K0p - g.K0;
+            for (int i = t; i < nslot * TCOL * padw; i += FTHREADS) {
+                const int s = i / (TCOL * padw), r = i - s * TCOL * padw;
+                const int c = r / padw, k = g.K0 + r % padw;
+                st_bf16(xt[s], tc::kmajor_offset(c, k, TLBO, sbo0), 0.0f);
             }
-            if (t < 3 * TTP) {
-                const int p = t / 3, d = t - 3 * (t / 3);
-                int64_t j = j0 + p;
+            if (t < nslot * 3 * TTP) {
+                const int s = t / (3 * TTP), r = t - s * 3 * TTP;
+                const int p = r / 3, d = r - 3 * (r / 3);
+                int64_t j = (int64_t)(2 * pair + s) * TTP + p;
                 if (j >= g.n) j = g.n - 1;
-                encode_axis(g, a.xyz[d * g.n + j], d, [&](int f, int s, float v) {
-                    st_bf16(xt, tc::kmajor_offset(4 * p + s, f, TLBO, sbo0), v);
+                encode_axis(g, a.xyz[d * g.n + j], d, [&](int f, int st, float v) {
+                    st_bf16(xt[s], tc::kmajor_offset(4 * p + st, f, TLBO, sbo0), v);
                 });
             }
         }
-        for (int l = 0; l < g.NH; ++l) {
-            const int Kp = l == 0 ? g.K0p : TW;
-            const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (t == 0) {
-                const uint32_t wa = smem_u32(wt[l]), xa = smem_u32(xt);
-                for (int s = 0; s < Kp / 16; ++s)
-                    tc::mma_bf16(tbase, tc::smem_desc(wa + s * 256u, TLBO, sbo), tc::smem_desc(xa + s * 256u, TLBO, sbo),
-                                 idesc, s > 0 ? 1u : 0u);
-                tc::mma_commit(bar);
-            }
-            const bool ok = mbar_wait(bar, phase);
-            phase ^= 1u;
-            if (!ok) atomicOr(abort_flag, 1);
-            tc::fence_after_sync();
-            __syncthreads();
-            if (*abort_flag) break;
-            // epilogue: thread = unit u of TMEM lane u; 32 columns (8 points) per load
-            const int u = warp * 32 + lane;
-            const float bu = bias[l * TW + u];
-            for (int cc = 0; cc < 4; ++cc) {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0)
+            for (int s = 0; s < nslot; ++s) issue(s, 0);
+        for (int s = 0; s < nslot; ++s) pending[s] = true;
+        for (int l = 0; l < g.NH && !*abort_flag; ++l) {
+            for (int s = 0; s < nslot; ++s) {
+                const bool ok = mbar_wait(&bar[s], phase[s]);
+                if (ok) phase[s] ^= 1u;
+                pending[s] = !ok;                 // a timed-out MMA is still in flight
+                if (!ok) atomicOr(abort_flag, 1);
+                tc::fence_after_sync();
+                __syncthreads();
+                if (*abort_flag) break;
+                const int64_t j0 = (int64_t)(2 * pair + s) * TTP;
                 float r[32];
-                tc::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+                tc::tmem_ld32(tbase + 128u * s + ((uint32_t)(32 * lq) << 16) + (uint32_t)(32 * cc), r);
+                const float bu = bias[l * TW + u];
+                float v[32];
 #pragma unroll
                 for (int pp = 0; pp < 8; ++pp) {
-                    const int p = cc * 8 + pp;
                     const float h = r[4 * pp] + bu;
                     const float sg = sgm(g.beta * h);
-                    const float v[4] = {sp_b(h, g.beta), sg * r[4 * pp + 1], sg * r[4 * pp + 2], sg * r[4 * pp + 3]};
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) st_bf16(xt, tc::kmajor_offset(4 * p + s, u, TLBO, 16u * 128u), v[s]);
-                    const int64_t j = j0 + p;
+                    v[4 * pp] = sp_b(h, g.beta);
+                    v[4 * pp + 1] = sg * r[4 * pp + 1];
+                    v[4 * pp + 2] = sg * r[4 * pp + 2];
+                    v[4 * pp + 3] = sg * r[4 * pp + 3];
+                    const int64_t j = j0 + 8 * cc + pp;
                     if (a.saved && j < g.n) {
                         float* dst = a.saved + (((int64_t)l * g.n + j) * 4) * TW + u;
                         dst[0] = h;
@@ -215,18 +270,36 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs
                         dst[3 * TW] = r[4 * pp + 3];
                     }
                 }
+                // next operand: 4 blocks of 8 columns, each an 8x8 transpose over 8 lanes
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    uint32_t q[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) q[k] = pack_bf16x2(v[8 * b + 2 * k], v[8 * b + 2 * k + 1]);
+                    transpose8x8_b16(q);
+                    const int c = 32 * cc + 8 * b + (lane & 7);
+                    const int u0 = 32 * lq + 8 * (lane >> 3);
+                    *reinterpret_cast<uint4*>(xt[s] + tc::kmajor_offset(c, u0, TLBO, 16u * 128u)) =
+                        make_uint4(q[0], q[1], q[2], q[3]);
+                }
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (l + 1 < g.NH) {
+                    if (t == 0) issue(s, l + 1);
+                    pending[s] = true;
+                }
             }
-            tc::fence_before_sync();
         }
         if (*abort_flag) break;
-        __syncthreads();
-        // head from the last BF16 activations, thread = column
-        {
-            const int c = t, p = c >> 2, s = c & 3;
-            const int64_t j = j0 + p;
+        // head from the last BF16 activations of both tiles, thread = (tile, column)
+        if (t < nslot * TCOL) {
+            const int s = t / TCOL, c = t - s * TCOL, p = c >> 2, st = c & 3;
+            const int64_t j = (int64_t)(2 * pair + s) * TTP + p;
             float v0 = 0.0f, v1 = 0.0f;
             for (int u8 = 0; u8 < TW; u8 += 8) {
-                const uint4 raw = *reinterpret_cast<const uint4*>(xt + tc::kmajor_offset(c, u8, TLBO, 16u * 128u));
+                const uint4 raw = *reinterpret_cast<const uint4*>(xt[s] + tc::kmajor_offset(c, u8, TLBO, 16u * 128u));
                 const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&raw);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
@@ -236,36 +309,37 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs
                 }
             }
             if (j < g.n) {
-                if (s == 0) {
+                if (st == 0) {
                     a.sdf[j] = v0 + head[2 * TW];
                     const float av = sgm(v1 + head[2 * TW + 1]);
                     if (a.refl) a.refl[j] = av;
                     if (a.saved) a.saved[(int64_t)g.NH * g.n * 4 * TW + j] = av;
                 } else if (a.grad) {
-                    a.grad[(int64_t)(s - 1) * g.n + j] = v0;
+                    a.grad[(int64_t)(st - 1) * g.n + j] = v0;
                 }
             }
         }
-        __syncthreads();   // the next tile's encoding overwrites the tile the head read
+        __syncthreads();   // the next pair's encoding overwrites the tiles the head read
     }
     if (*abort_flag && t == 0) {
         atomicOr(a.err, 1);
-        mbar_wait(bar, phase ^ 1u, 100000000ull);   // bounded: let the timed-out MMA finish before TMEM is freed
+        for (int s = 0; s < 2; ++s)      // bounded: let timed-out or issued MMAs finish before TMEM is freed
+            if (pending[s]) mbar_wait(&bar[s], phase[s], 100000000ull);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tbase, 128);
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
 size_t tc_fwd_smem(const TcGeom& g) {
     size_t off = 0;
     for (int l = 0; l < g.NH; ++l) off += (size_t)TW * (l == 0 ? g.K0p : TW) * 2;
     off = (off + 1023) & ~(size_t)1023;
-    off += TCOL * TW * 2;
+    off += 2 * TCOL * TW * 2;
     off += g.NH * TW * 4 + (2 * TW + 2) * 4;
     off = (off + 7) & ~(size_t)7;
-    return off + 16 + 1024;   // barrier, TMEM slot, abort flag; slack for the 1024-byte base alignment
+    return off + 24 + 1024;   // barriers, TMEM slot, abort flag; slack for the 1024-byte base alignment
 }
 
 // ------------------------------------------------------- adjoint (BF16 network)
@@ -588,9 +662,9 @@ geraf_status mlp_tc_forward_impl(const geraf_field_desc* d, const float* xyz, in
         attr = true;
     }
     int n_cta = device_sm_count();
-    if (n_cta > g.n_tiles) n_cta = g.n_tiles;
+    if (n_cta > (g.n_tiles + 1) / 2) n_cta = (g.n_tiles + 1) / 2;
     TcFwdArgs a{g, d->params, xyz, sdf, grad, refl, static_cast<float*>(saved), device_error_word()};
-    mlp_tc_fwd_kernel<<<n_cta, TTHREADS, smem, st>>>(a);
+    mlp_tc_fwd_kernel<<<n_cta, FTHREADS, smem, st>>>(a);
     return cuda_status(cudaGetLastError(), "fields(mlp bf16)");
 }
 
