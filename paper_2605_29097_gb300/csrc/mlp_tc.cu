@@ -453,7 +453,7 @@ __host__ __device__ inline BwdLayout bwd_layout(int kin) {
     L.zB = off;  off += (uint32_t)kin * BCOL * 2u;          // Z: rows k, K = 64 columns
     L.zs = off;  off += BCOL * TW * 4u;                     // FP32 staging [64][128]
     L.hsb = off; off += BCOL * TW * 4u;                     // FP32 staging [64][128]
-    L.bar = off; off += 16u;
+    L.bar = off; off += 16u + 4u * TW * 4u;                 // barrier, TMEM slot, abort flag, bias partials
     L.total = off;
     return L;
 }
@@ -461,14 +461,16 @@ __host__ __device__ inline BwdLayout bwd_layout(int kin) {
 // Rows c = 4 p + s of a [n][4][128] FP32 array for points j0 + p (p < 16)
 // into a [64][128] shared tile, all in flight; rows of points >= n read as 0.
 __device__ __forceinline__ void stage64(float* dst, const float* src, int64_t j0, int64_t n) {
-    for (int i = threadIdx.x; i < BCOL * (TW / 4); i += TTHREADS) {
+    for (int i = threadIdx.x; i < BCOL * (TW / 4); i += blockDim.x) {
         const int c = i >> 5, q = i & 31;
         const bool ok = j0 + (c >> 2) < n;
         cp_async16(dst + c * TW + 4 * q, ok ? src + (j0 * 4 + c) * TW + 4 * q : src, ok ? 16 : 0);
     }
 }
 
-__global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcBwdArgs a) {
+constexpr int BTHREADS = 512;    // 16 warps: thread = (unit, chunk of 4 points); warp = (lane quarter, chunk)
+
+__global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcBwdArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw;
     const TcGeom& g = a.g;
@@ -476,6 +478,9 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
     const int kin = li == 0 ? g.K0p : TW;     // padded input width (MMA N of dW, M of the input adjoint)
     const int K = li == 0 ? g.K0 : TW;        // true input width
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int uu = t & (TW - 1);              // unit (Hb) or input unit (Z) of this thread
+    const int ch = t >> 7;                    // chunk: points 4 ch .. 4 ch + 3 = columns 16 ch .. 16 ch + 15
+    const int lq = warp & 3;                  // TMEM lane quarter of this warp (lanes 32 lq .. + 31)
     const BwdLayout L = bwd_layout(kin);
     unsigned char* wt = smem + L.wt;
     unsigned char* hbB[2] = {smem + L.hbB, smem + L.hbB + BCOL * TW * 2};
@@ -486,17 +491,18 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 8);
     int* abort_flag = reinterpret_cast<int*>(smem + L.bar + 12);
+    float* redb = reinterpret_cast<float*>(smem + L.bar + 16);     // [4][128] bias partials
 
     // W^T as the A operand of the input adjoint (layers above the first)
     if (li > 0) {
         const float* W = a.params + g.off_w[li];      // [128 u][128 k]
-        for (int i = t; i < TW * TW; i += TTHREADS) {
+        for (int i = t; i < TW * TW; i += BTHREADS) {
             const int u = i / TW, k = i - u * TW;
             st_bf16(wt, tc::kmajor_offset(k, u, TLBO, B_SBO_K128), W[i]);
         }
     } else {
         // padding rows K0 .. K0p-1 of Z stay zero for every tile
-        for (int i = t; i < (kin - K) * BCOL; i += TTHREADS) {
+        for (int i = t; i < (kin - K) * BCOL; i += BTHREADS) {
             const int k = K + i / BCOL, c = i % BCOL;
             st_bf16(zB, tc::kmajor_offset(k, c, TLBO, B_SBO_K64), 0.0f);
         }
@@ -518,6 +524,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
     const float* hin = li > 0 ? a.saved + (int64_t)(li - 1) * g.n * 4 * TW : nullptr;
     const int n_tiles = (int)((g.n + BTP - 1) / BTP);
     uint32_t phase = 0;
+    bool pending = false;
     float accb = 0.0f;
     bool first = true;
 
@@ -527,46 +534,71 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
         stage64(hsb, hs, j0, g.n);
         cp_async_wait_all();
         __syncthreads();
-        // pre-activation adjoint, thread = unit u
+        // pre-activation adjoint of unit uu for 4 points: 16 columns, hi and lo
         {
-            const int u = t;
-            for (int p = 0; p < BTP; ++p) {
-                const float* z = zs + 4 * p * TW + u;
-                const float* h = hsb + 4 * p * TW + u;
+            float bv[16];
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const int c0 = 16 * ch + 4 * pp;
+                const float* z = zs + c0 * TW + uu;
+                const float* h = hsb + c0 * TW + uu;
                 const float h0 = h[0];
                 const float sg = sgm(g.beta * h0);
                 const float dsg = g.beta * sg * (1.0f - sg);
                 const float z0 = z[0], z1 = z[TW], z2 = z[2 * TW], z3 = z[3 * TW];
-                const float b[4] = {z0 * sg + (z1 * h[TW] + z2 * h[2 * TW] + z3 * h[3 * TW]) * dsg, sg * z1, sg * z2,
-                                    sg * z3};
-                accb += b[0];                         // 0 for points >= n (staged zeros)
+                bv[4 * pp] = z0 * sg + (z1 * h[TW] + z2 * h[2 * TW] + z3 * h[3 * TW]) * dsg;
+                bv[4 * pp + 1] = sg * z1;
+                bv[4 * pp + 2] = sg * z2;
+                bv[4 * pp + 3] = sg * z3;
+                accb += bv[4 * pp];                   // 0 for points >= n (staged zeros)
+            }
+            uint32_t qh[8], ql[8];
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    const float hi = bf16r(b[s]);
-                    const float lo = b[s] - hi;
-                    const int c = 4 * p + s;
-                    st_bf16(hbB[0], tc::kmajor_offset(c, u, TLBO, B_SBO_K128), hi);
-                    st_bf16(hbB[1], tc::kmajor_offset(c, u, TLBO, B_SBO_K128), lo);
-                    st_bf16(hbA[0], tc::kmajor_offset(u, c, TLBO, B_SBO_K64), hi);
-                    st_bf16(hbA[1], tc::kmajor_offset(u, c, TLBO, B_SBO_K64), lo);
-                }
+            for (int k = 0; k < 8; ++k) {
+                const float h0v = bf16r(bv[2 * k]), h1v = bf16r(bv[2 * k + 1]);
+                qh[k] = pack_bf16x2(h0v, h1v);
+                ql[k] = pack_bf16x2(bv[2 * k] - h0v, bv[2 * k + 1] - h1v);
+            }
+            // A operand of dW: row uu, columns 16 ch .. + 15 as two 16-byte rows
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const uint32_t o = tc::kmajor_offset(uu, 16 * ch + 8 * hh, TLBO, B_SBO_K64);
+                *reinterpret_cast<uint4*>(hbA[0] + o) = make_uint4(qh[4 * hh], qh[4 * hh + 1], qh[4 * hh + 2], qh[4 * hh + 3]);
+                *reinterpret_cast<uint4*>(hbA[1] + o) = make_uint4(ql[4 * hh], ql[4 * hh + 1], ql[4 * hh + 2], ql[4 * hh + 3]);
+            }
+            // B operand of the input adjoint: rows = columns, 8 units per 16 bytes (8x8 transpose over 8 lanes)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t th[4] = {qh[4 * hh], qh[4 * hh + 1], qh[4 * hh + 2], qh[4 * hh + 3]};
+                uint32_t tl[4] = {ql[4 * hh], ql[4 * hh + 1], ql[4 * hh + 2], ql[4 * hh + 3]};
+                transpose8x8_b16(th);
+                transpose8x8_b16(tl);
+                const int c = 16 * ch + 8 * hh + (lane & 7);
+                const int u0 = uu & ~7;
+                const uint32_t o = tc::kmajor_offset(c, u0, TLBO, B_SBO_K128);
+                *reinterpret_cast<uint4*>(hbB[0] + o) = make_uint4(th[0], th[1], th[2], th[3]);
+                *reinterpret_cast<uint4*>(hbB[1] + o) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
             }
         }
         __syncthreads();
-        // the layer's BF16 input Z (thread = input unit k), as the forward rounded it
+        // the layer's BF16 input Z (thread = input unit uu, 4 points), as the forward rounded it
         if (hin) {
             stage64(zs, hin, j0, g.n);
             cp_async_wait_all();
             __syncthreads();
-            const int k = t;
-            for (int p = 0; p < BTP; ++p) {
-                const float* x = zs + 4 * p * TW + k;
+            uint32_t q[8];
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const float* x = zs + (16 * ch + 4 * pp) * TW + uu;
                 const float x0 = x[0];
                 const float s0 = sgm(g.beta * x0);
-                const float v[4] = {sp_b(x0, g.beta), s0 * x[TW], s0 * x[2 * TW], s0 * x[3 * TW]};
-#pragma unroll
-                for (int s = 0; s < 4; ++s) st_bf16(zB, tc::kmajor_offset(k, 4 * p + s, TLBO, B_SBO_K64), v[s]);
+                q[2 * pp] = pack_bf16x2(sp_b(x0, g.beta), s0 * x[TW]);
+                q[2 * pp + 1] = pack_bf16x2(s0 * x[2 * TW], s0 * x[3 * TW]);
             }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+                *reinterpret_cast<uint4*>(zB + tc::kmajor_offset(uu, 16 * ch + 8 * hh, TLBO, B_SBO_K64)) =
+                    make_uint4(q[4 * hh], q[4 * hh + 1], q[4 * hh + 2], q[4 * hh + 3]);
         } else if (t < 3 * BTP) {
             const int p = t / 3, d = t - 3 * (t / 3);
             int64_t j = j0 + p;
@@ -602,46 +634,50 @@ __global__ void __launch_bounds__(TTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
         }
         first = false;
         const bool ok = mbar_wait(bar, phase);
-        phase ^= 1u;
+        if (ok) phase ^= 1u;
+        pending = !ok;
         if (!ok) atomicOr(abort_flag, 1);
         tc::fence_after_sync();
         __syncthreads();
         if (*abort_flag) break;
-        // adjoint of the layer input: thread = input unit k (TMEM lane), 64 columns
+        // adjoint of the layer input: warp = (lane quarter lq: input units, chunk ch: 16 columns)
         if (li > 0) {
-            const int k = warp * 32 + lane;
-            for (int cc = 0; cc < BCOL / 32; ++cc) {
-                float r[32];
-                tc::tmem_ld32(t_dx + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+            const int k = 32 * lq + lane;
+            float r[16];
+            tc::tmem_ld16(t_dx + ((uint32_t)(32 * lq) << 16) + (uint32_t)(16 * ch), r);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int c = cc * 32 + i;
-                    if (j0 + (c >> 2) < g.n) a.zbar[(j0 * 4 + c) * TW + k] = r[i];
-                }
+            for (int i = 0; i < 16; ++i) {
+                const int c = 16 * ch + i;
+                if (j0 + (c >> 2) < g.n) a.zbar[(j0 * 4 + c) * TW + k] = r[i];
             }
         }
         tc::fence_before_sync();
         __syncthreads();     // the next tile's staging and operands overwrite this tile's
     }
+    redb[ch * TW + uu] = accb;
     if (*abort_flag) {
         if (t == 0) {
             atomicOr(a.err, 1);
-            mbar_wait(bar, phase ^ 1u, 100000000ull);   // bounded: let the timed-out MMAs finish
+            if (pending) mbar_wait(bar, phase, 100000000ull);   // bounded: let the timed-out MMAs finish
         }
     } else {
-        // weight gradient of this CTA: thread = unit u (TMEM lane), columns k < K
-        const int u = warp * 32 + lane;
+        // weight gradient of this CTA: warp = (lane quarter: units, chunk: 32 input columns)
+        const int u = 32 * lq + lane;
         float* out = a.partial + (int64_t)blockIdx.x * a.n_params;
-        for (int cc = 0; cc < (kin + 31) / 32; ++cc) {
+        if (32 * ch < kin) {
             float r[32];
-            tc::tmem_ld32(t_dw + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+            tc::tmem_ld32(t_dw + ((uint32_t)(32 * lq) << 16) + (uint32_t)(32 * ch), r);
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                const int k = cc * 32 + i;
+                const int k = 32 * ch + i;
                 if (k < K) out[g.off_w[li] + (int64_t)u * K + k] = first ? 0.0f : r[i];
             }
         }
-        out[g.off_b[li] + u] = accb;
+    }
+    __syncthreads();
+    if (!*abort_flag && t < TW) {
+        float* out = a.partial + (int64_t)blockIdx.x * a.n_params;
+        out[g.off_b[li] + t] = ((redb[t] + redb[TW + t]) + redb[2 * TW + t]) + redb[3 * TW + t];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -693,7 +729,7 @@ geraf_status mlp_tc_backward_impl(const geraf_field_desc* d, const float* xyz, i
     for (int l = g.NH - 1; l >= 0; --l) {
         a.layer = l;
         const size_t smem = bwd_layout(l == 0 ? g.K0p : TW).total + 1024;
-        mlp_tc_layer_bwd_kernel<<<n_cta, TTHREADS, smem, st>>>(a);
+        mlp_tc_layer_bwd_kernel<<<n_cta, BTHREADS, smem, st>>>(a);
     }
     return cuda_status(cudaGetLastError(), "fields_backward(mlp bf16)");
 }
