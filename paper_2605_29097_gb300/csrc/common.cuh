@@ -91,6 +91,45 @@ __device__ __forceinline__ Range pair_range(float px, float py, float pz,
     return R;
 }
 
+// Coordinate split of the Chebyshev phasor kernels: x = h + l exactly, with h
+// on the 2^-10 m grid and |l| <= 2^-11 m. Differences of two h are exact in
+// FP32, and so is the sum of their three squares (multiples of 2^-20 below
+// 16 m^2) while every axis difference is below 2 m; the kernels' plan falls
+// back to the exact recurrence kernels beyond that.
+constexpr float kSplitScale = 1024.0f;
+__device__ __forceinline__ void split_coord(float x, float& h, float& l) {
+    h = __fmul_rn(rintf(__fmul_rn(x, kSplitScale)), 1.0f / kSplitScale);
+    l = __fsub_rn(x, h);
+}
+
+// Range r = |p - q| as a double-single pair from split coordinates (p = ph +
+// pl, q = qh + ql): with dh = ph - qh (exact) and dl = pl - ql,
+//   r^2 = |dh|^2 + sum dl (2 dh + dl),
+// the first term exact in FP32 and the second small (|dl| <= 2^-10 m), so one
+// Newton step on FP32 sqrt(r^2) gives r to ~1e-10 m (phase error < 1e-6 rad at
+// 81 GHz). About 22 instructions against ~53 for pair_range.
+__device__ __forceinline__ Range pair_range_split(float pxh, float pyh, float pzh, float pxl, float pyl,
+                                                  float pzl, float qxh, float qyh, float qzh, float qxl,
+                                                  float qyl, float qzl) {
+    Range R;
+    const float hx = __fsub_rn(pxh, qxh), hy = __fsub_rn(pyh, qyh), hz = __fsub_rn(pzh, qzh);
+    const float lx = __fsub_rn(pxl, qxl), ly = __fsub_rn(pyl, qyl), lz = __fsub_rn(pzl, qzl);
+    R.dx = __fadd_rn(hx, lx);
+    R.dy = __fadd_rn(hy, ly);
+    R.dz = __fadd_rn(hz, lz);
+    const float Sh = __fmaf_rn(hz, hz, __fmaf_rn(hy, hy, __fmul_rn(hx, hx)));
+    const float cross = __fmaf_rn(lx, __fmaf_rn(2.0f, hx, lx),
+                                  __fmaf_rn(ly, __fmaf_rn(2.0f, hy, ly), __fmul_rn(lz, __fmaf_rn(2.0f, hz, lz))));
+    const float S = fmaxf(__fadd_rn(Sh, cross), 1e-30f);
+    const float rs = rsqrtf(S);
+    const float r0 = __fmul_rn(S, rs);
+    const float resid = __fadd_rn(__fmaf_rn(-r0, r0, Sh), cross);
+    R.rh = r0;
+    R.rl = __fmul_rn(resid, __fmul_rn(0.5f, rs));
+    R.rs = rs;
+    return R;
+}
+
 // Fractional part (in cycles, |.| <= 0.5 + tiny) of (rh + rl) * (kh + kl).
 __device__ __forceinline__ float phase_frac(float rh, float rl, float kh, float kl) {
     float p = __fmul_rn(rh, kh);

@@ -37,13 +37,27 @@ constexpr float kInv16Pi2 = 0.0063325739776461107f;   // 1 / (16 pi^2)
 constexpr float kSqrt2 = 1.41421356237309505f;
 
 // ------------------------------------------------------------------ records
-// Point record of the phasor kernels (48 bytes):
-//  render / render backward: a = (x, y, z, w), b = (sqrt2*nx, sqrt2*ny, sqrt2*nz, t_eff),
-//                            c = (e, 1/|G|, 0, 0); e = 1 directional, -1 isotropic
-//  filter backward:          a = (x, y, z, c_re), b = (c_im, 0, 0, 0), c = 0
+// Point record of the phasor kernels (48 bytes); the position is split as
+// x = xh + xl (split_coord: xh on the 2^-10 m grid, xl the exact remainder):
+//  render / render backward: a = (xh, yh, zh, w), b = (sqrt2*nx, sqrt2*ny, sqrt2*nz, t_eff),
+//                            c = (xl, yl, zl, e); e = 1 directional, -1 isotropic
+//  filter backward:          a = (xh, yh, zh, c_re), b = (c_im, 0, 0, 0), c = (xl, yl, zl, 0)
 struct __align__(16) PtRec {
     float4 a, b, c;
 };
+
+// 1/|G| of a directional point (0 for an isotropic one), shared by the pack
+// kernel and the render adjoint's finalize so both see the same value
+__device__ __forceinline__ float inv_grad_norm(float gx, float gy, float gz, int directional) {
+    const float g2 = __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx)));
+    return (directional && g2 > 0.0f) ? 1.0f / sqrtf(g2) : 0.0f;
+}
+
+__device__ __forceinline__ void split3(float x, float y, float z, float4& hi, float4& lo) {
+    split_coord(x, hi.x, lo.x);
+    split_coord(y, hi.y, lo.y);
+    split_coord(z, hi.z, lo.z);
+}
 
 // --------------------------------------------------------------- pack kernels
 __global__ void pack_render_points(const float* __restrict__ xyz, const float* __restrict__ grad,
@@ -53,20 +67,20 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
     if (j >= n_pad) return;
     PtRec r;
     if (j < n) {
-        float x = xyz[j], y = xyz[n + j], z = xyz[2 * n + j];
-        float gx = grad[j], gy = grad[n + j], gz = grad[2 * n + j];
-        float g2 = gx * gx + gy * gy + gz * gz;
-        bool dir = directional && g2 > 0.0f;
-        float gn = sqrtf(g2);
-        float k = dir ? kSqrt2 / gn : 0.0f;
-        r.a = make_float4(x, y, z, w[j]);
+        const float gx = grad[j], gy = grad[n + j], gz = grad[2 * n + j];
+        const float ig = inv_grad_norm(gx, gy, gz, directional);
+        const bool dir = ig > 0.0f;
+        const float k = kSqrt2 * ig;
+        split3(xyz[j], xyz[n + j], xyz[2 * n + j], r.a, r.c);
+        r.a.w = w[j];
         r.b = make_float4(gx * k, gy * k, gz * k, t_eff[j]);
-        r.c = make_float4(dir ? 1.0f : -1.0f, dir ? 1.0f / gn : 0.0f, 0.0f, 0.0f);
+        r.c.w = dir ? 1.0f : -1.0f;
     } else {
         // padding: point 0's position with zero weight (inside every range bound)
-        r.a = make_float4(xyz[0], xyz[n], xyz[2 * n], 0.0f);
+        split3(xyz[0], xyz[n], xyz[2 * n], r.a, r.c);
+        r.a.w = 0.0f;
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        r.c = make_float4(-1.0f, 0.0f, 0.0f, 0.0f);
+        r.c.w = -1.0f;
     }
     out[j] = r;
 }
@@ -77,7 +91,6 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n_pad) return;
     PtRec r;
-    r.c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (j < n) {
         float2 m = M[j];
         double mag = sqrt((double)m.x * m.x + (double)m.y * m.y);
@@ -86,12 +99,15 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
             cr = (float)(dP[j] * (double)m.x / mag);
             ci = (float)(dP[j] * (double)m.y / mag);
         }
-        r.a = make_float4(vox[j], vox[n + j], vox[2 * n + j], cr);
+        split3(vox[j], vox[n + j], vox[2 * n + j], r.a, r.c);
+        r.a.w = cr;
         r.b = make_float4(ci, 0.0f, 0.0f, 0.0f);
     } else {
-        r.a = make_float4(vox[0], vox[n], vox[2 * n], 0.0f);
+        split3(vox[0], vox[n], vox[2 * n], r.a, r.c);
+        r.a.w = 0.0f;
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
+    r.c.w = 0.0f;
     out[j] = r;
 }
 
@@ -214,12 +230,12 @@ __global__ void __launch_bounds__(TB_THREADS, 2) to_bins_kernel(const ToBinsArgs
             const int p = q / A_T, a = q - p * A_T;
             const PtRec P = tile[p];
             const float4 A4 = ant_s[a];
-            Range R = pair_range(P.a.x, P.a.y, P.a.z, A4.x, A4.y, A4.z);
+            Range R = pair_range(P.a.x + P.c.x, P.a.y + P.c.y, P.a.z + P.c.z, A4.x, A4.y, A4.z);
             float amp = 0.0f;
             if (!kComplexAmp) {
                 float inv_r2 = R.rs * R.rs;
                 float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
-                float D = fmaxf(nd * nd * inv_r2 - P.c.x, 0.0f);
+                float D = fmaxf(nd * nd * inv_r2 - P.c.w, 0.0f);
                 float tt = __saturatef(P.b.w - A4.w);
                 amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
             } else {
@@ -393,9 +409,9 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
             pw[v] = pnx[v] = pny[v] = pnz[v] = pte[v] = pe[v] = 0.0f;
         } else {
             const PtRec P = args.pts[j];
-            px[v] = P.a.x; py[v] = P.a.y; pz[v] = P.a.z; pw[v] = P.a.w;
+            px[v] = P.a.x + P.c.x; py[v] = P.a.y + P.c.y; pz[v] = P.a.z + P.c.z; pw[v] = P.a.w;
             pnx[v] = P.b.x; pny[v] = P.b.y; pnz[v] = P.b.z; pte[v] = P.b.w;
-            pe[v] = P.c.x;
+            pe[v] = P.c.w;
         }
     }
     // outer (Kahan) accumulators; filter: M (re, im); render bwd: d_w, d_teff, Ud(3), Un
@@ -587,7 +603,8 @@ __global__ void sum_doubles(const double* __restrict__ x, int n, double* __restr
 }
 
 __global__ void render_bwd_finalize(const float* __restrict__ partial, int splits, int64_t n,
-                                    const PtRec* __restrict__ pts, float* __restrict__ d_w,
+                                    const PtRec* __restrict__ pts, const float* __restrict__ grad,
+                                    int directional, float* __restrict__ d_w,
                                     float* __restrict__ d_teff, float* __restrict__ d_grad) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -597,7 +614,7 @@ __global__ void render_bwd_finalize(const float* __restrict__ partial, int split
     d_w[j] = (float)acc[0];
     d_teff[j] = (float)acc[1];
     const PtRec P = pts[j];
-    const double ig = P.c.y;   // 1/|G| (0 when isotropic)
+    const double ig = inv_grad_norm(grad[j], grad[n + j], grad[2 * n + j], directional);   // 0 when isotropic
     d_grad[j] = (float)((acc[2] - acc[5] * P.b.x) * ig);
     d_grad[n + j] = (float)((acc[3] - acc[5] * P.b.y) * ig);
     d_grad[2 * n + j] = (float)((acc[4] - acc[5] * P.b.z) * ig);
@@ -747,7 +764,7 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
                                  int n_ant, double Kd, int n_f, double eps, ChebPlan* __restrict__ plan,
                                  double2* __restrict__ C) {
     __shared__ float box[6];
-    __shared__ float rr[2][256];
+    __shared__ float rr[3][256];
     __shared__ int sK;
     __shared__ float s_rc, s_inv;
     const int t = threadIdx.x;
@@ -757,7 +774,7 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
         box[t] = v;
     }
     __syncthreads();
-    float lo = INFINITY, hi = 0.0f;
+    float lo = INFINITY, hi = 0.0f, ext = 0.0f;
     for (int i = t; i < n_ant; i += blockDim.x) {
         float dn = 0.0f, df = 0.0f;
         for (int d = 0; d < 3; ++d) {
@@ -766,17 +783,20 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
             const float f = fmaxf(fabsf(a - box[d]), fabsf(box[3 + d] - a));
             dn += e * e;
             df += f * f;
+            ext = fmaxf(ext, f);
         }
         lo = fminf(lo, sqrtf(dn));
         hi = fmaxf(hi, sqrtf(df));
     }
     rr[0][t] = lo;
     rr[1][t] = hi;
+    rr[2][t] = ext;
     __syncthreads();
     for (int k = blockDim.x / 2; k > 0; k >>= 1) {
         if (t < k) {
             rr[0][t] = fminf(rr[0][t], rr[0][t + k]);
             rr[1][t] = fmaxf(rr[1][t], rr[1][t + k]);
+            rr[2][t] = fmaxf(rr[2][t], rr[2][t + k]);
         }
         __syncthreads();
     }
@@ -795,7 +815,8 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
             if (tail > eps) { K = k + 1; break; }
         }
         if (K < 2) K = 2;
-        const int direct = K > CH_KMAX;
+        // the split-coordinate range is exact only for axis differences below 2 m
+        const int direct = K > CH_KMAX || !(rr[2][0] < 1.99f);
         if (K > CH_KMAX) K = CH_KMAX;
         plan->r_c = rc;
         plan->inv_dr = inv;
@@ -845,14 +866,23 @@ struct ChebBinsArgs {
 
 // thread = antenna: Chebyshev moments of the antenna over the split's points.
 // Inner sums over CH_FLUSH tiles in registers, outer FP32 sums in shared memory.
-template <bool kComplexAmp>
-__global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArgs args) {
+// The core is 3 scalar FMAs per order (T_k recurrence, real and imaginary
+// accumulation): the FMA pipe, not the issue rate, bounds this kernel, and a
+// packed (re, im) form would spend a wasted lane on the recurrence.
+// KC = 8-order groups held in registers: the KC = 4 instance (orders 0..31,
+// no per-group guards, 64 moment registers, four CTAs per SM) runs when the
+// plan's K <= 32, the KC = 8 instance (orders 32..63 guarded by K) otherwise;
+// both are launched and the one that does not apply returns at once.
+template <bool kComplexAmp, int KC>
+__global__ void __launch_bounds__(CH_THREADS, KC == 4 ? 4 : 1) cheb_bins_kernel(const ChebBinsArgs args) {
+    constexpr int KM = 8 * KC;
     if (!args.plan->run_cheb) return;
+    if ((KC == 4) != (args.plan->K <= 32)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     PtRec* tiles = reinterpret_cast<PtRec*>(smem);                              // [2][CH_TP]
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * CH_TP * sizeof(PtRec));
     int* abort_flag = reinterpret_cast<int*>(bar + 2);
-    float2* outer = reinterpret_cast<float2*>(smem + 2 * CH_TP * sizeof(PtRec) + 32);   // [CH_KMAX][CH_THREADS]
+    float2* outer = reinterpret_cast<float2*>(smem + 2 * CH_TP * sizeof(PtRec) + 32);   // [KM][CH_THREADS]
     const int t = threadIdx.x;
     const int ia = blockIdx.x * CH_THREADS + t;
     const int split = blockIdx.y;
@@ -862,13 +892,15 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
     const int K = args.plan->K;
     const float r_c = args.plan->r_c, inv_dr = args.plan->inv_dr;
     const float4 A4 = args.ant[ia];                          // padded: always readable
+    float4 Ah, Al;
+    split3(A4.x, A4.y, A4.z, Ah, Al);
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
-    for (int k = 0; k < CH_KMAX; ++k) outer[k * CH_THREADS + t] = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < KM; ++k) outer[k * CH_THREADS + t] = make_float2(0.0f, 0.0f);
     __syncthreads();
     const uint32_t tile_bytes = (uint32_t)(CH_TP * sizeof(PtRec));
     if (t == 0)
@@ -876,9 +908,9 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
             mbar_arrive_expect_tx(&bar[s], tile_bytes);
             tma_load_1d(tiles + s * CH_TP, args.pts + (size_t)(tile0 + s) * CH_TP, tile_bytes, &bar[s]);
         }
-    float mr[CH_KMAX], mi[CH_KMAX];
+    float mr[KM], mi[KM];
 #pragma unroll
-    for (int k = 0; k < CH_KMAX; ++k) mr[k] = mi[k] = 0.0f;
+    for (int k = 0; k < KM; ++k) mr[k] = mi[k] = 0.0f;
 
     for (int it = 0; it < n_my; ++it) {
         const int buf = it & 1;
@@ -894,7 +926,8 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
         const PtRec* tile = tiles + buf * CH_TP;
         for (int p = 0; p < CH_TP; ++p) {
             const PtRec P = tile[p];
-            const Range R = pair_range(P.a.x, P.a.y, P.a.z, A4.x, A4.y, A4.z);
+            const Range R = pair_range_split(P.a.x, P.a.y, P.a.z, P.c.x, P.c.y, P.c.z, Ah.x, Ah.y, Ah.z, Al.x,
+                                             Al.y, Al.z);
             float ar_, ai_;
             {
                 const float fr = phase_frac(R.rh, R.rl, args.kh, args.kl);
@@ -903,7 +936,7 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
                 if (!kComplexAmp) {
                     const float inv_r2 = R.rs * R.rs;
                     const float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
-                    const float D = fmaxf(nd * nd * inv_r2 - P.c.x, 0.0f);
+                    const float D = fmaxf(nd * nd * inv_r2 - P.c.w, 0.0f);
                     const float tt = __saturatef(P.b.w - A4.w);
                     const float amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
                     ar_ = amp * cs;                          // A exp(-j 2 pi K0 r)
@@ -922,8 +955,8 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
             mr[1] = fmaf(ar_, x, mr[1]);
             mi[1] = fmaf(ai_, x, mi[1]);
 #pragma unroll
-            for (int kc = 0; kc < CH_KMAX; kc += 8) {
-                if (kc < K) {
+            for (int kc = 0; kc < KM; kc += 8) {
+                if (kc < 32 || kc < K) {
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         const int k = kc + kk;
@@ -940,8 +973,8 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
         }
         if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
 #pragma unroll
-            for (int kc = 0; kc < CH_KMAX; kc += 8)
-                if (kc < K)
+            for (int kc = 0; kc < KM; kc += 8)
+                if (kc < 32 || kc < K)
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         float2 o = outer[(kc + kk) * CH_THREADS + t];
@@ -963,7 +996,7 @@ __global__ void __launch_bounds__(CH_THREADS) cheb_bins_kernel(const ChebBinsArg
     }
 }
 
-size_t cheb_bins_smem() { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)CH_KMAX * CH_THREADS * sizeof(float2); }
+size_t cheb_bins_smem(int km) { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)km * CH_THREADS * sizeof(float2); }
 
 // out(i, n) = sum_k C_k(n) sum_splits M_k(i), FP64
 __global__ void cheb_reconstruct_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
@@ -994,9 +1027,12 @@ __global__ void cheb_reconstruct_kernel(const float2* __restrict__ partial, int 
     }
 }
 
-// antenna rows for the Chebyshev point kernels: head (x, y, z, c) + CH_KMAX float4
-// (h_re, h_re, h_im, h_im) with h_k = sum_n sig(n) * (conj ? conj(C_k(n)) : C_k(n))
-// and sig = (conj_sig ? conj(v) : v)
+// antenna rows for the Chebyshev point kernels: two heads, (xh, yh, zh, c) and
+// (xl, yl, zl, 0) (the split position), then CH_KMAX float4
+// s_k (h_re, h_re, h_im, h_im) with h_k = sum_n sig(n) * (conj ? conj(C_k(n)) : C_k(n)),
+// sig = (conj_sig ? conj(v) : v) and s_k = (-1)^floor(k/2), the sign of the
+// point kernels' packed V_k = s_k T_k recurrence
+constexpr int CH_ROW = 2 + CH_KMAX;
 __global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __restrict__ c_ant,
                                  const float2* __restrict__ sig, int n_ant, int n_ant_pad, int n_f,
                                  const ChebPlan* __restrict__ plan, const double2* __restrict__ C, int conj_c,
@@ -1004,10 +1040,15 @@ __global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __r
     if (!plan->run_cheb) return;
     const int i = blockIdx.x;
     if (i >= n_ant_pad) return;
-    float4* row = rows + (size_t)i * (1 + CH_KMAX);
+    float4* row = rows + (size_t)i * CH_ROW;
     if (threadIdx.x == 0) {
         const int q = i < n_ant ? i : 0;
-        row[0] = make_float4(ant[q], ant[n_ant + q], ant[2 * n_ant + q], c_ant ? c_ant[q] : 0.0f);
+        float4 hi, lo;
+        split3(ant[q], ant[n_ant + q], ant[2 * n_ant + q], hi, lo);
+        hi.w = c_ant ? c_ant[q] : 0.0f;
+        lo.w = 0.0f;
+        row[0] = hi;
+        row[1] = lo;
     }
     const int K = plan->K;
     for (int k = threadIdx.x; k < CH_KMAX; k += blockDim.x) {
@@ -1022,7 +1063,11 @@ __global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __r
                 hi += vr * ci + vi * cr;
             }
         }
-        row[1 + k] = make_float4((float)hr, (float)hr, (float)hi, (float)hi);
+        if ((k >> 1) & 1) {
+            hr = -hr;
+            hi = -hi;
+        }
+        row[2 + k] = make_float4((float)hr, (float)hr, (float)hi, (float)hi);
     }
 }
 
@@ -1043,13 +1088,21 @@ struct ChebPointsArgs {
 // thread = 2 points (the two lanes of the packed Chebyshev sums)
 static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread");
 
-template <int MODE>
-__global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPointsArgs args) {
+// KC = 8-order groups compiled in: the KC = 4 instance (orders 0..31, fully
+// unrolled, no guards) runs when the plan's K <= 32, the KC = 8 instance
+// otherwise; both are launched and the other returns at once.
+// Render adjoint: the per-point factors of the chain rule (the weight w, the
+// constant 1/(16 pi^2) of gamma, and the numeric factors of dD/dn) are taken out
+// of the antenna sums and applied once when the partials are written.
+template <int MODE, int KC>
+__global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 8 : 5) : 1) cheb_points_kernel(const ChebPointsArgs args) {
+    constexpr int KM = 8 * KC;
     if (!args.plan->run_cheb) return;
+    if ((KC == 4) != (args.plan->K <= 32)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int* abort_flag = reinterpret_cast<int*>(smem + 16);
-    constexpr int ROW = 1 + CH_KMAX;
+    constexpr int ROW = CH_ROW;
     float4* rows = reinterpret_cast<float4*>(smem + 32);   // [2][at][ROW]
     const int AT = args.at;
     const int t = threadIdx.x;
@@ -1073,21 +1126,21 @@ __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPoin
             tma_load_1d(rows + s * AT * ROW, args.rows + (size_t)(tile0 + s) * AT * ROW, tile_bytes, &bar[s]);
         }
     const int64_t jbase = (blockIdx.x * (int64_t)TPK_THREADS + t) * TPK_V;
-    float px[TPK_V], py[TPK_V], pz[TPK_V];
+    float4 ph[TPK_V], pl[TPK_V];                             // split positions
     float pw[TPK_V], pnx[TPK_V], pny[TPK_V], pnz[TPK_V], pte[TPK_V], pe[TPK_V];
 #pragma unroll
     for (int v = 0; v < TPK_V; ++v) {
         const int64_t j = min(jbase + v, args.n - 1);
         if (MODE == MODE_FILTER) {
-            px[v] = args.vox[j];
-            py[v] = args.vox[args.n + j];
-            pz[v] = args.vox[2 * args.n + j];
+            split3(args.vox[j], args.vox[args.n + j], args.vox[2 * args.n + j], ph[v], pl[v]);
             pw[v] = pnx[v] = pny[v] = pnz[v] = pte[v] = pe[v] = 0.0f;
         } else {
             const PtRec P = args.pts[j];
-            px[v] = P.a.x; py[v] = P.a.y; pz[v] = P.a.z; pw[v] = P.a.w;
+            ph[v] = P.a;
+            pl[v] = P.c;
+            pw[v] = P.a.w;
             pnx[v] = P.b.x; pny[v] = P.b.y; pnz[v] = P.b.z; pte[v] = P.b.w;
-            pe[v] = P.c.x;
+            pe[v] = P.c.w;
         }
     }
     constexpr int NACC = (MODE == MODE_FILTER) ? 2 : 6;
@@ -1115,36 +1168,44 @@ __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPoin
 #pragma unroll
             for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
         for (int a = 0; a < AT; ++a) {
-            const float4 head = tile[a * ROW];
-            const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 1);
+            const float4 head = tile[a * ROW], head_lo = tile[a * ROW + 1];
+            const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 2);
             Range R[TPK_V];
             float xs[TPK_V];
 #pragma unroll
             for (int v = 0; v < TPK_V; ++v) {
-                R[v] = pair_range(px[v], py[v], pz[v], head.x, head.y, head.z);
+                R[v] = pair_range_split(ph[v].x, ph[v].y, ph[v].z, pl[v].x, pl[v].y, pl[v].z, head.x, head.y,
+                                        head.z, head_lo.x, head_lo.y, head_lo.z);
                 xs[v] = __fmul_rn(__fadd_rn(__fsub_rn(R[v].rh, r_c), R[v].rl), inv_dr);
             }
-            // sum_k h_k T_k(x): T_k by the forward three-term recurrence (one
-            // FMA per point), the products accumulated for both points at
-            // once in the two lanes of packed FMAs
+            // sum_k h_k T_k(x) = sum_k (s_k h_k) V_k(x): V_k = s_k T_k for both
+            // points in the two lanes of one packed FMA (V_k = (+/-2x) V_{k-1}
+            // + V_{k-2}, minus for even k), the products accumulated for both
+            // points at once; the rows carry s_k h_k and are zero beyond K,
+            // so the loop may run to the next even order
             const ulonglong2 h0u = hk[0], h1u = hk[1];
-            float ta0 = 1.0f, tb0 = 1.0f, ta1 = xs[0], tb1 = xs[1];
-            const float x2a = 2.0f * xs[0], x2b = 2.0f * xs[1];
-            f2 Sr = h0u.x, Si = h0u.y;                       // T_0 = 1
-            {
-                const f2 T1 = pk2(ta1, tb1);
-                Sr = fma2(T1, h1u.x, Sr);
-                Si = fma2(T1, h1u.y, Si);
-            }
-#pragma unroll 4
-            for (int k = 2; k < K; ++k) {
-                const float ta2 = fmaf(x2a, ta1, -ta0), tb2 = fmaf(x2b, tb1, -tb0);
-                ta0 = ta1; tb0 = tb1;
-                ta1 = ta2; tb1 = tb2;
-                const ulonglong2 h = hk[k];
-                const f2 Tk = pk2(ta2, tb2);
-                Sr = fma2(Tk, h.x, Sr);
-                Si = fma2(Tk, h.y, Si);
+            const f2 mp = pk2(2.0f * xs[0], 2.0f * xs[1]), mn = pk2(-2.0f * xs[0], -2.0f * xs[1]);
+            f2 v0 = pk2(1.0f, 1.0f), v1 = pk2(xs[0], xs[1]);
+            f2 Sr = h0u.x, Si = h0u.y;                       // V_0 = 1
+            Sr = fma2(v1, h1u.x, Sr);
+            Si = fma2(v1, h1u.y, Si);
+#pragma unroll
+            for (int kc = 0; kc < KM; kc += 8) {
+                if (kc < 32 || kc < K) {
+#pragma unroll
+                    for (int k = (kc == 0 ? 2 : kc); k < kc + 8; k += 2) {
+                        const f2 ve = fma2(mn, v1, v0);
+                        const ulonglong2 he = hk[k];
+                        Sr = fma2(ve, he.x, Sr);
+                        Si = fma2(ve, he.y, Si);
+                        const f2 vo = fma2(mp, ve, v1);
+                        const ulonglong2 ho = hk[k + 1];
+                        Sr = fma2(vo, ho.x, Sr);
+                        Si = fma2(vo, ho.y, Si);
+                        v0 = ve;
+                        v1 = vo;
+                    }
+                }
             }
             float sr[TPK_V], si[TPK_V];
             upk2(Sr, sr[0], sr[1]);
@@ -1159,26 +1220,28 @@ __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPoin
                     in[v][0] += cs * sr[v] - sn * si[v];
                     in[v][1] += cs * si[v] + sn * sr[v];
                 } else {
-                    // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k)
+                    // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k); with A = w T'^2 gamma D,
+                    // gamma = k16 / r^2 and n' = sqrt2 n: the sums below times the
+                    // per-point factors (k16, 2 w k16, 2 sqrt2 w k16, sqrt2 w k16) are
+                    // dA/dw, dA/dT', and the parts of dA/dn' along d and along n'
                     const float q = cs * sr[v] + sn * si[v];
                     const float inv_r2 = R[v].rs * R[v].rs;
-                    const float gam = inv_r2 * kInv16Pi2;
+                    const float g = q * inv_r2;
                     const float nd = pnx[v] * R[v].dx + pny[v] * R[v].dy + pnz[v] * R[v].dz;
                     const float Dm = nd * nd * inv_r2 - pe[v];
                     const float D = fmaxf(Dm, 0.0f);
                     const float vv = pte[v] - head.w;
                     const float tt = __saturatef(vv);
-                    const float gq = gam * q;
-                    in[v][0] += tt * tt * D * gq;
-                    if (vv >= 0.0f && vv <= 1.0f) in[v][1] += pw[v] * 2.0f * tt * D * gq;
+                    const float dg = D * g;
+                    const float u = tt * tt * g;
+                    in[v][0] = fmaf(tt * tt, dg, in[v][0]);
+                    if (vv >= 0.0f && vv <= 1.0f) in[v][1] = fmaf(tt, dg, in[v][1]);
                     if (pe[v] > 0.0f && Dm > 0.0f) {
-                        const float kq = pw[v] * tt * tt * gq;
-                        const float c = nd * R[v].rs * (1.0f / kSqrt2);
-                        const float k1 = kq * 4.0f * c * R[v].rs;
-                        in[v][2] += k1 * R[v].dx;
-                        in[v][3] += k1 * R[v].dy;
-                        in[v][4] += k1 * R[v].dz;
-                        in[v][5] += kq * 4.0f * c * c * (1.0f / kSqrt2);
+                        const float w2 = u * nd * inv_r2;
+                        in[v][2] = fmaf(w2, R[v].dx, in[v][2]);
+                        in[v][3] = fmaf(w2, R[v].dy, in[v][3]);
+                        in[v][4] = fmaf(w2, R[v].dz, in[v][4]);
+                        in[v][5] = fmaf(w2, nd, in[v][5]);
                     }
                 }
             }
@@ -1208,8 +1271,11 @@ __global__ void __launch_bounds__(TPK_THREADS) cheb_points_kernel(const ChebPoin
             *dst = make_float2(__fsub_rn(hi[v][0], lo[v][0]), __fsub_rn(hi[v][1], lo[v][1]));
         } else {
             float* dst = args.partial + (size_t)split * 6 * args.n + j;
+            const float wk = pw[v] * kInv16Pi2;
+            const float fac[6] = {kInv16Pi2, 2.0f * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk,
+                                  kSqrt2 * wk};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = __fsub_rn(hi[v][k], lo[v][k]);
+            for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = __fsub_rn(hi[v][k], lo[v][k]) * fac[k];
         }
     }
 }
@@ -1268,7 +1334,7 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant) {
     q.ant_blocks = (n_ant + CH_THREADS - 1) / CH_THREADS;
     q.n_tiles = (int)(n_pad / CH_TP);
     const int64_t max_splits = std::max<int64_t>(1, (int64_t)(CH_PARTIAL_BYTES / ((size_t)n_ant * CH_KMAX * 8)));
-    const int64_t want = std::max<int64_t>(1, (4LL * 2 * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
+    const int64_t want = std::max<int64_t>(1, (4LL * 4 * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
     int64_t sp = std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles);
     q.tiles_per_split = (int)((q.n_tiles + sp - 1) / sp);
     q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
@@ -1314,8 +1380,10 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     if (!attr_set) {
         cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     const int* run_direct = nullptr;
@@ -1324,7 +1392,8 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         float kh, kl;
         k0_split(band, &kh, &kl);
         ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, kh, kl, cpart, err};
-        cheb_bins_kernel<kComplexAmp><<<dim3(q.ant_blocks, q.splits), CH_THREADS, cheb_bins_smem(), st>>>(ca);
+        cheb_bins_kernel<kComplexAmp, 4><<<dim3(q.ant_blocks, q.splits), CH_THREADS, cheb_bins_smem(32), st>>>(ca);
+        cheb_bins_kernel<kComplexAmp, 8><<<dim3(q.ant_blocks, q.splits), CH_THREADS, cheb_bins_smem(64), st>>>(ca);
         cheb_reconstruct_kernel<<<n_ant, 128, CH_KMAX * sizeof(double2), st>>>(cpart, q.splits, n_ant, band->n_f,
                                                                                cw.plan, cw.C,
                                                                                reinterpret_cast<float2*>(out));
@@ -1370,7 +1439,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     float4* crows = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_vox, band->n_f);
-        crows = c.take<float4>((size_t)p.n_ant_pad * (1 + CH_KMAX));
+        crows = c.take<float4>((size_t)p.n_ant_pad * CH_ROW);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
@@ -1378,7 +1447,9 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
         attr_set = true;
     }
@@ -1391,8 +1462,9 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
         k0_split(band, &kh, &kl);
         ChebPointsArgs ca{nullptr, vox, n_vox, crows, p.at, p.n_ant_tiles, p.tiles_per_split, cw.plan, kh, kl,
                           reinterpret_cast<float*>(part), err};
-        const size_t smem = 32 + 2 * (size_t)p.at * (1 + CH_KMAX) * sizeof(float4);
-        cheb_points_kernel<MODE_FILTER><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
+        const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
+        cheb_points_kernel<MODE_FILTER, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
+        cheb_points_kernel<MODE_FILTER, 8><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         run_direct = &cw.plan->use_direct;
     }
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
@@ -1424,7 +1496,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     float4* crows = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_pts, band->n_f);
-        crows = c.take<float4>((size_t)p.n_ant_pad * (1 + CH_KMAX));
+        crows = c.take<float4>((size_t)p.n_ant_pad * CH_ROW);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
@@ -1436,7 +1508,9 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
         attr_set = true;
     }
@@ -1449,8 +1523,9 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
         k0_split(band, &kh, &kl);
         ChebPointsArgs ca{pts, nullptr, n_pts, crows, p.at, p.n_ant_tiles, p.tiles_per_split, cw.plan, kh, kl, part,
                           err};
-        const size_t smem = 32 + 2 * (size_t)p.at * (1 + CH_KMAX) * sizeof(float4);
-        cheb_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
+        const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
+        cheb_points_kernel<MODE_RENDER_BWD, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
+        cheb_points_kernel<MODE_RENDER_BWD, 8><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         run_direct = &cw.plan->use_direct;
     }
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
@@ -1458,7 +1533,9 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     ToPointsArgs a{pts, nullptr, n_pts, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split, part, err, bk,
                    run_direct};
     to_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
-    render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, d_w, d_teff, d_grad);
+    render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, grad,
+                                                            (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, d_w,
+                                                            d_teff, d_grad);
     return check_launch("render_backward");
 }
 
