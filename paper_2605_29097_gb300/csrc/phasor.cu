@@ -693,6 +693,16 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
 // points and antennas, so the call stays asynchronous. If K would exceed
 // CH_KMAX the exact recurrence kernels run instead (decided on the device).
 constexpr int CH_KMAX = 64;
+// resident CTAs per SM asked of the compiler for the K <= 32 instances
+#ifndef GERAF_CH_BINS_CTAS
+#define GERAF_CH_BINS_CTAS 5
+#endif
+#ifndef GERAF_CH_FILTER_CTAS
+#define GERAF_CH_FILTER_CTAS 8
+#endif
+#ifndef GERAF_CH_RBWD_CTAS
+#define GERAF_CH_RBWD_CTAS 4
+#endif
 constexpr int CH_THREADS = 128;
 constexpr int CH_TP = 32;             // points per TMA tile
 constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before it joins the outer sum
@@ -874,7 +884,7 @@ struct ChebBinsArgs {
 // plan's K <= 32, the KC = 8 instance (orders 32..63 guarded by K) otherwise;
 // both are launched and the one that does not apply returns at once.
 template <bool kComplexAmp, int KC>
-__global__ void __launch_bounds__(CH_THREADS, KC == 4 ? 4 : 1) cheb_bins_kernel(const ChebBinsArgs args) {
+__global__ void __launch_bounds__(CH_THREADS, KC == 4 ? GERAF_CH_BINS_CTAS : 1) cheb_bins_kernel(const ChebBinsArgs args) {
     constexpr int KM = 8 * KC;
     if (!args.plan->run_cheb) return;
     if ((KC == 4) != (args.plan->K <= 32)) return;
@@ -1095,7 +1105,8 @@ static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread
 // constant 1/(16 pi^2) of gamma, and the numeric factors of dD/dn) are taken out
 // of the antenna sums and applied once when the partials are written.
 template <int MODE, int KC>
-__global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 8 : 5) : 1) cheb_points_kernel(const ChebPointsArgs args) {
+__global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? GERAF_CH_FILTER_CTAS : GERAF_CH_RBWD_CTAS) : 1)
+    cheb_points_kernel(const ChebPointsArgs args) {
     constexpr int KM = 8 * KC;
     if (!args.plan->run_cheb) return;
     if ((KC == 4) != (args.plan->K <= 32)) return;
