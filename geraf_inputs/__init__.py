@@ -141,13 +141,15 @@ class Scene:
 class MLPSpec:
     """SDF + reflectiveness network: PE with ``n_levels`` octaves over a cube
     (x normalised by (x - center)/half), ``n_hidden`` softplus layers of
-    ``width`` units, head [f, a_logit]."""
+    ``width`` units, head [f, a_logit] (``head_out`` = 2), or a single output
+    (``head_out`` = 1) for one of the two separate networks of FieldNets."""
     n_levels: int = 6
     width: int = 128
     n_hidden: int = 4
     beta: float = 100.0
     center: Tuple[float, float, float] = (0.0, 0.0, 0.15)
     half: float = 0.05
+    head_out: int = 2
 
     @property
     def in_dim(self) -> int:
@@ -156,7 +158,7 @@ class MLPSpec:
     def shapes(self):
         dims = [self.in_dim] + [self.width] * self.n_hidden
         out = [(dims[l + 1], dims[l]) for l in range(self.n_hidden)]
-        out.append((2, self.width))
+        out.append((self.head_out, self.width))
         return out
 
     @property
@@ -178,6 +180,31 @@ def mlp_init(spec: MLPSpec, seed: int, sdf_bias: float = 0.0) -> np.ndarray:
             b[0] += sdf_bias
         parts += [W.reshape(-1), b]
     return np.concatenate(parts).astype(np.float32)
+
+
+@dataclass
+class FieldNets:
+    """The paper's two field networks (App. C): an SDF network (head [f]) and a
+    separate reflectivity network (head [a_logit], a = sigmoid), both on the
+    positional encoding of x; packed parameters [SDF network | reflectivity
+    network], each packed like MLPSpec."""
+    sdf: MLPSpec
+    refl: MLPSpec
+
+    @property
+    def n_params(self) -> int:
+        return self.sdf.n_params + self.refl.n_params
+
+
+def paper_nets(center=(0.0, 0.0, 0.15), half=0.06, beta=100.0) -> FieldNets:
+    """SDF network 8 x 256, reflectivity network 4 x 256, 10-octave encoding
+    (App. C, "Training Setup"; softplus(beta) in both, a reading)."""
+    return FieldNets(MLPSpec(10, 256, 8, beta, tuple(center), half, 1),
+                     MLPSpec(10, 256, 4, beta, tuple(center), half, 1))
+
+
+def nets_init(nets: FieldNets, seed: int, sdf_bias: float = 0.0) -> np.ndarray:
+    return np.concatenate([mlp_init(nets.sdf, seed, sdf_bias), mlp_init(nets.refl, seed + 1000)])
 
 
 def unpack_params(spec: MLPSpec, params: np.ndarray):

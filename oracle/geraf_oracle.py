@@ -221,9 +221,10 @@ def mlp_forward(spec, params, xyz, precision="fp32"):
     Wh, bh = layers[-1]
     zr, dzr = r(z), r(dz)
     f = Wh[0] @ zr + bh[0]
-    logit = Wh[1] @ zr + bh[1]
     G = np.einsum("i,din->dn", Wh[0], dzr)
-    a = _sigmoid(logit)
+    a = None
+    if Wh.shape[0] == 2:                               # head [f, a_logit]
+        a = _sigmoid(Wh[1] @ zr + bh[1])
     cache["a"] = a
     return f, G, a, cache
 
@@ -240,16 +241,20 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
     r = bf16_round if cache.get("precision") == "bf16" else (lambda v: v)
     d_f = np.asarray(d_f, np.float64)
     d_G = np.asarray(d_G, np.float64)
-    a = cache["a"]
-    d_logit = np.asarray(d_a, np.float64) * a * (1.0 - a)
     grads = [None] * len(layers)
     Wh, _ = layers[-1]
     zL, dzL = r(cache["z"][-1]), r(cache["dz"][-1])
     gW = np.zeros_like(Wh)
     gW[0] = zL @ d_f + np.einsum("dn,din->i", d_G, dzL)
-    gW[1] = zL @ d_logit
-    grads[-1] = (gW, np.array([d_f.sum(), d_logit.sum()]))
-    zbar = np.outer(Wh[0], d_f) + np.outer(Wh[1], d_logit)
+    zbar = np.outer(Wh[0], d_f)
+    if Wh.shape[0] == 2:                               # head [f, a_logit]
+        a = cache["a"]
+        d_logit = np.asarray(d_a, np.float64) * a * (1.0 - a)
+        gW[1] = zL @ d_logit
+        grads[-1] = (gW, np.array([d_f.sum(), d_logit.sum()]))
+        zbar = zbar + np.outer(Wh[1], d_logit)
+    else:
+        grads[-1] = (gW, np.array([d_f.sum()]))
     dzbar = np.einsum("i,dn->din", Wh[0], d_G)
     for l in range(len(layers) - 2, -1, -1):
         W = r(layers[l][0])
@@ -264,6 +269,33 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
         zbar = W.T @ hbar
         dzbar = np.einsum("oi,don->din", W, dhbar)
     return np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
+
+
+def nets_forward(nets, params, xyz):
+    """The paper's two field networks (App. C, "Training Setup"; section 5.2
+    "Signal representation": a separate network of the position gives the
+    reflection coefficient): f and G = grad f from the SDF network, a =
+    sigmoid of the reflectivity network's output, both on the same encoding of
+    x. Returns (f, G, a, cache)."""
+    params = np.asarray(params, np.float32)
+    ns = nets.sdf.n_params
+    f, G, _, cs = mlp_forward(nets.sdf, params[:ns], xyz)
+    logit, _, _, cr = mlp_forward(nets.refl, params[ns:], xyz)
+    a = _sigmoid(logit)
+    return f, G, a, {"sdf": cs, "refl": cr, "a": a}
+
+
+def nets_backward(nets, params, cache, d_f, d_G, d_a):
+    """Adjoint of nets_forward: gradient of the packed [SDF | reflectivity]
+    parameters (FP64)."""
+    params = np.asarray(params, np.float32)
+    ns = nets.sdf.n_params
+    gs = mlp_backward(nets.sdf, params[:ns], cache["sdf"], d_f, d_G, None)
+    a = cache["a"]
+    d_logit = np.asarray(d_a, np.float64) * a * (1.0 - a)
+    n = a.shape[0]
+    gr = mlp_backward(nets.refl, params[ns:], cache["refl"], d_logit, np.zeros((3, n)), None)
+    return np.concatenate([gs, gr])
 
 
 # --------------------------------------------------------------------------

@@ -171,3 +171,61 @@ def test_mlp_bf16_network_and_straight_through_adjoint_match_torch(oracle):
     L = (tf * torch.tensor(d_f)).sum() + (tG * torch.tensor(d_G.T)).sum() + (ta * torch.tensor(d_a)).sum()
     tgp = torch.autograd.grad(L, p)[0].numpy()
     np.testing.assert_allclose(gp, tgp, rtol=1e-9, atol=1e-10 * np.abs(tgp).max())
+
+
+def _torch_nets(nets, params, xyz):
+    """Independent autograd reference of the paper's two networks: the SDF
+    network's f and its x-gradient (reverse-mode through the encoding), the
+    reflectivity network's sigmoid output, from the same packed parameters."""
+    p = torch.tensor(params.astype(np.float64), requires_grad=True)
+    x = torch.tensor(xyz.T.astype(np.float64), requires_grad=True)
+
+    def net(spec, q):
+        c = torch.tensor(np.asarray(spec.center, np.float32).astype(np.float64))
+        xt = (x - c) / float(np.float32(spec.half))
+        z = torch.cat([f((2.0 ** k) * np.pi * xt) for k in range(spec.n_levels) for f in (torch.sin, torch.cos)], 1)
+        off = 0
+        shapes = spec.shapes()
+        for li, (o, i) in enumerate(shapes):
+            W = q[off:off + o * i].view(o, i); off += o * i
+            b = q[off:off + o]; off += o
+            z = z @ W.T + b
+            if li < len(shapes) - 1:
+                z = torch.nn.functional.softplus(z, beta=spec.beta, threshold=1e6)
+        return z[:, 0]
+
+    ns = nets.sdf.n_params
+    f = net(nets.sdf, p[:ns])
+    a = torch.sigmoid(net(nets.refl, p[ns:]))
+    G = torch.autograd.grad(f.sum(), x, create_graph=True)[0]
+    return p, f, G, a
+
+
+@pytest.mark.parametrize("paper_size", [False, True])
+def test_two_networks_match_torch_autograd(oracle, paper_size):
+    """The paper's separate SDF and reflectivity networks (App. C): values,
+    SDF gradient and the adjoint of all packed parameters; the small case
+    checks every code path quickly, the paper-size case (8 x 256 and 4 x 256,
+    10 octaves) the shapes the GPU runs."""
+    if paper_size:
+        nets, n = gi.paper_nets(), 5
+    else:
+        nets = gi.FieldNets(gi.MLPSpec(4, 24, 3, 30.0, (0.0, 0.0, 0.15), 0.05, 1),
+                            gi.MLPSpec(4, 16, 2, 30.0, (0.0, 0.0, 0.15), 0.05, 1))
+        n = 29
+    params = gi.nets_init(nets, seed=7, sdf_bias=0.01)
+    assert params.size == nets.n_params
+    rng = np.random.default_rng(4)
+    xyz = (np.array([0.0, 0.0, 0.15])[:, None] + rng.uniform(-0.05, 0.05, (3, n))).astype(np.float32)
+    f, G, a, cache = oracle.nets_forward(nets, params, xyz)
+    p, tf, tG, ta = _torch_nets(nets, params, xyz)
+    np.testing.assert_allclose(f, tf.detach().numpy(), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(a, ta.detach().numpy(), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(G, tG.detach().numpy().T, rtol=1e-9, atol=1e-10 * np.abs(G).max())
+    d_f, d_G, d_a = rng.standard_normal(n), rng.standard_normal((3, n)), rng.standard_normal(n)
+    gp = oracle.nets_backward(nets, params, cache, d_f, d_G, d_a)
+    L = (tf * torch.tensor(d_f)).sum() + (tG * torch.tensor(d_G.T)).sum() + (ta * torch.tensor(d_a)).sum()
+    tgp = torch.autograd.grad(L, p)[0].numpy()
+    np.testing.assert_allclose(gp, tgp, rtol=1e-8, atol=1e-10 * np.abs(tgp).max())
+    # the reflectivity network's block gets its own gradient (a dropped d_a would zero it)
+    assert np.abs(gp[nets.sdf.n_params:]).max() > 0
