@@ -288,6 +288,59 @@ def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
             "steps": {"uniform": steps, "proposal": p_steps}}
 
 
+def paper_config_step(dev, warmup=3, steps=5):
+    """The paper's own training configuration (App. C "Training Setup";
+    section 5.3; section 9): N_ray = 1024 primary rays x N_z = 32 depths,
+    SDF network 8 x 256 and a separate reflectivity network 4 x 256 on a
+    10-octave encoding (FP32), the FMCW chirp read as 64 stepped frequencies,
+    a signal tracing bank of 3200-antenna patches (a 160 x 160 array at 2 mm in
+    8 patches of 80 x 40), 32^3 heatmap voxels (as many as the paper's
+    matched-filter points). One step traces one patch, filters the whole bank
+    and runs the adjoints of the patch and of both networks."""
+    import dataclasses
+    import torch
+    import geraf_inputs as gi
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import pipeline as PL
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.12, (32, 32, 32))
+    wl = gi.Workload("paper", 160, 0.002, 64, g, g, gi.SAMPLE_STRATIFIED, "mlp", "fp32", sharpness=2.0 / g.pitch[2])
+    geo = PL.make_geometry(wl, dev)
+    fb = gi.fmcw_band()
+    geo = dataclasses.replace(geo, band=G.Band(fb.f0, fb.df, fb.n_f))
+    nets = gi.paper_nets(center=(0.0, 0.0, 0.15), half=0.06)
+    params = torch.as_tensor(gi.nets_init(nets, seed=3, sdf_bias=0.02), device=dev)
+    field = G.MLPField(params, n_levels=10, width=256, n_hidden=8, beta=nets.sdf.beta, center=nets.sdf.center,
+                       half=nets.sdf.half, refl_hidden=4, refl_width=256)
+    target = PL.scene_target(geo, gi.c4_scene(4), noise_seed=4, device=dev)
+    bank = PL.SignalBank(geo, (160, 160), (80, 40))
+    bank.fill(field, 0, 0)
+    names = ["render", "render_backward", "filter", "filter_backward", "fields_backward"]
+    for k in range(warmup):
+        PL.forward_backward_bank(bank, field, target, 0, k)
+    torch.cuda.synchronize()
+    ev = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+          for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        PL.forward_backward_bank(bank, field, target, 0, warmup + k, timers=ev[k])
+    e1.record()
+    torch.cuda.synchronize()
+    G.geraf_poll_device_error()
+    ms = e0.elapsed_time(e1) / steps
+    n_pts, nf = g.n_pts, fb.n_f
+    n_ant, n_vox = int(geo.ant.shape[1]), int(geo.vox.shape[1])
+    terms = 2 * n_pts * bank.patch_size * nf + n_vox * n_ant * nf + n_vox * bank.patch_size * nf
+    return {"workload": "paper training configuration: 1024 rays x 32 depths, SDF net 8x256 + reflectivity net "
+                        "4x256, PE 10 octaves, fp32; FMCW 64 samples (3.59 GHz); 160x160 array @2mm in 3200-antenna "
+                        "bank patches; 32^3 heatmap",
+            "n_pts": n_pts, "patch_antennas": bank.patch_size, "n_antennas": n_ant, "n_f": nf, "n_vox": n_vox,
+            "ms_per_step": ms, "terms_per_step": terms, "terms_per_s": terms / (ms * 1e-3),
+            "per_call_ms": {nm: round(sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev) / steps, 3) for nm in names},
+            "paper_context": "50,000 iterations in 32 h on one H100 (about 2.3 s per iteration, whole training "
+                             "step, App. C); other hardware and code: context, not a target"}
+
+
 def mlp_bench(n_pts=1 << 21, reps=5):
     """Fields kernels alone on n_pts points (4x128 MLP, PE 6 octaves, value +
     3 gradient tangents): FP32 CUDA-core forward, BF16 tensor-core forward and
@@ -366,6 +419,8 @@ def main():
                     help="how the phasor sums step across the bins (default: by the number of bins)")
     ap.add_argument("--mlp-bench", type=int, default=0, metavar="N_PTS",
                     help="time only the fields kernels on N_PTS points and exit")
+    ap.add_argument("--paper-config", action="store_true",
+                    help="time only the paper's own training configuration and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -378,6 +433,12 @@ def main():
         return
     if args.mlp_bench:
         mlp_bench(args.mlp_bench)
+        return
+    if args.paper_config:
+        import torch
+        from paper_2605_29097_gb300 import _build
+        _build.build()
+        print(json.dumps({"mode": "paper_config", **paper_config_step(torch.device("cuda", local))}), flush=True)
         return
 
     import torch
@@ -584,11 +645,14 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "train_step": None,
+            "paper_config": None,
         }
         if not args.no_train and args.workload == "c2":
             del geo, field, target, params, geo_e, field_e
             torch.cuda.empty_cache()
             line["train_step"] = train_step_compare(dev)
+            torch.cuda.empty_cache()
+            line["paper_config"] = paper_config_step(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

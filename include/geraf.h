@@ -98,7 +98,18 @@ enum { GERAF_RENDER_DIRECTIONAL = 1 };
  *   positional encoding (section 9.3) of (x - center)/half with n_levels
  *   octaves (6 n_levels features: 6k+d = sin(2^k pi x_d), 6k+3+d = cos),
  *   n_hidden softplus(beta) layers of `width`, head [f, a_logit],
- *   a = sigmoid(a_logit). width must be 128 (the supported kernel shape). */
+ *   a = sigmoid(a_logit).
+ *   refl_hidden > 0 selects the paper's two separate networks (App. C
+ *   "Training Setup"; section 5.2 "Signal representation"): an SDF network
+ *   (n_hidden layers of `width`, head [f]) and a reflectivity network
+ *   (refl_hidden layers of refl_width, head [a_logit]) on the same encoding,
+ *   params packed [SDF network | reflectivity network], each as above.
+ *   One 128-wide trunk (refl_hidden = 0, width = 128) runs the fused kernels
+ *   in FP32 or BF16; every other shape (widths a multiple of 32 up to 1024,
+ *   up to 16 layers per network) runs layer by layer in FP32, keeps its layer
+ *   activations in `saved` (so `saved` is required even without a backward
+ *   pass) and must be called with grad and refl for a backward pass to
+ *   follow. Zero-initialised trailing fields keep the single-trunk form. */
 typedef struct {
     int32_t kind;
     const float* prims;
@@ -111,6 +122,8 @@ typedef struct {
     float center[3];
     float half;
     int32_t precision;
+    int32_t refl_hidden;     /* 0: one trunk with head [f, a_logit] */
+    int32_t refl_width;
 } geraf_field_desc;
 
 const char* geraf_last_error_string(void);
@@ -148,7 +161,7 @@ geraf_status geraf_sample(const geraf_grid* grid, int32_t mode, uint64_t seed, u
  * the ray-origin evaluations that need f only).
  * MLP fields need `saved` (activations kept for the backward pass) of
  * geraf_fields_saved_bytes() bytes, or NULL when no backward pass follows.
- * Errors: INVALID_ARG (null/bad sizes), UNSUPPORTED (width != 128),
+ * Errors: INVALID_ARG (null/bad sizes; `saved` NULL for a layer-by-layer network), UNSUPPORTED (shape),
  * WORKSPACE (saved too small).
  */
 geraf_status geraf_fields_saved_bytes(const geraf_field_desc* desc, int64_t n, size_t* bytes);

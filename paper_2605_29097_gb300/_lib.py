@@ -29,7 +29,7 @@ class GerafFieldDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("prims", vp), ("n_prims", ctypes.c_int32), ("params", vp),
                 ("n_levels", ctypes.c_int32), ("width", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
                 ("beta", ctypes.c_float), ("center", ctypes.c_float * 3), ("half", ctypes.c_float),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("refl_hidden", ctypes.c_int32), ("refl_width", ctypes.c_int32)]
 
 
 class GerafProposal(ctypes.Structure):

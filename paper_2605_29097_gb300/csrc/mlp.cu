@@ -487,7 +487,16 @@ int n_ctas_for(int n_tiles) {
 
 }  // namespace
 
+bool mlp_is_wide(const geraf_field_desc* d);
+geraf_status mlp_wide_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* bytes);
+geraf_status mlp_wide_forward(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
+                              float* refl, void* saved, size_t saved_bytes, cudaStream_t st);
+geraf_status mlp_wide_backward(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
+                               const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
+                               void* ws, size_t* ws_bytes, cudaStream_t st);
+
 geraf_status mlp_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* bytes) {
+    if (mlp_is_wide(d)) return mlp_wide_saved_bytes(d, n, bytes);
     MlpGeom g;
     if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
     *bytes = ((size_t)g.NH * n * 4 * MW + (size_t)n) * sizeof(float);
@@ -499,6 +508,7 @@ geraf_status mlp_tc_forward_impl(const geraf_field_desc*, const float*, int64_t,
 
 geraf_status mlp_forward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
                               float* refl, void* saved, size_t saved_bytes, cudaStream_t st) {
+    if (mlp_is_wide(d)) return mlp_wide_forward(d, xyz, n, sdf, grad, refl, saved, saved_bytes, st);
     MlpGeom g;
     if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
     if (d->precision != GERAF_PREC_FP32 && d->precision != GERAF_PREC_BF16)
@@ -527,6 +537,8 @@ geraf_status mlp_tc_backward_impl(const geraf_field_desc* d, const float* xyz, i
 geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
                                const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
                                void* ws, size_t* ws_bytes, cudaStream_t st) {
+    if (mlp_is_wide(d))
+        return mlp_wide_backward(d, xyz, n, saved, d_sdf, d_grad, d_refl, d_params, ws, ws_bytes, st);
     MlpGeom g;
     if (!make_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
     // BF16 networks: the straight-through adjoint on tcgen05 tensor cores; FP32

@@ -96,13 +96,23 @@ class AnalyticField:
 
 
 class MLPField:
-    """SDF + reflectiveness MLP with packed FP32 parameters."""
+    """SDF + reflectiveness MLP with packed FP32 parameters: one trunk with
+    head [f, a_logit] (refl_hidden = 0), or the paper's separate SDF and
+    reflectivity networks (refl_hidden layers of refl_width for the latter),
+    params packed [SDF network | reflectivity network]."""
 
     def __init__(self, params: torch.Tensor, n_levels=6, width=128, n_hidden=4, beta=100.0,
-                 center=(0.0, 0.0, 0.15), half=0.05, precision=PREC_FP32):
+                 center=(0.0, 0.0, 0.15), half=0.05, precision=PREC_FP32, refl_hidden=0, refl_width=0):
         self.params = _req(params, "params")
         self.n_levels, self.width, self.n_hidden = n_levels, width, n_hidden
         self.beta, self.center, self.half, self.precision = beta, tuple(center), half, precision
+        self.refl_hidden, self.refl_width = refl_hidden, refl_width
+
+    @property
+    def layer_by_layer(self) -> bool:
+        """Networks other than one 128-wide trunk keep their layer activations
+        in `saved`, which the library then needs on every call."""
+        return self.refl_hidden > 0 or self.width != 128
 
     def desc(self) -> GerafFieldDesc:
         d = GerafFieldDesc()
@@ -114,6 +124,7 @@ class MLPField:
             d.center[k] = float(self.center[k])
         d.half = float(self.half)
         d.precision = int(self.precision)
+        d.refl_hidden, d.refl_width = int(self.refl_hidden), int(self.refl_width)
         return d
 
 
@@ -142,7 +153,7 @@ def geraf_fields(field, xyz: torch.Tensor, want_grad=True, want_refl=True, keep_
     grad = torch.empty(3, n, dtype=torch.float32, device=dev) if want_grad else None
     refl = torch.empty(n, dtype=torch.float32, device=dev) if want_refl else None
     saved, nbytes = None, 0
-    if keep_saved:
+    if keep_saved or getattr(field, "layer_by_layer", False):
         sz = ctypes.c_size_t(0)
         check(_lib.lib().geraf_fields_saved_bytes(ctypes.byref(desc), n, ctypes.byref(sz)))
         nbytes = sz.value
