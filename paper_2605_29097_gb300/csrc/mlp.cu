@@ -115,7 +115,15 @@ struct FwdArgs {
     float* saved;   // [NH][n][4][128] pre-activations, then [n] reflectiveness; may be null
 };
 
-__global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
+// RU = output units per thread (8 x RU register tile): 8 gives 256 threads,
+// 4 gives 512 threads (twice the warps per SM for the same shared tiles)
+#ifndef GERAF_MLP_FWD_RU
+#define GERAF_MLP_FWD_RU 4
+#endif
+constexpr int FRU = GERAF_MLP_FWD_RU;
+constexpr int FT = 16 * (MW / FRU);
+
+__global__ void __launch_bounds__(FT, 1) mlp_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(16) float sm[];
     float* X0 = sm;
     float* X1 = X0 + MW * XS;
@@ -126,9 +134,9 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
     const int t = threadIdx.x;
     const int ub = t >> 4, cb = t & 15;
 
-    for (int i = t; i < 2 * MW; i += MTHREADS) head[i] = a.params[g.off_w[g.NH] + i];
+    for (int i = t; i < 2 * MW; i += FT) head[i] = a.params[g.off_w[g.NH] + i];
     if (t < 2) head[2 * MW + t] = a.params[g.off_b[g.NH] + t];
-    for (int i = t; i < MW * XS; i += MTHREADS) X0[i] = 0.0f;
+    for (int i = t; i < MW * XS; i += FT) X0[i] = 0.0f;
     __syncthreads();
 
     for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
@@ -144,28 +152,29 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
             // XS, columns K .. Kp-1 zero): asynchronous 16-byte copies when the
             // rows are 16-byte aligned
             if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0) {
-                for (int idx = t; idx < MW * (K / 4); idx += MTHREADS) {
+                for (int idx = t; idx < MW * (K / 4); idx += FT) {
                     const int u = idx / (K / 4), kq = idx - u * (K / 4);
                     cp_async16(Wt + u * XS + 4 * kq, W + (int64_t)u * K + 4 * kq, 16);
                 }
                 cp_async_wait_all();
             } else {
-                for (int idx = t; idx < MW * Kp; idx += MTHREADS) {
+                for (int idx = t; idx < MW * Kp; idx += FT) {
                     const int u = idx / Kp, k = idx - u * Kp;
                     Wt[u * XS + k] = k < K ? W[(int64_t)u * K + k] : 0.0f;
                 }
             }
             if (t < MW) bias[t] = a.params[g.off_b[l] + t];
             __syncthreads();
-            float acc[8][8];
+            float acc[FRU][8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < FRU; ++i)
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0f;
             for (int kq = 0; kq < Kp / 4; ++kq) {
-                float4 wq[8];
+                float4 wq[FRU];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) wq[i] = *reinterpret_cast<const float4*>(Wt + (8 * ub + i) * XS + 4 * kq);
+                for (int i = 0; i < FRU; ++i)
+                    wq[i] = *reinterpret_cast<const float4*>(Wt + (FRU * ub + i) * XS + 4 * kq);
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const int k = 4 * kq + m;
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
                     const float4 x1 = *reinterpret_cast<const float4*>(Xin + k * XS + 64 + 4 * cb);
                     const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < FRU; ++i) {
                         const float wv = m == 0 ? wq[i].x : (m == 1 ? wq[i].y : (m == 2 ? wq[i].z : wq[i].w));
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(wv, xv[jj], acc[i][jj]);
@@ -182,8 +191,8 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
             }
             // epilogue: value column (bias, softplus) and tangents (sigmoid(beta h) * dh)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int u = 8 * ub + i;
+            for (int i = 0; i < FRU; ++i) {
+                const int u = FRU * ub + i;
 #pragma unroll
                 for (int pp = 0; pp < 2; ++pp) {
                     const int col0 = pp * 64 + 4 * cb;
@@ -202,11 +211,12 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_fwd_kernel(const FwdArgs a) {
                     if (j < g.n) {
 #pragma unroll
                         for (int s = 0; s < 4; ++s) {
-                            float* dst = a.saved + (((int64_t)l * g.n + j) * 4 + s) * MW + 8 * ub;
-                            *reinterpret_cast<float4*>(dst) = make_float4(acc[0][4 * pp + s], acc[1][4 * pp + s],
-                                                                          acc[2][4 * pp + s], acc[3][4 * pp + s]);
-                            *reinterpret_cast<float4*>(dst + 4) = make_float4(
-                                acc[4][4 * pp + s], acc[5][4 * pp + s], acc[6][4 * pp + s], acc[7][4 * pp + s]);
+                            float* dst = a.saved + (((int64_t)l * g.n + j) * 4 + s) * MW + FRU * ub;
+#pragma unroll
+                            for (int q = 0; q < FRU; q += 4)
+                                *reinterpret_cast<float4*>(dst + q) = make_float4(
+                                    acc[q][4 * pp + s], acc[q + 1][4 * pp + s], acc[q + 2][4 * pp + s],
+                                    acc[q + 3][4 * pp + s]);
                         }
                     }
                 }
@@ -319,38 +329,47 @@ __global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a)
 // Rows c = 4 p + s of a [n][4][128] array for the tile's points j0 + p into a
 // [128][XS] shared tile, all in flight at once; rows of points >= n read as 0.
 __device__ __forceinline__ void stage_rows(float* dst, const float* src, int64_t j0, int64_t n) {
-    for (int i = threadIdx.x; i < MCOL * (MW / 4); i += MTHREADS) {
+    for (int i = threadIdx.x; i < MCOL * (MW / 4); i += blockDim.x) {
         const int c = i >> 5, q = i & 31;
         const bool ok = j0 + (c >> 2) < n;
         cp_async16(dst + c * XS + 4 * q, ok ? src + (j0 * 4 + c) * MW + 4 * q : src, ok ? 16 : 0);
     }
 }
 
+// BU = rows of each thread's register tiles: 8 gives 256 threads, 4 gives 512
+// threads (twice the warps per SM for the same shared tiles)
+#ifndef GERAF_MLP_BWD_BU
+#define GERAF_MLP_BWD_BU 8
+#endif
+constexpr int BU = GERAF_MLP_BWD_BU;
+constexpr int BT = 16 * (MW / BU);
+
 // hidden layer `layer`: pre-activation adjoint, weight/bias gradient, adjoint of the layer input
-__global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArgs a) {
+__global__ void __launch_bounds__(BT, 1) mlp_layer_bwd_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) float sm[];
     float* HbT = sm;                 // [128 c][XS]  HbT[c][u]
     float* ZT = HbT + MCOL * XS;     // [128 c][XS]  ZT[c][k]
     float* Ws = ZT + MCOL * XS;      // [128 u][XS]  W[u][k]
-    float* redb = Ws + MW * XS;      // [256]
+    float* redb = Ws + MW * XS;      // [BT]
     const MlpGeom& g = a.g;
     const int li = a.layer;
     const int K = g.k_in[li];
     const int t = threadIdx.x;
     const float* W = a.params + g.off_w[li];
-    for (int idx = t; idx < MW * K; idx += MTHREADS) {
+    for (int idx = t; idx < MW * K; idx += BT) {
         const int u = idx / K, k = idx - u * K;
         Ws[u * XS + k] = W[idx];
     }
-    for (int i = t; i < MCOL * XS; i += MTHREADS) ZT[i] = 0.0f;
+    for (int i = t; i < MCOL * XS; i += BT) ZT[i] = 0.0f;
     __syncthreads();
 
-    const int ub = t >> 4, kb = t & 15;          // weight-gradient tile
-    const int kq = t >> 4, cq = t & 15;          // input-adjoint tile
-    const int eu = t & (MW - 1), ehalf = t >> 7; // elementwise mapping
-    float accw[8][8];
+    constexpr int EG = BT / MW;                  // elementwise groups
+    const int ub = t >> 4, kb = t & 15;          // weight-gradient tile: units BU ub + i, inputs 4 kb (+64)
+    const int kq = t >> 4, cq = t & 15;          // input-adjoint tile: inputs BU kq + kk, columns cq + 16 i
+    const int eu = t & (MW - 1), eg = t >> 7;    // elementwise mapping
+    float accw[BU][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < BU; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) accw[i][jj] = 0.0f;
     float accb = 0.0f;
@@ -366,7 +385,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
         cp_async_wait_all();
         __syncthreads();
 #pragma unroll 4
-        for (int p = ehalf; p < MTP; p += 2) {
+        for (int p = eg; p < MTP; p += EG) {
             float* hb = HbT + 4 * p * XS + eu;
             const float* h = ZT + 4 * p * XS + eu;
             const float h0 = h[0];
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
             cp_async_wait_all();
             __syncthreads();
 #pragma unroll 4
-            for (int p = ehalf; p < MTP; p += 2) {
+            for (int p = eg; p < MTP; p += EG) {
                 float* z = ZT + 4 * p * XS + eu;
                 const float x0 = z[0];
                 const float s0 = sigm(g.beta * x0);
@@ -404,38 +423,44 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
         // weight gradient: accw[u][k] += sum_c HbT[c][u] ZT[c][k]
 #pragma unroll 2
         for (int c = 0; c < MCOL; ++c) {
-            const float4 h0 = *reinterpret_cast<const float4*>(HbT + c * XS + 8 * ub);
-            const float4 h1 = *reinterpret_cast<const float4*>(HbT + c * XS + 8 * ub + 4);
+            float hv[BU];
+#pragma unroll
+            for (int q = 0; q < BU; q += 4) {
+                const float4 h4 = *reinterpret_cast<const float4*>(HbT + c * XS + BU * ub + q);
+                hv[q] = h4.x; hv[q + 1] = h4.y; hv[q + 2] = h4.z; hv[q + 3] = h4.w;
+            }
             const float4 z0 = *reinterpret_cast<const float4*>(ZT + c * XS + 4 * kb);
             const float4 z1 = *reinterpret_cast<const float4*>(ZT + c * XS + 64 + 4 * kb);
-            const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
             const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < BU; ++i)
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) accw[i][jj] = fmaf(hv[i], zv[jj], accw[i][jj]);
         }
         // adjoint of the layer input: zbar[c][k] = sum_u HbT[c][u] W[u][k]  (in place)
         if (hin) {
-            float acc[8][8];
+            float acc[8][BU];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) acc[i][kk] = 0.0f;
+                for (int kk = 0; kk < BU; ++kk) acc[i][kk] = 0.0f;
             for (int u = 0; u < MW; u += 4) {
                 float4 hv[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) hv[i] = *reinterpret_cast<const float4*>(HbT + (cq + 16 * i) * XS + u);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 wa = *reinterpret_cast<const float4*>(Ws + (u + q) * XS + 8 * kq);
-                    const float4 wb = *reinterpret_cast<const float4*>(Ws + (u + q) * XS + 8 * kq + 4);
-                    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                    float wv[BU];
+#pragma unroll
+                    for (int r = 0; r < BU; r += 4) {
+                        const float4 w4 = *reinterpret_cast<const float4*>(Ws + (u + q) * XS + BU * kq + r);
+                        wv[r] = w4.x; wv[r + 1] = w4.y; wv[r + 2] = w4.z; wv[r + 3] = w4.w;
+                    }
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const float hq = q == 0 ? hv[i].x : (q == 1 ? hv[i].y : (q == 2 ? hv[i].z : hv[i].w));
 #pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) acc[i][kk] = fmaf(hq, wv[kk], acc[i][kk]);
+                        for (int kk = 0; kk < BU; ++kk) acc[i][kk] = fmaf(hq, wv[kk], acc[i][kk]);
                     }
                 }
             }
@@ -444,9 +469,11 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
                 const int c = cq + 16 * i, p = c >> 2, s = c & 3;
                 const int64_t j = j0 + p;
                 if (j < g.n) {
-                    float* dst = a.zbar + (j * 4 + s) * MW + 8 * kq;
-                    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-                    *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+                    float* dst = a.zbar + (j * 4 + s) * MW + BU * kq;
+#pragma unroll
+                    for (int r = 0; r < BU; r += 4)
+                        *reinterpret_cast<float4*>(dst + r) =
+                            make_float4(acc[i][r], acc[i][r + 1], acc[i][r + 2], acc[i][r + 3]);
                 }
             }
         }
@@ -455,8 +482,8 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
     // per-CTA partials
     float* out = a.partial + (int64_t)blockIdx.x * g.n_params;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int u = 8 * ub + i;
+    for (int i = 0; i < BU; ++i) {
+        const int u = BU * ub + i;
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
             const int k = jj < 4 ? 4 * kb + jj : 64 + 4 * kb + (jj - 4);
@@ -465,7 +492,11 @@ __global__ void __launch_bounds__(MTHREADS, 1) mlp_layer_bwd_kernel(const BwdArg
     }
     redb[t] = accb;
     __syncthreads();
-    if (t < MW) out[g.off_b[li] + t] = redb[t] + redb[t + MW];
+    if (t < MW) {
+        float sb = 0.0f;
+        for (int q = 0; q < EG; ++q) sb += redb[t + q * MW];
+        out[g.off_b[li] + t] = sb;
+    }
 }
 
 __global__ void reduce_partials(const float* __restrict__ partial, int n_cta, int64_t n_params,
@@ -478,7 +509,7 @@ __global__ void reduce_partials(const float* __restrict__ partial, int n_cta, in
 }
 
 size_t fwd_smem() { return (size_t)(3 * MW * XS + MW + 2 * MW + 2) * sizeof(float); }
-size_t bwd_smem() { return (size_t)(2 * MCOL * XS + MW * XS + MTHREADS) * sizeof(float); }
+size_t bwd_smem() { return (size_t)(2 * MCOL * XS + MW * XS + BT) * sizeof(float); }
 
 int n_ctas_for(int n_tiles) {
     const int sms = device_sm_count();
@@ -525,7 +556,7 @@ geraf_status mlp_forward_impl(const geraf_field_desc* d, const float* xyz, int64
         attr = true;
     }
     FwdArgs a{g, d->params, xyz, sdf, grad, refl, static_cast<float*>(saved)};
-    mlp_fwd_kernel<<<n_ctas_for(g.n_tiles), MTHREADS, fwd_smem(), st>>>(a);
+    mlp_fwd_kernel<<<n_ctas_for(g.n_tiles), FT, fwd_smem(), st>>>(a);
     return cuda_status(cudaGetLastError(), "fields(mlp)");
 }
 
@@ -567,7 +598,7 @@ geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int6
     mlp_head_bwd_kernel<<<n_cta, MTHREADS, 0, st>>>(a);
     for (int l = g.NH - 1; l >= 0; --l) {
         a.layer = l;
-        mlp_layer_bwd_kernel<<<n_cta, MTHREADS, bwd_smem(), st>>>(a);
+        mlp_layer_bwd_kernel<<<n_cta, BT, bwd_smem(), st>>>(a);
     }
     reduce_partials<<<(unsigned)((g.n_params + 255) / 256), 256, 0, st>>>(partial, n_cta, g.n_params, d_params);
     return cuda_status(cudaGetLastError(), "fields_backward(mlp)");

@@ -17,9 +17,10 @@ from . import geraf as G
 LAUNCHES = {"sample": 1, "fields": 1, "blend": 2, "render": 4, "filter": 4, "filter_backward": 4,
             "render_backward": 4, "blend_backward": 2}
 # with the Chebyshev form each phasor call adds the range bound, the plan and
-# the moment kernels; the recurrence kernels are still launched and return at
-# once unless the device-side plan falls back to them
-LAUNCHES_CHEBYSHEV = {"render": 8, "filter": 8, "filter_backward": 8, "render_backward": 8}
+# the moment kernels (a K <= 32 and a K <= 64 instance, one of which returns at
+# once); the recurrence kernels are still launched and return at once unless
+# the device-side plan falls back to them
+LAUNCHES_CHEBYSHEV = {"render": 9, "filter": 9, "filter_backward": 9, "render_backward": 9}
 
 
 def uses_chebyshev(band) -> bool:
