@@ -349,3 +349,35 @@ def test_fmcw_multi_plane_scan(G, oracle, method):
     assert rel_l2(host(gs), oracle.filter_backward(host(M), d_P, ant, vox, b)) < TOL
     if method == 2:
         assert G.geraf_chebyshev_order(cu(xyz), cu(ant), band) > 0
+
+
+@pytest.mark.parametrize("dist,cheb", [(1.8, True), (2.5, False)])
+def test_far_array_split_range_bound(G, oracle, dist, cheb):
+    """The Chebyshev kernels form the pair range from coordinates split on a
+    2^-10 m grid, exact while every axis difference stays below 2 m; the
+    device plan sends farther calls to the per-bin recurrence kernels. A small
+    array `dist` metres in front of the cube: at 1.8 m the Chebyshev form runs,
+    at 2.5 m the recurrence does, and both match the oracle."""
+    rng = np.random.default_rng(21)
+    n_pts, n_f = 1500, 128
+    xyz, grad, w, t_eff = _scene_points(rng, n_pts)
+    ant = gi.antenna_array(6, 5, 0.004, center=(0.01, -0.02, 0.15 - dist))
+    c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
+    b = gi.band(77e9, 81e9, n_f)
+    order = G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b))
+    assert (order > 0) == cheb, order
+    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), _band(G, b), True)
+    G.geraf_poll_device_error()
+    assert rel_l2(host(s), oracle.render(xyz, grad, w, t_eff, ant, c_ant, b)) < TOL
+    g = gi.complex_normal(rng, (ant.shape[1], n_f)).astype(np.complex64)
+    d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant),
+                                            _band(G, b), torch.as_tensor(g, device="cuda"))
+    G.geraf_poll_device_error()
+    ow, ot, og = oracle.render_backward(xyz, grad, w, t_eff, ant, c_ant, b, g)
+    assert rel_l2(host(d_w), ow) < TOL and rel_l2(host(d_t), ot) < TOL and rel_l2(host(d_g), og) < 3 * TOL
+    vox = (np.array([0.0, 0.0, 0.15])[:, None] + rng.uniform(-0.05, 0.05, (3, 900))).astype(np.float32)
+    sig = torch.as_tensor(oracle.render(xyz, grad, w, t_eff, ant, c_ant, b).astype(np.complex64), device="cuda")
+    P, M, _, _ = G.geraf_filter(sig, cu(ant), _band(G, b), cu(vox))
+    G.geraf_poll_device_error()
+    oM, _ = oracle.filter_forward(host(sig), ant, vox, b)
+    assert rel_l2(host(M), oM) < TOL
