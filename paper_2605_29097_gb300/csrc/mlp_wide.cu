@@ -228,7 +228,10 @@ struct LoadN {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(GT, 1) wgemm_kernel(const WGemm p) {
+#ifndef GERAF_WG_MINB
+#define GERAF_WG_MINB 2
+#endif
+__global__ void __launch_bounds__(GT, GERAF_WG_MINB) wgemm_kernel(const WGemm p) {
     extern __shared__ __align__(16) float wsm[];
     float* As = wsm;                  // [2][GK][GLD]
     float* Bs = wsm + 2 * GK * GLD;   // [2][GK][GLD]
@@ -427,15 +430,20 @@ __global__ void whead_bwd_kernel(WNet g, int64_t n, int64_t pps, const float* __
 }
 
 // pre-activation adjoint in place (zbar -> hbar) and the bias partials:
-// hb0 = zb0 sg + (sum_s zb_s h_s) beta sg (1 - sg), hb_s = sg zb_s
-__global__ void whbar_kernel(WNet g, int l, int64_t n, int64_t pps, const float* __restrict__ H,
-                             float* __restrict__ zbar, float* __restrict__ partial, int64_t split_stride) {
+// hb0 = zb0 sg + (sum_s zb_s h_s) beta sg (1 - sg), hb_s = sg zb_s.
+// Block (split, 32-unit chunk): threadIdx.x = unit, threadIdx.y = one of 8
+// point lanes; the lanes' bias sums are added in a fixed order.
+__global__ void __launch_bounds__(256) whbar_kernel(WNet g, int l, int64_t n, int64_t pps,
+                                                    const float* __restrict__ H, float* __restrict__ zbar,
+                                                    float* __restrict__ partial, int64_t split_stride) {
+    __shared__ float red[8][32];
     const int sp = blockIdx.x;
+    const int u = blockIdx.y * 32 + threadIdx.x;
     const int64_t j0 = (int64_t)sp * pps, j1 = min(n, j0 + pps);
-    float* part = partial + (int64_t)sp * split_stride;
-    for (int u = threadIdx.x; u < g.W; u += blockDim.x) {
-        float gb = 0.0f;
-        for (int64_t j = j0; j < j1; ++j) {
+    float gb = 0.0f;
+    if (u < g.W) {
+#pragma unroll 2
+        for (int64_t j = j0 + threadIdx.y; j < j1; j += 8) {
             const float* h = H + (j * g.S) * g.W;
             float* zb = zbar + (j * g.S) * g.W;
             const float hv = h[u];
@@ -455,7 +463,13 @@ __global__ void whbar_kernel(WNet g, int l, int64_t n, int64_t pps, const float*
             zb[u] = b0;
             gb += b0;
         }
-        part[g.off_b[l] + u] = gb;
+    }
+    red[threadIdx.y][threadIdx.x] = gb;
+    __syncthreads();
+    if (threadIdx.y == 0 && u < g.W) {
+        float t = 0.0f;
+        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+        partial[(int64_t)sp * split_stride + g.off_b[l] + u] = t;
     }
 }
 
@@ -596,7 +610,8 @@ void net_backward(const WNet& g, const float* xyz, int64_t n, const float* base,
     const int64_t rows = n * g.S;
     const int64_t rps = (pps * g.S + GK - 1) / GK * GK;
     for (int l = g.NH - 1; l >= 0; --l) {
-        whbar_kernel<<<splits, 256, 0, st>>>(g, l, n, pps, H_of(l), zA, partial, split_stride);
+        whbar_kernel<<<dim3(splits, gdiv(g.W, 32)), dim3(32, 8), 0, st>>>(g, l, n, pps, H_of(l), zA, partial,
+                                                                         split_stride);
         // weight gradient: partial[u][k] = sum over the split's rows of hb[r][u] z[r][k]
         WGemm w{};
         w.M = g.W;
