@@ -375,24 +375,28 @@ __global__ void whead_fwd_kernel(WNet g, int64_t n, const float* __restrict__ H,
 }
 
 // ------------------------------------------------------------- head adjoint
-// Split `sp` handles points [sp*pps, ...). Thread = unit u (strided). Writes
-// the top activation adjoint zbar[(j S + s) W + u] and the head's gradient
-// partials. For the reflectivity network (S = 1, head [a_logit]) d_row0 is
-// d_a a (1 - a); for the SDF network d_row0 = d_f with tangents d_grad; the
-// shared trunk adds row 1 (a_logit).
-__global__ void whead_bwd_kernel(WNet g, int64_t n, int64_t pps, const float* __restrict__ H,
-                                 const float* __restrict__ a_saved, const float* __restrict__ d_f,
-                                 const float* __restrict__ d_grad, const float* __restrict__ d_a, int refl_net,
-                                 float* __restrict__ zbar, float* __restrict__ partial, int64_t split_stride) {
+// Block (split, 32-unit chunk): threadIdx.x = unit u, threadIdx.y = one of 8
+// point lanes over the split's points [sp*pps, ...). Writes the top activation
+// adjoint zbar[(j S + s) W + u] and the head's gradient partials (lane sums
+// added in a fixed order). For the reflectivity network (S = 1, head
+// [a_logit]) the output adjoint is d_a a (1 - a); for the SDF network d_f with
+// tangents d_grad; the shared trunk adds row 1 (a_logit).
+__global__ void __launch_bounds__(256) whead_bwd_kernel(WNet g, int64_t n, int64_t pps, const float* __restrict__ H,
+                                                        const float* __restrict__ a_saved,
+                                                        const float* __restrict__ d_f,
+                                                        const float* __restrict__ d_grad,
+                                                        const float* __restrict__ d_a, int refl_net,
+                                                        float* __restrict__ zbar, float* __restrict__ partial,
+                                                        int64_t split_stride) {
+    __shared__ float red[4][8][32];
     const int sp = blockIdx.x;
+    const int u = blockIdx.y * 32 + threadIdx.x;
     const int64_t j0 = (int64_t)sp * pps, j1 = min(n, j0 + pps);
     const float* Wh = g.params + g.off_w[g.NH];
-    float* part = partial + (int64_t)sp * split_stride;
-    float gb0 = 0.0f, gb1 = 0.0f;
-    for (int u = threadIdx.x; u < g.W; u += blockDim.x) {
+    float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
+    if (u < g.W) {
         const float w0 = Wh[u], w1 = g.head_out == 2 ? Wh[g.W + u] : 0.0f;
-        float gw0 = 0.0f, gw1 = 0.0f;
-        for (int64_t j = j0; j < j1; ++j) {
+        for (int64_t j = j0 + threadIdx.y; j < j1; j += 8) {
             const float* h = H + (j * g.S) * g.W;
             const float hv = h[u];
             const float z0 = softplus_w(hv, g.beta);
@@ -415,17 +419,30 @@ __global__ void whead_bwd_kernel(WNet g, int64_t n, int64_t pps, const float* __
                     gw0 = fmaf(dg, sg * h[(int64_t)s * g.W + u], gw0);
                 }
             }
-            if (u == threadIdx.x && threadIdx.x == 0) {
-                gb0 += df;
-                gb1 += dl;
-            }
+            gb0 += df;
+            gb1 += dl;
         }
-        part[g.off_w[g.NH] + u] = gw0;
-        if (g.head_out == 2) part[g.off_w[g.NH] + g.W + u] = gw1;
     }
-    if (threadIdx.x == 0) {
-        part[g.off_b[g.NH]] = gb0;
-        if (g.head_out == 2) part[g.off_b[g.NH] + 1] = gb1;
+    red[0][threadIdx.y][threadIdx.x] = gw0;
+    red[1][threadIdx.y][threadIdx.x] = gw1;
+    red[2][threadIdx.y][threadIdx.x] = gb0;
+    red[3][threadIdx.y][threadIdx.x] = gb1;
+    __syncthreads();
+    if (threadIdx.y == 0 && u < g.W) {
+        float t0 = 0.0f, t1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+        for (int q = 0; q < 8; ++q) {
+            t0 += red[0][q][threadIdx.x];
+            t1 += red[1][q][threadIdx.x];
+            b0 += red[2][q][threadIdx.x];
+            b1 += red[3][q][threadIdx.x];
+        }
+        float* part = partial + (int64_t)sp * split_stride;
+        part[g.off_w[g.NH] + u] = t0;
+        if (g.head_out == 2) part[g.off_w[g.NH] + g.W + u] = t1;
+        if (u == 0) {
+            part[g.off_b[g.NH]] = b0;
+            if (g.head_out == 2) part[g.off_b[g.NH] + 1] = b1;
+        }
     }
 }
 
@@ -605,8 +622,9 @@ void net_backward(const WNet& g, const float* xyz, int64_t n, const float* base,
     const float* Z0 = base;
     const float* Hl = Z0 + (size_t)n * g.S * g.K0p;
     auto H_of = [&](int l) { return Hl + (size_t)l * n * g.S * g.W; };
-    whead_bwd_kernel<<<splits, 256, 0, st>>>(g, n, pps, H_of(g.NH - 1), a_saved, d_f, d_grad, d_a, refl_net, zA,
-                                             partial, split_stride);
+    whead_bwd_kernel<<<dim3(splits, gdiv(g.W, 32)), dim3(32, 8), 0, st>>>(g, n, pps, H_of(g.NH - 1), a_saved, d_f,
+                                                                        d_grad, d_a, refl_net, zA, partial,
+                                                                        split_stride);
     const int64_t rows = n * g.S;
     const int64_t rps = (pps * g.S + GK - 1) / GK * GK;
     for (int l = g.NH - 1; l >= 0; --l) {
