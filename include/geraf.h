@@ -139,6 +139,17 @@ int32_t geraf_version(void);
 geraf_status geraf_poll_device_error(void* stream);
 
 /*
+ * geraf_check_bounded_wait — self-test of the failure path every TMA kernel
+ * uses (not in the paper): one CTA waits on a shared-memory mbarrier that
+ * nothing arrives at, gives up after about limit_ns nanoseconds (1 us .. 1 s),
+ * records the timeout in the device error word and returns. The next
+ * geraf_poll_device_error on the same device then reports GERAF_ERR_TIMEOUT and
+ * clears the word; the context stays usable. Asynchronous on `stream`.
+ * Errors: INVALID_ARG for a limit outside the range, CUDA for launch failures.
+ */
+geraf_status geraf_check_bounded_wait(uint64_t limit_ns, void* stream);
+
+/*
  * geraf_sample — lensless sampling (section 6 "Primary Ray"; section 4 step 1).
  * Writes n_pts = n[0]*n[1]*n[2] points xyz [3][n_pts] (depth-major) and the
  * n_ray = n[0]*n[1] primary-ray start points xyz_apr [3][n_ray] = (x, y,

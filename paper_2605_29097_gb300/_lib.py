@@ -41,6 +41,7 @@ class GerafProposal(ctypes.Structure):
 # name -> argtypes (all return geraf_status as int)
 SIGNATURES = {
     "geraf_poll_device_error": [vp],
+    "geraf_check_bounded_wait": [u64, vp],
     "geraf_sample": [ctypes.POINTER(GerafGrid), i32, u64, u64, vp, vp, vp],
     "geraf_fields_saved_bytes": [ctypes.POINTER(GerafFieldDesc), i64, szp],
     "geraf_fields": [ctypes.POINTER(GerafFieldDesc), vp, i64, vp, vp, vp, vp, sz, vp],

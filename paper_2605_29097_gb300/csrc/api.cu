@@ -167,6 +167,26 @@ geraf_status geraf_poll_device_error(void* stream) {
     return GERAF_OK;
 }
 
+namespace {
+// one CTA: an mbarrier expecting one arrival that never comes; the bounded
+// wait runs out, the timeout goes to the device error word
+__global__ void bounded_wait_kernel(uint64_t limit_ns, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    geraf::mbar_init(&bar, 1);
+    geraf::fence_barrier_init();
+    if (!geraf::mbar_wait(&bar, 0, limit_ns)) atomicOr(err, 1);
+}
+}  // namespace
+
+geraf_status geraf_check_bounded_wait(uint64_t limit_ns, void* stream) {
+    REQUIRE(limit_ns >= 1000ull && limit_ns <= 1000000000ull, "check_bounded_wait: limit_ns must be in [1e3, 1e9]");
+    int* err = device_error_word();
+    if (!err) return fail(GERAF_ERR_CUDA, "device error word unavailable");
+    bounded_wait_kernel<<<1, 32, 0, S(stream)>>>(limit_ns, err);
+    return cuda_status(cudaGetLastError(), "check_bounded_wait");
+}
+
 geraf_status geraf_sample(const geraf_grid* grid, int32_t mode, uint64_t seed, uint64_t step, float* xyz,
                           float* xyz_apr, void* stream) {
     REQUIRE(grid && xyz, "sample: grid and xyz must not be NULL");

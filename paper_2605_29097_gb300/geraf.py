@@ -128,6 +128,12 @@ class MLPField:
         return d
 
 
+def geraf_check_bounded_wait(limit_ns: int):
+    """Self-test of the bounded-wait failure path (see include/geraf.h): the
+    next geraf_poll_device_error() raises GerafError with GERAF_ERR_TIMEOUT."""
+    check(_lib.lib().geraf_check_bounded_wait(int(limit_ns), _stream()))
+
+
 def geraf_poll_device_error():
     check(_lib.lib().geraf_poll_device_error(_stream()))
 
