@@ -397,3 +397,47 @@ def forward_backward_bank(bank: SignalBank, field, target: torch.Tensor, seed: i
     res.bank = {"patch": k, "xyz": xyz, "grad": grad, "w": w, "t_eff": t_eff, "c_ant": c_ant, "M": M, "dP": dP,
                 "g": g_p, "d_w": d_w, "d_teff": d_t, "d_G": d_G}
     return res
+
+
+# ------------------------------------------------------ checkpoint / resume
+def save_checkpoint(path, step: int, params: torch.Tensor, optimizer=None, proposal=None, proposal_trainer=None,
+                    extra=None):
+    """Training state to `path` (torch.save): the packed field parameters, the
+    optimiser state, the proposal (FP16 features and its MLP, with its own
+    trainer's FP32 masters and Adam state) and the step counter. Sampling
+    jitter and proposal draws come from counter-based generators keyed by
+    (seed, step, index), so resuming at `step` repeats the same samples."""
+    state = {"step": int(step), "params": params.detach().cpu()}
+    if optimizer is not None:
+        state["optimizer"] = optimizer.state_dict()
+    if proposal is not None:
+        state["proposal"] = {"features": proposal.features.detach().cpu(), "params": proposal.params.detach().cpu()}
+    if proposal_trainer is not None:
+        state["proposal_trainer"] = {"params": proposal_trainer.params.detach().cpu(),
+                                     "feats": proposal_trainer.feats.detach().cpu(),
+                                     "optimizer": proposal_trainer.opt.state_dict()}
+    if extra is not None:
+        state["extra"] = extra
+    torch.save(state, path)
+
+
+def load_checkpoint(path, params: torch.Tensor, optimizer=None, proposal=None, proposal_trainer=None) -> dict:
+    """Restores what save_checkpoint wrote into the given tensors and
+    optimisers (in place, on their devices); returns the state dict (its
+    "step" is the step to continue from)."""
+    state = torch.load(path, map_location="cpu", weights_only=False)
+    with torch.no_grad():
+        params.copy_(state["params"].to(params.device))
+    if optimizer is not None and "optimizer" in state:
+        optimizer.load_state_dict(state["optimizer"])
+    if proposal is not None and "proposal" in state:
+        with torch.no_grad():
+            proposal.features.copy_(state["proposal"]["features"].to(proposal.features.device))
+            proposal.params.copy_(state["proposal"]["params"].to(proposal.params.device))
+    if proposal_trainer is not None and "proposal_trainer" in state:
+        pt = state["proposal_trainer"]
+        with torch.no_grad():
+            proposal_trainer.params.copy_(pt["params"].to(proposal_trainer.params.device))
+            proposal_trainer.feats.copy_(pt["feats"].to(proposal_trainer.feats.device))
+        proposal_trainer.opt.load_state_dict(pt["optimizer"])
+    return state

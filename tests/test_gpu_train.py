@@ -102,3 +102,47 @@ def test_trained_proposal_beats_uniform_depths(G):
           f"trained {e_prop:.3e}; proposal KL {losses[0]:.3f} -> {losses[-1]:.3f}")
     assert losses[-1] < 0.5 * losses[0]
     assert e_prop < 0.5 * e_u16
+
+
+def test_checkpoint_resume_repeats_the_run_bit_for_bit(G, tmp_path):
+    """Training state saved at step 3 and restored into fresh tensors and
+    optimisers continues exactly as the uninterrupted run: the kernels are
+    deterministic (fixed-order reductions, no float atomics) and the samples
+    come from counter-based generators keyed by the step."""
+    from paper_2605_29097_gb300 import pipeline as PL
+    wl = gi.workload("c4-small")
+    geo = PL.make_geometry(wl)
+    target = PL.scene_target(geo, gi.c4_scene(5), noise_seed=5)
+    spec = gi.MLPSpec(center=(0.0, 0.0, 0.15), half=0.06)
+
+    def fresh():
+        p = torch.as_tensor(gi.mlp_init(spec, seed=8, sdf_bias=0.02), device="cuda")
+        master = p.clone().requires_grad_(True)
+        return p, master, torch.optim.Adam([master], lr=1e-3)
+
+    def run(p, master, opt, steps):
+        field = G.MLPField(p, center=spec.center, half=spec.half)
+        out = []
+        for step in steps:
+            r = PL.forward_backward(geo, field, target, seed=4, step=step)
+            out.append(float(r.loss))
+            opt.zero_grad()
+            master.grad = r.d_params.clone()
+            opt.step()
+            with torch.no_grad():
+                p.copy_(master)
+        return out
+
+    p, master, opt = fresh()
+    run(p, master, opt, range(3))
+    ck = tmp_path / "state.pt"
+    PL.save_checkpoint(ck, 3, master, opt)
+    tail = run(p, master, opt, range(3, 6))
+    p2, master2, opt2 = fresh()
+    st = PL.load_checkpoint(ck, master2, opt2)
+    with torch.no_grad():
+        p2.copy_(master2)
+    assert st["step"] == 3
+    resumed = run(p2, master2, opt2, range(st["step"], 6))
+    assert resumed == tail
+    assert torch.equal(p, p2)
