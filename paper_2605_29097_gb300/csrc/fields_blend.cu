@@ -131,29 +131,48 @@ __global__ void analytic_fields_kernel(const float* __restrict__ prims, int n_pr
 // accurate 1 - Phi_s(f) = sigma(-s f)
 __device__ __forceinline__ float one_minus_cdf(float x) { return 1.0f / (1.0f + expf(x)); }
 
-__global__ void blend_kernel(const float* __restrict__ sdf, const float* __restrict__ refl, int n_ray, int n_z,
-                             const float* __restrict__ sdf_apr, float s, float a_tx, float* __restrict__ alpha,
-                             float* __restrict__ T, float* __restrict__ w, float* __restrict__ t_eff) {
+// Thread = one primary column; the depth scan runs in chunks of BL_CH depths
+// whose loads are all issued before the chunk's arithmetic (the scan itself is
+// sequential per column, so memory-level parallelism comes from the chunk).
+constexpr int BL_CH = 16;
+constexpr int BL_THREADS = 64;
+
+__global__ void __launch_bounds__(BL_THREADS) blend_kernel(const float* __restrict__ sdf,
+                                                           const float* __restrict__ refl, int n_ray, int n_z,
+                                                           const float* __restrict__ sdf_apr, float s, float a_tx,
+                                                           float* __restrict__ alpha, float* __restrict__ T,
+                                                           float* __restrict__ w, float* __restrict__ t_eff) {
     const int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= n_ray) return;
     const float c_ray = 1.0f / (1.0f + expf(-s * sdf_apr[ray]));
     float Tk = 1.0f;
     float fk = sdf[ray];
-    for (int k = 0; k < n_z; ++k) {
-        const size_t j = (size_t)k * n_ray + ray;
-        float al = 0.0f;
-        float fn = 0.0f;
-        if (k + 1 < n_z) {
-            fn = sdf[j + n_ray];
-            // alpha = 1 - Phi(f_{k+1}) / Phi(f_k) = -expm1(s (f_{k+1} - f_k)) * sigma(-s f_{k+1})
-            if (fn < fk) al = -expm1f(s * (fn - fk)) * one_minus_cdf(s * fn);
+    for (int k0 = 0; k0 < n_z; k0 += BL_CH) {
+        float fv[BL_CH], av[BL_CH];
+#pragma unroll
+        for (int q = 0; q < BL_CH; ++q) {
+            const int k = k0 + q;
+            fv[q] = k + 1 < n_z ? sdf[(size_t)(k + 1) * n_ray + ray] : 0.0f;
+            av[q] = k < n_z ? refl[(size_t)k * n_ray + ray] : 0.0f;
         }
-        alpha[j] = al;
-        T[j] = Tk;
-        w[j] = refl[j] * al * a_tx;
-        t_eff[j] = Tk + c_ray;
-        Tk = Tk * (1.0f - al);
-        fk = fn;
+#pragma unroll
+        for (int q = 0; q < BL_CH; ++q) {
+            const int k = k0 + q;
+            if (k >= n_z) break;
+            const size_t j = (size_t)k * n_ray + ray;
+            float al = 0.0f;
+            const float fn = fv[q];
+            if (k + 1 < n_z) {
+                // alpha = 1 - Phi(f_{k+1}) / Phi(f_k) = -expm1(s (f_{k+1} - f_k)) * sigma(-s f_{k+1})
+                if (fn < fk) al = -expm1f(s * (fn - fk)) * one_minus_cdf(s * fn);
+            }
+            alpha[j] = al;
+            T[j] = Tk;
+            w[j] = av[q] * al * a_tx;
+            t_eff[j] = Tk + c_ray;
+            Tk = Tk * (1.0f - al);
+            fk = fn;
+        }
     }
 }
 
@@ -163,42 +182,59 @@ __global__ void cdf_kernel(const float* __restrict__ f, int n, float s, float* _
 }
 
 // reverse depth scan; per-ray partials of dL/ds and dL/dA'_tx in `part`
-__global__ void blend_backward_kernel(const float* __restrict__ sdf, const float* __restrict__ refl,
-                                      const float* __restrict__ alpha, const float* __restrict__ T, int n_ray,
-                                      int n_z, float s, float a_tx, const float* __restrict__ d_w,
-                                      const float* __restrict__ d_teff, float* __restrict__ d_sdf,
-                                      float* __restrict__ d_refl, float2* __restrict__ part) {
+__global__ void __launch_bounds__(BL_THREADS) blend_backward_kernel(
+    const float* __restrict__ sdf, const float* __restrict__ refl, const float* __restrict__ alpha,
+    const float* __restrict__ T, int n_ray, int n_z, float s, float a_tx, const float* __restrict__ d_w,
+    const float* __restrict__ d_teff, float* __restrict__ d_sdf, float* __restrict__ d_refl, float2* __restrict__ part) {
     const int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= n_ray) return;
     float gT_next = 0.0f;      // total dL/dT_{k+1}
     float carry = 0.0f;        // contribution to d_sdf[k+1] from alpha_{k+1} (left end point)
     float ds = 0.0f, datx = 0.0f;
     float f_next = 0.0f;
-    for (int k = n_z - 1; k >= 0; --k) {
-        const size_t j = (size_t)k * n_ray + ray;
-        const float fk = sdf[j], ak = refl[j], alk = alpha[j], Tk = T[j];
-        const float dwk = d_w ? d_w[j] : 0.0f;
-        const float dtk = d_teff ? d_teff[j] : 0.0f;
-        float dal = dwk * ak * a_tx;
-        d_refl[j] = dwk * alk * a_tx;
-        datx += dwk * ak * alk;
-        float gT = dtk;
-        float right = 0.0f, left = 0.0f;
-        if (k + 1 < n_z) {
-            dal -= gT_next * Tk;
-            gT = dtk + gT_next * (1.0f - alk);
-            if (f_next < fk) {
-                const float R = 1.0f - alk;                // Phi_{k+1} / Phi_k
-                const float s0 = one_minus_cdf(s * fk), s1 = one_minus_cdf(s * f_next);
-                left = dal * R * s * s0;
-                right = -dal * R * s * s1;
-                ds += -dal * R * (f_next * s1 - fk * s0);
-            }
-            d_sdf[j + n_ray] = carry + right;
+    // chunks of BL_CH depths from the top: [k1 - BL_CH + 1, k1], loads first
+    for (int k1 = n_z - 1; k1 >= 0; k1 -= BL_CH) {
+        float fv[BL_CH], av[BL_CH], alv[BL_CH], tv[BL_CH], dwv[BL_CH], dtv[BL_CH];
+#pragma unroll
+        for (int q = 0; q < BL_CH; ++q) {
+            const int k = k1 - q;
+            const bool ok = k >= 0;
+            const size_t j = (size_t)(ok ? k : 0) * n_ray + ray;
+            fv[q] = ok ? sdf[j] : 0.0f;
+            av[q] = ok ? refl[j] : 0.0f;
+            alv[q] = ok ? alpha[j] : 0.0f;
+            tv[q] = ok ? T[j] : 0.0f;
+            dwv[q] = ok && d_w ? d_w[j] : 0.0f;
+            dtv[q] = ok && d_teff ? d_teff[j] : 0.0f;
         }
-        carry = left;
-        gT_next = gT;
-        f_next = fk;
+#pragma unroll
+        for (int q = 0; q < BL_CH; ++q) {
+            const int k = k1 - q;
+            if (k < 0) break;
+            const size_t j = (size_t)k * n_ray + ray;
+            const float fk = fv[q], ak = av[q], alk = alv[q], Tk = tv[q];
+            const float dwk = dwv[q], dtk = dtv[q];
+            float dal = dwk * ak * a_tx;
+            d_refl[j] = dwk * alk * a_tx;
+            datx += dwk * ak * alk;
+            float gT = dtk;
+            float right = 0.0f, left = 0.0f;
+            if (k + 1 < n_z) {
+                dal -= gT_next * Tk;
+                gT = dtk + gT_next * (1.0f - alk);
+                if (f_next < fk) {
+                    const float R = 1.0f - alk;                // Phi_{k+1} / Phi_k
+                    const float s0 = one_minus_cdf(s * fk), s1 = one_minus_cdf(s * f_next);
+                    left = dal * R * s * s0;
+                    right = -dal * R * s * s1;
+                    ds += -dal * R * (f_next * s1 - fk * s0);
+                }
+                d_sdf[j + n_ray] = carry + right;
+            }
+            carry = left;
+            gT_next = gT;
+            f_next = fk;
+        }
     }
     d_sdf[ray] = carry;
     part[ray] = make_float2(ds, datx);
@@ -248,7 +284,8 @@ geraf_status analytic_fields_impl(const float* prims, int n_prims, const float* 
 geraf_status blend_impl(const float* sdf, const float* refl, int32_t n_ray, int32_t n_z, const float* sdf_apr,
                         const float* sdf_ant, int32_t n_ant, float s, float a_tx, float* alpha, float* T, float* w,
                         float* t_eff, float* c_ant, cudaStream_t st) {
-    blend_kernel<<<grid1d(n_ray, 128), 128, 0, st>>>(sdf, refl, n_ray, n_z, sdf_apr, s, a_tx, alpha, T, w, t_eff);
+    blend_kernel<<<grid1d(n_ray, BL_THREADS), BL_THREADS, 0, st>>>(sdf, refl, n_ray, n_z, sdf_apr, s, a_tx, alpha,
+                                                                     T, w, t_eff);
     if (n_ant > 0) cdf_kernel<<<grid1d(n_ant, 256), 256, 0, st>>>(sdf_ant, n_ant, s, c_ant);
     return cuda_status(cudaGetLastError(), "blend");
 }
@@ -262,8 +299,8 @@ geraf_status blend_backward_impl(const float* sdf, const float* refl, const floa
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "blend_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
-    blend_backward_kernel<<<grid1d(n_ray, 128), 128, 0, st>>>(sdf, refl, alpha, T, n_ray, n_z, s, a_tx, d_w, d_teff,
-                                                             d_sdf, d_refl, part);
+    blend_backward_kernel<<<grid1d(n_ray, BL_THREADS), BL_THREADS, 0, st>>>(sdf, refl, alpha, T, n_ray, n_z, s,
+                                                                           a_tx, d_w, d_teff, d_sdf, d_refl, part);
     reduce_pairs<<<1, 256, 0, st>>>(part, n_ray, d_scalars);
     return cuda_status(cudaGetLastError(), "blend_backward");
 }
