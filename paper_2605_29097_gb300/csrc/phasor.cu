@@ -1154,7 +1154,9 @@ __global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 
             pe[v] = P.c.w;
         }
     }
-    constexpr int NACC = (MODE == MODE_FILTER) ? 2 : 6;
+    // render adjoint: five sums; the sixth output, sum of w2 (n'.d), is n' dotted
+    // with the three sums of w2 d and is formed at the end
+    constexpr int NACC = (MODE == MODE_FILTER) ? 2 : 5;
     float hi[TPK_V][NACC], lo[TPK_V][NACC];
 #pragma unroll
     for (int v = 0; v < TPK_V; ++v)
@@ -1252,7 +1254,6 @@ __global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 
                         in[v][2] = fmaf(w2, R[v].dx, in[v][2]);
                         in[v][3] = fmaf(w2, R[v].dy, in[v][3]);
                         in[v][4] = fmaf(w2, R[v].dz, in[v][4]);
-                        in[v][5] = fmaf(w2, nd, in[v][5]);
                     }
                 }
             }
@@ -1285,8 +1286,12 @@ __global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 
             const float wk = pw[v] * kInv16Pi2;
             const float fac[6] = {kInv16Pi2, 2.0f * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk,
                                   kSqrt2 * wk};
+            float sum[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = __fsub_rn(hi[v][k], lo[v][k]) * fac[k];
+            for (int k = 0; k < 5; ++k) sum[k] = __fsub_rn(hi[v][k], lo[v][k]);
+            sum[5] = pnx[v] * sum[2] + pny[v] * sum[3] + pnz[v] * sum[4];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = sum[k] * fac[k];
         }
     }
 }
