@@ -1016,14 +1016,23 @@ __global__ void cheb_reconstruct_kernel(const float2* __restrict__ partial, int 
     extern __shared__ double2 Mi[];          // [CH_KMAX] moments of this block's antenna
     const int i = blockIdx.x;
     const int K = plan->K;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    // split sums: 4 consecutive lanes per order k, each over every 4th split,
+    // the lanes' sums added in a fixed order (blockDim.x = 128: 32 orders per pass)
+    const int r = threadIdx.x & 3;
+    for (int k0 = 0; k0 < CH_KMAX; k0 += (int)blockDim.x >> 2) {
+        const int k = k0 + (threadIdx.x >> 2);
         double sr = 0.0, si = 0.0;
-        for (int s = 0; s < splits; ++s) {
-            const float2 v = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
-            sr += v.x;
-            si += v.y;
-        }
-        Mi[k] = make_double2(sr, si);
+        if (k < K)
+            for (int s = r; s < splits; s += 4) {
+                const float2 v = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
+                sr += v.x;
+                si += v.y;
+            }
+        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+        si += __shfl_xor_sync(0xffffffffu, si, 1);
+        sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+        si += __shfl_xor_sync(0xffffffffu, si, 2);
+        if (r == 0 && k < K) Mi[k] = make_double2(sr, si);
     }
     __syncthreads();
     for (int n = threadIdx.x; n < n_f; n += blockDim.x) {
@@ -1060,11 +1069,14 @@ __global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __r
         row[0] = hi;
         row[1] = lo;
     }
+    // 4 consecutive lanes per order k, each summing every 4th bin (shorter FP64
+    // dependency chains); the lanes' sums are added in a fixed order
     const int K = plan->K;
-    for (int k = threadIdx.x; k < CH_KMAX; k += blockDim.x) {
+    const int r = threadIdx.x & 3;
+    for (int k = threadIdx.x >> 2; k < CH_KMAX; k += blockDim.x >> 2) {
         double hr = 0.0, hi = 0.0;
         if (i < n_ant && k < K) {
-            for (int n = 0; n < n_f; ++n) {
+            for (int n = r; n < n_f; n += 4) {
                 const float2 v = sig[(size_t)i * n_f + n];
                 const double vr = v.x, vi = conj_sig ? -(double)v.y : (double)v.y;
                 const double2 c = C[(size_t)k * n_f + n];
@@ -1073,11 +1085,17 @@ __global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __r
                 hi += vr * ci + vi * cr;
             }
         }
-        if ((k >> 1) & 1) {
-            hr = -hr;
-            hi = -hi;
+        hr += __shfl_xor_sync(0xffffffffu, hr, 1);
+        hi += __shfl_xor_sync(0xffffffffu, hi, 1);
+        hr += __shfl_xor_sync(0xffffffffu, hr, 2);
+        hi += __shfl_xor_sync(0xffffffffu, hi, 2);
+        if (r == 0) {
+            if ((k >> 1) & 1) {
+                hr = -hr;
+                hi = -hi;
+            }
+            row[2 + k] = make_float4((float)hr, (float)hr, (float)hi, (float)hi);
         }
-        row[2 + k] = make_float4((float)hr, (float)hr, (float)hi, (float)hi);
     }
 }
 
@@ -1472,7 +1490,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, vox, n_vox, ant_xyz, n_ant, band, st);
-        cheb_rows_kernel<<<p.n_ant_pad, 64, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
+        cheb_rows_kernel<<<p.n_ant_pad, 256, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
                                                     p.n_ant_pad, band->n_f, cw.plan, cw.C, 1, 0, crows);
         float kh, kl;
         k0_split(band, &kh, &kl);
@@ -1533,7 +1551,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, xyz, n_pts, ant_xyz, n_ant, band, st);
-        cheb_rows_kernel<<<p.n_ant_pad, 64, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
+        cheb_rows_kernel<<<p.n_ant_pad, 256, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
                                                     p.n_ant_pad, band->n_f, cw.plan, cw.C, 0, 1, crows);
         float kh, kl;
         k0_split(band, &kh, &kl);
