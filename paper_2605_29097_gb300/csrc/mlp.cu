@@ -36,6 +36,7 @@ struct MlpGeom {
     int64_t n_params;
     int64_t off_w[8], off_b[8];   // per layer (hidden layers then head)
     int k_in[8];
+    float wk[21];                 // 2^k pi / half: x-derivative factor of octave k
 };
 
 bool make_geom(const geraf_field_desc* d, int64_t n, MlpGeom* g) {
@@ -64,6 +65,7 @@ bool make_geom(const geraf_field_desc* d, int64_t n, MlpGeom* g) {
         g->off_b[l] = off; off += out;
     }
     g->n_params = off;
+    for (int k = 0; k < g->L; ++k) g->wk[k] = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g->half);
     return true;
 }
 
@@ -90,7 +92,7 @@ __device__ void pe_tile(float* X, const float* __restrict__ xyz, const MlpGeom& 
         const double r = t2 - 2.0 * rint(0.5 * t2);          // exact reduction mod 2
         float sn, cs;
         sincospif((float)r, &sn, &cs);                        // sin, cos of 2^k pi xt
-        const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
+        const float wk = g.wk[k];
         const int fs = 6 * k + d, fc = 6 * k + 3 + d;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -420,22 +422,41 @@ __global__ void __launch_bounds__(BT, 1) mlp_layer_bwd_kernel(const BwdArgs a) {
         // meet a zero HbT and contribute nothing)
         if (!hin) pe_tile<true>(ZT, a.xyz, g, j0);
         __syncthreads();
-        // weight gradient: accw[u][k] += sum_c HbT[c][u] ZT[c][k]
+        // weight gradient: accw[u][k] += sum_c HbT[c][u] ZT[c][k]; an input width of
+        // at most 64 (the encoding layer) leaves the upper half of the k tile zero
+        if (K > 64) {
 #pragma unroll 2
-        for (int c = 0; c < MCOL; ++c) {
-            float hv[BU];
+            for (int c = 0; c < MCOL; ++c) {
+                float hv[BU];
 #pragma unroll
-            for (int q = 0; q < BU; q += 4) {
-                const float4 h4 = *reinterpret_cast<const float4*>(HbT + c * XS + BU * ub + q);
-                hv[q] = h4.x; hv[q + 1] = h4.y; hv[q + 2] = h4.z; hv[q + 3] = h4.w;
+                for (int q = 0; q < BU; q += 4) {
+                    const float4 h4 = *reinterpret_cast<const float4*>(HbT + c * XS + BU * ub + q);
+                    hv[q] = h4.x; hv[q + 1] = h4.y; hv[q + 2] = h4.z; hv[q + 3] = h4.w;
+                }
+                const float4 z0 = *reinterpret_cast<const float4*>(ZT + c * XS + 4 * kb);
+                const float4 z1 = *reinterpret_cast<const float4*>(ZT + c * XS + 64 + 4 * kb);
+                const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+                for (int i = 0; i < BU; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) accw[i][jj] = fmaf(hv[i], zv[jj], accw[i][jj]);
             }
-            const float4 z0 = *reinterpret_cast<const float4*>(ZT + c * XS + 4 * kb);
-            const float4 z1 = *reinterpret_cast<const float4*>(ZT + c * XS + 64 + 4 * kb);
-            const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+        } else if (4 * kb < K) {
+#pragma unroll 2
+            for (int c = 0; c < MCOL; ++c) {
+                float hv[BU];
 #pragma unroll
-            for (int i = 0; i < BU; ++i)
+                for (int q = 0; q < BU; q += 4) {
+                    const float4 h4 = *reinterpret_cast<const float4*>(HbT + c * XS + BU * ub + q);
+                    hv[q] = h4.x; hv[q + 1] = h4.y; hv[q + 2] = h4.z; hv[q + 3] = h4.w;
+                }
+                const float4 z0 = *reinterpret_cast<const float4*>(ZT + c * XS + 4 * kb);
+                const float zv[4] = {z0.x, z0.y, z0.z, z0.w};
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) accw[i][jj] = fmaf(hv[i], zv[jj], accw[i][jj]);
+                for (int i = 0; i < BU; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) accw[i][jj] = fmaf(hv[i], zv[jj], accw[i][jj]);
+            }
         }
         // adjoint of the layer input: zbar[c][k] = sum_u HbT[c][u] W[u][k]  (in place)
         if (hin) {

@@ -40,6 +40,7 @@ struct WNet {
     float beta, cx, cy, cz, half;
     int64_t off_w[WMAX_LAYERS + 1], off_b[WMAX_LAYERS + 1];
     int64_t n_params;
+    float wk[21];            // 2^k pi / half: x-derivative factor of octave k
     int k_in(int l) const { return l == 0 ? K0 : W; }
     int k_pad(int l) const { return l == 0 ? K0p : W; }
 };
@@ -74,6 +75,7 @@ bool make_wnet(const float* params, int L, int W, int NH, int head_out, int S, c
         g->off_b[l] = off; off += out;
     }
     g->n_params = off;
+    for (int k = 0; k < L; ++k) g->wk[k] = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g->half);
     return true;
 }
 
@@ -97,7 +99,7 @@ __global__ void wpe_kernel(const float* __restrict__ xyz, int64_t n, WNet g, flo
         const double r = t2 - 2.0 * rint(0.5 * t2);          // exact reduction mod 2
         float sn, cs;
         sincospif((float)r, &sn, &cs);                        // sin, cos of 2^k pi xt
-        const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
+        const float wk = g.wk[k];
         const int fs = 6 * k + d, fc = 6 * k + 3 + d;
         for (int s = 0; s < g.S; ++s) {
             float vs, vc;
