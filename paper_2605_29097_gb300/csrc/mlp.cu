@@ -265,23 +265,27 @@ struct BwdArgs {
     int layer;          // hidden layer index for the layer kernel
 };
 
-// head: dL/dW_head, dL/db_head and the adjoint of the last hidden activation
-__global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a) {
-    __shared__ float red[MTHREADS * 2];
-    __shared__ float redb[2 * 8];
+// head: dL/dW_head, dL/db_head and the adjoint of the last hidden activation.
+// HT threads = HG groups of 128 (one unit each); group q takes points
+// base + HG r + q; the groups' sums are added in a fixed order.
+constexpr int HT = 1024;
+constexpr int HG = HT / MW;
+__global__ void __launch_bounds__(HT) mlp_head_bwd_kernel(const BwdArgs a) {
+    __shared__ float red[2][HT];
+    __shared__ float redb[2][HG];
     const MlpGeom& g = a.g;
-    const int t = threadIdx.x, u = t & (MW - 1), half = t >> 7;
+    const int t = threadIdx.x, u = t & (MW - 1), grp = t >> 7;
     const float* Wh = a.params + g.off_w[g.NH];
     const float w0 = Wh[u], w1 = Wh[MW + u];
     const float* hsv = a.saved + (int64_t)(g.NH - 1) * g.n * 4 * MW;
     const float* asv = a.saved + (int64_t)g.NH * g.n * 4 * MW;
     float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
-    constexpr int R = 8;                                   // points per thread per round, loads in flight
-    for (int64_t base = (int64_t)blockIdx.x * 2 * R; base < g.n; base += (int64_t)gridDim.x * 2 * R) {
+    constexpr int R = 4;                                   // points per thread per round, loads in flight
+    for (int64_t base = (int64_t)blockIdx.x * HG * R; base < g.n; base += (int64_t)gridDim.x * HG * R) {
         float df[R], dl[R], dG[R][3], h0[R], hd[R][3];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t j = base + 2 * r + half;
+            const int64_t j = base + HG * r + grp;
             const bool ok = j < g.n;
             const int64_t jj = ok ? j : 0;
             const float* h = hsv + jj * 4 * MW;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a)
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t j = base + 2 * r + half;
+            const int64_t j = base + HG * r + grp;
             if (j >= g.n) continue;
             const float sg = sigm(g.beta * h0[r]);
             const float z = softplus_b(h0[r], g.beta);
@@ -313,18 +317,28 @@ __global__ void __launch_bounds__(MTHREADS) mlp_head_bwd_kernel(const BwdArgs a)
             if (u == 0) { gb0 += df[r]; gb1 += dl[r]; }
         }
     }
-    red[t] = gw0;
-    red[MTHREADS + t] = gw1;
-    if (u == 0) { redb[2 * half] = gb0; redb[2 * half + 1] = gb1; }
+    red[0][t] = gw0;
+    red[1][t] = gw1;
+    if (u == 0) { redb[0][grp] = gb0; redb[1][grp] = gb1; }
     __syncthreads();
     float* out = a.partial + (int64_t)blockIdx.x * g.n_params;
     if (t < MW) {
-        out[g.off_w[g.NH] + t] = red[t] + red[t + MW];
-        out[g.off_w[g.NH] + MW + t] = red[MTHREADS + t] + red[MTHREADS + t + MW];
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int q = 0; q < HG; ++q) {
+            s0 += red[0][q * MW + t];
+            s1 += red[1][q * MW + t];
+        }
+        out[g.off_w[g.NH] + t] = s0;
+        out[g.off_w[g.NH] + MW + t] = s1;
     }
     if (t == 0) {
-        out[g.off_b[g.NH]] = redb[0] + redb[2];
-        out[g.off_b[g.NH] + 1] = redb[1] + redb[3];
+        float b0 = 0.0f, b1 = 0.0f;
+        for (int q = 0; q < HG; ++q) {
+            b0 += redb[0][q];
+            b1 += redb[1][q];
+        }
+        out[g.off_b[g.NH]] = b0;
+        out[g.off_b[g.NH] + 1] = b1;
     }
 }
 
@@ -616,7 +630,7 @@ geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int6
         attr = true;
     }
     BwdArgs a{g, d->params, xyz, static_cast<const float*>(saved), d_sdf, d_grad, d_refl, zbar, partial, 0};
-    mlp_head_bwd_kernel<<<n_cta, MTHREADS, 0, st>>>(a);
+    mlp_head_bwd_kernel<<<n_cta, HT, 0, st>>>(a);
     for (int l = g.NH - 1; l >= 0; --l) {
         a.layer = l;
         mlp_layer_bwd_kernel<<<n_cta, BT, bwd_smem(), st>>>(a);
