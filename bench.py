@@ -43,10 +43,10 @@ PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
 # of the small C2 case (65 536 points, 32^3 voxels, 4096 antennas, 128 bins),
 # scaled to a full launch by the points or voxels it processes (the records read
 # and the split partials written both grow in proportion).
-NCU_DRAM_SMALL = {"render": (29.36e6, "points", 65536), "render_backward": (7.48e6, "points", 65536),
-                  "filter": (4.73e6, "voxels", 32768), "filter_backward": (39.10e6, "voxels", 32768)}
+NCU_DRAM_SMALL = {"render": (9.36e6 + 15.67e6, "points", 65536), "render_backward": (7.48e6, "points", 65536),
+                  "filter": (4.73e6, "voxels", 32768), "filter_backward": (8.15e6 + 16.33e6, "voxels", 32768)}
 # the same counters taken at the full C2 size (one launch each, a 1-pass capture)
-NCU_DRAM_FULL = {"render": 102.91e6 + 42.44e6, "render_backward": 208.32e6 + 69.80e6}
+NCU_DRAM_FULL = {"render": 108.70e6 + 30.65e6, "render_backward": 208.32e6 + 69.80e6}
 
 
 def _env_int(k, d):
@@ -637,7 +637,9 @@ def main():
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": per_call_roof[dom]["frac"],
                          "traffic": traffic, "traffic_basis": traffic_basis,
                          "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz",
-                         "work_basis": ("Chebyshev phasor sums: pairs x order x 6 flops; per-bin recurrence: "
+                         "work_basis": ("Chebyshev phasor sums: pairs x order x 6 flops, order = the whole-set "
+                                        "order K (render and filter adjoint expand per split with orders <= K, "
+                                        "so their executed work is lower); per-bin recurrence: "
                                         "terms x 10 (render, filter adjoint) or 8 (filter, render adjoint) flops; "
                                         f"MLP adjoint: 2 x {macs} MAC per point"),
                          "calls": per_call_roof},

@@ -862,13 +862,24 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
     }
 }
 
+// Expansion of one split of the to-bins sums: the split's points form a thin
+// depth slab, so their range interval against the antennas, and with it the
+// order K, is narrower than the whole call's
+struct SplitPlan {
+    float r_c, inv_dr;
+    int K;
+    int pad;
+};
+
 struct ChebBinsArgs {
     const PtRec* pts;          // tiles of CH_TP records
     const float4* ant;         // n_ant_pad (x, y, z, c_ant)
     int n_ant;
     int n_tiles;
     int tiles_per_split;
-    const ChebPlan* plan;
+    const ChebPlan* plan;      // the whole call's plan (run_cheb)
+    const SplitPlan* splan;    // [splits]
+    const int* kmax;           // largest split order: picks the kernel instance
     float kh, kl;              // K0 = 2 f0 / c as double-single (cycles per metre)
     float2* partial;           // [splits][n_ant][CH_KMAX]
     int* err;
@@ -879,15 +890,22 @@ struct ChebBinsArgs {
 // The core is 3 scalar FMAs per order (T_k recurrence, real and imaginary
 // accumulation): the FMA pipe, not the issue rate, bounds this kernel, and a
 // packed (re, im) form would spend a wasted lane on the recurrence.
-// KC = 8-order groups held in registers: the KC = 4 instance (orders 0..31,
-// no per-group guards, 64 moment registers, four CTAs per SM) runs when the
-// plan's K <= 32, the KC = 8 instance (orders 32..63 guarded by K) otherwise;
-// both are launched and the one that does not apply returns at once.
+// KC = 8-order groups held in registers: the KC = 3 and KC = 4 instances
+// (orders 0..23 or 0..31, no per-group guards) run when the largest split
+// order is at most 24 or 32, the KC = 8 instance (orders beyond 32 guarded by
+// the split's K) otherwise; all are launched and those that do not apply
+// return at once. Each split expands the bin phase over its own range
+// interval (SplitPlan).
 template <bool kComplexAmp, int KC>
-__global__ void __launch_bounds__(CH_THREADS, KC == 4 ? GERAF_CH_BINS_CTAS : 1) cheb_bins_kernel(const ChebBinsArgs args) {
+__global__ void __launch_bounds__(CH_THREADS, KC <= 4 ? GERAF_CH_BINS_CTAS : 1) cheb_bins_kernel(const ChebBinsArgs args) {
     constexpr int KM = 8 * KC;
+    constexpr int KU = KC < 4 ? 8 * KC : 32;                 // orders computed without guards
     if (!args.plan->run_cheb) return;
-    if ((KC == 4) != (args.plan->K <= 32)) return;
+    {
+        const int km = *args.kmax;
+        const int want = km <= 24 ? 3 : (km <= 32 ? 4 : 8);
+        if (want != KC) return;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     PtRec* tiles = reinterpret_cast<PtRec*>(smem);                              // [2][CH_TP]
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * CH_TP * sizeof(PtRec));
@@ -899,8 +917,9 @@ __global__ void __launch_bounds__(CH_THREADS, KC == 4 ? GERAF_CH_BINS_CTAS : 1) 
     const int tile0 = split * args.tiles_per_split;
     const int tile1 = min(tile0 + args.tiles_per_split, args.n_tiles);
     const int n_my = tile1 - tile0;
-    const int K = args.plan->K;
-    const float r_c = args.plan->r_c, inv_dr = args.plan->inv_dr;
+    const SplitPlan sp = args.splan[split];
+    const int K = sp.K;
+    const float r_c = sp.r_c, inv_dr = sp.inv_dr;
     const float4 A4 = args.ant[ia];                          // padded: always readable
     float4 Ah, Al;
     split3(A4.x, A4.y, A4.z, Ah, Al);
@@ -966,7 +985,7 @@ __global__ void __launch_bounds__(CH_THREADS, KC == 4 ? GERAF_CH_BINS_CTAS : 1) 
             mi[1] = fmaf(ai_, x, mi[1]);
 #pragma unroll
             for (int kc = 0; kc < KM; kc += 8) {
-                if (kc < 32 || kc < K) {
+                if (kc < KU || kc < K) {
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         const int k = kc + kk;
@@ -984,7 +1003,7 @@ __global__ void __launch_bounds__(CH_THREADS, KC == 4 ? GERAF_CH_BINS_CTAS : 1) 
         if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
 #pragma unroll
             for (int kc = 0; kc < KM; kc += 8)
-                if (kc < 32 || kc < K)
+                if (kc < KU || kc < K)
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         float2 o = outer[(kc + kk) * CH_THREADS + t];
@@ -1006,45 +1025,191 @@ __global__ void __launch_bounds__(CH_THREADS, KC == 4 ? GERAF_CH_BINS_CTAS : 1) 
     }
 }
 
-size_t cheb_bins_smem(int km) { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)km * CH_THREADS * sizeof(float2); }
-
-// out(i, n) = sum_k C_k(n) sum_splits M_k(i), FP64
-__global__ void cheb_reconstruct_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
-                                        const ChebPlan* __restrict__ plan, const double2* __restrict__ C,
-                                        float2* __restrict__ out) {
-    if (!plan->run_cheb) return;
-    extern __shared__ double2 Mi[];          // [CH_KMAX] moments of this block's antenna
-    const int i = blockIdx.x;
-    const int K = plan->K;
-    // split sums: 4 consecutive lanes per order k, each over every 4th split,
-    // the lanes' sums added in a fixed order (blockDim.x = 128: 32 orders per pass)
-    const int r = threadIdx.x & 3;
-    for (int k0 = 0; k0 < CH_KMAX; k0 += (int)blockDim.x >> 2) {
-        const int k = k0 + (threadIdx.x >> 2);
-        double sr = 0.0, si = 0.0;
-        if (k < K)
-            for (int s = r; s < splits; s += 4) {
-                const float2 v = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
-                sr += v.x;
-                si += v.y;
-            }
-        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
-        si += __shfl_xor_sync(0xffffffffu, si, 1);
-        sr += __shfl_xor_sync(0xffffffffu, sr, 2);
-        si += __shfl_xor_sync(0xffffffffu, si, 2);
-        if (r == 0 && k < K) Mi[k] = make_double2(sr, si);
+// bounding box of each split's records (positions rebuilt exactly as xh + xl;
+// padding records included, they sit at a real point's position)
+__global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, int tiles_per_split,
+                                  float* __restrict__ box) {
+    __shared__ float red[6][256];
+    const int sp = blockIdx.x;
+    const int64_t r0 = (int64_t)sp * tiles_per_split * CH_TP;
+    const int64_t r1 = min((int64_t)(sp + 1) * tiles_per_split, (int64_t)n_tiles) * CH_TP;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const PtRec P = pts[r];
+        const float x[3] = {P.a.x + P.c.x, P.a.y + P.c.y, P.a.z + P.c.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fminf(mn[d], x[d]);
+            mx[d] = fmaxf(mx[d], x[d]);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        red[d][threadIdx.x] = mn[d];
+        red[3 + d][threadIdx.x] = mx[d];
     }
     __syncthreads();
-    for (int n = threadIdx.x; n < n_f; n += blockDim.x) {
-        double sr = 0.0, si = 0.0;
-        for (int k = 0; k < K; ++k) {
-            const double2 c = C[(size_t)k * n_f + n], m = Mi[k];
-            sr += c.x * m.x - c.y * m.y;
-            si += c.x * m.y + c.y * m.x;
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k)
+            for (int d = 0; d < 3; ++d) {
+                red[d][threadIdx.x] = fminf(red[d][threadIdx.x], red[d][threadIdx.x + k]);
+                red[3 + d][threadIdx.x] = fmaxf(red[3 + d][threadIdx.x], red[3 + d][threadIdx.x + k]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) box[sp * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// One block per split: the split's range interval against all antennas, its
+// order K (the whole call's rule: Bessel tail <= eps), and its FP32
+// coefficient table Cs[sp][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
+// (Bessel values in FP64). kmax collects the largest split order.
+__global__ void split_plan_kernel(const float* __restrict__ box, const float* __restrict__ ant, int n_ant,
+                                  double Kd, int n_f, double eps, const ChebPlan* __restrict__ gplan,
+                                  SplitPlan* __restrict__ splan, float2* __restrict__ Cs, int* __restrict__ kmax) {
+    if (!gplan->run_cheb) return;
+    __shared__ float rr[2][256];
+    __shared__ int sK;
+    __shared__ float s_rc, s_inv;
+    const int sp = blockIdx.x, t = threadIdx.x;
+    const float* bx = box + sp * 6;
+    float lo = INFINITY, hi = 0.0f;
+    for (int i = t; i < n_ant; i += blockDim.x) {
+        float dn = 0.0f, df = 0.0f;
+        for (int d = 0; d < 3; ++d) {
+            const float a = ant[d * n_ant + i];
+            const float e = fmaxf(fmaxf(bx[d] - a, a - bx[3 + d]), 0.0f);
+            const float f = fmaxf(fabsf(a - bx[d]), fabsf(bx[3 + d] - a));
+            dn += e * e;
+            df += f * f;
         }
-        out[(size_t)i * n_f + n] = make_float2((float)sr, (float)si);
+        lo = fminf(lo, sqrtf(dn));
+        hi = fmaxf(hi, sqrtf(df));
+    }
+    rr[0][t] = lo;
+    rr[1][t] = hi;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (t < k) {
+            rr[0][t] = fminf(rr[0][t], rr[0][t + k]);
+            rr[1][t] = fmaxf(rr[1][t], rr[1][t + k]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double rl = rr[0][0], rh = rr[1][0];
+        const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6, 1e-5);
+        const float rc = (float)(0.5 * (rh + rl));
+        const float inv = (float)(1.0 / dr);
+        const double a_max = 2.0 * 3.14159265358979323846 * (n_f - 1) * Kd / (double)inv;
+        double J[CH_KMAX + 8];
+        bessel_j(a_max, CH_KMAX + 8, J);
+        int K = CH_KMAX;
+        double tail = 0.0;
+        for (int k = CH_KMAX + 7; k >= 0; --k) {
+            tail += 2.0 * fabs(J[k]);
+            if (tail > eps) { K = k + 1; break; }
+        }
+        if (K < 2) K = 2;
+        if (K > CH_KMAX) K = CH_KMAX;
+        splan[sp] = SplitPlan{rc, inv, K, 0};
+        atomicMax(kmax, K);
+        sK = K;
+        s_rc = rc;
+        s_inv = inv;
+    }
+    __syncthreads();
+    const int K = sK;
+    const double dr = 1.0 / (double)s_inv;
+    float2* C = Cs + (size_t)sp * CH_KMAX * n_f;
+    for (int n = t; n < n_f; n += blockDim.x) {
+        double J[CH_KMAX];
+        const double an = 2.0 * 3.14159265358979323846 * n * Kd * dr;
+        bessel_j(an, K, J);
+        double sphi, cphi;
+        sincospi(-2.0 * (double)n * Kd * (double)s_rc, &sphi, &cphi);
+        for (int k = 0; k < K; ++k) {
+            const double m = (k == 0 ? 1.0 : 2.0) * J[k];
+            double pr, pi;      // (-j)^k
+            switch (k & 3) {
+                case 0: pr = 1.0; pi = 0.0; break;
+                case 1: pr = 0.0; pi = -1.0; break;
+                case 2: pr = -1.0; pi = 0.0; break;
+                default: pr = 0.0; pi = 1.0; break;
+            }
+            const double ar = m * pr, ai = m * pi;
+            C[(size_t)k * n_f + n] = make_float2((float)(cphi * ar - sphi * ai), (float)(cphi * ai + sphi * ar));
+        }
     }
 }
+
+// sum over the splits of a group of RS splits of sum_k Cs[sp][k][n] M_k(sp, i):
+// block = (RA antennas, split group); thread = bin, the RA antennas in
+// registers so each table value is loaded once; the per-split sums (FP32, at
+// most 64 terms) are added with Kahan compensation across the group's splits.
+// The groups' sums are added in FP64, in group order, by sum_split_groups.
+constexpr int RA = 4;
+constexpr int RS = 32;
+__global__ void cheb_reconstruct_split_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
+                                              const ChebPlan* __restrict__ gplan,
+                                              const SplitPlan* __restrict__ splan, const float2* __restrict__ Cs,
+                                              float2* __restrict__ group_out) {
+    if (!gplan->run_cheb) return;
+    const int i0 = blockIdx.x * RA;
+    const int s0 = blockIdx.y * RS, s1 = min(splits, s0 + RS);
+    for (int n = threadIdx.x; n < n_f; n += blockDim.x) {
+        float hr[RA], hi[RA], cr_[RA], ci_[RA];
+#pragma unroll
+        for (int q = 0; q < RA; ++q) hr[q] = hi[q] = cr_[q] = ci_[q] = 0.0f;
+        for (int s = s0; s < s1; ++s) {
+            const int K = splan[s].K;
+            const float2* C = Cs + (size_t)s * CH_KMAX * n_f + n;
+            float sr[RA], si[RA];
+#pragma unroll
+            for (int q = 0; q < RA; ++q) sr[q] = si[q] = 0.0f;
+            for (int k = 0; k < K; ++k) {
+                const float2 c = C[(size_t)k * n_f];
+#pragma unroll
+                for (int q = 0; q < RA; ++q) {
+                    const int i = min(i0 + q, n_ant - 1);
+                    const float2 m = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
+                    sr[q] = fmaf(c.x, m.x, fmaf(-c.y, m.y, sr[q]));
+                    si[q] = fmaf(c.x, m.y, fmaf(c.y, m.x, si[q]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RA; ++q) {
+                float y = sr[q] - cr_[q], tt = hr[q] + y;
+                cr_[q] = (tt - hr[q]) - y;
+                hr[q] = tt;
+                y = si[q] - ci_[q];
+                tt = hi[q] + y;
+                ci_[q] = (tt - hi[q]) - y;
+                hi[q] = tt;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RA; ++q)
+            if (i0 + q < n_ant)
+                group_out[((size_t)blockIdx.y * n_ant + i0 + q) * n_f + n] = make_float2(hr[q], hi[q]);
+    }
+}
+
+__global__ void sum_split_groups(const float2* __restrict__ group_out, int groups, int64_t n,
+                                 const ChebPlan* __restrict__ gplan, float2* __restrict__ out) {
+    if (!gplan->run_cheb) return;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double sr = 0.0, si = 0.0;
+    for (int g = 0; g < groups; ++g) {
+        const float2 v = group_out[(size_t)g * n + e];
+        sr += v.x;
+        si += v.y;
+    }
+    out[e] = make_float2((float)sr, (float)si);
+}
+
+size_t cheb_bins_smem(int km) { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)km * CH_THREADS * sizeof(float2); }
 
 // antenna rows for the Chebyshev point kernels: two heads, (xh, yh, zh, c) and
 // (xl, yl, zl, 0) (the split position), then CH_KMAX float4
@@ -1369,7 +1534,8 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant) {
     q.n_tiles = (int)(n_pad / CH_TP);
     const int64_t max_splits = std::max<int64_t>(1, (int64_t)(CH_PARTIAL_BYTES / ((size_t)n_ant * CH_KMAX * 8)));
     const int64_t want = std::max<int64_t>(1, (4LL * 4 * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
-    int64_t sp = std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles);
+    // at most 512 splits: each carries its own coefficient table
+    int64_t sp = std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles), 512);
     q.tiles_per_split = (int)((q.n_tiles + sp - 1) / sp);
     q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
     return q;
@@ -1397,9 +1563,19 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
     ChebWs cw{};
     float2* cpart = nullptr;
+    float* sbox = nullptr;
+    SplitPlan* splan = nullptr;
+    float2* scs = nullptr;
+    int* kmax = nullptr;
+    float2* gout = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_pts, band->n_f);
         cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
+        sbox = c.take<float>((size_t)q.splits * 6);
+        splan = c.take<SplitPlan>(q.splits);
+        scs = c.take<float2>((size_t)q.splits * CH_KMAX * band->n_f);
+        kmax = c.take<int>(1);
+        gout = c.take<float2>((size_t)((q.splits + RS - 1) / RS) * n_ant * band->n_f);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", name, *ws_bytes, c.used);
@@ -1414,6 +1590,8 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     if (!attr_set) {
         cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_bins_kernel<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(cheb_bins_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(cheb_bins_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(cheb_bins_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1423,14 +1601,23 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, positions, n_pts, ant_xyz, n_ant, band, st);
+        cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e, name);
+        split_bbox_kernel<<<q.splits, 256, 0, st>>>(pts, q.n_tiles, q.tiles_per_split, sbox);
+        split_plan_kernel<<<q.splits, 256, 0, st>>>(sbox, ant_xyz, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
+                                                    cw.plan, splan, scs, kmax);
         float kh, kl;
         k0_split(band, &kh, &kl);
-        ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, kh, kl, cpart, err};
-        cheb_bins_kernel<kComplexAmp, 4><<<dim3(q.ant_blocks, q.splits), CH_THREADS, cheb_bins_smem(32), st>>>(ca);
-        cheb_bins_kernel<kComplexAmp, 8><<<dim3(q.ant_blocks, q.splits), CH_THREADS, cheb_bins_smem(64), st>>>(ca);
-        cheb_reconstruct_kernel<<<n_ant, 128, CH_KMAX * sizeof(double2), st>>>(cpart, q.splits, n_ant, band->n_f,
-                                                                               cw.plan, cw.C,
-                                                                               reinterpret_cast<float2*>(out));
+        ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, splan, kmax, kh, kl, cpart, err};
+        const dim3 grid(q.ant_blocks, q.splits);
+        cheb_bins_kernel<kComplexAmp, 3><<<grid, CH_THREADS, cheb_bins_smem(24), st>>>(ca);
+        cheb_bins_kernel<kComplexAmp, 4><<<grid, CH_THREADS, cheb_bins_smem(32), st>>>(ca);
+        cheb_bins_kernel<kComplexAmp, 8><<<grid, CH_THREADS, cheb_bins_smem(64), st>>>(ca);
+        const int groups = (q.splits + RS - 1) / RS;
+        cheb_reconstruct_split_kernel<<<dim3((n_ant + RA - 1) / RA, groups), 128, 0, st>>>(
+            cpart, q.splits, n_ant, band->n_f, cw.plan, splan, scs, gout);
+        sum_split_groups<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(
+            gout, groups, (int64_t)n_ant * band->n_f, cw.plan, reinterpret_cast<float2*>(out));
         run_direct = &cw.plan->use_direct;
     }
     ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk, run_direct};
