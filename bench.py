@@ -43,10 +43,10 @@ PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
 # of the small C2 case (65 536 points, 32^3 voxels, 4096 antennas, 128 bins),
 # scaled to a full launch by the points or voxels it processes (the records read
 # and the split partials written both grow in proportion).
-NCU_DRAM_SMALL = {"render": (9.36e6 + 15.67e6, "points", 65536), "render_backward": (7.48e6, "points", 65536),
-                  "filter": (4.73e6, "voxels", 32768), "filter_backward": (8.15e6 + 16.33e6, "voxels", 32768)}
+NCU_DRAM_SMALL = {"render": (9.36e6 + 15.67e6, "points", 65536), "filter_backward": (8.15e6 + 16.33e6, "voxels", 32768),
+                  "render_backward": (141.86e6 + 18.92e6, "points", 65536)}
 # the same counters taken at the full C2 size (one launch each, a 1-pass capture)
-NCU_DRAM_FULL = {"render": 108.70e6 + 30.65e6, "render_backward": 208.32e6 + 69.80e6}
+NCU_DRAM_FULL = {"render": 108.70e6 + 30.65e6, "render_backward": 475.83e6 + 89.73e6}
 
 
 def _env_int(k, d):
@@ -576,6 +576,12 @@ def main():
     xyz_o, _ = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
     orders = {"points": G.geraf_chebyshev_order(xyz_o, geo.ant, geo.band),
               "voxels": G.geraf_chebyshev_order(geo.vox, geo.ant, geo.band)}
+    # orders each Chebyshev call evaluates (per split or point group; the mean
+    # over the points of the orders per pair the running kernel instance computes)
+    cheb_work = {"render": G.geraf_chebyshev_work(xyz_o, geo.ant, geo.band, False),
+                 "render_backward": G.geraf_chebyshev_work(xyz_o, geo.ant, geo.band, True),
+                 "filter": G.geraf_chebyshev_work(geo.vox, geo.ant, geo.band, True),
+                 "filter_backward": G.geraf_chebyshev_work(geo.vox, geo.ant, geo.band, False)}
     del xyz_o
 
     if rank == 0:
@@ -587,14 +593,22 @@ def main():
         n_vox = int(geo.vox.shape[1])
         pairs = {"render": n_pts * n_ant, "render_backward": n_pts * n_ant,
                  "filter": n_vox * n_ant, "filter_backward": n_vox * n_ant, "fields_backward": n_pts}
-        order_of = {"render": orders["points"], "render_backward": orders["points"],
-                    "filter": orders["voxels"], "filter_backward": orders["voxels"], "fields_backward": 0}
+        order_of = {nm: cheb_work[nm][3] for nm in PHASOR_CALLS}
+        order_of["fields_backward"] = 0
+        whole_order = {"render": orders["points"], "render_backward": orders["points"],
+                       "filter": orders["voxels"], "filter_backward": orders["voxels"]}
         macs = mlp_backward_macs(spec)
 
         def roof(nm, ms, order):
             fl = call_flops(nm, pairs[nm], geo.band.n_f, order, macs, n_pts)
-            return {"ms": round(ms, 3), "tflops": fl / (ms * 1e-3) / 1e12,
-                    "frac": fl / (ms * 1e-3) / 1e12 / fp32_peak}
+            r = {"ms": round(ms, 3), "tflops": fl / (ms * 1e-3) / 1e12,
+                 "frac": fl / (ms * 1e-3) / 1e12 / fp32_peak}
+            if order > 0:
+                # the same time against the work of one expansion over the whole set
+                fw = call_flops(nm, pairs[nm], geo.band.n_f, whole_order[nm], macs, n_pts)
+                r.update(orders_per_pair=round(order, 3), whole_set_order=whole_order[nm],
+                         frac_whole_set_order=fw / (ms * 1e-3) / 1e12 / fp32_peak)
+            return r
 
         per_call_roof = {nm: roof(nm, per_kernel[nm], order_of[nm]) for nm in names}
         rec_roof = {nm: roof(nm, per_kernel_rec[nm], 0) for nm in PHASOR_CALLS}
@@ -637,13 +651,17 @@ def main():
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": per_call_roof[dom]["frac"],
                          "traffic": traffic, "traffic_basis": traffic_basis,
                          "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz",
-                         "work_basis": ("Chebyshev phasor sums: pairs x order x 6 flops, order = the whole-set "
-                                        "order K (render and filter adjoint expand per split with orders <= K, "
-                                        "so their executed work is lower); per-bin recurrence: "
+                         "work_basis": ("Chebyshev phasor sums: pairs x orders evaluated per pair x 6 flops "
+                                        "(the running instance's orders per split or point group, mean over "
+                                        "the points, geraf_chebyshev_work; calls[*].frac_whole_set_order "
+                                        "counts one expansion of the whole set's order instead); per-bin recurrence: "
                                         "terms x 10 (render, filter adjoint) or 8 (filter, render adjoint) flops; "
                                         f"MLP adjoint: 2 x {macs} MAC per point"),
                          "calls": per_call_roof},
             "phasor_method": {"chebyshev_order": orders,
+                              "chebyshev_work": {nm: {"whole_set_order": w[0], "max_part_order": w[1],
+                                                      "instance_orders": w[2], "orders_per_pair": round(w[3], 3)}
+                                                 for nm, w in cheb_work.items()},
                               "recurrence_per_call_ms": {k: round(per_kernel_rec[k], 3) for k in PHASOR_CALLS},
                               "recurrence_roofline": rec_roof,
                               "recurrence_terms_per_s": 2 * (n_pts + n_vox) * n_ant * geo.band.n_f

@@ -66,11 +66,13 @@ typedef struct {
  *   GERAF_PHASOR_RECURRENCE: exact phasor per bin by angle-addition
  *     recurrence, re-seeded from a sincos every 32 bins;
  *   GERAF_PHASOR_CHEBYSHEV: the bin phase exp(-j 2 pi n df 2r/c) expanded in
- *     Chebyshev polynomials of the range over the call's range interval
- *     (Jacobi-Anger, terms kept until the Bessel tail is below 1e-9), so the
- *     work per (point, antenna) pair follows the order K instead of n_f;
- *     when K would exceed 64 the recurrence runs instead (decided on the
- *     device; geraf_chebyshev_order reports the choice);
+ *     Chebyshev polynomials of the range (Jacobi-Anger, terms kept until the
+ *     Bessel tail is below 1e-9), each run of consecutive points over its
+ *     own range interval, so the work per (point, antenna) pair follows the
+ *     order instead of n_f; when the whole call's order K would exceed 64
+ *     the recurrence runs instead (decided on the device;
+ *     geraf_chebyshev_order reports the choice, geraf_chebyshev_work the
+ *     orders evaluated);
  *   GERAF_PHASOR_AUTO (0): Chebyshev for n_f >= 64, recurrence below. */
 typedef struct {
     double f0;
@@ -333,6 +335,29 @@ geraf_status geraf_masked_loss(const float* P, const float* target, float* histo
 geraf_status geraf_chebyshev_order(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
                                    const geraf_band* band, void* ws, size_t* ws_bytes, int32_t* order,
                                    void* stream);
+
+/*
+ * geraf_chebyshev_work — the orders one Chebyshev phasor call evaluates for
+ * points (or voxels) xyz [3][n] against ant_xyz [3][n_ant] over `band`.
+ * to_points = 0: the to-bins direction (geraf_render on points,
+ * geraf_filter_backward on voxels), which expands each split of consecutive
+ * point tiles over its own range interval; to_points = 1: the to-points
+ * direction (geraf_filter, geraf_render_backward), which expands each group of
+ * consecutive points (at least 2048) over its own interval. Outputs:
+ * orders[0] = the whole set's order K (0: the recurrence runs; then all
+ * outputs are 0), orders[1] = the largest split or group order, orders[2] =
+ * the orders compiled into the kernel instance that runs (24, 32 or 64);
+ * *mean_orders = the orders evaluated per (point, antenna) pair, averaged
+ * over the points (the instance's 24 or 32, or for the 64-order instance 32
+ * plus the part's own orders beyond 32 in blocks of 8). Runs the same device
+ * plans as the sums, then waits for the stream: synchronous. The paper has no
+ * counterpart; this reports the cost model of a call. ws: ws == NULL queries
+ * *ws_bytes. GERAF_ERR_INVALID_ARG for n < 1, n >= 2^31, n_ant < 1, a NULL
+ * band, or to_points not 0 or 1.
+ */
+geraf_status geraf_chebyshev_work(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
+                                  const geraf_band* band, int32_t to_points, void* ws, size_t* ws_bytes,
+                                  int32_t* orders, double* mean_orders, void* stream);
 
 /*
  * Learned proposal sampler (the paper is silent on it; it cuts the number of

@@ -8,7 +8,7 @@ from .geraf import (AnalyticField, Band, MLPField, make_grid, geraf_sample, gera
                     geraf_render_backward, geraf_filter, geraf_filter_backward, geraf_poll_device_error,
                     geraf_check_bounded_wait,
                     geraf_render_noalloc, Proposal, geraf_proposal_density, geraf_sample_proposal,
-                    geraf_sample_backward, geraf_chebyshev_order, geraf_masked_loss,
+                    geraf_sample_backward, geraf_chebyshev_order, geraf_chebyshev_work, geraf_masked_loss,
                     SAMPLE_UNIFORM, SAMPLE_STRATIFIED, PREC_FP32, PREC_BF16,
                     PHASOR_AUTO, PHASOR_RECURRENCE, PHASOR_CHEBYSHEV)
 from ._lib import GerafError
@@ -18,5 +18,5 @@ __all__ = ["AnalyticField", "Band", "MLPField", "make_grid", "geraf_sample", "ge
            "geraf_render_backward", "geraf_filter", "geraf_filter_backward", "geraf_poll_device_error",
            "geraf_check_bounded_wait",
            "GerafError", "geraf_render_noalloc", "Proposal", "geraf_proposal_density", "geraf_sample_proposal",
-           "geraf_sample_backward", "geraf_chebyshev_order", "geraf_masked_loss", "SAMPLE_UNIFORM", "SAMPLE_STRATIFIED", "PREC_FP32",
+           "geraf_sample_backward", "geraf_chebyshev_order", "geraf_chebyshev_work", "geraf_masked_loss", "SAMPLE_UNIFORM", "SAMPLE_STRATIFIED", "PREC_FP32",
            "PREC_BF16", "PHASOR_AUTO", "PHASOR_RECURRENCE", "PHASOR_CHEBYSHEV"]

@@ -55,6 +55,8 @@ SIGNATURES = {
     "geraf_filter": [vp, vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp, vp, vp, vp],
     "geraf_filter_backward": [vp, i32, ctypes.POINTER(GerafBand), vp, i64, vp, vp, vp, szp, vp, vp],
     "geraf_chebyshev_order": [vp, i64, vp, i32, ctypes.POINTER(GerafBand), vp, szp, ctypes.POINTER(i32), vp],
+    "geraf_chebyshev_work": [vp, i64, vp, i32, ctypes.POINTER(GerafBand), i32, vp, szp, ctypes.POINTER(i32),
+                             ctypes.POINTER(ctypes.c_double), vp],
     "geraf_masked_loss": [vp, vp, vp, i64, f32, f32, vp, szp, vp, vp, vp, vp],
     "geraf_proposal_saved_bytes": [ctypes.POINTER(GerafProposal), szp],
     "geraf_proposal_density": [ctypes.POINTER(GerafProposal), vp, vp, vp, sz, vp],

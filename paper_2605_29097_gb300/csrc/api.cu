@@ -33,6 +33,8 @@ geraf_status masked_loss_impl(const float*, const float*, float*, int64_t, float
                               float*, float*, cudaStream_t);
 geraf_status chebyshev_order_impl(const float*, int64_t, const float*, int32_t, const geraf_band*, void*, size_t*,
                                   int32_t*, cudaStream_t);
+geraf_status chebyshev_work_impl(const float*, int64_t, const float*, int32_t, const geraf_band*, int32_t, void*,
+                                 size_t*, int32_t*, double*, cudaStream_t);
 geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
 geraf_status proposal_saved_bytes(const geraf_proposal*, size_t*);
 geraf_status proposal_density_impl(const geraf_proposal*, float*, float*, void*, size_t, cudaStream_t);
@@ -342,6 +344,20 @@ geraf_status geraf_chebyshev_order(const float* xyz, int64_t n, const float* ant
     REQUIRE(band, "chebyshev_order: band must not be NULL");
     if (ws) REQUIRE(xyz && ant_xyz && order, "chebyshev_order: null input or output");
     return chebyshev_order_impl(xyz, n, ant_xyz, n_ant, band, ws, ws_bytes, order, S(stream));
+}
+
+geraf_status geraf_chebyshev_work(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
+                                  const geraf_band* band, int32_t to_points, void* ws, size_t* ws_bytes,
+                                  int32_t* orders, double* mean_orders, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(n >= 1 && n_ant >= 1, "chebyshev_work: need n >= 1 and n_ant >= 1");
+    REQUIRE(n < (1ll << 31), "chebyshev_work: n must be below 2^31");
+    REQUIRE(band, "chebyshev_work: band must not be NULL");
+    REQUIRE(to_points == 0 || to_points == 1, "chebyshev_work: to_points must be 0 or 1");
+    if (ws) REQUIRE(xyz && ant_xyz && orders && mean_orders, "chebyshev_work: null input or output");
+    return chebyshev_work_impl(xyz, n, ant_xyz, n_ant, band, to_points, ws, ws_bytes, orders, mean_orders,
+                               S(stream));
 }
 
 geraf_status geraf_proposal_saved_bytes(const geraf_proposal* p, size_t* bytes) {

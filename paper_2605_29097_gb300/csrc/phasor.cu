@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -76,8 +77,9 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
         r.b = make_float4(gx * k, gy * k, gz * k, t_eff[j]);
         r.c.w = dir ? 1.0f : -1.0f;
     } else {
-        // padding: point 0's position with zero weight (inside every range bound)
-        split3(xyz[0], xyz[n], xyz[2 * n], r.a, r.c);
+        // padding: the last point's position with zero weight (inside the
+        // range bound of the call and of the last split)
+        split3(xyz[n - 1], xyz[2 * n - 1], xyz[3 * n - 1], r.a, r.c);
         r.a.w = 0.0f;
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         r.c.w = -1.0f;
@@ -103,7 +105,7 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
         r.a.w = cr;
         r.b = make_float4(ci, 0.0f, 0.0f, 0.0f);
     } else {
-        split3(vox[0], vox[n], vox[2 * n], r.a, r.c);
+        split3(vox[n - 1], vox[2 * n - 1], vox[3 * n - 1], r.a, r.c);
         r.a.w = 0.0f;
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
@@ -1217,49 +1219,112 @@ size_t cheb_bins_smem(int km) { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)
 // sig = (conj_sig ? conj(v) : v) and s_k = (-1)^floor(k/2), the sign of the
 // point kernels' packed V_k = s_k T_k recurrence
 constexpr int CH_ROW = 2 + CH_KMAX;
-__global__ void cheb_rows_kernel(const float* __restrict__ ant, const float* __restrict__ c_ant,
-                                 const float2* __restrict__ sig, int n_ant, int n_ant_pad, int n_f,
-                                 const ChebPlan* __restrict__ plan, const double2* __restrict__ C, int conj_c,
-                                 int conj_sig, float4* __restrict__ rows) {
+
+// Bounding box of each group of per_group consecutive points (xyz in [3][n]
+// layout): box[g] = (min x, min y, min z, max x, max y, max z).
+__global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int64_t per_group,
+                                  float* __restrict__ box) {
+    __shared__ float red[6][256];
+    const int g = blockIdx.x;
+    const int64_t j0 = (int64_t)g * per_group, j1 = min(n, j0 + per_group);
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float x = xyz[d * n + j];
+            mn[d] = fminf(mn[d], x);
+            mx[d] = fmaxf(mx[d], x);
+        }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        red[d][threadIdx.x] = mn[d];
+        red[3 + d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k)
+            for (int d = 0; d < 3; ++d) {
+                red[d][threadIdx.x] = fminf(red[d][threadIdx.x], red[d][threadIdx.x + k]);
+                red[3 + d][threadIdx.x] = fmaxf(red[3 + d][threadIdx.x], red[3 + d][threadIdx.x + k]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) box[g * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Antenna rows of the to-points kernels, one set per point group g (the
+// group's own interval and coefficient table C_g,k(n) from split_plan_kernel):
+// row(g, i) = two heads (the antenna's split position; c_ant in the first),
+// then for k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) C_g,k(n) (either
+// factor conjugated on request), zero beyond the group's order and for padding
+// antennas. Block = GR_T antennas of one group; thread = one order k and every
+// fourth antenna of the tile; bins staged in shared memory in chunks of GR_NC;
+// FP32 sums.
+constexpr int GR_T = 16;
+constexpr int GR_NC = 64;
+__global__ void __launch_bounds__(256) cheb_group_rows_kernel(
+    const float* __restrict__ ant, const float* __restrict__ c_ant, const float2* __restrict__ sig, int n_ant,
+    int n_ant_pad, int n_f, const ChebPlan* __restrict__ plan, const SplitPlan* __restrict__ gplan,
+    const float2* __restrict__ Cs, int conj_c, int conj_sig, float4* __restrict__ rows) {
     if (!plan->run_cheb) return;
-    const int i = blockIdx.x;
-    if (i >= n_ant_pad) return;
-    float4* row = rows + (size_t)i * CH_ROW;
-    if (threadIdx.x == 0) {
+    __shared__ float2 sC[CH_KMAX][GR_NC + 1];
+    __shared__ float2 sS[GR_T][GR_NC + 1];
+    const int g = blockIdx.y, i0 = blockIdx.x * GR_T, t = threadIdx.x;
+    const int K = gplan[g].K;
+    float4* grow = rows + (size_t)g * n_ant_pad * CH_ROW;
+    if (t < GR_T && i0 + t < n_ant_pad) {
+        const int i = i0 + t;
         const int q = i < n_ant ? i : 0;
         float4 hi, lo;
         split3(ant[q], ant[n_ant + q], ant[2 * n_ant + q], hi, lo);
         hi.w = c_ant ? c_ant[q] : 0.0f;
         lo.w = 0.0f;
-        row[0] = hi;
-        row[1] = lo;
+        grow[(size_t)i * CH_ROW] = hi;
+        grow[(size_t)i * CH_ROW + 1] = lo;
     }
-    // 4 consecutive lanes per order k, each summing every 4th bin (shorter FP64
-    // dependency chains); the lanes' sums are added in a fixed order
-    const int K = plan->K;
-    const int r = threadIdx.x & 3;
-    for (int k = threadIdx.x >> 2; k < CH_KMAX; k += blockDim.x >> 2) {
-        double hr = 0.0, hi = 0.0;
-        if (i < n_ant && k < K) {
-            for (int n = r; n < n_f; n += 4) {
-                const float2 v = sig[(size_t)i * n_f + n];
-                const double vr = v.x, vi = conj_sig ? -(double)v.y : (double)v.y;
-                const double2 c = C[(size_t)k * n_f + n];
-                const double cr = c.x, ci = conj_c ? -c.y : c.y;
-                hr += vr * cr - vi * ci;
-                hi += vr * ci + vi * cr;
+    const int k = t >> 2, r = t & 3;
+    const float2* C = Cs + (size_t)g * CH_KMAX * n_f;
+    float ar[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ai[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int n0 = 0; n0 < n_f; n0 += GR_NC) {
+        const int nc = min(GR_NC, n_f - n0);
+        __syncthreads();
+        for (int e = t; e < CH_KMAX * GR_NC; e += blockDim.x) {
+            const int kk = e / GR_NC, nn = e % GR_NC;
+            float2 c = make_float2(0.0f, 0.0f);
+            if (kk < K && nn < nc) {
+                c = C[(size_t)kk * n_f + n0 + nn];
+                if (conj_c) c.y = -c.y;
             }
+            sC[kk][nn] = c;
         }
-        hr += __shfl_xor_sync(0xffffffffu, hr, 1);
-        hi += __shfl_xor_sync(0xffffffffu, hi, 1);
-        hr += __shfl_xor_sync(0xffffffffu, hr, 2);
-        hi += __shfl_xor_sync(0xffffffffu, hi, 2);
-        if (r == 0) {
-            if ((k >> 1) & 1) {
-                hr = -hr;
-                hi = -hi;
+        for (int e = t; e < GR_T * GR_NC; e += blockDim.x) {
+            const int a = e / GR_NC, nn = e % GR_NC, i = i0 + a;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (i < n_ant && nn < nc) {
+                v = sig[(size_t)i * n_f + n0 + nn];
+                if (conj_sig) v.y = -v.y;
             }
-            row[2 + k] = make_float4((float)hr, (float)hr, (float)hi, (float)hi);
+            sS[a][nn] = v;
+        }
+        __syncthreads();
+        if (k < K)
+            for (int nn = 0; nn < nc; ++nn) {
+                const float2 c = sC[k][nn];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 v = sS[r + 4 * q][nn];
+                    ar[q] = fmaf(v.x, c.x, fmaf(-v.y, c.y, ar[q]));
+                    ai[q] = fmaf(v.x, c.y, fmaf(v.y, c.x, ai[q]));
+                }
+            }
+    }
+    const float sg = ((k >> 1) & 1) ? -1.0f : 1.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = i0 + r + 4 * q;
+        if (i < n_ant_pad) {
+            const float hr = sg * ar[q], hi = sg * ai[q];
+            grow[(size_t)i * CH_ROW + 2 + k] = make_float4(hr, hr, hi, hi);
         }
     }
 }
@@ -1268,11 +1333,15 @@ struct ChebPointsArgs {
     const PtRec* pts;
     const float* vox;
     int64_t n;
-    const float4* rows;
+    const float4* rows;        // [groups][n_ant_pad][CH_ROW]
+    size_t group_rows;         // float4 per group of rows
+    int ctas_per_group;        // point CTAs (blockIdx.x) per group
     int at;                    // antennas per tile
     int n_ant_tiles;
     int tiles_per_split;
     const ChebPlan* plan;
+    const SplitPlan* gplan;    // per group: interval and order
+    const int* kmax;           // largest group order
     float kh, kl;
     float* partial;
     int* err;
@@ -1281,18 +1350,24 @@ struct ChebPointsArgs {
 // thread = 2 points (the two lanes of the packed Chebyshev sums)
 static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread");
 
-// KC = 8-order groups compiled in: the KC = 4 instance (orders 0..31, fully
-// unrolled, no guards) runs when the plan's K <= 32, the KC = 8 instance
-// otherwise; both are launched and the other returns at once.
+// Each group of ctas_per_group point CTAs has its own interval and order
+// (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
+// and KC = 4 instances (orders 0..23 or 0..31, fully unrolled, no guards) run
+// when the largest group order is <= 24 or <= 32, the KC = 8 instance otherwise
+// (orders beyond 32 guarded by the group's own order); all three are launched
+// and the two that do not match return at once.
 // Render adjoint: the per-point factors of the chain rule (the weight w, the
 // constant 1/(16 pi^2) of gamma, and the numeric factors of dD/dn) are taken out
 // of the antenna sums and applied once when the partials are written.
 template <int MODE, int KC>
-__global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? GERAF_CH_FILTER_CTAS : GERAF_CH_RBWD_CTAS) : 1)
+__global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? GERAF_CH_FILTER_CTAS : GERAF_CH_RBWD_CTAS) : 1)
     cheb_points_kernel(const ChebPointsArgs args) {
     constexpr int KM = 8 * KC;
     if (!args.plan->run_cheb) return;
-    if ((KC == 4) != (args.plan->K <= 32)) return;
+    {
+        const int km = *args.kmax;
+        if (KC != (km <= 24 ? 3 : (km <= 32 ? 4 : 8))) return;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int* abort_flag = reinterpret_cast<int*>(smem + 16);
@@ -1305,8 +1380,11 @@ __global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 
     const int tile1 = min(tile0 + args.tiles_per_split, args.n_ant_tiles);
     const int n_my = tile1 - tile0;
     const uint32_t tile_bytes = (uint32_t)(AT * ROW * sizeof(float4));
-    const int K = args.plan->K;
-    const float r_c = args.plan->r_c, inv_dr = args.plan->inv_dr;
+    const int grp = blockIdx.x / args.ctas_per_group;
+    const float4* grows = args.rows + (size_t)grp * args.group_rows;
+    const SplitPlan gp = args.gplan[grp];
+    const int K = gp.K;
+    const float r_c = gp.r_c, inv_dr = gp.inv_dr;
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1317,7 +1395,7 @@ __global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 
     if (t == 0)
         for (int s = 0; s < 2 && s < n_my; ++s) {
             mbar_arrive_expect_tx(&bar[s], tile_bytes);
-            tma_load_1d(rows + s * AT * ROW, args.rows + (size_t)(tile0 + s) * AT * ROW, tile_bytes, &bar[s]);
+            tma_load_1d(rows + s * AT * ROW, grows + (size_t)(tile0 + s) * AT * ROW, tile_bytes, &bar[s]);
         }
     const int64_t jbase = (blockIdx.x * (int64_t)TPK_THREADS + t) * TPK_V;
     float4 ph[TPK_V], pl[TPK_V];                             // split positions
@@ -1453,7 +1531,7 @@ __global__ void __launch_bounds__(TPK_THREADS, KC == 4 ? (MODE == MODE_FILTER ? 
         __syncthreads();
         if (t == 0 && it + 2 < n_my) {
             mbar_arrive_expect_tx(&bar[buf], tile_bytes);
-            tma_load_1d(rows + buf * AT * ROW, args.rows + (size_t)(tile0 + it + 2) * AT * ROW, tile_bytes,
+            tma_load_1d(rows + buf * AT * ROW, grows + (size_t)(tile0 + it + 2) * AT * ROW, tile_bytes,
                         &bar[buf]);
         }
     }
@@ -1515,6 +1593,51 @@ ChebWs take_cheb(WsCarver& c, int64_t n_bbox, int n_f) {
     w.plan = c.take<ChebPlan>(1);
     w.C = c.take<double2>((size_t)CH_KMAX * n_f);
     return w;
+}
+
+// Point groups of the to-points calls: consecutive point CTAs, each group with
+// its own interval, order and antenna rows (at most 64 groups and 256 MiB of
+// rows; at least 8 CTAs = 2048 points per group).
+constexpr size_t CH_GROUP_ROWS_BYTES = 256ull << 20;
+struct PointGroups {
+    int groups, ctas_per_group;
+    float* box;
+    SplitPlan* plan;
+    float2* C;
+    int* kmax;
+    float4* rows;
+    size_t group_rows;
+};
+PointGroups plan_point_groups(int pt_ctas, int n_ant_pad) {
+    PointGroups g{};
+    g.group_rows = (size_t)n_ant_pad * CH_ROW;
+    const size_t cap = std::max<size_t>(1, std::min<size_t>(64, CH_GROUP_ROWS_BYTES / (g.group_rows * sizeof(float4))));
+    g.ctas_per_group = std::max<int>(8, (int)((pt_ctas + cap - 1) / cap));
+    g.groups = (pt_ctas + g.ctas_per_group - 1) / g.ctas_per_group;
+    return g;
+}
+PointGroups take_point_groups(WsCarver& c, int pt_ctas, int n_ant_pad, int n_f) {
+    PointGroups g = plan_point_groups(pt_ctas, n_ant_pad);
+    g.box = c.take<float>((size_t)g.groups * 6);
+    g.plan = c.take<SplitPlan>(g.groups);
+    g.C = c.take<float2>((size_t)g.groups * CH_KMAX * n_f);
+    g.kmax = c.take<int>(1);
+    g.rows = c.take<float4>((size_t)g.groups * g.group_rows);
+    return g;
+}
+// group boxes, group plans and tables, then the groups' antenna rows
+geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const float* xyz, int64_t n,
+                                 const float* ant_xyz, const float* c_ant, int n_ant, int n_ant_pad,
+                                 const geraf_band* band, const float2* sig, int conj_c, int conj_sig,
+                                 cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(g.kmax, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "point groups");
+    group_bbox_kernel<<<g.groups, 256, 0, st>>>(xyz, n, (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V, g.box);
+    split_plan_kernel<<<g.groups, 256, 0, st>>>(g.box, ant_xyz, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
+                                                cw.plan, g.plan, g.C, g.kmax);
+    cheb_group_rows_kernel<<<dim3((n_ant_pad + GR_T - 1) / GR_T, g.groups), 256, 0, st>>>(
+        ant_xyz, c_ant, sig, n_ant, n_ant_pad, band->n_f, cw.plan, g.plan, g.C, conj_c, conj_sig, g.rows);
+    return GERAF_OK;
 }
 
 void launch_cheb_plan(const ChebWs& w, const float* pts, int64_t n, const float* ant, int n_ant,
@@ -1657,10 +1780,10 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     const int fin_blocks = (int)grid1d(n_vox, 256);
     double* loss_blocks = c.take<double>(fin_blocks);
     ChebWs cw{};
-    float4* crows = nullptr;
+    PointGroups pg{};
     if (cheb) {
         cw = take_cheb(c, n_vox, band->n_f);
-        crows = c.take<float4>((size_t)p.n_ant_pad * CH_ROW);
+        pg = take_point_groups(c, p.pt_ctas, p.n_ant_pad, band->n_f);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
@@ -1668,6 +1791,8 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
         cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
         cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1677,13 +1802,15 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, vox, n_vox, ant_xyz, n_ant, band, st);
-        cheb_rows_kernel<<<p.n_ant_pad, 256, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
-                                                    p.n_ant_pad, band->n_f, cw.plan, cw.C, 1, 0, crows);
+        const geraf_status gs = launch_point_groups(pg, cw, vox, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad, band,
+                                                    reinterpret_cast<const float2*>(s), 1, 0, st);
+        if (gs != GERAF_OK) return gs;
         float kh, kl;
         k0_split(band, &kh, &kl);
-        ChebPointsArgs ca{nullptr, vox, n_vox, crows, p.at, p.n_ant_tiles, p.tiles_per_split, cw.plan, kh, kl,
-                          reinterpret_cast<float*>(part), err};
+        ChebPointsArgs ca{nullptr, vox, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
+                          p.tiles_per_split, cw.plan, pg.plan, pg.kmax, kh, kl, reinterpret_cast<float*>(part), err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
+        cheb_points_kernel<MODE_FILTER, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_FILTER, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_FILTER, 8><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         run_direct = &cw.plan->use_direct;
@@ -1714,10 +1841,10 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
     float* part = c.take<float>((size_t)p.splits * 6 * n_pts);
     ChebWs cw{};
-    float4* crows = nullptr;
+    PointGroups pg{};
     if (cheb) {
         cw = take_cheb(c, n_pts, band->n_f);
-        crows = c.take<float4>((size_t)p.n_ant_pad * CH_ROW);
+        pg = take_point_groups(c, p.pt_ctas, p.n_ant_pad, band->n_f);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
@@ -1729,6 +1856,8 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     if (!attr_set) {
         cudaFuncSetAttribute(to_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
+        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
         cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
         cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1738,13 +1867,15 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, xyz, n_pts, ant_xyz, n_ant, band, st);
-        cheb_rows_kernel<<<p.n_ant_pad, 256, 0, st>>>(ant_xyz, c_ant, reinterpret_cast<const float2*>(g_s), n_ant,
-                                                    p.n_ant_pad, band->n_f, cw.plan, cw.C, 0, 1, crows);
+        const geraf_status gs = launch_point_groups(pg, cw, xyz, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad, band,
+                                                    reinterpret_cast<const float2*>(g_s), 0, 1, st);
+        if (gs != GERAF_OK) return gs;
         float kh, kl;
         k0_split(band, &kh, &kl);
-        ChebPointsArgs ca{pts, nullptr, n_pts, crows, p.at, p.n_ant_tiles, p.tiles_per_split, cw.plan, kh, kl, part,
-                          err};
+        ChebPointsArgs ca{pts, nullptr, n_pts, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
+                          p.tiles_per_split, cw.plan, pg.plan, pg.kmax, kh, kl, part, err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
+        cheb_points_kernel<MODE_RENDER_BWD, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_RENDER_BWD, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_RENDER_BWD, 8><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         run_direct = &cw.plan->use_direct;
@@ -1823,6 +1954,75 @@ geraf_status chebyshev_order_impl(const float* xyz, int64_t n, const float* ant_
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e, "chebyshev_order: read back");
     *order = h.use_direct ? 0 : h.K;
+    return GERAF_OK;
+}
+
+// Orders one Chebyshev phasor call evaluates: the same device plans as the
+// call (whole set, then per split of point tiles for the to-bins direction or
+// per point group for the to-points direction), read back; the kernel
+// instance follows the largest part order (24, 32 or 64 orders compiled in;
+// the 64-order instance runs 32 orders plus the part's own beyond them, in
+// blocks of 8). mean_orders = orders per (point, antenna) pair, averaged over
+// the points.
+geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
+                                 const geraf_band* band, int32_t to_points, void* ws, size_t* ws_bytes,
+                                 int32_t* orders, double* mean_orders, cudaStream_t st) {
+    BandK bk;
+    if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
+    int parts = 0;
+    int64_t per_part = 0;
+    if (to_points) {
+        const ToPointsPlan p = plan_to_points(n, n_ant, bk.g);
+        const PointGroups g = plan_point_groups(p.pt_ctas, p.n_ant_pad);
+        parts = g.groups;
+        per_part = (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V;
+    } else {
+        const int64_t n_pad = (n + CH_TP - 1) / CH_TP * CH_TP;
+        const ToBinsPlan p = plan_to_bins(n_pad, n_ant, bk.g);
+        const ChebBinsPlan q = plan_cheb_bins((int64_t)p.n_tiles * p.TP, n_ant);
+        parts = q.splits;
+        per_part = (int64_t)q.tiles_per_split * CH_TP;
+    }
+    WsCarver c(ws);
+    ChebWs cw = take_cheb(c, n, band->n_f);
+    float* box = c.take<float>((size_t)parts * 6);
+    SplitPlan* splan = c.take<SplitPlan>(parts);
+    float2* Cs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
+    int* kmax = c.take<int>(1);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used)
+        return fail(GERAF_ERR_WORKSPACE, "chebyshev_work: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    orders[0] = orders[1] = orders[2] = 0;
+    *mean_orders = 0.0;
+    if (!use_cheb(band)) return GERAF_OK;
+    launch_cheb_plan(cw, xyz, n, ant_xyz, n_ant, band, st);
+    cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "chebyshev_work");
+    group_bbox_kernel<<<parts, 256, 0, st>>>(xyz, n, per_part, box);
+    split_plan_kernel<<<parts, 256, 0, st>>>(box, ant_xyz, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9, cw.plan,
+                                             splan, Cs, kmax);
+    geraf_status s = check_launch("chebyshev_work");
+    if (s != GERAF_OK) return s;
+    ChebPlan h;
+    std::vector<SplitPlan> hs((size_t)parts);
+    int km = 0;
+    e = cudaMemcpyAsync(&h, cw.plan, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), splan, sizeof(SplitPlan) * parts, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&km, kmax, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "chebyshev_work: read back");
+    if (!h.run_cheb) return GERAF_OK;
+    const int inst = km <= 24 ? 24 : (km <= 32 ? 32 : 64);
+    double sum = 0.0;
+    for (int g = 0; g < parts; ++g) {
+        const int64_t j0 = (int64_t)g * per_part, j1 = std::min<int64_t>(n, j0 + per_part);
+        const int ex = inst <= 32 ? inst : std::max(32, (hs[g].K + 7) / 8 * 8);
+        sum += (double)std::max<int64_t>(j1 - j0, 0) * ex;
+    }
+    orders[0] = h.K;
+    orders[1] = km;
+    orders[2] = inst;
+    *mean_orders = sum / (double)n;
     return GERAF_OK;
 }
 

@@ -336,6 +336,27 @@ def geraf_chebyshev_order(xyz, ant, band: Band) -> int:
     return int(order.value)
 
 
+def geraf_chebyshev_work(xyz, ant, band: Band, to_points: bool):
+    """Orders one Chebyshev phasor call evaluates: (K of the whole set, the
+    largest split or group order, the kernel instance's compiled orders, the
+    mean orders evaluated per (point, antenna) pair). to_points: the
+    direction of geraf_filter / geraf_render_backward, else that of
+    geraf_render / geraf_filter_backward. All zero when the recurrence runs.
+    Synchronous."""
+    _req(xyz, "xyz")
+    _req(ant, "ant")
+    cb = band.c()
+    orders = (ctypes.c_int32 * 3)()
+    mean = ctypes.c_double(0.0)
+    L = _lib.lib()
+    args = lambda wsp, b: L.geraf_chebyshev_work(_p(xyz), xyz.shape[-1], _p(ant), ant.shape[-1], ctypes.byref(cb),
+                                                 1 if to_points else 0, wsp, b, orders, ctypes.byref(mean),
+                                                 _stream())
+    ws, wsz = _workspace(args, xyz.device)
+    check(args(_p(ws), ctypes.byref(wsz)))
+    return int(orders[0]), int(orders[1]), int(orders[2]), float(mean.value)
+
+
 class Proposal:
     """Learned proposal: FP16 feature grid [G2, G1, G0, feat] and FP32 MLP params."""
 

@@ -18,11 +18,11 @@ LAUNCHES = {"sample": 1, "fields": 1, "blend": 2, "render": 4, "filter": 4, "fil
             "render_backward": 4, "blend_backward": 2}
 # with the Chebyshev form each phasor call adds the range bound, the plan and
 # the moment kernels (the to-bins calls per-split bounds and plans, three
-# kernel instances and a split-group sum; the to-points calls two; the
-# instances that do not apply return at once); the recurrence kernels are still
-# launched and return at
+# kernel instances and a split-group sum; the to-points calls per-group bounds,
+# plans and antenna rows and three kernel instances; the instances that do not
+# apply return at once); the recurrence kernels are still launched and return at
 # once unless the device-side plan falls back to them
-LAUNCHES_CHEBYSHEV = {"render": 13, "filter": 9, "filter_backward": 13, "render_backward": 9}
+LAUNCHES_CHEBYSHEV = {"render": 13, "filter": 12, "filter_backward": 13, "render_backward": 12}
 
 
 def uses_chebyshev(band) -> bool:

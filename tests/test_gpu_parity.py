@@ -381,3 +381,80 @@ def test_far_array_split_range_bound(G, oracle, dist, cheb):
     G.geraf_poll_device_error()
     oM, _ = oracle.filter_forward(host(sig), ant, vox, b)
     assert rel_l2(host(M), oM) < TOL
+
+
+@pytest.mark.parametrize("wide_first", [True, False])
+def test_chebyshev_groups_mixed_orders(G, oracle, wide_first):
+    """The Chebyshev kernels expand each split of points (to bins) and each
+    group of 2048 points or voxels (to points) over its own range interval with
+    its own order. Consecutive chunks of 2048 points here lie in clusters of
+    very different range spread (about 40 terms for the wide one, ~10 for the
+    compact ones), so the orders differ from group to group and the instance
+    chosen by the largest order (K <= 64 with the wide chunk, K <= 24 without)
+    runs groups of lower order; 3 x 2048 + 517 points leave a ragged last
+    group. Every phasor call against the oracle."""
+    rng = np.random.default_rng(31)
+    chunks = [((0.0, 0.0, 0.30), 0.12 if wide_first else 0.01, 2048), ((0.02, -0.01, 0.12), 0.01, 2048),
+              ((-0.03, 0.02, 0.20), 0.015, 2048), ((0.0, 0.04, 0.16), 0.008, 517)]
+    parts = [_scene_points(rng, n, c, h) for c, h, n in chunks]
+    xyz, grad, w, t_eff = (np.concatenate([p[i] for p in parts], axis=-1) for i in range(4))
+    n_f = 128
+    ant = gi.antenna_array(9, 8, 0.002)
+    c_ant = rng.uniform(0.2, 1.0, ant.shape[1]).astype(np.float32)
+    b = gi.band(77e9, 81e9, n_f)
+    band = _band(G, b, 2)
+    order = G.geraf_chebyshev_order(cu(xyz), cu(ant), band)
+    assert order > (32 if wide_first else 0), order
+    s = G.geraf_render(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), band, True)
+    G.geraf_poll_device_error()
+    want = oracle.render(xyz, grad, w, t_eff, ant, c_ant, b)
+    assert rel_l2(host(s), want) < TOL
+    g = gi.complex_normal(rng, (ant.shape[1], n_f)).astype(np.complex64)
+    d_w, d_t, d_g = G.geraf_render_backward(cu(xyz), cu(grad), cu(w), cu(t_eff), cu(ant), cu(c_ant), band,
+                                            torch.as_tensor(g, device="cuda"))
+    G.geraf_poll_device_error()
+    ow, ot, og = oracle.render_backward(xyz, grad, w, t_eff, ant, c_ant, b, g)
+    assert rel_l2(host(d_w), ow) < TOL and rel_l2(host(d_t), ot) < TOL and rel_l2(host(d_g), og) < 3 * TOL
+    sig = torch.as_tensor(want.astype(np.complex64), device="cuda")
+    P, M, _, _ = G.geraf_filter(sig, cu(ant), band, cu(xyz))
+    G.geraf_poll_device_error()
+    oM, _ = oracle.filter_forward(host(sig), ant, xyz, b)
+    assert rel_l2(host(M), oM) < TOL
+    d_P = rng.standard_normal(xyz.shape[1]).astype(np.float32)
+    gb = G.geraf_filter_backward(cu(ant), band, cu(xyz), M, cu(d_P))
+    G.geraf_poll_device_error()
+    assert rel_l2(host(gb), oracle.filter_backward(host(M), d_P, ant, xyz, b)) < TOL
+
+
+@pytest.mark.parametrize("wide_first", [True, False])
+def test_chebyshev_work_orders(G, wide_first):
+    """geraf_chebyshev_work against the order rule stated on the host: the
+    largest group order (groups of 2048 points, to points) and the largest
+    split order (splits of one 32-point tile here: 72 antennas leave one
+    antenna block, so the plan cuts the points into single tiles), the kernel
+    instance that follows from it and the mean orders per pair."""
+    rng = np.random.default_rng(31)
+    chunks = [((0.0, 0.0, 0.30), 0.12 if wide_first else 0.01, 2048), ((0.02, -0.01, 0.12), 0.01, 2048),
+              ((-0.03, 0.02, 0.20), 0.015, 2048), ((0.0, 0.04, 0.16), 0.008, 517)]
+    xyz = np.concatenate([(np.array(c)[:, None] + rng.uniform(-h, h, (3, n))) for c, h, n in chunks],
+                         axis=1).astype(np.float32)
+    n = xyz.shape[1]
+    ant = gi.antenna_array(9, 8, 0.002)
+    b = gi.band(77e9, 81e9, 128)
+    band = _band(G, b, 2)
+    K = G.geraf_chebyshev_order(cu(xyz), cu(ant), band)
+    inst_of = lambda km: 24 if km <= 24 else (32 if km <= 32 else 64)
+    for to_points, per in ((True, 2048), (False, 32)):
+        k0, km, inst, mean = G.geraf_chebyshev_work(cu(xyz), cu(ant), band, to_points)
+        assert k0 == K
+        host = [_host_order(xyz[:, j:j + per], ant, b) for j in range(0, n, per)]
+        assert abs(km - max(host)) <= 1 and km <= K, (km, max(host), K)
+        assert inst == inst_of(km)
+        counts = [min(n, j + per) - j for j in range(0, n, per)]
+        ex = [inst if inst <= 32 else max(32, (k + 7) // 8 * 8) for k in host]
+        want = sum(c * e for c, e in zip(counts, ex)) / n
+        assert abs(mean - want) < 3.0, (mean, want)
+        if not wide_first:
+            assert inst == 24 and mean == 24.0
+    # the recurrence: all zero
+    assert G.geraf_chebyshev_work(cu(xyz), cu(ant), _band(G, b, 1), True) == (0, 0, 0, 0.0)
