@@ -753,9 +753,10 @@ __device__ void bessel_j(double a, int kcount, double* out) {
     }
     int start = kcount + 20 + (int)a;
     start += start & 1;
+    const double inv_a2 = 2.0 / a;    // the one division: FP64 divides are long on this part
     double jp1 = 0.0, j = 1e-300, norm = 0.0;
     for (int k = start; k >= 1; --k) {
-        const double jm1 = (2.0 * k / a) * j - jp1;
+        const double jm1 = ((double)k * inv_a2) * j - jp1;
         jp1 = j;
         j = jm1;                      // j = J_{k-1}
         if (k - 1 < kcount) out[k - 1] = j;
@@ -768,7 +769,8 @@ __device__ void bessel_j(double a, int kcount, double* out) {
         }
     }
     norm += j;                        // J_0
-    for (int k = 0; k < kcount; ++k) out[k] /= norm;
+    const double inv_norm = 1.0 / norm;
+    for (int k = 0; k < kcount; ++k) out[k] *= inv_norm;
 }
 
 // one block: points bbox + antennas -> range bound, order K, coefficients C[k][n]
@@ -880,8 +882,9 @@ struct ChebBinsArgs {
     int n_tiles;
     int tiles_per_split;
     const ChebPlan* plan;      // the whole call's plan (run_cheb)
-    const SplitPlan* splan;    // [splits]
-    const int* kmax;           // largest split order: picks the kernel instance
+    const SplitPlan* splan;    // [splits][plan_blocks]
+    int plan_blocks;           // antenna blocks with their own plan: 1 or gridDim.x
+    const int* kmax;           // largest part order: picks the kernel instance
     float kh, kl;              // K0 = 2 f0 / c as double-single (cycles per metre)
     float2* partial;           // [splits][n_ant][CH_KMAX]
     int* err;
@@ -892,12 +895,73 @@ struct ChebBinsArgs {
 // The core is 3 scalar FMAs per order (T_k recurrence, real and imaginary
 // accumulation): the FMA pipe, not the issue rate, bounds this kernel, and a
 // packed (re, im) form would spend a wasted lane on the recurrence.
-// KC = 8-order groups held in registers: the KC = 3 and KC = 4 instances
-// (orders 0..23 or 0..31, no per-group guards) run when the largest split
-// order is at most 24 or 32, the KC = 8 instance (orders beyond 32 guarded by
-// the split's K) otherwise; all are launched and those that do not apply
-// return at once. Each split expands the bin phase over its own range
-// interval (SplitPlan).
+// KC = 8-order groups held in registers: the KC = 3 and KC = 4 instances run
+// when the largest part order is at most 24 or 32, each CTA with its part's
+// order rounded up to even (at least 16) as a compile-time loop bound (one
+// unrolled tile body per even order); the KC = 8 instance (orders beyond 32
+// guarded by the part's K) otherwise; all are launched and those that do not
+// apply return at once. Each part = (split of points, block of CH_THREADS
+// antennas) expands the bin phase over its own range interval (SplitPlan).
+// One tile of CH_TP point records against this thread's antenna: the pair's
+// range, amplitude times carrier phasor, and the moments M_k += A T_k(x) for
+// k < KE (KE even, fixed at compile time). kGuard (the 64-order instance):
+// orders past 32 run in blocks of 8 up to the part's own order K.
+template <bool kComplexAmp, int KM, int KE, bool kGuard>
+__device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const float4& Ah, const float4& Al,
+                                          float aw, float r_c, float inv_dr, float kh, float kl, int K,
+                                          float (&mr)[KM], float (&mi)[KM]) {
+    for (int p = 0; p < CH_TP; ++p) {
+        const PtRec P = tile[p];
+        const Range R = pair_range_split(P.a.x, P.a.y, P.a.z, P.c.x, P.c.y, P.c.z, Ah.x, Ah.y, Ah.z, Al.x, Al.y,
+                                         Al.z);
+        float ar_, ai_;
+        {
+            const float fr = phase_frac(R.rh, R.rl, kh, kl);
+            float sn, cs;
+            __sincosf(6.28318530717958648f * fr, &sn, &cs);
+            if (!kComplexAmp) {
+                const float inv_r2 = R.rs * R.rs;
+                const float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
+                const float D = fmaxf(nd * nd * inv_r2 - P.c.w, 0.0f);
+                const float tt = __saturatef(P.b.w - aw);
+                const float amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
+                ar_ = amp * cs;                          // A exp(-j 2 pi K0 r)
+                ai_ = -amp * sn;
+            } else {
+                const float cr = P.a.w, ci = P.b.x;
+                ar_ = cr * cs + ci * sn;
+                ai_ = ci * cs - cr * sn;
+            }
+        }
+        const float x = __fmul_rn(__fadd_rn(__fsub_rn(R.rh, r_c), R.rl), inv_dr);
+        const float x2 = 2.0f * x;
+        float tkm1 = 1.0f, tk = x;                       // T_0, T_1
+        mr[0] += ar_;
+        mi[0] += ai_;
+        mr[1] = fmaf(ar_, x, mr[1]);
+        mi[1] = fmaf(ai_, x, mi[1]);
+#pragma unroll
+        for (int kc = 0; kc < KE; kc += 8) {
+            if (!kGuard || kc < 32 || kc < K) {
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int k = kc + kk;
+                    if (k >= 2 && k < KE) {
+                        const float tn = fmaf(x2, tk, -tkm1);
+                        tkm1 = tk;
+                        tk = tn;
+                        mr[k] = fmaf(ar_, tn, mr[k]);
+                        mi[k] = fmaf(ai_, tn, mi[k]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+#define GERAF_BINS_CASE(E) \
+    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K, mr, mi); break;
+
 template <bool kComplexAmp, int KC>
 __global__ void __launch_bounds__(CH_THREADS, KC <= 4 ? GERAF_CH_BINS_CTAS : 1) cheb_bins_kernel(const ChebBinsArgs args) {
     constexpr int KM = 8 * KC;
@@ -919,8 +983,9 @@ __global__ void __launch_bounds__(CH_THREADS, KC <= 4 ? GERAF_CH_BINS_CTAS : 1) 
     const int tile0 = split * args.tiles_per_split;
     const int tile1 = min(tile0 + args.tiles_per_split, args.n_tiles);
     const int n_my = tile1 - tile0;
-    const SplitPlan sp = args.splan[split];
+    const SplitPlan sp = args.splan[split * args.plan_blocks + (args.plan_blocks > 1 ? blockIdx.x : 0)];
     const int K = sp.K;
+    const int ke = K <= 16 ? 16 : (K + 1) & ~1;              // orders run: K rounded up to even, >= 16
     const float r_c = sp.r_c, inv_dr = sp.inv_dr;
     const float4 A4 = args.ant[ia];                          // padded: always readable
     float4 Ah, Al;
@@ -955,51 +1020,14 @@ __global__ void __launch_bounds__(CH_THREADS, KC <= 4 ? GERAF_CH_BINS_CTAS : 1) 
             return;
         }
         const PtRec* tile = tiles + buf * CH_TP;
-        for (int p = 0; p < CH_TP; ++p) {
-            const PtRec P = tile[p];
-            const Range R = pair_range_split(P.a.x, P.a.y, P.a.z, P.c.x, P.c.y, P.c.z, Ah.x, Ah.y, Ah.z, Al.x,
-                                             Al.y, Al.z);
-            float ar_, ai_;
-            {
-                const float fr = phase_frac(R.rh, R.rl, args.kh, args.kl);
-                float sn, cs;
-                __sincosf(6.28318530717958648f * fr, &sn, &cs);
-                if (!kComplexAmp) {
-                    const float inv_r2 = R.rs * R.rs;
-                    const float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
-                    const float D = fmaxf(nd * nd * inv_r2 - P.c.w, 0.0f);
-                    const float tt = __saturatef(P.b.w - A4.w);
-                    const float amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
-                    ar_ = amp * cs;                          // A exp(-j 2 pi K0 r)
-                    ai_ = -amp * sn;
-                } else {
-                    const float cr = P.a.w, ci = P.b.x;
-                    ar_ = cr * cs + ci * sn;
-                    ai_ = ci * cs - cr * sn;
-                }
-            }
-            const float x = __fmul_rn(__fadd_rn(__fsub_rn(R.rh, r_c), R.rl), inv_dr);
-            const float x2 = 2.0f * x;
-            float tkm1 = 1.0f, tk = x;                       // T_0, T_1
-            mr[0] += ar_;
-            mi[0] += ai_;
-            mr[1] = fmaf(ar_, x, mr[1]);
-            mi[1] = fmaf(ai_, x, mi[1]);
-#pragma unroll
-            for (int kc = 0; kc < KM; kc += 8) {
-                if (kc < KU || kc < K) {
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const int k = kc + kk;
-                        if (k >= 2) {
-                            const float tn = fmaf(x2, tk, -tkm1);
-                            tkm1 = tk;
-                            tk = tn;
-                            mr[k] = fmaf(ar_, tn, mr[k]);
-                            mi[k] = fmaf(ai_, tn, mi[k]);
-                        }
-                    }
-                }
+        if constexpr (KC == 8) {
+            bins_tile<kComplexAmp, KM, KM, true>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K, mr, mi);
+        } else {
+            switch (ke) {
+                GERAF_BINS_CASE(16) GERAF_BINS_CASE(18) GERAF_BINS_CASE(20) GERAF_BINS_CASE(22)
+                GERAF_BINS_CASE(24) GERAF_BINS_CASE(26) GERAF_BINS_CASE(28) GERAF_BINS_CASE(30)
+                default: bins_tile<kComplexAmp, KM, KM, false>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K,
+                                                               mr, mi);
             }
         }
         if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
@@ -1062,21 +1090,27 @@ __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, in
     if (threadIdx.x < 6) box[sp * 6 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// One block per split: the split's range interval against all antennas, its
-// order K (the whole call's rule: Bessel tail <= eps), and its FP32
-// coefficient table Cs[sp][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
-// (Bessel values in FP64). kmax collects the largest split order.
+// One block per part = (split of points sp, block of antennas b), parts in
+// order sp * n_ab + b (n_ab blocks of ant_per_block consecutive antennas; one
+// block of all antennas for the point groups): the part's range interval
+// between the split's box and the block's antennas, its order K (the whole
+// call's rule: Bessel tail <= eps), and its FP32 coefficient table
+// Cs[part][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n) (Bessel values in
+// FP64). kmax collects the largest part order.
 __global__ void split_plan_kernel(const float* __restrict__ box, const float* __restrict__ ant, int n_ant,
-                                  double Kd, int n_f, double eps, const ChebPlan* __restrict__ gplan,
-                                  SplitPlan* __restrict__ splan, float2* __restrict__ Cs, int* __restrict__ kmax) {
+                                  int n_ab, int ant_per_block, double Kd, int n_f, double eps,
+                                  const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
+                                  float2* __restrict__ Cs, int* __restrict__ kmax) {
     if (!gplan->run_cheb) return;
     __shared__ float rr[2][256];
     __shared__ int sK;
     __shared__ float s_rc, s_inv;
     const int sp = blockIdx.x, t = threadIdx.x;
-    const float* bx = box + sp * 6;
+    const int b = sp % n_ab;
+    const float* bx = box + (sp / n_ab) * 6;
+    const int i0 = b * ant_per_block, i1 = min(n_ant, i0 + ant_per_block);
     float lo = INFINITY, hi = 0.0f;
-    for (int i = t; i < n_ant; i += blockDim.x) {
+    for (int i = i0 + t; i < i1; i += blockDim.x) {
         float dn = 0.0f, df = 0.0f;
         for (int d = 0; d < 3; ++d) {
             const float a = ant[d * n_ant + i];
@@ -1145,27 +1179,31 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float* __
     }
 }
 
-// sum over the splits of a group of RS splits of sum_k Cs[sp][k][n] M_k(sp, i):
+// sum over the splits of a group of RS splits of sum_k Cs[sp, b(i)][k][n] M_k(sp, i),
+// b(i) the antenna's block of CH_THREADS:
 // block = (RA antennas, split group); thread = bin, the RA antennas in
 // registers so each table value is loaded once; the per-split sums (FP32, at
 // most 64 terms) are added with Kahan compensation across the group's splits.
 // The groups' sums are added in FP64, in group order, by sum_split_groups.
 constexpr int RA = 4;
 constexpr int RS = 32;
+static_assert(CH_THREADS % RA == 0, "a reconstruction block stays in one antenna block");
 __global__ void cheb_reconstruct_split_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
-                                              const ChebPlan* __restrict__ gplan,
+                                              int n_ab, const ChebPlan* __restrict__ gplan,
                                               const SplitPlan* __restrict__ splan, const float2* __restrict__ Cs,
                                               float2* __restrict__ group_out) {
     if (!gplan->run_cheb) return;
     const int i0 = blockIdx.x * RA;
+    const int b = n_ab > 1 ? i0 / CH_THREADS : 0;   // antenna block of all RA antennas (RA divides CH_THREADS)
     const int s0 = blockIdx.y * RS, s1 = min(splits, s0 + RS);
     for (int n = threadIdx.x; n < n_f; n += blockDim.x) {
         float hr[RA], hi[RA], cr_[RA], ci_[RA];
 #pragma unroll
         for (int q = 0; q < RA; ++q) hr[q] = hi[q] = cr_[q] = ci_[q] = 0.0f;
         for (int s = s0; s < s1; ++s) {
-            const int K = splan[s].K;
-            const float2* C = Cs + (size_t)s * CH_KMAX * n_f + n;
+            const int part = s * n_ab + b;
+            const int K = splan[part].K;
+            const float2* C = Cs + (size_t)part * CH_KMAX * n_f + n;
             float sr[RA], si[RA];
 #pragma unroll
             for (int q = 0; q < RA; ++q) sr[q] = si[q] = 0.0f;
@@ -1350,12 +1388,109 @@ struct ChebPointsArgs {
 // thread = 2 points (the two lanes of the packed Chebyshev sums)
 static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread");
 
+// One tile of AT antenna rows against this thread's two points: the pair
+// ranges, sum_k h_k T_k(x) for k < KE (KE even, fixed at compile time; rows
+// are zero beyond the group's order), the carrier phasor, and the filter or
+// render-adjoint accumulation into in. kGuard (the 64-order instance): orders
+// past 32 run in blocks of 8 up to the group's own order K.
+template <int MODE, int KE, bool kGuard>
+__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, float r_c, float inv_dr,
+                                            float kh, float kl, const float4 (&ph)[TPK_V], const float4 (&pl)[TPK_V],
+                                            const float (&pnx)[TPK_V], const float (&pny)[TPK_V],
+                                            const float (&pnz)[TPK_V], const float (&pte)[TPK_V],
+                                            const float (&pe)[TPK_V],
+                                            float (&in)[TPK_V][MODE == MODE_FILTER ? 2 : 5]) {
+    constexpr int ROW = CH_ROW;
+    for (int a = 0; a < AT; ++a) {
+        const float4 head = tile[a * ROW], head_lo = tile[a * ROW + 1];
+        const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 2);
+        Range R[TPK_V];
+        float xs[TPK_V];
+#pragma unroll
+        for (int v = 0; v < TPK_V; ++v) {
+            R[v] = pair_range_split(ph[v].x, ph[v].y, ph[v].z, pl[v].x, pl[v].y, pl[v].z, head.x, head.y,
+                                    head.z, head_lo.x, head_lo.y, head_lo.z);
+            xs[v] = __fmul_rn(__fadd_rn(__fsub_rn(R[v].rh, r_c), R[v].rl), inv_dr);
+        }
+        // sum_k h_k T_k(x) = sum_k (s_k h_k) V_k(x): V_k = s_k T_k for both
+        // points in the two lanes of one packed FMA (V_k = (+/-2x) V_{k-1}
+        // + V_{k-2}, minus for even k), the products accumulated for both
+        // points at once; the rows carry s_k h_k and are zero beyond K,
+        // so the loop may run to the next even order
+        const ulonglong2 h0u = hk[0], h1u = hk[1];
+        const f2 mp = pk2(2.0f * xs[0], 2.0f * xs[1]), mn = pk2(-2.0f * xs[0], -2.0f * xs[1]);
+        f2 v0 = pk2(1.0f, 1.0f), v1 = pk2(xs[0], xs[1]);
+        f2 Sr = h0u.x, Si = h0u.y;                       // V_0 = 1
+        Sr = fma2(v1, h1u.x, Sr);
+        Si = fma2(v1, h1u.y, Si);
+#pragma unroll
+        for (int kc = 0; kc < KE; kc += 8) {
+            if (!kGuard || kc < 32 || kc < K) {
+#pragma unroll
+                for (int k = (kc == 0 ? 2 : kc); k < kc + 8 && k < KE; k += 2) {
+                    const f2 ve = fma2(mn, v1, v0);
+                    const ulonglong2 he = hk[k];
+                    Sr = fma2(ve, he.x, Sr);
+                    Si = fma2(ve, he.y, Si);
+                    const f2 vo = fma2(mp, ve, v1);
+                    const ulonglong2 ho = hk[k + 1];
+                    Sr = fma2(vo, ho.x, Sr);
+                    Si = fma2(vo, ho.y, Si);
+                    v0 = ve;
+                    v1 = vo;
+                }
+            }
+        }
+        float sr[TPK_V], si[TPK_V];
+        upk2(Sr, sr[0], sr[1]);
+        upk2(Si, si[0], si[1]);
+#pragma unroll
+        for (int v = 0; v < TPK_V; ++v) {
+            const float fr = phase_frac(R[v].rh, R[v].rl, kh, kl);
+            float sn, cs;
+            __sincosf(6.28318530717958648f * fr, &sn, &cs);
+            if (MODE == MODE_FILTER) {
+                // exp(+j 2 pi K0 r) * sum
+                in[v][0] += cs * sr[v] - sn * si[v];
+                in[v][1] += cs * si[v] + sn * sr[v];
+            } else {
+                // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k); with A = w T'^2 gamma D,
+                // gamma = k16 / r^2 and n' = sqrt2 n: the sums below times the
+                // per-point factors (k16, 2 w k16, 2 sqrt2 w k16, sqrt2 w k16) are
+                // dA/dw, dA/dT', and the parts of dA/dn' along d and along n'
+                const float q = cs * sr[v] + sn * si[v];
+                const float inv_r2 = R[v].rs * R[v].rs;
+                const float g = q * inv_r2;
+                const float nd = pnx[v] * R[v].dx + pny[v] * R[v].dy + pnz[v] * R[v].dz;
+                const float Dm = nd * nd * inv_r2 - pe[v];
+                const float D = fmaxf(Dm, 0.0f);
+                const float vv = pte[v] - head.w;
+                const float tt = __saturatef(vv);
+                const float dg = D * g;
+                const float u = tt * tt * g;
+                in[v][0] = fmaf(tt * tt, dg, in[v][0]);
+                if (vv >= 0.0f && vv <= 1.0f) in[v][1] = fmaf(tt, dg, in[v][1]);
+                if (pe[v] > 0.0f && Dm > 0.0f) {
+                    const float w2 = u * nd * inv_r2;
+                    in[v][2] = fmaf(w2, R[v].dx, in[v][2]);
+                    in[v][3] = fmaf(w2, R[v].dy, in[v][3]);
+                    in[v][4] = fmaf(w2, R[v].dz, in[v][4]);
+                }
+            }
+        }
+    }
+}
+
+#define GERAF_POINTS_CASE(E) \
+    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny, pnz, pte, pe, in); break;
+
 // Each group of ctas_per_group point CTAs has its own interval and order
 // (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
-// and KC = 4 instances (orders 0..23 or 0..31, fully unrolled, no guards) run
-// when the largest group order is <= 24 or <= 32, the KC = 8 instance otherwise
-// (orders beyond 32 guarded by the group's own order); all three are launched
-// and the two that do not match return at once.
+// and KC = 4 instances run when the largest group order is <= 24 or <= 32, each
+// CTA with its group's order rounded up to even (at least 16) as a compile-time
+// loop bound (one unrolled tile body per even order); the KC = 8 instance runs
+// otherwise (orders beyond 32 guarded by the group's own order); all three are
+// launched and the two that do not match return at once.
 // Render adjoint: the per-point factors of the chain rule (the weight w, the
 // constant 1/(16 pi^2) of gamma, and the numeric factors of dD/dn) are taken out
 // of the antenna sums and applied once when the partials are written.
@@ -1384,6 +1519,7 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
     const float4* grows = args.rows + (size_t)grp * args.group_rows;
     const SplitPlan gp = args.gplan[grp];
     const int K = gp.K;
+    const int ke = K <= 16 ? 16 : (K + 1) & ~1;              // orders run: K rounded up to even, >= 16
     const float r_c = gp.r_c, inv_dr = gp.inv_dr;
     if (t == 0) {
         mbar_init(&bar[0], 1);
@@ -1441,82 +1577,14 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
         for (int v = 0; v < TPK_V; ++v)
 #pragma unroll
             for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
-        for (int a = 0; a < AT; ++a) {
-            const float4 head = tile[a * ROW], head_lo = tile[a * ROW + 1];
-            const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 2);
-            Range R[TPK_V];
-            float xs[TPK_V];
-#pragma unroll
-            for (int v = 0; v < TPK_V; ++v) {
-                R[v] = pair_range_split(ph[v].x, ph[v].y, ph[v].z, pl[v].x, pl[v].y, pl[v].z, head.x, head.y,
-                                        head.z, head_lo.x, head_lo.y, head_lo.z);
-                xs[v] = __fmul_rn(__fadd_rn(__fsub_rn(R[v].rh, r_c), R[v].rl), inv_dr);
-            }
-            // sum_k h_k T_k(x) = sum_k (s_k h_k) V_k(x): V_k = s_k T_k for both
-            // points in the two lanes of one packed FMA (V_k = (+/-2x) V_{k-1}
-            // + V_{k-2}, minus for even k), the products accumulated for both
-            // points at once; the rows carry s_k h_k and are zero beyond K,
-            // so the loop may run to the next even order
-            const ulonglong2 h0u = hk[0], h1u = hk[1];
-            const f2 mp = pk2(2.0f * xs[0], 2.0f * xs[1]), mn = pk2(-2.0f * xs[0], -2.0f * xs[1]);
-            f2 v0 = pk2(1.0f, 1.0f), v1 = pk2(xs[0], xs[1]);
-            f2 Sr = h0u.x, Si = h0u.y;                       // V_0 = 1
-            Sr = fma2(v1, h1u.x, Sr);
-            Si = fma2(v1, h1u.y, Si);
-#pragma unroll
-            for (int kc = 0; kc < KM; kc += 8) {
-                if (kc < 32 || kc < K) {
-#pragma unroll
-                    for (int k = (kc == 0 ? 2 : kc); k < kc + 8; k += 2) {
-                        const f2 ve = fma2(mn, v1, v0);
-                        const ulonglong2 he = hk[k];
-                        Sr = fma2(ve, he.x, Sr);
-                        Si = fma2(ve, he.y, Si);
-                        const f2 vo = fma2(mp, ve, v1);
-                        const ulonglong2 ho = hk[k + 1];
-                        Sr = fma2(vo, ho.x, Sr);
-                        Si = fma2(vo, ho.y, Si);
-                        v0 = ve;
-                        v1 = vo;
-                    }
-                }
-            }
-            float sr[TPK_V], si[TPK_V];
-            upk2(Sr, sr[0], sr[1]);
-            upk2(Si, si[0], si[1]);
-#pragma unroll
-            for (int v = 0; v < TPK_V; ++v) {
-                const float fr = phase_frac(R[v].rh, R[v].rl, args.kh, args.kl);
-                float sn, cs;
-                __sincosf(6.28318530717958648f * fr, &sn, &cs);
-                if (MODE == MODE_FILTER) {
-                    // exp(+j 2 pi K0 r) * sum
-                    in[v][0] += cs * sr[v] - sn * si[v];
-                    in[v][1] += cs * si[v] + sn * sr[v];
-                } else {
-                    // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k); with A = w T'^2 gamma D,
-                    // gamma = k16 / r^2 and n' = sqrt2 n: the sums below times the
-                    // per-point factors (k16, 2 w k16, 2 sqrt2 w k16, sqrt2 w k16) are
-                    // dA/dw, dA/dT', and the parts of dA/dn' along d and along n'
-                    const float q = cs * sr[v] + sn * si[v];
-                    const float inv_r2 = R[v].rs * R[v].rs;
-                    const float g = q * inv_r2;
-                    const float nd = pnx[v] * R[v].dx + pny[v] * R[v].dy + pnz[v] * R[v].dz;
-                    const float Dm = nd * nd * inv_r2 - pe[v];
-                    const float D = fmaxf(Dm, 0.0f);
-                    const float vv = pte[v] - head.w;
-                    const float tt = __saturatef(vv);
-                    const float dg = D * g;
-                    const float u = tt * tt * g;
-                    in[v][0] = fmaf(tt * tt, dg, in[v][0]);
-                    if (vv >= 0.0f && vv <= 1.0f) in[v][1] = fmaf(tt, dg, in[v][1]);
-                    if (pe[v] > 0.0f && Dm > 0.0f) {
-                        const float w2 = u * nd * inv_r2;
-                        in[v][2] = fmaf(w2, R[v].dx, in[v][2]);
-                        in[v][3] = fmaf(w2, R[v].dy, in[v][3]);
-                        in[v][4] = fmaf(w2, R[v].dz, in[v][4]);
-                    }
-                }
+        if constexpr (KC == 8) {
+            points_tile<MODE, KM, true>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny, pnz, pte, pe, in);
+        } else {
+            switch (ke) {
+                GERAF_POINTS_CASE(16) GERAF_POINTS_CASE(18) GERAF_POINTS_CASE(20) GERAF_POINTS_CASE(22)
+                GERAF_POINTS_CASE(24) GERAF_POINTS_CASE(26) GERAF_POINTS_CASE(28) GERAF_POINTS_CASE(30)
+                default: points_tile<MODE, KM, false>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny,
+                                                      pnz, pte, pe, in);
             }
         }
 #pragma unroll
@@ -1633,7 +1701,7 @@ geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const f
     cudaError_t e = cudaMemsetAsync(g.kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "point groups");
     group_bbox_kernel<<<g.groups, 256, 0, st>>>(xyz, n, (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V, g.box);
-    split_plan_kernel<<<g.groups, 256, 0, st>>>(g.box, ant_xyz, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
+    split_plan_kernel<<<g.groups, 256, 0, st>>>(g.box, ant_xyz, n_ant, 1, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
                                                 cw.plan, g.plan, g.C, g.kmax);
     cheb_group_rows_kernel<<<dim3((n_ant_pad + GR_T - 1) / GR_T, g.groups), 256, 0, st>>>(
         ant_xyz, c_ant, sig, n_ant, n_ant_pad, band->n_f, cw.plan, g.plan, g.C, conj_c, conj_sig, g.rows);
@@ -1649,18 +1717,26 @@ void launch_cheb_plan(const ChebWs& w, const float* pts, int64_t n, const float*
 
 struct ChebBinsPlan {
     int ant_blocks, n_tiles, splits, tiles_per_split;
+    int plan_blocks;     // antenna blocks with their own plan per split (1: one plan per split)
 };
 
-ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant) {
+ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant, int n_f) {
     ChebBinsPlan q;
     q.ant_blocks = (n_ant + CH_THREADS - 1) / CH_THREADS;
     q.n_tiles = (int)(n_pad / CH_TP);
     const int64_t max_splits = std::max<int64_t>(1, (int64_t)(CH_PARTIAL_BYTES / ((size_t)n_ant * CH_KMAX * 8)));
     const int64_t want = std::max<int64_t>(1, (4LL * 4 * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
-    // at most 512 splits: each carries its own coefficient table
-    int64_t sp = std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles), 512);
+    // at most 512 splits; each part (a split, or a split and an antenna block)
+    // carries its own coefficient table
+    const int64_t sp = std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles), 512);
     q.tiles_per_split = (int)((q.n_tiles + sp - 1) / sp);
     q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
+    // a plan per (split, antenna block) pays when a part holds enough pairs to
+    // outweigh its FP64 plan (Bessel values of every bin): splits of at least
+    // 8192 points, and at most 256 MiB of tables; otherwise one plan per split
+    const int64_t max_parts = std::max<int64_t>(1, (int64_t)((256ull << 20) / ((size_t)CH_KMAX * n_f * 8)));
+    const bool blocks = (int64_t)q.tiles_per_split * CH_TP >= 8192 && (int64_t)q.splits * q.ant_blocks <= max_parts;
+    q.plan_blocks = blocks ? q.ant_blocks : 1;
     return q;
 }
 
@@ -1679,7 +1755,8 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     const int64_t n_rec = (int64_t)p.n_tiles * p.TP;
     const int n_ant_rec = std::max(p.n_ant_pad, (n_ant + CH_THREADS - 1) / CH_THREADS * CH_THREADS);
     ChebBinsPlan q{};
-    if (cheb) q = plan_cheb_bins(n_rec, n_ant);
+    if (cheb) q = plan_cheb_bins(n_rec, n_ant, band->n_f);
+    const int parts = q.splits * q.plan_blocks;
     WsCarver c(ws);
     PtRec* pts = c.take<PtRec>((size_t)n_rec);
     float4* ant = c.take<float4>(n_ant_rec);
@@ -1695,8 +1772,8 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         cw = take_cheb(c, n_pts, band->n_f);
         cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
         sbox = c.take<float>((size_t)q.splits * 6);
-        splan = c.take<SplitPlan>(q.splits);
-        scs = c.take<float2>((size_t)q.splits * CH_KMAX * band->n_f);
+        splan = c.take<SplitPlan>(parts);
+        scs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
         kmax = c.take<int>(1);
         gout = c.take<float2>((size_t)((q.splits + RS - 1) / RS) * n_ant * band->n_f);
     }
@@ -1727,18 +1804,20 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_status(e, name);
         split_bbox_kernel<<<q.splits, 256, 0, st>>>(pts, q.n_tiles, q.tiles_per_split, sbox);
-        split_plan_kernel<<<q.splits, 256, 0, st>>>(sbox, ant_xyz, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
-                                                    cw.plan, splan, scs, kmax);
+        split_plan_kernel<<<parts, 256, 0, st>>>(sbox, ant_xyz, n_ant, q.plan_blocks,
+                                                 q.plan_blocks > 1 ? CH_THREADS : n_ant, 2.0 * band->df / kC,
+                                                 band->n_f, 1e-9, cw.plan, splan, scs, kmax);
         float kh, kl;
         k0_split(band, &kh, &kl);
-        ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, splan, kmax, kh, kl, cpart, err};
+        ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, splan, q.plan_blocks, kmax, kh, kl,
+                        cpart, err};
         const dim3 grid(q.ant_blocks, q.splits);
         cheb_bins_kernel<kComplexAmp, 3><<<grid, CH_THREADS, cheb_bins_smem(24), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 4><<<grid, CH_THREADS, cheb_bins_smem(32), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 8><<<grid, CH_THREADS, cheb_bins_smem(64), st>>>(ca);
         const int groups = (q.splits + RS - 1) / RS;
         cheb_reconstruct_split_kernel<<<dim3((n_ant + RA - 1) / RA, groups), 128, 0, st>>>(
-            cpart, q.splits, n_ant, band->n_f, cw.plan, splan, scs, gout);
+            cpart, q.splits, n_ant, band->n_f, q.plan_blocks, cw.plan, splan, scs, gout);
         sum_split_groups<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(
             gout, groups, (int64_t)n_ant * band->n_f, cw.plan, reinterpret_cast<float2*>(out));
         run_direct = &cw.plan->use_direct;
@@ -1969,7 +2048,7 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
                                  int32_t* orders, double* mean_orders, cudaStream_t st) {
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    int parts = 0;
+    int parts = 0, n_ab = 1, ant_per_block = n_ant;
     int64_t per_part = 0;
     if (to_points) {
         const ToPointsPlan p = plan_to_points(n, n_ant, bk.g);
@@ -1979,13 +2058,16 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     } else {
         const int64_t n_pad = (n + CH_TP - 1) / CH_TP * CH_TP;
         const ToBinsPlan p = plan_to_bins(n_pad, n_ant, bk.g);
-        const ChebBinsPlan q = plan_cheb_bins((int64_t)p.n_tiles * p.TP, n_ant);
-        parts = q.splits;
+        const ChebBinsPlan q = plan_cheb_bins((int64_t)p.n_tiles * p.TP, n_ant, band->n_f);
+        n_ab = q.plan_blocks;
+        ant_per_block = n_ab > 1 ? CH_THREADS : n_ant;
+        parts = q.splits * n_ab;
         per_part = (int64_t)q.tiles_per_split * CH_TP;
     }
+    const int n_splits = parts / n_ab;
     WsCarver c(ws);
     ChebWs cw = take_cheb(c, n, band->n_f);
-    float* box = c.take<float>((size_t)parts * 6);
+    float* box = c.take<float>((size_t)n_splits * 6);
     SplitPlan* splan = c.take<SplitPlan>(parts);
     float2* Cs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
     int* kmax = c.take<int>(1);
@@ -1998,9 +2080,9 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     launch_cheb_plan(cw, xyz, n, ant_xyz, n_ant, band, st);
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "chebyshev_work");
-    group_bbox_kernel<<<parts, 256, 0, st>>>(xyz, n, per_part, box);
-    split_plan_kernel<<<parts, 256, 0, st>>>(box, ant_xyz, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9, cw.plan,
-                                             splan, Cs, kmax);
+    group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz, n, per_part, box);
+    split_plan_kernel<<<parts, 256, 0, st>>>(box, ant_xyz, n_ant, n_ab, ant_per_block, 2.0 * band->df / kC,
+                                             band->n_f, 1e-9, cw.plan, splan, Cs, kmax);
     geraf_status s = check_launch("chebyshev_work");
     if (s != GERAF_OK) return s;
     ChebPlan h;
@@ -2015,14 +2097,17 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     const int inst = km <= 24 ? 24 : (km <= 32 ? 32 : 64);
     double sum = 0.0;
     for (int g = 0; g < parts; ++g) {
-        const int64_t j0 = (int64_t)g * per_part, j1 = std::min<int64_t>(n, j0 + per_part);
-        const int ex = inst <= 32 ? inst : std::max(32, (hs[g].K + 7) / 8 * 8);
-        sum += (double)std::max<int64_t>(j1 - j0, 0) * ex;
+        const int sp = g / n_ab, b = g % n_ab;
+        const int64_t j0 = (int64_t)sp * per_part, j1 = std::min<int64_t>(n, j0 + per_part);
+        const int64_t a0 = (int64_t)b * ant_per_block, a1 = std::min<int64_t>(n_ant, a0 + ant_per_block);
+        const int Kp = hs[g].K;
+        const int ex = inst <= 32 ? std::min(inst, Kp <= 16 ? 16 : (Kp + 1) & ~1) : std::max(32, (Kp + 7) / 8 * 8);
+        sum += (double)std::max<int64_t>(j1 - j0, 0) * (double)std::max<int64_t>(a1 - a0, 0) * ex;
     }
     orders[0] = h.K;
     orders[1] = km;
     orders[2] = inst;
-    *mean_orders = sum / (double)n;
+    *mean_orders = sum / ((double)n * (double)n_ant);
     return GERAF_OK;
 }
 
