@@ -41,12 +41,13 @@ CHEB_FLOPS_PER_ORDER = 6
 PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
 # DRAM bytes (read + write) of each Chebyshev phasor kernel from one ncu capture
 # of the small C2 case (65 536 points, 32^3 voxels, 4096 antennas, 128 bins),
-# scaled to a full launch by the points or voxels it processes (the records read
-# and the split partials written both grow in proportion).
-NCU_DRAM_SMALL = {"render": (9.36e6 + 15.67e6, "points", 65536), "filter_backward": (8.15e6 + 16.33e6, "voxels", 32768),
-                  "render_backward": (141.86e6 + 18.92e6, "points", 65536)}
+# used as they are for that case and, for a kernel with no full-size capture,
+# scaled by the points or voxels it processes (an approximation: the records
+# and split partials grow in proportion, the per-group antenna rows do not).
+NCU_DRAM_SMALL = {"render": (8.83e6 + 14.92e6, "points", 65536), "render_backward": (142.02e6 + 16.26e6, "points", 65536),
+                  "filter": (69.67e6 + 0.98e6, "voxels", 32768), "filter_backward": (7.52e6 + 15.55e6, "voxels", 32768)}
 # the same counters taken at the full C2 size (one launch each, a 1-pass capture)
-NCU_DRAM_FULL = {"render": 108.70e6 + 30.65e6, "render_backward": 475.83e6 + 89.73e6}
+NCU_DRAM_FULL = {"render": 109.05e6 + 28.33e6, "render_backward": 473.97e6 + 88.62e6}
 
 
 def _env_int(k, d):
