@@ -773,14 +773,13 @@ __device__ void bessel_j(double a, int kcount, double* out) {
     for (int k = 0; k < kcount; ++k) out[k] *= inv_norm;
 }
 
-// one block: points bbox + antennas -> range bound, order K, coefficients C[k][n]
+// one block: points bbox + antennas -> the whole call's range bound and order
+// K, and the choice between the Chebyshev form and the recurrence (the
+// coefficient tables come per part from split_plan_kernel)
 __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, const float* __restrict__ ant,
-                                 int n_ant, double Kd, int n_f, double eps, ChebPlan* __restrict__ plan,
-                                 double2* __restrict__ C) {
+                                 int n_ant, double Kd, int n_f, double eps, ChebPlan* __restrict__ plan) {
     __shared__ float box[6];
     __shared__ float rr[3][256];
-    __shared__ int sK;
-    __shared__ float s_rc, s_inv;
     const int t = threadIdx.x;
     if (t < 6) {
         float v = t < 3 ? INFINITY : -INFINITY;
@@ -837,32 +836,6 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
         plan->K = K;
         plan->use_direct = direct;
         plan->run_cheb = !direct;
-        sK = K;
-        s_rc = rc;
-        s_inv = inv;
-    }
-    __syncthreads();
-    const int K = sK;
-    const double dr = 1.0 / (double)s_inv;
-    for (int n = t; n < n_f; n += blockDim.x) {
-        double J[CH_KMAX];
-        const double an = 2.0 * 3.14159265358979323846 * n * Kd * dr;
-        bessel_j(an, K, J);
-        // exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
-        double sphi, cphi;
-        sincospi(-2.0 * (double)n * Kd * (double)s_rc, &sphi, &cphi);
-        for (int k = 0; k < K; ++k) {
-            const double m = (k == 0 ? 1.0 : 2.0) * J[k];
-            double pr, pi;      // (-j)^k
-            switch (k & 3) {
-                case 0: pr = 1.0; pi = 0.0; break;
-                case 1: pr = 0.0; pi = -1.0; break;
-                case 2: pr = -1.0; pi = 0.0; break;
-                default: pr = 0.0; pi = 1.0; break;
-            }
-            const double ar = m * pr, ai = m * pi;
-            C[(size_t)k * n_f + n] = make_double2(cphi * ar - sphi * ai, cphi * ai + sphi * ar);
-        }
     }
 }
 
@@ -965,7 +938,7 @@ __device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const 
 template <bool kComplexAmp, int KC>
 __global__ void __launch_bounds__(CH_THREADS, KC <= 4 ? GERAF_CH_BINS_CTAS : 1) cheb_bins_kernel(const ChebBinsArgs args) {
     constexpr int KM = 8 * KC;
-    constexpr int KU = KC < 4 ? 8 * KC : 32;                 // orders computed without guards
+    constexpr int KU = KC < 4 ? 8 * KC : 32;                 // orders every flush covers
     if (!args.plan->run_cheb) return;
     {
         const int km = *args.kmax;
@@ -1650,16 +1623,14 @@ namespace {
 struct ChebWs {
     float* bbox;
     ChebPlan* plan;
-    double2* C;
     int n_bbox_blocks;
 };
 
-ChebWs take_cheb(WsCarver& c, int64_t n_bbox, int n_f) {
+ChebWs take_cheb(WsCarver& c, int64_t n_bbox) {
     ChebWs w;
     w.n_bbox_blocks = (int)std::min<int64_t>((n_bbox + 255) / 256, 1024);
     w.bbox = c.take<float>((size_t)w.n_bbox_blocks * 6);
     w.plan = c.take<ChebPlan>(1);
-    w.C = c.take<double2>((size_t)CH_KMAX * n_f);
     return w;
 }
 
@@ -1712,7 +1683,7 @@ void launch_cheb_plan(const ChebWs& w, const float* pts, int64_t n, const float*
                       const geraf_band* band, cudaStream_t st) {
     bbox_partial_kernel<<<w.n_bbox_blocks, 256, 0, st>>>(pts, n, w.bbox);
     cheb_plan_kernel<<<1, 256, 0, st>>>(w.bbox, w.n_bbox_blocks, ant, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
-                                        w.plan, w.C);
+                                        w.plan);
 }
 
 struct ChebBinsPlan {
@@ -1769,7 +1740,7 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     int* kmax = nullptr;
     float2* gout = nullptr;
     if (cheb) {
-        cw = take_cheb(c, n_pts, band->n_f);
+        cw = take_cheb(c, n_pts);
         cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
         sbox = c.take<float>((size_t)q.splits * 6);
         splan = c.take<SplitPlan>(parts);
@@ -1861,7 +1832,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     ChebWs cw{};
     PointGroups pg{};
     if (cheb) {
-        cw = take_cheb(c, n_vox, band->n_f);
+        cw = take_cheb(c, n_vox);
         pg = take_point_groups(c, p.pt_ctas, p.n_ant_pad, band->n_f);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
@@ -1922,7 +1893,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     ChebWs cw{};
     PointGroups pg{};
     if (cheb) {
-        cw = take_cheb(c, n_pts, band->n_f);
+        cw = take_cheb(c, n_pts);
         pg = take_point_groups(c, p.pt_ctas, p.n_ant_pad, band->n_f);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
@@ -2017,7 +1988,7 @@ geraf_status chebyshev_order_impl(const float* xyz, int64_t n, const float* ant_
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
     WsCarver c(ws);
-    ChebWs cw = take_cheb(c, n, band->n_f);
+    ChebWs cw = take_cheb(c, n);
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "chebyshev_order: workspace %zu < %zu bytes", *ws_bytes, c.used);
@@ -2066,7 +2037,7 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     }
     const int n_splits = parts / n_ab;
     WsCarver c(ws);
-    ChebWs cw = take_cheb(c, n, band->n_f);
+    ChebWs cw = take_cheb(c, n);
     float* box = c.take<float>((size_t)n_splits * 6);
     SplitPlan* splan = c.take<SplitPlan>(parts);
     float2* Cs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
