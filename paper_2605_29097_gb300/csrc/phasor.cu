@@ -699,6 +699,11 @@ constexpr int CH_KMAX = 64;
 #ifndef GERAF_CH_BINS_CTAS
 #define GERAF_CH_BINS_CTAS 5
 #endif
+// the render's K <= 24 instance fits six (78 registers, no spills; measured
+// 34.9 against 35.7 ms at C2); the filter adjoint's ran slower at six
+#ifndef GERAF_CH_BINS_CTAS_24
+#define GERAF_CH_BINS_CTAS_24 6
+#endif
 #ifndef GERAF_CH_FILTER_CTAS
 #define GERAF_CH_FILTER_CTAS 8
 #endif
@@ -936,7 +941,9 @@ __device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const 
     case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K, mr, mi); break;
 
 template <bool kComplexAmp, int KC>
-__global__ void __launch_bounds__(CH_THREADS, KC <= 4 ? GERAF_CH_BINS_CTAS : 1) cheb_bins_kernel(const ChebBinsArgs args) {
+__global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_CH_BINS_CTAS_24
+                                                                     : (KC <= 4 ? GERAF_CH_BINS_CTAS : 1))
+    cheb_bins_kernel(const ChebBinsArgs args) {
     constexpr int KM = 8 * KC;
     constexpr int KU = KC < 4 ? 8 * KC : 32;                 // orders every flush covers
     if (!args.plan->run_cheb) return;
