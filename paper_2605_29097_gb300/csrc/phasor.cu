@@ -844,9 +844,11 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
     }
 }
 
-// Expansion of one split of the to-bins sums: the split's points form a thin
-// depth slab, so their range interval against the antennas, and with it the
-// order K, is narrower than the whole call's
+// Expansion of one part of a Chebyshev call (a split of point tiles, possibly
+// times a block of antennas, for the to-bins sums; a group of points for the
+// to-points sums): its range interval r_c +/- 1/inv_dr and order K. Consecutive
+// points of the depth-major sampler form thin depth slabs, so a part's interval,
+// and with it K, is narrower than the whole call's.
 struct SplitPlan {
     float r_c, inv_dr;
     int K;
