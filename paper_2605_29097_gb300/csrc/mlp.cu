@@ -435,6 +435,16 @@ __global__ void __launch_bounds__(BT, 1) mlp_layer_bwd_kernel(const BwdArgs a) {
         // first layer: its input is the positional encoding (columns of points beyond n
         // meet a zero HbT and contribute nothing)
         if (!hin) pe_tile<true>(ZT, a.xyz, g, j0);
+        // the next tile's rows (contiguous 2 KB per point in each array) head for
+        // L2 while this tile's two products run, so its staging reads L2
+        const int next = tile + gridDim.x;
+        if (t == 0 && next < g.n_tiles) {
+            const int64_t jn = (int64_t)next * MTP;
+            const uint32_t bytes = (uint32_t)(min((int64_t)MTP, g.n - jn) * 4 * MW * sizeof(float));
+            prefetch_l2_bulk(a.zbar + jn * 4 * MW, bytes);
+            prefetch_l2_bulk(hs + jn * 4 * MW, bytes);
+            if (hin) prefetch_l2_bulk(hin + jn * 4 * MW, bytes);
+        }
         __syncthreads();
         // weight gradient: accw[u][k] += sum_c HbT[c][u] ZT[c][k]; an input width of
         // at most 64 (the encoding layer) leaves the upper half of the k tile zero
