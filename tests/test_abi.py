@@ -67,4 +67,15 @@ def test_argument_errors_return_status_without_device(libgeraf):
     order = ctypes.c_int32(-1)
     assert libgeraf.geraf_chebyshev_order(None, 100, None, 4, ctypes.byref(cheb), None, ctypes.byref(n),
                                           ctypes.byref(order), None) == 0 and n.value > 0
+    # the orders query: size query in both directions, bad direction rejected
+    orders = (ctypes.c_int32 * 3)()
+    mean = ctypes.c_double(0.0)
+    for to_points in (0, 1):
+        n.value = 0
+        assert libgeraf.geraf_chebyshev_work(None, 5000, None, 300, ctypes.byref(cheb), to_points, None,
+                                             ctypes.byref(n), orders, ctypes.byref(mean), None) == 0
+        assert n.value > 0
+    assert libgeraf.geraf_chebyshev_work(None, 5000, None, 300, ctypes.byref(cheb), 2, None, ctypes.byref(n),
+                                         orders, ctypes.byref(mean), None) == 1
+    assert b"to_points" in libgeraf.geraf_last_error_string()
     assert libgeraf.geraf_version() >= 1
