@@ -682,7 +682,7 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
 // Per antenna i, the frequency dependence of a term is exp(-j 2 pi (f0 + n df)
 // 2 r / c). The f0 part is folded into the point's complex amplitude (one
 // double-single phase and one sincos per pair); with r = r_c + dr x, |x| <= 1
-// over the whole call, the Jacobi-Anger expansion
+// over a range interval, the Jacobi-Anger expansion
 //   exp(-j a_n x) = sum_k eps_k (-j)^k J_k(a_n) T_k(x),  a_n = 2 pi n (2 df / c) dr,
 // truncated where the Bessel tail falls below 1e-9, turns the bin sums into
 // K Chebyshev moments per antenna (K ~ a_max + 15, about 30 for a 4 GHz sweep
@@ -690,10 +690,13 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
 //   to bins:   s(i, n) = sum_k C_k(n) M_k(i),  M_k(i) = sum_j A'_ij T_k(x_ij)
 //   to points: sum_n s(i, n) exp(+j ...) = exp(+j 2 pi K0 r) sum_k T_k(x) S_k(i),
 //              evaluated per pair with T_k from the three-term recurrence.
-// C_k(n) = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n) is computed on the device
-// (Miller's backward recurrence in FP64) from a range bound of the call's
-// points and antennas, so the call stays asynchronous. If K would exceed
-// CH_KMAX the exact recurrence kernels run instead (decided on the device).
+// Each part of a call (a split of point tiles, possibly times a block of
+// antennas, to bins; a group of points, to points) has its own interval, order
+// and table C_k(n) = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n), computed on the
+// device (Miller's backward recurrence in FP64) from the part's bounding box and
+// antennas, so the call stays asynchronous. If the whole call's order K would
+// exceed CH_KMAX the exact recurrence kernels run instead (decided on the
+// device).
 constexpr int CH_KMAX = 64;
 // resident CTAs per SM asked of the compiler for the K <= 32 instances
 #ifndef GERAF_CH_BINS_CTAS
