@@ -50,12 +50,12 @@ static double directional_factor(double gx, double gy, double gz,
  * transmittance, integrated as in App. B.2): t_eff_j = T_j + Phi_s(f(x_apr)) is
  * the primary-ray transmittance plus the primary origin's sigmoid-SDF, c_ant_i
  * = Phi_s(f(a_i)) the real origin's; the result is clamped to [0, 1]. The
- * clamp's slope is 1 on the closed interval, decided in FP32 like the kernel. */
+ * clamp's slope (the subgradient taken at its two kinks) is 1 on the closed
+ * interval 0 <= t_eff - c_ant <= 1, decided in FP64 on the exact difference. */
 static double lensless_T(double t_eff, double c_ant, int* inside)
 {
     double v = t_eff - c_ant;
-    float vf = (float)t_eff - (float)c_ant;
-    *inside = (vf >= 0.0f && vf <= 1.0f);
+    *inside = (v >= 0.0 && v <= 1.0);
     if (v < 0.0) return 0.0;
     if (v > 1.0) return 1.0;
     return v;

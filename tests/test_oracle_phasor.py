@@ -236,6 +236,37 @@ def test_render_backward_matches_finite_differences(oracle):
                                        rtol=1e-5, atol=1e-8 * abs(d_G).max())
 
 
+def test_render_backward_clamp_slope_decided_on_the_exact_difference(oracle):
+    """The lensless transmittance T' = clamp(t_eff - c_ant, 0, 1) (section 6,
+    App. B.2) has kinks at 0 and 1. The oracle takes the side of each kink
+    from the exact FP64 difference of its (FP32-valued) inputs: pairs 2^-24 or
+    2^-25 away from a kink, where FP32 rounding of the difference would land
+    on the kink itself, get the derivative of the side they lie on (central
+    differences with a step well inside that side), and 0 outside [0, 1]."""
+    band = gi.band(77e9, 81e9, 5)
+    ant = np.zeros((3, 1))
+    xyz = np.array([[0.004], [-0.003], [0.13]])
+    G = np.zeros((3, 1))                                   # isotropic: D = 1
+    w = np.array([0.7])
+    g = gi.complex_normal(np.random.default_rng(3), (1, band.n_f))
+    cases = [(1.5, 0.5 - 2.0 ** -25, False),               # t - c = 1 + 2^-25: clamped at 1
+             (1.5, 0.5 + 2.0 ** -24, True),                # 1 - 2^-24: inside
+             (0.5, 0.5 + 2.0 ** -24, False),               # -2^-24: clamped at 0
+             (0.5, 0.5 - 2.0 ** -25, True)]                # 2^-25: inside
+    for t0, c0, inside in cases:
+        t_eff, c_ant = np.array([t0]), np.array([c0])
+        assert np.float32(t0) == t0 and np.float32(c0) == c0
+        L = lambda t_: np.real(np.vdot(g, oracle.render(xyz, G, w, t_, ant, c_ant, band)))
+        _, d_t, _ = oracle.render_backward(xyz, G, w, t_eff, ant, c_ant, band, g)
+        h = 2.0 ** -32
+        fd = (L(t_eff + h) - L(t_eff - h)) / (2 * h)
+        if inside:
+            assert d_t[0] != 0.0
+            np.testing.assert_allclose(d_t[0], fd, rtol=1e-4)
+        else:
+            assert d_t[0] == 0.0 and fd == 0.0
+
+
 def test_filter_backward_matches_finite_differences(oracle):
     rng = np.random.default_rng(7)
     band = gi.band(77e9, 81e9, 4)
