@@ -212,7 +212,7 @@ def mlp_forward(spec, params, xyz, precision="fp32"):
     for W, b in layers[:-1]:
         Wr, zr, dzr = r(W), r(z), r(dz)
         h = Wr @ zr + b[:, None]
-        dh = np.einsum("oi,din->don", Wr, dzr)
+        dh = Wr @ dzr                                  # [3, out, N]: W times each tangent
         s = _sigmoid(spec.beta * h)
         z = _softplus(h, spec.beta)
         dz = s[None] * dh
@@ -221,7 +221,7 @@ def mlp_forward(spec, params, xyz, precision="fp32"):
     Wh, bh = layers[-1]
     zr, dzr = r(z), r(dz)
     f = Wh[0] @ zr + bh[0]
-    G = np.einsum("i,din->dn", Wh[0], dzr)
+    G = Wh[0] @ dzr                                    # [3, N]
     a = None
     if Wh.shape[0] == 2:                               # head [f, a_logit]
         a = _sigmoid(Wh[1] @ zr + bh[1])
@@ -245,7 +245,7 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
     Wh, _ = layers[-1]
     zL, dzL = r(cache["z"][-1]), r(cache["dz"][-1])
     gW = np.zeros_like(Wh)
-    gW[0] = zL @ d_f + np.einsum("dn,din->i", d_G, dzL)
+    gW[0] = zL @ d_f + sum(dzL[d] @ d_G[d] for d in range(3))
     zbar = np.outer(Wh[0], d_f)
     if Wh.shape[0] == 2:                               # head [f, a_logit]
         a = cache["a"]
@@ -255,7 +255,7 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
         zbar = zbar + np.outer(Wh[1], d_logit)
     else:
         grads[-1] = (gW, np.array([d_f.sum()]))
-    dzbar = np.einsum("i,dn->din", Wh[0], d_G)
+    dzbar = Wh[0][None, :, None] * d_G[:, None, :]     # [3, width, N]
     for l in range(len(layers) - 2, -1, -1):
         W = r(layers[l][0])
         h, dh = cache["h"][l], cache["dh"][l]
@@ -264,10 +264,10 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
         dhbar = s[None] * dzbar                        # through dz = s * dh
         hbar = zbar * s + (dzbar * dh).sum(0) * ds     # through z = softplus(h) and s(h)
         zin, dzin = r(cache["z"][l]), r(cache["dz"][l])
-        gW = hbar @ zin.T + np.einsum("don,din->oi", dhbar, dzin)
+        gW = hbar @ zin.T + sum(dhbar[d] @ dzin[d].T for d in range(3))
         grads[l] = (gW, hbar.sum(1))
         zbar = W.T @ hbar
-        dzbar = np.einsum("oi,don->din", W, dhbar)
+        dzbar = W.T @ dhbar                            # [3, in, N]
     return np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
 
 
