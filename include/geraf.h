@@ -243,7 +243,7 @@ geraf_status geraf_render(const float* xyz, const float* grad, const float* w, c
                           void* ws, size_t* ws_bytes, float* s_out, void* stream);
 
 /*
- * geraf_render_noalloc — the same signal tracing as geraf_render, for callers
+ * geraf_render_noalloc — the signal tracing of geraf_render, for callers
  * that cannot allocate device memory themselves (for example a plug-in whose
  * host application owns every device allocation, or code that runs where the
  * application forbids new allocations): it takes no workspace and allocates
@@ -256,7 +256,10 @@ geraf_status geraf_render(const float* xyz, const float* grad, const float* w, c
  * streams or from different host threads) race and give undefined results.
  * Inputs that need more than 32 MiB of scratch (the packed points, 48 bytes
  * each, plus at least one n_ant x 32*ceil(n_f/32) complex partial) are
- * rejected with GERAF_ERR_UNSUPPORTED; use geraf_render for them. Results
+ * rejected with GERAF_ERR_UNSUPPORTED; use geraf_render for them. It always
+ * steps across the bins by the per-bin recurrence, whatever band->method asks
+ * (the Chebyshev form's tables would not fit the static array), so at 64 bins
+ * and more it is several times slower than geraf_render's default. Results
  * match geraf_render to FP32 rounding (the split of the point sum may differ).
  */
 geraf_status geraf_render_noalloc(const float* xyz, const float* grad, const float* w, const float* t_eff,

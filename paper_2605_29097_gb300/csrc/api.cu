@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -90,6 +91,26 @@ int* device_error_word() {
         if (cudaGetSymbolAddress(&p, g_device_error_word) == cudaSuccess) g_err_ptr[d] = static_cast<int*>(p);
     }
     return g_err_ptr[d];
+}
+
+// (kernel, device, bytes) opted in to large dynamic shared memory so far
+struct SmemAttr {
+    const void* func;
+    int dev;
+    int bytes;
+};
+static std::mutex g_attr_mu;
+static std::vector<SmemAttr> g_attr_done;
+
+geraf_status ensure_smem_attr(const void* func, int bytes, const char* what) {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    for (const SmemAttr& a : g_attr_done)
+        if (a.func == func && a.dev == d && a.bytes >= bytes) return GERAF_OK;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return cuda_status(e, what);
+    g_attr_done.push_back(SmemAttr{func, d, bytes});
+    return GERAF_OK;
 }
 
 int device_sm_count() {

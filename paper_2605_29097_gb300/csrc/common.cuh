@@ -16,6 +16,17 @@ geraf_status fail(geraf_status st, const char* fmt, ...);
 geraf_status cuda_status(cudaError_t e, const char* what);
 int device_sm_count();
 
+// Opts a kernel in to `bytes` of dynamic shared memory on the current device,
+// once per (kernel, device): thread-safe, and the CUDA error of a failed
+// attempt is returned (nothing is recorded then, so a later call retries).
+geraf_status ensure_smem_attr(const void* func, int bytes, const char* what);
+template <class... F>
+geraf_status smem_attrs(int bytes, const char* what, F*... funcs) {
+    geraf_status st = GERAF_OK;
+    ((st = st == GERAF_OK ? ensure_smem_attr(reinterpret_cast<const void*>(funcs), bytes, what) : st), ...);
+    return st;
+}
+
 // device error word: bit 0 = a bounded wait timed out. Read and cleared by
 // geraf_poll_device_error().
 int* device_error_word();

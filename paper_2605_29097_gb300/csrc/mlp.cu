@@ -595,10 +595,9 @@ geraf_status mlp_forward_impl(const geraf_field_desc* d, const float* xyz, int64
         if (saved_bytes < need) return fail(GERAF_ERR_WORKSPACE, "fields: saved %zu < %zu bytes", saved_bytes, need);
     }
     if (d->precision == GERAF_PREC_BF16) return mlp_tc_forward_impl(d, xyz, n, sdf, grad, refl, saved, st);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
-        attr = true;
+    {
+        const geraf_status as = smem_attrs((int)fwd_smem(), "shared-memory opt-in", mlp_fwd_kernel);
+        if (as != GERAF_OK) return as;
     }
     FwdArgs a{g, d->params, xyz, sdf, grad, refl, static_cast<float*>(saved)};
     mlp_fwd_kernel<<<n_ctas_for(g.n_tiles), FT, fwd_smem(), st>>>(a);
@@ -634,10 +633,9 @@ geraf_status mlp_backward_impl(const geraf_field_desc* d, const float* xyz, int6
         reduce_partials<<<(unsigned)((g.n_params + 255) / 256), 256, 0, st>>>(partial, n_cta, g.n_params, d_params);
         return cuda_status(cudaGetLastError(), "fields_backward(mlp bf16)");
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_layer_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
-        attr = true;
+    {
+        const geraf_status as = smem_attrs((int)bwd_smem(), "shared-memory opt-in", mlp_layer_bwd_kernel);
+        if (as != GERAF_OK) return as;
     }
     BwdArgs a{g, d->params, xyz, static_cast<const float*>(saved), d_sdf, d_grad, d_refl, zbar, partial, 0};
     mlp_head_bwd_kernel<<<n_cta, HT, 0, st>>>(a);

@@ -692,10 +692,9 @@ geraf_status mlp_tc_forward_impl(const geraf_field_desc* d, const float* xyz, in
     TcGeom g;
     if (!make_tc_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
     const size_t smem = tc_fwd_smem(g);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
+    {
+        const geraf_status as = smem_attrs(227 * 1024, "shared-memory opt-in", mlp_tc_fwd_kernel);
+        if (as != GERAF_OK) return as;
     }
     int n_cta = device_sm_count();
     if (n_cta > (g.n_tiles + 1) / 2) n_cta = (g.n_tiles + 1) / 2;
@@ -718,10 +717,9 @@ geraf_status mlp_tc_backward_impl(const geraf_field_desc* d, const float* xyz, i
                                   float* partial, int64_t n_params, int n_cta, cudaStream_t st) {
     TcGeom g;
     if (!make_tc_geom(d, n, &g)) return GERAF_ERR_UNSUPPORTED;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_tc_layer_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
+    {
+        const geraf_status as = smem_attrs(227 * 1024, "shared-memory opt-in", mlp_tc_layer_bwd_kernel);
+        if (as != GERAF_OK) return as;
     }
     TcBwdArgs a{g, d->params, xyz, static_cast<const float*>(saved), d_sdf, d_grad, d_refl, zbar, partial,
                 n_params, 0, device_error_word()};

@@ -583,12 +583,10 @@ geraf_status mlp_wide_forward(const geraf_field_desc* d, const float* xyz, int64
     // tangent streams only when the gradient is asked for
     Nets nets;
     if (!make_nets(d, grad ? 4 : 1, &nets)) return GERAF_ERR_UNSUPPORTED;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(wgemm_kernel<WG_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgemm_smem());
-        cudaFuncSetAttribute(wgemm_kernel<WG_DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgemm_smem());
-        cudaFuncSetAttribute(wgemm_kernel<WG_DW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgemm_smem());
-        attr = true;
+    {
+        const geraf_status as = smem_attrs((int)wgemm_smem(), "shared-memory opt-in", wgemm_kernel<WG_FWD>,
+                                           wgemm_kernel<WG_DZ>, wgemm_kernel<WG_DW>);
+        if (as != GERAF_OK) return as;
     }
     Nets full;
     make_nets(d, 4, &full);
@@ -690,11 +688,10 @@ geraf_status mlp_wide_backward(const geraf_field_desc* d, const float* xyz, int6
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "fields_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
     if (!saved) return fail(GERAF_ERR_INVALID_ARG, "fields_backward: saved is NULL");
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(wgemm_kernel<WG_DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgemm_smem());
-        cudaFuncSetAttribute(wgemm_kernel<WG_DW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgemm_smem());
-        attr = true;
+    {
+        const geraf_status as = smem_attrs((int)wgemm_smem(), "shared-memory opt-in", wgemm_kernel<WG_DZ>,
+                                           wgemm_kernel<WG_DW>);
+        if (as != GERAF_OK) return as;
     }
     // every split row of `partial` is written in full by the kernels below
     cudaError_t e = cudaMemsetAsync(partial, 0, (size_t)splits * nets.n_params * sizeof(float), st);

@@ -1769,17 +1769,13 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     else
         pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts);
     pack_antennas<<<grid1d(n_ant_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, n_ant_rec, ant);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(to_bins_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_bins_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
+    {
+        const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_bins_kernel<false>,
+                                           to_bins_kernel<true>, cheb_bins_kernel<false, 3>,
+                                           cheb_bins_kernel<true, 3>, cheb_bins_kernel<false, 4>,
+                                           cheb_bins_kernel<true, 4>, cheb_bins_kernel<false, 8>,
+                                           cheb_bins_kernel<true, 8>);
+        if (as != GERAF_OK) return as;
     }
     const int* run_direct = nullptr;
     if (cheb) {
@@ -1850,16 +1846,11 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
     int* err = device_error_word();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(to_points_kernel<MODE_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_FILTER, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        attr_set = true;
+    {
+        const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_points_kernel<MODE_FILTER>,
+                                           cheb_points_kernel<MODE_FILTER, 3>, cheb_points_kernel<MODE_FILTER, 4>,
+                                           cheb_points_kernel<MODE_FILTER, 8>);
+        if (as != GERAF_OK) return as;
     }
     const int* run_direct = nullptr;
     if (cheb) {
@@ -1914,17 +1905,12 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     int* err = device_error_word();
     pack_render_points<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pts,
                                                            (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(to_points_kernel<MODE_RENDER_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(cheb_points_kernel<MODE_RENDER_BWD, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        attr_set = true;
+    {
+        const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_points_kernel<MODE_RENDER_BWD>,
+                                           cheb_points_kernel<MODE_RENDER_BWD, 3>,
+                                           cheb_points_kernel<MODE_RENDER_BWD, 4>,
+                                           cheb_points_kernel<MODE_RENDER_BWD, 8>);
+        if (as != GERAF_OK) return as;
     }
     const int* run_direct = nullptr;
     if (cheb) {
@@ -2103,7 +2089,10 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
 // this library holds until the process exits. All calls share the array, so
 // calls that overlap on the GPU (other streams, other host threads) race on
 // it. Nothing in it must start at zero: every call rewrites all the records
-// and partials it later reads.
+// and partials it later reads. It always runs the per-bin recurrence
+// (to_bins_kernel): the Chebyshev form's coefficient tables and moment partials
+// (up to hundreds of MiB) do not fit a modest static array, so band->method is
+// not consulted.
 namespace geraf {
 namespace {
 constexpr size_t kNoAllocScratchBytes = 32ull << 20;   // 32 MiB
@@ -2155,17 +2144,17 @@ geraf_status render_noalloc_impl(const float* xyz, const float* grad, const floa
     float4* ant = c.take<float4>(p.n_ant_pad);
     float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
     if (c.used > kNoAllocScratchBytes) return fail(GERAF_ERR_UNSUPPORTED, "render_noalloc: scratch overflow");
+    {
+        // per device, before anything is launched: a failure leaves nothing in flight
+        const geraf_status as = smem_attrs(200 * 1024, "render_noalloc: shared-memory opt-in", to_bins_kernel<false>);
+        if (as != GERAF_OK) return as;
+    }
     int* err = device_error_word();
     const int64_t n_pad = (int64_t)p.n_tiles * p.TP;
     pack_render_points<<<grid1d(n_pad, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pad,
                                                            (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
     pack_antennas<<<grid1d(p.n_ant_pad, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, p.n_ant_pad, ant);
     ToBinsArgs a{pts, ant, part, err, p.TP, p.n_tiles, p.tiles_per_split, p.n_ant_pad, p.A_T, bk, nullptr};
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(to_bins_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
     to_bins_kernel<false><<<dim3(p.ant_ctas, p.splits), TB_THREADS, p.smem, st>>>(a);
     reduce_bins<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(part, p.splits, n_ant, p.n_ant_pad,
                                                                          band->n_f, 32 * p.G,

@@ -445,10 +445,9 @@ geraf_status sample_backward_impl(const geraf_proposal* p, const geraf_grid* gr,
     prop_loss_kernel<<<g1(plane, 128), 128, 0, st>>>(g, logits, hist, dlog, col_loss);
     if (loss) sum_doubles_1<<<1, 256, 0, st>>>(col_loss, plane, loss);
     const size_t smem = (size_t)(2 * g.n_params + 2 * PBT * PW + PBT) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(prop_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
+    {
+        const geraf_status as = smem_attrs(220 * 1024, "shared-memory opt-in", prop_backward_kernel);
+        if (as != GERAF_OK) return as;
     }
     prop_backward_kernel<<<n_cta, PBT, smem, st>>>(g, static_cast<const __half*>(p->features), p->params,
                                                    static_cast<const float*>(saved), dlog, d_features, partial);

@@ -93,3 +93,73 @@ def test_mlp_bf16_tensor_cores(G, oracle, n, n_levels, n_hidden):
     gp = G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a))
     ogp = oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)
     assert rel_l2(h(gp), ogp) < 2e-3
+
+
+def _many_tiles_case(spec, n, seed):
+    params = gi.mlp_init(spec, seed=seed)
+    rng = np.random.default_rng(seed)
+    xyz = (np.array(spec.center)[:, None] + rng.uniform(-spec.half, spec.half, (3, n))).astype(np.float32)
+    d = (rng.standard_normal(n).astype(np.float32), rng.standard_normal((3, n)).astype(np.float32),
+         rng.standard_normal(n).astype(np.float32))
+    return params, xyz, d
+
+
+def test_mlp_fp32_persistent_tiles(G, oracle):
+    """70 001 points (ragged) = 2188 tiles of 32 points over at most one CTA per
+    SM: every CTA of the forward runs its persistent tile loop 14-15 times, and
+    every CTA of each hidden layer's adjoint accumulates the weight gradient in
+    registers over as many tiles while it prefetches the next tile's rows into
+    L2. Every output and every layer's weight and bias block against the FP64
+    oracle at relative L2 1e-5."""
+    n = 70001
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert (n + 31) // 32 >= 8 * sms
+    spec = gi.MLPSpec()
+    params, xyz, (d_f, d_G, d_a) = _many_tiles_case(spec, n, 21)
+    field = G.MLPField(torch.as_tensor(params, device="cuda"))
+    xt = torch.as_tensor(xyz, device="cuda")
+    f, grad, a, saved = G.geraf_fields(field, xt, keep_saved=True)
+    G.geraf_poll_device_error()
+    of, oG, oa, cache = oracle.mlp_forward(spec, params, xyz)
+    h = lambda t: t.detach().cpu().numpy()
+    assert rel_l2(h(f), of) < 1e-5
+    assert rel_l2(h(a), oa) < 1e-5
+    assert rel_l2(h(grad), oG) < 1e-5
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    gp = h(G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a)))
+    G.geraf_poll_device_error()
+    ogp = oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)
+    assert rel_l2(gp, ogp) < 1e-5
+    off = 0
+    for li, (o, i) in enumerate(spec.shapes()):
+        for name, sz in (("W", o * i), ("b", o)):
+            e = rel_l2(gp[off:off + sz], ogp[off:off + sz])
+            assert e < 1e-5, f"layer {li} {name}: {e:.2e}"
+            off += sz
+
+
+def test_mlp_bf16_persistent_tiles(G, oracle):
+    """The BF16 tensor-core kernels at 70 001 points: the forward runs pairs of
+    32-point tiles (1094 pairs, ~7 per CTA), the adjoint 16-point tiles (4376,
+    ~29 per CTA) with each layer's weight gradient accumulated in TMEM across
+    them. Against the oracle's BF16 network definition at 2e-3."""
+    n = 70001
+    spec = gi.MLPSpec()
+    params, xyz, (d_f, d_G, d_a) = _many_tiles_case(spec, n, 22)
+    field = G.MLPField(torch.as_tensor(params, device="cuda"), precision=G.PREC_BF16)
+    xt = torch.as_tensor(xyz, device="cuda")
+    f, grad, a, saved = G.geraf_fields(field, xt, keep_saved=True)
+    G.geraf_poll_device_error()
+    of, oG, oa, cache = oracle.mlp_forward(spec, params, xyz, precision="bf16")
+    h = lambda t: t.detach().cpu().numpy()
+    assert max(rel_l2(h(f), of), rel_l2(h(a), oa), rel_l2(h(grad), oG)) < 2e-3
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    gp = h(G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a)))
+    G.geraf_poll_device_error()
+    ogp = oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)
+    assert rel_l2(gp, ogp) < 2e-3
+    off = 0
+    for li, (o, i) in enumerate(spec.shapes()):
+        e = rel_l2(gp[off:off + o * i], ogp[off:off + o * i])
+        assert e < 2e-3, f"layer {li} W: {e:.2e}"
+        off += o * i + o

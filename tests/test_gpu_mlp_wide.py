@@ -78,6 +78,40 @@ def test_two_networks_forward_backward(G, oracle, paper_size, n):
         off += o * i + o
 
 
+def test_paper_networks_many_splits(G, oracle):
+    """The paper's two networks on 32 771 points (ragged): the adjoint's weight
+    gradients run over SMs/2 = 76 splits of the rows (432 points each), their
+    partials summed in FP64 in a fixed order, and the GEMMs over 257 row tiles
+    of 128. Every output, each network's block and each SDF layer's weight
+    block against the FP64 oracle."""
+    n = 32771
+    nets = gi.paper_nets()
+    params = gi.nets_init(nets, seed=5, sdf_bias=0.01)
+    xyz, rng = _points(nets.sdf, n, 13)
+    field = _field(G, nets, params)
+    xt = torch.as_tensor(xyz, device="cuda")
+    f, grad, a, saved = G.geraf_fields(field, xt, keep_saved=True)
+    G.geraf_poll_device_error()
+    of, oG, oa, cache = oracle.nets_forward(nets, params, xyz)
+    h = lambda t: t.detach().cpu().numpy()
+    assert rel_l2(h(f), of) < 1e-5 and rel_l2(h(a), oa) < 1e-5 and rel_l2(h(grad), oG) < 1e-5
+    d_f = rng.standard_normal(n).astype(np.float32)
+    d_G = rng.standard_normal((3, n)).astype(np.float32)
+    d_a = rng.standard_normal(n).astype(np.float32)
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    gp = h(G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a)))
+    G.geraf_poll_device_error()
+    ogp = oracle.nets_backward(nets, params, cache, d_f, d_G, d_a)
+    assert rel_l2(gp, ogp) < 3e-5
+    ns = nets.sdf.n_params
+    assert rel_l2(gp[ns:], ogp[ns:]) < 3e-5
+    off = 0
+    for li, (o, i) in enumerate(nets.sdf.shapes()):
+        e = rel_l2(gp[off:off + o * i], ogp[off:off + o * i])
+        assert e < 3e-5, f"SDF layer {li}: {e:.2e}"
+        off += o * i + o
+
+
 def test_wide_single_trunk(G, oracle):
     """One trunk with head [f, a_logit] at width 256 runs the layer-by-layer
     kernels too; ragged point count."""

@@ -50,7 +50,12 @@ def _rel(a, b):
     return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
 
 
-@pytest.mark.parametrize("n_pts,n_side,n_f", [(5003, 10, 45), (32769, 16, 32)])
+# (5003, 10, 96): 64 bins and more, where geraf_render runs its Chebyshev form
+# and the no-allocation call still runs the per-bin recurrence;
+# (600 001, 16, 512): 28.8 MB of packed points leave room for only 4 of the
+# 1 MB split partials, so the call merges point tiles into fewer splits.
+@pytest.mark.parametrize("n_pts,n_side,n_f", [(5003, 10, 45), (32769, 16, 32), (5003, 10, 96),
+                                              (600001, 16, 512)])
 def test_noalloc_matches_render_twice(G, n_pts, n_side, n_f):
     rng = np.random.default_rng(n_pts)
     args, b = _inputs(rng, n_pts, n_side, n_f)
