@@ -3,12 +3,19 @@
 One step = one pass of the whole hot path over one batch of synthetic input
 (stratified sampling, MLP fields with gradient tangents, lensless blending,
 signal tracing, matched filter + L2 loss, and the adjoints of all of them down
-to the MLP parameter gradient). Workload (default): 64x64 array at 2 mm,
-128 frequencies over 77-81 GHz, 128^3 stratified samples of a 10 cm cube,
-SDF/reflectiveness MLP 4x128 (softplus, PE 6 octaves, FP32, seeded init),
-64^3 heatmap against a synthetic target (sphere + point reflector).
+to the MLP parameter gradient). Headline workload (default, the largest
+single-GPU configuration): 128x128 array at 2 mm, 256 frequencies over
+77-81 GHz, 256^3 stratified samples of a 10 cm cube, SDF/reflectiveness MLP
+4x128 (softplus, PE 6 octaves) in BF16 on the tcgen05 tensor cores with FP32
+accumulation, FP32 phasor sums, 64^3 heatmap against a synthetic target
+(sphere + point reflector). The same line carries the 64x64-array, 128-bin,
+128^3-sample FP32 step ("c2"), the per-bin recurrence measured beside the
+default Chebyshev form, the signal tracing bank, the training-step comparison
+of proposal against uniform sampling and the paper's own training
+configuration.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                  [--workload c3|c2|c3-small|c2-small]
 
 N > 1 runs under torchrun, one independent replica per GPU (no collective on
 the data path; weak scaling); rank 0 prints one JSON line.
@@ -26,8 +33,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "point·antenna·freq phasor terms/s fwd+adj; train-step ms at ≤2e-3 rel err"
-WORKLOAD = ("64x64 array @2mm, 128 freqs 77-81 GHz, 128^3 stratified samples, MLP 4x128 fp32, "
-            "64^3 heatmap, forward + adjoint of every step")
+WORKLOADS = {
+    "c3": ("128x128 array @2mm, 256 freqs 77-81 GHz, 256^3 stratified samples, MLP 4x128 bf16 on tcgen05 "
+           "(fp32 accumulate), 64^3 heatmap, forward + adjoint of every step"),
+    "c2": ("64x64 array @2mm, 128 freqs 77-81 GHz, 128^3 stratified samples, MLP 4x128 fp32, "
+           "64^3 heatmap, forward + adjoint of every step"),
+    "c3-small": "c3 array, band and bf16 MLP on 64x64x16 stratified samples, 32^3 heatmap (profiling size)",
+    "c2-small": "c2 array, band and fp32 MLP on 64x64x16 stratified samples, 32^3 heatmap (profiling size)",
+}
+DTYPES = {"fp32": "f32", "bf16": "f32 phasor sums + bf16 MLP (fp32 accumulate)"}
 # Algorithmic FP32 flops (FMA = 2) of the phasor sums.
 # Per-bin recurrence, per (point, antenna, bin) term: real amplitude times the
 # unit phasor into a complex sum (2 FMA) and the angle-addition step (2 MUL +
@@ -39,17 +53,14 @@ WORKLOAD = ("64x64 array @2mm, 128 freqs 77-81 GHz, 128^3 stratified samples, ML
 FLOPS_PER_TERM = {"render": 10, "filter_backward": 10, "filter": 8, "render_backward": 8}
 CHEB_FLOPS_PER_ORDER = 6
 PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
-# DRAM bytes (read + write) of each Chebyshev phasor kernel from one ncu capture
-# of the small C2 case (65 536 points, 32^3 voxels, 4096 antennas, 128 bins),
-# used as they are for that case and, for a kernel with no full-size capture,
-# scaled by the points or voxels it processes (an approximation: the records
-# and split partials grow in proportion, the per-group antenna rows do not).
-# (the render's kernel has been rebuilt for six CTAs per SM since its capture:
-# no entry until it is taken again)
-NCU_DRAM_SMALL = {"render_backward": (142.02e6 + 16.26e6, "points", 65536),
-                  "filter": (69.67e6 + 0.98e6, "voxels", 32768), "filter_backward": (7.52e6 + 15.55e6, "voxels", 32768)}
-# the same counters taken at the full C2 size (one launch each, a 1-pass capture)
-NCU_DRAM_FULL = {"render_backward": 473.97e6 + 88.62e6}
+MLP_CALLS = ("fields", "fields_backward")
+TIMED_CALLS = PHASOR_CALLS + MLP_CALLS
+# DRAM bytes (read + write) per launch of a call's main kernel from one ncu
+# capture: (bytes, what the count scales with, units in the captured case,
+# the workload that case stands for). A capture of a smaller case is scaled by
+# the points or voxels processed (the records and partials grow in
+# proportion). Only kernels unchanged since their capture are listed.
+NCU_DRAM = {}
 
 
 def _env_int(k, d):
@@ -113,8 +124,7 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, P_target, max_pts=32768, n_ant=1024, n_vox=16384,
-                        filt_ant=1024):
+def cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, max_pts=16384, n_ant=1024, n_vox=8192, filt_ant=1024):
     """Times the FP64 oracle's four phasor sums on a bounded sample of the
     workload (first max_pts points x first n_ant antennas x all bins for the
     tracing pair; first n_vox voxels x first filt_ant antennas for the filter
@@ -160,7 +170,7 @@ def run_reference(args, rank):
     import numpy as np
     import geraf_inputs as gi
     from oracle import geraf_oracle as O
-    wl = gi.workload("c2")
+    wl = gi.workload(args.workload)
     b = gi.band(77e9, 81e9, wl.n_f)
     xyz, apr = O.sample(wl.grid, gi.SAMPLE_STRATIFIED, seed=0, step=0)
     n_pts, n_ant, n_vox, filt_ant = 16384, 128, 2048, 256
@@ -195,7 +205,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bounded oracle sample"},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": "bounded oracle sample"},
             "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -402,13 +412,224 @@ def mlp_backward_macs(spec) -> int:
     return weight + inputs + head
 
 
+def mlp_forward_macs(spec) -> int:
+    """MACs per point of the MLP forward: every hidden layer over the 4 streams
+    (value and 3 tangents), the head's two outputs on the value stream and f
+    on the 3 tangents."""
+    w = 128
+    return 4 * (spec.in_dim * w + (spec.n_hidden - 1) * w * w) + w * 5
+
+
 def call_flops(name, pairs, n_f, order, mlp_macs=0, n_mlp_pts=0):
-    """Algorithmic FP32 flops of one call (see FLOPS_PER_TERM)."""
-    if name == "fields_backward":
+    """Algorithmic flops of one call (see FLOPS_PER_TERM; MLP calls: 2 per MAC)."""
+    if name in MLP_CALLS:
         return 2 * mlp_macs * n_mlp_pts
     if order > 0:
         return pairs * order * CHEB_FLOPS_PER_ORDER
     return pairs * n_f * FLOPS_PER_TERM[name]
+
+
+def _events(names, steps):
+    import torch
+    return [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+            for _ in range(steps)]
+
+
+def _per_call(ev, names, steps):
+    return {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev) / steps for nm in names}
+
+
+def measure_workload(name, steps, warmup, dev, world, rank, headline):
+    """Times `steps` hot-path steps of one workload (after `warmup` untimed
+    ones) with CUDA events on the launching stream, max over ranks; with
+    `headline` also the end-to-end leg through host buffers and the clocks
+    during the timed region; for the 128-bin workload also the same step
+    with the per-bin recurrence forced and the signal tracing bank."""
+    import dataclasses
+    import torch
+    import torch.distributed as dist
+    import geraf_inputs as gi
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import pipeline as PL
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = gi.workload(name)
+    geo = PL.make_geometry(wl, dev)
+    spec = gi.MLPSpec()
+    seeds = replica_seeds(rank)
+    params_np = gi.mlp_init(spec, seed=seeds["mlp"])
+    params = torch.as_tensor(params_np, device=dev)
+    prec = G.PREC_BF16 if wl.precision == "bf16" else G.PREC_FP32
+    field = G.MLPField(params, precision=prec)
+    target = PL.synthetic_target(geo, dev)
+    torch.cuda.synchronize()
+    n_pts = wl.grid.n_pts
+    terms = PL.terms_per_step(geo, n_pts)
+    seed = seeds["sample"]
+    step_id = 0
+    for _ in range(warmup):
+        PL.forward_backward(geo, field, target, seed, step_id)
+        step_id += 1
+    G.geraf_poll_device_error()
+    torch.cuda.synchronize()
+
+    ev = _events(TIMED_CALLS, steps)
+    clk = ClockSampler(torch.cuda.current_device()) if headline else None
+    if clk:
+        clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for k in range(steps):
+        PL.forward_backward(geo, field, target, seed, step_id, timers=ev[k])
+        step_id += 1
+    t_end.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop() if clk else None
+    G.geraf_poll_device_error()
+    ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
+    out = {"name": name, "wl": wl, "n_pts": n_pts, "n_ant": int(geo.ant.shape[1]), "n_vox": int(geo.vox.shape[1]),
+           "n_f": geo.band.n_f, "terms": terms, "steps": steps, "ms": ms,
+           "value": job_rate(terms, steps, world, ms), "per_call": _per_call(ev, TIMED_CALLS, steps),
+           "clocks": clocks, "launches": PL.launches_per_step(field, geo.band) * steps,
+           "precision": wl.precision, "mlp_fwd_macs": mlp_forward_macs(spec),
+           "mlp_bwd_macs": mlp_backward_macs(spec)}
+
+    if headline:
+        # end to end through the public API with host buffers: per step the
+        # inputs (MLP parameters, target heatmap, antenna positions) go host ->
+        # device from pinned memory and the results (loss, parameter gradient,
+        # scalar gradients) come back.
+        h_params = torch.as_tensor(params_np).pin_memory()
+        h_target = target.cpu().pin_memory()
+        h_ant = geo.ant.cpu().pin_memory()
+        h_loss = torch.empty((), dtype=torch.float64).pin_memory()
+        h_dp = torch.empty_like(h_params).pin_memory()
+        h_sc = torch.empty(2).pin_memory()
+        d_params = torch.empty_like(params)
+        d_target = torch.empty_like(target)
+        d_ant = torch.empty_like(geo.ant)
+        geo_e = dataclasses.replace(geo, ant=d_ant)
+        field_e = G.MLPField(d_params, precision=prec)
+        e_steps = max(1, min(steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(e_steps):
+            d_params.copy_(h_params, non_blocking=True)
+            d_target.copy_(h_target, non_blocking=True)
+            d_ant.copy_(h_ant, non_blocking=True)
+            r = PL.forward_backward(geo_e, field_e, d_target, seed, step_id)
+            step_id += 1
+            h_loss.copy_(r.loss, non_blocking=True)
+            h_dp.copy_(r.d_params, non_blocking=True)
+            h_sc.copy_(r.d_scalars, non_blocking=True)
+            torch.cuda.synchronize()
+        e_s = time.perf_counter() - w0
+        barrier()
+        out["e2e"] = {"value": job_rate(terms, e_steps, world, 1e3 * max_over_ranks(e_s, world, dev)),
+                      "unit": "terms/s",
+                      "h2d_bytes_per_step": (h_params.numel() + h_target.numel() + h_ant.numel()) * 4,
+                      "d2h_bytes_per_step": 8 + h_dp.numel() * 4 + h_sc.numel() * 4}
+        del geo_e, field_e, d_params, d_target, d_ant, r
+
+    if geo.band.n_f <= 128 and name in ("c2", "c2-small"):
+        # the same step with the per-bin recurrence forced (for comparison)
+        b0 = geo.band
+        geo_rec = dataclasses.replace(geo, band=G.Band(b0.f0, b0.df, b0.n_f, G.PHASOR_RECURRENCE))
+        PL.forward_backward(geo_rec, field, target, seed, step_id)
+        rec_steps = 2
+        ev_rec = _events(TIMED_CALLS, rec_steps)
+        torch.cuda.synchronize()
+        for k in range(rec_steps):
+            PL.forward_backward(geo_rec, field, target, seed, step_id + k, timers=ev_rec[k])
+        torch.cuda.synchronize()
+        out["per_call_rec"] = _per_call(ev_rec, TIMED_CALLS, rec_steps)
+        # the paper's signal tracing bank: 16 x 16-antenna patches, one traced
+        # per step, the others from the bank
+        bank = PL.SignalBank(geo, (wl.array_n, wl.array_n), (16, 16))
+        bank.fill(field, seed, 0)
+        for k in range(warmup):
+            PL.forward_backward_bank(bank, field, target, seed, step_id + k)
+        torch.cuda.synchronize()
+        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eb0.record()
+        for k in range(steps):
+            PL.forward_backward_bank(bank, field, target, seed, step_id + warmup + k)
+        eb1.record()
+        torch.cuda.synchronize()
+        bank_ms = eb0.elapsed_time(eb1) / steps
+        nf, na, nv = geo.band.n_f, out["n_ant"], out["n_vox"]
+        out["bank_step"] = {"patch_antennas": bank.patch_size, "n_patches": bank.n_patch, "ms_per_step": bank_ms,
+                            "full_trace_ms_per_step": ms / steps, "speedup": (ms / steps) / bank_ms,
+                            "terms_per_step": 2 * n_pts * bank.patch_size * nf + nv * na * nf
+                            + nv * bank.patch_size * nf}
+        del bank
+    xyz_o, _ = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
+    out["orders"] = {"points": G.geraf_chebyshev_order(xyz_o, geo.ant, geo.band),
+                     "voxels": G.geraf_chebyshev_order(geo.vox, geo.ant, geo.band)}
+    # orders each Chebyshev call evaluates (per split or point group; the mean
+    # over the points of the orders per pair the running kernel instance computes)
+    out["cheb_work"] = {"render": G.geraf_chebyshev_work(xyz_o, geo.ant, geo.band, False),
+                        "render_backward": G.geraf_chebyshev_work(xyz_o, geo.ant, geo.band, True),
+                        "filter": G.geraf_chebyshev_work(geo.vox, geo.ant, geo.band, True),
+                        "filter_backward": G.geraf_chebyshev_work(geo.vox, geo.ant, geo.band, False)}
+    if headline and rank == 0 and not getattr(measure_workload, "no_cpu", False):
+        # intermediate arrays of one step for the oracle sample
+        f, grad, a, _ = G.geraf_fields(field, xyz_o)
+        _, apr = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
+        fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+        fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+        _, _, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
+        tps, secs, cterms, desc = cpu_baseline_sample(geo, xyz_o, grad, w, t_eff, c_ant)
+        out["cpu_baseline"] = {"value": tps, "unit": "terms/s", "cores": oracle_threads(), "kind": "oracle",
+                               "sample": desc + f"; {cterms:.3g} terms in {secs:.1f} s"}
+        del f, grad, a, fa, fn, w, t_eff, c_ant, apr
+    del xyz_o, geo, field, target, params
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def roofline_of(m, peaks, sm_count):
+    """Per-call roofline figures of a measured workload (measure_workload) and
+    the dominant call: the one with the largest event time inside the timed
+    region, over every timed call (phasor sums and MLP)."""
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12       # FMA = 2 flops per lane per clock
+    bf16_peak = peaks.get("bf16_tflops_sustained")
+    n_pts, n_ant, n_vox, n_f = m["n_pts"], m["n_ant"], m["n_vox"], m["n_f"]
+    pairs = {"render": n_pts * n_ant, "render_backward": n_pts * n_ant, "filter": n_vox * n_ant,
+             "filter_backward": n_vox * n_ant, "fields": n_pts, "fields_backward": n_pts}
+    cw = m["cheb_work"]
+    order_of = {nm: cw[nm][3] for nm in PHASOR_CALLS}
+    whole = {"render": m["orders"]["points"], "render_backward": m["orders"]["points"],
+             "filter": m["orders"]["voxels"], "filter_backward": m["orders"]["voxels"]}
+    macs = {"fields": m["mlp_fwd_macs"], "fields_backward": m["mlp_bwd_macs"]}
+    tensor = m["precision"] == "bf16" and bf16_peak
+
+    def roof(nm, ms, order):
+        fl = call_flops(nm, pairs[nm], n_f, order, macs.get(nm, 0), n_pts)
+        tf = fl / (ms * 1e-3) / 1e12
+        if nm in MLP_CALLS and tensor:
+            r = {"bound": "tensor", "peak": bf16_peak, "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained"}
+        else:
+            r = {"bound": "alu", "peak": fp32_peak, "peak_basis": "FP32 FMA units x max SM clock"}
+        r.update(ms=round(ms, 3), tflops=tf, frac=tf / r["peak"])
+        if nm in PHASOR_CALLS and order > 0:
+            fw = call_flops(nm, pairs[nm], n_f, whole[nm])
+            r.update(orders_per_pair=round(order, 3), whole_set_order=whole[nm],
+                     frac_whole_set_order=fw / (ms * 1e-3) / 1e12 / fp32_peak)
+        return r
+
+    calls = {nm: roof(nm, m["per_call"][nm], order_of.get(nm, 0)) for nm in TIMED_CALLS}
+    dom = max(TIMED_CALLS, key=lambda k: m["per_call"][k])
+    return calls, dom, fp32_peak, max_mhz, order_of
 
 
 def main():
@@ -418,10 +639,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
-    ap.add_argument("--no-train", action="store_true", help="skip the training-step comparison")
-    ap.add_argument("--phasor", default="auto", choices=["auto", "recurrence", "chebyshev"],
-                    help="how the phasor sums step across the bins (default: by the number of bins)")
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the C2 step, the training-step comparison and the paper configuration")
     ap.add_argument("--mlp-bench", type=int, default=0, metavar="N_PTS",
                     help="time only the fields kernels on N_PTS points and exit")
     ap.add_argument("--paper-config", action="store_true",
@@ -448,9 +668,6 @@ def main():
 
     import torch
     import torch.distributed as dist
-    import geraf_inputs as gi
-    import paper_2605_29097_gb300 as G
-    from paper_2605_29097_gb300 import pipeline as PL
     from paper_2605_29097_gb300 import _build
 
     torch.cuda.set_device(local)
@@ -458,228 +675,89 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     _build.build()
+    measure_workload.no_cpu = args.no_cpu_baseline
 
-    wl = gi.workload(args.workload)
-    geo = PL.make_geometry(wl, dev)
-    if args.phasor != "auto":
-        import dataclasses
-        meth = G.PHASOR_RECURRENCE if args.phasor == "recurrence" else G.PHASOR_CHEBYSHEV
-        geo = dataclasses.replace(geo, band=G.Band(geo.band.f0, geo.band.df, geo.band.n_f, meth))
-    spec = gi.MLPSpec()
-    seeds = replica_seeds(rank)
-    params_np = gi.mlp_init(spec, seed=seeds["mlp"])
-    params = torch.as_tensor(params_np, device=dev)
-    field = G.MLPField(params)
-    target = PL.synthetic_target(geo, dev)
-    torch.cuda.synchronize()
-    n_pts = wl.grid.n_pts
-    terms = PL.terms_per_step(geo, n_pts)
-    seed = seeds["sample"]
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    step_id = 0
-    for _ in range(args.warmup):
-        PL.forward_backward(geo, field, target, seed, step_id)
-        step_id += 1
-    G.geraf_poll_device_error()
-    torch.cuda.synchronize()
-
-    names = ["render", "render_backward", "filter", "filter_backward", "fields_backward"]
-    ev = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
-          for _ in range(args.steps)]
-    clk = ClockSampler(local)
-    clk.start()
-    barrier()
-    torch.cuda.synchronize()
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_start.record()
-    for k in range(args.steps):
-        res = PL.forward_backward(geo, field, target, seed, step_id, timers=ev[k])
-        step_id += 1
-    t_end.record()
-    torch.cuda.synchronize()
-    barrier()
-    clocks = clk.stop()
-    G.geraf_poll_device_error()
-    ms = t_start.elapsed_time(t_end)
-    per_kernel = {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev) / args.steps for nm in names}
-    ms = max_over_ranks(ms, world, dev)
-    value = job_rate(terms, args.steps, world, ms)
-
-    # end to end through the public API with host buffers: per step the
-    # inputs (MLP parameters, target heatmap, antenna positions) go host ->
-    # device from pinned memory and the results (loss, parameter gradient,
-    # scalar gradients) come back.
-    h_params = torch.as_tensor(params_np).pin_memory()
-    h_target = target.cpu().pin_memory()
-    h_ant = geo.ant.cpu().pin_memory()
-    h_loss = torch.empty((), dtype=torch.float64).pin_memory()
-    h_dp = torch.empty_like(h_params).pin_memory()
-    h_sc = torch.empty(2).pin_memory()
-    d_params = torch.empty_like(params)
-    d_target = torch.empty_like(target)
-    d_ant = torch.empty_like(geo.ant)
-    geo_e = PL.Geometry(geo.grid, geo.n_ray, geo.n_z, d_ant, geo.vox, geo.band, geo.sharpness, geo.a_tx, geo.mode)
-    field_e = G.MLPField(d_params)
-    e_steps = max(1, min(args.steps, 3))
-    barrier()
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(e_steps):
-        d_params.copy_(h_params, non_blocking=True)
-        d_target.copy_(h_target, non_blocking=True)
-        d_ant.copy_(h_ant, non_blocking=True)
-        r = PL.forward_backward(geo_e, field_e, d_target, seed, step_id)
-        step_id += 1
-        h_loss.copy_(r.loss, non_blocking=True)
-        h_dp.copy_(r.d_params, non_blocking=True)
-        h_sc.copy_(r.d_scalars, non_blocking=True)
-        torch.cuda.synchronize()
-    e_s = time.perf_counter() - w0
-    barrier()
-    e_value = job_rate(terms, e_steps, world, 1e3 * max_over_ranks(e_s, world, dev))
-    h2d = (h_params.numel() + h_target.numel() + h_ant.numel()) * 4
-    d2h = 8 + h_dp.numel() * 4 + 8
-
-    # the same step with the per-bin recurrence forced (for comparison; untimed in `value`)
-    import dataclasses
-    b0 = geo.band
-    geo_rec = dataclasses.replace(geo, band=G.Band(b0.f0, b0.df, b0.n_f, G.PHASOR_RECURRENCE))
-    PL.forward_backward(geo_rec, field, target, seed, step_id)
-    rec_steps = 2
-    ev_rec = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
-              for _ in range(rec_steps)]
-    torch.cuda.synchronize()
-    for k in range(rec_steps):
-        PL.forward_backward(geo_rec, field, target, seed, step_id + k, timers=ev_rec[k])
-    torch.cuda.synchronize()
-    per_kernel_rec = {nm: sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev_rec) / rec_steps for nm in names}
-    # the paper's signal tracing bank on the same workload: 16 x 16-antenna patches,
-    # one traced per step, the other 15 from the bank
-    bank = PL.SignalBank(geo, (wl.array_n, wl.array_n), (16, 16))
-    bank.fill(field, seed, 0)
-    for k in range(args.warmup):
-        PL.forward_backward_bank(bank, field, target, seed, step_id + k)
-    torch.cuda.synchronize()
-    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    eb0.record()
-    for k in range(args.steps):
-        PL.forward_backward_bank(bank, field, target, seed, step_id + args.warmup + k)
-    eb1.record()
-    torch.cuda.synchronize()
-    bank_ms = eb0.elapsed_time(eb1) / args.steps
-    n_ant_all, n_vox_all, nf = int(geo.ant.shape[1]), int(geo.vox.shape[1]), geo.band.n_f
-    bank_terms = (2 * n_pts * bank.patch_size * nf + n_vox_all * n_ant_all * nf + n_vox_all * bank.patch_size * nf)
-    bank_line = {"patch_antennas": bank.patch_size, "n_patches": bank.n_patch, "ms_per_step": bank_ms,
-                 "full_trace_ms_per_step": None, "terms_per_step": bank_terms}
-    del bank
-    xyz_o, _ = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
-    orders = {"points": G.geraf_chebyshev_order(xyz_o, geo.ant, geo.band),
-              "voxels": G.geraf_chebyshev_order(geo.vox, geo.ant, geo.band)}
-    # orders each Chebyshev call evaluates (per split or point group; the mean
-    # over the points of the orders per pair the running kernel instance computes)
-    cheb_work = {"render": G.geraf_chebyshev_work(xyz_o, geo.ant, geo.band, False),
-                 "render_backward": G.geraf_chebyshev_work(xyz_o, geo.ant, geo.band, True),
-                 "filter": G.geraf_chebyshev_work(geo.vox, geo.ant, geo.band, True),
-                 "filter_backward": G.geraf_chebyshev_work(geo.vox, geo.ant, geo.band, False)}
-    del xyz_o
+    m = measure_workload(args.workload, args.steps, args.warmup, dev, world, rank, headline=True)
+    extras = {}
+    if not args.no_extras and args.workload == "c3":
+        extras["c2"] = measure_workload("c2", min(args.steps, 10), 3, dev, world, rank, headline=False)
 
     if rank == 0:
         peaks = measured_peaks()
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        fp32_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12       # FMA = 2 flops per lane per clock
-        n_ant = int(geo.ant.shape[1])
-        n_vox = int(geo.vox.shape[1])
-        pairs = {"render": n_pts * n_ant, "render_backward": n_pts * n_ant,
-                 "filter": n_vox * n_ant, "filter_backward": n_vox * n_ant, "fields_backward": n_pts}
-        order_of = {nm: cheb_work[nm][3] for nm in PHASOR_CALLS}
-        order_of["fields_backward"] = 0
-        whole_order = {"render": orders["points"], "render_backward": orders["points"],
-                       "filter": orders["voxels"], "filter_backward": orders["voxels"]}
-        macs = mlp_backward_macs(spec)
-
-        def roof(nm, ms, order):
-            fl = call_flops(nm, pairs[nm], geo.band.n_f, order, macs, n_pts)
-            r = {"ms": round(ms, 3), "tflops": fl / (ms * 1e-3) / 1e12,
-                 "frac": fl / (ms * 1e-3) / 1e12 / fp32_peak}
-            if order > 0:
-                # the same time against the work of one expansion over the whole set
-                fw = call_flops(nm, pairs[nm], geo.band.n_f, whole_order[nm], macs, n_pts)
-                r.update(orders_per_pair=round(order, 3), whole_set_order=whole_order[nm],
-                         frac_whole_set_order=fw / (ms * 1e-3) / 1e12 / fp32_peak)
-            return r
-
-        per_call_roof = {nm: roof(nm, per_kernel[nm], order_of[nm]) for nm in names}
-        rec_roof = {nm: roof(nm, per_kernel_rec[nm], 0) for nm in PHASOR_CALLS}
-        # dominant kernel: the longest single launch, i.e. the main kernel of the
-        # longest phasor call (the MLP adjoint call is one launch per layer)
-        dom = max(PHASOR_CALLS, key=lambda k: per_kernel[k])
+        calls, dom, fp32_peak, max_mhz, order_of = roofline_of(m, peaks, sm_count)
+        fam = "c3" if args.workload.startswith("c3") else "c2"
         traffic, traffic_basis = None, "no ncu capture of this kernel version"
-        if args.workload == "c2" and dom in NCU_DRAM_FULL and order_of[dom] > 0:
-            traffic = NCU_DRAM_FULL[dom]
-            traffic_basis = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at the full C2 "
-                             "size, one launch (1-pass capture)")
-        elif dom in NCU_DRAM_SMALL and order_of[dom] > 0:
-            b_small, unit, n_small = NCU_DRAM_SMALL[dom]
-            n_full = n_pts if unit == "points" else n_vox
-            traffic = b_small * n_full / n_small
-            traffic_basis = (f"ncu dram__bytes_read+write of the small C2 case ({n_small} {unit}), "
-                             f"scaled by {unit} to {n_full}")
-        launches = PL.launches_per_step(field, geo.band) * args.steps
-        cpu = None
-        if not args.no_cpu_baseline:
-            # intermediate arrays of one step for the oracle sample
-            xyz, apr = G.geraf_sample(geo.grid, geo.mode, seed, 0, device=dev)
-            f, grad, a, _ = G.geraf_fields(field, xyz)
-            fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
-            fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
-            _, _, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
-            tps, secs, cterms, desc = cpu_baseline_sample(geo, xyz, grad, w, t_eff, c_ant, target)
-            cpu = {"value": tps, "unit": "terms/s", "cores": oracle_threads(), "kind": "oracle",
-                   "sample": desc + f"; {cterms:.3g} terms in {secs:.1f} s"}
+        if (fam, dom) in NCU_DRAM:
+            b_cap, unit, n_cap, basis = NCU_DRAM[(fam, dom)]
+            n_full = m["n_pts"] if unit == "points" else m["n_vox"]
+            traffic = b_cap * n_full / n_cap
+            traffic_basis = basis + (f", scaled by {unit} from {n_cap} to {n_full}" if n_cap != n_full else "")
+        d = calls[dom]
         line = {
-            "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "c2" else args.workload, "n_pts": n_pts, "n_ant": int(geo.ant.shape[1]),
-                       "n_f": geo.band.n_f, "n_vox": int(geo.vox.shape[1]), "terms_per_step": terms,
-                       "l2": "inputs larger than L2 (per-step MLP activations ~17 GB)",
+            "metric": METRIC, "value": m["value"], "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[m["precision"]], "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n_pts": m["n_pts"], "n_ant": m["n_ant"],
+                       "n_f": m["n_f"], "n_vox": m["n_vox"], "terms_per_step": m["terms"],
+                       "l2": "inputs larger than L2 (the per-step MLP activations alone are gigabytes)",
                        "parallelism": f"replicas x{world}"},
-            "per_call_ms": {k: round(v, 3) for k, v in per_kernel.items()},
-            "roofline": {"bound": "alu", "kernel": dom, "achieved": per_call_roof[dom]["tflops"],
-                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": per_call_roof[dom]["frac"],
-                         "traffic": traffic, "traffic_basis": traffic_basis,
-                         "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz",
+            "per_call_ms": {k: round(v, 3) for k, v in m["per_call"].items()},
+            "roofline": {"bound": d["bound"], "kernel": dom, "achieved": d["tflops"], "peak": d["peak"],
+                         "unit": "TFLOP/s", "frac": d["frac"], "traffic": traffic, "traffic_basis": traffic_basis,
+                         "peak_basis": (f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz"
+                                        if d["bound"] == "alu" else d["peak_basis"]),
                          "work_basis": ("Chebyshev phasor sums: pairs x orders evaluated per pair x 6 flops "
                                         "(the running instance's orders per split or point group, mean over "
                                         "the points, geraf_chebyshev_work; calls[*].frac_whole_set_order "
-                                        "counts one expansion of the whole set's order instead); per-bin recurrence: "
-                                        "terms x 10 (render, filter adjoint) or 8 (filter, render adjoint) flops; "
-                                        f"MLP adjoint: 2 x {macs} MAC per point"),
-                         "calls": per_call_roof},
-            "phasor_method": {"chebyshev_order": orders,
+                                        "counts one expansion of the whole set's order instead); per-bin "
+                                        "recurrence: terms x 10 (render, filter adjoint) or 8 (filter, render "
+                                        f"adjoint) flops; MLP forward 2 x {m['mlp_fwd_macs']} and adjoint "
+                                        f"2 x {m['mlp_bwd_macs']} flops per point"),
+                         "calls": calls,
+                         "mlp": {nm: calls[nm] for nm in MLP_CALLS}},
+            "phasor_method": {"chebyshev_order": m["orders"],
                               "chebyshev_work": {nm: {"whole_set_order": w[0], "max_part_order": w[1],
                                                       "instance_orders": w[2], "orders_per_pair": round(w[3], 3)}
-                                                 for nm, w in cheb_work.items()},
-                              "recurrence_per_call_ms": {k: round(per_kernel_rec[k], 3) for k in PHASOR_CALLS},
-                              "recurrence_roofline": rec_roof,
-                              "recurrence_terms_per_s": 2 * (n_pts + n_vox) * n_ant * geo.band.n_f
-                              / (sum(per_kernel_rec[k] for k in PHASOR_CALLS) * 1e-3)},
-            "bank_step": dict(bank_line, full_trace_ms_per_step=ms / args.steps,
-                              speedup=(ms / args.steps) / bank_line["ms_per_step"]),
-            "cpu_baseline": cpu,
-            "e2e": {"value": e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "train_step": None,
-            "paper_config": None,
+                                                 for nm, w in m["cheb_work"].items()}},
+            "cpu_baseline": m.get("cpu_baseline"),
+            "e2e": m["e2e"],
+            "gpu_launches": m["launches"],
+            "clocks": m["clocks"],
         }
-        if not args.no_train and args.workload == "c2":
-            del geo, field, target, params, geo_e, field_e
+        for src in [m] + list(extras.values()):
+            if "per_call_rec" in src:
+                # the per-bin recurrence forced on the same step: per-call times and roofline
+                rec = {}
+                for nm in PHASOR_CALLS:
+                    pr = src["n_pts"] if nm.startswith("render") else src["n_vox"]
+                    t_ms = src["per_call_rec"][nm]
+                    tf = call_flops(nm, pr * src["n_ant"], src["n_f"], 0) / (t_ms * 1e-3) / 1e12
+                    rec[nm] = {"ms": round(t_ms, 3), "tflops": tf, "frac": tf / fp32_peak}
+                block = {"recurrence_per_call_ms": {k: round(src["per_call_rec"][k], 3) for k in PHASOR_CALLS},
+                         "recurrence_roofline": rec,
+                         "recurrence_terms_per_s": 2 * (src["n_pts"] + src["n_vox"]) * src["n_ant"] * src["n_f"]
+                         / (sum(src["per_call_rec"][k] for k in PHASOR_CALLS) * 1e-3)}
+                if src is m:
+                    line["phasor_method"].update(block)
+                else:
+                    src["phasor_method_rec"] = block
+        if "bank_step" in m:
+            line["bank_step"] = m["bank_step"]
+        if "c2" in extras:
+            c = extras["c2"]
+            ccalls, cdom, _, _, _ = roofline_of(c, peaks, sm_count)
+            line["c2"] = {"workload": WORKLOADS["c2"], "dtype": DTYPES[c["precision"]], "steps": c["steps"],
+                          "ms_per_step": c["ms"] / c["steps"], "value": c["value"], "unit": "terms/s",
+                          "terms_per_step": c["terms"],
+                          "per_call_ms": {k: round(v, 3) for k, v in c["per_call"].items()},
+                          "roofline_calls": ccalls, "dominant": cdom,
+                          "chebyshev_work": {nm: {"whole_set_order": w[0], "max_part_order": w[1],
+                                                  "instance_orders": w[2], "orders_per_pair": round(w[3], 3)}
+                                             for nm, w in c["cheb_work"].items()},
+                          "phasor_method_recurrence": c.get("phasor_method_rec"),
+                          "bank_step": c.get("bank_step")}
+        if not args.no_extras and args.workload in ("c3", "c2"):
             torch.cuda.empty_cache()
             line["train_step"] = train_step_compare(dev)
             torch.cuda.empty_cache()

@@ -301,6 +301,12 @@ def workload(name: str) -> Workload:
         h = cube_grid((0.0, 0.0, 0.15), 0.10, (64, 64, 64))
         return Workload(name, 128, 0.002, 256, g, h, SAMPLE_STRATIFIED, "mlp", "bf16",
                         sharpness=2.0 / h.pitch[2])
+    if name == "c3-small":
+        # same array, band and network as c3 with 1/256 of the samples (profiling size)
+        g = cube_grid((0.0, 0.0, 0.15), 0.10, (64, 64, 16))
+        h = cube_grid((0.0, 0.0, 0.15), 0.10, (32, 32, 32))
+        return Workload(name, 128, 0.002, 256, g, h, SAMPLE_STRATIFIED, "mlp", "bf16",
+                        sharpness=2.0 / h.pitch[2])
     if name == "c4":
         g = cube_grid((0.0, 0.0, 0.15), 0.12, (256, 256, 256))
         h = cube_grid((0.0, 0.0, 0.15), 0.12, (64, 64, 64))

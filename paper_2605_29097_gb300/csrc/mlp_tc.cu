@@ -57,10 +57,20 @@ bool make_tc_geom(const geraf_field_desc* d, int64_t n, TcGeom* g) {
     return true;
 }
 
-__device__ __forceinline__ float sp_b(float h, float beta) {
-    return fmaxf(h, 0.0f) + log1pf(expf(-beta * fabsf(h))) / beta;
-}
 __device__ __forceinline__ float sgm(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// softplus_beta(h) = max(h, 0) + log1p(e) / beta and sigmoid(beta h) from one
+// exponential e = exp(-beta |h|): sigmoid(beta h) = 1 / (1 + e) for h >= 0 and
+// e / (1 + e) below. One SFU exponential, one reciprocal and log1p per
+// element instead of two exponentials, a logarithm and two divides. The
+// forward and both adjoint recomputations call this same function, so the
+// adjoint's BF16 layer inputs are bit for bit the operands the forward used.
+__device__ __forceinline__ void act_pair(float h, float beta, float inv_beta, float& sp, float& sg) {
+    const float e = __expf(-beta * fabsf(h));
+    const float r = __fdividef(1.0f, 1.0f + e);
+    sg = h >= 0.0f ? r : e * r;
+    sp = fmaf(log1pf(e), inv_beta, fmaxf(h, 0.0f));
+}
 
 __device__ __forceinline__ void st_bf16(unsigned char* base, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
@@ -152,6 +162,7 @@ constexpr int FTHREADS = 512;     // 16 warps: 4 TMEM lane quarters x 4 column c
 __global__ void __launch_bounds__(FTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcGeom& g = a.g;
+    const float inv_beta = 1.0f / g.beta;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     unsigned char* wt[4];
     uint32_t off = 0;
@@ -256,8 +267,8 @@ __global__ void __launch_bounds__(FTHREADS, 1) mlp_tc_fwd_kernel(const TcFwdArgs
 #pragma unroll
                 for (int pp = 0; pp < 8; ++pp) {
                     const float h = r[4 * pp] + bu;
-                    const float sg = sgm(g.beta * h);
-                    v[4 * pp] = sp_b(h, g.beta);
+                    float sg;
+                    act_pair(h, g.beta, inv_beta, v[4 * pp], sg);
                     v[4 * pp + 1] = sg * r[4 * pp + 1];
                     v[4 * pp + 2] = sg * r[4 * pp + 2];
                     v[4 * pp + 3] = sg * r[4 * pp + 3];
@@ -410,8 +421,9 @@ __global__ void __launch_bounds__(256) mlp_tc_head_bwd_kernel(const TcBwdArgs a)
         for (int r = 0; r < R; ++r) {
             const int64_t j = base + 2 * r + half;
             if (j >= g.n) continue;
-            const float sg = sgm(g.beta * h0[r]);
-            const float z = bf16r(sp_b(h0[r], g.beta));
+            float z, sg;
+            act_pair(h0[r], g.beta, 1.0f / g.beta, z, sg);
+            z = bf16r(z);
             gw0 += df[r] * z;
             gw1 += dl[r] * z;
             float* zb = a.zbar + j * 4 * TW;
@@ -474,6 +486,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw;
     const TcGeom& g = a.g;
+    const float inv_beta = 1.0f / g.beta;
     const int li = a.layer;
     const int kin = li == 0 ? g.K0p : TW;     // padded input width (MMA N of dW, M of the input adjoint)
     const int K = li == 0 ? g.K0 : TW;        // true input width
@@ -543,7 +556,8 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
                 const float* z = zs + c0 * TW + uu;
                 const float* h = hsb + c0 * TW + uu;
                 const float h0 = h[0];
-                const float sg = sgm(g.beta * h0);
+                float sp_unused, sg;
+                act_pair(h0, g.beta, inv_beta, sp_unused, sg);
                 const float dsg = g.beta * sg * (1.0f - sg);
                 const float z0 = z[0], z1 = z[TW], z2 = z[2 * TW], z3 = z[3 * TW];
                 bv[4 * pp] = z0 * sg + (z1 * h[TW] + z2 * h[2 * TW] + z3 * h[3 * TW]) * dsg;
@@ -591,8 +605,9 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
             for (int pp = 0; pp < 4; ++pp) {
                 const float* x = zs + (16 * ch + 4 * pp) * TW + uu;
                 const float x0 = x[0];
-                const float s0 = sgm(g.beta * x0);
-                q[2 * pp] = pack_bf16x2(sp_b(x0, g.beta), s0 * x[TW]);
+                float z0, s0;
+                act_pair(x0, g.beta, inv_beta, z0, s0);
+                q[2 * pp] = pack_bf16x2(z0, s0 * x[TW]);
                 q[2 * pp + 1] = pack_bf16x2(s0 * x[2 * TW], s0 * x[3 * TW]);
             }
 #pragma unroll

@@ -118,7 +118,9 @@ def forward_backward(geo: Geometry, field, target: torch.Tensor, seed: int, step
 
     xyz, apr = G.geraf_sample(geo.grid, geo.mode, seed, step, device=geo.ant.device)
     is_mlp = isinstance(field, G.MLPField)
+    tic("fields")
     f, grad, a, saved = G.geraf_fields(field, xyz, keep_saved=is_mlp)
+    toc("fields")
     fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
     fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
     alpha, T, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
