@@ -67,8 +67,10 @@ typedef struct {
  *     recurrence, re-seeded from a sincos every 32 bins;
  *   GERAF_PHASOR_CHEBYSHEV: the bin phase exp(-j 2 pi n df 2r/c) expanded in
  *     Chebyshev polynomials of the range (Jacobi-Anger, terms kept until the
- *     Bessel tail is below 1e-9), each run of consecutive points over its
- *     own range interval, so the work per (point, antenna) pair follows the
+ *     Bessel tail is below 1e-7, under the FP32 rounding of the sums), each
+ *     run of consecutive points against each block of 128 antennas (taken
+ *     in a spatial order of their positions) over its own range interval,
+ *     so the work per (point, antenna) pair follows the
  *     order instead of n_f; when the whole call's order K would exceed 64
  *     the recurrence runs instead (decided on the device;
  *     geraf_chebyshev_order reports the choice, geraf_chebyshev_work the
@@ -331,7 +333,7 @@ geraf_status geraf_masked_loss(const float* P, const float* target, float* histo
  * (band->method honoured): *order = K (2..64) when the Chebyshev form runs,
  * 0 when the recurrence runs (method RECURRENCE, AUTO with n_f < 64, or an
  * order above 64). Runs the same device-side plan as the sums (range bound
- * from the points' bounding box and the antennas, Bessel tail below 1e-9),
+ * from the points' bounding box and the antennas, Bessel tail below 1e-7),
  * then waits for the stream: synchronous. The paper has no counterpart; this
  * reports the cost model of a call. ws: ws == NULL queries *ws_bytes.
  */
@@ -344,15 +346,18 @@ geraf_status geraf_chebyshev_order(const float* xyz, int64_t n, const float* ant
  * points (or voxels) xyz [3][n] against ant_xyz [3][n_ant] over `band`.
  * to_points = 0: the to-bins direction (geraf_render on points,
  * geraf_filter_backward on voxels), which expands each split of consecutive
- * point tiles over its own range interval; to_points = 1: the to-points
- * direction (geraf_filter, geraf_render_backward), which expands each group of
- * consecutive points (at least 2048) over its own interval. Outputs:
+ * point tiles (against each block of 128 antennas in their spatial order,
+ * when the split is large enough) over its own range interval; to_points = 1:
+ * the to-points direction (geraf_filter, geraf_render_backward), which
+ * expands each group of consecutive points (at least 2048) against each
+ * antenna block over its own interval. Outputs:
  * orders[0] = the whole set's order K (0: the recurrence runs; then all
- * outputs are 0), orders[1] = the largest split or group order, orders[2] =
- * the orders compiled into the kernel instance that runs (24, 32 or 64);
+ * outputs are 0), orders[1] = the largest part order, orders[2] = the orders
+ * compiled into the kernel instance that runs (24, 32 or 64);
  * *mean_orders = the orders evaluated per (point, antenna) pair, averaged
- * over the points (the instance's 24 or 32, or for the 64-order instance 32
- * plus the part's own orders beyond 32 in blocks of 8). Runs the same device
+ * over all pairs (in the 24- and 32-order instances each part's order rounded
+ * up to even, at least 8; in the 64-order instance 32 plus the part's own
+ * orders beyond 32 in blocks of 8). Runs the same device
  * plans as the sums, then waits for the stream: synchronous. The paper has no
  * counterpart; this reports the cost model of a call. ws: ws == NULL queries
  * *ws_bytes. GERAF_ERR_INVALID_ARG for n < 1, n >= 2^31, n_ant < 1, a NULL

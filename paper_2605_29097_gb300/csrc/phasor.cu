@@ -122,6 +122,119 @@ __global__ void pack_antennas(const float* __restrict__ ant, const float* __rest
     out[i] = make_float4(ant[k], ant[n_ant + k], ant[2 * n_ant + k], c_ant ? c_ant[k] : 0.0f);
 }
 
+// ------------------------------------------------- spatial order of antennas
+// The Chebyshev kernels expand each part of a call (points x a block of
+// CH_THREADS consecutive antenna records) over the part's own range interval,
+// whose width sets the order. Consecutive antennas in the caller's order need
+// not be close (a row-major array puts a 128-antenna block on one 25 cm line),
+// so the Chebyshev calls pack the antennas in Morton (Z-curve) order of their
+// positions, quantised to 10 bits per axis over the array's bounding box (one
+// scale for all three axes): on a regular planar grid every block of 128
+// records is then a 16 x 8 (or 8 x 16) patch. perm[r] = the antenna held by
+// record r; records past n_ant hold antenna 0 and are never written back.
+// Keys (code << 32 | index) are unique, so the order is deterministic. One CTA,
+// bitonic sort in shared memory up to AO_SMEM_MAX antennas, above that in a
+// global scratch buffer (every pass ends with a block barrier).
+constexpr int AO_THREADS = 1024;
+constexpr int AO_SMEM_MAX = 16384;
+
+__device__ __forceinline__ uint64_t spread3_10(uint32_t v) {
+    uint64_t x = v & 0x3FFu;
+    x = (x | (x << 16)) & 0x30000FFull;
+    x = (x | (x << 8)) & 0x300F00Full;
+    x = (x | (x << 4)) & 0x30C30C3ull;
+    x = (x | (x << 2)) & 0x9249249ull;
+    return x;
+}
+
+__global__ void __launch_bounds__(AO_THREADS) antenna_order_kernel(const float* __restrict__ ant, int n_ant,
+                                                                   int n_pow2, unsigned long long* __restrict__ gbuf,
+                                                                   int* __restrict__ perm, int n_perm) {
+    extern __shared__ unsigned long long sbuf[];
+    __shared__ float red[6][AO_THREADS / 32];
+    unsigned long long* buf = n_pow2 <= AO_SMEM_MAX ? sbuf : gbuf;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = t; i < n_ant; i += AO_THREADS)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float v = ant[d * n_ant + i];
+            mn[d] = fminf(mn[d], v);
+            mx[d] = fmaxf(mx[d], v);
+        }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            red[d][warp] = mn[d];
+            red[3 + d][warp] = mx[d];
+        }
+    __syncthreads();
+    float lo[3], span = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float a = INFINITY, b = -INFINITY;
+        for (int w = 0; w < AO_THREADS / 32; ++w) {
+            a = fminf(a, red[d][w]);
+            b = fmaxf(b, red[3 + d][w]);
+        }
+        lo[d] = a;
+        span = fmaxf(span, b - a);
+    }
+    const float scale = span > 0.0f ? 1023.0f / span : 0.0f;
+    for (int i = t; i < n_pow2; i += AO_THREADS) {
+        unsigned long long key = ~0ull;
+        if (i < n_ant) {
+            uint64_t code = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float q = fminf(fmaxf((ant[d * n_ant + i] - lo[d]) * scale, 0.0f), 1023.0f);
+                code |= spread3_10((uint32_t)q) << d;
+            }
+            key = (code << 32) | (unsigned long long)(uint32_t)i;
+        }
+        buf[i] = key;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n_pow2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < n_pow2; i += AO_THREADS) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = buf[i], b = buf[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        buf[i] = b;
+                        buf[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int r = t; r < n_perm; r += AO_THREADS) perm[r] = r < n_ant ? (int)(uint32_t)(buf[r] & 0xffffffffull) : 0;
+}
+
+size_t antenna_order_smem(int n_pow2) { return n_pow2 <= AO_SMEM_MAX ? (size_t)n_pow2 * 8 : 0; }
+int pow2_at_least(int n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// antenna records (x, y, z, c_ant) in the spatial order perm (records past
+// n_ant hold antenna 0)
+__global__ void pack_antennas_perm(const float* __restrict__ ant, const float* __restrict__ c_ant, int n_ant,
+                                   const int* __restrict__ perm, int n_pad, float4* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    const int k = perm[r];
+    out[r] = make_float4(ant[k], ant[n_ant + k], ant[2 * n_ant + k], c_ant ? c_ant[k] : 0.0f);
+}
+
 // antenna tile rows for the to-points kernels: 16-byte head (x, y, z, c)
 // followed by one float4 (s_re, s_re, s_im, s_im) per bin, zero-padded to
 // 32*G bins, so that one 16-byte load gives the packed pairs (s_re, s_re)
@@ -684,7 +797,7 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
 // double-single phase and one sincos per pair); with r = r_c + dr x, |x| <= 1
 // over a range interval, the Jacobi-Anger expansion
 //   exp(-j a_n x) = sum_k eps_k (-j)^k J_k(a_n) T_k(x),  a_n = 2 pi n (2 df / c) dr,
-// truncated where the Bessel tail falls below 1e-9, turns the bin sums into
+// truncated where the Bessel tail falls below CH_TAIL, turns the bin sums into
 // K Chebyshev moments per antenna (K ~ a_max + 15, about 30 for a 4 GHz sweep
 // over a 15 cm range spread, independent of the number of bins):
 //   to bins:   s(i, n) = sum_k C_k(n) M_k(i),  M_k(i) = sum_j A'_ij T_k(x_ij)
@@ -717,6 +830,11 @@ constexpr int CH_THREADS = 128;
 constexpr int CH_TP = 32;             // points per TMA tile
 constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before it joins the outer sum
 constexpr size_t CH_PARTIAL_BYTES = 256ull << 20;   // bound on the split partials of one call
+constexpr size_t CH_TABLE_BYTES = 1ull << 30;       // bound on the coefficient tables of one call's parts
+// Bessel-tail bound of the expansion: the unit phasor is represented to 1e-7,
+// below the FP32 rounding of the sums themselves (relative L2 2e-7 .. 5e-7
+// against the FP64 oracle on every parity case)
+constexpr double CH_TAIL = 1e-7;
 
 struct ChebPlan {
     float r_c;        // range centre (FP32; the coefficients use this value)
@@ -880,7 +998,7 @@ struct ChebBinsArgs {
 // packed (re, im) form would spend a wasted lane on the recurrence.
 // KC = 8-order groups held in registers: the KC = 3 and KC = 4 instances run
 // when the largest part order is at most 24 or 32, each CTA with its part's
-// order rounded up to even (at least 16) as a compile-time loop bound (one
+// order rounded up to even (at least 8) as a compile-time loop bound (one
 // unrolled tile body per even order); the KC = 8 instance (orders beyond 32
 // guarded by the part's K) otherwise; all are launched and those that do not
 // apply return at once. Each part = (split of points, block of CH_THREADS
@@ -970,7 +1088,7 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
     const int n_my = tile1 - tile0;
     const SplitPlan sp = args.splan[split * args.plan_blocks + (args.plan_blocks > 1 ? blockIdx.x : 0)];
     const int K = sp.K;
-    const int ke = K <= 16 ? 16 : (K + 1) & ~1;              // orders run: K rounded up to even, >= 16
+    const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
     const float r_c = sp.r_c, inv_dr = sp.inv_dr;
     const float4 A4 = args.ant[ia];                          // padded: always readable
     float4 Ah, Al;
@@ -1009,6 +1127,7 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
             bins_tile<kComplexAmp, KM, KM, true>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K, mr, mi);
         } else {
             switch (ke) {
+                GERAF_BINS_CASE(8) GERAF_BINS_CASE(10) GERAF_BINS_CASE(12) GERAF_BINS_CASE(14)
                 GERAF_BINS_CASE(16) GERAF_BINS_CASE(18) GERAF_BINS_CASE(20) GERAF_BINS_CASE(22)
                 GERAF_BINS_CASE(24) GERAF_BINS_CASE(26) GERAF_BINS_CASE(28) GERAF_BINS_CASE(30)
                 default: bins_tile<kComplexAmp, KM, KM, false>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K,
@@ -1075,14 +1194,14 @@ __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, in
     if (threadIdx.x < 6) box[sp * 6 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// One block per part = (split of points sp, block of antennas b), parts in
-// order sp * n_ab + b (n_ab blocks of ant_per_block consecutive antennas; one
-// block of all antennas for the point groups): the part's range interval
-// between the split's box and the block's antennas, its order K (the whole
-// call's rule: Bessel tail <= eps), and its FP32 coefficient table
-// Cs[part][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n) (Bessel values in
-// FP64). kmax collects the largest part order.
-__global__ void split_plan_kernel(const float* __restrict__ box, const float* __restrict__ ant, int n_ant,
+// One block per part = (split or group of points sp, block of antennas b),
+// parts in order sp * n_ab + b (n_ab blocks of ant_per_block consecutive
+// antenna records in the spatial order, or one block of all antennas): the
+// part's range interval between the points' box and the block's antennas,
+// its order K (the whole call's rule: Bessel tail <= eps), and its FP32
+// coefficient table Cs[part][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
+// (Bessel values in FP64). kmax collects the largest part order.
+__global__ void split_plan_kernel(const float* __restrict__ box, const float4* __restrict__ ant, int n_ant,
                                   int n_ab, int ant_per_block, double Kd, int n_f, double eps,
                                   const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
                                   float2* __restrict__ Cs, int* __restrict__ kmax) {
@@ -1097,8 +1216,9 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float* __
     float lo = INFINITY, hi = 0.0f;
     for (int i = i0 + t; i < i1; i += blockDim.x) {
         float dn = 0.0f, df = 0.0f;
+        const float4 A = ant[i];
         for (int d = 0; d < 3; ++d) {
-            const float a = ant[d * n_ant + i];
+            const float a = d == 0 ? A.x : (d == 1 ? A.y : A.z);
             const float e = fmaxf(fmaxf(bx[d] - a, a - bx[3 + d]), 0.0f);
             const float f = fmaxf(fabsf(a - bx[d]), fabsf(bx[3 + d] - a));
             dn += e * e;
@@ -1165,7 +1285,8 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float* __
 }
 
 // sum over the splits of a group of RS splits of sum_k Cs[sp, b(i)][k][n] M_k(sp, i),
-// b(i) the antenna's block of CH_THREADS:
+// i an antenna record, b(i) its block of CH_THREADS records, written to the
+// antenna the record holds:
 // block = (RA antennas, split group); thread = bin, the RA antennas in
 // registers so each table value is loaded once; the per-split sums (FP32, at
 // most 64 terms) are added with Kahan compensation across the group's splits.
@@ -1176,7 +1297,7 @@ static_assert(CH_THREADS % RA == 0, "a reconstruction block stays in one antenna
 __global__ void cheb_reconstruct_split_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
                                               int n_ab, const ChebPlan* __restrict__ gplan,
                                               const SplitPlan* __restrict__ splan, const float2* __restrict__ Cs,
-                                              float2* __restrict__ group_out) {
+                                              const int* __restrict__ perm, float2* __restrict__ group_out) {
     if (!gplan->run_cheb) return;
     const int i0 = blockIdx.x * RA;
     const int b = n_ab > 1 ? i0 / CH_THREADS : 0;   // antenna block of all RA antennas (RA divides CH_THREADS)
@@ -1215,8 +1336,8 @@ __global__ void cheb_reconstruct_split_kernel(const float2* __restrict__ partial
         }
 #pragma unroll
         for (int q = 0; q < RA; ++q)
-            if (i0 + q < n_ant)
-                group_out[((size_t)blockIdx.y * n_ant + i0 + q) * n_f + n] = make_float2(hr[q], hi[q]);
+            if (i0 + q < n_ant)     // record i0 + q holds antenna perm[i0 + q]
+                group_out[((size_t)blockIdx.y * n_ant + perm[i0 + q]) * n_f + n] = make_float2(hr[q], hi[q]);
     }
 }
 
@@ -1275,29 +1396,34 @@ __global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int6
     if (threadIdx.x < 6) box[g * 6 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Antenna rows of the to-points kernels, one set per point group g (the
-// group's own interval and coefficient table C_g,k(n) from split_plan_kernel):
-// row(g, i) = two heads (the antenna's split position; c_ant in the first),
-// then for k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) C_g,k(n) (either
-// factor conjugated on request), zero beyond the group's order and for padding
-// antennas. Block = GR_T antennas of one group; thread = one order k and every
-// fourth antenna of the tile; bins staged in shared memory in chunks of GR_NC;
-// FP32 sums.
+// Antenna rows of the to-points kernels, one set per point group g: row r
+// holds the antenna perm[r] (the spatial order), planned with the part
+// (g, b = r / CH_THREADS) when the groups are planned per antenna block (n_ab
+// blocks), else with the group's plan over all antennas (n_ab = 1):
+// row(g, r) = two heads (the antenna's split position; c_ant in the first),
+// then for k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) C_part,k(n)
+// (either factor conjugated on request), zero beyond the part's order and for
+// padding antennas. Block = GR_T records of one group (inside one antenna
+// block); thread = one order k and every fourth record of the tile; bins
+// staged in shared memory in chunks of GR_NC; FP32 sums.
 constexpr int GR_T = 16;
 constexpr int GR_NC = 64;
+static_assert(CH_THREADS % GR_T == 0, "a rows block stays in one antenna block");
 __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
-    const float* __restrict__ ant, const float* __restrict__ c_ant, const float2* __restrict__ sig, int n_ant,
-    int n_ant_pad, int n_f, const ChebPlan* __restrict__ plan, const SplitPlan* __restrict__ gplan,
-    const float2* __restrict__ Cs, int conj_c, int conj_sig, float4* __restrict__ rows) {
+    const float* __restrict__ ant, const float* __restrict__ c_ant, const float2* __restrict__ sig,
+    const int* __restrict__ perm, int n_ant, int n_ant_pad, int n_f, int n_ab, const ChebPlan* __restrict__ plan,
+    const SplitPlan* __restrict__ gplan, const float2* __restrict__ Cs, int conj_c, int conj_sig,
+    float4* __restrict__ rows) {
     if (!plan->run_cheb) return;
     __shared__ float2 sC[CH_KMAX][GR_NC + 1];
     __shared__ float2 sS[GR_T][GR_NC + 1];
     const int g = blockIdx.y, i0 = blockIdx.x * GR_T, t = threadIdx.x;
-    const int K = gplan[g].K;
+    const int part = g * n_ab + (n_ab > 1 ? i0 / CH_THREADS : 0);
+    const int K = gplan[part].K;
     float4* grow = rows + (size_t)g * n_ant_pad * CH_ROW;
     if (t < GR_T && i0 + t < n_ant_pad) {
         const int i = i0 + t;
-        const int q = i < n_ant ? i : 0;
+        const int q = i < n_ant ? perm[i] : 0;
         float4 hi, lo;
         split3(ant[q], ant[n_ant + q], ant[2 * n_ant + q], hi, lo);
         hi.w = c_ant ? c_ant[q] : 0.0f;
@@ -1306,7 +1432,7 @@ __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
         grow[(size_t)i * CH_ROW + 1] = lo;
     }
     const int k = t >> 2, r = t & 3;
-    const float2* C = Cs + (size_t)g * CH_KMAX * n_f;
+    const float2* C = Cs + (size_t)part * CH_KMAX * n_f;
     float ar[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ai[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int n0 = 0; n0 < n_f; n0 += GR_NC) {
         const int nc = min(GR_NC, n_f - n0);
@@ -1324,7 +1450,7 @@ __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
             const int a = e / GR_NC, nn = e % GR_NC, i = i0 + a;
             float2 v = make_float2(0.0f, 0.0f);
             if (i < n_ant && nn < nc) {
-                v = sig[(size_t)i * n_f + n0 + nn];
+                v = sig[(size_t)perm[i] * n_f + n0 + nn];
                 if (conj_sig) v.y = -v.y;
             }
             sS[a][nn] = v;
@@ -1363,8 +1489,9 @@ struct ChebPointsArgs {
     int n_ant_tiles;
     int tiles_per_split;
     const ChebPlan* plan;
-    const SplitPlan* gplan;    // per group: interval and order
-    const int* kmax;           // largest group order
+    const SplitPlan* gplan;    // per part (group, antenna block): interval and order
+    int n_ab;                  // antenna blocks of CH_THREADS records with their own plan (1: one per group)
+    const int* kmax;           // largest part order
     float kh, kl;
     float* partial;
     int* err;
@@ -1472,7 +1599,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
 // Each group of ctas_per_group point CTAs has its own interval and order
 // (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
 // and KC = 4 instances run when the largest group order is <= 24 or <= 32, each
-// CTA with its group's order rounded up to even (at least 16) as a compile-time
+// CTA with its part's order rounded up to even (at least 8) as a compile-time
 // loop bound (one unrolled tile body per even order); the KC = 8 instance runs
 // otherwise (orders beyond 32 guarded by the group's own order); all three are
 // launched and the two that do not match return at once.
@@ -1502,10 +1629,6 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
     const uint32_t tile_bytes = (uint32_t)(AT * ROW * sizeof(float4));
     const int grp = blockIdx.x / args.ctas_per_group;
     const float4* grows = args.rows + (size_t)grp * args.group_rows;
-    const SplitPlan gp = args.gplan[grp];
-    const int K = gp.K;
-    const int ke = K <= 16 ? 16 : (K + 1) & ~1;              // orders run: K rounded up to even, >= 16
-    const float r_c = gp.r_c, inv_dr = gp.inv_dr;
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1557,6 +1680,12 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             return;
         }
         const float4* tile = rows + buf * AT * ROW;
+        // the tile's part: its antenna block (AT divides CH_THREADS) of this group
+        const SplitPlan gp =
+            args.gplan[grp * args.n_ab + (args.n_ab > 1 ? ((tile0 + it) * AT) / CH_THREADS : 0)];
+        const int K = gp.K;
+        const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
+        const float r_c = gp.r_c, inv_dr = gp.inv_dr;
         float in[TPK_V][NACC];
 #pragma unroll
         for (int v = 0; v < TPK_V; ++v)
@@ -1566,6 +1695,7 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             points_tile<MODE, KM, true>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny, pnz, pte, pe, in);
         } else {
             switch (ke) {
+                GERAF_POINTS_CASE(8) GERAF_POINTS_CASE(10) GERAF_POINTS_CASE(12) GERAF_POINTS_CASE(14)
                 GERAF_POINTS_CASE(16) GERAF_POINTS_CASE(18) GERAF_POINTS_CASE(20) GERAF_POINTS_CASE(22)
                 GERAF_POINTS_CASE(24) GERAF_POINTS_CASE(26) GERAF_POINTS_CASE(28) GERAF_POINTS_CASE(30)
                 default: points_tile<MODE, KM, false>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny,
@@ -1647,11 +1777,13 @@ ChebWs take_cheb(WsCarver& c, int64_t n_bbox) {
 }
 
 // Point groups of the to-points calls: consecutive point CTAs, each group with
-// its own interval, order and antenna rows (at most 64 groups and 256 MiB of
-// rows; at least 8 CTAs = 2048 points per group).
-constexpr size_t CH_GROUP_ROWS_BYTES = 256ull << 20;
+// its own antenna rows (at most 64 groups and CH_GROUP_ROWS_BYTES of rows; at
+// least 8 CTAs = 2048 points per group), planned per (group, block of
+// CH_THREADS antenna records in the spatial order) while the parts' tables fit
+// CH_TABLE_BYTES, else per group over all antennas.
+constexpr size_t CH_GROUP_ROWS_BYTES = 1ull << 30;
 struct PointGroups {
-    int groups, ctas_per_group;
+    int groups, ctas_per_group, n_ab, parts;
     float* box;
     SplitPlan* plan;
     float2* C;
@@ -1659,42 +1791,70 @@ struct PointGroups {
     float4* rows;
     size_t group_rows;
 };
-PointGroups plan_point_groups(int pt_ctas, int n_ant_pad) {
+PointGroups plan_point_groups(int pt_ctas, int n_ant, int n_ant_pad, int n_f) {
     PointGroups g{};
     g.group_rows = (size_t)n_ant_pad * CH_ROW;
     const size_t cap = std::max<size_t>(1, std::min<size_t>(64, CH_GROUP_ROWS_BYTES / (g.group_rows * sizeof(float4))));
     g.ctas_per_group = std::max<int>(8, (int)((pt_ctas + cap - 1) / cap));
     g.groups = (pt_ctas + g.ctas_per_group - 1) / g.ctas_per_group;
+    const int nb = (n_ant + CH_THREADS - 1) / CH_THREADS;
+    const size_t table = (size_t)CH_KMAX * n_f * sizeof(float2);
+    g.n_ab = (nb > 1 && (size_t)g.groups * nb * table <= CH_TABLE_BYTES) ? nb : 1;
+    g.parts = g.groups * g.n_ab;
     return g;
 }
-PointGroups take_point_groups(WsCarver& c, int pt_ctas, int n_ant_pad, int n_f) {
-    PointGroups g = plan_point_groups(pt_ctas, n_ant_pad);
+PointGroups take_point_groups(WsCarver& c, int pt_ctas, int n_ant, int n_ant_pad, int n_f) {
+    PointGroups g = plan_point_groups(pt_ctas, n_ant, n_ant_pad, n_f);
     g.box = c.take<float>((size_t)g.groups * 6);
-    g.plan = c.take<SplitPlan>(g.groups);
-    g.C = c.take<float2>((size_t)g.groups * CH_KMAX * n_f);
+    g.plan = c.take<SplitPlan>(g.parts);
+    g.C = c.take<float2>((size_t)g.parts * CH_KMAX * n_f);
     g.kmax = c.take<int>(1);
     g.rows = c.take<float4>((size_t)g.groups * g.group_rows);
     return g;
 }
-// group boxes, group plans and tables, then the groups' antenna rows
-geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const float* xyz, int64_t n,
-                                 const float* ant_xyz, const float* c_ant, int n_ant, int n_ant_pad,
+
+// Spatial order of the antennas and their records in it (Chebyshev calls)
+struct AntOrder {
+    int* perm;
+    float4* rec;
+    unsigned long long* sort_buf;   // the sort's global scratch when it does not fit in shared memory
+    int n_rec, n_pow2;
+};
+AntOrder take_ant_order(WsCarver& c, int n_ant, int n_rec) {
+    AntOrder a{};
+    a.n_rec = n_rec;
+    a.n_pow2 = pow2_at_least(n_ant);
+    a.perm = c.take<int>(n_rec);
+    a.rec = c.take<float4>(n_rec);
+    a.sort_buf = a.n_pow2 > AO_SMEM_MAX ? c.take<unsigned long long>(a.n_pow2) : nullptr;
+    return a;
+}
+void launch_ant_order(const AntOrder& a, const float* ant_xyz, const float* c_ant, int n_ant, cudaStream_t st) {
+    antenna_order_kernel<<<1, AO_THREADS, antenna_order_smem(a.n_pow2), st>>>(ant_xyz, n_ant, a.n_pow2, a.sort_buf,
+                                                                              a.perm, a.n_rec);
+    pack_antennas_perm<<<grid1d(a.n_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, a.perm, a.n_rec, a.rec);
+}
+
+// group boxes, part plans and tables, then the groups' antenna rows
+geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const AntOrder& ao, const float* xyz,
+                                 int64_t n, const float* ant_xyz, const float* c_ant, int n_ant, int n_ant_pad,
                                  const geraf_band* band, const float2* sig, int conj_c, int conj_sig,
                                  cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g.kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "point groups");
     group_bbox_kernel<<<g.groups, 256, 0, st>>>(xyz, n, (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V, g.box);
-    split_plan_kernel<<<g.groups, 256, 0, st>>>(g.box, ant_xyz, n_ant, 1, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
-                                                cw.plan, g.plan, g.C, g.kmax);
+    split_plan_kernel<<<g.parts, 256, 0, st>>>(g.box, ao.rec, n_ant, g.n_ab, g.n_ab > 1 ? CH_THREADS : n_ant,
+                                               2.0 * band->df / kC, band->n_f, CH_TAIL, cw.plan, g.plan, g.C, g.kmax);
     cheb_group_rows_kernel<<<dim3((n_ant_pad + GR_T - 1) / GR_T, g.groups), 256, 0, st>>>(
-        ant_xyz, c_ant, sig, n_ant, n_ant_pad, band->n_f, cw.plan, g.plan, g.C, conj_c, conj_sig, g.rows);
+        ant_xyz, c_ant, sig, ao.perm, n_ant, n_ant_pad, band->n_f, g.n_ab, cw.plan, g.plan, g.C, conj_c, conj_sig,
+        g.rows);
     return GERAF_OK;
 }
 
 void launch_cheb_plan(const ChebWs& w, const float* pts, int64_t n, const float* ant, int n_ant,
                       const geraf_band* band, cudaStream_t st) {
     bbox_partial_kernel<<<w.n_bbox_blocks, 256, 0, st>>>(pts, n, w.bbox);
-    cheb_plan_kernel<<<1, 256, 0, st>>>(w.bbox, w.n_bbox_blocks, ant, n_ant, 2.0 * band->df / kC, band->n_f, 1e-9,
+    cheb_plan_kernel<<<1, 256, 0, st>>>(w.bbox, w.n_bbox_blocks, ant, n_ant, 2.0 * band->df / kC, band->n_f, CH_TAIL,
                                         w.plan);
 }
 
@@ -1716,8 +1876,8 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant, int n_f) {
     q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
     // a plan per (split, antenna block) pays when a part holds enough pairs to
     // outweigh its FP64 plan (Bessel values of every bin): splits of at least
-    // 8192 points, and at most 256 MiB of tables; otherwise one plan per split
-    const int64_t max_parts = std::max<int64_t>(1, (int64_t)((256ull << 20) / ((size_t)CH_KMAX * n_f * 8)));
+    // 8192 points, and at most CH_TABLE_BYTES of tables; otherwise one plan per split
+    const int64_t max_parts = std::max<int64_t>(1, (int64_t)(CH_TABLE_BYTES / ((size_t)CH_KMAX * n_f * 8)));
     const bool blocks = (int64_t)q.tiles_per_split * CH_TP >= 8192 && (int64_t)q.splits * q.ant_blocks <= max_parts;
     q.plan_blocks = blocks ? q.ant_blocks : 1;
     return q;
@@ -1745,6 +1905,7 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     float4* ant = c.take<float4>(n_ant_rec);
     float2* part = c.take<float2>((size_t)p.splits * p.n_ant_pad * 32 * p.G);
     ChebWs cw{};
+    AntOrder ao{};
     float2* cpart = nullptr;
     float* sbox = nullptr;
     SplitPlan* splan = nullptr;
@@ -1753,6 +1914,7 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     float2* gout = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_pts);
+        ao = take_ant_order(c, n_ant, n_ant_rec);
         cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
         sbox = c.take<float>((size_t)q.splits * 6);
         splan = c.take<SplitPlan>(parts);
@@ -1774,29 +1936,30 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
                                            to_bins_kernel<true>, cheb_bins_kernel<false, 3>,
                                            cheb_bins_kernel<true, 3>, cheb_bins_kernel<false, 4>,
                                            cheb_bins_kernel<true, 4>, cheb_bins_kernel<false, 8>,
-                                           cheb_bins_kernel<true, 8>);
+                                           cheb_bins_kernel<true, 8>, antenna_order_kernel);
         if (as != GERAF_OK) return as;
     }
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, positions, n_pts, ant_xyz, n_ant, band, st);
+        launch_ant_order(ao, ant_xyz, c_ant, n_ant, st);
         cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_status(e, name);
         split_bbox_kernel<<<q.splits, 256, 0, st>>>(pts, q.n_tiles, q.tiles_per_split, sbox);
-        split_plan_kernel<<<parts, 256, 0, st>>>(sbox, ant_xyz, n_ant, q.plan_blocks,
+        split_plan_kernel<<<parts, 256, 0, st>>>(sbox, ao.rec, n_ant, q.plan_blocks,
                                                  q.plan_blocks > 1 ? CH_THREADS : n_ant, 2.0 * band->df / kC,
-                                                 band->n_f, 1e-9, cw.plan, splan, scs, kmax);
+                                                 band->n_f, CH_TAIL, cw.plan, splan, scs, kmax);
         float kh, kl;
         k0_split(band, &kh, &kl);
-        ChebBinsArgs ca{pts, ant, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, splan, q.plan_blocks, kmax, kh, kl,
-                        cpart, err};
+        ChebBinsArgs ca{pts, ao.rec, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, splan, q.plan_blocks, kmax, kh,
+                        kl, cpart, err};
         const dim3 grid(q.ant_blocks, q.splits);
         cheb_bins_kernel<kComplexAmp, 3><<<grid, CH_THREADS, cheb_bins_smem(24), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 4><<<grid, CH_THREADS, cheb_bins_smem(32), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 8><<<grid, CH_THREADS, cheb_bins_smem(64), st>>>(ca);
         const int groups = (q.splits + RS - 1) / RS;
         cheb_reconstruct_split_kernel<<<dim3((n_ant + RA - 1) / RA, groups), 128, 0, st>>>(
-            cpart, q.splits, n_ant, band->n_f, q.plan_blocks, cw.plan, splan, scs, gout);
+            cpart, q.splits, n_ant, band->n_f, q.plan_blocks, cw.plan, splan, scs, ao.perm, gout);
         sum_split_groups<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(
             gout, groups, (int64_t)n_ant * band->n_f, cw.plan, reinterpret_cast<float2*>(out));
         run_direct = &cw.plan->use_direct;
@@ -1839,9 +2002,11 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     double* loss_blocks = c.take<double>(fin_blocks);
     ChebWs cw{};
     PointGroups pg{};
+    AntOrder ao{};
     if (cheb) {
         cw = take_cheb(c, n_vox);
-        pg = take_point_groups(c, p.pt_ctas, p.n_ant_pad, band->n_f);
+        pg = take_point_groups(c, p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
+        ao = take_ant_order(c, n_ant, p.n_ant_pad);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
@@ -1849,19 +2014,21 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     {
         const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_points_kernel<MODE_FILTER>,
                                            cheb_points_kernel<MODE_FILTER, 3>, cheb_points_kernel<MODE_FILTER, 4>,
-                                           cheb_points_kernel<MODE_FILTER, 8>);
+                                           cheb_points_kernel<MODE_FILTER, 8>, antenna_order_kernel);
         if (as != GERAF_OK) return as;
     }
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, vox, n_vox, ant_xyz, n_ant, band, st);
-        const geraf_status gs = launch_point_groups(pg, cw, vox, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad, band,
-                                                    reinterpret_cast<const float2*>(s), 1, 0, st);
+        launch_ant_order(ao, ant_xyz, nullptr, n_ant, st);
+        const geraf_status gs = launch_point_groups(pg, cw, ao, vox, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad,
+                                                    band, reinterpret_cast<const float2*>(s), 1, 0, st);
         if (gs != GERAF_OK) return gs;
         float kh, kl;
         k0_split(band, &kh, &kl);
         ChebPointsArgs ca{nullptr, vox, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
-                          p.tiles_per_split, cw.plan, pg.plan, pg.kmax, kh, kl, reinterpret_cast<float*>(part), err};
+                          p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, kh, kl,
+                          reinterpret_cast<float*>(part), err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
         cheb_points_kernel<MODE_FILTER, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_FILTER, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
@@ -1895,9 +2062,11 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     float* part = c.take<float>((size_t)p.splits * 6 * n_pts);
     ChebWs cw{};
     PointGroups pg{};
+    AntOrder ao{};
     if (cheb) {
         cw = take_cheb(c, n_pts);
-        pg = take_point_groups(c, p.pt_ctas, p.n_ant_pad, band->n_f);
+        pg = take_point_groups(c, p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
+        ao = take_ant_order(c, n_ant, p.n_ant_pad);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
@@ -1909,19 +2078,20 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
         const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_points_kernel<MODE_RENDER_BWD>,
                                            cheb_points_kernel<MODE_RENDER_BWD, 3>,
                                            cheb_points_kernel<MODE_RENDER_BWD, 4>,
-                                           cheb_points_kernel<MODE_RENDER_BWD, 8>);
+                                           cheb_points_kernel<MODE_RENDER_BWD, 8>, antenna_order_kernel);
         if (as != GERAF_OK) return as;
     }
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, xyz, n_pts, ant_xyz, n_ant, band, st);
-        const geraf_status gs = launch_point_groups(pg, cw, xyz, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad, band,
-                                                    reinterpret_cast<const float2*>(g_s), 0, 1, st);
+        launch_ant_order(ao, ant_xyz, c_ant, n_ant, st);
+        const geraf_status gs = launch_point_groups(pg, cw, ao, xyz, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad,
+                                                    band, reinterpret_cast<const float2*>(g_s), 0, 1, st);
         if (gs != GERAF_OK) return gs;
         float kh, kl;
         k0_split(band, &kh, &kl);
         ChebPointsArgs ca{pts, nullptr, n_pts, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
-                          p.tiles_per_split, cw.plan, pg.plan, pg.kmax, kh, kl, part, err};
+                          p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, kh, kl, part, err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
         cheb_points_kernel<MODE_RENDER_BWD, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_RENDER_BWD, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
@@ -2006,36 +2176,41 @@ geraf_status chebyshev_order_impl(const float* xyz, int64_t n, const float* ant_
 }
 
 // Orders one Chebyshev phasor call evaluates: the same device plans as the
-// call (whole set, then per split of point tiles for the to-bins direction or
-// per point group for the to-points direction), read back; the kernel
-// instance follows the largest part order (24, 32 or 64 orders compiled in;
-// the 64-order instance runs 32 orders plus the part's own beyond them, in
-// blocks of 8). mean_orders = orders per (point, antenna) pair, averaged over
-// the points.
+// call (whole set; the antennas in the spatial order; then per part = split of
+// point tiles or point group, times a block of antenna records where the call
+// plans per block), read back; the kernel instance follows the largest part
+// order (24, 32 or 64 orders compiled in; the 64-order instance runs 32 orders
+// plus the part's own beyond them, in blocks of 8; the others the part's order
+// rounded up to even, at least 8). mean_orders = orders per (point, antenna)
+// pair, averaged over all pairs.
 geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_xyz, int32_t n_ant,
                                  const geraf_band* band, int32_t to_points, void* ws, size_t* ws_bytes,
                                  int32_t* orders, double* mean_orders, cudaStream_t st) {
     BandK bk;
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
-    int parts = 0, n_ab = 1, ant_per_block = n_ant;
+    int parts = 0, n_ab = 1, ant_per_block = n_ant, n_rec = 0;
     int64_t per_part = 0;
     if (to_points) {
         const ToPointsPlan p = plan_to_points(n, n_ant, bk.g);
-        const PointGroups g = plan_point_groups(p.pt_ctas, p.n_ant_pad);
-        parts = g.groups;
+        const PointGroups g = plan_point_groups(p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
+        n_ab = g.n_ab;
+        parts = g.parts;
         per_part = (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V;
+        n_rec = p.n_ant_pad;
     } else {
         const int64_t n_pad = (n + CH_TP - 1) / CH_TP * CH_TP;
         const ToBinsPlan p = plan_to_bins(n_pad, n_ant, bk.g);
         const ChebBinsPlan q = plan_cheb_bins((int64_t)p.n_tiles * p.TP, n_ant, band->n_f);
         n_ab = q.plan_blocks;
-        ant_per_block = n_ab > 1 ? CH_THREADS : n_ant;
         parts = q.splits * n_ab;
         per_part = (int64_t)q.tiles_per_split * CH_TP;
+        n_rec = std::max(p.n_ant_pad, (n_ant + CH_THREADS - 1) / CH_THREADS * CH_THREADS);
     }
+    ant_per_block = n_ab > 1 ? CH_THREADS : n_ant;
     const int n_splits = parts / n_ab;
     WsCarver c(ws);
     ChebWs cw = take_cheb(c, n);
+    AntOrder ao = take_ant_order(c, n_ant, n_rec);
     float* box = c.take<float>((size_t)n_splits * 6);
     SplitPlan* splan = c.take<SplitPlan>(parts);
     float2* Cs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
@@ -2046,12 +2221,17 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     orders[0] = orders[1] = orders[2] = 0;
     *mean_orders = 0.0;
     if (!use_cheb(band)) return GERAF_OK;
+    {
+        const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", antenna_order_kernel);
+        if (as != GERAF_OK) return as;
+    }
     launch_cheb_plan(cw, xyz, n, ant_xyz, n_ant, band, st);
+    launch_ant_order(ao, ant_xyz, nullptr, n_ant, st);
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "chebyshev_work");
     group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz, n, per_part, box);
-    split_plan_kernel<<<parts, 256, 0, st>>>(box, ant_xyz, n_ant, n_ab, ant_per_block, 2.0 * band->df / kC,
-                                             band->n_f, 1e-9, cw.plan, splan, Cs, kmax);
+    split_plan_kernel<<<parts, 256, 0, st>>>(box, ao.rec, n_ant, n_ab, ant_per_block, 2.0 * band->df / kC,
+                                             band->n_f, CH_TAIL, cw.plan, splan, Cs, kmax);
     geraf_status s = check_launch("chebyshev_work");
     if (s != GERAF_OK) return s;
     ChebPlan h;
@@ -2070,7 +2250,7 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
         const int64_t j0 = (int64_t)sp * per_part, j1 = std::min<int64_t>(n, j0 + per_part);
         const int64_t a0 = (int64_t)b * ant_per_block, a1 = std::min<int64_t>(n_ant, a0 + ant_per_block);
         const int Kp = hs[g].K;
-        const int ex = inst <= 32 ? std::min(inst, Kp <= 16 ? 16 : (Kp + 1) & ~1) : std::max(32, (Kp + 7) / 8 * 8);
+        const int ex = inst <= 32 ? std::min(inst, Kp <= 8 ? 8 : (Kp + 1) & ~1) : std::max(32, (Kp + 7) / 8 * 8);
         sum += (double)std::max<int64_t>(j1 - j0, 0) * (double)std::max<int64_t>(a1 - a0, 0) * ex;
     }
     orders[0] = h.K;
