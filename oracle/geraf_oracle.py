@@ -271,16 +271,17 @@ def mlp_backward(spec, params, cache, d_f, d_G, d_a):
     return np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
 
 
-def nets_forward(nets, params, xyz):
+def nets_forward(nets, params, xyz, precision="fp32"):
     """The paper's two field networks (App. C, "Training Setup"; section 5.2
     "Signal representation": a separate network of the position gives the
     reflection coefficient): f and G = grad f from the SDF network, a =
     sigmoid of the reflectivity network's output, both on the same encoding of
-    x. Returns (f, G, a, cache)."""
+    x. precision "bf16" applies the BF16 network reading of mlp_forward to both
+    networks. Returns (f, G, a, cache)."""
     params = np.asarray(params, np.float32)
     ns = nets.sdf.n_params
-    f, G, _, cs = mlp_forward(nets.sdf, params[:ns], xyz)
-    logit, _, _, cr = mlp_forward(nets.refl, params[ns:], xyz)
+    f, G, _, cs = mlp_forward(nets.sdf, params[:ns], xyz, precision=precision)
+    logit, _, _, cr = mlp_forward(nets.refl, params[ns:], xyz, precision=precision)
     a = _sigmoid(logit)
     return f, G, a, {"sdf": cs, "refl": cr, "a": a}
 

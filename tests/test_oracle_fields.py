@@ -229,3 +229,68 @@ def test_two_networks_match_torch_autograd(oracle, paper_size):
     np.testing.assert_allclose(gp, tgp, rtol=1e-8, atol=1e-10 * np.abs(tgp).max())
     # the reflectivity network's block gets its own gradient (a dropped d_a would zero it)
     assert np.abs(gp[nets.sdf.n_params:]).max() > 0
+
+
+def _torch_bf16_net(spec, q, x):
+    """One network of the BF16 reading as explicit value and tangent streams
+    (hidden weights and every hidden layer's inputs rounded to bfloat16 by
+    torch's own cast, straight-through gradient; head FP32): (out, tangents)
+    of its single output."""
+    from torch.func import jvp
+    c = torch.tensor(np.asarray(spec.center, np.float32).astype(np.float64))
+    half = float(np.float32(spec.half))
+
+    def pe(xx):
+        xt = (xx - c) / half
+        return torch.cat([f((2.0 ** k) * np.pi * xt) for k in range(spec.n_levels) for f in (torch.sin, torch.cos)], 1)
+
+    def rnd(t):
+        return t + (t.to(torch.float32).to(torch.bfloat16).to(torch.float64) - t).detach()
+
+    z = pe(x)
+    dz = [jvp(pe, (x,), (torch.nn.functional.one_hot(torch.full((x.shape[0],), d), 3).double(),))[1]
+          for d in range(3)]
+    off = 0
+    shapes = spec.shapes()
+    for li, (o, i) in enumerate(shapes):
+        W = q[off:off + o * i].view(o, i); off += o * i
+        b = q[off:off + o]; off += o
+        zr, dzr = rnd(z), [rnd(t) for t in dz]
+        if li < len(shapes) - 1:
+            Wr = rnd(W)
+            h = zr @ Wr.T + b
+            dh = [t @ Wr.T for t in dzr]
+            s = torch.sigmoid(spec.beta * h)
+            z = torch.nn.functional.softplus(h, beta=spec.beta, threshold=1e6)
+            dz = [s * t for t in dh]
+        else:
+            return (zr @ W.T + b)[:, 0], torch.stack([t @ W[0] for t in dzr], 1)
+
+
+def test_two_networks_bf16_match_torch(oracle):
+    """The BF16 reading applied to the paper's two networks (a small shape of
+    the same structure): values, SDF gradient and the straight-through adjoint
+    of all packed parameters against an explicit torch construction."""
+    nets = gi.FieldNets(gi.MLPSpec(4, 24, 3, 30.0, (0.0, 0.0, 0.15), 0.05, 1),
+                        gi.MLPSpec(4, 16, 2, 30.0, (0.0, 0.0, 0.15), 0.05, 1))
+    n = 31
+    params = gi.nets_init(nets, seed=8, sdf_bias=0.01)
+    rng = np.random.default_rng(6)
+    xyz = (np.array([0.0, 0.0, 0.15])[:, None] + rng.uniform(-0.05, 0.05, (3, n))).astype(np.float32)
+    f, G, a, cache = oracle.nets_forward(nets, params, xyz, precision="bf16")
+    p = torch.tensor(params.astype(np.float64), requires_grad=True)
+    x = torch.tensor(xyz.T.astype(np.float64))
+    ns = nets.sdf.n_params
+    tf, tG = _torch_bf16_net(nets.sdf, p[:ns], x)
+    tl, _ = _torch_bf16_net(nets.refl, p[ns:], x)
+    ta = torch.sigmoid(tl)
+    np.testing.assert_allclose(f, tf.detach().numpy(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(a, ta.detach().numpy(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(G, tG.detach().numpy().T, rtol=1e-10, atol=1e-11 * np.abs(G).max())
+    f32, _, _, _ = oracle.nets_forward(nets, params, xyz)
+    assert np.abs(f - f32).max() > 1e-6                  # the roundings are applied
+    d_f, d_G, d_a = rng.standard_normal(n), rng.standard_normal((3, n)), rng.standard_normal(n)
+    gp = oracle.nets_backward(nets, params, cache, d_f, d_G, d_a)
+    L = (tf * torch.tensor(d_f)).sum() + (tG * torch.tensor(d_G.T)).sum() + (ta * torch.tensor(d_a)).sum()
+    tgp = torch.autograd.grad(L, p)[0].numpy()
+    np.testing.assert_allclose(gp, tgp, rtol=1e-9, atol=1e-10 * np.abs(tgp).max())
