@@ -303,7 +303,7 @@ def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
             "steps": {"uniform": steps, "proposal": p_steps}}
 
 
-def paper_config_step(dev, warmup=3, steps=5):
+def paper_config_step(dev, warmup=3, steps=5, precision="fp32"):
     """The paper's own training configuration (App. C "Training Setup";
     section 5.3; section 9): N_ray = 1024 primary rays x N_z = 32 depths,
     SDF network 8 x 256 and a separate reflectivity network 4 x 256 on a
@@ -325,7 +325,8 @@ def paper_config_step(dev, warmup=3, steps=5):
     nets = gi.paper_nets(center=(0.0, 0.0, 0.15), half=0.06)
     params = torch.as_tensor(gi.nets_init(nets, seed=3, sdf_bias=0.02), device=dev)
     field = G.MLPField(params, n_levels=10, width=256, n_hidden=8, beta=nets.sdf.beta, center=nets.sdf.center,
-                       half=nets.sdf.half, refl_hidden=4, refl_width=256)
+                       half=nets.sdf.half, refl_hidden=4, refl_width=256,
+                       precision=G.PREC_BF16 if precision == "bf16" else G.PREC_FP32)
     target = PL.scene_target(geo, gi.c4_scene(4), noise_seed=4, device=dev)
     bank = PL.SignalBank(geo, (160, 160), (80, 40))
     bank.fill(field, 0, 0)
@@ -347,8 +348,8 @@ def paper_config_step(dev, warmup=3, steps=5):
     n_ant, n_vox = int(geo.ant.shape[1]), int(geo.vox.shape[1])
     terms = 2 * n_pts * bank.patch_size * nf + n_vox * n_ant * nf + n_vox * bank.patch_size * nf
     return {"workload": "paper training configuration: 1024 rays x 32 depths, SDF net 8x256 + reflectivity net "
-                        "4x256, PE 10 octaves, fp32; FMCW 64 samples (3.59 GHz); 160x160 array @2mm in 3200-antenna "
-                        "bank patches; 32^3 heatmap",
+                        f"4x256, PE 10 octaves, {precision}" + (" on tcgen05" if precision == "bf16" else "")
+                        + "; FMCW 64 samples (3.59 GHz); 160x160 array @2mm in 3200-antenna bank patches; 32^3 heatmap",
             "n_pts": n_pts, "patch_antennas": bank.patch_size, "n_antennas": n_ant, "n_f": nf, "n_vox": n_vox,
             "ms_per_step": ms, "terms_per_step": terms, "terms_per_s": terms / (ms * 1e-3),
             "per_call_ms": {nm: round(sum(e[nm][0].elapsed_time(e[nm][1]) for e in ev) / steps, 3) for nm in names},
@@ -663,7 +664,9 @@ def main():
         import torch
         from paper_2605_29097_gb300 import _build
         _build.build()
-        print(json.dumps({"mode": "paper_config", **paper_config_step(torch.device("cuda", local))}), flush=True)
+        dev = torch.device("cuda", local)
+        print(json.dumps({"mode": "paper_config", "fp32": paper_config_step(dev),
+                          "bf16": paper_config_step(dev, precision="bf16")}), flush=True)
         return
 
     import torch
@@ -762,6 +765,8 @@ def main():
             line["train_step"] = train_step_compare(dev)
             torch.cuda.empty_cache()
             line["paper_config"] = paper_config_step(dev)
+            torch.cuda.empty_cache()
+            line["paper_config_bf16"] = paper_config_step(dev, precision="bf16")
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -2,7 +2,8 @@
 // networks (App. C "Training Setup": an SDF network of 8 softplus layers of
 // 256 on a 10-octave positional encoding, and a separate reflectivity network
 // of 4 layers of 256 on the same encoding; section 5.2 "Signal
-// representation"), FP32 on CUDA cores.
+// representation"), FP32 on CUDA cores (the BF16 form of these networks runs
+// on the tensor cores: mlp_wide_tc.cu).
 //
 // Layer-major: the positional encoding, every layer and the head are separate
 // launches over all points, with the pre-activations of each layer kept in the
@@ -560,7 +561,15 @@ void net_forward(const WNet& g, const float* xyz, int64_t n, float* base, cudaSt
 // ---------------------------------------------------------------- entry glue
 bool mlp_is_wide(const geraf_field_desc* d) { return d->refl_hidden > 0 || d->width != 128; }
 
+geraf_status mlp_wide_tc_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* bytes);
+geraf_status mlp_wide_tc_forward(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
+                                 float* refl, void* saved, size_t saved_bytes, cudaStream_t st);
+geraf_status mlp_wide_tc_backward(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
+                                  const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
+                                  void* ws, size_t* ws_bytes, cudaStream_t st);
+
 geraf_status mlp_wide_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* bytes) {
+    if (d->precision == GERAF_PREC_BF16) return mlp_wide_tc_saved_bytes(d, n, bytes);
     Nets nets;
     if (!make_nets(d, 4, &nets)) return GERAF_ERR_UNSUPPORTED;
     size_t f = net_floats(nets.sdf, n) + (size_t)n;
@@ -571,8 +580,10 @@ geraf_status mlp_wide_saved_bytes(const geraf_field_desc* d, int64_t n, size_t* 
 
 geraf_status mlp_wide_forward(const geraf_field_desc* d, const float* xyz, int64_t n, float* sdf, float* grad,
                               float* refl, void* saved, size_t saved_bytes, cudaStream_t st) {
+    if (d->precision == GERAF_PREC_BF16)
+        return mlp_wide_tc_forward(d, xyz, n, sdf, grad, refl, saved, saved_bytes, st);
     if (d->precision != GERAF_PREC_FP32)
-        return fail(GERAF_ERR_UNSUPPORTED, "fields: networks other than one 128-wide trunk run in FP32 only");
+        return fail(GERAF_ERR_UNSUPPORTED, "fields: MLP precision %d unknown", d->precision);
     if (!saved)
         return fail(GERAF_ERR_INVALID_ARG, "fields: this network keeps its layer activations in `saved`, which "
                                            "must be given even without a backward pass");
@@ -672,8 +683,10 @@ void net_backward(const WNet& g, const float* xyz, int64_t n, const float* base,
 geraf_status mlp_wide_backward(const geraf_field_desc* d, const float* xyz, int64_t n, const void* saved,
                                const float* d_sdf, const float* d_grad, const float* d_refl, float* d_params,
                                void* ws, size_t* ws_bytes, cudaStream_t st) {
+    if (d->precision == GERAF_PREC_BF16)
+        return mlp_wide_tc_backward(d, xyz, n, saved, d_sdf, d_grad, d_refl, d_params, ws, ws_bytes, st);
     if (d->precision != GERAF_PREC_FP32)
-        return fail(GERAF_ERR_UNSUPPORTED, "fields_backward: networks other than one 128-wide trunk run in FP32 only");
+        return fail(GERAF_ERR_UNSUPPORTED, "fields_backward: MLP precision %d unknown", d->precision);
     Nets nets;
     if (!make_nets(d, 4, &nets)) return GERAF_ERR_UNSUPPORTED;
     const int splits = wide_splits(n);

@@ -142,3 +142,82 @@ def test_wide_network_needs_saved(G):
     f = torch.empty(8, device="cuda")
     st = _lib.lib().geraf_fields(ctypes.byref(desc), xyz.data_ptr(), 8, f.data_ptr(), None, None, None, 0, None)
     assert st == 1    # GERAF_ERR_INVALID_ARG
+
+
+# BF16 networks on the tensor cores against the oracle's BF16 network reading
+# (weights and every hidden layer's inputs rounded to bfloat16, FP32 sums
+# stand in for exact ones): relative L2 2e-3, the BF16 path's bound.
+BF16_TOL = 2e-3
+
+
+def _bf16_case(G, oracle, nets, n, seed):
+    params = gi.nets_init(nets, seed=seed, sdf_bias=0.01)
+    xyz, rng = _points(nets.sdf, n, seed)
+    s = nets.sdf
+    field = G.MLPField(torch.as_tensor(params, device="cuda"), n_levels=s.n_levels, width=s.width,
+                       n_hidden=s.n_hidden, beta=s.beta, center=s.center, half=s.half,
+                       refl_hidden=nets.refl.n_hidden, refl_width=nets.refl.width, precision=G.PREC_BF16)
+    xt = torch.as_tensor(xyz, device="cuda")
+    f, grad, a, saved = G.geraf_fields(field, xt, keep_saved=True)
+    G.geraf_poll_device_error()
+    of, oG, oa, cache = oracle.nets_forward(nets, params, xyz, precision="bf16")
+    h = lambda t: t.detach().cpu().numpy()
+    errs = {"f": rel_l2(h(f), of), "a": rel_l2(h(a), oa), "G": rel_l2(h(grad), oG)}
+    # value only (no tangent streams, no reflectivity network): the same f
+    f1, _, _, _ = G.geraf_fields(field, xt, want_grad=False, want_refl=False)
+    errs["f value-only"] = rel_l2(h(f1), of)
+    d_f = rng.standard_normal(n).astype(np.float32)
+    d_G = rng.standard_normal((3, n)).astype(np.float32)
+    d_a = rng.standard_normal(n).astype(np.float32)
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    gp = h(G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a)))
+    G.geraf_poll_device_error()
+    ogp = oracle.nets_backward(nets, params, cache, d_f, d_G, d_a)
+    errs["d_params"] = rel_l2(gp, ogp)
+    ns = nets.sdf.n_params
+    errs["d_params refl"] = rel_l2(gp[ns:], ogp[ns:])
+    off = 0
+    for li, (o, i) in enumerate(nets.sdf.shapes()):
+        errs[f"d_W sdf {li}"] = rel_l2(gp[off:off + o * i], ogp[off:off + o * i])
+        errs[f"d_b sdf {li}"] = rel_l2(gp[off + o * i:off + o * i + o], ogp[off + o * i:off + o * i + o])
+        off += o * i + o
+    print({k: f"{v:.2e}" for k, v in errs.items()})
+    bad = {k: v for k, v in errs.items() if not v < BF16_TOL}
+    assert not bad, bad
+
+
+def test_paper_networks_bf16_tensor_cores(G, oracle):
+    """The paper's two networks (SDF 8 x 256, reflectivity 4 x 256, 10 octaves)
+    in BF16 on tcgen05 at 32 771 points: every GEMM of the forward and the
+    adjoint runs over 1025 row tiles (the last ragged), the weight gradients
+    over 76 splits of the rows."""
+    _bf16_case(G, oracle, gi.paper_nets(), 32771, 17)
+
+
+def test_small_networks_bf16_tensor_cores(G, oracle):
+    """Other shapes on the same kernels: a 3 x 128 SDF network and a 2 x 64
+    reflectivity network on a 4-octave encoding (24 features padded to 64), 300
+    points (a single partly filled row tile for the reflectivity network)."""
+    nets = gi.FieldNets(gi.MLPSpec(4, 128, 3, 50.0, (0.0, 0.0, 0.15), 0.06, 1),
+                        gi.MLPSpec(4, 64, 2, 50.0, (0.0, 0.0, 0.15), 0.06, 1))
+    _bf16_case(G, oracle, nets, 300, 19)
+
+
+def test_wide_single_trunk_bf16(G, oracle):
+    """One 256-wide trunk with head [f, a_logit] in BF16 on the tensor cores."""
+    spec = gi.MLPSpec(n_levels=6, width=256, n_hidden=3, beta=100.0, center=(0.0, 0.0, 0.15), half=0.05)
+    params = gi.mlp_init(spec, seed=23)
+    xyz, rng = _points(spec, 77, 23)
+    field = G.MLPField(torch.as_tensor(params, device="cuda"), n_levels=6, width=256, n_hidden=3,
+                       beta=spec.beta, center=spec.center, half=spec.half, precision=G.PREC_BF16)
+    xt = torch.as_tensor(xyz, device="cuda")
+    f, grad, a, saved = G.geraf_fields(field, xt, keep_saved=True)
+    G.geraf_poll_device_error()
+    of, oG, oa, cache = oracle.mlp_forward(spec, params, xyz, precision="bf16")
+    h = lambda t: t.detach().cpu().numpy()
+    assert max(rel_l2(h(f), of), rel_l2(h(a), oa), rel_l2(h(grad), oG)) < BF16_TOL
+    d_f, d_G, d_a = (rng.standard_normal(s).astype(np.float32) for s in ((77,), (3, 77), (77,)))
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    gp = G.geraf_fields_backward(field, xt, saved, cu(d_f), cu(d_G), cu(d_a))
+    G.geraf_poll_device_error()
+    assert rel_l2(h(gp), oracle.mlp_backward(spec, params, cache, d_f, d_G, d_a)) < BF16_TOL
