@@ -109,11 +109,15 @@ enum { GERAF_RENDER_DIRECTIONAL = 1 };
  *   (refl_hidden layers of refl_width, head [a_logit]) on the same encoding,
  *   params packed [SDF network | reflectivity network], each as above.
  *   One 128-wide trunk (refl_hidden = 0, width = 128) runs the fused kernels
- *   in FP32 or BF16; every other shape (widths a multiple of 32 up to 1024,
- *   up to 16 layers per network) runs layer by layer in FP32, keeps its layer
- *   activations in `saved` (so `saved` is required even without a backward
- *   pass) and must be called with grad and refl for a backward pass to
- *   follow. Zero-initialised trailing fields keep the single-trunk form. */
+ *   in FP32 or BF16; every other shape runs layer by layer, in FP32 on CUDA
+ *   cores (widths a multiple of 32 up to 1024) or in BF16 on the tensor cores
+ *   (widths a multiple of 64 up to 256), up to 16 layers per network; it
+ *   keeps its layer activations in `saved` (so `saved` is required even
+ *   without a backward pass) and must be called with grad and refl for a
+ *   backward pass to follow. BF16 means the BF16 network reading: weights and
+ *   every hidden layer's inputs rounded to bfloat16, FP32 accumulation, bias,
+ *   nonlinearity and head in FP32, straight-through adjoint.
+ *   Zero-initialised trailing fields keep the single-trunk form. */
 typedef struct {
     int32_t kind;
     const float* prims;
