@@ -231,27 +231,41 @@ def job_rate(units_per_step_per_rank: int, steps: int, world: int, max_ms: float
     return units_per_step_per_rank * steps * world / (max_ms * 1e-3)
 
 
-def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
-    """Training step on the random-scene workload: 2^24 stratified samples
-    (256^2 columns x 256 depths) vs 2^20 proposal samples (256^2 x 16), both
-    with the MLP's Adam update (and the proposal's own update); then, at fixed
-    parameters, heatmap rel L2 and MLP-gradient cosine of proposal vs uniform
-    sampling and the fallback decision (proposal error > 2e-3 -> uniform)."""
-    import numpy as np
+def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, m=12, r_max=4, prop_steps=150,
+                       m_table=(4, 8, 12, 16, 24)):
+    """Training step on the random-scene workload (1-8 ellipsoids and boxes
+    behind a 0.5 occluder, 10 dB noise; 64x64 array, 128 bins, 64^3 heatmap):
+    2^24 stratified samples (256^2 columns x 256 depths) against the same
+    grid's own samples in the m proposal cells (of 64 per column) of largest q
+    plus r_max run-closing samples per column (m 4 + r_max samples per column),
+    both with the MLP's Adam update (the proposal also learns from its pass).
+    The proposal is first trained on the blended weights T alpha of dense
+    renders of the analytic scene (the converged geometry). Then, at fixed
+    parameters: heatmap relative L2 of the cell-subset pass against the dense
+    pass (identical samples in the kept cells) on the analytic scene, for the
+    trained proposal and for the exact dense weight histogram, at several m;
+    the same on the MLP field being trained; MLP-gradient cosine; and the
+    fallback decision (error on the converged geometry > 2e-3 -> uniform)."""
     import torch
     import geraf_inputs as gi
     import paper_2605_29097_gb300 as G
     from paper_2605_29097_gb300 import pipeline as PL
     wl = gi.workload("c4")
     geo = PL.make_geometry(wl, dev)
-    target = PL.scene_target(geo, gi.c4_scene(4), noise_seed=4, device=dev)
+    scene = gi.c4_scene(4)
+    target = PL.scene_target(geo, scene, noise_seed=4, device=dev)
     spec = gi.MLPSpec(center=(0.0, 0.0, 0.15), half=0.06)
     p = torch.as_tensor(gi.mlp_init(spec, seed=11, sdf_bias=0.02), device=dev)
     field = G.MLPField(p, center=spec.center, half=spec.half)
     master = p.clone().requires_grad_(True)
     opt = torch.optim.Adam([master], lr=1e-3)
-    prop, pm = PL.init_proposal(gshape=(64, 64, 64), depth=16, seed=5, device=dev)
+    gshape = (64, 64, 64)
+    prop, pm = PL.init_proposal(gshape=gshape, depth=16, seed=5, device=dev)
     ptrain = PL.ProposalTrainer(prop, pm, lr=1e-2)
+    afield = PL.scene_field(scene, dev)
+    for k in range(prop_steps):
+        dp, df, _ = PL.proposal_signal_dense(geo, afield, prop, seed=41, step=k)
+        ptrain.step(dp, df)
 
     def apply(d):
         opt.zero_grad(set_to_none=False)
@@ -261,16 +275,13 @@ def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
             p.copy_(master)
 
     def uniform_step(k):
-        r = PL.forward_backward(geo, field, target, seed=21, step=k)
-        apply(r.d_params)
-        return r
+        apply(PL.forward_backward(geo, field, target, seed=21, step=k).d_params)
 
-    def proposal_step(k):
-        r = PL.proposal_forward_backward(geo, field, prop, target, seed=23, step=k)
+    def cells_step(k):
+        r = PL.cells_forward_backward(geo, field, prop, target, m, r_max, seed=23, step=k)
         apply(r.d_params)
         dp, df, _ = r.proposal
         ptrain.step(dp, df)
-        return r
 
     def timed(fn, w, n, k0):
         for i in range(w):
@@ -286,21 +297,43 @@ def train_step_compare(dev, warmup=1, steps=2, p_warmup=3, p_steps=3):
 
     ms_u = timed(uniform_step, warmup, steps, 0)
     torch.cuda.empty_cache()
-    ms_p = timed(proposal_step, p_warmup, p_steps, 100)
-    # fixed-parameter comparison
+    ms_c = timed(cells_step, c_warmup, c_steps, 100)
+    torch.cuda.empty_cache()
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
+
+    # fixed parameters, identical samples in the kept cells (seed 31, step 0)
+    _, q_prop, _ = G.geraf_proposal_density(prop, keep_saved=False)
+    q_best = PL.dense_weight_histogram(geo, afield, gshape, seed=31, step=0)
+    Pu = PL.forward_backward(geo, afield, target, seed=31, step=0).P
+    table = []
+    for mm in m_table:
+        row = {"m": mm, "samples_per_column": mm * (geo.n_z // gshape[2]) + r_max,
+               "kept_fraction": (mm * (geo.n_z // gshape[2]) + r_max) / geo.n_z}
+        for name, q in (("trained_proposal", q_prop), ("exact_histogram", q_best)):
+            Pc = PL.cells_forward_backward(geo, afield, prop, target, mm, r_max, seed=31, step=0, q=q,
+                                           train_proposal=False).P
+            row[name] = rel(Pc, Pu)
+        table.append(row)
+        torch.cuda.empty_cache()
+    err = next(r["trained_proposal"] for r in table if r["m"] == m)
     ru = PL.forward_backward(geo, field, target, seed=31, step=0)
-    rp = PL.proposal_forward_backward(geo, field, prop, target, seed=31, step=0)
-    Pu, Pp = ru.P.double(), rp.P.double()
-    err = float(torch.linalg.norm(Pp - Pu) / torch.linalg.norm(Pu))
-    gu, gp = ru.d_params.double(), rp.d_params.double()
-    cos = float((gu @ gp) / (torch.linalg.norm(gu) * torch.linalg.norm(gp)))
+    rc = PL.cells_forward_backward(geo, field, prop, target, m, r_max, seed=31, step=0, train_proposal=False)
+    err_mlp = rel(rc.P, ru.P)
+    gu, gc = ru.d_params.double(), rc.d_params.double()
+    cos = float((gu @ gc) / (torch.linalg.norm(gu) * torch.linalg.norm(gc)))
     torch.cuda.synchronize()
     return {"workload": "random ellipsoids/boxes behind a 0.5 occluder, 10 dB noise; 64x64 array, 128 freqs, "
                         "MLP 4x128 fp32, 64^3 heatmap",
-            "uniform_samples": wl.grid.n_pts, "proposal_samples": geo.n_ray * prop.depth,
-            "uniform_step_ms": ms_u, "proposal_step_ms": ms_p, "speedup": ms_u / ms_p,
-            "heatmap_rel_l2": err, "grad_cosine": cos, "tolerance": 2e-3, "fallback_to_uniform": err > 2e-3,
-            "steps": {"uniform": steps, "proposal": p_steps}}
+            "uniform_samples": wl.grid.n_pts, "cell_samples": geo.n_ray * rc.n_out,
+            "cells": {"m": m, "of": gshape[2], "r_max": r_max, "samples_per_column": rc.n_out},
+            "proposal_training_steps_on_scene": prop_steps,
+            "uniform_step_ms": ms_u, "cells_step_ms": ms_c, "speedup": ms_u / ms_c,
+            "heatmap_rel_l2_converged_geometry": err, "heatmap_rel_l2_table": table,
+            "heatmap_rel_l2_mlp_field": err_mlp, "grad_cosine_mlp_field": cos,
+            "tolerance": 2e-3, "fallback_to_uniform": err > 2e-3,
+            "steps": {"uniform": steps, "cells": c_steps}}
 
 
 def paper_config_step(dev, warmup=3, steps=5, precision="fp32"):
@@ -647,6 +680,8 @@ def main():
                     help="time only the fields kernels on N_PTS points and exit")
     ap.add_argument("--paper-config", action="store_true",
                     help="time only the paper's own training configuration and exit")
+    ap.add_argument("--train-step", action="store_true",
+                    help="run only the uniform vs proposal-cell training-step comparison and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -659,6 +694,12 @@ def main():
         return
     if args.mlp_bench:
         mlp_bench(args.mlp_bench)
+        return
+    if args.train_step:
+        import torch
+        from paper_2605_29097_gb300 import _build
+        _build.build()
+        print(json.dumps({"mode": "train_step", **train_step_compare(torch.device("cuda", local))}), flush=True)
         return
     if args.paper_config:
         import torch

@@ -212,21 +212,27 @@ geraf_status geraf_fields_backward(const geraf_field_desc* desc, const float* xy
  * t_eff_k = T_k + Phi_s(f(x_apr)); c_ant [n_ant] = Phi_s(f(x_ant)).
  * Antenna i then sees T' = clamp(t_eff - c_ant_i, 0, 1) (App. B.2 integration;
  * the origin terms carry no gradient, section 6).
+ * keep [n_ray*n_z] (NULL = all ones) multiplies w: a sample with keep = 0
+ * still closes the interval of the sample before it (its f enters that
+ * alpha) and its own alpha still attenuates T, but it reflects nothing (the
+ * run-closing and padding samples of geraf_sample_cells).
  */
 geraf_status geraf_blend(const float* sdf, const float* refl, int32_t n_ray, int32_t n_z,
                          const float* sdf_apr, const float* sdf_ant, int32_t n_ant,
                          float s, float a_tx,
-                         float* alpha, float* T, float* w, float* t_eff, float* c_ant, void* stream);
+                         float* alpha, float* T, float* w, float* t_eff, float* c_ant, const float* keep,
+                         void* stream);
 
 /*
  * geraf_blend_backward — adjoint of geraf_blend for upstream d_w, d_teff
- * [n_ray*n_z] (either may be NULL = zero). Writes d_sdf, d_refl [n_ray*n_z]
- * and d_scalars[2] = {dL/ds, dL/dA'_tx} (device, overwritten).
+ * [n_ray*n_z] (either may be NULL = zero), with the forward's keep (or NULL).
+ * Writes d_sdf, d_refl [n_ray*n_z] and d_scalars[2] = {dL/ds, dL/dA'_tx}
+ * (device, overwritten).
  */
 geraf_status geraf_blend_backward(const float* sdf, const float* refl, const float* alpha,
                                   const float* T, int32_t n_ray, int32_t n_z, float s, float a_tx,
                                   const float* d_w, const float* d_teff,
-                                  float* d_sdf, float* d_refl, float* d_scalars,
+                                  float* d_sdf, float* d_refl, float* d_scalars, const float* keep,
                                   void* ws, size_t* ws_bytes, void* stream);
 
 /*
@@ -421,6 +427,34 @@ geraf_status geraf_proposal_density(const geraf_proposal* p, float* logits, floa
 geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal* p, const float* q,
                                    uint64_t seed, uint64_t step, float* xyz, float* xyz_apr, int32_t* idx,
                                    void* stream);
+
+/*
+ * geraf_sample_cells — lensless samples restricted to the depth cells the
+ * proposal ranks highest (the task's learned sampler; the paper has none):
+ * the grid's n[2] fine depths per column are grouped into the proposal's G2
+ * cells of s = n[2] / G2 consecutive depths. Per grid column (the fine column
+ * (ix, iy) uses (ix*G0/nx, iy*G1/ny)) the m cells of largest q (FP32 q of
+ * geraf_proposal_density; ties go to the lower cell) are kept, and a fine
+ * column's samples are exactly the STRATIFIED grid's own points in those
+ * cells (geraf_sample with the same seed and step gives the same values bit
+ * for bit), in depth order. After each run of consecutive kept cells (the
+ * first r_max runs in depth order; not after the last cell) one more sample,
+ * the first fine depth of the next cell, closes the run: the NeuS alpha of the
+ * run's last sample then spans one fine interval, and the closing sample's own
+ * alpha spans the skipped gap to the next kept sample (exactly the gap's
+ * transmittance when f decreases through it). The column's n_out = m s +
+ * r_max slots are filled with copies of its last sample (alpha 0). keep = 1
+ * on kept-cell samples, 0 on closing and padding samples (pass it to
+ * geraf_blend). Outputs (depth-major, n = n_ray * n_out): xyz [3][n],
+ * xyz_apr [3][n_ray] (may be NULL), idx [n] = grid cell of each sample (the
+ * next cell for a closing sample), keep [n]. Requires n[2] % G2 == 0,
+ * n[0] % G0 == 0, n[1] % G1 == 0, 1 <= m <= G2, 0 <= r_max <= m; a workspace
+ * (per grid column table of n_out int32; ws == NULL queries *ws_bytes).
+ * Deterministic and bit-exact with any IEEE implementation given the same q.
+ */
+geraf_status geraf_sample_cells(const geraf_grid* grid, const geraf_proposal* p, const float* q, int32_t m,
+                                int32_t r_max, uint64_t seed, uint64_t step, float* xyz, float* xyz_apr,
+                                int32_t* idx, float* keep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
  * geraf_sample_backward — online training signal of the proposal from the

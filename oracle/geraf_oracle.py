@@ -320,9 +320,14 @@ def cdf(s, f):
     return np.exp(_log_cdf(s * np.asarray(f, np.float64)))
 
 
-def blend(sdf, refl, n_ray, n_z, sdf_apr, sdf_ant, s, a_tx):
+def blend(sdf, refl, n_ray, n_z, sdf_apr, sdf_ant, s, a_tx, keep=None):
+    """keep (optional, per sample) multiplies w: a sample with keep = 0 still
+    ends the interval of the sample before it and its own alpha still
+    attenuates T, but it reflects nothing."""
     f = np.asarray(sdf, np.float64).reshape(n_z, n_ray)
     a = np.asarray(refl, np.float64).reshape(n_z, n_ray)
+    if keep is not None:
+        a = a * np.asarray(keep, np.float64).reshape(n_z, n_ray)
     lc = _log_cdf(s * f)
     alpha = np.zeros((n_z, n_ray))
     alpha[:-1] = np.maximum(-np.expm1(lc[1:] - lc[:-1]), 0.0)
@@ -335,7 +340,7 @@ def blend(sdf, refl, n_ray, n_z, sdf_apr, sdf_ant, s, a_tx):
     return (alpha.reshape(-1), T.reshape(-1), w.reshape(-1), t_eff.reshape(-1), c_ant)
 
 
-def blend_backward(sdf, refl, n_ray, n_z, s, a_tx, d_w, d_teff):
+def blend_backward(sdf, refl, n_ray, n_z, s, a_tx, d_w, d_teff, keep=None):
     """Adjoint of blend for (w, t_eff); origin terms carry no gradient
     (section 6, stop-gradient on the ray-origin sigmoid-SDF).
     Returns (d_sdf [N], d_refl [N], d_s, d_a_tx)."""
@@ -344,6 +349,8 @@ def blend_backward(sdf, refl, n_ray, n_z, s, a_tx, d_w, d_teff):
     alpha, T, _, _, _ = blend(sdf, refl, n_ray, n_z, np.zeros(n_ray), np.zeros(1), s, a_tx)
     alpha = alpha.reshape(n_z, n_ray); T = T.reshape(n_z, n_ray)
     dw = np.asarray(d_w, np.float64).reshape(n_z, n_ray)
+    if keep is not None:                              # w = keep a alpha A'_tx
+        dw = dw * np.asarray(keep, np.float64).reshape(n_z, n_ray)
     dt = np.asarray(d_teff, np.float64).reshape(n_z, n_ray)
     d_alpha = dw * a * a_tx
     d_a = dw * alpha * a_tx
@@ -574,6 +581,51 @@ def proposal_sample(grid, gshape, q_f32, D, seed, step):
     apr = np.stack([xr, yr, np.full(n_ray, np.float32(grid.aperture_z))]).astype(np.float32)
     gcell = (cell * G1 + gyi[:, None]) * G0 + gxi[:, None]
     return xyz, apr, gcell.T.reshape(-1).astype(np.int32)
+
+
+def sample_cells(grid, gshape, q_f32, m, r_max, seed, step):
+    """Samples of the m cells of largest q per grid column (the learned
+    sampler's cell selection): the STRATIFIED grid's own points of the kept
+    cells (taken from `sample`, so bit-exact with the dense grid), in depth
+    order; after each of the first r_max runs of consecutive kept cells (not
+    after the last cell) the first fine depth of the next cell closes the run;
+    the column is padded to n_out = m s + r_max with its last sample. keep = 1
+    on kept-cell samples, 0 on the others; idx = the grid cell of each sample.
+    Returns (xyz [3, n_ray n_out], apr [3, n_ray], idx, keep, n_out)."""
+    G0, G1, G2 = gshape
+    nx, ny, nz = grid.n
+    s_fine = nz // G2
+    n_out = m * s_fine + r_max
+    n_ray = nx * ny
+    dense, apr = sample(grid, 1, seed, step)          # STRATIFIED, [3, nz n_ray]
+    q = np.asarray(q_f32, np.float32).reshape(G2, G1 * G0)
+    tables = []
+    for col in range(G1 * G0):
+        order = np.argsort(-q[:, col], kind="stable")    # largest first, ties to the lower cell
+        cells = sorted(int(c) for c in order[:m])
+        t, runs = [], 0
+        for i, c in enumerate(cells):
+            t += [(c * s_fine + d, 1) for d in range(s_fine)]
+            run_end = i + 1 == m or cells[i + 1] != c + 1
+            if run_end and runs < r_max and c + 1 < G2:
+                t.append(((c + 1) * s_fine, 0))
+                runs += 1
+        while len(t) < n_out:
+            t.append((t[-1][0], 0))
+        tables.append(t)
+    n = n_ray * n_out
+    xyz = np.zeros((3, n), np.float32)
+    idx = np.zeros(n, np.int32)
+    keep = np.zeros(n, np.float32)
+    for ray in range(n_ray):
+        ix, iy = ray % nx, ray // nx
+        col = (iy * G1 // ny) * G0 + (ix * G0 // nx)
+        for slot, (kz, kp) in enumerate(tables[col]):
+            p = slot * n_ray + ray
+            xyz[:, p] = dense[:, kz * n_ray + ray]
+            idx[p] = (kz // s_fine) * (G0 * G1) + col
+            keep[p] = kp
+    return xyz, apr, idx, keep, n_out
 
 
 def proposal_targets(omega, idx, n_cells):

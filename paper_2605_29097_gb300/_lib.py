@@ -46,8 +46,8 @@ SIGNATURES = {
     "geraf_fields_saved_bytes": [ctypes.POINTER(GerafFieldDesc), i64, szp],
     "geraf_fields": [ctypes.POINTER(GerafFieldDesc), vp, i64, vp, vp, vp, vp, sz, vp],
     "geraf_fields_backward": [ctypes.POINTER(GerafFieldDesc), vp, i64, vp, vp, vp, vp, vp, vp, szp, vp],
-    "geraf_blend": [vp, vp, i32, i32, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp, vp],
-    "geraf_blend_backward": [vp, vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp, vp, vp, szp, vp],
+    "geraf_blend": [vp, vp, i32, i32, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp, vp, vp],
+    "geraf_blend_backward": [vp, vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp, vp, vp, vp, szp, vp],
     "geraf_render": [vp, vp, vp, vp, i64, vp, vp, i32, ctypes.POINTER(GerafBand), i32, vp, szp, vp, vp],
     "geraf_render_noalloc": [vp, vp, vp, vp, i64, vp, vp, i32, ctypes.POINTER(GerafBand), i32, vp, vp],
     "geraf_render_backward": [vp, vp, vp, vp, i64, vp, vp, i32, ctypes.POINTER(GerafBand), i32, vp, vp, szp,
@@ -61,6 +61,8 @@ SIGNATURES = {
     "geraf_proposal_saved_bytes": [ctypes.POINTER(GerafProposal), szp],
     "geraf_proposal_density": [ctypes.POINTER(GerafProposal), vp, vp, vp, sz, vp],
     "geraf_sample_proposal": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, u64, u64, vp, vp, vp, vp],
+    "geraf_sample_cells": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, i32, i32, u64, u64, vp, vp,
+                           vp, vp, vp, szp, vp],
     "geraf_sample_backward": [ctypes.POINTER(GerafProposal), ctypes.POINTER(GerafGrid), i32, vp, vp, vp, vp, vp, vp,
                               vp, vp, vp, szp, vp],
 }

@@ -14,11 +14,11 @@ namespace geraf {
 // implemented in fields_blend.cu, phasor.cu, mlp.cu
 geraf_status sample_impl(const geraf_grid*, int32_t, uint64_t, uint64_t, float*, float*, cudaStream_t);
 geraf_status analytic_fields_impl(const float*, int, const float*, int64_t, float*, float*, float*, cudaStream_t);
-geraf_status blend_impl(const float*, const float*, int32_t, int32_t, const float*, const float*, int32_t, float,
-                        float, float*, float*, float*, float*, float*, cudaStream_t);
-geraf_status blend_backward_impl(const float*, const float*, const float*, const float*, int32_t, int32_t, float,
-                                 float, const float*, const float*, float*, float*, float*, void*, size_t*,
-                                 cudaStream_t);
+geraf_status blend_impl(const float*, const float*, const float*, int32_t, int32_t, const float*, const float*,
+                        int32_t, float, float, float*, float*, float*, float*, float*, cudaStream_t);
+geraf_status blend_backward_impl(const float*, const float*, const float*, const float*, const float*, int32_t,
+                                 int32_t, float, float, const float*, const float*, float*, float*, float*, void*,
+                                 size_t*, cudaStream_t);
 geraf_status render_impl(const float*, const float*, const float*, const float*, int64_t, const float*,
                          const float*, int32_t, const geraf_band*, int32_t, void*, size_t*, float*, cudaStream_t);
 geraf_status render_backward_impl(const float*, const float*, const float*, const float*, int64_t, const float*,
@@ -39,6 +39,8 @@ geraf_status chebyshev_work_impl(const float*, int64_t, const float*, int32_t, c
 geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
 geraf_status proposal_saved_bytes(const geraf_proposal*, size_t*);
 geraf_status proposal_density_impl(const geraf_proposal*, float*, float*, void*, size_t, cudaStream_t);
+geraf_status sample_cells_impl(const geraf_grid*, const geraf_proposal*, const float*, int32_t, int32_t, uint64_t,
+                               uint64_t, float*, float*, int32_t*, float*, void*, size_t*, cudaStream_t);
 geraf_status sample_proposal_impl(const geraf_grid*, const geraf_proposal*, const float*, uint64_t, uint64_t, float*,
                                   float*, int32_t*, cudaStream_t);
 geraf_status sample_backward_impl(const geraf_proposal*, const geraf_grid*, int32_t, const float*, const float*,
@@ -260,25 +262,26 @@ geraf_status geraf_fields_backward(const geraf_field_desc* desc, const float* xy
 
 geraf_status geraf_blend(const float* sdf, const float* refl, int32_t n_ray, int32_t n_z, const float* sdf_apr,
                          const float* sdf_ant, int32_t n_ant, float s, float a_tx, float* alpha, float* T, float* w,
-                         float* t_eff, float* c_ant, void* stream) {
+                         float* t_eff, float* c_ant, const float* keep, void* stream) {
     REQUIRE(n_ray >= 1 && n_z >= 1 && n_ant >= 0, "blend: bad sizes");
     REQUIRE(sdf && refl && sdf_apr && alpha && T && w && t_eff, "blend: null input or output");
     REQUIRE(n_ant == 0 || (sdf_ant && c_ant), "blend: null antenna arrays");
     REQUIRE(s > 0.0f, "blend: sharpness s must be positive");
-    return blend_impl(sdf, refl, n_ray, n_z, sdf_apr, sdf_ant, n_ant, s, a_tx, alpha, T, w, t_eff, c_ant, S(stream));
+    return blend_impl(sdf, refl, keep, n_ray, n_z, sdf_apr, sdf_ant, n_ant, s, a_tx, alpha, T, w, t_eff, c_ant,
+                      S(stream));
 }
 
 geraf_status geraf_blend_backward(const float* sdf, const float* refl, const float* alpha, const float* T,
                                   int32_t n_ray, int32_t n_z, float s, float a_tx, const float* d_w,
-                                  const float* d_teff, float* d_sdf, float* d_refl, float* d_scalars, void* ws,
-                                  size_t* ws_bytes, void* stream) {
+                                  const float* d_teff, float* d_sdf, float* d_refl, float* d_scalars,
+                                  const float* keep, void* ws, size_t* ws_bytes, void* stream) {
     geraf_status st = check_ws(ws, ws_bytes);
     if (st != GERAF_OK) return st;
     REQUIRE(n_ray >= 1 && n_z >= 1, "blend_backward: bad sizes");
     if (ws)
         REQUIRE(sdf && refl && alpha && T && d_sdf && d_refl && d_scalars, "blend_backward: null input or output");
-    return blend_backward_impl(sdf, refl, alpha, T, n_ray, n_z, s, a_tx, d_w, d_teff, d_sdf, d_refl, d_scalars, ws,
-                               ws_bytes, S(stream));
+    return blend_backward_impl(sdf, refl, keep, alpha, T, n_ray, n_z, s, a_tx, d_w, d_teff, d_sdf, d_refl, d_scalars,
+                               ws, ws_bytes, S(stream));
 }
 
 geraf_status geraf_render(const float* xyz, const float* grad, const float* w, const float* t_eff, int64_t n_pts,
@@ -412,6 +415,18 @@ geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal*
     REQUIRE((int64_t)grid->n[0] * grid->n[1] * p->depth < (1ll << 40), "sample_proposal: too many samples");
     REQUIRE(step < (1ull << 22), "sample_proposal: step must be below 2^22");
     return sample_proposal_impl(grid, p, q, seed, step, xyz, xyz_apr, idx, S(stream));
+}
+
+geraf_status geraf_sample_cells(const geraf_grid* grid, const geraf_proposal* p, const float* q, int32_t m,
+                                int32_t r_max, uint64_t seed, uint64_t step, float* xyz, float* xyz_apr, int32_t* idx,
+                                float* keep, void* ws, size_t* ws_bytes, void* stream) {
+    geraf_status st = check_ws(ws, ws_bytes);
+    if (st != GERAF_OK) return st;
+    REQUIRE(grid && p, "sample_cells: grid and proposal must not be NULL");
+    REQUIRE(grid->n[0] >= 1 && grid->n[1] >= 1 && grid->n[2] >= 1, "sample_cells: bad grid");
+    REQUIRE(step < (1ull << 22), "sample_cells: step must be below 2^22");
+    if (ws) REQUIRE(q && xyz && idx && keep, "sample_cells: null input or output");
+    return sample_cells_impl(grid, p, q, m, r_max, seed, step, xyz, xyz_apr, idx, keep, ws, ws_bytes, S(stream));
 }
 
 geraf_status geraf_sample_backward(const geraf_proposal* p, const geraf_grid* grid, int32_t n_z, const float* alpha,

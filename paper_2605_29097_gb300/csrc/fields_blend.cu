@@ -138,7 +138,8 @@ constexpr int BL_CH = 16;
 constexpr int BL_THREADS = 64;
 
 __global__ void __launch_bounds__(BL_THREADS) blend_kernel(const float* __restrict__ sdf,
-                                                           const float* __restrict__ refl, int n_ray, int n_z,
+                                                           const float* __restrict__ refl,
+                                                           const float* __restrict__ keep, int n_ray, int n_z,
                                                            const float* __restrict__ sdf_apr, float s, float a_tx,
                                                            float* __restrict__ alpha, float* __restrict__ T,
                                                            float* __restrict__ w, float* __restrict__ t_eff) {
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(BL_THREADS) blend_kernel(const float* __restri
             const int k = k0 + q;
             fv[q] = k + 1 < n_z ? sdf[(size_t)(k + 1) * n_ray + ray] : 0.0f;
             av[q] = k < n_z ? refl[(size_t)k * n_ray + ray] : 0.0f;
+            if (keep && k < n_z) av[q] *= keep[(size_t)k * n_ray + ray];
         }
 #pragma unroll
         for (int q = 0; q < BL_CH; ++q) {
@@ -183,8 +185,9 @@ __global__ void cdf_kernel(const float* __restrict__ f, int n, float s, float* _
 
 // reverse depth scan; per-ray partials of dL/ds and dL/dA'_tx in `part`
 __global__ void __launch_bounds__(BL_THREADS) blend_backward_kernel(
-    const float* __restrict__ sdf, const float* __restrict__ refl, const float* __restrict__ alpha,
-    const float* __restrict__ T, int n_ray, int n_z, float s, float a_tx, const float* __restrict__ d_w,
+    const float* __restrict__ sdf, const float* __restrict__ refl, const float* __restrict__ keep,
+    const float* __restrict__ alpha, const float* __restrict__ T, int n_ray, int n_z, float s, float a_tx,
+    const float* __restrict__ d_w,
     const float* __restrict__ d_teff, float* __restrict__ d_sdf, float* __restrict__ d_refl, float2* __restrict__ part) {
     const int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= n_ray) return;
@@ -205,6 +208,7 @@ __global__ void __launch_bounds__(BL_THREADS) blend_backward_kernel(
             alv[q] = ok ? alpha[j] : 0.0f;
             tv[q] = ok ? T[j] : 0.0f;
             dwv[q] = ok && d_w ? d_w[j] : 0.0f;
+            if (ok && keep) dwv[q] *= keep[j];     // w = keep a alpha A'_tx: d_w reaches a, alpha, A'_tx through keep
             dtv[q] = ok && d_teff ? d_teff[j] : 0.0f;
         }
 #pragma unroll
@@ -281,17 +285,17 @@ geraf_status analytic_fields_impl(const float* prims, int n_prims, const float* 
     return cuda_status(cudaGetLastError(), "fields(analytic)");
 }
 
-geraf_status blend_impl(const float* sdf, const float* refl, int32_t n_ray, int32_t n_z, const float* sdf_apr,
-                        const float* sdf_ant, int32_t n_ant, float s, float a_tx, float* alpha, float* T, float* w,
-                        float* t_eff, float* c_ant, cudaStream_t st) {
-    blend_kernel<<<grid1d(n_ray, BL_THREADS), BL_THREADS, 0, st>>>(sdf, refl, n_ray, n_z, sdf_apr, s, a_tx, alpha,
-                                                                     T, w, t_eff);
+geraf_status blend_impl(const float* sdf, const float* refl, const float* keep, int32_t n_ray, int32_t n_z,
+                        const float* sdf_apr, const float* sdf_ant, int32_t n_ant, float s, float a_tx, float* alpha,
+                        float* T, float* w, float* t_eff, float* c_ant, cudaStream_t st) {
+    blend_kernel<<<grid1d(n_ray, BL_THREADS), BL_THREADS, 0, st>>>(sdf, refl, keep, n_ray, n_z, sdf_apr, s, a_tx,
+                                                                     alpha, T, w, t_eff);
     if (n_ant > 0) cdf_kernel<<<grid1d(n_ant, 256), 256, 0, st>>>(sdf_ant, n_ant, s, c_ant);
     return cuda_status(cudaGetLastError(), "blend");
 }
 
-geraf_status blend_backward_impl(const float* sdf, const float* refl, const float* alpha, const float* T,
-                                 int32_t n_ray, int32_t n_z, float s, float a_tx, const float* d_w,
+geraf_status blend_backward_impl(const float* sdf, const float* refl, const float* keep, const float* alpha,
+                                 const float* T, int32_t n_ray, int32_t n_z, float s, float a_tx, const float* d_w,
                                  const float* d_teff, float* d_sdf, float* d_refl, float* d_scalars, void* ws,
                                  size_t* ws_bytes, cudaStream_t st) {
     WsCarver c(ws);
@@ -299,8 +303,8 @@ geraf_status blend_backward_impl(const float* sdf, const float* refl, const floa
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "blend_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
-    blend_backward_kernel<<<grid1d(n_ray, BL_THREADS), BL_THREADS, 0, st>>>(sdf, refl, alpha, T, n_ray, n_z, s,
-                                                                           a_tx, d_w, d_teff, d_sdf, d_refl, part);
+    blend_backward_kernel<<<grid1d(n_ray, BL_THREADS), BL_THREADS, 0, st>>>(sdf, refl, keep, alpha, T, n_ray, n_z,
+                                                                           s, a_tx, d_w, d_teff, d_sdf, d_refl, part);
     reduce_pairs<<<1, 256, 0, st>>>(part, n_ray, d_scalars);
     return cuda_status(cudaGetLastError(), "blend_backward");
 }

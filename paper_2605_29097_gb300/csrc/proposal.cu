@@ -189,6 +189,93 @@ __global__ void prop_sample_kernel(geraf_grid gr, PropGeom g, const float* __res
     }
 }
 
+// ------------------------------------------------- samples of selected cells
+// Depth cells of a grid column: the G2 cells of s = n_z / G2 consecutive fine
+// depths each. Per grid column the m cells with the largest q (ties: the lower
+// cell index) are kept; a fine column samples exactly the stratified grid's
+// own points of those cells (bit for bit the points of a dense STRATIFIED
+// geraf_sample with the same seed and step), so the kept part of the column is
+// the dense render's; after each run of consecutive kept cells (the first
+// r_max runs in depth order, and not past the last cell) one more sample, the
+// first fine depth of the next cell, closes the run's last interval (its alpha
+// uses f there, not at the next kept sample); that sample and the padding
+// that fills the column's n_out = m s + r_max slots (copies of its last
+// sample, so their alpha is 0) carry keep = 0.
+// Table per grid column [n_out]: fine depth | (keep << 30).
+__global__ void cells_select_kernel(PropGeom g, int s_fine, int m, int r_max, int n_out, const float* __restrict__ q,
+                                    int32_t* __restrict__ table) {
+    __shared__ float qs[256];
+    __shared__ int sel[256];
+    __shared__ int list[256];
+    const int col = blockIdx.x, k = threadIdx.x;
+    const int plane = g.G0 * g.G1;
+    if (k < g.G2) qs[k] = q[(int64_t)k * plane + col];
+    __syncthreads();
+    int keep_k = 0;
+    if (k < g.G2) {
+        const float v = qs[k];
+        int rank = 0;
+        for (int j = 0; j < g.G2; ++j) rank += (qs[j] > v || (qs[j] == v && j < k)) ? 1 : 0;
+        keep_k = rank < m;
+    }
+    sel[k] = keep_k;
+    __syncthreads();
+    if (keep_k) {
+        int pos = 0;
+        for (int j = 0; j < k; ++j) pos += sel[j];
+        list[pos] = k;
+    }
+    __syncthreads();
+    if (k == 0) {
+        int32_t* t = table + (int64_t)col * n_out;
+        int o = 0, runs = 0;
+        for (int i = 0; i < m; ++i) {
+            const int c = list[i];
+            for (int d = 0; d < s_fine; ++d) t[o++] = (c * s_fine + d) | (1 << 30);
+            const bool run_end = i + 1 == m || list[i + 1] != c + 1;
+            if (run_end && runs < r_max && c + 1 < g.G2) {
+                t[o++] = (c + 1) * s_fine;
+                ++runs;
+            }
+        }
+        const int32_t last = t[o - 1] & ~(1 << 30);
+        while (o < n_out) t[o++] = last;
+    }
+}
+
+// thread = (fine column, slot): the slot's stratified grid point
+__global__ void cells_sample_kernel(geraf_grid gr, PropGeom g, int s_fine, int n_out,
+                                    const int32_t* __restrict__ table, uint64_t seed, uint64_t step,
+                                    float* __restrict__ xyz, float* __restrict__ apr, int32_t* __restrict__ idx,
+                                    float* __restrict__ keep) {
+    const int64_t n_ray = (int64_t)gr.n[0] * gr.n[1];
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_ray * n_out) return;
+    const int64_t slot = e / n_ray, ray = e - slot * n_ray;
+    const int64_t n = n_ray * n_out;
+    const int64_t ix = ray % gr.n[0], iy = ray / gr.n[0];
+    const int gx = (int)(ix * g.G0 / gr.n[0]), gy = (int)(iy * g.G1 / gr.n[1]);
+    const int col = gy * g.G0 + gx;
+    const int32_t code = table[(int64_t)col * n_out + slot];
+    const int64_t kz = code & ~(1 << 30);
+    const uint64_t s0 = step << 42;
+    const double ux = (double)(splitmix64(seed, s0 | (0ull << 40) | (uint64_t)ray) >> 11) * 0x1.0p-53;
+    const double uy = (double)(splitmix64(seed, s0 | (1ull << 40) | (uint64_t)ray) >> 11) * 0x1.0p-53;
+    const double uz = (double)(splitmix64(seed, s0 | (2ull << 40) | (uint64_t)(kz * n_ray + ray)) >> 11) * 0x1.0p-53;
+    const float x = grid_coord(gr.lo[0], ix, ux, gr.pitch[0]);
+    const float y = grid_coord(gr.lo[1], iy, uy, gr.pitch[1]);
+    xyz[e] = x;
+    xyz[n + e] = y;
+    xyz[2 * n + e] = grid_coord(gr.lo[2], kz, uz, gr.pitch[2]);
+    idx[e] = (int32_t)((kz / s_fine) * (g.G0 * g.G1) + col);
+    keep[e] = (code >> 30) & 1 ? 1.0f : 0.0f;
+    if (apr && slot == 0) {
+        apr[ray] = x;
+        apr[n_ray + ray] = y;
+        apr[2 * n_ray + ray] = gr.aperture_z;
+    }
+}
+
 // --------------------------------------------------------- targets and loss
 // histogram of T alpha over grid cells, gathered per cell in a fixed order
 __global__ void prop_hist_kernel(geraf_grid gr, PropGeom g, int n_z, const float* __restrict__ alpha,
@@ -421,6 +508,30 @@ geraf_status sample_proposal_impl(const geraf_grid* gr, const geraf_proposal* p,
     const int64_t n_ray = (int64_t)gr->n[0] * gr->n[1];
     prop_sample_kernel<<<g1(n_ray, 128), 128, 0, st>>>(*gr, g, q, seed, step, pz_cell, xyz, apr, idx);
     return cuda_status(cudaGetLastError(), "sample_proposal");
+}
+
+geraf_status sample_cells_impl(const geraf_grid* gr, const geraf_proposal* p, const float* q, int32_t m,
+                               int32_t r_max, uint64_t seed, uint64_t step, float* xyz, float* apr, int32_t* idx,
+                               float* keep, void* ws, size_t* ws_bytes, cudaStream_t st) {
+    PropGeom g;
+    if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
+    if (gr->n[2] % g.G2 != 0 || gr->n[0] % g.G0 != 0 || gr->n[1] % g.G1 != 0)
+        return fail(GERAF_ERR_INVALID_ARG, "sample_cells: the grid's columns and depths must be multiples of the "
+                                           "proposal grid's");
+    if (m < 1 || m > g.G2 || r_max < 0 || r_max > m)
+        return fail(GERAF_ERR_INVALID_ARG, "sample_cells: need 1 <= m <= G2 and 0 <= r_max <= m");
+    const int s_fine = gr->n[2] / g.G2;
+    const int n_out = m * s_fine + r_max;
+    const int plane = g.G0 * g.G1;
+    WsCarver c(ws);
+    int32_t* table = c.take<int32_t>((size_t)plane * n_out);
+    if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
+    if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "sample_cells: workspace %zu < %zu bytes", *ws_bytes, c.used);
+    cells_select_kernel<<<plane, 256, 0, st>>>(g, s_fine, m, r_max, n_out, q, table);
+    const int64_t n_ray = (int64_t)gr->n[0] * gr->n[1];
+    cells_sample_kernel<<<g1(n_ray * n_out, 256), 256, 0, st>>>(*gr, g, s_fine, n_out, table, seed, step, xyz, apr,
+                                                               idx, keep);
+    return cuda_status(cudaGetLastError(), "sample_cells");
 }
 
 geraf_status sample_backward_impl(const geraf_proposal* p, const geraf_grid* gr, int32_t n_z, const float* alpha,

@@ -184,22 +184,25 @@ def geraf_fields_backward(field, xyz, saved, d_sdf=None, d_grad=None, d_refl=Non
     return d_params
 
 
-def geraf_blend(sdf, refl, n_ray: int, n_z: int, sdf_apr, sdf_ant, s: float, a_tx: float):
-    """Lensless alpha blending -> (alpha, T, w, t_eff, c_ant)."""
+def geraf_blend(sdf, refl, n_ray: int, n_z: int, sdf_apr, sdf_ant, s: float, a_tx: float, keep=None):
+    """Lensless alpha blending -> (alpha, T, w, t_eff, c_ant); `keep` (optional,
+    per sample) multiplies w, as for the padding samples of geraf_sample_cells."""
     for t, nm in ((sdf, "sdf"), (refl, "refl"), (sdf_apr, "sdf_apr"), (sdf_ant, "sdf_ant")):
         _req(t, nm)
+    if keep is not None:
+        _req(keep, "keep")
     n = n_ray * n_z
     dev = sdf.device
     alpha, T, w, t_eff = (torch.empty(n, dtype=torch.float32, device=dev) for _ in range(4))
     c_ant = torch.empty(sdf_ant.numel(), dtype=torch.float32, device=dev)
     check(_lib.lib().geraf_blend(_p(sdf), _p(refl), n_ray, n_z, _p(sdf_apr), _p(sdf_ant), sdf_ant.numel(),
                                  float(s), float(a_tx), _p(alpha), _p(T), _p(w), _p(t_eff), _p(c_ant),
-                                 _stream()))
+                                 _p(keep), _stream()))
     return alpha, T, w, t_eff, c_ant
 
 
-def geraf_blend_backward(sdf, refl, alpha, T, n_ray, n_z, s, a_tx, d_w=None, d_teff=None):
-    """-> (d_sdf, d_refl, d_scalars [2] = (dL/ds, dL/dA'_tx))."""
+def geraf_blend_backward(sdf, refl, alpha, T, n_ray, n_z, s, a_tx, d_w=None, d_teff=None, keep=None):
+    """-> (d_sdf, d_refl, d_scalars [2] = (dL/ds, dL/dA'_tx)); `keep` as in geraf_blend."""
     n = n_ray * n_z
     dev = sdf.device
     d_sdf = torch.empty(n, dtype=torch.float32, device=dev)
@@ -208,7 +211,7 @@ def geraf_blend_backward(sdf, refl, alpha, T, n_ray, n_z, s, a_tx, d_w=None, d_t
     L = _lib.lib()
     args = lambda w, b: L.geraf_blend_backward(_p(sdf), _p(refl), _p(alpha), _p(T), n_ray, n_z, float(s),
                                                float(a_tx), _p(d_w), _p(d_teff), _p(d_sdf), _p(d_refl), _p(d_sc),
-                                               w, b, _stream())
+                                               _p(keep), w, b, _stream())
     ws, wsz = _workspace(args, dev)
     check(args(_p(ws), ctypes.byref(wsz)))
     return d_sdf, d_refl, d_sc
@@ -417,6 +420,29 @@ def geraf_sample_proposal(grid: GerafGrid, prop: Proposal, q, seed=0, step=0):
     check(_lib.lib().geraf_sample_proposal(ctypes.byref(grid), ctypes.byref(cp), _p(_req(q, "q")), int(seed),
                                            int(step), _p(xyz), _p(apr), _p(idx), _stream()))
     return xyz, apr, idx
+
+
+def geraf_sample_cells(grid: GerafGrid, prop: Proposal, q, m: int, r_max: int, seed=0, step=0):
+    """Stratified grid samples of the m proposal cells of largest q per column,
+    with run-closing samples -> (xyz [3, n_ray*n_out], xyz_apr [3, n_ray],
+    idx int32 [n_ray*n_out], keep [n_ray*n_out], n_out = m s + r_max)."""
+    dev = prop.features.device
+    n_ray = grid.n[0] * grid.n[1]
+    s_fine = grid.n[2] // prop.gshape[2]
+    n_out = m * s_fine + r_max
+    n = n_ray * n_out
+    xyz = torch.empty(3, n, dtype=torch.float32, device=dev)
+    apr = torch.empty(3, n_ray, dtype=torch.float32, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    keep = torch.empty(n, dtype=torch.float32, device=dev)
+    cp = prop.c()
+    L = _lib.lib()
+    args = lambda w, b: L.geraf_sample_cells(ctypes.byref(grid), ctypes.byref(cp), _p(_req(q, "q")), int(m),
+                                             int(r_max), int(seed), int(step), _p(xyz), _p(apr), _p(idx), _p(keep),
+                                             w, b, _stream())
+    ws, wsz = _workspace(args, dev)
+    check(args(_p(ws), ctypes.byref(wsz)))
+    return xyz, apr, idx, keep, n_out
 
 
 def geraf_sample_backward(prop: Proposal, grid: GerafGrid, n_z: int, alpha, T, idx, logits, saved):

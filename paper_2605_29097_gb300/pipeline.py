@@ -254,6 +254,65 @@ def proposal_forward_backward(geo: Geometry, field, prop, target, seed: int, ste
     return res
 
 
+def cells_forward_backward(geo: Geometry, field, prop, target, m: int, r_max: int, seed: int, step: int,
+                           q=None, timers=None, train_proposal=True):
+    """One hot-path pass on the stratified grid's own samples in the m proposal
+    cells of largest q per column (geraf_sample_cells: closing samples after
+    each run, keep = 0 on closing and padding samples), plus the proposal's
+    training signal from this pass's blended weights. `q` overrides the
+    proposal's own distribution (for measurements)."""
+    def tic(name):
+        if timers is not None and name in timers:
+            timers[name][0].record()
+
+    def toc(name):
+        if timers is not None and name in timers:
+            timers[name][1].record()
+
+    logits, q_prop, psaved = G.geraf_proposal_density(prop)
+    xyz, apr, idx, keep, n_out = G.geraf_sample_cells(geo.grid, prop, q_prop if q is None else q, m, r_max, seed,
+                                                      step)
+    is_mlp = isinstance(field, G.MLPField)
+    f, grad, a, saved = G.geraf_fields(field, xyz, keep_saved=is_mlp)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+    alpha, T, w, t_eff, c_ant = G.geraf_blend(f, a, geo.n_ray, n_out, fa, fn, geo.sharpness, geo.a_tx, keep)
+    tic("render")
+    s = G.geraf_render(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band)
+    toc("render")
+    P, M, loss, dP = G.geraf_filter(s, geo.ant, geo.band, geo.vox, target)
+    g_s = G.geraf_filter_backward(geo.ant, geo.band, geo.vox, M, dP)
+    tic("render_backward")
+    d_w, d_t, d_G = G.geraf_render_backward(xyz, grad, w, t_eff, geo.ant, c_ant, geo.band, g_s)
+    toc("render_backward")
+    d_f, d_a, d_sc = G.geraf_blend_backward(f, a, alpha, T, geo.n_ray, n_out, geo.sharpness, geo.a_tx, d_w, d_t,
+                                            keep)
+    d_params = G.geraf_fields_backward(field, xyz, saved, d_f, d_G, d_a) if is_mlp else None
+    res = StepResult(loss, d_params, d_sc, P)
+    res.n_out = n_out
+    res.proposal = (G.geraf_sample_backward(prop, geo.grid, n_out, alpha, T, idx, logits, psaved)
+                    if train_proposal else None)
+    return res
+
+
+def dense_weight_histogram(geo: Geometry, field, gshape, seed: int, step: int):
+    """Measurement helper: per proposal grid column, the normalised histogram
+    of the dense stratified render's geometric weights T alpha over its G2
+    depth cells (fine columns of a grid column pooled), as FP32 q [n_cells]
+    ordered (gz, gy, gx): the distribution a perfect proposal would learn."""
+    G0, G1, G2 = gshape
+    xyz, apr = G.geraf_sample(geo.grid, geo.mode, seed, step, device=geo.ant.device)
+    f, _, a, _ = G.geraf_fields(field, xyz, want_grad=False)
+    fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)
+    fn, _, _, _ = G.geraf_fields(field, geo.ant, want_grad=False, want_refl=False)
+    alpha, T, _, _, _ = G.geraf_blend(f, a, geo.n_ray, geo.n_z, fa, fn, geo.sharpness, geo.a_tx)
+    nx, ny, nz = geo.grid.n[0], geo.grid.n[1], geo.grid.n[2]
+    # depth-major [nz][ny][nx] -> [cell z, fine z, grid y, fine y, grid x, fine x], summed over the fine axes
+    h = (T * alpha).double().view(G2, nz // G2, G1, ny // G1, G0, nx // G0).sum(dim=(1, 3, 5))
+    h = h / h.sum(dim=0, keepdim=True).clamp_min(1e-300)
+    return h.float().contiguous().reshape(-1)
+
+
 def proposal_signal_dense(geo: Geometry, field, prop, seed: int, step: int):
     """Proposal training signal from a dense regular-grid render of `field`
     (geo.grid's own depths, a multiple of the proposal's G2)."""

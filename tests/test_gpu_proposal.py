@@ -93,3 +93,54 @@ def test_training_signal_matches_oracle(G, oracle, use_idx):
     odp, odf = oracle.proposal_backward(feats.reshape(-1, 8), params, 64, 3, 10.0, cache, od)
     assert rel(d_p.cpu().numpy(), odp) < 1e-5
     assert rel(d_f.cpu().numpy().reshape(-1, 8), odf) < 1e-5
+
+
+@pytest.mark.parametrize("m,r_max", [(5, 2), (16, 16), (1, 0)])
+def test_sample_cells_bit_exact(G, oracle, m, r_max):
+    """Cell-subset sampling from the network's own FP32 q (with ties planted
+    in q): points, ray starts, cell indices and keep flags bit-exact with the
+    oracle, which takes the points from the dense stratified grid."""
+    prop, _, _ = _prop(G, gshape=(8, 4, 16))
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.08, (32, 24, 64))
+    grid = G.make_grid(g.lo, g.pitch, g.n, g.aperture_z)
+    _, q, _ = G.geraf_proposal_density(prop)
+    qh = q.cpu().numpy().copy().reshape(16, 4 * 8)      # [gz][gy gx]
+    qh[3, :] = qh[7, :]                                   # ties between cells 3 and 7 of every column
+    qh = qh.ravel()
+    q = torch.as_tensor(qh, device="cuda")
+    xyz, apr, idx, keep, n_out = G.geraf_sample_cells(grid, prop, q, m, r_max, seed=5, step=3)
+    G.geraf_poll_device_error()
+    ox, oa, oi, ok, on = oracle.sample_cells(g, (8, 4, 16), qh, m, r_max, seed=5, step=3)
+    assert n_out == on
+    np.testing.assert_array_equal(xyz.cpu().numpy().view(np.uint32), ox.view(np.uint32))
+    np.testing.assert_array_equal(apr.cpu().numpy().view(np.uint32), oa.view(np.uint32))
+    np.testing.assert_array_equal(idx.cpu().numpy(), oi)
+    np.testing.assert_array_equal(keep.cpu().numpy(), ok)
+
+
+def test_blend_keep_and_backward(G, oracle):
+    """geraf_blend with a keep mask (w = keep a alpha A'_tx) and its adjoint
+    against the oracle at 1e-5 (the dL/df tolerance of the plain blend, 1e-4)."""
+    rng = np.random.default_rng(12)
+    n_ray, n_z = 301, 37
+    sdf = np.cumsum(-rng.uniform(0.0, 0.002, (n_z, n_ray)), axis=0).astype(np.float32).ravel() + 0.02
+    refl = rng.uniform(0.2, 1.0, n_ray * n_z).astype(np.float32)
+    keep = (rng.uniform(0, 1, n_ray * n_z) < 0.7).astype(np.float32)
+    apr = rng.uniform(-0.01, 0.03, n_ray).astype(np.float32)
+    ant = rng.uniform(-0.01, 0.03, 17).astype(np.float32)
+    s, atx = np.float32(500.0), np.float32(1.3)
+    cu = lambda x: torch.as_tensor(x, device="cuda")
+    al, T, w, te, ca = G.geraf_blend(cu(sdf), cu(refl), n_ray, n_z, cu(apr), cu(ant), float(s), float(atx), cu(keep))
+    G.geraf_poll_device_error()
+    oal, oT, ow, ote, oca = oracle.blend(sdf, refl, n_ray, n_z, apr, ant, s, atx, keep)
+    assert rel(w.cpu().numpy(), ow) < 1e-5 and rel(T.cpu().numpy(), oT) < 1e-5
+    assert np.all(w.cpu().numpy()[keep == 0] == 0.0)
+    d_w = rng.standard_normal(n_ray * n_z).astype(np.float32)
+    d_t = rng.standard_normal(n_ray * n_z).astype(np.float32)
+    d_f, d_a, d_sc = G.geraf_blend_backward(cu(sdf), cu(refl), al, T, n_ray, n_z, float(s), float(atx), cu(d_w),
+                                            cu(d_t), cu(keep))
+    G.geraf_poll_device_error()
+    od_f, od_a, od_s, od_atx = oracle.blend_backward(sdf, refl, n_ray, n_z, s, atx, d_w, d_t, keep)
+    assert rel(d_f.cpu().numpy(), od_f) < 1e-4
+    assert rel(d_a.cpu().numpy(), od_a) < 1e-5
+    np.testing.assert_allclose(d_sc.cpu().numpy(), [od_s, od_atx], rtol=1e-4)

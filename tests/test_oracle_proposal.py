@@ -104,3 +104,96 @@ def test_uniform_proposal_is_stratified_closed_form(oracle):
     pz = np.float64(np.float32(g.pitch[2] * 64 / 64))
     want = (np.float64(np.float32(g.lo[2])) + (u + 0.5) / 2.0 ** 14 * pz).astype(np.float32)
     np.testing.assert_array_equal(xyz[2].reshape(16, -1), want)
+
+
+def _cells_case(oracle, q_fn, m, r_max, gshape=(3, 2, 12), n=(6, 4, 48)):
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.06, n)
+    G0, G1, G2 = gshape
+    q = q_fn(np.random.default_rng(3), G2, G1 * G0).astype(np.float32)
+    return g, q, oracle.sample_cells(g, gshape, q, m, r_max, seed=11, step=2)
+
+
+def test_sample_cells_selection_and_layout(oracle):
+    """Top-m cells of q per grid column (ties to the lower cell), in depth
+    order; every kept sample is the dense STRATIFIED grid's own point; one
+    closing sample (the next cell's first depth) after each of the first
+    r_max runs; padding repeats the column's last sample; keep and idx."""
+    G0, G1, G2 = 3, 2, 12
+    def q_fn(rng, g2, cols):
+        q = rng.uniform(0.0, 1.0, (g2, cols))
+        q[5, :] = q[6, :] = 2.0                            # a tie: cells 5 and 6 both kept
+        q[9, 0] = q[3, 0] = 1.5
+        return q
+    m, r_max = 5, 2
+    g, q, (xyz, apr, idx, keep, n_out) = _cells_case(oracle, q_fn, m, r_max)
+    s_fine = g.n[2] // G2
+    assert n_out == m * s_fine + r_max
+    dense, dapr = oracle.sample(g, gi.SAMPLE_STRATIFIED, seed=11, step=2)
+    assert np.array_equal(apr.view(np.uint32), dapr.view(np.uint32))
+    n_ray = g.n[0] * g.n[1]
+    for ray in range(n_ray):
+        ix, iy = ray % g.n[0], ray // g.n[0]
+        col = (iy * G1 // g.n[1]) * G0 + (ix * G0 // g.n[0])
+        want = sorted(sorted(range(G2), key=lambda c: (-q[c, col], c))[:m])
+        slots = [s * n_ray + ray for s in range(n_out)]
+        z = xyz[2, slots]
+        kp = keep[slots]
+        cells = idx[slots] // (G0 * G1)
+        assert sorted(set(cells[kp == 1])) == want
+        assert (kp == 1).sum() == m * s_fine
+        # every sample is a dense grid point of this column, in depth order
+        dz = dense[2, ray::n_ray]
+        k_of = [int(np.nonzero(dz == zz)[0][0]) for zz in z]
+        assert all(np.array_equal(xyz[:, p].view(np.uint32), dense[:, k * n_ray + ray].view(np.uint32))
+                   for p, k in zip(slots, k_of))
+        assert all(b >= a for a, b in zip(k_of, k_of[1:]))
+        # closing samples: first depth of the cell after a run, keep 0
+        runs = [c for i, c in enumerate(want) if i + 1 == m or want[i + 1] != c + 1]
+        closing = [(c + 1) * s_fine for c in runs if c + 1 < G2][:r_max]
+        emitted = [k for k, kk in zip(k_of, kp) if kk == 0]
+        assert emitted[:len(closing)] == closing
+        assert all(k == k_of[-1] for k in emitted[len(closing):])   # padding
+
+
+def test_sample_cells_blend_equals_dense_blend_through_closed_gaps(oracle):
+    """NeuS alpha telescopes: prod (1 - alpha) over consecutive samples is
+    Phi(f_end)/Phi(f_start) where f decreases. On a column whose SDF falls
+    monotonically in depth (a plane facing the array), the kept samples'
+    T and w from the cell subset (closing samples: keep 0) equal the dense
+    grid's at the same points; without the closing samples they do not."""
+    G0, G1, G2 = 3, 2, 12
+    def q_fn(rng, g2, cols):
+        q = np.zeros((g2, cols))
+        q[[0, 1, 5, 8, 9], :] = 1.0                        # runs {0, 1}, {5}, {8, 9}: every gap closed
+        return q
+    g, q, (xyz, apr, idx, keep, n_out) = _cells_case(oracle, q_fn, 5, 3)
+    n_ray = g.n[0] * g.n[1]
+    dense, dapr = oracle.sample(g, gi.SAMPLE_STRATIFIED, seed=11, step=2)
+    z_plane, s_sharp = 0.15, 400.0
+    f_of = lambda x: z_plane - x[2].astype(np.float64)   # decreasing in depth
+    a_of = lambda x: 0.5 + 0.1 * np.sin(40.0 * x[0].astype(np.float64))
+    al_d, T_d, w_d, _, _ = oracle.blend(f_of(dense), a_of(dense), n_ray, g.n[2], np.zeros(n_ray), np.zeros(1),
+                                        s_sharp, 1.0)
+    al_s, T_s, w_s, _, _ = oracle.blend(f_of(xyz), a_of(xyz), n_ray, n_out, np.zeros(n_ray), np.zeros(1), s_sharp,
+                                        1.0, keep)
+    dz = dense[2].reshape(g.n[2], n_ray)
+    for p in np.nonzero(keep == 1)[0]:
+        ray = p % n_ray
+        k = int(np.nonzero(dz[:, ray] == xyz[2, p])[0][0])
+        j = k * n_ray + ray
+        np.testing.assert_allclose(T_s[p], T_d[j], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(w_s[p], w_d[j], rtol=1e-12, atol=1e-15)
+    assert np.all(w_s[keep == 0] == 0.0)
+    # without closing samples the alpha of each run's last sample spans the
+    # gap: T after the gap still telescopes, but that sample's w takes the
+    # whole gap's opacity
+    _, q2, (xyz2, _, _, keep2, n2) = _cells_case(oracle, q_fn, 5, 0)
+    _, T2, w2, _, _ = oracle.blend(f_of(xyz2), a_of(xyz2), n_ray, n2, np.zeros(n_ray), np.zeros(1), s_sharp, 1.0,
+                                   keep2)
+    dev = []
+    for p in np.nonzero(keep2 == 1)[0]:
+        ray = p % n_ray
+        j = int(np.nonzero(dz[:, ray] == xyz2[2, p])[0][0]) * n_ray + ray
+        np.testing.assert_allclose(T2[p], T_d[j], rtol=1e-12, atol=1e-15)
+        dev.append(abs(w2[p] - w_d[j]) / abs(w_d).max())
+    assert max(dev) > 1e-3
