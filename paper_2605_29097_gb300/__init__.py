@@ -7,7 +7,7 @@ from .geraf import (AnalyticField, Band, MLPField, make_grid, geraf_sample, gera
                     geraf_fields_backward, geraf_blend, geraf_blend_backward, geraf_render,
                     geraf_render_backward, geraf_filter, geraf_filter_backward, geraf_poll_device_error,
                     geraf_check_bounded_wait,
-                    geraf_render_noalloc, Proposal, geraf_proposal_density, geraf_sample_proposal,
+                    geraf_render_noalloc, Proposal, geraf_proposal_density, geraf_sample_proposal, geraf_sample_cells,
                     geraf_sample_backward, geraf_chebyshev_order, geraf_chebyshev_work, geraf_masked_loss,
                     SAMPLE_UNIFORM, SAMPLE_STRATIFIED, PREC_FP32, PREC_BF16,
                     PHASOR_AUTO, PHASOR_RECURRENCE, PHASOR_CHEBYSHEV)
@@ -18,5 +18,6 @@ __all__ = ["AnalyticField", "Band", "MLPField", "make_grid", "geraf_sample", "ge
            "geraf_render_backward", "geraf_filter", "geraf_filter_backward", "geraf_poll_device_error",
            "geraf_check_bounded_wait",
            "GerafError", "geraf_render_noalloc", "Proposal", "geraf_proposal_density", "geraf_sample_proposal",
+           "geraf_sample_cells",
            "geraf_sample_backward", "geraf_chebyshev_order", "geraf_chebyshev_work", "geraf_masked_loss", "SAMPLE_UNIFORM", "SAMPLE_STRATIFIED", "PREC_FP32",
            "PREC_BF16", "PHASOR_AUTO", "PHASOR_RECURRENCE", "PHASOR_CHEBYSHEV"]
