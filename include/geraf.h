@@ -433,8 +433,11 @@ geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal*
  * proposal ranks highest (the task's learned sampler; the paper has none):
  * the grid's n[2] fine depths per column are grouped into the proposal's G2
  * cells of s = n[2] / G2 consecutive depths. Per grid column (the fine column
- * (ix, iy) uses (ix*G0/nx, iy*G1/ny)) the m cells of largest q (FP32 q of
- * geraf_proposal_density; ties go to the lower cell) are kept, and a fine
+ * (ix, iy) uses (ix*G0/nx, iy*G1/ny)) the m cells ranked first are kept: by
+ * the largest q within `dilate` cells of the cell (dilate = 0: its own q),
+ * then by its own q, then the lower cell (FP32 q of geraf_proposal_density),
+ * so that with dilate > 0 the neighbours of a peak, where the tails of its
+ * weight lie, come before lone cells elsewhere. A fine
  * column's samples are exactly the STRATIFIED grid's own points in those
  * cells (geraf_sample with the same seed and step gives the same values bit
  * for bit), in depth order. After each run of consecutive kept cells (the
@@ -448,13 +451,14 @@ geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal*
  * geraf_blend). Outputs (depth-major, n = n_ray * n_out): xyz [3][n],
  * xyz_apr [3][n_ray] (may be NULL), idx [n] = grid cell of each sample (the
  * next cell for a closing sample), keep [n]. Requires n[2] % G2 == 0,
- * n[0] % G0 == 0, n[1] % G1 == 0, 1 <= m <= G2, 0 <= r_max <= m; a workspace
+ * n[0] % G0 == 0, n[1] % G1 == 0, 1 <= m <= G2, 0 <= r_max <= m,
+ * 0 <= dilate < G2; a workspace
  * (per grid column table of n_out int32; ws == NULL queries *ws_bytes).
  * Deterministic and bit-exact with any IEEE implementation given the same q.
  */
 geraf_status geraf_sample_cells(const geraf_grid* grid, const geraf_proposal* p, const float* q, int32_t m,
-                                int32_t r_max, uint64_t seed, uint64_t step, float* xyz, float* xyz_apr,
-                                int32_t* idx, float* keep, void* ws, size_t* ws_bytes, void* stream);
+                                int32_t r_max, int32_t dilate, uint64_t seed, uint64_t step, float* xyz,
+                                float* xyz_apr, int32_t* idx, float* keep, void* ws, size_t* ws_bytes, void* stream);
 
 /*
  * geraf_sample_backward — online training signal of the proposal from the

@@ -583,13 +583,15 @@ def proposal_sample(grid, gshape, q_f32, D, seed, step):
     return xyz, apr, gcell.T.reshape(-1).astype(np.int32)
 
 
-def sample_cells(grid, gshape, q_f32, m, r_max, seed, step):
+def sample_cells(grid, gshape, q_f32, m, r_max, seed, step, dilate=0):
     """Samples of the m cells of largest q per grid column (the learned
     sampler's cell selection): the STRATIFIED grid's own points of the kept
     cells (taken from `sample`, so bit-exact with the dense grid), in depth
     order; after each of the first r_max runs of consecutive kept cells (not
     after the last cell) the first fine depth of the next cell closes the run;
-    the column is padded to n_out = m s + r_max with its last sample. keep = 1
+    the column is padded to n_out = m s + r_max with its last sample. Cells are
+    ranked by the largest q within `dilate` cells, then their own q, then the
+    lower index. keep = 1
     on kept-cell samples, 0 on the others; idx = the grid cell of each sample.
     Returns (xyz [3, n_ray n_out], apr [3, n_ray], idx, keep, n_out)."""
     G0, G1, G2 = gshape
@@ -601,7 +603,9 @@ def sample_cells(grid, gshape, q_f32, m, r_max, seed, step):
     q = np.asarray(q_f32, np.float32).reshape(G2, G1 * G0)
     tables = []
     for col in range(G1 * G0):
-        order = np.argsort(-q[:, col], kind="stable")    # largest first, ties to the lower cell
+        qc = q[:, col].astype(np.float64)
+        qd = np.array([qc[max(0, k - dilate):k + dilate + 1].max() for k in range(G2)])
+        order = np.lexsort((np.arange(G2), -qc, -qd))    # dilated q, own q, lower cell
         cells = sorted(int(c) for c in order[:m])
         t, runs = [], 0
         for i, c in enumerate(cells):

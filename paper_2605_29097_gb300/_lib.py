@@ -61,8 +61,8 @@ SIGNATURES = {
     "geraf_proposal_saved_bytes": [ctypes.POINTER(GerafProposal), szp],
     "geraf_proposal_density": [ctypes.POINTER(GerafProposal), vp, vp, vp, sz, vp],
     "geraf_sample_proposal": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, u64, u64, vp, vp, vp, vp],
-    "geraf_sample_cells": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, i32, i32, u64, u64, vp, vp,
-                           vp, vp, vp, szp, vp],
+    "geraf_sample_cells": [ctypes.POINTER(GerafGrid), ctypes.POINTER(GerafProposal), vp, i32, i32, i32, u64, u64, vp,
+                           vp, vp, vp, vp, szp, vp],
     "geraf_sample_backward": [ctypes.POINTER(GerafProposal), ctypes.POINTER(GerafGrid), i32, vp, vp, vp, vp, vp, vp,
                               vp, vp, vp, szp, vp],
 }

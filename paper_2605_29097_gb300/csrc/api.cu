@@ -39,8 +39,8 @@ geraf_status chebyshev_work_impl(const float*, int64_t, const float*, int32_t, c
 geraf_status mlp_saved_bytes(const geraf_field_desc*, int64_t, size_t*);
 geraf_status proposal_saved_bytes(const geraf_proposal*, size_t*);
 geraf_status proposal_density_impl(const geraf_proposal*, float*, float*, void*, size_t, cudaStream_t);
-geraf_status sample_cells_impl(const geraf_grid*, const geraf_proposal*, const float*, int32_t, int32_t, uint64_t,
-                               uint64_t, float*, float*, int32_t*, float*, void*, size_t*, cudaStream_t);
+geraf_status sample_cells_impl(const geraf_grid*, const geraf_proposal*, const float*, int32_t, int32_t, int32_t,
+                               uint64_t, uint64_t, float*, float*, int32_t*, float*, void*, size_t*, cudaStream_t);
 geraf_status sample_proposal_impl(const geraf_grid*, const geraf_proposal*, const float*, uint64_t, uint64_t, float*,
                                   float*, int32_t*, cudaStream_t);
 geraf_status sample_backward_impl(const geraf_proposal*, const geraf_grid*, int32_t, const float*, const float*,
@@ -418,15 +418,16 @@ geraf_status geraf_sample_proposal(const geraf_grid* grid, const geraf_proposal*
 }
 
 geraf_status geraf_sample_cells(const geraf_grid* grid, const geraf_proposal* p, const float* q, int32_t m,
-                                int32_t r_max, uint64_t seed, uint64_t step, float* xyz, float* xyz_apr, int32_t* idx,
-                                float* keep, void* ws, size_t* ws_bytes, void* stream) {
+                                int32_t r_max, int32_t dilate, uint64_t seed, uint64_t step, float* xyz,
+                                float* xyz_apr, int32_t* idx, float* keep, void* ws, size_t* ws_bytes, void* stream) {
     geraf_status st = check_ws(ws, ws_bytes);
     if (st != GERAF_OK) return st;
     REQUIRE(grid && p, "sample_cells: grid and proposal must not be NULL");
     REQUIRE(grid->n[0] >= 1 && grid->n[1] >= 1 && grid->n[2] >= 1, "sample_cells: bad grid");
     REQUIRE(step < (1ull << 22), "sample_cells: step must be below 2^22");
     if (ws) REQUIRE(q && xyz && idx && keep, "sample_cells: null input or output");
-    return sample_cells_impl(grid, p, q, m, r_max, seed, step, xyz, xyz_apr, idx, keep, ws, ws_bytes, S(stream));
+    return sample_cells_impl(grid, p, q, m, r_max, dilate, seed, step, xyz, xyz_apr, idx, keep, ws, ws_bytes,
+                             S(stream));
 }
 
 geraf_status geraf_sample_backward(const geraf_proposal* p, const geraf_grid* grid, int32_t n_z, const float* alpha,

@@ -191,8 +191,9 @@ __global__ void prop_sample_kernel(geraf_grid gr, PropGeom g, const float* __res
 
 // ------------------------------------------------- samples of selected cells
 // Depth cells of a grid column: the G2 cells of s = n_z / G2 consecutive fine
-// depths each. Per grid column the m cells with the largest q (ties: the lower
-// cell index) are kept; a fine column samples exactly the stratified grid's
+// depths each. Per grid column the m cells ranked first are kept (by the
+// largest q within `dilate` cells, then the cell's own q, then the lower
+// index); a fine column samples exactly the stratified grid's
 // own points of those cells (bit for bit the points of a dense STRATIFIED
 // geraf_sample with the same seed and step), so the kept part of the column is
 // the dense render's; after each run of consecutive kept cells (the first
@@ -202,20 +203,31 @@ __global__ void prop_sample_kernel(geraf_grid gr, PropGeom g, const float* __res
 // that fills the column's n_out = m s + r_max slots (copies of its last
 // sample, so their alpha is 0) carry keep = 0.
 // Table per grid column [n_out]: fine depth | (keep << 30).
-__global__ void cells_select_kernel(PropGeom g, int s_fine, int m, int r_max, int n_out, const float* __restrict__ q,
-                                    int32_t* __restrict__ table) {
+__global__ void cells_select_kernel(PropGeom g, int s_fine, int m, int r_max, int dilate, int n_out,
+                                    const float* __restrict__ q, int32_t* __restrict__ table) {
     __shared__ float qs[256];
+    __shared__ float qd[256];
     __shared__ int sel[256];
     __shared__ int list[256];
     const int col = blockIdx.x, k = threadIdx.x;
     const int plane = g.G0 * g.G1;
     if (k < g.G2) qs[k] = q[(int64_t)k * plane + col];
     __syncthreads();
+    // ranking key: the largest q within `dilate` cells (so the neighbours of a
+    // peak come before a lone cell of smaller q), then the cell's own q, then
+    // the lower cell index
+    if (k < g.G2) {
+        float v = qs[k];
+        for (int j = max(0, k - dilate); j <= min(g.G2 - 1, k + dilate); ++j) v = fmaxf(v, qs[j]);
+        qd[k] = v;
+    }
+    __syncthreads();
     int keep_k = 0;
     if (k < g.G2) {
-        const float v = qs[k];
+        const float vd = qd[k], v = qs[k];
         int rank = 0;
-        for (int j = 0; j < g.G2; ++j) rank += (qs[j] > v || (qs[j] == v && j < k)) ? 1 : 0;
+        for (int j = 0; j < g.G2; ++j)
+            rank += (qd[j] > vd || (qd[j] == vd && (qs[j] > v || (qs[j] == v && j < k)))) ? 1 : 0;
         keep_k = rank < m;
     }
     sel[k] = keep_k;
@@ -511,15 +523,15 @@ geraf_status sample_proposal_impl(const geraf_grid* gr, const geraf_proposal* p,
 }
 
 geraf_status sample_cells_impl(const geraf_grid* gr, const geraf_proposal* p, const float* q, int32_t m,
-                               int32_t r_max, uint64_t seed, uint64_t step, float* xyz, float* apr, int32_t* idx,
-                               float* keep, void* ws, size_t* ws_bytes, cudaStream_t st) {
+                               int32_t r_max, int32_t dilate, uint64_t seed, uint64_t step, float* xyz, float* apr,
+                               int32_t* idx, float* keep, void* ws, size_t* ws_bytes, cudaStream_t st) {
     PropGeom g;
     if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
     if (gr->n[2] % g.G2 != 0 || gr->n[0] % g.G0 != 0 || gr->n[1] % g.G1 != 0)
         return fail(GERAF_ERR_INVALID_ARG, "sample_cells: the grid's columns and depths must be multiples of the "
                                            "proposal grid's");
-    if (m < 1 || m > g.G2 || r_max < 0 || r_max > m)
-        return fail(GERAF_ERR_INVALID_ARG, "sample_cells: need 1 <= m <= G2 and 0 <= r_max <= m");
+    if (m < 1 || m > g.G2 || r_max < 0 || r_max > m || dilate < 0 || dilate >= g.G2)
+        return fail(GERAF_ERR_INVALID_ARG, "sample_cells: need 1 <= m <= G2, 0 <= r_max <= m, 0 <= dilate < G2");
     const int s_fine = gr->n[2] / g.G2;
     const int n_out = m * s_fine + r_max;
     const int plane = g.G0 * g.G1;
@@ -527,7 +539,7 @@ geraf_status sample_cells_impl(const geraf_grid* gr, const geraf_proposal* p, co
     int32_t* table = c.take<int32_t>((size_t)plane * n_out);
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "sample_cells: workspace %zu < %zu bytes", *ws_bytes, c.used);
-    cells_select_kernel<<<plane, 256, 0, st>>>(g, s_fine, m, r_max, n_out, q, table);
+    cells_select_kernel<<<plane, 256, 0, st>>>(g, s_fine, m, r_max, dilate, n_out, q, table);
     const int64_t n_ray = (int64_t)gr->n[0] * gr->n[1];
     cells_sample_kernel<<<g1(n_ray * n_out, 256), 256, 0, st>>>(*gr, g, s_fine, n_out, table, seed, step, xyz, apr,
                                                                idx, keep);

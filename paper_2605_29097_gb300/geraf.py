@@ -422,7 +422,7 @@ def geraf_sample_proposal(grid: GerafGrid, prop: Proposal, q, seed=0, step=0):
     return xyz, apr, idx
 
 
-def geraf_sample_cells(grid: GerafGrid, prop: Proposal, q, m: int, r_max: int, seed=0, step=0):
+def geraf_sample_cells(grid: GerafGrid, prop: Proposal, q, m: int, r_max: int, seed=0, step=0, dilate=0):
     """Stratified grid samples of the m proposal cells of largest q per column,
     with run-closing samples -> (xyz [3, n_ray*n_out], xyz_apr [3, n_ray],
     idx int32 [n_ray*n_out], keep [n_ray*n_out], n_out = m s + r_max)."""
@@ -438,8 +438,8 @@ def geraf_sample_cells(grid: GerafGrid, prop: Proposal, q, m: int, r_max: int, s
     cp = prop.c()
     L = _lib.lib()
     args = lambda w, b: L.geraf_sample_cells(ctypes.byref(grid), ctypes.byref(cp), _p(_req(q, "q")), int(m),
-                                             int(r_max), int(seed), int(step), _p(xyz), _p(apr), _p(idx), _p(keep),
-                                             w, b, _stream())
+                                             int(r_max), int(dilate), int(seed), int(step), _p(xyz), _p(apr), _p(idx),
+                                             _p(keep), w, b, _stream())
     ws, wsz = _workspace(args, dev)
     check(args(_p(ws), ctypes.byref(wsz)))
     return xyz, apr, idx, keep, n_out

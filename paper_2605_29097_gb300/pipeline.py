@@ -255,7 +255,7 @@ def proposal_forward_backward(geo: Geometry, field, prop, target, seed: int, ste
 
 
 def cells_forward_backward(geo: Geometry, field, prop, target, m: int, r_max: int, seed: int, step: int,
-                           q=None, timers=None, train_proposal=True):
+                           q=None, timers=None, train_proposal=True, dilate=1):
     """One hot-path pass on the stratified grid's own samples in the m proposal
     cells of largest q per column (geraf_sample_cells: closing samples after
     each run, keep = 0 on closing and padding samples), plus the proposal's
@@ -271,7 +271,7 @@ def cells_forward_backward(geo: Geometry, field, prop, target, m: int, r_max: in
 
     logits, q_prop, psaved = G.geraf_proposal_density(prop)
     xyz, apr, idx, keep, n_out = G.geraf_sample_cells(geo.grid, prop, q_prop if q is None else q, m, r_max, seed,
-                                                      step)
+                                                      step, dilate=dilate)
     is_mlp = isinstance(field, G.MLPField)
     f, grad, a, saved = G.geraf_fields(field, xyz, keep_saved=is_mlp)
     fa, _, _, _ = G.geraf_fields(field, apr, want_grad=False, want_refl=False)

@@ -95,8 +95,8 @@ def test_training_signal_matches_oracle(G, oracle, use_idx):
     assert rel(d_f.cpu().numpy().reshape(-1, 8), odf) < 1e-5
 
 
-@pytest.mark.parametrize("m,r_max", [(5, 2), (16, 16), (1, 0)])
-def test_sample_cells_bit_exact(G, oracle, m, r_max):
+@pytest.mark.parametrize("m,r_max,dilate", [(5, 2, 0), (16, 16, 0), (1, 0, 0), (6, 3, 1), (9, 2, 2)])
+def test_sample_cells_bit_exact(G, oracle, m, r_max, dilate):
     """Cell-subset sampling from the network's own FP32 q (with ties planted
     in q): points, ray starts, cell indices and keep flags bit-exact with the
     oracle, which takes the points from the dense stratified grid."""
@@ -108,9 +108,9 @@ def test_sample_cells_bit_exact(G, oracle, m, r_max):
     qh[3, :] = qh[7, :]                                   # ties between cells 3 and 7 of every column
     qh = qh.ravel()
     q = torch.as_tensor(qh, device="cuda")
-    xyz, apr, idx, keep, n_out = G.geraf_sample_cells(grid, prop, q, m, r_max, seed=5, step=3)
+    xyz, apr, idx, keep, n_out = G.geraf_sample_cells(grid, prop, q, m, r_max, seed=5, step=3, dilate=dilate)
     G.geraf_poll_device_error()
-    ox, oa, oi, ok, on = oracle.sample_cells(g, (8, 4, 16), qh, m, r_max, seed=5, step=3)
+    ox, oa, oi, ok, on = oracle.sample_cells(g, (8, 4, 16), qh, m, r_max, seed=5, step=3, dilate=dilate)
     assert n_out == on
     np.testing.assert_array_equal(xyz.cpu().numpy().view(np.uint32), ox.view(np.uint32))
     np.testing.assert_array_equal(apr.cpu().numpy().view(np.uint32), oa.view(np.uint32))

@@ -106,11 +106,30 @@ def test_uniform_proposal_is_stratified_closed_form(oracle):
     np.testing.assert_array_equal(xyz[2].reshape(16, -1), want)
 
 
-def _cells_case(oracle, q_fn, m, r_max, gshape=(3, 2, 12), n=(6, 4, 48)):
+def _cells_case(oracle, q_fn, m, r_max, gshape=(3, 2, 12), n=(6, 4, 48), dilate=0):
     g = gi.cube_grid((0.0, 0.0, 0.15), 0.06, n)
     G0, G1, G2 = gshape
     q = q_fn(np.random.default_rng(3), G2, G1 * G0).astype(np.float32)
-    return g, q, oracle.sample_cells(g, gshape, q, m, r_max, seed=11, step=2)
+    return g, q, oracle.sample_cells(g, gshape, q, m, r_max, seed=11, step=2, dilate=dilate)
+
+
+def test_sample_cells_dilated_ranking(oracle):
+    """With dilate = 1 a cell ranks by the largest q of itself and its two
+    neighbours: the neighbours of the column's peak (cells 4 and 6 around a
+    peak at 5) come before a lone cell of larger own q elsewhere (cell 10),
+    and among them the larger own q first."""
+    def q_fn(rng, g2, cols):
+        q = np.full((g2, cols), 0.01)
+        q[5, :] = 1.0
+        q[6, :] = 0.05
+        q[4, :] = 0.02
+        q[10, :] = 0.3
+        return q
+    g, q, (xyz, apr, idx, keep, n_out) = _cells_case(oracle, q_fn, 3, 1, dilate=1)
+    cells = set(np.unique(idx[keep == 1] // 6).tolist())
+    assert cells == {4, 5, 6}
+    g, q, (xyz, apr, idx, keep, n_out) = _cells_case(oracle, q_fn, 3, 1, dilate=0)
+    assert set(np.unique(idx[keep == 1] // 6).tolist()) == {5, 10, 6}
 
 
 def test_sample_cells_selection_and_layout(oracle):
