@@ -232,7 +232,7 @@ def job_rate(units_per_step_per_rank: int, steps: int, world: int, max_ms: float
 
 
 def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, r_max=4, prop_steps=300,
-                       m_table=(8, 10, 12, 14, 16), dilates=(0, 1, 2)):
+                       m_table=(8, 10, 12, 14, 16), dilates=(0, 1, 2), gshape=(64, 64, 64)):
     """Training step on the random-scene workload (1-8 ellipsoids and boxes
     behind a 0.5 occluder, 10 dB noise; 64x64 array, 128 bins, 64^3 heatmap):
     2^24 stratified samples (256^2 columns x 256 depths) against the same
@@ -258,7 +258,6 @@ def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, r_max=4, p
     geo = PL.make_geometry(wl, dev)
     scene = gi.c4_scene(4)
     target = PL.scene_target(geo, scene, noise_seed=4, device=dev)
-    gshape = (64, 64, 64)
     s_fine = geo.n_z // gshape[2]
     prop, pm = PL.init_proposal(gshape=gshape, depth=16, seed=5, device=dev)
     ptrain = PL.ProposalTrainer(prop, pm, lr=1e-2)
