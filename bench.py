@@ -231,14 +231,14 @@ def job_rate(units_per_step_per_rank: int, steps: int, world: int, max_ms: float
     return units_per_step_per_rank * steps * world / (max_ms * 1e-3)
 
 
-def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, r_max=4, prop_steps=300,
-                       m_table=(8, 10, 12, 14, 16), dilates=(0, 1, 2), gshape=(64, 64, 64)):
+def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, r_max=2, prop_steps=300,
+                       m_table=(22, 24, 26, 28, 30), dilates=(1, 2), gshape=(64, 64, 128)):
     """Training step on the random-scene workload (1-8 ellipsoids and boxes
     behind a 0.5 occluder, 10 dB noise; 64x64 array, 128 bins, 64^3 heatmap):
     2^24 stratified samples (256^2 columns x 256 depths) against the same
-    grid's own samples in the m proposal cells (of 64 per column) of largest q
-    plus r_max run-closing samples per column (4 m + r_max samples per
-    column). First the proposal is trained on the blended weights T alpha of
+    grid's own samples in the m proposal cells (of 128 per column, 2 depths
+    each) ranked first plus r_max run-closing samples per column (2 m + r_max
+    samples per column). First the proposal is trained on the blended weights T alpha of
     dense renders of the analytic scene (the converged geometry); then, at
     fixed parameters, the heatmap relative L2 of the cell-subset pass against
     the dense pass (identical samples in the kept cells) on that scene, for the

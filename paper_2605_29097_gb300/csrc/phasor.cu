@@ -61,13 +61,16 @@ __device__ __forceinline__ void split3(float x, float y, float z, float4& hi, fl
 }
 
 // --------------------------------------------------------------- pack kernels
+// record j holds point perm[j] (perm NULL: point j)
 __global__ void pack_render_points(const float* __restrict__ xyz, const float* __restrict__ grad,
                                    const float* __restrict__ w, const float* __restrict__ t_eff,
-                                   int64_t n, int64_t n_pad, int directional, PtRec* __restrict__ out) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n_pad) return;
+                                   int64_t n, int64_t n_pad, int directional, PtRec* __restrict__ out,
+                                   const int* __restrict__ perm = nullptr) {
+    const int64_t r_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r_ >= n_pad) return;
+    const int64_t j = r_ < n && perm ? perm[r_] : r_;
     PtRec r;
-    if (j < n) {
+    if (r_ < n) {
         const float gx = grad[j], gy = grad[n + j], gz = grad[2 * n + j];
         const float ig = inv_grad_norm(gx, gy, gz, directional);
         const bool dir = ig > 0.0f;
@@ -84,16 +87,17 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         r.c.w = -1.0f;
     }
-    out[j] = r;
+    out[r_] = r;
 }
 
 __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const float2* __restrict__ M,
                                        const float* __restrict__ dP, int64_t n, int64_t n_pad,
-                                       PtRec* __restrict__ out) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n_pad) return;
+                                       PtRec* __restrict__ out, const int* __restrict__ perm = nullptr) {
+    const int64_t r_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r_ >= n_pad) return;
+    const int64_t j = r_ < n && perm ? perm[r_] : r_;
     PtRec r;
-    if (j < n) {
+    if (r_ < n) {
         float2 m = M[j];
         double mag = sqrt((double)m.x * m.x + (double)m.y * m.y);
         float cr = 0.0f, ci = 0.0f;
@@ -110,7 +114,7 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     r.c.w = 0.0f;
-    out[j] = r;
+    out[r_] = r;
 }
 
 // antenna records (x, y, z, c_ant), padded with copies of antenna 0
@@ -669,14 +673,16 @@ __global__ void __launch_bounds__(TPK_THREADS) to_points_kernel(const ToPointsAr
 }
 
 // filter finalize: M = sum of split partials (FP64), P = |M|, loss terms
+// record j -> voxel o = perm[j] (perm NULL: o = j)
 __global__ void filter_finalize(const float2* __restrict__ partial, int splits, int64_t n,
                                 const float* __restrict__ target, const float* __restrict__ mask,
                                 float* __restrict__ P, float2* __restrict__ M, float* __restrict__ dP,
-                                double* __restrict__ loss_blocks) {
+                                double* __restrict__ loss_blocks, const int* __restrict__ perm) {
     __shared__ double red[256];
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double l = 0.0;
     if (j < n) {
+        const int64_t o = perm ? perm[j] : j;
         double mr = 0.0, mi = 0.0;
         for (int s = 0; s < splits; ++s) {
             float2 v = partial[(size_t)s * n + j];
@@ -684,13 +690,13 @@ __global__ void filter_finalize(const float2* __restrict__ partial, int splits, 
             mi += v.y;
         }
         double p = sqrt(mr * mr + mi * mi);
-        M[j] = make_float2((float)mr, (float)mi);
-        P[j] = (float)p;
+        M[o] = make_float2((float)mr, (float)mi);
+        P[o] = (float)p;
         if (target) {
-            double m = mask ? (double)mask[j] : 1.0;
-            double r = p - (double)target[j];
+            double m = mask ? (double)mask[o] : 1.0;
+            double r = p - (double)target[o];
             l = m * r * r;
-            if (dP) dP[j] = (float)(2.0 * m * r);
+            if (dP) dP[o] = (float)(2.0 * m * r);
         }
     }
     if (loss_blocks) {
@@ -717,22 +723,25 @@ __global__ void sum_doubles(const double* __restrict__ x, int n, double* __restr
     if (threadIdx.x == 0) *out = red[0];
 }
 
+// record j -> point o = perm[j] (perm NULL: o = j)
 __global__ void render_bwd_finalize(const float* __restrict__ partial, int splits, int64_t n,
                                     const PtRec* __restrict__ pts, const float* __restrict__ grad,
                                     int directional, float* __restrict__ d_w,
-                                    float* __restrict__ d_teff, float* __restrict__ d_grad) {
+                                    float* __restrict__ d_teff, float* __restrict__ d_grad,
+                                    const int* __restrict__ perm) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
+    const int64_t o = perm ? perm[j] : j;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int s = 0; s < splits; ++s)
         for (int k = 0; k < 6; ++k) acc[k] += partial[((size_t)s * 6 + k) * n + j];
-    d_w[j] = (float)acc[0];
-    d_teff[j] = (float)acc[1];
+    d_w[o] = (float)acc[0];
+    d_teff[o] = (float)acc[1];
     const PtRec P = pts[j];
-    const double ig = inv_grad_norm(grad[j], grad[n + j], grad[2 * n + j], directional);   // 0 when isotropic
-    d_grad[j] = (float)((acc[2] - acc[5] * P.b.x) * ig);
-    d_grad[n + j] = (float)((acc[3] - acc[5] * P.b.y) * ig);
-    d_grad[2 * n + j] = (float)((acc[4] - acc[5] * P.b.z) * ig);
+    const double ig = inv_grad_norm(grad[o], grad[n + o], grad[2 * n + o], directional);   // 0 when isotropic
+    d_grad[o] = (float)((acc[2] - acc[5] * P.b.x) * ig);
+    d_grad[n + o] = (float)((acc[3] - acc[5] * P.b.y) * ig);
+    d_grad[2 * n + o] = (float)((acc[4] - acc[5] * P.b.z) * ig);
 }
 
 // --------------------------------------------------------------- launch glue
@@ -842,7 +851,8 @@ struct ChebPlan {
     int K;            // Chebyshev order
     int use_direct;   // 1: the exact recurrence kernels must run instead
     int run_cheb;     // = !use_direct
-    int pad[3];
+    float box[6];     // the points' bounding box (min xyz, max xyz)
+    int pad;
 };
 
 __global__ void bbox_partial_kernel(const float* __restrict__ xyz, int64_t n, float* __restrict__ part) {
@@ -962,7 +972,138 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
         plan->K = K;
         plan->use_direct = direct;
         plan->run_cheb = !direct;
+        for (int d = 0; d < 6; ++d) plan->box[d] = box[d];
     }
+}
+
+// --------------------------------------------------- spatial order of points
+// The Chebyshev parts are runs of consecutive point records; so that a run is
+// a compact brick of space rather than a slab of the whole volume, the
+// Chebyshev calls pack the points in brick order: the points' bounding box cut
+// into 8 x 8 x 8 bricks numbered along a Z-curve, a stable counting sort by
+// brick (order of the caller kept inside a brick, so the result is
+// deterministic). perm[r] = the point held by record r. Each warp owns a
+// sub-chunk of PO_SUB consecutive points: histogram per sub-chunk, exclusive
+// scan over sub-chunks in segments of PO_SEG and over the segments and the
+// buckets, then each warp places its points in order (peers of equal bucket
+// ranked by lane within each round of 32).
+constexpr int PO_BUCKETS = 512;
+constexpr int PO_SUB = 512;
+constexpr int PO_WARPS = 16;
+constexpr int PO_SEG = 64;
+
+__device__ __forceinline__ int point_bucket(float x, float y, float z, const float (&box)[6]) {
+    const float v[3] = {x, y, z};
+    int code = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float span = box[3 + d] - box[d];
+        int b = span > 0.0f ? (int)((v[d] - box[d]) * (8.0f / span)) : 0;
+        b = min(max(b, 0), 7);
+#pragma unroll
+        for (int bit = 0; bit < 3; ++bit) code |= ((b >> bit) & 1) << (3 * bit + d);
+    }
+    return code;
+}
+
+__global__ void __launch_bounds__(32 * PO_WARPS) point_hist_kernel(const float* __restrict__ xyz, int64_t n,
+                                                                   const ChebPlan* __restrict__ plan,
+                                                                   uint16_t* __restrict__ bkt,
+                                                                   int* __restrict__ hist) {
+    __shared__ int h[PO_WARPS][PO_BUCKETS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = lane; i < PO_BUCKETS; i += 32) h[warp][i] = 0;
+    __syncwarp();
+    float box[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) box[d] = plan->box[d];
+    const int64_t sc = (int64_t)blockIdx.x * PO_WARPS + warp;
+    const int64_t j0 = sc * PO_SUB, j1 = min(n, j0 + PO_SUB);
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+        const int b = point_bucket(xyz[j], xyz[n + j], xyz[2 * n + j], box);
+        bkt[j] = (uint16_t)b;
+        atomicAdd(&h[warp][b], 1);
+    }
+    __syncwarp();
+    for (int i = lane; i < PO_BUCKETS; i += 32) hist[sc * PO_BUCKETS + i] = h[warp][i];
+}
+
+// exclusive scan over the sub-chunks of one segment, per bucket, in place;
+// seg[segment][bucket] = the segment's totals
+__global__ void point_scan_segments(int* __restrict__ hist, int64_t n_sub, int* __restrict__ seg) {
+    const int b = threadIdx.x;
+    const int64_t s0 = (int64_t)blockIdx.x * PO_SEG, s1 = min(n_sub, s0 + PO_SEG);
+    int run = 0;
+    for (int64_t sc = s0; sc < s1; ++sc) {
+        const int v = hist[sc * PO_BUCKETS + b];
+        hist[sc * PO_BUCKETS + b] = run;
+        run += v;
+    }
+    seg[(int64_t)blockIdx.x * PO_BUCKETS + b] = run;
+}
+
+// exclusive scan over the segments per bucket (in place), then over the
+// buckets: base[b] = the number of points in buckets below b
+__global__ void point_scan_totals(int* __restrict__ seg, int n_seg, int* __restrict__ base) {
+    __shared__ int tot[PO_BUCKETS];
+    const int b = threadIdx.x;
+    int run = 0;
+    for (int g = 0; g < n_seg; ++g) {
+        const int v = seg[(int64_t)g * PO_BUCKETS + b];
+        seg[(int64_t)g * PO_BUCKETS + b] = run;
+        run += v;
+    }
+    tot[b] = run;
+    __syncthreads();
+    if (b == 0) {
+        int acc = 0;
+        for (int i = 0; i < PO_BUCKETS; ++i) {
+            const int v = tot[i];
+            tot[i] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    base[b] = tot[b];
+}
+
+__global__ void __launch_bounds__(32 * PO_WARPS) point_scatter_kernel(const uint16_t* __restrict__ bkt, int64_t n,
+                                                                      const int* __restrict__ hist,
+                                                                      const int* __restrict__ seg,
+                                                                      const int* __restrict__ base,
+                                                                      int* __restrict__ perm) {
+    __shared__ int cnt[PO_WARPS][PO_BUCKETS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t sc = (int64_t)blockIdx.x * PO_WARPS + warp;
+    const int64_t g = sc / PO_SEG;
+    for (int i = lane; i < PO_BUCKETS; i += 32)
+        cnt[warp][i] = base[i] + seg[g * PO_BUCKETS + i] + hist[sc * PO_BUCKETS + i];
+    __syncwarp();
+    const int64_t j0 = sc * PO_SUB, j1 = min(n, j0 + PO_SUB);
+    for (int64_t jb = j0; jb < j1; jb += 32) {
+        const int64_t j = jb + lane;
+        const unsigned active = __ballot_sync(0xffffffffu, j < j1);
+        if (j < j1) {
+            const int b = bkt[j];
+            const unsigned peers = __match_any_sync(active, b);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            perm[cnt[warp][b] + rank] = (int)j;
+            __syncwarp(active);
+            if (rank == 0) cnt[warp][b] += __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// records' source order -> permuted SoA copy of three coordinate planes
+__global__ void gather_xyz(const float* __restrict__ xyz, int64_t n, const int* __restrict__ perm,
+                           float* __restrict__ out) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t j = perm[r];
+    out[r] = xyz[j];
+    out[n + r] = xyz[n + j];
+    out[2 * n + r] = xyz[2 * n + j];
 }
 
 // Expansion of one part of a Chebyshev call (a split of point tiles, possibly
@@ -1835,6 +1976,37 @@ void launch_ant_order(const AntOrder& a, const float* ant_xyz, const float* c_an
     pack_antennas_perm<<<grid1d(a.n_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, a.perm, a.n_rec, a.rec);
 }
 
+// Brick order of the points (Chebyshev calls): perm and the sort's buffers
+struct PointOrder {
+    int* perm;
+    uint16_t* bkt;
+    int* hist;
+    int* seg;
+    int* base;
+    int64_t n, n_sub;
+    int n_seg;
+    unsigned blocks;
+};
+PointOrder take_point_order(WsCarver& c, int64_t n) {
+    PointOrder o{};
+    o.n = n;
+    o.blocks = (unsigned)((n + (int64_t)PO_SUB * PO_WARPS - 1) / ((int64_t)PO_SUB * PO_WARPS));
+    o.n_sub = (int64_t)o.blocks * PO_WARPS;          // every warp's sub-chunk, empty ones included
+    o.n_seg = (int)((o.n_sub + PO_SEG - 1) / PO_SEG);
+    o.perm = c.take<int>((size_t)n);
+    o.bkt = c.take<uint16_t>((size_t)n);
+    o.hist = c.take<int>((size_t)o.n_sub * PO_BUCKETS);
+    o.seg = c.take<int>((size_t)o.n_seg * PO_BUCKETS);
+    o.base = c.take<int>(PO_BUCKETS);
+    return o;
+}
+void launch_point_order(const PointOrder& o, const float* xyz, const ChebPlan* plan, cudaStream_t st) {
+    point_hist_kernel<<<o.blocks, 32 * PO_WARPS, 0, st>>>(xyz, o.n, plan, o.bkt, o.hist);
+    point_scan_segments<<<o.n_seg, PO_BUCKETS, 0, st>>>(o.hist, o.n_sub, o.seg);
+    point_scan_totals<<<1, PO_BUCKETS, 0, st>>>(o.seg, o.n_seg, o.base);
+    point_scatter_kernel<<<o.blocks, 32 * PO_WARPS, 0, st>>>(o.bkt, o.n, o.hist, o.seg, o.base, o.perm);
+}
+
 // group boxes, part plans and tables, then the groups' antenna rows
 geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const AntOrder& ao, const float* xyz,
                                  int64_t n, const float* ant_xyz, const float* c_ant, int n_ant, int n_ant_pad,
@@ -1912,9 +2084,11 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     float2* scs = nullptr;
     int* kmax = nullptr;
     float2* gout = nullptr;
+    PointOrder po{};
     if (cheb) {
         cw = take_cheb(c, n_pts);
         ao = take_ant_order(c, n_ant, n_ant_rec);
+        po = take_point_order(c, n_pts);
         cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
         sbox = c.take<float>((size_t)q.splits * 6);
         splan = c.take<SplitPlan>(parts);
@@ -1925,12 +2099,6 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", name, *ws_bytes, c.used);
     int* err = device_error_word();
-    if (!kComplexAmp)
-        pack_render_points<<<grid1d(n_rec, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_rec,
-                                                               (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
-    else
-        pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts);
-    pack_antennas<<<grid1d(n_ant_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, n_ant_rec, ant);
     {
         const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_bins_kernel<false>,
                                            to_bins_kernel<true>, cheb_bins_kernel<false, 3>,
@@ -1939,9 +2107,20 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
                                            cheb_bins_kernel<true, 8>, antenna_order_kernel);
         if (as != GERAF_OK) return as;
     }
+    if (cheb) {
+        // whole-call plan (and the points' box), then the points in brick order
+        launch_cheb_plan(cw, positions, n_pts, ant_xyz, n_ant, band, st);
+        launch_point_order(po, positions, cw.plan, st);
+    }
+    if (!kComplexAmp)
+        pack_render_points<<<grid1d(n_rec, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_rec,
+                                                               (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts,
+                                                               po.perm);
+    else
+        pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts, po.perm);
+    pack_antennas<<<grid1d(n_ant_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, n_ant_rec, ant);
     const int* run_direct = nullptr;
     if (cheb) {
-        launch_cheb_plan(cw, positions, n_pts, ant_xyz, n_ant, band, st);
         launch_ant_order(ao, ant_xyz, c_ant, n_ant, st);
         cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_status(e, name);
@@ -2003,10 +2182,14 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     ChebWs cw{};
     PointGroups pg{};
     AntOrder ao{};
+    PointOrder po{};
+    float* vox_p = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_vox);
         pg = take_point_groups(c, p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
         ao = take_ant_order(c, n_ant, p.n_ant_pad);
+        po = take_point_order(c, n_vox);
+        vox_p = c.take<float>((size_t)3 * n_vox);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used) return fail(GERAF_ERR_WORKSPACE, "filter: workspace %zu < %zu bytes", *ws_bytes, c.used);
@@ -2020,13 +2203,15 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     const int* run_direct = nullptr;
     if (cheb) {
         launch_cheb_plan(cw, vox, n_vox, ant_xyz, n_ant, band, st);
+        launch_point_order(po, vox, cw.plan, st);
+        gather_xyz<<<grid1d(n_vox, 256), 256, 0, st>>>(vox, n_vox, po.perm, vox_p);
         launch_ant_order(ao, ant_xyz, nullptr, n_ant, st);
-        const geraf_status gs = launch_point_groups(pg, cw, ao, vox, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad,
+        const geraf_status gs = launch_point_groups(pg, cw, ao, vox_p, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad,
                                                     band, reinterpret_cast<const float2*>(s), 1, 0, st);
         if (gs != GERAF_OK) return gs;
         float kh, kl;
         k0_split(band, &kh, &kl);
-        ChebPointsArgs ca{nullptr, vox, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
+        ChebPointsArgs ca{nullptr, vox_p, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
                           p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, kh, kl,
                           reinterpret_cast<float*>(part), err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
@@ -2037,13 +2222,13 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     }
     pack_antenna_rows<<<p.n_ant_pad, 128, 0, st>>>(ant_xyz, nullptr, reinterpret_cast<const float2*>(s), n_ant,
                                                    p.n_ant_pad, band->n_f, p.n_f_pad, rows, run_direct);
-    ToPointsArgs a{nullptr, vox, n_vox, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split,
+    ToPointsArgs a{nullptr, cheb ? vox_p : vox, n_vox, rows, p.row_f4, p.at, p.n_ant_tiles, p.tiles_per_split,
                    reinterpret_cast<float*>(part), err, bk, run_direct};
     to_points_kernel<MODE_FILTER><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
     const bool want_loss = target != nullptr;
     filter_finalize<<<fin_blocks, 256, 0, st>>>(part, p.splits, n_vox, target, mask, P,
                                                 reinterpret_cast<float2*>(M), want_loss ? dloss_dP : nullptr,
-                                                want_loss ? loss_blocks : nullptr);
+                                                want_loss ? loss_blocks : nullptr, po.perm);
     if (want_loss && loss) sum_doubles<<<1, 256, 0, st>>>(loss_blocks, fin_blocks, loss);
     return check_launch("filter");
 }
@@ -2063,17 +2248,27 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     ChebWs cw{};
     PointGroups pg{};
     AntOrder ao{};
+    PointOrder po{};
+    float* xyz_p = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_pts);
         pg = take_point_groups(c, p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
         ao = take_ant_order(c, n_ant, p.n_ant_pad);
+        po = take_point_order(c, n_pts);
+        xyz_p = c.take<float>((size_t)3 * n_pts);
     }
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "render_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
     int* err = device_error_word();
+    if (cheb) {
+        // whole-call plan (and the points' box), then the points in brick order
+        launch_cheb_plan(cw, xyz, n_pts, ant_xyz, n_ant, band, st);
+        launch_point_order(po, xyz, cw.plan, st);
+        gather_xyz<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, n_pts, po.perm, xyz_p);
+    }
     pack_render_points<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pts,
-                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts);
+                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts, po.perm);
     {
         const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_points_kernel<MODE_RENDER_BWD>,
                                            cheb_points_kernel<MODE_RENDER_BWD, 3>,
@@ -2083,9 +2278,8 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     }
     const int* run_direct = nullptr;
     if (cheb) {
-        launch_cheb_plan(cw, xyz, n_pts, ant_xyz, n_ant, band, st);
         launch_ant_order(ao, ant_xyz, c_ant, n_ant, st);
-        const geraf_status gs = launch_point_groups(pg, cw, ao, xyz, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad,
+        const geraf_status gs = launch_point_groups(pg, cw, ao, xyz_p, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad,
                                                     band, reinterpret_cast<const float2*>(g_s), 0, 1, st);
         if (gs != GERAF_OK) return gs;
         float kh, kl;
@@ -2105,7 +2299,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     to_points_kernel<MODE_RENDER_BWD><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, p.smem, st>>>(a);
     render_bwd_finalize<<<grid1d(n_pts, 256), 256, 0, st>>>(part, p.splits, n_pts, pts, grad,
                                                             (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, d_w,
-                                                            d_teff, d_grad);
+                                                            d_teff, d_grad, po.perm);
     return check_launch("render_backward");
 }
 
@@ -2211,6 +2405,8 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     WsCarver c(ws);
     ChebWs cw = take_cheb(c, n);
     AntOrder ao = take_ant_order(c, n_ant, n_rec);
+    PointOrder po = take_point_order(c, n);
+    float* xyz_p = c.take<float>((size_t)3 * n);
     float* box = c.take<float>((size_t)n_splits * 6);
     SplitPlan* splan = c.take<SplitPlan>(parts);
     float2* Cs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
@@ -2226,10 +2422,12 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
         if (as != GERAF_OK) return as;
     }
     launch_cheb_plan(cw, xyz, n, ant_xyz, n_ant, band, st);
+    launch_point_order(po, xyz, cw.plan, st);
+    gather_xyz<<<grid1d(n, 256), 256, 0, st>>>(xyz, n, po.perm, xyz_p);
     launch_ant_order(ao, ant_xyz, nullptr, n_ant, st);
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "chebyshev_work");
-    group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz, n, per_part, box);
+    group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz_p, n, per_part, box);
     split_plan_kernel<<<parts, 256, 0, st>>>(box, ao.rec, n_ant, n_ab, ant_per_block, 2.0 * band->df / kC,
                                              band->n_f, CH_TAIL, cw.plan, splan, Cs, kmax);
     geraf_status s = check_launch("chebyshev_work");
