@@ -838,8 +838,29 @@ constexpr int CH_KMAX = 64;
 constexpr int CH_THREADS = 128;
 constexpr int CH_TP = 32;             // points per TMA tile
 constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before it joins the outer sum
-constexpr size_t CH_PARTIAL_BYTES = 256ull << 20;   // bound on the split partials of one call
-constexpr size_t CH_TABLE_BYTES = 1ull << 30;       // bound on the coefficient tables of one call's parts
+#ifndef GERAF_CH_PARTIAL_MIB
+#define GERAF_CH_PARTIAL_MIB 256
+#endif
+#ifndef GERAF_CH_TABLE_MIB
+#define GERAF_CH_TABLE_MIB 1024
+#endif
+#ifndef GERAF_CH_MAX_SPLITS
+#define GERAF_CH_MAX_SPLITS 512
+#endif
+#ifndef GERAF_CH_SPLIT_CTAS_PER_SM
+#define GERAF_CH_SPLIT_CTAS_PER_SM 16
+#endif
+#ifndef GERAF_CH_SPLIT_PTS_PER_BIN
+#define GERAF_CH_SPLIT_PTS_PER_BIN 0
+#endif
+#ifndef GERAF_CH_MAX_GROUPS
+#define GERAF_CH_MAX_GROUPS 64
+#endif
+#ifndef GERAF_CH_GROUP_ROWS_MIB
+#define GERAF_CH_GROUP_ROWS_MIB 1024
+#endif
+constexpr size_t CH_PARTIAL_BYTES = (size_t)GERAF_CH_PARTIAL_MIB << 20;   // bound on the split partials of one call
+constexpr size_t CH_TABLE_BYTES = (size_t)GERAF_CH_TABLE_MIB << 20;       // bound on the coefficient tables of one call's parts
 // Bessel-tail bound of the expansion: the unit phasor is represented to 1e-7,
 // below the FP32 rounding of the sums themselves (relative L2 2e-7 .. 5e-7
 // against the FP64 oracle on every parity case)
@@ -1922,7 +1943,7 @@ ChebWs take_cheb(WsCarver& c, int64_t n_bbox) {
 // least 8 CTAs = 2048 points per group), planned per (group, block of
 // CH_THREADS antenna records in the spatial order) while the parts' tables fit
 // CH_TABLE_BYTES, else per group over all antennas.
-constexpr size_t CH_GROUP_ROWS_BYTES = 1ull << 30;
+constexpr size_t CH_GROUP_ROWS_BYTES = (size_t)GERAF_CH_GROUP_ROWS_MIB << 20;
 struct PointGroups {
     int groups, ctas_per_group, n_ab, parts;
     float* box;
@@ -1935,7 +1956,8 @@ struct PointGroups {
 PointGroups plan_point_groups(int pt_ctas, int n_ant, int n_ant_pad, int n_f) {
     PointGroups g{};
     g.group_rows = (size_t)n_ant_pad * CH_ROW;
-    const size_t cap = std::max<size_t>(1, std::min<size_t>(64, CH_GROUP_ROWS_BYTES / (g.group_rows * sizeof(float4))));
+    const size_t cap = std::max<size_t>(
+        1, std::min<size_t>(GERAF_CH_MAX_GROUPS, CH_GROUP_ROWS_BYTES / (g.group_rows * sizeof(float4))));
     g.ctas_per_group = std::max<int>(8, (int)((pt_ctas + cap - 1) / cap));
     g.groups = (pt_ctas + g.ctas_per_group - 1) / g.ctas_per_group;
     const int nb = (n_ant + CH_THREADS - 1) / CH_THREADS;
@@ -2040,10 +2062,14 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant, int n_f) {
     q.ant_blocks = (n_ant + CH_THREADS - 1) / CH_THREADS;
     q.n_tiles = (int)(n_pad / CH_TP);
     const int64_t max_splits = std::max<int64_t>(1, (int64_t)(CH_PARTIAL_BYTES / ((size_t)n_ant * CH_KMAX * 8)));
-    const int64_t want = std::max<int64_t>(1, (4LL * 4 * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
-    // at most 512 splits; each part (a split, or a split and an antenna block)
-    // carries its own coefficient table
-    const int64_t sp = std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles), 512);
+    int64_t want = std::max<int64_t>(
+        1, ((int64_t)GERAF_CH_SPLIT_CTAS_PER_SM * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
+    if (GERAF_CH_SPLIT_PTS_PER_BIN > 0)
+        want = std::max<int64_t>(want, n_pad / ((int64_t)std::max(1, GERAF_CH_SPLIT_PTS_PER_BIN) * n_f));
+    // at most GERAF_CH_MAX_SPLITS splits; each part (a split, or a split and an
+    // antenna block) carries its own coefficient table
+    const int64_t sp = std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles),
+                                         GERAF_CH_MAX_SPLITS);
     q.tiles_per_split = (int)((q.n_tiles + sp - 1) / sp);
     q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
     // a plan per (split, antenna block) pays when a part holds enough pairs to

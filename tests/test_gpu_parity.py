@@ -238,6 +238,27 @@ def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f, method):
     assert rel_l2(host(g), og) < TOL
 
 
+def _brick_order(xyz):
+    """The Chebyshev calls' record order, stated on the host: the points'
+    bounding box cut into 8 x 8 x 8 bricks (FP32 cell index per axis, the
+    bit of axis d at position 3 * bit + d of the brick code, a Z-curve),
+    a stable sort by brick code."""
+    x = np.ascontiguousarray(xyz, dtype=np.float32)
+    lo, hi = x.min(1), x.max(1)
+    code = np.zeros(x.shape[1], dtype=np.int64)
+    for d in range(3):
+        span = np.float32(hi[d] - lo[d])
+        if span > 0:
+            q = np.float32(8.0) / span
+            c = ((x[d] - lo[d]).astype(np.float32) * q).astype(np.float32).astype(np.int64)
+        else:
+            c = np.zeros(x.shape[1], dtype=np.int64)
+        c = np.clip(c, 0, 7)
+        for bit in range(3):
+            code |= ((c >> bit) & 1) << (3 * bit + d)
+    return np.argsort(code, kind="stable")
+
+
 def _host_order(xyz, ant, b, eps=1e-7, kmax=64):
     """Chebyshev order from the bounding box and the Bessel tail, on the host
     (scipy's J_k): the rule the device plan follows, stated independently."""
@@ -438,7 +459,8 @@ def test_chebyshev_work_orders(G, wide_first):
     largest group order (groups of 2048 points, to points) and the largest
     part order (splits of one 32-point tile here: 72 antennas leave one
     antenna block, so the plan cuts the points into single tiles), the kernel
-    instance that follows from it and the mean orders per pair."""
+    instance that follows from it and the mean orders per pair. Parts are
+    runs of consecutive records in the brick order (_brick_order)."""
     rng = np.random.default_rng(31)
     chunks = [((0.0, 0.0, 0.30), 0.12 if wide_first else 0.01, 2048), ((0.02, -0.01, 0.12), 0.01, 2048),
               ((-0.03, 0.02, 0.20), 0.015, 2048), ((0.0, 0.04, 0.16), 0.008, 517)]
@@ -453,7 +475,8 @@ def test_chebyshev_work_orders(G, wide_first):
     for to_points, per in ((True, 2048), (False, 32)):
         k0, km, inst, mean = G.geraf_chebyshev_work(cu(xyz), cu(ant), band, to_points)
         assert k0 == K
-        host = [_host_order(xyz[:, j:j + per], ant, b) for j in range(0, n, per)]
+        xs = xyz[:, _brick_order(xyz)]
+        host = [_host_order(xs[:, j:j + per], ant, b) for j in range(0, n, per)]
         assert abs(km - max(host)) <= 1 and km <= K, (km, max(host), K)
         assert inst == inst_of(km)
         counts = [min(n, j + per) - j for j in range(0, n, per)]
