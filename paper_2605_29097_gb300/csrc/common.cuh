@@ -113,12 +113,34 @@ __device__ __forceinline__ void split_coord(float x, float& h, float& l) {
     l = __fsub_rn(x, h);
 }
 
+// Coordinate split in carrier cycles (the Chebyshev kernels): X = K0 x with
+// K0 = 2 f0 / c cycles per metre (FP64 product of the FP32 coordinate),
+// X = h + l with h on the half-cycle grid (exact in FP32 below 2^22 cycles)
+// and l the FP32 rounding of the remainder (|l| <= 1/4 cycle, about 0.5 mm).
+// Differences of two h are exact, and so is the sum of their three squares
+// (multiples of 1/4 below 3 * 2^20) while every axis difference is below 1024
+// cycles (about 2 m at 77 GHz); the kernels' plan falls back to the exact
+// recurrence kernels beyond that. A range in cycles makes the carrier phase
+// its fractional part (cyc_frac).
+constexpr double kCycGrid = 2.0;
+constexpr float kCycAxisMax = 1023.9f;    // cycles: bound on every axis difference
+__device__ __forceinline__ void split_cyc(float x, double k0, float& h, float& l) {
+    const double X = k0 * (double)x;
+    const double hd = rint(X * kCycGrid) * (1.0 / kCycGrid);
+    h = (float)hd;
+    l = (float)(X - hd);
+}
+
+// Fractional part (|.| <= 0.5 + tiny) of a range rh + rl in cycles.
+__device__ __forceinline__ float cyc_frac(float rh, float rl) { return __fadd_rn(__fsub_rn(rh, rintf(rh)), rl); }
+
 // Range r = |p - q| as a double-single pair from split coordinates (p = ph +
-// pl, q = qh + ql): with dh = ph - qh (exact) and dl = pl - ql,
+// pl, q = qh + ql, in metres with the 2^-10 m grid or in cycles with the
+// half-cycle grid): with dh = ph - qh (exact) and dl = pl - ql,
 //   r^2 = |dh|^2 + sum dl (2 dh + dl),
-// the first term exact in FP32 and the second small (|dl| <= 2^-10 m), so one
-// Newton step on FP32 sqrt(r^2) gives r to ~1e-10 m (phase error < 1e-6 rad at
-// 81 GHz). About 22 instructions against ~53 for pair_range.
+// the first term exact in FP32 and the second small (|dl| at most one grid
+// step), so one Newton step on FP32 sqrt(r^2) gives r to ~1e-10 m (phase
+// error < 1e-6 rad at 81 GHz). About 22 instructions against ~53 for pair_range.
 __device__ __forceinline__ Range pair_range_split(float pxh, float pyh, float pzh, float pxl, float pyl,
                                                   float pzl, float qxh, float qyh, float qzh, float qxl,
                                                   float qyl, float qzl) {

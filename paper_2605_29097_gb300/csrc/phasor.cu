@@ -39,7 +39,8 @@ constexpr float kSqrt2 = 1.41421356237309505f;
 
 // ------------------------------------------------------------------ records
 // Point record of the phasor kernels (48 bytes); the position is split as
-// x = xh + xl (split_coord: xh on the 2^-10 m grid, xl the exact remainder):
+// x = xh + xl (split_coord: xh on the 2^-10 m grid, xl the exact remainder;
+// for the Chebyshev kernels in carrier cycles, split_cyc):
 //  render / render backward: a = (xh, yh, zh, w), b = (sqrt2*nx, sqrt2*ny, sqrt2*nz, t_eff),
 //                            c = (xl, yl, zl, e); e = 1 directional, -1 isotropic
 //  filter backward:          a = (xh, yh, zh, c_re), b = (c_im, 0, 0, 0), c = (xl, yl, zl, 0)
@@ -60,12 +61,30 @@ __device__ __forceinline__ void split3(float x, float y, float z, float4& hi, fl
     split_coord(z, hi.z, lo.z);
 }
 
+// the same in carrier cycles (split_cyc), for the Chebyshev kernels
+__device__ __forceinline__ void split3c(float x, float y, float z, double k0, float4& hi, float4& lo) {
+    split_cyc(x, k0, hi.x, lo.x);
+    split_cyc(y, k0, hi.y, lo.y);
+    split_cyc(z, k0, hi.z, lo.z);
+}
+
+// split in cycles when the call runs the Chebyshev kernels (cyc_if not NULL
+// and *cyc_if, the plan's run_cheb), else in metres for the recurrence kernels
+__device__ __forceinline__ void split3p(float x, float y, float z, const int* cyc_if, double k0, float4& hi,
+                                        float4& lo) {
+    if (cyc_if && *cyc_if)
+        split3c(x, y, z, k0, hi, lo);
+    else
+        split3(x, y, z, hi, lo);
+}
+
 // --------------------------------------------------------------- pack kernels
 // record j holds point perm[j] (perm NULL: point j)
 __global__ void pack_render_points(const float* __restrict__ xyz, const float* __restrict__ grad,
                                    const float* __restrict__ w, const float* __restrict__ t_eff,
                                    int64_t n, int64_t n_pad, int directional, PtRec* __restrict__ out,
-                                   const int* __restrict__ perm = nullptr) {
+                                   const int* __restrict__ perm = nullptr, const int* cyc_if = nullptr,
+                                   double k0 = 0.0) {
     const int64_t r_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r_ >= n_pad) return;
     const int64_t j = r_ < n && perm ? perm[r_] : r_;
@@ -75,14 +94,14 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
         const float ig = inv_grad_norm(gx, gy, gz, directional);
         const bool dir = ig > 0.0f;
         const float k = kSqrt2 * ig;
-        split3(xyz[j], xyz[n + j], xyz[2 * n + j], r.a, r.c);
+        split3p(xyz[j], xyz[n + j], xyz[2 * n + j], cyc_if, k0, r.a, r.c);
         r.a.w = w[j];
         r.b = make_float4(gx * k, gy * k, gz * k, t_eff[j]);
         r.c.w = dir ? 1.0f : -1.0f;
     } else {
         // padding: the last point's position with zero weight (inside the
         // range bound of the call and of the last split)
-        split3(xyz[n - 1], xyz[2 * n - 1], xyz[3 * n - 1], r.a, r.c);
+        split3p(xyz[n - 1], xyz[2 * n - 1], xyz[3 * n - 1], cyc_if, k0, r.a, r.c);
         r.a.w = 0.0f;
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         r.c.w = -1.0f;
@@ -92,7 +111,8 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
 
 __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const float2* __restrict__ M,
                                        const float* __restrict__ dP, int64_t n, int64_t n_pad,
-                                       PtRec* __restrict__ out, const int* __restrict__ perm = nullptr) {
+                                       PtRec* __restrict__ out, const int* __restrict__ perm = nullptr,
+                                       const int* cyc_if = nullptr, double k0 = 0.0) {
     const int64_t r_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r_ >= n_pad) return;
     const int64_t j = r_ < n && perm ? perm[r_] : r_;
@@ -105,11 +125,11 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
             cr = (float)(dP[j] * (double)m.x / mag);
             ci = (float)(dP[j] * (double)m.y / mag);
         }
-        split3(vox[j], vox[n + j], vox[2 * n + j], r.a, r.c);
+        split3p(vox[j], vox[n + j], vox[2 * n + j], cyc_if, k0, r.a, r.c);
         r.a.w = cr;
         r.b = make_float4(ci, 0.0f, 0.0f, 0.0f);
     } else {
-        split3(vox[n - 1], vox[2 * n - 1], vox[3 * n - 1], r.a, r.c);
+        split3p(vox[n - 1], vox[2 * n - 1], vox[3 * n - 1], cyc_if, k0, r.a, r.c);
         r.a.w = 0.0f;
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
@@ -838,11 +858,14 @@ constexpr int CH_KMAX = 64;
 constexpr int CH_THREADS = 128;
 constexpr int CH_TP = 32;             // points per TMA tile
 constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before it joins the outer sum
+// Part sizes of the Chebyshev sums. Smaller parts mean narrower range
+// intervals and lower orders, at the cost of more split partials, coefficient
+// tables and (to points) antenna rows; the byte caps bound those buffers.
 #ifndef GERAF_CH_PARTIAL_MIB
-#define GERAF_CH_PARTIAL_MIB 256
+#define GERAF_CH_PARTIAL_MIB 6144
 #endif
 #ifndef GERAF_CH_TABLE_MIB
-#define GERAF_CH_TABLE_MIB 1024
+#define GERAF_CH_TABLE_MIB 12288
 #endif
 #ifndef GERAF_CH_MAX_SPLITS
 #define GERAF_CH_MAX_SPLITS 512
@@ -850,14 +873,14 @@ constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before i
 #ifndef GERAF_CH_SPLIT_CTAS_PER_SM
 #define GERAF_CH_SPLIT_CTAS_PER_SM 16
 #endif
-#ifndef GERAF_CH_SPLIT_PTS_PER_BIN
-#define GERAF_CH_SPLIT_PTS_PER_BIN 0
+#ifndef GERAF_CH_SPLIT_MIN_PTS
+#define GERAF_CH_SPLIT_MIN_PTS 8192
 #endif
 #ifndef GERAF_CH_MAX_GROUPS
-#define GERAF_CH_MAX_GROUPS 64
+#define GERAF_CH_MAX_GROUPS 128
 #endif
 #ifndef GERAF_CH_GROUP_ROWS_MIB
-#define GERAF_CH_GROUP_ROWS_MIB 1024
+#define GERAF_CH_GROUP_ROWS_MIB 8192
 #endif
 constexpr size_t CH_PARTIAL_BYTES = (size_t)GERAF_CH_PARTIAL_MIB << 20;   // bound on the split partials of one call
 constexpr size_t CH_TABLE_BYTES = (size_t)GERAF_CH_TABLE_MIB << 20;       // bound on the coefficient tables of one call's parts
@@ -934,7 +957,7 @@ __device__ void bessel_j(double a, int kcount, double* out) {
 // K, and the choice between the Chebyshev form and the recurrence (the
 // coefficient tables come per part from split_plan_kernel)
 __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, const float* __restrict__ ant,
-                                 int n_ant, double Kd, int n_f, double eps, ChebPlan* __restrict__ plan) {
+                                 int n_ant, double Kd, int n_f, double eps, double k0, ChebPlan* __restrict__ plan) {
     __shared__ float box[6];
     __shared__ float rr[3][256];
     const int t = threadIdx.x;
@@ -985,8 +1008,9 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
             if (tail > eps) { K = k + 1; break; }
         }
         if (K < 2) K = 2;
-        // the split-coordinate range is exact only for axis differences below 2 m
-        const int direct = K > CH_KMAX || !(rr[2][0] < 1.99f);
+        // the split-coordinate range in cycles is exact only for axis
+        // differences below 1024 cycles (about 2 m at 77 GHz)
+        const int direct = K > CH_KMAX || !(rr[2][0] * (float)k0 < kCycAxisMax);
         if (K > CH_KMAX) K = CH_KMAX;
         plan->r_c = rc;
         plan->inv_dr = inv;
@@ -1001,9 +1025,9 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
 // The Chebyshev parts are runs of consecutive point records; so that a run is
 // a compact brick of space rather than a slab of the whole volume, the
 // Chebyshev calls pack the points in brick order: the points' bounding box cut
-// into 8 x 8 x 8 bricks numbered along a Z-curve, a stable counting sort by
-// brick (order of the caller kept inside a brick, so the result is
-// deterministic). perm[r] = the point held by record r. Each warp owns a
+// into 8 x 8 x 8 bricks numbered along a Hilbert curve (a run that ends in one
+// brick continues in a face neighbour), a stable counting sort by brick
+// (order of the caller kept inside a brick, so the result is deterministic). perm[r] = the point held by record r. Each warp owns a
 // sub-chunk of PO_SUB consecutive points: histogram per sub-chunk, exclusive
 // scan over sub-chunks in segments of PO_SEG and over the segments and the
 // buckets, then each warp places its points in order (peers of equal bucket
@@ -1013,18 +1037,53 @@ constexpr int PO_SUB = 512;
 constexpr int PO_WARPS = 16;
 constexpr int PO_SEG = 64;
 
+// Index of brick (x, y, z), 3 bits per axis, along a 3-D Hilbert curve
+// (Skilling's transpose form, AIP Conf. Proc. 707, 2004): undo the excess
+// work of the inverse transform bit plane by bit plane, Gray-encode, then
+// read the index bits out plane-major. Consecutive indices are face
+// neighbours, so a run of records that straddles two bricks stays compact.
+__device__ __forceinline__ int hilbert_brick(int x, int y, int z) {
+    int X[3] = {x, y, z};
+#pragma unroll
+    for (int Q = 4; Q > 1; Q >>= 1) {
+        const int P = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const int t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    int t = 0;
+#pragma unroll
+    for (int Q = 4; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    X[0] ^= t;
+    X[1] ^= t;
+    X[2] ^= t;
+    int h = 0;
+#pragma unroll
+    for (int j = 2; j >= 0; --j)
+        h = (h << 3) | (((X[0] >> j) & 1) << 2) | (((X[1] >> j) & 1) << 1) | ((X[2] >> j) & 1);
+    return h;
+}
+
 __device__ __forceinline__ int point_bucket(float x, float y, float z, const float (&box)[6]) {
     const float v[3] = {x, y, z};
-    int code = 0;
+    int b[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float span = box[3 + d] - box[d];
-        int b = span > 0.0f ? (int)((v[d] - box[d]) * (8.0f / span)) : 0;
-        b = min(max(b, 0), 7);
-#pragma unroll
-        for (int bit = 0; bit < 3; ++bit) code |= ((b >> bit) & 1) << (3 * bit + d);
+        const int c = span > 0.0f ? (int)((v[d] - box[d]) * (8.0f / span)) : 0;
+        b[d] = min(max(c, 0), 7);
     }
-    return code;
+    return hilbert_brick(b[0], b[1], b[2]);
 }
 
 __global__ void __launch_bounds__(32 * PO_WARPS) point_hist_kernel(const float* __restrict__ xyz, int64_t n,
@@ -1148,7 +1207,8 @@ struct ChebBinsArgs {
     const SplitPlan* splan;    // [splits][plan_blocks]
     int plan_blocks;           // antenna blocks with their own plan: 1 or gridDim.x
     const int* kmax;           // largest part order: picks the kernel instance
-    float kh, kl;              // K0 = 2 f0 / c as double-single (cycles per metre)
+    double k0;                 // K0 = 2 f0 / c, cycles per metre (positions in cycles)
+    float amp_scale;           // factor of every moment: gamma's 1 / (16 pi^2) per square cycle (render), 1
     float2* partial;           // [splits][n_ant][CH_KMAX]
     int* err;
 };
@@ -1166,28 +1226,30 @@ struct ChebBinsArgs {
 // apply return at once. Each part = (split of points, block of CH_THREADS
 // antennas) expands the bin phase over its own range interval (SplitPlan).
 // One tile of CH_TP point records against this thread's antenna: the pair's
-// range, amplitude times carrier phasor, and the moments M_k += A T_k(x) for
-// k < KE (KE even, fixed at compile time). kGuard (the 64-order instance):
-// orders past 32 run in blocks of 8 up to the part's own order K.
+// range in cycles, amplitude times carrier phasor, and the moments
+// M_k += A T_k(x) for k < KE (KE even, fixed at compile time). kGuard (the
+// 64-order instance): orders past 32 run in blocks of 8 up to the part's own
+// order K.
 template <bool kComplexAmp, int KM, int KE, bool kGuard>
 __device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const float4& Ah, const float4& Al,
-                                          float aw, float r_c, float inv_dr, float kh, float kl, int K,
-                                          float (&mr)[KM], float (&mi)[KM]) {
+                                          float aw, float r_c, float inv_dr, int K, float (&mr)[KM],
+                                          float (&mi)[KM]) {
     for (int p = 0; p < CH_TP; ++p) {
         const PtRec P = tile[p];
         const Range R = pair_range_split(P.a.x, P.a.y, P.a.z, P.c.x, P.c.y, P.c.z, Ah.x, Ah.y, Ah.z, Al.x, Al.y,
                                          Al.z);
         float ar_, ai_;
         {
-            const float fr = phase_frac(R.rh, R.rl, kh, kl);
+            const float fr = cyc_frac(R.rh, R.rl);      // carrier phase, cycles
             float sn, cs;
             __sincosf(6.28318530717958648f * fr, &sn, &cs);
             if (!kComplexAmp) {
-                const float inv_r2 = R.rs * R.rs;
-                const float nd = P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz;
-                const float D = fmaxf(nd * nd * inv_r2 - P.c.w, 0.0f);
-                const float tt = __saturatef(P.b.w - aw);
-                const float amp = P.a.w * tt * tt * (inv_r2 * kInv16Pi2) * D;
+                // A / (gamma's constant) = w T'^2 D / r^2: with n' = sqrt2 n,
+                // nd = n'.d / r and D = max(nd^2 - e, 0); u = T' / r
+                const float nd = (P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz) * R.rs;
+                const float D = fmaxf(fmaf(nd, nd, -P.c.w), 0.0f);
+                const float u = __saturatef(P.b.w - aw) * R.rs;
+                const float amp = P.a.w * (u * u) * D;
                 ar_ = amp * cs;                          // A exp(-j 2 pi K0 r)
                 ai_ = -amp * sn;
             } else {
@@ -1223,7 +1285,7 @@ __device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const 
 }
 
 #define GERAF_BINS_CASE(E) \
-    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K, mr, mi); break;
+    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, Ah, Al, A4.w, r_c, inv_dr, K, mr, mi); break;
 
 template <bool kComplexAmp, int KC>
 __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_CH_BINS_CTAS_24
@@ -1254,7 +1316,7 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
     const float r_c = sp.r_c, inv_dr = sp.inv_dr;
     const float4 A4 = args.ant[ia];                          // padded: always readable
     float4 Ah, Al;
-    split3(A4.x, A4.y, A4.z, Ah, Al);
+    split3c(A4.x, A4.y, A4.z, args.k0, Ah, Al);
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1286,14 +1348,13 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
         }
         const PtRec* tile = tiles + buf * CH_TP;
         if constexpr (KC == 8) {
-            bins_tile<kComplexAmp, KM, KM, true>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K, mr, mi);
+            bins_tile<kComplexAmp, KM, KM, true>(tile, Ah, Al, A4.w, r_c, inv_dr, K, mr, mi);
         } else {
             switch (ke) {
                 GERAF_BINS_CASE(8) GERAF_BINS_CASE(10) GERAF_BINS_CASE(12) GERAF_BINS_CASE(14)
                 GERAF_BINS_CASE(16) GERAF_BINS_CASE(18) GERAF_BINS_CASE(20) GERAF_BINS_CASE(22)
                 GERAF_BINS_CASE(24) GERAF_BINS_CASE(26) GERAF_BINS_CASE(28) GERAF_BINS_CASE(30)
-                default: bins_tile<kComplexAmp, KM, KM, false>(tile, Ah, Al, A4.w, r_c, inv_dr, args.kh, args.kl, K,
-                                                               mr, mi);
+                default: bins_tile<kComplexAmp, KM, KM, false>(tile, Ah, Al, A4.w, r_c, inv_dr, K, mr, mi);
             }
         }
         if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
@@ -1317,7 +1378,10 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
     }
     if (ia < args.n_ant) {
         float2* dst = args.partial + ((size_t)split * args.n_ant + ia) * CH_KMAX;
-        for (int k = 0; k < K; ++k) dst[k] = outer[k * CH_THREADS + t];
+        for (int k = 0; k < K; ++k) {
+            const float2 o = outer[k * CH_THREADS + t];
+            dst[k] = make_float2(o.x * args.amp_scale, o.y * args.amp_scale);
+        }
     }
 }
 
@@ -1364,7 +1428,7 @@ __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, in
 // coefficient table Cs[part][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
 // (Bessel values in FP64). kmax collects the largest part order.
 __global__ void split_plan_kernel(const float* __restrict__ box, const float4* __restrict__ ant, int n_ant,
-                                  int n_ab, int ant_per_block, double Kd, int n_f, double eps,
+                                  int n_ab, int ant_per_block, double Kd, int n_f, double eps, double k0,
                                   const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
                                   float2* __restrict__ Cs, int* __restrict__ kmax) {
     if (!gplan->run_cheb) return;
@@ -1373,14 +1437,15 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
     __shared__ float s_rc, s_inv;
     const int sp = blockIdx.x, t = threadIdx.x;
     const int b = sp % n_ab;
-    const float* bx = box + (sp / n_ab) * 6;
+    const float* bx = box + (sp / n_ab) * 6;     // in cycles
     const int i0 = b * ant_per_block, i1 = min(n_ant, i0 + ant_per_block);
+    const float k0f = (float)k0;
     float lo = INFINITY, hi = 0.0f;
     for (int i = i0 + t; i < i1; i += blockDim.x) {
         float dn = 0.0f, df = 0.0f;
-        const float4 A = ant[i];
+        const float4 A = ant[i];                  // metres
         for (int d = 0; d < 3; ++d) {
-            const float a = d == 0 ? A.x : (d == 1 ? A.y : A.z);
+            const float a = k0f * (d == 0 ? A.x : (d == 1 ? A.y : A.z));
             const float e = fmaxf(fmaxf(bx[d] - a, a - bx[3 + d]), 0.0f);
             const float f = fmaxf(fabsf(a - bx[d]), fabsf(bx[3 + d] - a));
             dn += e * e;
@@ -1399,12 +1464,15 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
         }
         __syncthreads();
     }
+    // the part's interval and table in cycles: Kc = bin spacing of the
+    // phase in cycles per cycle of range; margins 1e-6 m and 1e-5 m in cycles
+    const double Kc = Kd / k0;
     if (t == 0) {
         const double rl = rr[0][0], rh = rr[1][0];
-        const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6, 1e-5);
+        const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6 * k0, 1e-5 * k0);
         const float rc = (float)(0.5 * (rh + rl));
         const float inv = (float)(1.0 / dr);
-        const double a_max = 2.0 * 3.14159265358979323846 * (n_f - 1) * Kd / (double)inv;
+        const double a_max = 2.0 * 3.14159265358979323846 * (n_f - 1) * Kc / (double)inv;
         double J[CH_KMAX + 8];
         bessel_j(a_max, CH_KMAX + 8, J);
         int K = CH_KMAX;
@@ -1427,10 +1495,10 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
     float2* C = Cs + (size_t)sp * CH_KMAX * n_f;
     for (int n = t; n < n_f; n += blockDim.x) {
         double J[CH_KMAX];
-        const double an = 2.0 * 3.14159265358979323846 * n * Kd * dr;
+        const double an = 2.0 * 3.14159265358979323846 * n * Kc * dr;
         bessel_j(an, K, J);
         double sphi, cphi;
-        sincospi(-2.0 * (double)n * Kd * (double)s_rc, &sphi, &cphi);
+        sincospi(-2.0 * (double)n * Kc * (double)s_rc, &sphi, &cphi);
         for (int k = 0; k < K; ++k) {
             const double m = (k == 0 ? 1.0 : 2.0) * J[k];
             double pr, pi;      // (-j)^k
@@ -1528,7 +1596,7 @@ constexpr int CH_ROW = 2 + CH_KMAX;
 
 // Bounding box of each group of per_group consecutive points (xyz in [3][n]
 // layout): box[g] = (min x, min y, min z, max x, max y, max z).
-__global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int64_t per_group,
+__global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int64_t per_group, float k0f,
                                   float* __restrict__ box) {
     __shared__ float red[6][256];
     const int g = blockIdx.x;
@@ -1555,14 +1623,14 @@ __global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int6
             }
         __syncthreads();
     }
-    if (threadIdx.x < 6) box[g * 6 + threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x < 6) box[g * 6 + threadIdx.x] = red[threadIdx.x][0] * k0f;   // cycles (k0f > 0)
 }
 
 // Antenna rows of the to-points kernels, one set per point group g: row r
 // holds the antenna perm[r] (the spatial order), planned with the part
 // (g, b = r / CH_THREADS) when the groups are planned per antenna block (n_ab
 // blocks), else with the group's plan over all antennas (n_ab = 1):
-// row(g, r) = two heads (the antenna's split position; c_ant in the first),
+// row(g, r) = two heads (the antenna's split position in cycles; c_ant in the first),
 // then for k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) C_part,k(n)
 // (either factor conjugated on request), zero beyond the part's order and for
 // padding antennas. Block = GR_T records of one group (inside one antenna
@@ -1574,7 +1642,7 @@ static_assert(CH_THREADS % GR_T == 0, "a rows block stays in one antenna block")
 __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
     const float* __restrict__ ant, const float* __restrict__ c_ant, const float2* __restrict__ sig,
     const int* __restrict__ perm, int n_ant, int n_ant_pad, int n_f, int n_ab, const ChebPlan* __restrict__ plan,
-    const SplitPlan* __restrict__ gplan, const float2* __restrict__ Cs, int conj_c, int conj_sig,
+    const SplitPlan* __restrict__ gplan, const float2* __restrict__ Cs, int conj_c, int conj_sig, double k0,
     float4* __restrict__ rows) {
     if (!plan->run_cheb) return;
     __shared__ float2 sC[CH_KMAX][GR_NC + 1];
@@ -1587,7 +1655,7 @@ __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
         const int i = i0 + t;
         const int q = i < n_ant ? perm[i] : 0;
         float4 hi, lo;
-        split3(ant[q], ant[n_ant + q], ant[2 * n_ant + q], hi, lo);
+        split3c(ant[q], ant[n_ant + q], ant[2 * n_ant + q], k0, hi, lo);
         hi.w = c_ant ? c_ant[q] : 0.0f;
         lo.w = 0.0f;
         grow[(size_t)i * CH_ROW] = hi;
@@ -1654,7 +1722,8 @@ struct ChebPointsArgs {
     const SplitPlan* gplan;    // per part (group, antenna block): interval and order
     int n_ab;                  // antenna blocks of CH_THREADS records with their own plan (1: one per group)
     const int* kmax;           // largest part order
-    float kh, kl;
+    double k0;                 // K0 = 2 f0 / c, cycles per metre (positions in cycles)
+    float gscale;              // gamma's 1 / (16 pi^2) per square cycle (render adjoint)
     float* partial;
     int* err;
 };
@@ -1669,7 +1738,7 @@ static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread
 // past 32 run in blocks of 8 up to the group's own order K.
 template <int MODE, int KE, bool kGuard>
 __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, float r_c, float inv_dr,
-                                            float kh, float kl, const float4 (&ph)[TPK_V], const float4 (&pl)[TPK_V],
+                                            const float4 (&ph)[TPK_V], const float4 (&pl)[TPK_V],
                                             const float (&pnx)[TPK_V], const float (&pny)[TPK_V],
                                             const float (&pnz)[TPK_V], const float (&pte)[TPK_V],
                                             const float (&pe)[TPK_V],
@@ -1720,7 +1789,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
         upk2(Si, si[0], si[1]);
 #pragma unroll
         for (int v = 0; v < TPK_V; ++v) {
-            const float fr = phase_frac(R[v].rh, R[v].rl, kh, kl);
+            const float fr = cyc_frac(R[v].rh, R[v].rl);   // carrier phase, cycles
             float sn, cs;
             __sincosf(6.28318530717958648f * fr, &sn, &cs);
             if (MODE == MODE_FILTER) {
@@ -1756,7 +1825,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
 }
 
 #define GERAF_POINTS_CASE(E) \
-    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny, pnz, pte, pe, in); break;
+    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, r_c, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in); break;
 
 // Each group of ctas_per_group point CTAs has its own interval and order
 // (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
@@ -1810,7 +1879,7 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
     for (int v = 0; v < TPK_V; ++v) {
         const int64_t j = min(jbase + v, args.n - 1);
         if (MODE == MODE_FILTER) {
-            split3(args.vox[j], args.vox[args.n + j], args.vox[2 * args.n + j], ph[v], pl[v]);
+            split3c(args.vox[j], args.vox[args.n + j], args.vox[2 * args.n + j], args.k0, ph[v], pl[v]);
             pw[v] = pnx[v] = pny[v] = pnz[v] = pte[v] = pe[v] = 0.0f;
         } else {
             const PtRec P = args.pts[j];
@@ -1854,14 +1923,14 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
 #pragma unroll
             for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
         if constexpr (KC == 8) {
-            points_tile<MODE, KM, true>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny, pnz, pte, pe, in);
+            points_tile<MODE, KM, true>(tile, AT, K, r_c, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in);
         } else {
             switch (ke) {
                 GERAF_POINTS_CASE(8) GERAF_POINTS_CASE(10) GERAF_POINTS_CASE(12) GERAF_POINTS_CASE(14)
                 GERAF_POINTS_CASE(16) GERAF_POINTS_CASE(18) GERAF_POINTS_CASE(20) GERAF_POINTS_CASE(22)
                 GERAF_POINTS_CASE(24) GERAF_POINTS_CASE(26) GERAF_POINTS_CASE(28) GERAF_POINTS_CASE(30)
-                default: points_tile<MODE, KM, false>(tile, AT, K, r_c, inv_dr, args.kh, args.kl, ph, pl, pnx, pny,
-                                                      pnz, pte, pe, in);
+                default: points_tile<MODE, KM, false>(tile, AT, K, r_c, inv_dr, ph, pl, pnx, pny, pnz, pte, pe,
+                                                      in);
             }
         }
 #pragma unroll
@@ -1889,8 +1958,8 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             *dst = make_float2(__fsub_rn(hi[v][0], lo[v][0]), __fsub_rn(hi[v][1], lo[v][1]));
         } else {
             float* dst = args.partial + (size_t)split * 6 * args.n + j;
-            const float wk = pw[v] * kInv16Pi2;
-            const float fac[6] = {kInv16Pi2, 2.0f * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk,
+            const float wk = pw[v] * args.gscale;
+            const float fac[6] = {args.gscale, 2.0f * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk, 2.0f * kSqrt2 * wk,
                                   kSqrt2 * wk};
             float sum[6];
 #pragma unroll
@@ -1908,10 +1977,15 @@ bool use_cheb(const geraf_band* band) {
     return band->n_f >= 64;
 }
 
-void k0_split(const geraf_band* band, float* kh, float* kl) {
-    const double K0 = 2.0 * band->f0 / kC;
-    *kh = (float)K0;
-    *kl = (float)(K0 - (double)*kh);
+// K0 = 2 f0 / c: carrier cycles per metre of range (the Chebyshev kernels'
+// coordinate unit)
+double k0_of(const geraf_band* band) { return 2.0 * band->f0 / kC; }
+
+// 1 / (16 pi^2) per square cycle of range, the factor of gamma = 1 / (4 pi r)^2
+// for ranges in cycles
+float gamma_scale(const geraf_band* band) {
+    const double k0 = k0_of(band);
+    return (float)(0.0063325739776461107 * k0 * k0);
 }
 
 geraf_status check_launch(const char* what) { return cuda_status(cudaGetLastError(), what); }
@@ -1939,7 +2013,7 @@ ChebWs take_cheb(WsCarver& c, int64_t n_bbox) {
 }
 
 // Point groups of the to-points calls: consecutive point CTAs, each group with
-// its own antenna rows (at most 64 groups and CH_GROUP_ROWS_BYTES of rows; at
+// its own antenna rows (at most GERAF_CH_MAX_GROUPS groups and CH_GROUP_ROWS_BYTES of rows; at
 // least 8 CTAs = 2048 points per group), planned per (group, block of
 // CH_THREADS antenna records in the spatial order) while the parts' tables fit
 // CH_TABLE_BYTES, else per group over all antennas.
@@ -2036,12 +2110,13 @@ geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const A
                                  cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g.kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "point groups");
-    group_bbox_kernel<<<g.groups, 256, 0, st>>>(xyz, n, (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V, g.box);
+    group_bbox_kernel<<<g.groups, 256, 0, st>>>(xyz, n, (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V,
+                                                (float)k0_of(band), g.box);
     split_plan_kernel<<<g.parts, 256, 0, st>>>(g.box, ao.rec, n_ant, g.n_ab, g.n_ab > 1 ? CH_THREADS : n_ant,
-                                               2.0 * band->df / kC, band->n_f, CH_TAIL, cw.plan, g.plan, g.C, g.kmax);
+                                               2.0 * band->df / kC, band->n_f, CH_TAIL, k0_of(band), cw.plan, g.plan, g.C, g.kmax);
     cheb_group_rows_kernel<<<dim3((n_ant_pad + GR_T - 1) / GR_T, g.groups), 256, 0, st>>>(
         ant_xyz, c_ant, sig, ao.perm, n_ant, n_ant_pad, band->n_f, g.n_ab, cw.plan, g.plan, g.C, conj_c, conj_sig,
-        g.rows);
+        k0_of(band), g.rows);
     return GERAF_OK;
 }
 
@@ -2049,7 +2124,7 @@ void launch_cheb_plan(const ChebWs& w, const float* pts, int64_t n, const float*
                       const geraf_band* band, cudaStream_t st) {
     bbox_partial_kernel<<<w.n_bbox_blocks, 256, 0, st>>>(pts, n, w.bbox);
     cheb_plan_kernel<<<1, 256, 0, st>>>(w.bbox, w.n_bbox_blocks, ant, n_ant, 2.0 * band->df / kC, band->n_f, CH_TAIL,
-                                        w.plan);
+                                        k0_of(band), w.plan);
 }
 
 struct ChebBinsPlan {
@@ -2064,8 +2139,10 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant, int n_f) {
     const int64_t max_splits = std::max<int64_t>(1, (int64_t)(CH_PARTIAL_BYTES / ((size_t)n_ant * CH_KMAX * 8)));
     int64_t want = std::max<int64_t>(
         1, ((int64_t)GERAF_CH_SPLIT_CTAS_PER_SM * device_sm_count() + q.ant_blocks - 1) / q.ant_blocks);
-    if (GERAF_CH_SPLIT_PTS_PER_BIN > 0)
-        want = std::max<int64_t>(want, n_pad / ((int64_t)std::max(1, GERAF_CH_SPLIT_PTS_PER_BIN) * n_f));
+    // as many splits of at least GERAF_CH_SPLIT_MIN_PTS points as there is
+    // room for: each split is then a compact brick of the point order, and
+    // splits of that size get a plan per antenna block
+    want = std::max<int64_t>(want, n_pad / GERAF_CH_SPLIT_MIN_PTS);
     // at most GERAF_CH_MAX_SPLITS splits; each part (a split, or a split and an
     // antenna block) carries its own coefficient table
     const int64_t sp = std::min<int64_t>(std::min<int64_t>(std::min<int64_t>(max_splits, want), q.n_tiles),
@@ -2076,7 +2153,7 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant, int n_f) {
     // outweigh its FP64 plan (Bessel values of every bin): splits of at least
     // 8192 points, and at most CH_TABLE_BYTES of tables; otherwise one plan per split
     const int64_t max_parts = std::max<int64_t>(1, (int64_t)(CH_TABLE_BYTES / ((size_t)CH_KMAX * n_f * 8)));
-    const bool blocks = (int64_t)q.tiles_per_split * CH_TP >= 8192 && (int64_t)q.splits * q.ant_blocks <= max_parts;
+    const bool blocks = (int64_t)q.tiles_per_split * CH_TP >= GERAF_CH_SPLIT_MIN_PTS && (int64_t)q.splits * q.ant_blocks <= max_parts;
     q.plan_blocks = blocks ? q.ant_blocks : 1;
     return q;
 }
@@ -2141,9 +2218,12 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     if (!kComplexAmp)
         pack_render_points<<<grid1d(n_rec, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_rec,
                                                                (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts,
-                                                               po.perm);
+                                                               po.perm, cheb ? &cw.plan->run_cheb : nullptr,
+                                                               k0_of(band));
     else
-        pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts, po.perm);
+        pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts, po.perm,
+                                                                   cheb ? &cw.plan->run_cheb : nullptr,
+                                                                   k0_of(band));
     pack_antennas<<<grid1d(n_ant_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, n_ant_rec, ant);
     const int* run_direct = nullptr;
     if (cheb) {
@@ -2153,11 +2233,10 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         split_bbox_kernel<<<q.splits, 256, 0, st>>>(pts, q.n_tiles, q.tiles_per_split, sbox);
         split_plan_kernel<<<parts, 256, 0, st>>>(sbox, ao.rec, n_ant, q.plan_blocks,
                                                  q.plan_blocks > 1 ? CH_THREADS : n_ant, 2.0 * band->df / kC,
-                                                 band->n_f, CH_TAIL, cw.plan, splan, scs, kmax);
-        float kh, kl;
-        k0_split(band, &kh, &kl);
-        ChebBinsArgs ca{pts, ao.rec, n_ant, q.n_tiles, q.tiles_per_split, cw.plan, splan, q.plan_blocks, kmax, kh,
-                        kl, cpart, err};
+                                                 band->n_f, CH_TAIL, k0_of(band), cw.plan, splan, scs, kmax);
+        ChebBinsArgs ca{pts,    ao.rec, n_ant, q.n_tiles, q.tiles_per_split,   cw.plan,
+                        splan,  q.plan_blocks, kmax, k0_of(band), kComplexAmp ? 1.0f : gamma_scale(band),
+                        cpart,  err};
         const dim3 grid(q.ant_blocks, q.splits);
         cheb_bins_kernel<kComplexAmp, 3><<<grid, CH_THREADS, cheb_bins_smem(24), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 4><<<grid, CH_THREADS, cheb_bins_smem(32), st>>>(ca);
@@ -2235,10 +2314,8 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
         const geraf_status gs = launch_point_groups(pg, cw, ao, vox_p, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad,
                                                     band, reinterpret_cast<const float2*>(s), 1, 0, st);
         if (gs != GERAF_OK) return gs;
-        float kh, kl;
-        k0_split(band, &kh, &kl);
         ChebPointsArgs ca{nullptr, vox_p, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
-                          p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, kh, kl,
+                          p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, k0_of(band), 1.0f,
                           reinterpret_cast<float*>(part), err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
         cheb_points_kernel<MODE_FILTER, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
@@ -2294,7 +2371,8 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
         gather_xyz<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, n_pts, po.perm, xyz_p);
     }
     pack_render_points<<<grid1d(n_pts, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_pts,
-                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts, po.perm);
+                                                           (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts, po.perm,
+                                                           cheb ? &cw.plan->run_cheb : nullptr, k0_of(band));
     {
         const geraf_status as = smem_attrs(200 * 1024, "shared-memory opt-in", to_points_kernel<MODE_RENDER_BWD>,
                                            cheb_points_kernel<MODE_RENDER_BWD, 3>,
@@ -2308,10 +2386,9 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
         const geraf_status gs = launch_point_groups(pg, cw, ao, xyz_p, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad,
                                                     band, reinterpret_cast<const float2*>(g_s), 0, 1, st);
         if (gs != GERAF_OK) return gs;
-        float kh, kl;
-        k0_split(band, &kh, &kl);
-        ChebPointsArgs ca{pts, nullptr, n_pts, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
-                          p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, kh, kl, part, err};
+        ChebPointsArgs ca{pts,     nullptr,  n_pts,      pg.rows,     pg.group_rows,       pg.ctas_per_group,
+                          p.at,    p.n_ant_tiles, p.tiles_per_split, cw.plan, pg.plan, pg.n_ab,
+                          pg.kmax, k0_of(band),   gamma_scale(band), part,    err};
         const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
         cheb_points_kernel<MODE_RENDER_BWD, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_RENDER_BWD, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
@@ -2453,9 +2530,9 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     launch_ant_order(ao, ant_xyz, nullptr, n_ant, st);
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "chebyshev_work");
-    group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz_p, n, per_part, box);
+    group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz_p, n, per_part, (float)k0_of(band), box);
     split_plan_kernel<<<parts, 256, 0, st>>>(box, ao.rec, n_ant, n_ab, ant_per_block, 2.0 * band->df / kC,
-                                             band->n_f, CH_TAIL, cw.plan, splan, Cs, kmax);
+                                             band->n_f, CH_TAIL, k0_of(band), cw.plan, splan, Cs, kmax);
     geraf_status s = check_launch("chebyshev_work");
     if (s != GERAF_OK) return s;
     ChebPlan h;

@@ -19,6 +19,7 @@ constexpr int PW = 64;        // maximum hidden width (kernels use fixed 64-wide
 constexpr int PF = 16;        // maximum feature dimension
 constexpr int PNH = 4;        // maximum hidden layers
 constexpr int PBT = 128;      // cells per backward tile / threads per CTA
+constexpr int PWS = PW + 1;   // row stride of the backward's per-cell shared rows (thread = row: no bank conflicts)
 
 struct PropGeom {
     int G0, G1, G2, F, W, NH, D;
@@ -320,6 +321,40 @@ __global__ void prop_hist_kernel(geraf_grid gr, PropGeom g, int n_z, const float
     hist[cell] = s;
 }
 
+// The same histogram for samples with a cell index (idx): thread = grid
+// column, one pass over the column's fine rays and their n_z samples, each
+// sample added to the cell idx names (cells of other columns or out of range
+// are skipped, as in prop_hist_kernel). A cell's sum runs in the same order
+// (rays row by row, then depth) as prop_hist_kernel's, so the FP64 results
+// are the same bit for bit, without every cell of a column rescanning the
+// column's samples. Shared histogram [G2][blockDim] (conflict-free).
+__global__ void prop_hist_cols_kernel(geraf_grid gr, PropGeom g, int n_z, const float* __restrict__ alpha,
+                                      const float* __restrict__ T, const int32_t* __restrict__ idx,
+                                      double* __restrict__ hist) {
+    extern __shared__ double hs[];
+    const int t = threadIdx.x, nb = blockDim.x;
+    const int plane = g.G0 * g.G1;
+    const int col = blockIdx.x * nb + t;
+    for (int k = 0; k < g.G2; ++k) hs[k * nb + t] = 0.0;
+    if (col >= plane) return;
+    const int gy = col / g.G0, gx = col - gy * g.G0;
+    const int fx = gr.n[0] / g.G0, fy = gr.n[1] / g.G1;
+    const int64_t n_ray = (int64_t)gr.n[0] * gr.n[1];
+    for (int iy = gy * fy; iy < (gy + 1) * fy; ++iy)
+        for (int ix = gx * fx; ix < (gx + 1) * fx; ++ix) {
+            const int64_t ray = (int64_t)iy * gr.n[0] + ix;
+            for (int j = 0; j < n_z; ++j) {
+                const int64_t p = (int64_t)j * n_ray + ray;
+                const int64_t rel = (int64_t)idx[p] - col;
+                if (rel < 0 || rel % plane != 0) continue;
+                const int64_t gz = rel / plane;
+                if (gz >= g.G2) continue;
+                hs[gz * nb + t] += (double)T[p] * (double)alpha[p];
+            }
+        }
+    for (int k = 0; k < g.G2; ++k) hist[(int64_t)k * plane + col] = hs[k * nb + t];
+}
+
 // per grid column: KL(p || q) and dL/dlogits (FP64 internally)
 __global__ void prop_loss_kernel(PropGeom g, const float* __restrict__ logits, const double* __restrict__ hist,
                                  float* __restrict__ d_logits, double* __restrict__ col_loss) {
@@ -383,9 +418,9 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
     extern __shared__ float sm[];
     float* sw = sm;                               // parameters
     float* gacc = sw + g.n_params;                // parameter gradient of this CTA
-    float* hb = gacc + g.n_params;                // [PBT][PW] pre-activation adjoint
-    float* zi = hb + PBT * PW;                    // [PBT][PW] layer input
-    float* dl = zi + PBT * PW;                    // [PBT] d logits
+    float* hb = gacc + g.n_params;                // [PBT][PWS] pre-activation adjoint
+    float* zi = hb + PBT * PWS;                    // [PBT][PWS] layer input
+    float* dl = zi + PBT * PWS;                    // [PBT] d logits
     const int t = threadIdx.x;
     for (int i = t; i < g.n_params; i += PBT) {
         sw[i] = params[i];
@@ -409,13 +444,13 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
                 zz = sp_b(saved[((int64_t)(g.NH - 1) * W + u) * g.n_cells + cc], g.beta);
                 b = Wo[u] * dlog;
             }
-            zi[t * PW + u] = zz;
+            zi[t * PWS + u] = zz;
             zb[u] = b;
         }
         __syncthreads();
         for (int k = t; k < W; k += PBT) {
             float a = 0.0f;
-            for (int q = 0; q < PBT; ++q) a = fmaf(dl[q], zi[q * PW + k], a);
+            for (int q = 0; q < PBT; ++q) a = fmaf(dl[q], zi[q * PWS + k], a);
             gacc[g.off_w[g.NH] + k] += a;
         }
         if (t == 0) {
@@ -434,7 +469,7 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
                     const float h = saved[((int64_t)l * W + u) * g.n_cells + cc];
                     v = zb[u] * sig(g.beta * h);
                 }
-                hb[t * PW + u] = v;
+                hb[t * PWS + u] = v;
             }
 #pragma unroll
             for (int k = 0; k < PW; ++k) {
@@ -443,19 +478,19 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
                     if (l > 0) v = sp_b(saved[((int64_t)(l - 1) * W + k) * g.n_cells + cc], g.beta);
                     else v = __half2float(feat[cc * g.F + k]);
                 }
-                zi[t * PW + k] = v;
+                zi[t * PWS + k] = v;
             }
             __syncthreads();
             // weight / bias gradient sums over the tile's cells, thread = entry
             for (int e = t; e < W * K; e += PBT) {
                 const int u = e / K, k = e - u * K;
                 float a = 0.0f;
-                for (int q = 0; q < PBT; ++q) a = fmaf(hb[q * PW + u], zi[q * PW + k], a);
+                for (int q = 0; q < PBT; ++q) a = fmaf(hb[q * PWS + u], zi[q * PWS + k], a);
                 gacc[g.off_w[l] + e] += a;
             }
             for (int u = t; u < W; u += PBT) {
                 float a = 0.0f;
-                for (int q = 0; q < PBT; ++q) a += hb[q * PW + u];
+                for (int q = 0; q < PBT; ++q) a += hb[q * PWS + u];
                 gacc[g.off_b[l] + u] += a;
             }
             // adjoint of the layer input, thread = cell
@@ -465,7 +500,7 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
             for (int k = 0; k < PW; ++k) {
                 float a = 0.0f;
                 if (k < K) {
-                    for (int u = 0; u < W; ++u) a = fmaf(Wl[u * K + k], hb[t * PW + u], a);
+                    for (int u = 0; u < W; ++u) a = fmaf(Wl[u * K + k], hb[t * PWS + u], a);
                 }
                 nz[k] = a;
             }
@@ -564,10 +599,17 @@ geraf_status sample_backward_impl(const geraf_proposal* p, const geraf_grid* gr,
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
     if (*ws_bytes < c.used)
         return fail(GERAF_ERR_WORKSPACE, "sample_backward: workspace %zu < %zu bytes", *ws_bytes, c.used);
-    prop_hist_kernel<<<g1(g.n_cells, 128), 128, 0, st>>>(*gr, g, n_z, alpha, T, idx, hist);
+    if (idx) {
+        int hb = 32;
+        while (hb > 1 && (size_t)g.G2 * hb * sizeof(double) > 32768) hb /= 2;
+        prop_hist_cols_kernel<<<g1(plane, hb), hb, (size_t)g.G2 * hb * sizeof(double), st>>>(*gr, g, n_z, alpha, T,
+                                                                                            idx, hist);
+    } else {
+        prop_hist_kernel<<<g1(g.n_cells, 128), 128, 0, st>>>(*gr, g, n_z, alpha, T, idx, hist);
+    }
     prop_loss_kernel<<<g1(plane, 128), 128, 0, st>>>(g, logits, hist, dlog, col_loss);
     if (loss) sum_doubles_1<<<1, 256, 0, st>>>(col_loss, plane, loss);
-    const size_t smem = (size_t)(2 * g.n_params + 2 * PBT * PW + PBT) * sizeof(float);
+    const size_t smem = (size_t)(2 * g.n_params + 2 * PBT * PWS + PBT) * sizeof(float);
     {
         const geraf_status as = smem_attrs(220 * 1024, "shared-memory opt-in", prop_backward_kernel);
         if (as != GERAF_OK) return as;
