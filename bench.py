@@ -50,8 +50,18 @@ DTYPES = {"fp32": "f32", "bf16": "f32 phasor sums + bf16 MLP (fp32 accumulate)"}
 # Chebyshev form, per (point, antenna) pair and order k: the three-term
 # recurrence of T_k (1 FMA) and the complex moment or series sum (2 FMA) =
 # 6 flops per order.
+# Besides the orders, the Chebyshev form does fixed arithmetic per pair, FP32
+# flops (FMA = 2) counted from its steps: the range as a double-single from
+# split coordinates in carrier cycles (differences 9, |dh|^2 5, cross term 11,
+# sum, square root product and Newton correction 6: 32), the carrier phase's
+# fractional cycle and angle (3), x and 2x (4), and the call's own terms:
+# render, the amplitude w (T'/r)^2 D and its product with the phasor (15);
+# render adjoint, Re(conj(g) x the series sum) and the chain rule of
+# A = w T'^2 gamma D into its five sums (30); filter, the phasor-rotated series
+# sum into M (8); filter adjoint, the complex amplitude times the phasor (6).
 FLOPS_PER_TERM = {"render": 10, "filter_backward": 10, "filter": 8, "render_backward": 8}
 CHEB_FLOPS_PER_ORDER = 6
+CHEB_FLOPS_PER_PAIR = {"render": 54, "render_backward": 69, "filter": 47, "filter_backward": 45}
 PHASOR_CALLS = ("render", "render_backward", "filter", "filter_backward")
 MLP_CALLS = ("fields", "fields_backward")
 TIMED_CALLS = PHASOR_CALLS + MLP_CALLS
@@ -476,7 +486,7 @@ def call_flops(name, pairs, n_f, order, mlp_macs=0, n_mlp_pts=0):
     if name in MLP_CALLS:
         return 2 * mlp_macs * n_mlp_pts
     if order > 0:
-        return pairs * order * CHEB_FLOPS_PER_ORDER
+        return pairs * (order * CHEB_FLOPS_PER_ORDER + CHEB_FLOPS_PER_PAIR[name])
     return pairs * n_f * FLOPS_PER_TERM[name]
 
 
@@ -674,7 +684,9 @@ def roofline_of(m, peaks, sm_count):
         r.update(ms=round(ms, 3), tflops=tf, frac=tf / r["peak"])
         if nm in PHASOR_CALLS and order > 0:
             fw = call_flops(nm, pairs[nm], n_f, whole[nm])
+            fo = pairs[nm] * order * CHEB_FLOPS_PER_ORDER
             r.update(orders_per_pair=round(order, 3), whole_set_order=whole[nm],
+                     frac_orders_only=fo / (ms * 1e-3) / 1e12 / fp32_peak,
                      frac_whole_set_order=fw / (ms * 1e-3) / 1e12 / fp32_peak)
         return r
 
@@ -768,10 +780,12 @@ def main():
                          "unit": "TFLOP/s", "frac": d["frac"], "traffic": traffic, "traffic_basis": traffic_basis,
                          "peak_basis": (f"{sm_count} SMs x 128 FP32 lanes x 2 flops (FMA) x {max_mhz:.0f} MHz"
                                         if d["bound"] == "alu" else d["peak_basis"]),
-                         "work_basis": ("Chebyshev phasor sums: pairs x orders evaluated per pair x 6 flops "
-                                        "(the running instance's orders per split or point group, mean over "
-                                        "the points, geraf_chebyshev_work; calls[*].frac_whole_set_order "
-                                        "counts one expansion of the whole set's order instead); per-bin "
+                         "work_basis": ("Chebyshev phasor sums: pairs x (the form's fixed per-pair flops "
+                                        f"{CHEB_FLOPS_PER_PAIR} + 6 flops x orders evaluated per pair) (the "
+                                        "running instance's orders per split or point group, mean over the "
+                                        "points, geraf_chebyshev_work; calls[*].frac_orders_only counts the "
+                                        "orders alone, calls[*].frac_whole_set_order one expansion of the "
+                                        "whole set's order instead); per-bin "
                                         "recurrence: terms x 10 (render, filter adjoint) or 8 (filter, render "
                                         f"adjoint) flops; MLP forward 2 x {m['mlp_fwd_macs']} and adjoint "
                                         f"2 x {m['mlp_bwd_macs']} flops per point"),

@@ -387,23 +387,27 @@ struct TcBwdArgs {
 };
 
 // head: dL/dW_head, dL/db_head (from the BF16-rounded last activations) and
-// the adjoint of the last hidden activation (through the FP32 head weights)
-__global__ void __launch_bounds__(256) mlp_tc_head_bwd_kernel(const TcBwdArgs a) {
-    __shared__ float red[2 * 256];
-    __shared__ float redb[2 * 2];
+// the adjoint of the last hidden activation (through the FP32 head weights);
+// thread = (unit, point slot of HB_SLOTS), R points per slot in flight
+constexpr int HB_SLOTS = 8;
+constexpr int HB_THREADS = HB_SLOTS * TW;
+__global__ void __launch_bounds__(HB_THREADS) mlp_tc_head_bwd_kernel(const TcBwdArgs a) {
+    __shared__ float red[2 * HB_THREADS];
+    __shared__ float redb[2 * HB_SLOTS];
     const TcGeom& g = a.g;
-    const int t = threadIdx.x, u = t & (TW - 1), half = t >> 7;
+    const int t = threadIdx.x, u = t & (TW - 1), half = t >> 7;   // half: the thread's point slot
     const float* Wh = a.params + g.off_w[g.NH];
     const float w0 = Wh[u], w1 = Wh[TW + u];
     const float* hsv = a.saved + (int64_t)(g.NH - 1) * g.n * 4 * TW;
     const float* asv = a.saved + (int64_t)g.NH * g.n * 4 * TW;
     float gw0 = 0.0f, gw1 = 0.0f, gb0 = 0.0f, gb1 = 0.0f;
-    constexpr int R = 8;                                   // points per thread per round, loads in flight
-    for (int64_t base = (int64_t)blockIdx.x * 2 * R; base < g.n; base += (int64_t)gridDim.x * 2 * R) {
+    constexpr int R = 4;                                   // points per thread per round, loads in flight
+    for (int64_t base = (int64_t)blockIdx.x * HB_SLOTS * R; base < g.n;
+         base += (int64_t)gridDim.x * HB_SLOTS * R) {
         float df[R], dl[R], dG[R][3], h0[R], hd[R][3];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t j = base + 2 * r + half;
+            const int64_t j = base + HB_SLOTS * r + half;
             const bool ok = j < g.n;
             const int64_t jj = ok ? j : 0;
             const float* h = hsv + jj * 4 * TW;
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(256) mlp_tc_head_bwd_kernel(const TcBwdArgs a)
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t j = base + 2 * r + half;
+            const int64_t j = base + HB_SLOTS * r + half;
             if (j >= g.n) continue;
             float z, sg;
             act_pair(h0[r], g.beta, 1.0f / g.beta, z, sg);
@@ -437,22 +441,32 @@ __global__ void __launch_bounds__(256) mlp_tc_head_bwd_kernel(const TcBwdArgs a)
         }
     }
     red[t] = gw0;
-    red[256 + t] = gw1;
+    red[HB_THREADS + t] = gw1;
     if (u == 0) { redb[2 * half] = gb0; redb[2 * half + 1] = gb1; }
     __syncthreads();
     float* out = a.partial + (int64_t)blockIdx.x * a.n_params;
-    if (t < TW) {
-        out[g.off_w[g.NH] + t] = red[t] + red[t + TW];
-        out[g.off_w[g.NH] + TW + t] = red[256 + t] + red[256 + t + TW];
+    if (t < TW) {                                     // slots added in a fixed order
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int q = 0; q < HB_SLOTS; ++q) {
+            s0 += red[q * TW + t];
+            s1 += red[HB_THREADS + q * TW + t];
+        }
+        out[g.off_w[g.NH] + t] = s0;
+        out[g.off_w[g.NH] + TW + t] = s1;
     }
     if (t == 0) {
-        out[g.off_b[g.NH]] = redb[0] + redb[2];
-        out[g.off_b[g.NH] + 1] = redb[1] + redb[3];
+        float b0 = 0.0f, b1 = 0.0f;
+        for (int q = 0; q < HB_SLOTS; ++q) {
+            b0 += redb[2 * q];
+            b1 += redb[2 * q + 1];
+        }
+        out[g.off_b[g.NH]] = b0;
+        out[g.off_b[g.NH] + 1] = b1;
     }
 }
 
 struct BwdLayout {
-    uint32_t wt, hbB, hbA, zB, zs, hsb, bar;
+    uint32_t wt, hbB, hbA, zB, zs, hsb, zin, bar;
     uint32_t total;
 };
 
@@ -465,6 +479,7 @@ __host__ __device__ inline BwdLayout bwd_layout(int kin) {
     L.zB = off;  off += (uint32_t)kin * BCOL * 2u;          // Z: rows k, K = 64 columns
     L.zs = off;  off += BCOL * TW * 4u;                     // FP32 staging [64][128]
     L.hsb = off; off += BCOL * TW * 4u;                     // FP32 staging [64][128]
+    L.zin = off; off += BCOL * TW * 4u;                     // FP32 staging [64][128]: the layer input's pre-activations
     L.bar = off; off += 16u + 4u * TW * 4u;                 // barrier, TMEM slot, abort flag, bias partials
     L.total = off;
     return L;
@@ -501,6 +516,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
     unsigned char* zB = smem + L.zB;
     float* zs = reinterpret_cast<float*>(smem + L.zs);
     float* hsb = reinterpret_cast<float*>(smem + L.hsb);
+    float* zin = reinterpret_cast<float*>(smem + L.zin);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 8);
     int* abort_flag = reinterpret_cast<int*>(smem + L.bar + 12);
@@ -541,10 +557,17 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
     float accb = 0.0f;
     bool first = true;
 
+    // the tile's three FP32 inputs (activation adjoint, this layer's and the
+    // layer below's pre-activations), all in flight; the next tile's are
+    // issued while this tile's MMAs, read-back and stores run
+    auto stage_tile = [&](int64_t jt) {
+        stage64(zs, a.zbar, jt, g.n);
+        stage64(hsb, hs, jt, g.n);
+        if (hin) stage64(zin, hin, jt, g.n);
+    };
+    if (blockIdx.x < n_tiles) stage_tile((int64_t)blockIdx.x * BTP);
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t j0 = (int64_t)tile * BTP;
-        stage64(zs, a.zbar, j0, g.n);
-        stage64(hsb, hs, j0, g.n);
         cp_async_wait_all();
         __syncthreads();
         // pre-activation adjoint of unit uu for 4 points: 16 columns, hi and lo
@@ -594,16 +617,12 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
                 *reinterpret_cast<uint4*>(hbB[1] + o) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
             }
         }
-        __syncthreads();
         // the layer's BF16 input Z (thread = input unit uu, 4 points), as the forward rounded it
         if (hin) {
-            stage64(zs, hin, j0, g.n);
-            cp_async_wait_all();
-            __syncthreads();
             uint32_t q[8];
 #pragma unroll
             for (int pp = 0; pp < 4; ++pp) {
-                const float* x = zs + (16 * ch + 4 * pp) * TW + uu;
+                const float* x = zin + (16 * ch + 4 * pp) * TW + uu;
                 const float x0 = x[0];
                 float z0, s0;
                 act_pair(x0, g.beta, inv_beta, z0, s0);
@@ -626,6 +645,8 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
+        // the staging buffers are consumed: the next tile's inputs may land
+        if (tile + (int)gridDim.x < n_tiles) stage_tile((int64_t)(tile + gridDim.x) * BTP);
         if (t == 0) {
             const uint32_t zb_a = smem_u32(zB);
             for (int h = 0; h < 2; ++h) {
@@ -669,6 +690,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) mlp_tc_layer_bwd_kernel(const TcB
         tc::fence_before_sync();
         __syncthreads();     // the next tile's staging and operands overwrite this tile's
     }
+    cp_async_wait_all();      // a prefetch left in flight by an abort lands before the CTA exits
     redb[ch * TW + uu] = accb;
     if (*abort_flag) {
         if (t == 0) {
@@ -738,7 +760,7 @@ geraf_status mlp_tc_backward_impl(const geraf_field_desc* d, const float* xyz, i
     }
     TcBwdArgs a{g, d->params, xyz, static_cast<const float*>(saved), d_sdf, d_grad, d_refl, zbar, partial,
                 n_params, 0, device_error_word()};
-    mlp_tc_head_bwd_kernel<<<n_cta, 256, 0, st>>>(a);
+    mlp_tc_head_bwd_kernel<<<n_cta, HB_THREADS, 0, st>>>(a);
     for (int l = g.NH - 1; l >= 0; --l) {
         a.layer = l;
         const size_t smem = bwd_layout(l == 0 ? g.K0p : TW).total + 1024;
