@@ -61,54 +61,97 @@ __device__ __forceinline__ float sp_b(float h, float beta) {
 __device__ __forceinline__ float sig(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // ---------------------------------------------------------- network forward
-__global__ void __launch_bounds__(128) prop_forward_kernel(PropGeom g, const __half* __restrict__ feat,
-                                                           const float* __restrict__ params,
-                                                           float* __restrict__ logits, float* __restrict__ saved) {
-    extern __shared__ float sw[];
-    for (int i = threadIdx.x; i < g.n_params; i += blockDim.x) sw[i] = params[i];
-    __syncthreads();
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= g.n_cells) return;
-    float z[PW], h[PW];
-#pragma unroll
-    for (int k = 0; k < PW; ++k) z[k] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < PF; ++k)
-        if (k < g.F) z[k] = __half2float(feat[c * g.F + k]);
-    for (int l = 0; l < g.NH; ++l) {
-        const float* Wl = sw + g.off_w[l];
-        const float* bl = sw + g.off_b[l];
-        const int K = g.k_in[l];
-#pragma unroll
-        for (int u = 0; u < PW; ++u) {
-            float a = 0.0f;
-            if (u < g.W) {
-                a = bl[u];
-#pragma unroll
-                for (int k = 0; k < PW; ++k)
-                    if (k < K) a = fmaf(Wl[u * K + k], z[k], a);
-            }
-            h[u] = a;
-        }
-#pragma unroll
-        for (int u = 0; u < PW; ++u) {
-            if (u < g.W) {
-                if (saved) saved[((int64_t)l * g.W + u) * g.n_cells + c] = h[u];
-                z[u] = sp_b(h[u], g.beta);
-            } else {
-                z[u] = 0.0f;
-            }
-        }
-    }
-    const float* Wo = sw + g.off_w[g.NH];
-    float a = sw[g.off_b[g.NH]];
-#pragma unroll
-    for (int k = 0; k < PW; ++k)
-        if (k < g.W) a = fmaf(Wo[k], z[k], a);
-    logits[c] = a;
+// CTA = PFT cells; the hidden layers as register-tiled products: thread =
+// (block of 8 cells, block of 8 units), 64 accumulators, the layer input held
+// transposed in shared memory [k][cell] and the weights transposed [k][unit],
+// so each input index k costs four 16-byte loads for 64 FMAs. Every unit's
+// sum starts from its bias and adds the inputs in index order, as a plain
+// dot product would. The output layer (one logit) runs per cell.
+constexpr int PFT = 128;                 // cells per forward CTA
+constexpr int PZS = PFT + 4;             // row stride of the transposed activations
+static_assert(PW % 8 == 0 && PFT == 16 * 8, "forward tiling: 16 cell blocks x 8 unit blocks of 8");
+
+size_t prop_forward_smem(const PropGeom& g) {
+    return ((size_t)g.NH * PW * PW + (size_t)g.NH * PW + PW + 4 + (size_t)PW * PZS) * sizeof(float);
 }
 
-// per grid column: q = (1 - eps) softmax + eps / G2 (FP64 internally)
+__global__ void __launch_bounds__(PFT) prop_forward_kernel(PropGeom g, const __half* __restrict__ feat,
+                                                           const float* __restrict__ params,
+                                                           float* __restrict__ logits, float* __restrict__ saved) {
+    extern __shared__ __align__(16) float sm[];
+    float* wt = sm;                                  // [NH][PW k][PW u], zero for u >= W or k >= K
+    float* bs = wt + (size_t)g.NH * PW * PW;         // [NH][PW]
+    float* wo = bs + g.NH * PW;                      // [PW] output weights, then the output bias
+    float* zs = wo + PW + 4;                         // [PW k][PZS]: the layer input, transposed
+    const int t = threadIdx.x;
+    for (int i = t; i < g.NH * PW * PW; i += PFT) {
+        const int l = i / (PW * PW), r = i - l * PW * PW, k = r / PW, u = r - k * PW;
+        const int K = g.k_in[l];
+        wt[i] = (u < g.W && k < K) ? params[g.off_w[l] + u * K + k] : 0.0f;
+    }
+    for (int i = t; i < g.NH * PW; i += PFT) {
+        const int l = i / PW, u = i - l * PW;
+        bs[i] = u < g.W ? params[g.off_b[l] + u] : 0.0f;
+    }
+    for (int i = t; i < PW; i += PFT) wo[i] = i < g.W ? params[g.off_w[g.NH] + i] : 0.0f;
+    if (t == 0) wo[PW] = params[g.off_b[g.NH]];
+    const int64_t c0 = (int64_t)blockIdx.x * PFT;
+    {
+        const int64_t c = min(c0 + t, g.n_cells - 1);
+        for (int k = 0; k < g.F; ++k) zs[k * PZS + t] = __half2float(feat[c * g.F + k]);
+    }
+    __syncthreads();
+    const int ci = t >> 3, ui = t & 7;               // cells 8 ci .. + 7, units 8 ui .. + 7
+    for (int l = 0; l < g.NH; ++l) {
+        const int K = g.k_in[l];
+        const float* wl = wt + (size_t)l * PW * PW;
+        float acc[8][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float b = bs[l * PW + 8 * ui + j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i][j] = b;
+        }
+        for (int k = 0; k < K; ++k) {
+            const float4 z0 = *reinterpret_cast<const float4*>(zs + k * PZS + 8 * ci);
+            const float4 z1 = *reinterpret_cast<const float4*>(zs + k * PZS + 8 * ci + 4);
+            const float4 w0 = *reinterpret_cast<const float4*>(wl + k * PW + 8 * ui);
+            const float4 w1 = *reinterpret_cast<const float4*>(wl + k * PW + 8 * ui + 4);
+            const float zc[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            const float wu[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(wu[j], zc[i], acc[i][j]);
+        }
+        __syncthreads();                              // every thread has read this layer's input
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int u = 8 * ui + j;
+            if (u >= g.W) continue;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t c = c0 + 8 * ci + i;
+                if (saved && c < g.n_cells) saved[((int64_t)l * g.W + u) * g.n_cells + c] = acc[i][j];
+            }
+            float4 v0, v1;
+            v0.x = sp_b(acc[0][j], g.beta); v0.y = sp_b(acc[1][j], g.beta);
+            v0.z = sp_b(acc[2][j], g.beta); v0.w = sp_b(acc[3][j], g.beta);
+            v1.x = sp_b(acc[4][j], g.beta); v1.y = sp_b(acc[5][j], g.beta);
+            v1.z = sp_b(acc[6][j], g.beta); v1.w = sp_b(acc[7][j], g.beta);
+            *reinterpret_cast<float4*>(zs + u * PZS + 8 * ci) = v0;
+            *reinterpret_cast<float4*>(zs + u * PZS + 8 * ci + 4) = v1;
+        }
+        __syncthreads();
+    }
+    const int64_t c = c0 + t;
+    if (c < g.n_cells) {
+        float a = wo[PW];
+        for (int k = 0; k < g.W; ++k) a = fmaf(wo[k], zs[k * PZS + t], a);
+        logits[c] = a;
+    }
+}
+
 __global__ void prop_q_kernel(PropGeom g, const float* __restrict__ logits, float* __restrict__ q) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     const int plane = g.G0 * g.G1;
@@ -481,12 +524,34 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
                 zi[t * PWS + k] = v;
             }
             __syncthreads();
-            // weight / bias gradient sums over the tile's cells, thread = entry
-            for (int e = t; e < W * K; e += PBT) {
-                const int u = e / K, k = e - u * K;
-                float a = 0.0f;
-                for (int q = 0; q < PBT; ++q) a = fmaf(hb[q * PWS + u], zi[q * PWS + k], a);
-                gacc[g.off_w[l] + e] += a;
+            // weight / bias gradient sums over the tile's cells: thread = block
+            // of 4 units x 8 inputs, each entry summed over the cells in order
+            {
+                const int KB = (K + 7) / 8;
+                for (int e = t; e < (W + 3) / 4 * KB; e += PBT) {
+                    const int u0 = 4 * (e / KB), k0 = 8 * (e - (e / KB) * KB);
+                    float acc[4][8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+                    for (int q = 0; q < PBT; ++q) {
+                        float hv[4], zv[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) hv[i] = hb[q * PWS + min(u0 + i, PW - 1)];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) zv[j] = zi[q * PWS + min(k0 + j, PW - 1)];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(hv[i], zv[j], acc[i][j]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (u0 + i < W && k0 + j < K) gacc[g.off_w[l] + (u0 + i) * K + k0 + j] += acc[i][j];
+                }
             }
             for (int u = t; u < W; u += PBT) {
                 float a = 0.0f;
@@ -497,12 +562,13 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
             const float* Wl = sw + g.off_w[l];
             float nz[PW];
 #pragma unroll
-            for (int k = 0; k < PW; ++k) {
-                float a = 0.0f;
-                if (k < K) {
-                    for (int u = 0; u < W; ++u) a = fmaf(Wl[u * K + k], hb[t * PWS + u], a);
-                }
-                nz[k] = a;
+            for (int k = 0; k < PW; ++k) nz[k] = 0.0f;
+            for (int u = 0; u < W; ++u) {             // each nz[k] summed over u in order
+                const float h = hb[t * PWS + u];
+                const float* wr = Wl + u * K;
+#pragma unroll
+                for (int k = 0; k < PW; ++k)
+                    if (k < K) nz[k] = fmaf(wr[k], h, nz[k]);
             }
             if (l == 0 && valid) {
                 for (int k = 0; k < g.F; ++k) d_feat[c * g.F + k] = nz[k];
@@ -541,7 +607,11 @@ geraf_status proposal_density_impl(const geraf_proposal* p, float* logits, float
     if (!make_prop(p, &g)) return GERAF_ERR_INVALID_ARG;
     if (saved && saved_bytes < (size_t)g.NH * g.W * g.n_cells * sizeof(float))
         return fail(GERAF_ERR_WORKSPACE, "proposal_density: saved buffer too small");
-    prop_forward_kernel<<<g1(g.n_cells, 128), 128, g.n_params * sizeof(float), st>>>(
+    {
+        const geraf_status as = smem_attrs((int)prop_forward_smem(g), "shared-memory opt-in", prop_forward_kernel);
+        if (as != GERAF_OK) return as;
+    }
+    prop_forward_kernel<<<g1(g.n_cells, PFT), PFT, prop_forward_smem(g), st>>>(
         g, static_cast<const __half*>(p->features), p->params, logits, static_cast<float*>(saved));
     if (q) prop_q_kernel<<<g1((int64_t)g.G0 * g.G1, 128), 128, 0, st>>>(g, logits, q);
     return cuda_status(cudaGetLastError(), "proposal_density");
