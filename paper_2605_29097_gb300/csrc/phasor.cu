@@ -1427,6 +1427,96 @@ __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, in
 // its order K (the whole call's rule: Bessel tail <= eps), and its FP32
 // coefficient table Cs[part][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
 // (Bessel values in FP64). kmax collects the largest part order.
+// Double-single FP32 arithmetic (value = h + l, |l| <= ulp(h) / 2) for the
+// coefficient tables: error-free products by FMA and Knuth's two-sum, so the
+// Bessel recurrence keeps ~44 bits without FP64 (slow on this part).
+struct DS {
+    float h, l;
+};
+__device__ __forceinline__ DS ds_renorm(float s, float e) {
+    const float h = __fadd_rn(s, e);
+    return DS{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DS ds_mul(DS a, DS b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ds_renorm(p, e);
+}
+__device__ __forceinline__ DS ds_mulf(DS a, float b) {
+    const float p = __fmul_rn(a.h, b);
+    float e = __fmaf_rn(a.h, b, -p);
+    e = __fmaf_rn(a.l, b, e);
+    return ds_renorm(p, e);
+}
+__device__ __forceinline__ DS ds_add(DS a, DS b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return ds_renorm(s, e);
+}
+
+// C[k n_f] for k < K, one bin: (2 - [k = 0]) J_k(a) (-j)^k (cphi + j sphi),
+// J_k by Miller's backward recurrence in double-single, normalised by
+// J_0 + 2 sum J_2m = 1. Two passes over the same recurrence: the first finds
+// the normalisation and how often the running values were rescaled (by
+// 1e-20 whenever they pass 1e20), the second writes each J_k scaled into the
+// final scale (a value recorded two or more rescales before the end is below
+// 1e-20 of the largest and written as 0).
+__device__ void bessel_table_ds(double a, int K, float cphi, float sphi, float2* __restrict__ C, int n_f) {
+    if (!(a > 1e-20)) {                      // J_0 = 1, the others vanish
+        for (int k = 0; k < K; ++k) C[(size_t)k * n_f] = k == 0 ? make_float2(cphi, sphi) : make_float2(0.0f, 0.0f);
+        return;
+    }
+    int start = K + 20 + (int)a;
+    start += start & 1;
+    const double inv = 2.0 / a;
+    const DS inv2{(float)inv, (float)(inv - (double)(float)inv)};
+    int R = 0;
+    DS nrm{0.0f, 0.0f};
+    for (int pass = 0; pass < 2; ++pass) {
+        DS jp1{0.0f, 0.0f}, j{1e-30f, 0.0f};
+        DS acc{0.0f, 0.0f};
+        int r = 0;
+        float inv_n = 0.0f;
+        if (pass == 1) inv_n = (float)(1.0 / ((double)nrm.h + (double)nrm.l));
+        for (int k = start; k >= 1; --k) {
+            const DS jm1 = ds_add(ds_mul(ds_mulf(inv2, (float)k), j), DS{-jp1.h, -jp1.l});
+            jp1 = j;
+            j = jm1;
+            if (fabsf(j.h) > 1e20f) {
+                j = ds_mulf(j, 1e-20f);
+                jp1 = ds_mulf(jp1, 1e-20f);
+                acc = ds_mulf(acc, 1e-20f);
+                ++r;
+            }
+            const int q = k - 1;
+            if (pass == 0) {
+                if ((q & 1) == 0 && q > 0) acc = ds_add(acc, ds_mulf(j, 2.0f));
+            } else if (q < K) {
+                const int lag = R - r;
+                float v = lag >= 2 ? 0.0f : __fadd_rn(j.h, j.l) * inv_n;
+                if (lag == 1) v *= 1e-20f;
+                const float m = q == 0 ? v : 2.0f * v;
+                float ar, ai;                    // m (-j)^q
+                switch (q & 3) {
+                    case 0: ar = m; ai = 0.0f; break;
+                    case 1: ar = 0.0f; ai = -m; break;
+                    case 2: ar = -m; ai = 0.0f; break;
+                    default: ar = 0.0f; ai = m; break;
+                }
+                C[(size_t)q * n_f] = make_float2(cphi * ar - sphi * ai, cphi * ai + sphi * ar);
+            }
+        }
+        if (pass == 0) {
+            nrm = ds_add(acc, j);                // + J_0
+            R = r;
+        }
+    }
+}
+
 __global__ void split_plan_kernel(const float* __restrict__ box, const float4* __restrict__ ant, int n_ant,
                                   int n_ab, int ant_per_block, double Kd, int n_f, double eps, double k0,
                                   const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
@@ -1494,23 +1584,10 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
     const double dr = 1.0 / (double)s_inv;
     float2* C = Cs + (size_t)sp * CH_KMAX * n_f;
     for (int n = t; n < n_f; n += blockDim.x) {
-        double J[CH_KMAX];
         const double an = 2.0 * 3.14159265358979323846 * n * Kc * dr;
-        bessel_j(an, K, J);
         double sphi, cphi;
         sincospi(-2.0 * (double)n * Kc * (double)s_rc, &sphi, &cphi);
-        for (int k = 0; k < K; ++k) {
-            const double m = (k == 0 ? 1.0 : 2.0) * J[k];
-            double pr, pi;      // (-j)^k
-            switch (k & 3) {
-                case 0: pr = 1.0; pi = 0.0; break;
-                case 1: pr = 0.0; pi = -1.0; break;
-                case 2: pr = -1.0; pi = 0.0; break;
-                default: pr = 0.0; pi = 1.0; break;
-            }
-            const double ar = m * pr, ai = m * pi;
-            C[(size_t)k * n_f + n] = make_float2((float)(cphi * ar - sphi * ai), (float)(cphi * ai + sphi * ar));
-        }
+        bessel_table_ds(an, K, (float)cphi, (float)sphi, C + n, n_f);
     }
 }
 
