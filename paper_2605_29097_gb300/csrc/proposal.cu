@@ -471,25 +471,32 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
     }
     __syncthreads();
     const int W = g.W;
+    // saved pre-activations of layer ll for the tile's cells into rows
+    // dst[cell * PWS + unit], every load in flight (coalesced along the cells)
+    auto stage = [&](float* dst, int ll, int64_t tile0) {
+        const float* src = saved + (int64_t)ll * W * g.n_cells;
+        for (int i = t; i < W * PBT; i += PBT) {
+            const int u = i / PBT, q = i - u * PBT;
+            const int64_t cq = min(tile0 + q, g.n_cells - 1);
+            cp_async4(dst + q * PWS + u, src + (int64_t)u * g.n_cells + cq);
+        }
+    };
     for (int64_t tile = blockIdx.x; tile * PBT < g.n_cells; tile += gridDim.x) {
         const int64_t c = tile * PBT + t;
         const bool valid = c < g.n_cells;
         const int64_t cc = valid ? c : g.n_cells - 1;
         // output layer: zin = softplus(h_{NH-1}), hbar = d_logit
+        stage(zi, g.NH - 1, tile * PBT);
         const float dlog = valid ? d_logits[cc] : 0.0f;
         dl[t] = dlog;
         float zb[PW];
         const float* Wo = sw + g.off_w[g.NH];
 #pragma unroll
-        for (int u = 0; u < PW; ++u) {
-            float zz = 0.0f, b = 0.0f;
-            if (u < W) {
-                zz = sp_b(saved[((int64_t)(g.NH - 1) * W + u) * g.n_cells + cc], g.beta);
-                b = Wo[u] * dlog;
-            }
-            zi[t * PWS + u] = zz;
-            zb[u] = b;
-        }
+        for (int u = 0; u < PW; ++u) zb[u] = u < W ? Wo[u] * dlog : 0.0f;
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PW; ++u) zi[t * PWS + u] = u < W ? sp_b(zi[t * PWS + u], g.beta) : 0.0f;
         __syncthreads();
         for (int k = t; k < W; k += PBT) {
             float a = 0.0f;
@@ -504,21 +511,24 @@ __global__ void __launch_bounds__(PBT, 1) prop_backward_kernel(PropGeom g, const
         __syncthreads();
         for (int l = g.NH - 1; l >= 0; --l) {
             const int K = g.k_in[l];
-            // pre-activation adjoint and this layer's input, thread = cell
+            // this layer's and (above the first) the layer below's
+            // pre-activations, then, thread = cell, the pre-activation adjoint
+            // and this layer's input in place
+            stage(hb, l, tile * PBT);
+            if (l > 0) stage(zi, l - 1, tile * PBT);
+            cp_async_wait_all();
+            __syncthreads();
 #pragma unroll
             for (int u = 0; u < PW; ++u) {
                 float v = 0.0f;
-                if (u < W && valid) {
-                    const float h = saved[((int64_t)l * W + u) * g.n_cells + cc];
-                    v = zb[u] * sig(g.beta * h);
-                }
+                if (u < W && valid) v = zb[u] * sig(g.beta * hb[t * PWS + u]);
                 hb[t * PWS + u] = v;
             }
 #pragma unroll
             for (int k = 0; k < PW; ++k) {
                 float v = 0.0f;
                 if (k < K) {
-                    if (l > 0) v = sp_b(saved[((int64_t)(l - 1) * W + k) * g.n_cells + cc], g.beta);
+                    if (l > 0) v = sp_b(zi[t * PWS + k], g.beta);
                     else v = __half2float(feat[cc * g.F + k]);
                 }
                 zi[t * PWS + k] = v;
