@@ -241,8 +241,8 @@ def job_rate(units_per_step_per_rank: int, steps: int, world: int, max_ms: float
     return units_per_step_per_rank * steps * world / (max_ms * 1e-3)
 
 
-def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, r_max=2, prop_steps=300,
-                       m_table=(22, 24, 26, 28, 30), dilates=(1, 2), gshape=(64, 64, 128)):
+def train_step_compare(dev, warmup=1, steps=2, c_warmup=2, c_steps=3, r_max=2, prop_steps=800,
+                       m_table=(24, 26, 27, 28, 30), dilates=(1, 2), gshape=(64, 64, 128)):
     """Training step on the random-scene workload (1-8 ellipsoids and boxes
     behind a 0.5 occluder, 10 dB noise; 64x64 array, 128 bins, 64^3 heatmap):
     2^24 stratified samples (256^2 columns x 256 depths) against the same
@@ -460,6 +460,52 @@ def mlp_bench(n_pts=1 << 21, reps=5):
         out[f"backward_{name}_ms"] = e0.elapsed_time(e1) / reps
     G.geraf_poll_device_error()
     print(json.dumps(out), flush=True)
+
+
+def phasor_case(shape, reps=3, seed=0):
+    """Render and render adjoint of the 256^3-sample workload's array and band
+    (128x128 antennas at 2 mm, 256 bins) against a `shape` stratified grid of
+    its 10 cm cube, random gradients, weights and transmittances, and
+    a random signal adjoint: two untimed calls of each, then `reps` timed with
+    CUDA events; prints their mean times and the Chebyshev work."""
+    import torch
+    import geraf_inputs as gi
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda:0")
+    wl = gi.workload("c3")
+    g = gi.cube_grid((0.0, 0.0, 0.15), 0.10, shape)
+    xyz, _ = G.geraf_sample(G.make_grid(g.lo, g.pitch, g.n), gi.SAMPLE_STRATIFIED, seed=1, step=0)
+    n = xyz.shape[1]
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    grad = torch.randn(3, n, device=dev, generator=gen)
+    w = torch.rand(n, device=dev, generator=gen)
+    t_eff = 0.3 + 1.7 * torch.rand(n, device=dev, generator=gen)
+    ant = torch.as_tensor(gi.antenna_array(wl.array_n, wl.array_n, wl.array_pitch), device=dev)
+    c_ant = 0.1 * torch.rand(ant.shape[1], device=dev, generator=gen)
+    b = gi.band(77e9, 81e9, wl.n_f)
+    band = G.Band(b.f0, b.df, b.n_f)
+    g_s = torch.view_as_complex(torch.randn(ant.shape[1], wl.n_f, 2, device=dev, generator=gen)).contiguous()
+    for _ in range(2):
+        G.geraf_render(xyz, grad, w, t_eff, ant, c_ant, band)
+        G.geraf_render_backward(xyz, grad, w, t_eff, ant, c_ant, band, g_s)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tr = tb = 0.0
+    for _ in range(reps):
+        ev[0].record()
+        G.geraf_render(xyz, grad, w, t_eff, ant, c_ant, band)
+        ev[1].record()
+        G.geraf_render_backward(xyz, grad, w, t_eff, ant, c_ant, band, g_s)
+        ev[2].record()
+        torch.cuda.synchronize()
+        tr += ev[0].elapsed_time(ev[1])
+        tb += ev[1].elapsed_time(ev[2])
+    G.geraf_poll_device_error()
+    work = {k: G.geraf_chebyshev_work(xyz, ant, band, tp) for k, tp in (("render", False), ("render_backward", True))}
+    print(json.dumps({"mode": "phasor_case", "n_pts": n, "n_ant": ant.shape[1], "n_f": wl.n_f,
+                      "render_ms": tr / reps, "render_backward_ms": tb / reps, "work": work}), flush=True)
 
 
 def mlp_backward_macs(spec) -> int:
@@ -711,6 +757,9 @@ def main():
                     help="time only the paper's own training configuration and exit")
     ap.add_argument("--train-step", action="store_true",
                     help="run only the uniform vs proposal-cell training-step comparison and exit")
+    ap.add_argument("--phasor-case", default="", metavar="NX,NY,NZ",
+                    help="time only render and render adjoint of the 256^3-sample workload's array and band "
+                         "against an NX x NY x NZ stratified grid of its cube (the profiling case) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -723,6 +772,9 @@ def main():
         return
     if args.mlp_bench:
         mlp_bench(args.mlp_bench)
+        return
+    if args.phasor_case:
+        phasor_case(tuple(int(v) for v in args.phasor_case.split(",")), reps=args.steps)
         return
     if args.train_step:
         import torch

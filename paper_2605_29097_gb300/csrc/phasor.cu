@@ -1465,15 +1465,25 @@ __device__ __forceinline__ DS ds_add(DS a, DS b) {
 // 1e-20 whenever they pass 1e20), the second writes each J_k scaled into the
 // final scale (a value recorded two or more rescales before the end is below
 // 1e-20 of the largest and written as 0).
-__device__ void bessel_table_ds(double a, int K, float cphi, float sphi, float2* __restrict__ C, int n_f) {
-    if (!(a > 1e-20)) {                      // J_0 = 1, the others vanish
+// 2 / a in double-single: the FP32 quotient and one correction by the residual
+__device__ __forceinline__ DS ds_two_over(DS a) {
+    const float r0 = __fdiv_rn(2.0f, a.h);
+    const float p = __fmul_rn(a.h, r0);
+    const float pe = __fmaf_rn(a.h, r0, -p);
+    float e = __fsub_rn(2.0f, p);            // exact: p is within an ulp of 2
+    e = __fsub_rn(e, pe);
+    e = __fmaf_rn(-a.l, r0, e);
+    return ds_renorm(r0, __fmul_rn(e, __fmul_rn(0.5f, r0)));   // 2/a = r0 + e r0 / 2 to second order
+}
+
+__device__ void bessel_table_ds(DS a, int K, float cphi, float sphi, float2* __restrict__ C, int n_f) {
+    if (!(a.h > 1e-20f)) {                   // J_0 = 1, the others vanish
         for (int k = 0; k < K; ++k) C[(size_t)k * n_f] = k == 0 ? make_float2(cphi, sphi) : make_float2(0.0f, 0.0f);
         return;
     }
-    int start = K + 20 + (int)a;
+    int start = K + 20 + (int)a.h;
     start += start & 1;
-    const double inv = 2.0 / a;
-    const DS inv2{(float)inv, (float)(inv - (double)(float)inv)};
+    const DS inv2 = ds_two_over(a);
     int R = 0;
     DS nrm{0.0f, 0.0f};
     for (int pass = 0; pass < 2; ++pass) {
@@ -1517,6 +1527,55 @@ __device__ void bessel_table_ds(double a, int K, float cphi, float sphi, float2*
     }
 }
 
+// The expansion order for argument a: the smallest K with
+// sum_{k >= K} 2 |J_k(a)| <= eps over k < kcount (K >= 1), by the same two-pass
+// double-single recurrence: the first pass normalises, the second accumulates
+// the tail from the top and stops where it first exceeds eps.
+__device__ int bessel_order_ds(DS a, int kcount, float eps) {
+    if (!(a.h > 1e-20f)) return 1;
+    int start = kcount + 20 + (int)a.h;
+    start += start & 1;
+    const DS inv2 = ds_two_over(a);
+    int R = 0;
+    DS nrm{0.0f, 0.0f};
+    for (int pass = 0; pass < 2; ++pass) {
+        DS jp1{0.0f, 0.0f}, j{1e-30f, 0.0f};
+        DS acc{0.0f, 0.0f};
+        float tail = 0.0f;
+        int r = 0;
+        float inv_n = 0.0f;
+        if (pass == 1) inv_n = __fdiv_rn(1.0f, __fadd_rn(nrm.h, nrm.l));
+        for (int k = start; k >= 1; --k) {
+            const DS jm1 = ds_add(ds_mul(ds_mulf(inv2, (float)k), j), DS{-jp1.h, -jp1.l});
+            jp1 = j;
+            j = jm1;
+            if (fabsf(j.h) > 1e20f) {
+                j = ds_mulf(j, 1e-20f);
+                jp1 = ds_mulf(jp1, 1e-20f);
+                acc = ds_mulf(acc, 1e-20f);
+                tail *= 1e-20f;
+                ++r;
+            }
+            const int q = k - 1;
+            if (pass == 0) {
+                if ((q & 1) == 0 && q > 0) acc = ds_add(acc, ds_mulf(j, 2.0f));
+            } else if (q < kcount) {
+                tail += 2.0f * fabsf(__fadd_rn(j.h, j.l));
+                const int lag = R - r;
+                if (lag <= 1) {
+                    const float v = tail * inv_n * (lag == 1 ? 1e-20f : 1.0f);
+                    if (v > eps) return q + 1;
+                }
+            }
+        }
+        if (pass == 0) {
+            nrm = ds_add(acc, j);
+            R = r;
+        }
+    }
+    return 1;
+}
+
 __global__ void split_plan_kernel(const float* __restrict__ box, const float4* __restrict__ ant, int n_ant,
                                   int n_ab, int ant_per_block, double Kd, int n_f, double eps, double k0,
                                   const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
@@ -1524,7 +1583,7 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
     if (!gplan->run_cheb) return;
     __shared__ float rr[2][256];
     __shared__ int sK;
-    __shared__ float s_rc, s_inv;
+    __shared__ DS s_a1, s_ph1;
     const int sp = blockIdx.x, t = threadIdx.x;
     const int b = sp % n_ab;
     const float* bx = box + (sp / n_ab) * 6;     // in cycles
@@ -1562,32 +1621,40 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
         const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6 * k0, 1e-5 * k0);
         const float rc = (float)(0.5 * (rh + rl));
         const float inv = (float)(1.0 / dr);
-        const double a_max = 2.0 * 3.14159265358979323846 * (n_f - 1) * Kc / (double)inv;
-        double J[CH_KMAX + 8];
-        bessel_j(a_max, CH_KMAX + 8, J);
-        int K = CH_KMAX;
-        double tail = 0.0;
-        for (int k = CH_KMAX + 7; k >= 0; --k) {
-            tail += 2.0 * fabs(J[k]);
-            if (tail > eps) { K = k + 1; break; }
-        }
+        // per-bin argument step a1 = 2 pi Kc dr and phase step Kc r_c (cycles),
+        // double-single; every bin's quantities follow in FP32 arithmetic
+        const double dr_f = 1.0 / (double)inv;
+        const double a1 = 2.0 * 3.14159265358979323846 * Kc * dr_f;
+        const double ph1 = Kc * (double)rc;
+        const double a_max = a1 * (double)(n_f - 1);
+        const DS am{(float)a_max, (float)(a_max - (double)(float)a_max)};
+        int K = bessel_order_ds(am, CH_KMAX + 8, (float)eps);
         if (K < 2) K = 2;
         if (K > CH_KMAX) K = CH_KMAX;
         splan[sp] = SplitPlan{rc, inv, K, 0};
         atomicMax(kmax, K);
         sK = K;
-        s_rc = rc;
-        s_inv = inv;
+        s_a1 = DS{(float)a1, (float)(a1 - (double)(float)a1)};
+        s_ph1 = DS{(float)ph1, (float)(ph1 - (double)(float)ph1)};
     }
     __syncthreads();
     const int K = sK;
-    const double dr = 1.0 / (double)s_inv;
+    const DS a1 = s_a1, ph1 = s_ph1;
     float2* C = Cs + (size_t)sp * CH_KMAX * n_f;
     for (int n = t; n < n_f; n += blockDim.x) {
-        const double an = 2.0 * 3.14159265358979323846 * n * Kc * dr;
-        double sphi, cphi;
-        sincospi(-2.0 * (double)n * Kc * (double)s_rc, &sphi, &cphi);
-        bessel_table_ds(an, K, (float)cphi, (float)sphi, C + n, n_f);
+        const float fn = (float)n;
+        // exp(-j 2 pi n Kc r_c): the fractional cycle of n ph1 in double-single
+        const float p = __fmul_rn(fn, ph1.h);
+        const float pe = __fmaf_rn(fn, ph1.h, -p);
+        const float t0 = __fsub_rn(p, rintf(p));            // exact
+        const float u = __fmaf_rn(fn, ph1.l, pe);
+        const float fh = __fadd_rn(t0, u);
+        const float fl = __fsub_rn(u, __fsub_rn(fh, t0));
+        float sn, cs;
+        sincospif(-2.0f * fh, &sn, &cs);
+        const float d = -6.28318530717958648f * fl;          // exp(-j 2 pi fl) = 1 + j d to first order
+        const float cphi = __fmaf_rn(-sn, d, cs), sphi = __fmaf_rn(cs, d, sn);
+        bessel_table_ds(ds_mulf(a1, fn), K, cphi, sphi, C + n, n_f);
     }
 }
 
@@ -1886,10 +1953,10 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
                 const float D = fmaxf(Dm, 0.0f);
                 const float vv = pte[v] - head.w;
                 const float tt = __saturatef(vv);
-                const float dg = D * g;
-                const float u = tt * tt * g;
-                in[v][0] = fmaf(tt * tt, dg, in[v][0]);
-                if (vv >= 0.0f && vv <= 1.0f) in[v][1] = fmaf(tt, dg, in[v][1]);
+                const float tg = tt * g;
+                const float u = tt * tg;                   // T'^2 g
+                in[v][0] = fmaf(u, D, in[v][0]);
+                if (tt == vv) in[v][1] = fmaf(tg, D, in[v][1]);   // slope region 0 <= t_eff - c_ant <= 1
                 if (pe[v] > 0.0f && Dm > 0.0f) {
                     const float w2 = u * nd * inv_r2;
                     in[v][2] = fmaf(w2, R[v].dx, in[v][2]);
