@@ -462,6 +462,49 @@ def mlp_bench(n_pts=1 << 21, reps=5):
     print(json.dumps(out), flush=True)
 
 
+def blend_case(shape, reps=3, seed=0):
+    """Lensless alpha blending and its adjoint on n_ray columns x n_z depths
+    (SDF falling through zero along each column, reflectiveness in [0.2, 1]):
+    two untimed calls, then `reps` timed with CUDA events; prints the times and
+    the achieved bandwidth in the algorithmic bytes (blend: f and a read, alpha,
+    T, w and t_eff written, 24 B per point; adjoint: f, a, alpha, T, dL/dw and
+    dL/dT' read, dL/df and dL/da written, 32 B per point)."""
+    import torch
+    import paper_2605_29097_gb300 as G
+    from paper_2605_29097_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda:0")
+    n_ray, n_z = shape
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    z = torch.linspace(0.1, 0.2, n_z, device=dev)[:, None]
+    sdf = (0.15 - z + 0.01 * torch.randn(n_z, n_ray, device=dev, generator=gen)).reshape(-1).contiguous()
+    refl = (0.2 + 0.8 * torch.rand(n_z * n_ray, device=dev, generator=gen)).contiguous()
+    apr = 0.02 * torch.rand(n_ray, device=dev, generator=gen)
+    antf = 0.02 * torch.rand(1024, device=dev, generator=gen)
+    d_w = torch.randn(n_z * n_ray, device=dev, generator=gen)
+    d_t = torch.randn(n_z * n_ray, device=dev, generator=gen)
+    s_, atx = 300.0, 1.0
+    for _ in range(2):
+        out = G.geraf_blend(sdf, refl, n_ray, n_z, apr, antf, s_, atx)
+        G.geraf_blend_backward(sdf, refl, out[0], out[1], n_ray, n_z, s_, atx, d_w, d_t)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf = tb = 0.0
+    for _ in range(reps):
+        ev[0].record()
+        out = G.geraf_blend(sdf, refl, n_ray, n_z, apr, antf, s_, atx)
+        ev[1].record()
+        G.geraf_blend_backward(sdf, refl, out[0], out[1], n_ray, n_z, s_, atx, d_w, d_t)
+        ev[2].record()
+        torch.cuda.synchronize()
+        tf += ev[0].elapsed_time(ev[1])
+        tb += ev[1].elapsed_time(ev[2])
+    n = n_ray * n_z
+    tf, tb = tf / reps, tb / reps
+    print(json.dumps({"mode": "blend_case", "n_pts": n, "blend_ms": tf, "blend_gbs": 24 * n / (tf * 1e-3) / 1e9,
+                      "blend_backward_ms": tb, "blend_backward_gbs": 32 * n / (tb * 1e-3) / 1e9}), flush=True)
+
+
 def phasor_case(shape, reps=3, seed=0):
     """Render and render adjoint of the 256^3-sample workload's array and band
     (128x128 antennas at 2 mm, 256 bins) against a `shape` stratified grid of
@@ -757,6 +800,8 @@ def main():
                     help="time only the paper's own training configuration and exit")
     ap.add_argument("--train-step", action="store_true",
                     help="run only the uniform vs proposal-cell training-step comparison and exit")
+    ap.add_argument("--blend-case", default="", metavar="N_RAY,N_Z",
+                    help="time only blend and its adjoint on N_RAY columns x N_Z depths and exit")
     ap.add_argument("--phasor-case", default="", metavar="NX,NY,NZ",
                     help="time only render and render adjoint of the 256^3-sample workload's array and band "
                          "against an NX x NY x NZ stratified grid of its cube (the profiling case) and exit")
@@ -772,6 +817,9 @@ def main():
         return
     if args.mlp_bench:
         mlp_bench(args.mlp_bench)
+        return
+    if args.blend_case:
+        blend_case(tuple(int(v) for v in args.blend_case.split(",")), reps=args.steps)
         return
     if args.phasor_case:
         phasor_case(tuple(int(v) for v in args.phasor_case.split(",")), reps=args.steps)
