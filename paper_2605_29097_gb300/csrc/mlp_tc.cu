@@ -30,6 +30,7 @@ struct TcGeom {
     int64_t n;
     int n_tiles;
     int64_t off_w[8], off_b[8];
+    float wk[21];       // 2^k pi / half: the encoding's x-derivative factors, per octave
 };
 
 bool make_tc_geom(const geraf_field_desc* d, int64_t n, TcGeom* g) {
@@ -45,6 +46,7 @@ bool make_tc_geom(const geraf_field_desc* d, int64_t n, TcGeom* g) {
     g->beta = d->beta;
     g->cx = d->center[0]; g->cy = d->center[1]; g->cz = d->center[2];
     g->half = d->half;
+    for (int k = 0; k < g->L; ++k) g->wk[k] = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g->half);
     g->n = n;
     g->n_tiles = (int)((n + TTP - 1) / TTP);
     int64_t off = 0;
@@ -89,7 +91,7 @@ __device__ __forceinline__ void encode_axis(const TcGeom& g, float x, int d, Put
         const double r = t2 - 2.0 * rint(0.5 * t2);
         float sn, cs;
         sincospif((float)r, &sn, &cs);
-        const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
+        const float wk = g.wk[k];
         const int fs = 6 * k + d, fc = 6 * k + 3 + d;
 #pragma unroll
         for (int s = 0; s < 4; ++s) {

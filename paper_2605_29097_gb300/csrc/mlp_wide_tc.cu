@@ -133,25 +133,33 @@ __global__ void __launch_bounds__(128) wtc_encode_kernel(const float* __restrict
     const int64_t j = valid ? r / g.S : 0;
     const int s = valid ? (int)(r % g.S) : 0;
     const int64_t z_kc = g.K0p / WC, zt_kc = R / WC;
+    // the encoded coordinate of each axis, once per row (FP64: the divide is the
+    // expensive part on this GPU's FP64 pipe)
+    double xt[3];
+    const double pih = 3.14159265358979323846 / (double)g.half;   // 2^k pi / half = 2^k (pi / half) exactly
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float x = xyz[(int64_t)d * n + j];
+        const float c = d == 0 ? g.cx : (d == 1 ? g.cy : g.cz);
+        xt[d] = ((double)x - (double)c) / (double)g.half;
+    }
     for (int k0 = 0; k0 < g.K0p; k0 += 8) {
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int f = k0 + e;
             float val = 0.0f;
-            if (valid && f < g.K0) {
-                const int k = f / 6, rem = f % 6, d = rem % 3;
+            const int k = f / 6, rem = f % 6, d = rem % 3;
+            if (valid && f < g.K0 && (s == 0 || s - 1 == d)) {   // a tangent row is zero off its own axis
                 const bool is_cos = rem >= 3;
-                const float x = xyz[(int64_t)d * n + j];
-                const float c = d == 0 ? g.cx : (d == 1 ? g.cy : g.cz);
-                const double t2 = (((double)x - (double)c) / (double)g.half) * (double)(1 << k);
+                const double t2 = xt[d] * (double)(1 << k);
                 const double rr = t2 - 2.0 * rint(0.5 * t2);          // exact reduction mod 2
                 float sn, cs;
                 sincospif((float)rr, &sn, &cs);                       // sin, cos of 2^k pi xt
                 if (s == 0) {
                     val = is_cos ? cs : sn;
                 } else if (s - 1 == d) {
-                    const float wk = (float)((double)(1 << k) * 3.14159265358979323846 / (double)g.half);
+                    const float wk = (float)((double)(1 << k) * pih);
                     val = is_cos ? -wk * sn : wk * cs;
                 }
             }
@@ -433,13 +441,28 @@ __global__ void __launch_bounds__(256) wtc_hbar_kernel(const float* __restrict__
     }
 }
 
-// bias gradient of a layer: the 64-row block sums in FP64, in block order
-__global__ void wtc_bias_reduce(const float* __restrict__ bsum, int64_t n_blocks, int W, float* __restrict__ out) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= W) return;
+// bias gradient of a layer: the 64-row block sums in FP64. Block = 32 units x
+// BR_SLICES slices of the row blocks; each thread sums its slice in block
+// order, the slices are added in slice order, so the result does not depend
+// on the launch.
+constexpr int BR_SLICES = 8;
+__global__ void __launch_bounds__(32 * BR_SLICES) wtc_bias_reduce(const float* __restrict__ bsum, int64_t n_blocks,
+                                                                  int W, float* __restrict__ out) {
+    __shared__ double part[BR_SLICES][32];
+    const int lu = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int u = blockIdx.x * 32 + lu;
+    const int64_t per = (n_blocks + BR_SLICES - 1) / BR_SLICES;
+    const int64_t b0 = sl * per, b1 = min(n_blocks, b0 + per);
     double acc = 0.0;
-    for (int64_t b = 0; b < n_blocks; ++b) acc += bsum[(size_t)b * W + u];
-    out[u] = (float)acc;
+    if (u < W)
+        for (int64_t b = b0; b < b1; ++b) acc += bsum[(size_t)b * W + u];
+    part[sl][lu] = acc;
+    __syncthreads();
+    if (sl == 0 && u < W) {
+        double s = 0.0;
+        for (int q = 0; q < BR_SLICES; ++q) s += part[q][lu];
+        out[u] = (float)s;
+    }
 }
 
 // ------------------------------------------------------------------ head
@@ -725,7 +748,7 @@ geraf_status tnet_backward(const TNet& g, int64_t n, const unsigned char* base, 
         const float* Hl = reinterpret_cast<const float*>(base + L.H[l]);
         wtc_hbar_kernel<<<dim3((unsigned)(R / 64), g.W / 32), 256, 0, st>>>(
             zA, Hl, g.W, g.S, g.beta, g.inv_beta, rows, R, w.hb_hi, w.hb_lo, w.hbt_hi, w.hbt_lo, w.bsum);
-        wtc_bias_reduce<<<tdiv(g.W, 128), 128, 0, st>>>(w.bsum, R / 64, g.W, partial + g.off_b[l]);
+        wtc_bias_reduce<<<tdiv(g.W, 32), 32 * BR_SLICES, 0, st>>>(w.bsum, R / 64, g.W, partial + g.off_b[l]);
         WtcArgs a = gemm_args(WTC_DW, err);
         a.a0 = w.hbt_hi;
         a.a1 = w.hbt_lo;
