@@ -877,7 +877,7 @@ constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before i
 #define GERAF_CH_SPLIT_MIN_PTS 8192
 #endif
 #ifndef GERAF_CH_MAX_GROUPS
-#define GERAF_CH_MAX_GROUPS 128
+#define GERAF_CH_MAX_GROUPS 256
 #endif
 #ifndef GERAF_CH_GROUP_ROWS_MIB
 #define GERAF_CH_GROUP_ROWS_MIB 8192
