@@ -821,24 +821,33 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
 }
 
 // ==================================================== Chebyshev phasor sums
-// Per antenna i, the frequency dependence of a term is exp(-j 2 pi (f0 + n df)
-// 2 r / c). The f0 part is folded into the point's complex amplitude (one
-// double-single phase and one sincos per pair); with r = r_c + dr x, |x| <= 1
-// over a range interval, the Jacobi-Anger expansion
-//   exp(-j a_n x) = sum_k eps_k (-j)^k J_k(a_n) T_k(x),  a_n = 2 pi n (2 df / c) dr,
-// truncated where the Bessel tail falls below CH_TAIL, turns the bin sums into
-// K Chebyshev moments per antenna (K ~ a_max + 15, about 30 for a 4 GHz sweep
-// over a 15 cm range spread, independent of the number of bins):
-//   to bins:   s(i, n) = sum_k C_k(n) M_k(i),  M_k(i) = sum_j A'_ij T_k(x_ij)
-//   to points: sum_n s(i, n) exp(+j ...) = exp(+j 2 pi K0 r) sum_k T_k(x) S_k(i),
+// Per antenna i, the frequency dependence of a term is exp(-j 2 pi f_n 2 r / c)
+// with f_n = f_c + m df, f_c the band's centre and m = n - (n_f - 1) / 2. The
+// f_c part (K0 = 2 f_c / c, carrier cycles per metre; ranges R = K0 r in
+// cycles) is folded into the point's complex amplitude (one double-single
+// phase and one sincos per pair); with R = r_c(i) + dr x, |x| <= 1 over a
+// range interval centred on each antenna's own ranges, the Jacobi-Anger
+// expansion
+//   exp(-j a_m x) = sum_k eps_k (-j)^k J_k(a_m) T_k(x),  a_m = 2 pi m Kc dr,
+// Kc = df / f_c (bin phase step in cycles per cycle of range), truncated where
+// the Bessel tail falls below CH_TAIL, turns the bin sums into K Chebyshev
+// moments per antenna (K ~ |a_m|max + 15, about 25 for a 4 GHz sweep over a
+// 15 cm range spread, independent of the number of bins):
+//   to bins:   s(i, n) = exp(-j 2 pi m Kc r_c(i)) sum_k B_k(m) M_k(i),
+//              M_k(i) = sum_j A'_ij T_k(x_ij)
+//   to points: sum_n s(i, n) exp(+j ...) = exp(+j 2 pi R) sum_k T_k(x) S_k(i),
 //              evaluated per pair with T_k from the three-term recurrence.
-// Each part of a call (a split of point tiles, possibly times a block of
-// antennas, to bins; a group of points, to points) has its own interval, order
-// and table C_k(n) = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n), computed on the
-// device (Miller's backward recurrence in FP64) from the part's bounding box and
-// antennas, so the call stays asynchronous. If the whole call's order K would
-// exceed CH_KMAX the exact recurrence kernels run instead (decided on the
-// device).
+// The centred band halves the largest Bessel argument against a band-edge
+// carrier, and the per-antenna centre leaves only the part's own extent along
+// each antenna's line of sight in the half range dr, not the spread of ranges
+// across a block of antennas. Each part of a call (a split of point tiles,
+// possibly times a block of antennas, to bins; a group of points, to points)
+// has its own half range, order and table B_k(m) = eps_k (-j)^k J_k(a_m),
+// computed on the device from the part's bounding box and antennas, so the
+// call stays asynchronous; the phase exp(-j 2 pi m Kc r_c(i)) is applied per
+// (part, antenna, bin) where the moments meet the bins. If the whole call's
+// order K would exceed CH_KMAX the exact recurrence kernels run instead
+// (decided on the device).
 constexpr int CH_KMAX = 64;
 // resident CTAs per SM asked of the compiler for the K <= 32 instances
 #ifndef GERAF_CH_BINS_CTAS
@@ -890,8 +899,7 @@ constexpr size_t CH_TABLE_BYTES = (size_t)GERAF_CH_TABLE_MIB << 20;       // bou
 constexpr double CH_TAIL = 1e-7;
 
 struct ChebPlan {
-    float r_c;        // range centre (FP32; the coefficients use this value)
-    float inv_dr;     // 1 / half range (FP32; the coefficients use 1 / inv_dr)
+    float inv_dr;     // 1 / the whole set's half range (largest over the antennas), metres
     int K;            // Chebyshev order
     int use_direct;   // 1: the exact recurrence kernels must run instead
     int run_cheb;     // = !use_direct
@@ -954,12 +962,14 @@ __device__ void bessel_j(double a, int kcount, double* out) {
 }
 
 // one block: points bbox + antennas -> the whole call's range bound and order
-// K, and the choice between the Chebyshev form and the recurrence (the
-// coefficient tables come per part from split_plan_kernel)
+// K (the part rule over the whole set: the largest half range over the
+// antennas, each about its own centre), and the choice between the Chebyshev
+// form and the recurrence (the coefficient tables come per part from
+// split_plan_kernel)
 __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, const float* __restrict__ ant,
                                  int n_ant, double Kd, int n_f, double eps, double k0, ChebPlan* __restrict__ plan) {
     __shared__ float box[6];
-    __shared__ float rr[3][256];
+    __shared__ float rr[2][256];
     const int t = threadIdx.x;
     if (t < 6) {
         float v = t < 3 ? INFINITY : -INFINITY;
@@ -967,7 +977,7 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
         box[t] = v;
     }
     __syncthreads();
-    float lo = INFINITY, hi = 0.0f, ext = 0.0f;
+    float hw = 0.0f, ext = 0.0f;
     for (int i = t; i < n_ant; i += blockDim.x) {
         float dn = 0.0f, df = 0.0f;
         for (int d = 0; d < 3; ++d) {
@@ -978,27 +988,23 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
             df += f * f;
             ext = fmaxf(ext, f);
         }
-        lo = fminf(lo, sqrtf(dn));
-        hi = fmaxf(hi, sqrtf(df));
+        hw = fmaxf(hw, 0.5f * (sqrtf(df) - sqrtf(dn)));
     }
-    rr[0][t] = lo;
-    rr[1][t] = hi;
-    rr[2][t] = ext;
+    rr[0][t] = hw;
+    rr[1][t] = ext;
     __syncthreads();
     for (int k = blockDim.x / 2; k > 0; k >>= 1) {
         if (t < k) {
-            rr[0][t] = fminf(rr[0][t], rr[0][t + k]);
+            rr[0][t] = fmaxf(rr[0][t], rr[0][t + k]);
             rr[1][t] = fmaxf(rr[1][t], rr[1][t + k]);
-            rr[2][t] = fmaxf(rr[2][t], rr[2][t + k]);
         }
         __syncthreads();
     }
     if (t == 0) {
-        const double rl = rr[0][0], rh = rr[1][0];
-        const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6, 1e-5);
-        const float rc = (float)(0.5 * (rh + rl));
+        const double dr = fmax((double)rr[0][0] * 1.001 + 1e-6, 1e-5);
         const float inv = (float)(1.0 / dr);
-        const double a_max = 2.0 * 3.14159265358979323846 * (n_f - 1) * Kd / (double)inv;
+        // largest |a_m|: the bin offset (n_f - 1) / 2 from the band's centre
+        const double a_max = 3.14159265358979323846 * (n_f - 1) * Kd / (double)inv;
         double J[CH_KMAX + 8];
         bessel_j(a_max, CH_KMAX + 8, J);
         int K = CH_KMAX + 1;
@@ -1009,10 +1015,9 @@ __global__ void cheb_plan_kernel(const float* __restrict__ part, int n_part, con
         }
         if (K < 2) K = 2;
         // the split-coordinate range in cycles is exact only for axis
-        // differences below 1024 cycles (about 2 m at 77 GHz)
-        const int direct = K > CH_KMAX || !(rr[2][0] * (float)k0 < kCycAxisMax);
+        // differences below 1024 cycles (about 2 m at 79 GHz)
+        const int direct = K > CH_KMAX || !(rr[1][0] * (float)k0 < kCycAxisMax);
         if (K > CH_KMAX) K = CH_KMAX;
-        plan->r_c = rc;
         plan->inv_dr = inv;
         plan->K = K;
         plan->use_direct = direct;
@@ -1188,13 +1193,11 @@ __global__ void gather_xyz(const float* __restrict__ xyz, int64_t n, const int* 
 
 // Expansion of one part of a Chebyshev call (a split of point tiles, possibly
 // times a block of antennas, for the to-bins sums; a group of points for the
-// to-points sums): its range interval r_c +/- 1/inv_dr and order K. Consecutive
-// points of the depth-major sampler form thin depth slabs, so a part's interval,
-// and with it K, is narrower than the whole call's.
+// to-points sums): its half range 1/inv_dr (each antenna's interval is centred
+// on that antenna's own range centre, rcs) and order K.
 struct SplitPlan {
-    float r_c, inv_dr;
+    float inv_dr;
     int K;
-    int pad;
 };
 
 struct ChebBinsArgs {
@@ -1206,6 +1209,8 @@ struct ChebBinsArgs {
     const ChebPlan* plan;      // the whole call's plan (run_cheb)
     const SplitPlan* splan;    // [splits][plan_blocks]
     int plan_blocks;           // antenna blocks with their own plan: 1 or gridDim.x
+    const float* rcs;          // [splits][n_rec]: each antenna record's range centre (cycles)
+    int n_rec;
     const int* kmax;           // largest part order: picks the kernel instance
     double k0;                 // K0 = 2 f0 / c, cycles per metre (positions in cycles)
     float amp_scale;           // factor of every moment: gamma's 1 / (16 pi^2) per square cycle (render), 1
@@ -1224,7 +1229,8 @@ struct ChebBinsArgs {
 // unrolled tile body per even order); the KC = 8 instance (orders beyond 32
 // guarded by the part's K) otherwise; all are launched and those that do not
 // apply return at once. Each part = (split of points, block of CH_THREADS
-// antennas) expands the bin phase over its own range interval (SplitPlan).
+// antennas) expands the bin phase over its own half range (SplitPlan), each
+// antenna about its own range centre (rcs).
 // One tile of CH_TP point records against this thread's antenna: the pair's
 // range in cycles, amplitude times carrier phasor, and the moments
 // M_k += A T_k(x) for k < KE (KE even, fixed at compile time). kGuard (the
@@ -1313,7 +1319,8 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
     const SplitPlan sp = args.splan[split * args.plan_blocks + (args.plan_blocks > 1 ? blockIdx.x : 0)];
     const int K = sp.K;
     const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
-    const float r_c = sp.r_c, inv_dr = sp.inv_dr;
+    const float inv_dr = sp.inv_dr;
+    const float r_c = args.rcs[(size_t)split * args.n_rec + ia];   // this antenna's range centre
     const float4 A4 = args.ant[ia];                          // padded: always readable
     float4 Ah, Al;
     split3c(A4.x, A4.y, A4.z, args.k0, Ah, Al);
@@ -1422,11 +1429,13 @@ __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, in
 
 // One block per part = (split or group of points sp, block of antennas b),
 // parts in order sp * n_ab + b (n_ab blocks of ant_per_block consecutive
-// antenna records in the spatial order, or one block of all antennas): the
-// part's range interval between the points' box and the block's antennas,
-// its order K (the whole call's rule: Bessel tail <= eps), and its FP32
-// coefficient table Cs[part][k][n] = exp(-j 2 pi n Kd r_c) eps_k (-j)^k J_k(a_n)
-// (Bessel values in FP64). kmax collects the largest part order.
+// antenna records in the spatial order, or one block of all antennas): each
+// record's range centre r_c(i) (midpoint of its nearest and farthest range to
+// the points' box, written to rcs[sp][i] for every record, padding ones
+// included), the part's half range (the largest over its antennas of half
+// that span), its order K (the whole call's rule: Bessel tail <= eps) and its
+// FP32 coefficient table Cs[part][k][n] = eps_k (-j)^k J_k(a_m), m = n -
+// (n_f - 1) / 2. kmax collects the largest part order.
 // Double-single FP32 arithmetic (value = h + l, |l| <= ulp(h) / 2) for the
 // coefficient tables: error-free products by FMA and Knuth's two-sum, so the
 // Bessel recurrence keeps ~44 bits without FP64 (slow on this part).
@@ -1458,8 +1467,9 @@ __device__ __forceinline__ DS ds_add(DS a, DS b) {
     return ds_renorm(s, e);
 }
 
-// C[k n_f] for k < K, one bin: (2 - [k = 0]) J_k(a) (-j)^k (cphi + j sphi),
-// J_k by Miller's backward recurrence in double-single, normalised by
+// C[k n_f] for k < K, one bin: (2 - [k = 0]) J_k(s a) (-j)^k for a >= 0 and
+// the sign s = -1 when neg (J_k(-a) = (-1)^k J_k(a), so the factor becomes
+// j^k), J_k by Miller's backward recurrence in double-single, normalised by
 // J_0 + 2 sum J_2m = 1. Two passes over the same recurrence: the first finds
 // the normalisation and how often the running values were rescaled (by
 // 1e-20 whenever they pass 1e20), the second writes each J_k scaled into the
@@ -1476,9 +1486,9 @@ __device__ __forceinline__ DS ds_two_over(DS a) {
     return ds_renorm(r0, __fmul_rn(e, __fmul_rn(0.5f, r0)));   // 2/a = r0 + e r0 / 2 to second order
 }
 
-__device__ void bessel_table_ds(DS a, int K, float cphi, float sphi, float2* __restrict__ C, int n_f) {
+__device__ void bessel_table_ds(DS a, int K, bool neg, float2* __restrict__ C, int n_f) {
     if (!(a.h > 1e-20f)) {                   // J_0 = 1, the others vanish
-        for (int k = 0; k < K; ++k) C[(size_t)k * n_f] = k == 0 ? make_float2(cphi, sphi) : make_float2(0.0f, 0.0f);
+        for (int k = 0; k < K; ++k) C[(size_t)k * n_f] = make_float2(k == 0 ? 1.0f : 0.0f, 0.0f);
         return;
     }
     int start = K + 20 + (int)a.h;
@@ -1510,14 +1520,16 @@ __device__ void bessel_table_ds(DS a, int K, float cphi, float sphi, float2* __r
                 float v = lag >= 2 ? 0.0f : __fadd_rn(j.h, j.l) * inv_n;
                 if (lag == 1) v *= 1e-20f;
                 const float m = q == 0 ? v : 2.0f * v;
-                float ar, ai;                    // m (-j)^q
+                // m (-j)^q, or m j^q for a negative argument
+                const float si = neg ? -m : m;
+                float2 c;
                 switch (q & 3) {
-                    case 0: ar = m; ai = 0.0f; break;
-                    case 1: ar = 0.0f; ai = -m; break;
-                    case 2: ar = -m; ai = 0.0f; break;
-                    default: ar = 0.0f; ai = m; break;
+                    case 0: c = make_float2(m, 0.0f); break;
+                    case 1: c = make_float2(0.0f, -si); break;
+                    case 2: c = make_float2(-m, 0.0f); break;
+                    default: c = make_float2(0.0f, si); break;
                 }
-                C[(size_t)q * n_f] = make_float2(cphi * ar - sphi * ai, cphi * ai + sphi * ar);
+                C[(size_t)q * n_f] = c;
             }
         }
         if (pass == 0) {
@@ -1576,21 +1588,43 @@ __device__ int bessel_order_ds(DS a, int kcount, float eps) {
     return 1;
 }
 
+// exp(-j 2 pi m Kc r_c) for the bin offset m (exact in FP32) and the range
+// centre r_c in cycles, Kc = kch + kcl in double-single: the fractional cycle
+// of m Kc r_c in double-single (error-free products by FMA, so a phase of tens
+// of cycles keeps ~1e-12 cycle), then sincospi of its leading part with a
+// first-order correction for the rest.
+__device__ __forceinline__ float2 bin_phase(float m, float kch, float kcl, float rc) {
+    const float p1 = __fmul_rn(kch, rc);
+    const DS ph = ds_renorm(p1, __fmaf_rn(kcl, rc, __fmaf_rn(kch, rc, -p1)));
+    const float p = __fmul_rn(m, ph.h);
+    const float pe = __fmaf_rn(m, ph.h, -p);
+    const float t0 = __fsub_rn(p, rintf(p));            // exact
+    const float u = __fmaf_rn(m, ph.l, pe);
+    const float fh = __fadd_rn(t0, u);
+    const float fl = __fsub_rn(u, __fsub_rn(fh, t0));
+    float sn, cs;
+    sincospif(-2.0f * fh, &sn, &cs);
+    const float d = -6.28318530717958648f * fl;          // exp(-j 2 pi fl) = 1 + j d to first order
+    return make_float2(__fmaf_rn(-sn, d, cs), __fmaf_rn(cs, d, sn));
+}
+
 __global__ void split_plan_kernel(const float* __restrict__ box, const float4* __restrict__ ant, int n_ant,
-                                  int n_ab, int ant_per_block, double Kd, int n_f, double eps, double k0,
-                                  const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
-                                  float2* __restrict__ Cs, int* __restrict__ kmax) {
+                                  int n_rec, int n_ab, int ant_per_block, double Kd, int n_f, double eps,
+                                  double k0, const ChebPlan* __restrict__ gplan, SplitPlan* __restrict__ splan,
+                                  float* __restrict__ rcs, float2* __restrict__ Cs, int* __restrict__ kmax) {
     if (!gplan->run_cheb) return;
-    __shared__ float rr[2][256];
+    __shared__ float rr[256];
     __shared__ int sK;
-    __shared__ DS s_a1, s_ph1;
+    __shared__ DS s_a1;
     const int sp = blockIdx.x, t = threadIdx.x;
     const int b = sp % n_ab;
     const float* bx = box + (sp / n_ab) * 6;     // in cycles
     const int i0 = b * ant_per_block, i1 = min(n_ant, i0 + ant_per_block);
+    const int iw = n_ab > 1 ? min(n_rec, i0 + ant_per_block) : n_rec;   // records whose centre this part writes
+    float* rc_out = rcs + (size_t)(sp / n_ab) * n_rec;
     const float k0f = (float)k0;
-    float lo = INFINITY, hi = 0.0f;
-    for (int i = i0 + t; i < i1; i += blockDim.x) {
+    float hw = 0.0f;
+    for (int i = i0 + t; i < iw; i += blockDim.x) {
         float dn = 0.0f, df = 0.0f;
         const float4 A = ant[i];                  // metres
         for (int d = 0; d < 3; ++d) {
@@ -1600,70 +1634,55 @@ __global__ void split_plan_kernel(const float* __restrict__ box, const float4* _
             dn += e * e;
             df += f * f;
         }
-        lo = fminf(lo, sqrtf(dn));
-        hi = fmaxf(hi, sqrtf(df));
+        const float lo = sqrtf(dn), hi = sqrtf(df);
+        rc_out[i] = 0.5f * (lo + hi);
+        if (i < i1) hw = fmaxf(hw, 0.5f * (hi - lo));
     }
-    rr[0][t] = lo;
-    rr[1][t] = hi;
+    rr[t] = hw;
     __syncthreads();
     for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if (t < k) {
-            rr[0][t] = fminf(rr[0][t], rr[0][t + k]);
-            rr[1][t] = fmaxf(rr[1][t], rr[1][t + k]);
-        }
+        if (t < k) rr[t] = fmaxf(rr[t], rr[t + k]);
         __syncthreads();
     }
-    // the part's interval and table in cycles: Kc = bin spacing of the
-    // phase in cycles per cycle of range; margins 1e-6 m and 1e-5 m in cycles
+    // the part's half range and table in cycles: Kc = bin phase step in
+    // cycles per cycle of range; margins 1e-6 m and 1e-5 m in cycles
     const double Kc = Kd / k0;
     if (t == 0) {
-        const double rl = rr[0][0], rh = rr[1][0];
-        const double dr = fmax(0.5 * (rh - rl) * 1.001 + 1e-6 * k0, 1e-5 * k0);
-        const float rc = (float)(0.5 * (rh + rl));
+        const double dr = fmax((double)rr[0] * 1.001 + 1e-6 * k0, 1e-5 * k0);
         const float inv = (float)(1.0 / dr);
-        // per-bin argument step a1 = 2 pi Kc dr and phase step Kc r_c (cycles),
-        // double-single; every bin's quantities follow in FP32 arithmetic
+        // argument step a1 = 2 pi Kc dr per bin of offset (double-single);
+        // every bin's argument follows in FP32 arithmetic
         const double dr_f = 1.0 / (double)inv;
         const double a1 = 2.0 * 3.14159265358979323846 * Kc * dr_f;
-        const double ph1 = Kc * (double)rc;
-        const double a_max = a1 * (double)(n_f - 1);
+        const double a_max = a1 * 0.5 * (double)(n_f - 1);
         const DS am{(float)a_max, (float)(a_max - (double)(float)a_max)};
         int K = bessel_order_ds(am, CH_KMAX + 8, (float)eps);
         if (K < 2) K = 2;
         if (K > CH_KMAX) K = CH_KMAX;
-        splan[sp] = SplitPlan{rc, inv, K, 0};
+        splan[sp] = SplitPlan{inv, K};
         atomicMax(kmax, K);
         sK = K;
         s_a1 = DS{(float)a1, (float)(a1 - (double)(float)a1)};
-        s_ph1 = DS{(float)ph1, (float)(ph1 - (double)(float)ph1)};
     }
     __syncthreads();
     const int K = sK;
-    const DS a1 = s_a1, ph1 = s_ph1;
+    const DS a1 = s_a1;
+    const float nc = 0.5f * (float)(n_f - 1);
     float2* C = Cs + (size_t)sp * CH_KMAX * n_f;
     for (int n = t; n < n_f; n += blockDim.x) {
-        const float fn = (float)n;
-        // exp(-j 2 pi n Kc r_c): the fractional cycle of n ph1 in double-single
-        const float p = __fmul_rn(fn, ph1.h);
-        const float pe = __fmaf_rn(fn, ph1.h, -p);
-        const float t0 = __fsub_rn(p, rintf(p));            // exact
-        const float u = __fmaf_rn(fn, ph1.l, pe);
-        const float fh = __fadd_rn(t0, u);
-        const float fl = __fsub_rn(u, __fsub_rn(fh, t0));
-        float sn, cs;
-        sincospif(-2.0f * fh, &sn, &cs);
-        const float d = -6.28318530717958648f * fl;          // exp(-j 2 pi fl) = 1 + j d to first order
-        const float cphi = __fmaf_rn(-sn, d, cs), sphi = __fmaf_rn(cs, d, sn);
-        bessel_table_ds(ds_mulf(a1, fn), K, cphi, sphi, C + n, n_f);
+        const float m = (float)n - nc;                   // exact: a multiple of 1/2
+        bessel_table_ds(ds_mulf(a1, fabsf(m)), K, m < 0.0f, C + n, n_f);
     }
 }
 
-// sum over the splits of a group of RS splits of sum_k Cs[sp, b(i)][k][n] M_k(sp, i),
+// sum over the splits of a group of RS splits of
+//   exp(-j 2 pi m Kc r_c(sp, i)) sum_k Cs[sp, b(i)][k][n] M_k(sp, i),
 // i an antenna record, b(i) its block of CH_THREADS records, written to the
 // antenna the record holds:
 // block = (RA antennas, split group); thread = bin, the RA antennas in
 // registers so each table value is loaded once; the per-split sums (FP32, at
-// most 64 terms) are added with Kahan compensation across the group's splits.
+// most 64 terms) are turned by the record's bin phase and added with Kahan
+// compensation across the group's splits.
 // The groups' sums are added in FP64, in group order, by sum_split_groups.
 constexpr int RA = 4;
 constexpr int RS = 32;
@@ -1671,12 +1690,16 @@ static_assert(CH_THREADS % RA == 0, "a reconstruction block stays in one antenna
 __global__ void cheb_reconstruct_split_kernel(const float2* __restrict__ partial, int splits, int n_ant, int n_f,
                                               int n_ab, const ChebPlan* __restrict__ gplan,
                                               const SplitPlan* __restrict__ splan, const float2* __restrict__ Cs,
+                                              const float* __restrict__ rcs, int n_rec, double kc,
                                               const int* __restrict__ perm, float2* __restrict__ group_out) {
     if (!gplan->run_cheb) return;
     const int i0 = blockIdx.x * RA;
     const int b = n_ab > 1 ? i0 / CH_THREADS : 0;   // antenna block of all RA antennas (RA divides CH_THREADS)
     const int s0 = blockIdx.y * RS, s1 = min(splits, s0 + RS);
+    const float kch = (float)kc, kcl = (float)(kc - (double)kch);
+    const float nc = 0.5f * (float)(n_f - 1);
     for (int n = threadIdx.x; n < n_f; n += blockDim.x) {
+        const float m = (float)n - nc;
         float hr[RA], hi[RA], cr_[RA], ci_[RA];
 #pragma unroll
         for (int q = 0; q < RA; ++q) hr[q] = hi[q] = cr_[q] = ci_[q] = 0.0f;
@@ -1692,17 +1715,19 @@ __global__ void cheb_reconstruct_split_kernel(const float2* __restrict__ partial
 #pragma unroll
                 for (int q = 0; q < RA; ++q) {
                     const int i = min(i0 + q, n_ant - 1);
-                    const float2 m = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
-                    sr[q] = fmaf(c.x, m.x, fmaf(-c.y, m.y, sr[q]));
-                    si[q] = fmaf(c.x, m.y, fmaf(c.y, m.x, si[q]));
+                    const float2 mo = partial[((size_t)s * n_ant + i) * CH_KMAX + k];
+                    sr[q] = fmaf(c.x, mo.x, fmaf(-c.y, mo.y, sr[q]));
+                    si[q] = fmaf(c.x, mo.y, fmaf(c.y, mo.x, si[q]));
                 }
             }
 #pragma unroll
             for (int q = 0; q < RA; ++q) {
-                float y = sr[q] - cr_[q], tt = hr[q] + y;
+                const float2 ph = bin_phase(m, kch, kcl, rcs[(size_t)s * n_rec + min(i0 + q, n_ant - 1)]);
+                const float pr = ph.x * sr[q] - ph.y * si[q], pi = ph.x * si[q] + ph.y * sr[q];
+                float y = pr - cr_[q], tt = hr[q] + y;
                 cr_[q] = (tt - hr[q]) - y;
                 hr[q] = tt;
-                y = si[q] - ci_[q];
+                y = pi - ci_[q];
                 tt = hi[q] + y;
                 ci_[q] = (tt - hi[q]) - y;
                 hi[q] = tt;
@@ -1774,11 +1799,13 @@ __global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int6
 // holds the antenna perm[r] (the spatial order), planned with the part
 // (g, b = r / CH_THREADS) when the groups are planned per antenna block (n_ab
 // blocks), else with the group's plan over all antennas (n_ab = 1):
-// row(g, r) = two heads (the antenna's split position in cycles; c_ant in the first),
-// then for k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) C_part,k(n)
-// (either factor conjugated on request), zero beyond the part's order and for
-// padding antennas. Block = GR_T records of one group (inside one antenna
-// block); thread = one order k and every fourth record of the tile; bins
+// row(g, r) = two heads (the antenna's split position in cycles; c_ant in the
+// first, the record's range centre r_c(g, r) in the second), then for
+// k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) P(r, n) C_part,k(n),
+// P = exp(-j 2 pi m Kc r_c) the record's bin phase (P and C both conjugated,
+// and sig, on request), zero beyond the part's order and for padding antennas.
+// Block = GR_T records of one group (inside one antenna block); thread = one
+// order k and every fourth record of the tile; bins (turned by their phase)
 // staged in shared memory in chunks of GR_NC; FP32 sums.
 constexpr int GR_T = 16;
 constexpr int GR_NC = 64;
@@ -1786,35 +1813,42 @@ static_assert(CH_THREADS % GR_T == 0, "a rows block stays in one antenna block")
 __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
     const float* __restrict__ ant, const float* __restrict__ c_ant, const float2* __restrict__ sig,
     const int* __restrict__ perm, int n_ant, int n_ant_pad, int n_f, int n_ab, const ChebPlan* __restrict__ plan,
-    const SplitPlan* __restrict__ gplan, const float2* __restrict__ Cs, int conj_c, int conj_sig, double k0,
-    float4* __restrict__ rows) {
+    const SplitPlan* __restrict__ gplan, const float2* __restrict__ Cs, const float* __restrict__ rcs, double kc,
+    int conj_c, int conj_sig, double k0, float4* __restrict__ rows) {
     if (!plan->run_cheb) return;
     __shared__ float2 sC[CH_KMAX][GR_NC + 1];
     __shared__ float2 sS[GR_T][GR_NC + 1];
+    __shared__ float sRc[GR_T];
     const int g = blockIdx.y, i0 = blockIdx.x * GR_T, t = threadIdx.x;
     const int part = g * n_ab + (n_ab > 1 ? i0 / CH_THREADS : 0);
     const int K = gplan[part].K;
     float4* grow = rows + (size_t)g * n_ant_pad * CH_ROW;
-    if (t < GR_T && i0 + t < n_ant_pad) {
-        const int i = i0 + t;
-        const int q = i < n_ant ? perm[i] : 0;
-        float4 hi, lo;
-        split3c(ant[q], ant[n_ant + q], ant[2 * n_ant + q], k0, hi, lo);
-        hi.w = c_ant ? c_ant[q] : 0.0f;
-        lo.w = 0.0f;
-        grow[(size_t)i * CH_ROW] = hi;
-        grow[(size_t)i * CH_ROW + 1] = lo;
+    const float* grc = rcs + (size_t)g * n_ant_pad;
+    if (t < GR_T) {
+        const int i = min(i0 + t, n_ant_pad - 1);
+        sRc[t] = grc[i];
+        if (i0 + t < n_ant_pad) {
+            const int q = i < n_ant ? perm[i] : 0;
+            float4 hi, lo;
+            split3c(ant[q], ant[n_ant + q], ant[2 * n_ant + q], k0, hi, lo);
+            hi.w = c_ant ? c_ant[q] : 0.0f;
+            lo.w = grc[i];
+            grow[(size_t)i * CH_ROW] = hi;
+            grow[(size_t)i * CH_ROW + 1] = lo;
+        }
     }
+    const float kch = (float)kc, kcl = (float)(kc - (double)kch);
+    const float nc = 0.5f * (float)(n_f - 1);
     const int k = t >> 2, r = t & 3;
     const float2* C = Cs + (size_t)part * CH_KMAX * n_f;
     float ar[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ai[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int n0 = 0; n0 < n_f; n0 += GR_NC) {
-        const int nc = min(GR_NC, n_f - n0);
+        const int nc_ = min(GR_NC, n_f - n0);
         __syncthreads();
         for (int e = t; e < CH_KMAX * GR_NC; e += blockDim.x) {
             const int kk = e / GR_NC, nn = e % GR_NC;
             float2 c = make_float2(0.0f, 0.0f);
-            if (kk < K && nn < nc) {
+            if (kk < K && nn < nc_) {
                 c = C[(size_t)kk * n_f + n0 + nn];
                 if (conj_c) c.y = -c.y;
             }
@@ -1823,15 +1857,18 @@ __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
         for (int e = t; e < GR_T * GR_NC; e += blockDim.x) {
             const int a = e / GR_NC, nn = e % GR_NC, i = i0 + a;
             float2 v = make_float2(0.0f, 0.0f);
-            if (i < n_ant && nn < nc) {
+            if (i < n_ant && nn < nc_) {
                 v = sig[(size_t)perm[i] * n_f + n0 + nn];
                 if (conj_sig) v.y = -v.y;
+                float2 ph = bin_phase((float)(n0 + nn) - nc, kch, kcl, sRc[a]);
+                if (conj_c) ph.y = -ph.y;
+                v = make_float2(v.x * ph.x - v.y * ph.y, v.x * ph.y + v.y * ph.x);
             }
             sS[a][nn] = v;
         }
         __syncthreads();
         if (k < K)
-            for (int nn = 0; nn < nc; ++nn) {
+            for (int nn = 0; nn < nc_; ++nn) {
                 const float2 c = sC[k][nn];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -1881,7 +1918,7 @@ static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread
 // render-adjoint accumulation into in. kGuard (the 64-order instance): orders
 // past 32 run in blocks of 8 up to the group's own order K.
 template <int MODE, int KE, bool kGuard>
-__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, float r_c, float inv_dr,
+__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, float inv_dr,
                                             const float4 (&ph)[TPK_V], const float4 (&pl)[TPK_V],
                                             const float (&pnx)[TPK_V], const float (&pny)[TPK_V],
                                             const float (&pnz)[TPK_V], const float (&pte)[TPK_V],
@@ -1890,6 +1927,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
     constexpr int ROW = CH_ROW;
     for (int a = 0; a < AT; ++a) {
         const float4 head = tile[a * ROW], head_lo = tile[a * ROW + 1];
+        const float r_c = head_lo.w;                     // the antenna's range centre for this group
         const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 2);
         Range R[TPK_V];
         float xs[TPK_V];
@@ -1969,7 +2007,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
 }
 
 #define GERAF_POINTS_CASE(E) \
-    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, r_c, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in); break;
+    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in); break;
 
 // Each group of ctas_per_group point CTAs has its own interval and order
 // (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
@@ -2060,20 +2098,20 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             args.gplan[grp * args.n_ab + (args.n_ab > 1 ? ((tile0 + it) * AT) / CH_THREADS : 0)];
         const int K = gp.K;
         const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
-        const float r_c = gp.r_c, inv_dr = gp.inv_dr;
+        const float inv_dr = gp.inv_dr;
         float in[TPK_V][NACC];
 #pragma unroll
         for (int v = 0; v < TPK_V; ++v)
 #pragma unroll
             for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
         if constexpr (KC == 8) {
-            points_tile<MODE, KM, true>(tile, AT, K, r_c, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in);
+            points_tile<MODE, KM, true>(tile, AT, K, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in);
         } else {
             switch (ke) {
                 GERAF_POINTS_CASE(8) GERAF_POINTS_CASE(10) GERAF_POINTS_CASE(12) GERAF_POINTS_CASE(14)
                 GERAF_POINTS_CASE(16) GERAF_POINTS_CASE(18) GERAF_POINTS_CASE(20) GERAF_POINTS_CASE(22)
                 GERAF_POINTS_CASE(24) GERAF_POINTS_CASE(26) GERAF_POINTS_CASE(28) GERAF_POINTS_CASE(30)
-                default: points_tile<MODE, KM, false>(tile, AT, K, r_c, inv_dr, ph, pl, pnx, pny, pnz, pte, pe,
+                default: points_tile<MODE, KM, false>(tile, AT, K, inv_dr, ph, pl, pnx, pny, pnz, pte, pe,
                                                       in);
             }
         }
@@ -2121,9 +2159,12 @@ bool use_cheb(const geraf_band* band) {
     return band->n_f >= 64;
 }
 
-// K0 = 2 f0 / c: carrier cycles per metre of range (the Chebyshev kernels'
-// coordinate unit)
-double k0_of(const geraf_band* band) { return 2.0 * band->f0 / kC; }
+// K0 = 2 f_c / c with f_c = f0 + (n_f - 1) df / 2 the band's centre: carrier
+// cycles per metre of range (the Chebyshev kernels' coordinate unit)
+double k0_of(const geraf_band* band) { return 2.0 * (band->f0 + 0.5 * (band->n_f - 1) * band->df) / kC; }
+
+// Kc = df / f_c: the bin phase step in cycles per cycle of range
+double kc_of(const geraf_band* band) { return band->df / (band->f0 + 0.5 * (band->n_f - 1) * band->df); }
 
 // 1 / (16 pi^2) per square cycle of range, the factor of gamma = 1 / (4 pi r)^2
 // for ranges in cycles
@@ -2166,6 +2207,7 @@ struct PointGroups {
     int groups, ctas_per_group, n_ab, parts;
     float* box;
     SplitPlan* plan;
+    float* rcs;          // [groups][n_ant_pad]: each antenna record's range centre per group
     float2* C;
     int* kmax;
     float4* rows;
@@ -2188,6 +2230,7 @@ PointGroups take_point_groups(WsCarver& c, int pt_ctas, int n_ant, int n_ant_pad
     PointGroups g = plan_point_groups(pt_ctas, n_ant, n_ant_pad, n_f);
     g.box = c.take<float>((size_t)g.groups * 6);
     g.plan = c.take<SplitPlan>(g.parts);
+    g.rcs = c.take<float>((size_t)g.groups * n_ant_pad);
     g.C = c.take<float2>((size_t)g.parts * CH_KMAX * n_f);
     g.kmax = c.take<int>(1);
     g.rows = c.take<float4>((size_t)g.groups * g.group_rows);
@@ -2256,11 +2299,12 @@ geraf_status launch_point_groups(const PointGroups& g, const ChebWs& cw, const A
     if (e != cudaSuccess) return cuda_status(e, "point groups");
     group_bbox_kernel<<<g.groups, 256, 0, st>>>(xyz, n, (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V,
                                                 (float)k0_of(band), g.box);
-    split_plan_kernel<<<g.parts, 256, 0, st>>>(g.box, ao.rec, n_ant, g.n_ab, g.n_ab > 1 ? CH_THREADS : n_ant,
-                                               2.0 * band->df / kC, band->n_f, CH_TAIL, k0_of(band), cw.plan, g.plan, g.C, g.kmax);
+    split_plan_kernel<<<g.parts, 256, 0, st>>>(g.box, ao.rec, n_ant, n_ant_pad, g.n_ab,
+                                               g.n_ab > 1 ? CH_THREADS : n_ant, 2.0 * band->df / kC, band->n_f,
+                                               CH_TAIL, k0_of(band), cw.plan, g.plan, g.rcs, g.C, g.kmax);
     cheb_group_rows_kernel<<<dim3((n_ant_pad + GR_T - 1) / GR_T, g.groups), 256, 0, st>>>(
-        ant_xyz, c_ant, sig, ao.perm, n_ant, n_ant_pad, band->n_f, g.n_ab, cw.plan, g.plan, g.C, conj_c, conj_sig,
-        k0_of(band), g.rows);
+        ant_xyz, c_ant, sig, ao.perm, n_ant, n_ant_pad, band->n_f, g.n_ab, cw.plan, g.plan, g.C, g.rcs,
+        kc_of(band), conj_c, conj_sig, k0_of(band), g.rows);
     return GERAF_OK;
 }
 
@@ -2328,6 +2372,7 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
     float2* cpart = nullptr;
     float* sbox = nullptr;
     SplitPlan* splan = nullptr;
+    float* srcs = nullptr;
     float2* scs = nullptr;
     int* kmax = nullptr;
     float2* gout = nullptr;
@@ -2339,6 +2384,7 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         cpart = c.take<float2>((size_t)q.splits * n_ant * CH_KMAX);
         sbox = c.take<float>((size_t)q.splits * 6);
         splan = c.take<SplitPlan>(parts);
+        srcs = c.take<float>((size_t)q.splits * n_ant_rec);
         scs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
         kmax = c.take<int>(1);
         gout = c.take<float2>((size_t)((q.splits + RS - 1) / RS) * n_ant * band->n_f);
@@ -2375,19 +2421,20 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_status(e, name);
         split_bbox_kernel<<<q.splits, 256, 0, st>>>(pts, q.n_tiles, q.tiles_per_split, sbox);
-        split_plan_kernel<<<parts, 256, 0, st>>>(sbox, ao.rec, n_ant, q.plan_blocks,
+        split_plan_kernel<<<parts, 256, 0, st>>>(sbox, ao.rec, n_ant, n_ant_rec, q.plan_blocks,
                                                  q.plan_blocks > 1 ? CH_THREADS : n_ant, 2.0 * band->df / kC,
-                                                 band->n_f, CH_TAIL, k0_of(band), cw.plan, splan, scs, kmax);
+                                                 band->n_f, CH_TAIL, k0_of(band), cw.plan, splan, srcs, scs, kmax);
         ChebBinsArgs ca{pts,    ao.rec, n_ant, q.n_tiles, q.tiles_per_split,   cw.plan,
-                        splan,  q.plan_blocks, kmax, k0_of(band), kComplexAmp ? 1.0f : gamma_scale(band),
-                        cpart,  err};
+                        splan,  q.plan_blocks, srcs, n_ant_rec, kmax, k0_of(band),
+                        kComplexAmp ? 1.0f : gamma_scale(band), cpart,  err};
         const dim3 grid(q.ant_blocks, q.splits);
         cheb_bins_kernel<kComplexAmp, 3><<<grid, CH_THREADS, cheb_bins_smem(24), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 4><<<grid, CH_THREADS, cheb_bins_smem(32), st>>>(ca);
         cheb_bins_kernel<kComplexAmp, 8><<<grid, CH_THREADS, cheb_bins_smem(64), st>>>(ca);
         const int groups = (q.splits + RS - 1) / RS;
         cheb_reconstruct_split_kernel<<<dim3((n_ant + RA - 1) / RA, groups), 128, 0, st>>>(
-            cpart, q.splits, n_ant, band->n_f, q.plan_blocks, cw.plan, splan, scs, ao.perm, gout);
+            cpart, q.splits, n_ant, band->n_f, q.plan_blocks, cw.plan, splan, scs, srcs, n_ant_rec, kc_of(band),
+            ao.perm, gout);
         sum_split_groups<<<grid1d((int64_t)n_ant * band->n_f, 256), 256, 0, st>>>(
             gout, groups, (int64_t)n_ant * band->n_f, cw.plan, reinterpret_cast<float2*>(out));
         run_direct = &cw.plan->use_direct;
@@ -2656,6 +2703,7 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     float* xyz_p = c.take<float>((size_t)3 * n);
     float* box = c.take<float>((size_t)n_splits * 6);
     SplitPlan* splan = c.take<SplitPlan>(parts);
+    float* rcs = c.take<float>((size_t)n_splits * n_rec);
     float2* Cs = c.take<float2>((size_t)parts * CH_KMAX * band->n_f);
     int* kmax = c.take<int>(1);
     if (!ws) { *ws_bytes = c.used; return GERAF_OK; }
@@ -2675,8 +2723,8 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_status(e, "chebyshev_work");
     group_bbox_kernel<<<n_splits, 256, 0, st>>>(xyz_p, n, per_part, (float)k0_of(band), box);
-    split_plan_kernel<<<parts, 256, 0, st>>>(box, ao.rec, n_ant, n_ab, ant_per_block, 2.0 * band->df / kC,
-                                             band->n_f, CH_TAIL, k0_of(band), cw.plan, splan, Cs, kmax);
+    split_plan_kernel<<<parts, 256, 0, st>>>(box, ao.rec, n_ant, n_rec, n_ab, ant_per_block, 2.0 * band->df / kC,
+                                             band->n_f, CH_TAIL, k0_of(band), cw.plan, splan, rcs, Cs, kmax);
     geraf_status s = check_launch("chebyshev_work");
     if (s != GERAF_OK) return s;
     ChebPlan h;

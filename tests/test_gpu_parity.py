@@ -143,10 +143,11 @@ def test_render(G, oracle, n_pts, n_ant_side, n_f, directional, method):
     assert rel_l2(host(s), want) < TOL
 
 
-# Range spreads that put the Chebyshev order on either side of its 64-term cap
-# (the direct recurrence kernels run above it; the choice is made on the device):
-# 0.29 m spread -> about 40 terms over 4 GHz; 1.2 m spread -> above 64 terms.
-SPREADS = [((0.0, 0.0, 0.30), 0.12), ((0.0, 0.0, 0.60), 0.50)]
+# Range spreads that put the Chebyshev order in the 32- and 64-order kernel
+# instances and above its 64-term cap (the direct recurrence kernels run above
+# it; the choice is made on the device), over 4 GHz: a 0.24 m cube -> about 27
+# terms, a 0.5 m cube -> about 44, a 1 m cube -> above 64.
+SPREADS = [((0.0, 0.0, 0.30), 0.12), ((0.0, 0.0, 0.35), 0.25), ((0.0, 0.0, 0.60), 0.50)]
 
 
 @pytest.mark.parametrize("centre,half", SPREADS)
@@ -241,14 +242,18 @@ def test_filter_and_backward(G, oracle, n_vox, n_ant_side, n_f, method):
 
 def _host_order(xyz, ant, b, eps=1e-7, kmax=64):
     """Chebyshev order from the bounding box and the Bessel tail, on the host
-    (scipy's J_k): the rule the device plan follows, stated independently."""
+    (scipy's J_k): the rule the device plan follows, stated independently.
+    Each antenna's interval runs from its nearest to its farthest range to the
+    box, about its own centre; the half range dr is the largest half span over
+    the antennas, and the largest Bessel argument is pi (n_f - 1) (2 df / c) dr
+    (bin offsets of at most (n_f - 1) / 2 from the band's centre)."""
     special = pytest.importorskip("scipy.special")
     lo, hi = xyz.min(1).astype(np.float64), xyz.max(1).astype(np.float64)
     a = ant.astype(np.float64)
-    near = np.sqrt((np.maximum(np.maximum(lo[:, None] - a, a - hi[:, None]), 0.0) ** 2).sum(0)).min()
-    far = np.sqrt((np.maximum(np.abs(a - lo[:, None]), np.abs(hi[:, None] - a)) ** 2).sum(0)).max()
-    dr = max(0.5 * (far - near) * 1.001 + 1e-6, 1e-5)
-    amax = 2 * np.pi * (b.n_f - 1) * (2 * b.df / 299792458.0) * dr
+    near = np.sqrt((np.maximum(np.maximum(lo[:, None] - a, a - hi[:, None]), 0.0) ** 2).sum(0))
+    far = np.sqrt((np.maximum(np.abs(a - lo[:, None]), np.abs(hi[:, None] - a)) ** 2).sum(0))
+    dr = max((0.5 * (far - near)).max() * 1.001 + 1e-6, 1e-5)
+    amax = np.pi * (b.n_f - 1) * (2 * b.df / 299792458.0) * dr
     J = np.abs(special.jv(np.arange(kmax + 8), amax))
     tail = np.cumsum((2 * J)[::-1])[::-1]            # tail[k] = sum_{m >= k} 2 |J_m|
     above = np.nonzero(tail > eps)[0]
@@ -266,7 +271,7 @@ def test_chebyshev_order(G, centre, half):
     got = G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b))
     assert abs(got - want) <= 1 and (got == 0) == (want == 0), (got, want)
     b32 = gi.band(77e9, 81e9, 32)
-    if half < 0.2:
+    if want:
         assert 20 <= got <= 64
         # the order follows the band's span, not its bin count
         assert G.geraf_chebyshev_order(cu(xyz), cu(ant), _band(G, b32, 2)) == got
@@ -360,7 +365,7 @@ def test_fmcw_multi_plane_scan(G, oracle, method):
 def test_far_array_split_range_bound(G, oracle, dist, cheb):
     """The Chebyshev kernels form the pair range from coordinates in carrier
     cycles split on a half-cycle grid, exact while every axis difference stays
-    below 1024 cycles (about 2 m at 77 GHz); the device plan sends farther
+    below 1024 cycles (about 1.94 m at the 79 GHz band centre); the device plan sends farther
     calls to the per-bin recurrence kernels. A small array `dist` metres in
     front of the cube: at 1.8 m the Chebyshev form runs, at 2.5 m the
     recurrence does, and both match the oracle."""
@@ -395,13 +400,14 @@ def test_chebyshev_groups_mixed_orders(G, oracle, wide_first):
     """The Chebyshev kernels expand each split of points (to bins) and each
     group of 2048 points or voxels (to points) over its own range interval with
     its own order. Consecutive chunks of 2048 points here lie in clusters of
-    very different range spread (about 40 terms for the wide one, ~10 for the
+    very different range spread (about 44 terms for the wide one, ~8 for the
     compact ones), so the orders differ from group to group and the instance
     chosen by the largest order (K <= 64 with the wide chunk, K <= 24 without)
     runs groups of lower order; 3 x 2048 + 517 points leave a ragged last
     group. Every phasor call against the oracle."""
     rng = np.random.default_rng(31)
-    chunks = [((0.0, 0.0, 0.30), 0.12 if wide_first else 0.01, 2048), ((0.02, -0.01, 0.12), 0.01, 2048),
+    chunks = [((0.0, 0.0, 0.35) if wide_first else (0.0, 0.0, 0.30), 0.25 if wide_first else 0.01, 2048),
+              ((0.02, -0.01, 0.12), 0.01, 2048),
               ((-0.03, 0.02, 0.20), 0.015, 2048), ((0.0, 0.04, 0.16), 0.008, 517)]
     parts = [_scene_points(rng, n, c, h) for c, h, n in chunks]
     xyz, grad, w, t_eff = (np.concatenate([p[i] for p in parts], axis=-1) for i in range(4))
@@ -475,15 +481,15 @@ def test_chebyshev_work_orders(G, wide_first):
     assert G.geraf_chebyshev_work(cu(xyz), cu(ant), _band(G, b, 1), True) == (0, 0, 0, 0.0)
 
 
-@pytest.mark.parametrize("half", [0.025, 0.04, 0.05])
+@pytest.mark.parametrize("half", [0.025, 0.05, 0.08, 0.1])
 def test_chebyshev_even_order_dispatch(G, oracle, half):
     """Each CTA of the Chebyshev kernels runs its part's order rounded up to
     even (at least 8) as a compile-time loop bound. Random points in cubes
-    of half-side 2.5, 4 and 5 cm in front of a 12 x 11 array (132 antennas:
-    two blocks of antenna records, each with its own plan) put the part
-    orders (one 32-point tile x one antenna block to bins, 2048-point groups
-    x one antenna block to points) between about 12 and 26, so most of the
-    even bodies run; every phasor call against the oracle."""
+    of half-side 2.5, 5, 8 and 10 cm in front of a 12 x 11 array (132
+    antennas: two blocks of antenna records, each with its own plan) put the
+    part orders (one 32-point tile x one antenna block to bins, 2048-point
+    groups x one antenna block to points) between about 10 and 25, so most of
+    the even bodies run; every phasor call against the oracle."""
     rng = np.random.default_rng(41)
     n_pts, n_f = 4099, 128
     xyz, grad, w, t_eff = _scene_points(rng, n_pts, (0.0, 0.0, 0.15), half)
