@@ -48,6 +48,25 @@ struct __align__(16) PtRec {
     float4 a, b, c;
 };
 
+// Pair layout of the to-bins Chebyshev records: records 2p and 2p + 1 share
+// 96 bytes, field f (a.x .. c.w, in that order) of record 2p + s at float
+// 24 p + 2 f + s, so that one 16-byte load gives two fields of both points as
+// two packed (f32x2) operands.
+__device__ __forceinline__ void store_rec(PtRec* __restrict__ out, int64_t r, const PtRec& v, bool pair) {
+    if (!pair) {
+        out[r] = v;
+        return;
+    }
+    float* base = reinterpret_cast<float*>(out) + (r >> 1) * 24 + (r & 1);
+    const float f[12] = {v.a.x, v.a.y, v.a.z, v.a.w, v.b.x, v.b.y, v.b.z, v.b.w, v.c.x, v.c.y, v.c.z, v.c.w};
+#pragma unroll
+    for (int q = 0; q < 12; ++q) base[2 * q] = f[q];
+}
+// field f of record r in the pair layout
+__device__ __forceinline__ float pair_field(const PtRec* __restrict__ pts, int64_t r, int f) {
+    return reinterpret_cast<const float*>(pts)[(r >> 1) * 24 + 2 * f + (r & 1)];
+}
+
 // 1/|G| of a directional point (0 for an isotropic one), shared by the pack
 // kernel and the render adjoint's finalize so both see the same value
 __device__ __forceinline__ float inv_grad_norm(float gx, float gy, float gz, int directional) {
@@ -79,14 +98,16 @@ __device__ __forceinline__ void split3p(float x, float y, float z, const int* cy
 }
 
 // --------------------------------------------------------------- pack kernels
-// record j holds point perm[j] (perm NULL: point j)
+// record j holds point perm[j] (perm NULL: point j); with pair set, the
+// records of a Chebyshev call (*cyc_if) take the pair layout (n_pad even)
 __global__ void pack_render_points(const float* __restrict__ xyz, const float* __restrict__ grad,
                                    const float* __restrict__ w, const float* __restrict__ t_eff,
                                    int64_t n, int64_t n_pad, int directional, PtRec* __restrict__ out,
                                    const int* __restrict__ perm = nullptr, const int* cyc_if = nullptr,
-                                   double k0 = 0.0) {
+                                   double k0 = 0.0, int pair = 0) {
     const int64_t r_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r_ >= n_pad) return;
+    const bool pl = pair && cyc_if && *cyc_if;
     const int64_t j = r_ < n && perm ? perm[r_] : r_;
     PtRec r;
     if (r_ < n) {
@@ -106,15 +127,16 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         r.c.w = -1.0f;
     }
-    out[r_] = r;
+    store_rec(out, r_, r, pl);
 }
 
 __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const float2* __restrict__ M,
                                        const float* __restrict__ dP, int64_t n, int64_t n_pad,
                                        PtRec* __restrict__ out, const int* __restrict__ perm = nullptr,
-                                       const int* cyc_if = nullptr, double k0 = 0.0) {
+                                       const int* cyc_if = nullptr, double k0 = 0.0, int pair = 0) {
     const int64_t r_ = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r_ >= n_pad) return;
+    const bool pl = pair && cyc_if && *cyc_if;
     const int64_t j = r_ < n && perm ? perm[r_] : r_;
     PtRec r;
     if (r_ < n) {
@@ -134,7 +156,7 @@ __global__ void pack_filter_bwd_points(const float* __restrict__ vox, const floa
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     r.c.w = 0.0f;
-    out[r_] = r;
+    store_rec(out, r_, r, pl);
 }
 
 // antenna records (x, y, z, c_ant), padded with copies of antenna 0
@@ -1231,46 +1253,89 @@ struct ChebBinsArgs {
 // apply return at once. Each part = (split of points, block of CH_THREADS
 // antennas) expands the bin phase over its own half range (SplitPlan), each
 // antenna about its own range centre (rcs).
-// One tile of CH_TP point records against this thread's antenna: the pair's
-// range in cycles, amplitude times carrier phasor, and the moments
-// M_k += A T_k(x) for k < KE (KE even, fixed at compile time). kGuard (the
-// 64-order instance): orders past 32 run in blocks of 8 up to the part's own
-// order K.
+// This thread's antenna for the to-bins tiles, every value in both lanes:
+// split position in cycles (h, l), c_ant, and its range centre for the part.
+struct BinsAnt {
+    f2 hx, hy, hz, lx, ly, lz, cw, rc;
+};
+
+// One tile of CH_TP point records (pair layout) against this thread's
+// antenna, two points at a time in the two lanes of every packed (f32x2)
+// operation: the pair ranges in double-single (the split-coordinate form of
+// pair_range_split, lane-wise), amplitude times carrier phasor, and the
+// moments M'_k += A V_k for k < KE (KE even, fixed at compile time), V_k =
+// s_k T_k(x) with s_k = (-1)^floor(k/2) by the sign-alternating recurrence
+// V_k = (-/+ 2x) V_{k-1} + V_{k-2} (minus for even k), one packed FMA for both
+// points; the moments themselves are scalar sums over both lanes, and s_k is
+// applied when they are written. Only the square roots, the sincos and the
+// rounding and clamps run per lane. kGuard (the 64-order instance): orders
+// past 32 run in blocks of 8 up to the part's own order K.
 template <bool kComplexAmp, int KM, int KE, bool kGuard>
-__device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const float4& Ah, const float4& Al,
-                                          float aw, float r_c, float inv_dr, int K, float (&mr)[KM],
-                                          float (&mi)[KM]) {
-    for (int p = 0; p < CH_TP; ++p) {
-        const PtRec P = tile[p];
-        const Range R = pair_range_split(P.a.x, P.a.y, P.a.z, P.c.x, P.c.y, P.c.z, Ah.x, Ah.y, Ah.z, Al.x, Al.y,
-                                         Al.z);
-        float ar_, ai_;
-        {
-            const float fr = cyc_frac(R.rh, R.rl);      // carrier phase, cycles
-            float sn, cs;
-            __sincosf(6.28318530717958648f * fr, &sn, &cs);
-            if (!kComplexAmp) {
-                // A / (gamma's constant) = w T'^2 D / r^2: with n' = sqrt2 n,
-                // nd = n'.d / r and D = max(nd^2 - e, 0); u = T' / r
-                const float nd = (P.b.x * R.dx + P.b.y * R.dy + P.b.z * R.dz) * R.rs;
-                const float D = fmaxf(fmaf(nd, nd, -P.c.w), 0.0f);
-                const float u = __saturatef(P.b.w - aw) * R.rs;
-                const float amp = P.a.w * (u * u) * D;
-                ar_ = amp * cs;                          // A exp(-j 2 pi K0 r)
-                ai_ = -amp * sn;
-            } else {
-                const float cr = P.a.w, ci = P.b.x;
-                ar_ = cr * cs + ci * sn;
-                ai_ = ci * cs - cr * sn;
-            }
+__device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const BinsAnt& A, f2 INV, int K,
+                                          float (&mr)[KM], float (&mi)[KM]) {
+    const f2 TWO = pk2(2.0f, 2.0f), NEG1 = pk2(-1.0f, -1.0f), HALF = pk2(0.5f, 0.5f);
+    for (int p = 0; p < CH_TP / 2; ++p) {
+        const ulonglong2* Q = reinterpret_cast<const ulonglong2*>(tile + 6 * p);
+        // fields in pairs: (xh | yh), (zh | w or c_re), (n'x or c_im | n'y), (n'z | t_eff), (xl | yl), (zl | e)
+        const ulonglong2 q0 = Q[0], q1 = Q[1], q2 = Q[2], q4 = Q[4], q5 = Q[5];
+        const f2 hx = sub2(q0.x, A.hx), hy = sub2(q0.y, A.hy), hz = sub2(q1.x, A.hz);
+        const f2 lx = sub2(q4.x, A.lx), ly = sub2(q4.y, A.ly), lz = sub2(q5.x, A.lz);
+        const f2 Sh = fma2(hz, hz, fma2(hy, hy, mul2(hx, hx)));              // exact
+        const f2 cross = fma2(lx, fma2(TWO, hx, lx), fma2(ly, fma2(TWO, hy, ly), mul2(lz, fma2(TWO, hz, lz))));
+        float s0, s1;
+        upk2(add2(Sh, cross), s0, s1);
+        s0 = fmaxf(s0, 1e-30f);
+        s1 = fmaxf(s1, 1e-30f);
+        const f2 S = pk2(s0, s1), RS = pk2(rsqrtf(s0), rsqrtf(s1));
+        const f2 r0 = mul2(S, RS);
+        const f2 rl = mul2(add2(fma2(r0, mul2(r0, NEG1), Sh), cross), mul2(HALF, RS));
+        // carrier phase: the fractional cycle of r0 + rl
+        float a0, a1;
+        upk2(r0, a0, a1);
+        const f2 fr = add2(sub2(r0, pk2(rintf(a0), rintf(a1))), rl);
+        f2 AR, AI;
+        if (!kComplexAmp) {
+            // A / (gamma's constant) = w T'^2 D / r^2: with n' = sqrt2 n,
+            // nd = n'.d / r and D = max(nd^2 - e, 0); u = T' / r;
+            // A exp(-j 2 pi K0 r) from the sincos of the negated angle
+            float f0, f1;
+            upk2(mul2(fr, pk2(-6.28318530717958648f, -6.28318530717958648f)), f0, f1);
+            float sn0, cs0, sn1, cs1;
+            __sincosf(f0, &sn0, &cs0);
+            __sincosf(f1, &sn1, &cs1);
+            const ulonglong2 q3 = Q[3];
+            const f2 dx = add2(hx, lx), dy = add2(hy, ly), dz = add2(hz, lz);
+            const f2 nd = mul2(fma2(q3.x, dz, fma2(q2.y, dy, mul2(q2.x, dx))), RS);
+            float d0, d1, v0, v1;
+            upk2(sub2(mul2(nd, nd), q5.y), d0, d1);
+            upk2(sub2(q3.y, A.cw), v0, v1);
+            const f2 D = pk2(fmaxf(d0, 0.0f), fmaxf(d1, 0.0f));
+            const f2 u = mul2(pk2(__saturatef(v0), __saturatef(v1)), RS);
+            const f2 amp = mul2(q1.y, mul2(mul2(u, u), D));
+            AR = mul2(amp, pk2(cs0, cs1));
+            AI = mul2(amp, pk2(sn0, sn1));
+        } else {
+            float f0, f1;
+            upk2(mul2(fr, pk2(6.28318530717958648f, 6.28318530717958648f)), f0, f1);
+            float sn0, cs0, sn1, cs1;
+            __sincosf(f0, &sn0, &cs0);
+            __sincosf(f1, &sn1, &cs1);
+            const f2 CS = pk2(cs0, cs1), SN = pk2(sn0, sn1);
+            const f2 cr = q1.y, ci = q2.x;
+            AR = fma2(ci, SN, mul2(cr, CS));                                 // c exp(-j 2 pi K0 r)
+            AI = fma2(cr, mul2(SN, NEG1), mul2(ci, CS));
         }
-        const float x = __fmul_rn(__fadd_rn(__fsub_rn(R.rh, r_c), R.rl), inv_dr);
-        const float x2 = 2.0f * x;
-        float tkm1 = 1.0f, tk = x;                       // T_0, T_1
-        mr[0] += ar_;
-        mi[0] += ai_;
-        mr[1] = fmaf(ar_, x, mr[1]);
-        mi[1] = fmaf(ai_, x, mi[1]);
+        const f2 xs = mul2(add2(sub2(r0, A.rc), rl), INV);                   // (r - r_c) / dr
+        float ar0, ar1, ai0, ai1, x0, x1;
+        upk2(AR, ar0, ar1);
+        upk2(AI, ai0, ai1);
+        upk2(xs, x0, x1);
+        mr[0] += ar0 + ar1;
+        mi[0] += ai0 + ai1;
+        mr[1] = fmaf(ar0, x0, fmaf(ar1, x1, mr[1]));
+        mi[1] = fmaf(ai0, x0, fmaf(ai1, x1, mi[1]));
+        const f2 mp = mul2(TWO, xs), mn = mul2(pk2(-2.0f, -2.0f), xs);
+        f2 vkm1 = pk2(1.0f, 1.0f), vk = xs;                                  // V_0, V_1
 #pragma unroll
         for (int kc = 0; kc < KE; kc += 8) {
             if (!kGuard || kc < 32 || kc < K) {
@@ -1278,11 +1343,13 @@ __device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const 
                 for (int kk = 0; kk < 8; ++kk) {
                     const int k = kc + kk;
                     if (k >= 2 && k < KE) {
-                        const float tn = fmaf(x2, tk, -tkm1);
-                        tkm1 = tk;
-                        tk = tn;
-                        mr[k] = fmaf(ar_, tn, mr[k]);
-                        mi[k] = fmaf(ai_, tn, mi[k]);
+                        const f2 vn = fma2((k & 1) ? mp : mn, vk, vkm1);
+                        vkm1 = vk;
+                        vk = vn;
+                        float w0, w1;
+                        upk2(vn, w0, w1);
+                        mr[k] = fmaf(ar0, w0, fmaf(ar1, w1, mr[k]));
+                        mi[k] = fmaf(ai0, w0, fmaf(ai1, w1, mi[k]));
                     }
                 }
             }
@@ -1291,7 +1358,7 @@ __device__ __forceinline__ void bins_tile(const PtRec* __restrict__ tile, const 
 }
 
 #define GERAF_BINS_CASE(E) \
-    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, Ah, Al, A4.w, r_c, inv_dr, K, mr, mi); break;
+    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, BA, INV, K, mr, mi); break;
 
 template <bool kComplexAmp, int KC>
 __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_CH_BINS_CTAS_24
@@ -1319,11 +1386,17 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
     const SplitPlan sp = args.splan[split * args.plan_blocks + (args.plan_blocks > 1 ? blockIdx.x : 0)];
     const int K = sp.K;
     const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
-    const float inv_dr = sp.inv_dr;
+    const f2 INV = pk2(sp.inv_dr, sp.inv_dr);
     const float r_c = args.rcs[(size_t)split * args.n_rec + ia];   // this antenna's range centre
     const float4 A4 = args.ant[ia];                          // padded: always readable
-    float4 Ah, Al;
-    split3c(A4.x, A4.y, A4.z, args.k0, Ah, Al);
+    BinsAnt BA;
+    {
+        float4 Ah, Al;
+        split3c(A4.x, A4.y, A4.z, args.k0, Ah, Al);
+        BA.hx = pk2(Ah.x, Ah.x); BA.hy = pk2(Ah.y, Ah.y); BA.hz = pk2(Ah.z, Ah.z);
+        BA.lx = pk2(Al.x, Al.x); BA.ly = pk2(Al.y, Al.y); BA.lz = pk2(Al.z, Al.z);
+        BA.cw = pk2(A4.w, A4.w); BA.rc = pk2(r_c, r_c);
+    }
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1353,15 +1426,15 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
             }
             return;
         }
-        const PtRec* tile = tiles + buf * CH_TP;
+        const float4* tile = reinterpret_cast<const float4*>(tiles + buf * CH_TP);
         if constexpr (KC == 8) {
-            bins_tile<kComplexAmp, KM, KM, true>(tile, Ah, Al, A4.w, r_c, inv_dr, K, mr, mi);
+            bins_tile<kComplexAmp, KM, KM, true>(tile, BA, INV, K, mr, mi);
         } else {
             switch (ke) {
                 GERAF_BINS_CASE(8) GERAF_BINS_CASE(10) GERAF_BINS_CASE(12) GERAF_BINS_CASE(14)
                 GERAF_BINS_CASE(16) GERAF_BINS_CASE(18) GERAF_BINS_CASE(20) GERAF_BINS_CASE(22)
                 GERAF_BINS_CASE(24) GERAF_BINS_CASE(26) GERAF_BINS_CASE(28) GERAF_BINS_CASE(30)
-                default: bins_tile<kComplexAmp, KM, KM, false>(tile, Ah, Al, A4.w, r_c, inv_dr, K, mr, mi);
+                default: bins_tile<kComplexAmp, KM, KM, false>(tile, BA, INV, K, mr, mi);
             }
         }
         if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
@@ -1384,16 +1457,18 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
         }
     }
     if (ia < args.n_ant) {
+        // M_k = s_k M'_k, s_k = (-1)^floor(k/2)
         float2* dst = args.partial + ((size_t)split * args.n_ant + ia) * CH_KMAX;
         for (int k = 0; k < K; ++k) {
             const float2 o = outer[k * CH_THREADS + t];
-            dst[k] = make_float2(o.x * args.amp_scale, o.y * args.amp_scale);
+            const float sc = ((k >> 1) & 1) ? -args.amp_scale : args.amp_scale;
+            dst[k] = make_float2(o.x * sc, o.y * sc);
         }
     }
 }
 
-// bounding box of each split's records (positions rebuilt exactly as xh + xl;
-// padding records included, they sit at a real point's position)
+// bounding box of each split's records (pair layout; positions rebuilt exactly
+// as xh + xl; padding records included, they sit at a real point's position)
 __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, int tiles_per_split,
                                   float* __restrict__ box) {
     __shared__ float red[6][256];
@@ -1402,8 +1477,9 @@ __global__ void split_bbox_kernel(const PtRec* __restrict__ pts, int n_tiles, in
     const int64_t r1 = min((int64_t)(sp + 1) * tiles_per_split, (int64_t)n_tiles) * CH_TP;
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const PtRec P = pts[r];
-        const float x[3] = {P.a.x + P.c.x, P.a.y + P.c.y, P.a.z + P.c.z};
+        // the pair layout: (xh, yh, zh) are fields 0-2, (xl, yl, zl) fields 8-10
+        const float x[3] = {pair_field(pts, r, 0) + pair_field(pts, r, 8), pair_field(pts, r, 1) + pair_field(pts, r, 9),
+                            pair_field(pts, r, 2) + pair_field(pts, r, 10)};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             mn[d] = fminf(mn[d], x[d]);
@@ -1756,12 +1832,16 @@ __global__ void sum_split_groups(const float2* __restrict__ group_out, int group
 
 size_t cheb_bins_smem(int km) { return 2 * CH_TP * sizeof(PtRec) + 32 + (size_t)km * CH_THREADS * sizeof(float2); }
 
-// antenna rows for the Chebyshev point kernels: two heads, (xh, yh, zh, c) and
-// (xl, yl, zl, 0) (the split position), then CH_KMAX float4
-// s_k (h_re, h_re, h_im, h_im) with h_k = sum_n sig(n) * (conj ? conj(C_k(n)) : C_k(n)),
-// sig = (conj_sig ? conj(v) : v) and s_k = (-1)^floor(k/2), the sign of the
-// point kernels' packed V_k = s_k T_k recurrence
-constexpr int CH_ROW = 2 + CH_KMAX;
+// antenna rows for the Chebyshev point kernels: four heads with every value
+// twice, so that one 16-byte load gives two packed (f32x2) operands:
+// (xh, xh, yh, yh), (zh, zh, c, c), (xl, xl, yl, yl), (zl, zl, r_c, r_c) (the
+// split position, c_ant and the antenna's range centre for the group), then
+// CH_KMAX float4 s_k (h_re, h_re, h_im, h_im) with h_k = sum_n sig(n) * (conj ?
+// conj(C_k(n)) : C_k(n)), sig = (conj_sig ? conj(v) : v) and s_k =
+// (-1)^floor(k/2), the sign of the point kernels' packed V_k = s_k T_k
+// recurrence
+constexpr int CH_HEADS = 4;
+constexpr int CH_ROW = CH_HEADS + CH_KMAX;
 
 // Bounding box of each group of per_group consecutive points (xyz in [3][n]
 // layout): box[g] = (min x, min y, min z, max x, max y, max z).
@@ -1799,8 +1879,8 @@ __global__ void group_bbox_kernel(const float* __restrict__ xyz, int64_t n, int6
 // holds the antenna perm[r] (the spatial order), planned with the part
 // (g, b = r / CH_THREADS) when the groups are planned per antenna block (n_ab
 // blocks), else with the group's plan over all antennas (n_ab = 1):
-// row(g, r) = two heads (the antenna's split position in cycles; c_ant in the
-// first, the record's range centre r_c(g, r) in the second), then for
+// row(g, r) = the heads (the antenna's split position in cycles, c_ant, the
+// record's range centre r_c(g, r); CH_ROW), then for
 // k < CH_KMAX the packed s_k h_k, h_k = sum_n sig(i, n) P(r, n) C_part,k(n),
 // P = exp(-j 2 pi m Kc r_c) the record's bin phase (P and C both conjugated,
 // and sig, on request), zero beyond the part's order and for padding antennas.
@@ -1831,10 +1911,12 @@ __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
             const int q = i < n_ant ? perm[i] : 0;
             float4 hi, lo;
             split3c(ant[q], ant[n_ant + q], ant[2 * n_ant + q], k0, hi, lo);
-            hi.w = c_ant ? c_ant[q] : 0.0f;
-            lo.w = grc[i];
-            grow[(size_t)i * CH_ROW] = hi;
-            grow[(size_t)i * CH_ROW + 1] = lo;
+            const float cw = c_ant ? c_ant[q] : 0.0f, rc = grc[i];
+            float4* h = grow + (size_t)i * CH_ROW;
+            h[0] = make_float4(hi.x, hi.x, hi.y, hi.y);
+            h[1] = make_float4(hi.z, hi.z, cw, cw);
+            h[2] = make_float4(lo.x, lo.x, lo.y, lo.y);
+            h[3] = make_float4(lo.z, lo.z, rc, rc);
         }
     }
     const float kch = (float)kc, kcl = (float)(kc - (double)kch);
@@ -1884,7 +1966,7 @@ __global__ void __launch_bounds__(256) cheb_group_rows_kernel(
         const int i = i0 + r + 4 * q;
         if (i < n_ant_pad) {
             const float hr = sg * ar[q], hi = sg * ai[q];
-            grow[(size_t)i * CH_ROW + 2 + k] = make_float4(hr, hr, hi, hi);
+            grow[(size_t)i * CH_ROW + CH_HEADS + k] = make_float4(hr, hr, hi, hi);
         }
     }
 }
@@ -1912,39 +1994,55 @@ struct ChebPointsArgs {
 // thread = 2 points (the two lanes of the packed Chebyshev sums)
 static_assert(TPK_V == 2, "the packed Chebyshev sums carry two points per thread");
 
-// One tile of AT antenna rows against this thread's two points: the pair
-// ranges, sum_k h_k T_k(x) for k < KE (KE even, fixed at compile time; rows
-// are zero beyond the group's order), the carrier phasor, and the filter or
-// render-adjoint accumulation into in. kGuard (the 64-order instance): orders
-// past 32 run in blocks of 8 up to the group's own order K.
+// A thread's two points, each quantity packed as (point 0, point 1): split
+// position in cycles (h, l), and for the render adjoint the scaled normal
+// n' = sqrt2 n, the transmittance T' and the directional offset, negated (-e).
+struct PtPair {
+    f2 hx, hy, hz, lx, ly, lz;
+    f2 nx, ny, nz, te, ne;
+};
+
+__device__ __forceinline__ f2 dup2(float v) { return pk2(v, v); }
+
+// One tile of AT antenna rows against this thread's two points, both points in
+// the two lanes of every packed (f32x2) operation: the pair ranges in
+// double-single (the split-coordinate form of pair_range_split, lane-wise),
+// sum_k h_k T_k(x) for k < KE (KE even, fixed at compile time; rows are zero
+// beyond the group's order), the carrier phasor, and the filter or
+// render-adjoint accumulation into in. Only the square roots, the sincos and
+// the rounding, clamps and masks run per lane. kGuard (the 64-order
+// instance): orders past 32 run in blocks of 8 up to the group's own order K.
 template <int MODE, int KE, bool kGuard>
-__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, float inv_dr,
-                                            const float4 (&ph)[TPK_V], const float4 (&pl)[TPK_V],
-                                            const float (&pnx)[TPK_V], const float (&pny)[TPK_V],
-                                            const float (&pnz)[TPK_V], const float (&pte)[TPK_V],
-                                            const float (&pe)[TPK_V],
-                                            float (&in)[TPK_V][MODE == MODE_FILTER ? 2 : 5]) {
+__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, f2 INV,
+                                            const PtPair& P, f2 (&in)[MODE == MODE_FILTER ? 2 : 5]) {
     constexpr int ROW = CH_ROW;
+    const f2 TWO = dup2(2.0f), NEG1 = dup2(-1.0f), HALF = dup2(0.5f);
     for (int a = 0; a < AT; ++a) {
-        const float4 head = tile[a * ROW], head_lo = tile[a * ROW + 1];
-        const float r_c = head_lo.w;                     // the antenna's range centre for this group
-        const ulonglong2* hk = reinterpret_cast<const ulonglong2*>(tile + a * ROW + 2);
-        Range R[TPK_V];
-        float xs[TPK_V];
-#pragma unroll
-        for (int v = 0; v < TPK_V; ++v) {
-            R[v] = pair_range_split(ph[v].x, ph[v].y, ph[v].z, pl[v].x, pl[v].y, pl[v].z, head.x, head.y,
-                                    head.z, head_lo.x, head_lo.y, head_lo.z);
-            xs[v] = __fmul_rn(__fadd_rn(__fsub_rn(R[v].rh, r_c), R[v].rl), inv_dr);
-        }
+        const ulonglong2* row = reinterpret_cast<const ulonglong2*>(tile + a * ROW);
+        const ulonglong2 h0 = row[0], h1 = row[1], h2 = row[2], h3 = row[3];
+        // h0 = (xh | yh), h1 = (zh | c_ant), h2 = (xl | yl), h3 = (zl | r_c), each in both lanes
+        const f2 hx = sub2(P.hx, h0.x), hy = sub2(P.hy, h0.y), hz = sub2(P.hz, h1.x);
+        const f2 lx = sub2(P.lx, h2.x), ly = sub2(P.ly, h2.y), lz = sub2(P.lz, h3.x);
+        const f2 Sh = fma2(hz, hz, fma2(hy, hy, mul2(hx, hx)));              // exact
+        const f2 cross = fma2(lx, fma2(TWO, hx, lx), fma2(ly, fma2(TWO, hy, ly), mul2(lz, fma2(TWO, hz, lz))));
+        float s0, s1;
+        upk2(add2(Sh, cross), s0, s1);
+        s0 = fmaxf(s0, 1e-30f);
+        s1 = fmaxf(s1, 1e-30f);
+        const f2 S = pk2(s0, s1), RS = pk2(rsqrtf(s0), rsqrtf(s1));
+        const f2 r0 = mul2(S, RS);                                           // range, leading part
+        const f2 resid = add2(fma2(r0, mul2(r0, NEG1), Sh), cross);
+        const f2 rl = mul2(resid, mul2(HALF, RS));                           // one Newton step: r = r0 + rl
+        const f2 xs = mul2(add2(sub2(r0, h3.y), rl), INV);                   // (r - r_c) / dr
         // sum_k h_k T_k(x) = sum_k (s_k h_k) V_k(x): V_k = s_k T_k for both
         // points in the two lanes of one packed FMA (V_k = (+/-2x) V_{k-1}
         // + V_{k-2}, minus for even k), the products accumulated for both
         // points at once; the rows carry s_k h_k and are zero beyond K,
         // so the loop may run to the next even order
+        const ulonglong2* hk = row + CH_HEADS;
         const ulonglong2 h0u = hk[0], h1u = hk[1];
-        const f2 mp = pk2(2.0f * xs[0], 2.0f * xs[1]), mn = pk2(-2.0f * xs[0], -2.0f * xs[1]);
-        f2 v0 = pk2(1.0f, 1.0f), v1 = pk2(xs[0], xs[1]);
+        const f2 mp = mul2(TWO, xs), mn = mul2(dup2(-2.0f), xs);
+        f2 v0 = dup2(1.0f), v1 = xs;
         f2 Sr = h0u.x, Si = h0u.y;                       // V_0 = 1
         Sr = fma2(v1, h1u.x, Sr);
         Si = fma2(v1, h1u.y, Si);
@@ -1966,48 +2064,58 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
                 }
             }
         }
-        float sr[TPK_V], si[TPK_V];
-        upk2(Sr, sr[0], sr[1]);
-        upk2(Si, si[0], si[1]);
-#pragma unroll
-        for (int v = 0; v < TPK_V; ++v) {
-            const float fr = cyc_frac(R[v].rh, R[v].rl);   // carrier phase, cycles
-            float sn, cs;
-            __sincosf(6.28318530717958648f * fr, &sn, &cs);
-            if (MODE == MODE_FILTER) {
-                // exp(+j 2 pi K0 r) * sum
-                in[v][0] += cs * sr[v] - sn * si[v];
-                in[v][1] += cs * si[v] + sn * sr[v];
-            } else {
-                // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k); with A = w T'^2 gamma D,
-                // gamma = k16 / r^2 and n' = sqrt2 n: the sums below times the
-                // per-point factors (k16, 2 w k16, 2 sqrt2 w k16, sqrt2 w k16) are
-                // dA/dw, dA/dT', and the parts of dA/dn' along d and along n'
-                const float q = cs * sr[v] + sn * si[v];
-                const float inv_r2 = R[v].rs * R[v].rs;
-                const float g = q * inv_r2;
-                const float nd = pnx[v] * R[v].dx + pny[v] * R[v].dy + pnz[v] * R[v].dz;
-                const float Dm = nd * nd * inv_r2 - pe[v];
-                const float D = fmaxf(Dm, 0.0f);
-                const float vv = pte[v] - head.w;
-                const float tt = __saturatef(vv);
-                const float tg = tt * g;
-                const float u = tt * tg;                   // T'^2 g
-                in[v][0] = fmaf(u, D, in[v][0]);
-                if (tt == vv) in[v][1] = fmaf(tg, D, in[v][1]);   // slope region 0 <= t_eff - c_ant <= 1
-                if (pe[v] > 0.0f && Dm > 0.0f) {
-                    const float w2 = u * nd * inv_r2;
-                    in[v][2] = fmaf(w2, R[v].dx, in[v][2]);
-                    in[v][3] = fmaf(w2, R[v].dy, in[v][3]);
-                    in[v][4] = fmaf(w2, R[v].dz, in[v][4]);
-                }
-            }
+        // carrier phase in cycles: the fractional part of r0 + rl
+        float a0, a1;
+        upk2(r0, a0, a1);
+        const f2 fr = add2(sub2(r0, pk2(rintf(a0), rintf(a1))), rl);
+        float f0, f1;
+        upk2(mul2(fr, dup2(6.28318530717958648f)), f0, f1);
+        float sn0, cs0, sn1, cs1;
+        __sincosf(f0, &sn0, &cs0);
+        __sincosf(f1, &sn1, &cs1);
+        const f2 CS = pk2(cs0, cs1), SN = pk2(sn0, sn1);
+        if (MODE == MODE_FILTER) {
+            // exp(+j 2 pi K0 r) * sum
+            in[0] = fma2(CS, Sr, in[0]);
+            in[0] = fma2(mul2(SN, NEG1), Si, in[0]);
+            in[1] = fma2(CS, Si, in[1]);
+            in[1] = fma2(SN, Sr, in[1]);
+        } else {
+            // q = Re(exp(-j 2 pi K0 r) * sum_k T_k H_k); with A = w T'^2 gamma D,
+            // gamma = k16 / r^2 and n' = sqrt2 n: the sums below times the
+            // per-point factors (k16, 2 w k16, 2 sqrt2 w k16, sqrt2 w k16) are
+            // dA/dw, dA/dT', and the parts of dA/dn' along d and along n'
+            const f2 q = fma2(SN, Si, mul2(CS, Sr));
+            const f2 dx = add2(hx, lx), dy = add2(hy, ly), dz = add2(hz, lz);
+            const f2 inv_r2 = mul2(RS, RS);
+            const f2 g = mul2(q, inv_r2);
+            const f2 nd = fma2(P.nz, dz, fma2(P.ny, dy, mul2(P.nx, dx)));
+            const f2 Dm2 = fma2(mul2(nd, nd), inv_r2, P.ne);
+            const f2 vv = sub2(P.te, h1.y);
+            float dm0, dm1, vv0, vv1, ne0, ne1;
+            upk2(Dm2, dm0, dm1);
+            upk2(vv, vv0, vv1);
+            upk2(P.ne, ne0, ne1);
+            const float tt0 = __saturatef(vv0), tt1 = __saturatef(vv1);
+            const f2 D = pk2(fmaxf(dm0, 0.0f), fmaxf(dm1, 0.0f));
+            const f2 tg = mul2(pk2(tt0, tt1), g);
+            const f2 u = mul2(pk2(tt0, tt1), tg);                            // T'^2 g
+            in[0] = fma2(u, D, in[0]);
+            // slope region 0 <= t_eff - c_ant <= 1 only
+            const f2 m1 = pk2(tt0 == vv0 ? 1.0f : 0.0f, tt1 == vv1 ? 1.0f : 0.0f);
+            in[1] = fma2(mul2(tg, D), m1, in[1]);
+            // the directional factor's slope: e > 0 and D > 0 only
+            const f2 m2 = pk2((ne0 < 0.0f && dm0 > 0.0f) ? 1.0f : 0.0f, (ne1 < 0.0f && dm1 > 0.0f) ? 1.0f : 0.0f);
+            const f2 w2 = mul2(mul2(u, nd), mul2(inv_r2, m2));
+            in[2] = fma2(w2, dx, in[2]);
+            in[3] = fma2(w2, dy, in[3]);
+            in[4] = fma2(w2, dz, in[4]);
         }
     }
 }
 
 #define GERAF_POINTS_CASE(E) \
-    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in); break;
+    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, INV, P, in); break;
 
 // Each group of ctas_per_group point CTAs has its own interval and order
 // (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
@@ -2064,22 +2172,25 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             split3c(args.vox[j], args.vox[args.n + j], args.vox[2 * args.n + j], args.k0, ph[v], pl[v]);
             pw[v] = pnx[v] = pny[v] = pnz[v] = pte[v] = pe[v] = 0.0f;
         } else {
-            const PtRec P = args.pts[j];
-            ph[v] = P.a;
-            pl[v] = P.c;
-            pw[v] = P.a.w;
-            pnx[v] = P.b.x; pny[v] = P.b.y; pnz[v] = P.b.z; pte[v] = P.b.w;
-            pe[v] = P.c.w;
+            const PtRec Q = args.pts[j];
+            ph[v] = Q.a;
+            pl[v] = Q.c;
+            pw[v] = Q.a.w;
+            pnx[v] = Q.b.x; pny[v] = Q.b.y; pnz[v] = Q.b.z; pte[v] = Q.b.w;
+            pe[v] = Q.c.w;
         }
     }
+    PtPair P;
+    P.hx = pk2(ph[0].x, ph[1].x); P.hy = pk2(ph[0].y, ph[1].y); P.hz = pk2(ph[0].z, ph[1].z);
+    P.lx = pk2(pl[0].x, pl[1].x); P.ly = pk2(pl[0].y, pl[1].y); P.lz = pk2(pl[0].z, pl[1].z);
+    P.nx = pk2(pnx[0], pnx[1]); P.ny = pk2(pny[0], pny[1]); P.nz = pk2(pnz[0], pnz[1]);
+    P.te = pk2(pte[0], pte[1]); P.ne = pk2(-pe[0], -pe[1]);
     // render adjoint: five sums; the sixth output, sum of w2 (n'.d), is n' dotted
     // with the three sums of w2 d and is formed at the end
     constexpr int NACC = (MODE == MODE_FILTER) ? 2 : 5;
-    float hi[TPK_V][NACC], lo[TPK_V][NACC];
+    f2 hi[NACC], lo[NACC];                                   // Kahan sums over the tiles, both points
 #pragma unroll
-    for (int v = 0; v < TPK_V; ++v)
-#pragma unroll
-        for (int k = 0; k < NACC; ++k) hi[v][k] = lo[v][k] = 0.0f;
+    for (int k = 0; k < NACC; ++k) hi[k] = lo[k] = pk2(0.0f, 0.0f);
 
     for (int it = 0; it < n_my; ++it) {
         const int buf = it & 1;
@@ -2098,32 +2209,27 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             args.gplan[grp * args.n_ab + (args.n_ab > 1 ? ((tile0 + it) * AT) / CH_THREADS : 0)];
         const int K = gp.K;
         const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
-        const float inv_dr = gp.inv_dr;
-        float in[TPK_V][NACC];
+        const f2 INV = dup2(gp.inv_dr);
+        f2 in[NACC];
 #pragma unroll
-        for (int v = 0; v < TPK_V; ++v)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) in[v][k] = 0.0f;
+        for (int k = 0; k < NACC; ++k) in[k] = pk2(0.0f, 0.0f);
         if constexpr (KC == 8) {
-            points_tile<MODE, KM, true>(tile, AT, K, inv_dr, ph, pl, pnx, pny, pnz, pte, pe, in);
+            points_tile<MODE, KM, true>(tile, AT, K, INV, P, in);
         } else {
             switch (ke) {
                 GERAF_POINTS_CASE(8) GERAF_POINTS_CASE(10) GERAF_POINTS_CASE(12) GERAF_POINTS_CASE(14)
                 GERAF_POINTS_CASE(16) GERAF_POINTS_CASE(18) GERAF_POINTS_CASE(20) GERAF_POINTS_CASE(22)
                 GERAF_POINTS_CASE(24) GERAF_POINTS_CASE(26) GERAF_POINTS_CASE(28) GERAF_POINTS_CASE(30)
-                default: points_tile<MODE, KM, false>(tile, AT, K, inv_dr, ph, pl, pnx, pny, pnz, pte, pe,
-                                                      in);
+                default: points_tile<MODE, KM, false>(tile, AT, K, INV, P, in);
             }
         }
 #pragma unroll
-        for (int v = 0; v < TPK_V; ++v)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) {
-                const float y = __fsub_rn(in[v][k], lo[v][k]);
-                const float s = __fadd_rn(hi[v][k], y);
-                lo[v][k] = __fsub_rn(__fsub_rn(s, hi[v][k]), y);
-                hi[v][k] = s;
-            }
+        for (int k = 0; k < NACC; ++k) {
+            const f2 y = sub2(in[k], lo[k]);
+            const f2 sum = add2(hi[k], y);
+            lo[k] = sub2(sub2(sum, hi[k]), y);
+            hi[k] = sum;
+        }
         __syncthreads();
         if (t == 0 && it + 2 < n_my) {
             mbar_arrive_expect_tx(&bar[buf], tile_bytes);
@@ -2135,9 +2241,17 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
     for (int v = 0; v < TPK_V; ++v) {
         const int64_t j = jbase + v;
         if (j >= args.n) continue;
+        float acc[NACC];
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) {
+            float h0, h1, l0, l1;
+            upk2(hi[k], h0, h1);
+            upk2(lo[k], l0, l1);
+            acc[k] = v == 0 ? __fsub_rn(h0, l0) : __fsub_rn(h1, l1);
+        }
         if (MODE == MODE_FILTER) {
             float2* dst = reinterpret_cast<float2*>(args.partial) + (size_t)split * args.n + j;
-            *dst = make_float2(__fsub_rn(hi[v][0], lo[v][0]), __fsub_rn(hi[v][1], lo[v][1]));
+            *dst = make_float2(acc[0], acc[1]);
         } else {
             float* dst = args.partial + (size_t)split * 6 * args.n + j;
             const float wk = pw[v] * args.gscale;
@@ -2145,7 +2259,7 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
                                   kSqrt2 * wk};
             float sum[6];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) sum[k] = __fsub_rn(hi[v][k], lo[v][k]);
+            for (int k = 0; k < 5; ++k) sum[k] = acc[k];
             sum[5] = pnx[v] * sum[2] + pny[v] * sum[3] + pnz[v] * sum[4];
 #pragma unroll
             for (int k = 0; k < 6; ++k) dst[(size_t)k * args.n] = sum[k] * fac[k];
@@ -2409,11 +2523,11 @@ geraf_status to_bins_call(int64_t n_pts, const float* ant_xyz, const float* c_an
         pack_render_points<<<grid1d(n_rec, 256), 256, 0, st>>>(xyz, grad, w, t_eff, n_pts, n_rec,
                                                                (flags & GERAF_RENDER_DIRECTIONAL) ? 1 : 0, pts,
                                                                po.perm, cheb ? &cw.plan->run_cheb : nullptr,
-                                                               k0_of(band));
+                                                               k0_of(band), 1);
     else
         pack_filter_bwd_points<<<grid1d(n_rec, 256), 256, 0, st>>>(vox, M, dP, n_pts, n_rec, pts, po.perm,
                                                                    cheb ? &cw.plan->run_cheb : nullptr,
-                                                                   k0_of(band));
+                                                                   k0_of(band), 1);
     pack_antennas<<<grid1d(n_ant_rec, 256), 256, 0, st>>>(ant_xyz, c_ant, n_ant, n_ant_rec, ant);
     const int* run_direct = nullptr;
     if (cheb) {
