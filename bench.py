@@ -71,6 +71,15 @@ TIMED_CALLS = PHASOR_CALLS + MLP_CALLS
 # the points or voxels processed (the records and partials grow in
 # proportion). Only kernels unchanged since their capture are listed.
 NCU_DRAM = {}
+# Captures whose traffic does not grow in proportion to the points (stated, not
+# scaled): the render adjoint's DRAM reads are mostly its point groups' antenna
+# rows, whose size depends on the group count and the antennas, not the points.
+NCU_DRAM_UNSCALED = {
+    ("c3", "render_backward"): "ncu capture of cheb_points_kernel<1,3> on the same array, band and part "
+                               "rules at 2^20 points (bench.py --phasor-case 128,128,64): 4.91e9 B per launch, "
+                               "4.56e9 B of it the 256 groups' antenna rows (the same 256 groups at 2^24 points); "
+                               "not scaled",
+}
 
 
 def _env_int(k, d):
@@ -860,7 +869,7 @@ def main():
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         calls, dom, fp32_peak, max_mhz, order_of = roofline_of(m, peaks, sm_count)
         fam = "c3" if args.workload.startswith("c3") else "c2"
-        traffic, traffic_basis = None, "no ncu capture of this kernel version"
+        traffic, traffic_basis = None, NCU_DRAM_UNSCALED.get((fam, dom), "no ncu capture of this kernel version")
         if (fam, dom) in NCU_DRAM:
             b_cap, unit, n_cap, basis = NCU_DRAM[(fam, dom)]
             n_full = m["n_pts"] if unit == "points" else m["n_vox"]
