@@ -875,10 +875,11 @@ constexpr int CH_KMAX = 64;
 #ifndef GERAF_CH_BINS_CTAS
 #define GERAF_CH_BINS_CTAS 5
 #endif
-// the render's K <= 24 instance fits six (78 registers, no spills; measured
-// 34.9 against 35.7 ms at C2); the filter adjoint's ran slower at six
+// the render's K <= 24 instance: four (the packed two-point body; six, five and
+// four measured 50.5, 49.1 and 48.0 ms on 2^20 points x the 128 x 128 array;
+// unrolling two record pairs at four, 49.1)
 #ifndef GERAF_CH_BINS_CTAS_24
-#define GERAF_CH_BINS_CTAS_24 6
+#define GERAF_CH_BINS_CTAS_24 4
 #endif
 #ifndef GERAF_CH_FILTER_CTAS
 #define GERAF_CH_FILTER_CTAS 8
@@ -886,6 +887,17 @@ constexpr int CH_KMAX = 64;
 #ifndef GERAF_CH_RBWD_CTAS
 #define GERAF_CH_RBWD_CTAS 4
 #endif
+// unroll factors of the per-tile loops (two points of a record tile to bins,
+// one antenna row to points); unrolling two antenna rows to points measured
+// 64.0 against 63.2 ms on 2^20 points x the 128 x 128 array
+#ifndef GERAF_CH_BINS_UNROLL
+#define GERAF_CH_BINS_UNROLL 1
+#endif
+#ifndef GERAF_CH_PTS_UNROLL
+#define GERAF_CH_PTS_UNROLL 1
+#endif
+constexpr int kBinsUnroll = GERAF_CH_BINS_UNROLL;
+constexpr int kPtsUnroll = GERAF_CH_PTS_UNROLL;
 constexpr int CH_THREADS = 128;
 constexpr int CH_TP = 32;             // points per TMA tile
 constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before it joins the outer sum
@@ -907,11 +919,14 @@ constexpr int CH_FLUSH = 8;           // tiles per inner (register) sum before i
 #ifndef GERAF_CH_SPLIT_MIN_PTS
 #define GERAF_CH_SPLIT_MIN_PTS 8192
 #endif
+// point groups of the to-points sums: up to 512 (one brick each at 2^24
+// points: render adjoint 8.2 orders per pair and 796 ms against 9.8 and 821 ms
+// with 256 groups of two bricks), at most 16 GiB of antenna rows
 #ifndef GERAF_CH_MAX_GROUPS
-#define GERAF_CH_MAX_GROUPS 256
+#define GERAF_CH_MAX_GROUPS 512
 #endif
 #ifndef GERAF_CH_GROUP_ROWS_MIB
-#define GERAF_CH_GROUP_ROWS_MIB 8192
+#define GERAF_CH_GROUP_ROWS_MIB 16384
 #endif
 constexpr size_t CH_PARTIAL_BYTES = (size_t)GERAF_CH_PARTIAL_MIB << 20;   // bound on the split partials of one call
 constexpr size_t CH_TABLE_BYTES = (size_t)GERAF_CH_TABLE_MIB << 20;       // bound on the coefficient tables of one call's parts
@@ -1274,6 +1289,7 @@ template <bool kComplexAmp, int KM, int KE, bool kGuard>
 __device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const BinsAnt& A, f2 INV, int K,
                                           float (&mr)[KM], float (&mi)[KM]) {
     const f2 TWO = pk2(2.0f, 2.0f), NEG1 = pk2(-1.0f, -1.0f), HALF = pk2(0.5f, 0.5f);
+#pragma unroll kBinsUnroll
     for (int p = 0; p < CH_TP / 2; ++p) {
         const ulonglong2* Q = reinterpret_cast<const ulonglong2*>(tile + 6 * p);
         // fields in pairs: (xh | yh), (zh | w or c_re), (n'x or c_im | n'y), (n'z | t_eff), (xl | yl), (zl | e)
@@ -2017,6 +2033,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
                                             const PtPair& P, f2 (&in)[MODE == MODE_FILTER ? 2 : 5]) {
     constexpr int ROW = CH_ROW;
     const f2 TWO = dup2(2.0f), NEG1 = dup2(-1.0f), HALF = dup2(0.5f);
+#pragma unroll kPtsUnroll
     for (int a = 0; a < AT; ++a) {
         const ulonglong2* row = reinterpret_cast<const ulonglong2*>(tile + a * ROW);
         const ulonglong2 h0 = row[0], h1 = row[1], h2 = row[2], h3 = row[3];
