@@ -74,7 +74,12 @@ NCU_DRAM = {}
 # Captures whose traffic does not grow in proportion to the points (stated, not
 # scaled): the render adjoint's DRAM reads are mostly its point groups' antenna
 # rows, whose size depends on the group count and the antennas, not the points.
-NCU_DRAM_UNSCALED = {}
+NCU_DRAM_UNSCALED = {
+    ("c3", "render_backward"): "ncu capture of cheb_points_kernel<1,3> on the same array, band and part "
+                               "rules at 2^20 points (bench.py --phasor-case 128,128,64): 9.32e9 B per launch, "
+                               "9.13e9 B of it the 512 groups' antenna rows (the same 512 groups at 2^24 points); "
+                               "not scaled",
+}
 
 
 def _env_int(k, d):
