@@ -51,7 +51,7 @@ struct __align__(16) PtRec {
 // Pair layout of the to-bins Chebyshev records: records 2p and 2p + 1 share
 // 96 bytes, field f (a.x .. c.w, in that order) of record 2p + s at float
 // 24 p + 2 f + s, so that one 16-byte load gives two fields of both points as
-// two packed (f32x2) operands.
+// two packed (f32x2) operands. The render records hold -e in c.w there.
 __device__ __forceinline__ void store_rec(PtRec* __restrict__ out, int64_t r, const PtRec& v, bool pair) {
     if (!pair) {
         out[r] = v;
@@ -127,6 +127,7 @@ __global__ void pack_render_points(const float* __restrict__ xyz, const float* _
         r.b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         r.c.w = -1.0f;
     }
+    if (pl) r.c.w = -r.c.w;
     store_rec(out, r_, r, pl);
 }
 
@@ -1286,7 +1287,7 @@ struct BinsAnt {
 // rounding and clamps run per lane. kGuard (the 64-order instance): orders
 // past 32 run in blocks of 8 up to the part's own order K.
 template <bool kComplexAmp, int KM, int KE, bool kGuard>
-__device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const BinsAnt& A, f2 INV, int K,
+__device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const BinsAnt& A, f2 INV, f2 HINV, int K,
                                           float (&mr)[KM], float (&mi)[KM]) {
     const f2 TWO = pk2(2.0f, 2.0f), NEG1 = pk2(-1.0f, -1.0f), HALF = pk2(0.5f, 0.5f);
 #pragma unroll kBinsUnroll
@@ -1304,11 +1305,11 @@ __device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const
         s1 = fmaxf(s1, 1e-30f);
         const f2 S = pk2(s0, s1), RS = pk2(rsqrtf(s0), rsqrtf(s1));
         const f2 r0 = mul2(S, RS);
-        const f2 rl = mul2(add2(fma2(r0, mul2(r0, NEG1), Sh), cross), mul2(HALF, RS));
+        const f2 rl2 = mul2(add2(fma2(r0, mul2(r0, NEG1), Sh), cross), RS);    // 2 rl: r = r0 + rl
         // carrier phase: the fractional cycle of r0 + rl
         float a0, a1;
         upk2(r0, a0, a1);
-        const f2 fr = add2(sub2(r0, pk2(rintf(a0), rintf(a1))), rl);
+        const f2 fr = fma2(rl2, HALF, sub2(r0, pk2(rintf(a0), rintf(a1))));
         f2 AR, AI;
         if (!kComplexAmp) {
             // A / (gamma's constant) = w T'^2 D / r^2: with n' = sqrt2 n,
@@ -1323,7 +1324,7 @@ __device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const
             const f2 dx = add2(hx, lx), dy = add2(hy, ly), dz = add2(hz, lz);
             const f2 nd = mul2(fma2(q3.x, dz, fma2(q2.y, dy, mul2(q2.x, dx))), RS);
             float d0, d1, v0, v1;
-            upk2(sub2(mul2(nd, nd), q5.y), d0, d1);
+            upk2(fma2(nd, nd, q5.y), d0, d1);                                // nd^2 - e (records hold -e)
             upk2(sub2(q3.y, A.cw), v0, v1);
             const f2 D = pk2(fmaxf(d0, 0.0f), fmaxf(d1, 0.0f));
             const f2 u = mul2(pk2(__saturatef(v0), __saturatef(v1)), RS);
@@ -1341,7 +1342,7 @@ __device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const
             AR = fma2(ci, SN, mul2(cr, CS));                                 // c exp(-j 2 pi K0 r)
             AI = fma2(cr, mul2(SN, NEG1), mul2(ci, CS));
         }
-        const f2 xs = mul2(add2(sub2(r0, A.rc), rl), INV);                   // (r - r_c) / dr
+        const f2 xs = fma2(rl2, HINV, mul2(sub2(r0, A.rc), INV));             // (r - r_c) / dr
         float ar0, ar1, ai0, ai1, x0, x1;
         upk2(AR, ar0, ar1);
         upk2(AI, ai0, ai1);
@@ -1374,7 +1375,7 @@ __device__ __forceinline__ void bins_tile(const float4* __restrict__ tile, const
 }
 
 #define GERAF_BINS_CASE(E) \
-    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, BA, INV, K, mr, mi); break;
+    case E: bins_tile<kComplexAmp, KM, ((E) < KM ? (E) : KM), false>(tile, BA, INV, HINV, K, mr, mi); break;
 
 template <bool kComplexAmp, int KC>
 __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_CH_BINS_CTAS_24
@@ -1402,7 +1403,7 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
     const SplitPlan sp = args.splan[split * args.plan_blocks + (args.plan_blocks > 1 ? blockIdx.x : 0)];
     const int K = sp.K;
     const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
-    const f2 INV = pk2(sp.inv_dr, sp.inv_dr);
+    const f2 INV = pk2(sp.inv_dr, sp.inv_dr), HINV = pk2(0.5f * sp.inv_dr, 0.5f * sp.inv_dr);
     const float r_c = args.rcs[(size_t)split * args.n_rec + ia];   // this antenna's range centre
     const float4 A4 = args.ant[ia];                          // padded: always readable
     BinsAnt BA;
@@ -1444,13 +1445,13 @@ __global__ void __launch_bounds__(CH_THREADS, (KC == 3 && !kComplexAmp) ? GERAF_
         }
         const float4* tile = reinterpret_cast<const float4*>(tiles + buf * CH_TP);
         if constexpr (KC == 8) {
-            bins_tile<kComplexAmp, KM, KM, true>(tile, BA, INV, K, mr, mi);
+            bins_tile<kComplexAmp, KM, KM, true>(tile, BA, INV, HINV, K, mr, mi);
         } else {
             switch (ke) {
                 GERAF_BINS_CASE(8) GERAF_BINS_CASE(10) GERAF_BINS_CASE(12) GERAF_BINS_CASE(14)
                 GERAF_BINS_CASE(16) GERAF_BINS_CASE(18) GERAF_BINS_CASE(20) GERAF_BINS_CASE(22)
                 GERAF_BINS_CASE(24) GERAF_BINS_CASE(26) GERAF_BINS_CASE(28) GERAF_BINS_CASE(30)
-                default: bins_tile<kComplexAmp, KM, KM, false>(tile, BA, INV, K, mr, mi);
+                default: bins_tile<kComplexAmp, KM, KM, false>(tile, BA, INV, HINV, K, mr, mi);
             }
         }
         if (((it + 1) % CH_FLUSH) == 0 || it + 1 == n_my) {
@@ -2029,7 +2030,7 @@ __device__ __forceinline__ f2 dup2(float v) { return pk2(v, v); }
 // the rounding, clamps and masks run per lane. kGuard (the 64-order
 // instance): orders past 32 run in blocks of 8 up to the group's own order K.
 template <int MODE, int KE, bool kGuard>
-__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, f2 INV,
+__device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int AT, int K, f2 INV, f2 HINV,
                                             const PtPair& P, f2 (&in)[MODE == MODE_FILTER ? 2 : 5]) {
     constexpr int ROW = CH_ROW;
     const f2 TWO = dup2(2.0f), NEG1 = dup2(-1.0f), HALF = dup2(0.5f);
@@ -2049,8 +2050,8 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
         const f2 S = pk2(s0, s1), RS = pk2(rsqrtf(s0), rsqrtf(s1));
         const f2 r0 = mul2(S, RS);                                           // range, leading part
         const f2 resid = add2(fma2(r0, mul2(r0, NEG1), Sh), cross);
-        const f2 rl = mul2(resid, mul2(HALF, RS));                           // one Newton step: r = r0 + rl
-        const f2 xs = mul2(add2(sub2(r0, h3.y), rl), INV);                   // (r - r_c) / dr
+        const f2 rl2 = mul2(resid, RS);                                      // one Newton step: r = r0 + rl2 / 2
+        const f2 xs = fma2(rl2, HINV, mul2(sub2(r0, h3.y), INV));             // (r - r_c) / dr
         // sum_k h_k T_k(x) = sum_k (s_k h_k) V_k(x): V_k = s_k T_k for both
         // points in the two lanes of one packed FMA (V_k = (+/-2x) V_{k-1}
         // + V_{k-2}, minus for even k), the products accumulated for both
@@ -2084,7 +2085,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
         // carrier phase in cycles: the fractional part of r0 + rl
         float a0, a1;
         upk2(r0, a0, a1);
-        const f2 fr = add2(sub2(r0, pk2(rintf(a0), rintf(a1))), rl);
+        const f2 fr = fma2(rl2, HALF, sub2(r0, pk2(rintf(a0), rintf(a1))));
         float f0, f1;
         upk2(mul2(fr, dup2(6.28318530717958648f)), f0, f1);
         float sn0, cs0, sn1, cs1;
@@ -2118,12 +2119,14 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
             const f2 tg = mul2(pk2(tt0, tt1), g);
             const f2 u = mul2(pk2(tt0, tt1), tg);                            // T'^2 g
             in[0] = fma2(u, D, in[0]);
-            // slope region 0 <= t_eff - c_ant <= 1 only
-            const f2 m1 = pk2(tt0 == vv0 ? 1.0f : 0.0f, tt1 == vv1 ? 1.0f : 0.0f);
-            in[1] = fma2(mul2(tg, D), m1, in[1]);
+            // slope region 0 <= t_eff - c_ant <= 1 only (a per-lane select)
+            float tg0, tg1;
+            upk2(tg, tg0, tg1);
+            in[1] = fma2(pk2(tt0 == vv0 ? tg0 : 0.0f, tt1 == vv1 ? tg1 : 0.0f), D, in[1]);
             // the directional factor's slope: e > 0 and D > 0 only
-            const f2 m2 = pk2((ne0 < 0.0f && dm0 > 0.0f) ? 1.0f : 0.0f, (ne1 < 0.0f && dm1 > 0.0f) ? 1.0f : 0.0f);
-            const f2 w2 = mul2(mul2(u, nd), mul2(inv_r2, m2));
+            float w0, w1;
+            upk2(mul2(mul2(u, nd), inv_r2), w0, w1);
+            const f2 w2 = pk2((ne0 < 0.0f && dm0 > 0.0f) ? w0 : 0.0f, (ne1 < 0.0f && dm1 > 0.0f) ? w1 : 0.0f);
             in[2] = fma2(w2, dx, in[2]);
             in[3] = fma2(w2, dy, in[3]);
             in[4] = fma2(w2, dz, in[4]);
@@ -2132,7 +2135,7 @@ __device__ __forceinline__ void points_tile(const float4* __restrict__ tile, int
 }
 
 #define GERAF_POINTS_CASE(E) \
-    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, INV, P, in); break;
+    case E: points_tile<MODE, ((E) < KM ? (E) : KM), false>(tile, AT, K, INV, HINV, P, in); break;
 
 // Each group of ctas_per_group point CTAs has its own interval and order
 // (gplan) and its own antenna rows. KC = 8-order groups compiled in: the KC = 3
@@ -2226,18 +2229,18 @@ __global__ void __launch_bounds__(TPK_THREADS, KC <= 4 ? (MODE == MODE_FILTER ? 
             args.gplan[grp * args.n_ab + (args.n_ab > 1 ? ((tile0 + it) * AT) / CH_THREADS : 0)];
         const int K = gp.K;
         const int ke = K <= 8 ? 8 : (K + 1) & ~1;                // orders run: K rounded up to even, >= 8
-        const f2 INV = dup2(gp.inv_dr);
+        const f2 INV = dup2(gp.inv_dr), HINV = dup2(0.5f * gp.inv_dr);
         f2 in[NACC];
 #pragma unroll
         for (int k = 0; k < NACC; ++k) in[k] = pk2(0.0f, 0.0f);
         if constexpr (KC == 8) {
-            points_tile<MODE, KM, true>(tile, AT, K, INV, P, in);
+            points_tile<MODE, KM, true>(tile, AT, K, INV, HINV, P, in);
         } else {
             switch (ke) {
                 GERAF_POINTS_CASE(8) GERAF_POINTS_CASE(10) GERAF_POINTS_CASE(12) GERAF_POINTS_CASE(14)
                 GERAF_POINTS_CASE(16) GERAF_POINTS_CASE(18) GERAF_POINTS_CASE(20) GERAF_POINTS_CASE(22)
                 GERAF_POINTS_CASE(24) GERAF_POINTS_CASE(26) GERAF_POINTS_CASE(28) GERAF_POINTS_CASE(30)
-                default: points_tile<MODE, KM, false>(tile, AT, K, INV, P, in);
+                default: points_tile<MODE, KM, false>(tile, AT, K, INV, HINV, P, in);
             }
         }
 #pragma unroll
