@@ -493,13 +493,20 @@ __global__ void __launch_bounds__(256) whbar_kernel(WNet g, int l, int64_t n, in
     }
 }
 
+// the per-split parameter-gradient partials summed in split order, Kahan
+// compensated in FP32 (deterministic; FP64 is a small fraction of FP32 here)
 __global__ void wreduce_partials(const float* __restrict__ partial, int n_split, int64_t stride, int64_t n,
                                  float* __restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = 0.0;
-    for (int c = 0; c < n_split; ++c) s += partial[(int64_t)c * stride + i];
-    out[i] = (float)s;
+    float acc = 0.0f, cmp = 0.0f;
+    for (int c = 0; c < n_split; ++c) {
+        const float y = partial[(int64_t)c * stride + i] - cmp;
+        const float t = acc + y;
+        cmp = (t - acc) - y;
+        acc = t;
+    }
+    out[i] = acc - cmp;
 }
 
 inline unsigned gdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

@@ -342,17 +342,25 @@ __global__ void __launch_bounds__(WT, 1) wtc_gemm_kernel(const WtcArgs a) {
                     }
                     put_row8(a.z, a.z_kc, a.zt, a.zt_kc, row, u0 + 8 * g8, v, valid);
                 }
-            } else if (a.mode == WTC_DZ) {
-                if (row < a.rows_valid)
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (u0 + i < a.n_valid) a.out[row * a.ld + u0 + i] = acc[i];
             } else {
-                if (row < a.rows_valid) {
-                    float* dst = a.partial + (size_t)blockIdx.x * a.p_stride + a.p_off + (size_t)row * a.n_valid;
+                // the row's 32 columns: 16-byte stores where the row is 16-byte
+                // aligned and the block lies in the written columns, else scalar
+                float* dst = nullptr;
+                if (a.mode == WTC_DZ) {
+                    if (row < a.rows_valid) dst = a.out + row * a.ld;
+                } else if (row < a.rows_valid) {
+                    dst = a.partial + (size_t)blockIdx.x * a.p_stride + a.p_off + (size_t)row * a.n_valid;
+                }
+                if (dst) {
+                    if (u0 + 32 <= a.n_valid && (reinterpret_cast<uintptr_t>(dst + u0) & 15u) == 0) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (u0 + i < a.n_valid) dst[u0 + i] = acc[i];
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4*>(dst + u0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (u0 + i < a.n_valid) dst[u0 + i] = acc[i];
+                    }
                 }
             }
         }
@@ -441,11 +449,12 @@ __global__ void __launch_bounds__(256) wtc_hbar_kernel(const float* __restrict__
     }
 }
 
-// bias gradient of a layer: the 64-row block sums in FP64. Block = 32 units x
+// bias gradient of a layer: the 64-row block sums. Block = 32 units x
 // BR_SLICES slices of the row blocks; each thread sums its slice in block
-// order, the slices are added in slice order, so the result does not depend
-// on the launch.
-constexpr int BR_SLICES = 8;
+// order with Kahan compensation in FP32 (FP64 is a small fraction of FP32 on
+// this part), the slices are added in slice order in FP64, so the result does
+// not depend on the launch.
+constexpr int BR_SLICES = 32;
 __global__ void __launch_bounds__(32 * BR_SLICES) wtc_bias_reduce(const float* __restrict__ bsum, int64_t n_blocks,
                                                                   int W, float* __restrict__ out) {
     __shared__ double part[BR_SLICES][32];
@@ -453,10 +462,15 @@ __global__ void __launch_bounds__(32 * BR_SLICES) wtc_bias_reduce(const float* _
     const int u = blockIdx.x * 32 + lu;
     const int64_t per = (n_blocks + BR_SLICES - 1) / BR_SLICES;
     const int64_t b0 = sl * per, b1 = min(n_blocks, b0 + per);
-    double acc = 0.0;
+    float acc = 0.0f, cmp = 0.0f;
     if (u < W)
-        for (int64_t b = b0; b < b1; ++b) acc += bsum[(size_t)b * W + u];
-    part[sl][lu] = acc;
+        for (int64_t b = b0; b < b1; ++b) {
+            const float y = bsum[(size_t)b * W + u] - cmp;
+            const float t = acc + y;
+            cmp = (t - acc) - y;
+            acc = t;
+        }
+    part[sl][lu] = (double)acc - (double)cmp;
     __syncthreads();
     if (sl == 0 && u < W) {
         double s = 0.0;
@@ -579,13 +593,20 @@ __global__ void __launch_bounds__(256) wtc_head_bwd_kernel(TNet g, int64_t n, in
     }
 }
 
+// the per-split parameter-gradient partials summed in split order, Kahan
+// compensated in FP32 (deterministic; FP64 is a small fraction of FP32 here)
 __global__ void wtc_reduce_partials(const float* __restrict__ partial, int n_split, int64_t stride, int64_t n,
                                     float* __restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double acc = 0.0;
-    for (int c = 0; c < n_split; ++c) acc += partial[(int64_t)c * stride + i];
-    out[i] = (float)acc;
+    float acc = 0.0f, cmp = 0.0f;
+    for (int c = 0; c < n_split; ++c) {
+        const float y = partial[(int64_t)c * stride + i] - cmp;
+        const float t = acc + y;
+        cmp = (t - acc) - y;
+        acc = t;
+    }
+    out[i] = acc - cmp;
 }
 
 inline unsigned tdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
