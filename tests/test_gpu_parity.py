@@ -444,8 +444,8 @@ def test_chebyshev_groups_mixed_orders(G, oracle, wide_first):
 def test_chebyshev_work_orders(G, wide_first):
     """geraf_chebyshev_work against the order rule stated on the host: the
     largest group order (groups of 2048 points, to points) and the largest
-    part order (splits of one 32-point tile here: 72 antennas leave one
-    antenna block, so the plan cuts the points into single tiles), the kernel
+    part order (splits of one 128-point record tile here: 72 antennas leave
+    one antenna block, so the plan cuts the points into single tiles), the kernel
     instance that follows from it and the mean orders per pair. Parts are
     runs of consecutive records in the brick order (brick_order)."""
     rng = np.random.default_rng(31)
@@ -459,7 +459,7 @@ def test_chebyshev_work_orders(G, wide_first):
     band = _band(G, b, 2)
     K = G.geraf_chebyshev_order(cu(xyz), cu(ant), band)
     inst_of = lambda km: 24 if km <= 24 else (32 if km <= 32 else 64)
-    for to_points, per in ((True, 2048), (False, 32)):
+    for to_points, per in ((True, 2048), (False, 128)):
         k0, km, inst, mean = G.geraf_chebyshev_work(cu(xyz), cu(ant), band, to_points)
         assert k0 == K
         xs = xyz[:, brick_order(xyz)]
@@ -487,7 +487,7 @@ def test_chebyshev_even_order_dispatch(G, oracle, half):
     even (at least 8) as a compile-time loop bound. Random points in cubes
     of half-side 2.5, 5, 8 and 10 cm in front of a 12 x 11 array (132
     antennas: two blocks of antenna records, each with its own plan) put the
-    part orders (one 32-point tile x one antenna block to bins, 2048-point
+    part orders (one 128-point tile x one antenna block to bins, 2048-point
     groups x one antenna block to points) between about 10 and 25, so most of
     the even bodies run; every phasor call against the oracle."""
     rng = np.random.default_rng(41)
@@ -531,7 +531,7 @@ def test_render_antenna_block_plans(G, oracle):
     """With splits of at least 8192 points the to-bins kernels plan each
     (split, 128-antenna block) over its own range interval: 128 x 128 x 40
     ray-ordered stratified samples against the 64 x 64 array (4096 antennas,
-    32 blocks) give 76 splits of 8640 points. The oracle computes the signal
+    32 blocks) give 80 splits of 8192 points. The oracle computes the signal
     of 48 antennas spread over the blocks; the GPU computes all of them."""
     g = gi.cube_grid((0.0, 0.0, 0.15), 0.10, (128, 128, 40))
     xyz, _ = oracle.sample(g, gi.SAMPLE_STRATIFIED, seed=3, step=0)
