@@ -843,6 +843,24 @@ ToPointsPlan plan_to_points(int64_t n, int n_ant, int G) {
     return p;
 }
 
+// Antenna tiles of the Chebyshev to-points kernels: CH_PT_AT rows of 1 KB
+// (the per-bin recurrence kernels' rows hold every bin and take p.at), with
+// the same splits of the antenna tiles as the recurrence plan, so both
+// paths leave p.splits partials per point (a split with no tiles writes
+// zeros).
+struct ChebPointsTiles {
+    int at, n_ant_pad, n_ant_tiles, tiles_per_split;
+};
+constexpr int CH_PT_AT = 16;
+ChebPointsTiles cheb_points_tiles(const ToPointsPlan& p, int n_ant) {
+    ChebPointsTiles q;
+    q.at = CH_PT_AT;
+    q.n_ant_pad = std::max(p.n_ant_pad, (n_ant + CH_PT_AT - 1) / CH_PT_AT * CH_PT_AT);
+    q.n_ant_tiles = q.n_ant_pad / CH_PT_AT;
+    q.tiles_per_split = (q.n_ant_tiles + p.splits - 1) / p.splits;
+    return q;
+}
+
 // ==================================================== Chebyshev phasor sums
 // Per antenna i, the frequency dependence of a term is exp(-j 2 pi f_n 2 r / c)
 // with f_n = f_c + m df, f_c the band's centre and m = n - (n_f - 1) / 2. The
@@ -2614,6 +2632,7 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
     const bool cheb = use_cheb(band);
     ToPointsPlan p = plan_to_points(n_vox, n_ant, bk.g);
+    const ChebPointsTiles cq = cheb_points_tiles(p, n_ant);
     WsCarver c(ws);
     float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
     float2* part = c.take<float2>((size_t)p.splits * n_vox);
@@ -2626,8 +2645,8 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
     float* vox_p = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_vox);
-        pg = take_point_groups(c, p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
-        ao = take_ant_order(c, n_ant, p.n_ant_pad);
+        pg = take_point_groups(c, p.pt_ctas, n_ant, cq.n_ant_pad, band->n_f);
+        ao = take_ant_order(c, n_ant, cq.n_ant_pad);
         po = take_point_order(c, n_vox);
         vox_p = c.take<float>((size_t)3 * n_vox);
     }
@@ -2646,13 +2665,13 @@ geraf_status filter_impl(const float* s, const float* ant_xyz, int32_t n_ant, co
         launch_point_order(po, vox, cw.plan, st);
         gather_xyz<<<grid1d(n_vox, 256), 256, 0, st>>>(vox, n_vox, po.perm, vox_p);
         launch_ant_order(ao, ant_xyz, nullptr, n_ant, st);
-        const geraf_status gs = launch_point_groups(pg, cw, ao, vox_p, n_vox, ant_xyz, nullptr, n_ant, p.n_ant_pad,
+        const geraf_status gs = launch_point_groups(pg, cw, ao, vox_p, n_vox, ant_xyz, nullptr, n_ant, cq.n_ant_pad,
                                                     band, reinterpret_cast<const float2*>(s), 1, 0, st);
         if (gs != GERAF_OK) return gs;
-        ChebPointsArgs ca{nullptr, vox_p, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, p.at, p.n_ant_tiles,
-                          p.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, k0_of(band), 1.0f,
+        ChebPointsArgs ca{nullptr, vox_p, n_vox, pg.rows, pg.group_rows, pg.ctas_per_group, cq.at, cq.n_ant_tiles,
+                          cq.tiles_per_split, cw.plan, pg.plan, pg.n_ab, pg.kmax, k0_of(band), 1.0f,
                           reinterpret_cast<float*>(part), err};
-        const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
+        const size_t smem = 32 + 2 * (size_t)cq.at * CH_ROW * sizeof(float4);
         cheb_points_kernel<MODE_FILTER, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_FILTER, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_FILTER, 8><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
@@ -2679,6 +2698,7 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     if (!make_band_k(band, &bk)) return GERAF_ERR_INVALID_ARG;
     const bool cheb = use_cheb(band);
     ToPointsPlan p = plan_to_points(n_pts, n_ant, bk.g);
+    const ChebPointsTiles cq = cheb_points_tiles(p, n_ant);
     WsCarver c(ws);
     PtRec* pts = c.take<PtRec>((size_t)n_pts);
     float4* rows = c.take<float4>((size_t)p.n_ant_pad * p.row_f4);
@@ -2690,8 +2710,8 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     float* xyz_p = nullptr;
     if (cheb) {
         cw = take_cheb(c, n_pts);
-        pg = take_point_groups(c, p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
-        ao = take_ant_order(c, n_ant, p.n_ant_pad);
+        pg = take_point_groups(c, p.pt_ctas, n_ant, cq.n_ant_pad, band->n_f);
+        ao = take_ant_order(c, n_ant, cq.n_ant_pad);
         po = take_point_order(c, n_pts);
         xyz_p = c.take<float>((size_t)3 * n_pts);
     }
@@ -2718,13 +2738,13 @@ geraf_status render_backward_impl(const float* xyz, const float* grad, const flo
     const int* run_direct = nullptr;
     if (cheb) {
         launch_ant_order(ao, ant_xyz, c_ant, n_ant, st);
-        const geraf_status gs = launch_point_groups(pg, cw, ao, xyz_p, n_pts, ant_xyz, c_ant, n_ant, p.n_ant_pad,
+        const geraf_status gs = launch_point_groups(pg, cw, ao, xyz_p, n_pts, ant_xyz, c_ant, n_ant, cq.n_ant_pad,
                                                     band, reinterpret_cast<const float2*>(g_s), 0, 1, st);
         if (gs != GERAF_OK) return gs;
         ChebPointsArgs ca{pts,     nullptr,  n_pts,      pg.rows,     pg.group_rows,       pg.ctas_per_group,
-                          p.at,    p.n_ant_tiles, p.tiles_per_split, cw.plan, pg.plan, pg.n_ab,
+                          cq.at,   cq.n_ant_tiles, cq.tiles_per_split, cw.plan, pg.plan, pg.n_ab,
                           pg.kmax, k0_of(band),   gamma_scale(band), part,    err};
-        const size_t smem = 32 + 2 * (size_t)p.at * CH_ROW * sizeof(float4);
+        const size_t smem = 32 + 2 * (size_t)cq.at * CH_ROW * sizeof(float4);
         cheb_points_kernel<MODE_RENDER_BWD, 3><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_RENDER_BWD, 4><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
         cheb_points_kernel<MODE_RENDER_BWD, 8><<<dim3(p.pt_ctas, p.splits), TPK_THREADS, smem, st>>>(ca);
@@ -2824,11 +2844,11 @@ geraf_status chebyshev_work_impl(const float* xyz, int64_t n, const float* ant_x
     int64_t per_part = 0;
     if (to_points) {
         const ToPointsPlan p = plan_to_points(n, n_ant, bk.g);
-        const PointGroups g = plan_point_groups(p.pt_ctas, n_ant, p.n_ant_pad, band->n_f);
+        const PointGroups g = plan_point_groups(p.pt_ctas, n_ant, cheb_points_tiles(p, n_ant).n_ant_pad, band->n_f);
         n_ab = g.n_ab;
         parts = g.parts;
         per_part = (int64_t)g.ctas_per_group * TPK_THREADS * TPK_V;
-        n_rec = p.n_ant_pad;
+        n_rec = cheb_points_tiles(p, n_ant).n_ant_pad;
     } else {
         const int64_t n_pad = (n + CH_TP - 1) / CH_TP * CH_TP;
         const ToBinsPlan p = plan_to_bins(n_pad, n_ant, bk.g);
