@@ -24,7 +24,7 @@
  *   geraf_last_error_string() gives a one-line description of the last error
  *   on the calling thread. No exception crosses the ABI.
  * - Results are deterministic: no floating-point atomics; split reductions are
- *   summed in a fixed order in FP64.
+ *   summed in a fixed order (in FP64, or in FP32 with Kahan compensation).
  */
 #ifndef GERAF_H
 #define GERAF_H
@@ -65,12 +65,14 @@ typedef struct {
  * rounding:
  *   GERAF_PHASOR_RECURRENCE: exact phasor per bin by angle-addition
  *     recurrence, re-seeded from a sincos every 32 bins;
- *   GERAF_PHASOR_CHEBYSHEV: the bin phase exp(-j 2 pi n df 2r/c) expanded in
- *     Chebyshev polynomials of the range (Jacobi-Anger, terms kept until the
- *     Bessel tail is below 1e-7, under the FP32 rounding of the sums), each
- *     run of consecutive points against each block of 128 antennas (taken
- *     in a spatial order of their positions) over its own range interval,
- *     so the work per (point, antenna) pair follows the
+ *   GERAF_PHASOR_CHEBYSHEV: the bin phase about the band's centre f_c,
+ *     exp(-j 2 pi (n - (n_f - 1) / 2) df 2r/c), expanded in Chebyshev
+ *     polynomials of the range (Jacobi-Anger, terms kept until the Bessel
+ *     tail is below 1e-7, under the FP32 rounding of the sums), each run of
+ *     consecutive points against each block of 128 antennas (taken in a
+ *     spatial order of their positions) with its own half range, each
+ *     antenna's interval centred on that antenna's own ranges, so the work
+ *     per (point, antenna) pair follows the
  *     order instead of n_f; when the whole call's order K would exceed 64
  *     the recurrence runs instead (decided on the device;
  *     geraf_chebyshev_order reports the choice, geraf_chebyshev_work the
@@ -342,8 +344,10 @@ geraf_status geraf_masked_loss(const float* P, const float* target, float* histo
  * points (or voxels) xyz [3][n] against ant_xyz [3][n_ant] over `band`
  * (band->method honoured): *order = K (2..64) when the Chebyshev form runs,
  * 0 when the recurrence runs (method RECURRENCE, AUTO with n_f < 64, or an
- * order above 64). Runs the same device-side plan as the sums (range bound
- * from the points' bounding box and the antennas, Bessel tail below 1e-7),
+ * order above 64). Runs the same device-side plan as the sums (the largest
+ * half range over the antennas from the points' bounding box, each antenna's
+ * interval about its own centre; the largest Bessel argument at the bins
+ * (n_f - 1) / 2 from the band's centre; Bessel tail below 1e-7),
  * then waits for the stream: synchronous. The paper has no counterpart; this
  * reports the cost model of a call. ws: ws == NULL queries *ws_bytes.
  */
