@@ -343,25 +343,26 @@ __global__ void __launch_bounds__(WT, 1) wtc_gemm_kernel(const WtcArgs a) {
                     put_row8(a.z, a.z_kc, a.zt, a.zt_kc, row, u0 + 8 * g8, v, valid);
                 }
             } else {
-                // the row's 32 columns: 16-byte stores where the row is 16-byte
-                // aligned and the block lies in the written columns, else scalar
-                float* dst = nullptr;
-                if (a.mode == WTC_DZ) {
-                    if (row < a.rows_valid) dst = a.out + row * a.ld;
-                } else if (row < a.rows_valid) {
-                    dst = a.partial + (size_t)blockIdx.x * a.p_stride + a.p_off + (size_t)row * a.n_valid;
-                }
-                if (dst) {
-                    if (u0 + 32 <= a.n_valid && (reinterpret_cast<uintptr_t>(dst + u0) & 15u) == 0) {
+                // the warp's 32 rows x 32 columns through a padded shared-memory
+                // transpose (the stage ring, free once every MMA has completed),
+                // so that each store writes 32 consecutive columns of one row
+                float* tb = reinterpret_cast<float*>(sm) + warp * 32 * 33;
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4)
-                            *reinterpret_cast<float4*>(dst + u0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (u0 + i < a.n_valid) dst[u0 + i] = acc[i];
+                for (int i = 0; i < 32; ++i) tb[lane * 33 + i] = acc[i];
+                __syncwarp();
+                const int64_t row0 = mb * WB + warp * 32;
+                const bool col_ok = u0 + lane < a.n_valid;
+                for (int i = 0; i < 32; ++i) {
+                    const int64_t r = row0 + i;
+                    if (r < a.rows_valid && col_ok) {
+                        const float v = tb[i * 33 + lane];
+                        if (a.mode == WTC_DZ)
+                            a.out[r * a.ld + u0 + lane] = v;
+                        else
+                            a.partial[(size_t)blockIdx.x * a.p_stride + a.p_off + (size_t)r * a.n_valid + u0 + lane] = v;
                     }
                 }
+                __syncwarp();
             }
         }
     }
