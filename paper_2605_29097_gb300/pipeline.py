@@ -16,13 +16,15 @@ from . import geraf as G
 # kernel launches made by one call of each entry point (for launch accounting)
 LAUNCHES = {"sample": 1, "fields": 1, "blend": 2, "render": 4, "filter": 4, "filter_backward": 4,
             "render_backward": 4, "blend_backward": 2}
-# with the Chebyshev form each phasor call adds the range bound, the plan and
-# the moment kernels (the to-bins calls per-split bounds and plans, three
-# kernel instances and a split-group sum; the to-points calls per-group bounds,
-# plans and antenna rows and three kernel instances; the instances that do not
-# apply return at once); the recurrence kernels are still launched and return at
-# once unless the device-side plan falls back to them
-LAUNCHES_CHEBYSHEV = {"render": 13, "filter": 12, "filter_backward": 13, "render_backward": 12}
+# with the Chebyshev form each phasor call launches: the whole-call range bound
+# and plan (2), the points' brick-order sort (4), the antenna order (2), the
+# record packs, the part bounds and plans, three kernel instances (those that
+# do not apply return at once), the to-bins reconstruction and split-group sum
+# or the to-points antenna rows, and the recurrence kernels and their
+# reduction (launched either way; they return at once unless the device-side
+# plan falls back to them): 19 per call, counted from the launch list of one
+# step of the 256^3-sample workload (90 launches per step with the 4x128 network)
+LAUNCHES_CHEBYSHEV = {"render": 19, "filter": 19, "filter_backward": 19, "render_backward": 19}
 
 
 def uses_chebyshev(band) -> bool:
