@@ -114,12 +114,13 @@ __device__ __forceinline__ void split_coord(float x, float& h, float& l) {
 }
 
 // Coordinate split in carrier cycles (the Chebyshev kernels): X = K0 x with
-// K0 = 2 f0 / c cycles per metre (FP64 product of the FP32 coordinate),
+// K0 = 2 f_c / c cycles per metre at the band centre f_c (FP64 product of the
+// FP32 coordinate),
 // X = h + l with h on the half-cycle grid (exact in FP32 below 2^22 cycles)
 // and l the FP32 rounding of the remainder (|l| <= 1/4 cycle, about 0.5 mm).
 // Differences of two h are exact, and so is the sum of their three squares
 // (multiples of 1/4 below 3 * 2^20) while every axis difference is below 1024
-// cycles (about 2 m at 77 GHz); the kernels' plan falls back to the exact
+// cycles (about 1.94 m at 79 GHz); the kernels' plan falls back to the exact
 // recurrence kernels beyond that. A range in cycles makes the carrier phase
 // its fractional part (cyc_frac).
 constexpr double kCycGrid = 2.0;

@@ -1278,7 +1278,7 @@ struct ChebBinsArgs {
     const float* rcs;          // [splits][n_rec]: each antenna record's range centre (cycles)
     int n_rec;
     const int* kmax;           // largest part order: picks the kernel instance
-    double k0;                 // K0 = 2 f0 / c, cycles per metre (positions in cycles)
+    double k0;                 // K0 = 2 f_c / c at the band centre f_c, cycles per metre (positions in cycles)
     float amp_scale;           // factor of every moment: gamma's 1 / (16 pi^2) per square cycle (render), 1
     float2* partial;           // [splits][n_ant][CH_KMAX]
     int* err;
@@ -2030,7 +2030,7 @@ struct ChebPointsArgs {
     const SplitPlan* gplan;    // per part (group, antenna block): interval and order
     int n_ab;                  // antenna blocks of CH_THREADS records with their own plan (1: one per group)
     const int* kmax;           // largest part order
-    double k0;                 // K0 = 2 f0 / c, cycles per metre (positions in cycles)
+    double k0;                 // K0 = 2 f_c / c at the band centre f_c, cycles per metre (positions in cycles)
     float gscale;              // gamma's 1 / (16 pi^2) per square cycle (render adjoint)
     float* partial;
     int* err;
