@@ -2500,7 +2500,7 @@ ChebBinsPlan plan_cheb_bins(int64_t n_pad, int n_ant, int n_f) {
     q.tiles_per_split = (int)((q.n_tiles + sp - 1) / sp);
     q.splits = (q.n_tiles + q.tiles_per_split - 1) / q.tiles_per_split;
     // a plan per (split, antenna block) pays when a part holds enough pairs to
-    // outweigh its FP64 plan (Bessel values of every bin): splits of at least
+    // outweigh its plan (Bessel values of every bin): splits of at least
     // 8192 points, and at most CH_TABLE_BYTES of tables; otherwise one plan per split
     const int64_t max_parts = std::max<int64_t>(1, (int64_t)(CH_TABLE_BYTES / ((size_t)CH_KMAX * n_f * 8)));
     const bool blocks = (int64_t)q.tiles_per_split * CH_TP >= GERAF_CH_SPLIT_MIN_PTS && (int64_t)q.splits * q.ant_blocks <= max_parts;
